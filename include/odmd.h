@@ -1,0 +1,146 @@
+/*
+ * odmd.h -- C ABI of the online dynamic mode decomposition (DMD) library for GB300.
+ *
+ * The library keeps a DMD model of a snapshot stream u^0, u^1, ... on one GPU and
+ * updates it with one rank-1 step per snapshot, as in Suh, Chung, Bremer, Choi,
+ * "Accelerating Flow Simulations using Online Dynamic Mode Decomposition" (NeurIPS
+ * 2023 ML4PS workshop), Section 2.3:
+ *
+ *   U^- = [u^0 .. u^{m-1}] ~ L S R^T  (truncated SVD, rank r <= r_max)
+ *   U^+ = [u^1 .. u^m]
+ *   A~_r = L^T U^+ R S^{-1} = V Lambda V^{-1},  Phi = L V
+ *   u(t) = Phi Lambda^t Phi^+ u(0)     (t in steps, counted from u^0)
+ *
+ * and exposes the credibility test of Section 2.2 as a relative L2 distance between a
+ * prediction and a full-order-model (FOM) snapshot.  The update is Brand's rank-1
+ * append (the method Section 2.3 adopts), kept in product form L = L0 Q: the tall
+ * basis L0 (N x r0) only gains columns, the small r0 x r factor Q absorbs the
+ * rotations, and L0 is compacted to L0 Q when r0 reaches r_max + slack.
+ *
+ * Conventions for every call
+ * --------------------------
+ * - Every function returns an odmd_status and never aborts.  ODMD_OK is 0.
+ * - "device" pointers are CUDA global-memory addresses of the GPU the handle was
+ *   created on; "host" pointers are ordinary CPU memory.  The caller owns all of them.
+ * - Work is enqueued on the handle's stream (a cudaStream_t passed as void*; NULL is
+ *   the legacy default stream).  Calls that return numbers to the host (check, get_*,
+ *   sync) synchronise that stream; the others are asynchronous.  A device-side error
+ *   (non-finite input, a solver that did not converge) is recorded on the device and
+ *   reported by the next synchronising call.
+ * - A handle is not thread-safe; different handles may be used concurrently.
+ * - Snapshot element type: double for ODMD_FP64, float for ODMD_FP32 and ODMD_BF16.
+ *   Snapshots are contiguous vectors of n elements.
+ */
+#ifndef ODMD_H
+#define ODMD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct odmd_instance* odmd_t;
+
+typedef enum {
+  ODMD_OK = 0,
+  ODMD_ERR_ARG = 1,      /* bad argument (null pointer, size out of range, misalignment) */
+  ODMD_ERR_STATE = 2,    /* call not valid in the current state (e.g. predict before a model exists) */
+  ODMD_ERR_NOMEM = 3,    /* workspace too small, or a host allocation failed */
+  ODMD_ERR_CUDA = 4,     /* a CUDA runtime call failed; see odmd_last_error */
+  ODMD_ERR_NUMERIC = 5,  /* non-finite input or result, or an ill-conditioned eigenbasis */
+  ODMD_ERR_TIMEOUT = 6   /* a bounded device-side wait ran out */
+} odmd_status;
+
+/* Storage of the tall basis L0 (the arithmetic of the tall passes is always
+ * compensated: products are formed exactly and summed in a two-float accumulator).
+ *   ODMD_FP64: basis as an unevaluated sum of two floats (hi + lo, 48-bit significand),
+ *              snapshots and outputs double.
+ *   ODMD_FP32: basis float, snapshots and outputs float.
+ *   ODMD_BF16: basis bfloat16, snapshots and outputs float.
+ * The small solves (core SVD, operator update, eigensolve) are FP64 in every mode. */
+typedef enum { ODMD_FP64 = 0, ODMD_FP32 = 1, ODMD_BF16 = 2 } odmd_precision;
+
+typedef struct {
+  int64_t n;            /* state length N, 1 <= n <= 2^31 - 1 */
+  int32_t r_max;        /* rank cap, 1 <= r_max <= 64 */
+  int32_t slack;        /* extra basis columns before compaction, 0 <= slack <= 32
+                           (0: the tall basis is rotated on every update at full rank) */
+  double trunc_tol;     /* tau: a new direction enters iff rho > tau*max(sigma_1, ||c||);
+                           singular values <= tau*sigma_1 are dropped.  1e-13 <= tau < 1 */
+  double check_tol;     /* default tolerance of odmd_check (Sec. 3 uses 1e-5) */
+  odmd_precision prec;  /* basis storage, see above */
+  int32_t refine_every; /* re-orthonormalise L0 every this many compactions (0: never) */
+  uint32_t flags;       /* reserved, must be 0 */
+} odmd_config;
+
+/* Fill *cfg with the defaults for a stream of length n and rank cap r_max:
+ * slack 16, trunc_tol 1e-10, check_tol 1e-5, ODMD_FP64, refine_every 0, flags 0. */
+odmd_status odmd_config_default(odmd_config* cfg, int64_t n, int32_t r_max);
+
+/* Device bytes the handle needs (the workspace passed to odmd_create), so that a caller
+ * can admit instances against free HBM before allocating anything. */
+odmd_status odmd_footprint(const odmd_config* cfg, size_t* device_bytes);
+
+/* Create a handle.  workspace_dev: device memory of at least odmd_footprint() bytes,
+ * 256-byte aligned, owned by the caller and not touched by anyone else until
+ * odmd_destroy returns; the library allocates no device memory of its own.  The
+ * workspace is initialised on `stream` (asynchronously).  *out receives the handle. */
+odmd_status odmd_create(const odmd_config* cfg, void* workspace_dev, size_t bytes,
+                        void* stream, odmd_t* out);
+
+/* Append snapshot u^k (device, n elements of the snapshot type, any alignment).
+ * The first call stores u^0; every later call adds the pair (u^{k-1}, u^k): U^- gains
+ * u^{k-1}, U^+ gains u^k, and the model is updated by one rank-1 step (Sec. 2.3).
+ * The snapshot is copied into the workspace on the stream, so the caller may reuse
+ * its buffer once the stream has passed this call. */
+odmd_status odmd_update(odmd_t h, const void* x_dev);
+
+/* Predict u(t_j) = Re(Phi Lambda^{t_j} Phi^+ u^0) for j < k (Sec. 2.3).  t_host: k step
+ * counts from u^0 (host, any real value >= 0).  out_dev: device, column j at
+ * out_dev + j*ld elements of the snapshot type, ld >= n.  Needs a model (two
+ * snapshots with a nonzero first one); the eigendecomposition is recomputed lazily
+ * after updates.  Asynchronous. */
+odmd_status odmd_predict(odmd_t h, const double* t_host, int32_t k, void* out_dev, int64_t ld);
+
+/* Credibility check (Sec. 2.2): rel_err = ||u(t) - x_fom|| / ||x_fom|| (0 if both are
+ * zero, +inf if only x_fom is), pass = rel_err <= tol (tol <= 0 selects the handle's
+ * check_tol).  x_fom_dev: device snapshot.  The prediction is never written to memory.
+ * Synchronises the stream; both outputs are host pointers (either may be NULL). */
+odmd_status odmd_check(odmd_t h, double t, const void* x_fom_dev, double tol,
+                       double* rel_err, int32_t* pass);
+
+/* Wait for the handle's stream and report any recorded device-side error. */
+odmd_status odmd_sync(odmd_t h);
+
+/* Current rank r (synchronises). */
+odmd_status odmd_get_rank(odmd_t h, int32_t* r);
+
+/* Singular values S (descending, host, up to cap of them) and the rank (synchronises). */
+odmd_status odmd_get_singular_values(odmd_t h, double* s_host, int32_t cap, int32_t* r);
+
+/* DMD eigenvalues Lambda (host re/im arrays, up to cap) and, if amp_host is not NULL,
+ * each mode's amplitude |b_i| ||Phi e_i|| with b = Phi^+ u^0 (synchronises). */
+odmd_status odmd_get_eigs(odmd_t h, double* re_host, double* im_host, double* amp_host,
+                          int32_t cap, int32_t* r);
+
+/* Write the orthonormal basis L = L0 Q (n x r, column-major, leading dimension ld >= n,
+ * snapshot type) to out_dev and its rank to *r (synchronises to learn r first; out_dev
+ * must hold r_max columns). */
+odmd_status odmd_get_basis(odmd_t h, void* out_dev, int64_t ld, int32_t* r);
+
+/* Number of snapshots received and number of compactions performed (host counters). */
+odmd_status odmd_get_counts(odmd_t h, int64_t* snapshots, int64_t* compactions);
+
+/* Release the handle (synchronises first).  The workspace is the caller's again. */
+odmd_status odmd_destroy(odmd_t h);
+
+/* Message describing the last error on this handle (or the last global error if h is
+ * NULL).  The string lives until the next call on the same handle. */
+const char* odmd_last_error(odmd_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ODMD_H */

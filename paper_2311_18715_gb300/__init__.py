@@ -1,0 +1,16 @@
+"""GB300-native online dynamic mode decomposition (hot path of arXiv 2311.18715).
+
+The C ABI lives in include/odmd.h and libodmd.so (built in-tree by ``build()``);
+``OnlineDMD`` wraps it for torch tensors.
+"""
+from ._build import build
+from ._lib import EXPORTED, OdmdError, load_library
+
+__all__ = ["build", "load_library", "OdmdError", "EXPORTED", "OnlineDMD"]
+
+
+def __getattr__(name):
+    if name == "OnlineDMD":
+        from .odmd import OnlineDMD
+        return OnlineDMD
+    raise AttributeError(name)

@@ -1,0 +1,83 @@
+"""ctypes declarations of the C ABI in include/odmd.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from ._build import LIB
+
+ODMD_OK = 0
+STATUS_NAMES = {0: "ODMD_OK", 1: "ODMD_ERR_ARG", 2: "ODMD_ERR_STATE", 3: "ODMD_ERR_NOMEM",
+                4: "ODMD_ERR_CUDA", 5: "ODMD_ERR_NUMERIC", 6: "ODMD_ERR_TIMEOUT"}
+PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
+
+EXPORTED = [
+    "odmd_config_default", "odmd_footprint", "odmd_create", "odmd_update", "odmd_predict",
+    "odmd_check", "odmd_sync", "odmd_get_rank", "odmd_get_singular_values", "odmd_get_eigs",
+    "odmd_get_basis", "odmd_get_counts", "odmd_destroy", "odmd_last_error",
+]
+
+
+class OdmdConfig(C.Structure):
+    _fields_ = [
+        ("n", C.c_int64),
+        ("r_max", C.c_int32),
+        ("slack", C.c_int32),
+        ("trunc_tol", C.c_double),
+        ("check_tol", C.c_double),
+        ("prec", C.c_int),
+        ("refine_every", C.c_int32),
+        ("flags", C.c_uint32),
+    ]
+
+
+class OdmdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str | None = None) -> C.CDLL:
+    """Load libodmd.so; raises if it has not been built (there is no fallback)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB
+    if not os.path.exists(p):
+        raise ImportError(f"{p} is missing: build it with paper_2311_18715_gb300.build()")
+    lib = C.CDLL(p)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    cfgp = C.POINTER(OdmdConfig)
+    sig = {
+        "odmd_config_default": [cfgp, i64, i32],
+        "odmd_footprint": [cfgp, C.POINTER(C.c_size_t)],
+        "odmd_create": [cfgp, vp, C.c_size_t, vp, C.POINTER(vp)],
+        "odmd_update": [vp, vp],
+        "odmd_predict": [vp, C.POINTER(dbl), i32, vp, i64],
+        "odmd_check": [vp, dbl, vp, dbl, C.POINTER(dbl), C.POINTER(i32)],
+        "odmd_sync": [vp],
+        "odmd_get_rank": [vp, C.POINTER(i32)],
+        "odmd_get_singular_values": [vp, C.POINTER(dbl), i32, C.POINTER(i32)],
+        "odmd_get_eigs": [vp, C.POINTER(dbl), C.POINTER(dbl), C.POINTER(dbl), i32, C.POINTER(i32)],
+        "odmd_get_basis": [vp, vp, i64, C.POINTER(i32)],
+        "odmd_get_counts": [vp, C.POINTER(i64), C.POINTER(i64)],
+        "odmd_destroy": [vp],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    lib.odmd_last_error.argtypes = [vp]
+    lib.odmd_last_error.restype = C.c_char_p
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def check(lib, status: int, handle=None) -> None:
+    if status != ODMD_OK:
+        msg = lib.odmd_last_error(handle)
+        raise OdmdError(status, msg.decode() if msg else "")

@@ -1,0 +1,493 @@
+// C ABI of libodmd: argument checks, workspace layout, call sequencing.  Every O(N)
+// or O(r^3) step runs in the kernels of tall.cu and small.cu; this file only decides
+// which kernels to enqueue and carries a few bytes between host and device.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/odmd.h"
+#include "odmd_internal.cuh"
+
+using namespace odmd;
+
+struct odmd_instance {
+  odmd_config cfg;
+  Ws ws;
+  cudaStream_t stream;
+  int device;
+  int64_t nsnap;       // snapshots received
+  int64_t compactions; // host mirror is refreshed at sync points
+  int cur_h;           // host mirror of Ctl::cur (flips on every update after the first)
+  int curc_h;          // host mirror of Ctl::cur_c
+  bool eig_dirty;
+  double* pinned;      // 8 doubles of pinned host memory for read-backs
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Layout {
+  size_t total;
+  size_t off_ctl, off_hdr[2], off_state[2], off_small, off_eig, off_out2, off_part, off_Lh, off_Ll, off_c[2],
+      off_x;
+  size_t state_doubles, small_bytes, eig_doubles;
+  int64_t npad;
+  int ldg, cap, rmax, partrows;
+};
+
+constexpr int kPartRows = 512;
+
+int esz_of(int prec) { return prec == ODMD_BF16 ? 2 : 4; }
+int vsz_of(int prec) { return prec == ODMD_FP64 ? 8 : 4; }
+
+odmd_status check_cfg(const odmd_config* c, std::string& why) {
+  if (!c) {
+    why = "config is NULL";
+    return ODMD_ERR_ARG;
+  }
+  if (c->n < 1 || c->n > 2147483647LL) {
+    why = "n out of range [1, 2^31-1]";
+    return ODMD_ERR_ARG;
+  }
+  if (c->r_max < 1 || c->r_max > kMaxR) {
+    why = "r_max out of range [1, 64]";
+    return ODMD_ERR_ARG;
+  }
+  if (c->slack < 0 || c->slack > kMaxSlack) {
+    why = "slack out of range [0, 32]";
+    return ODMD_ERR_ARG;
+  }
+  if (!(c->trunc_tol >= 1e-13 && c->trunc_tol < 1.0)) {
+    why = "trunc_tol out of range [1e-13, 1)";
+    return ODMD_ERR_ARG;
+  }
+  if (c->prec != ODMD_FP64 && c->prec != ODMD_FP32 && c->prec != ODMD_BF16) {
+    why = "unknown precision";
+    return ODMD_ERR_ARG;
+  }
+  if (c->flags != 0) {
+    why = "flags must be 0";
+    return ODMD_ERR_ARG;
+  }
+  if (c->refine_every < 0) {
+    why = "refine_every must be >= 0";
+    return ODMD_ERR_ARG;
+  }
+  return ODMD_OK;
+}
+
+Layout make_layout(const odmd_config& c) {
+  Layout L{};
+  L.cap = c.r_max + c.slack;
+  L.rmax = c.r_max;
+  L.ldg = (int)align_up((size_t)L.cap, 8);
+  L.npad = (int64_t)align_up((size_t)c.n, kTile);
+  L.partrows = kPartRows;
+  const int qld = L.cap + 1;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = align_up(o + bytes, 256);
+    return at;
+  };
+  L.off_ctl = take(sizeof(Ctl));
+  L.off_hdr[0] = take(sizeof(StateHdr));
+  L.off_hdr[1] = take(sizeof(StateHdr));
+  L.state_doubles = 3 * (size_t)L.rmax + (size_t)L.rmax * L.rmax + (size_t)qld * L.rmax + qld;
+  L.off_state[0] = take(L.state_doubles * 8);
+  L.off_state[1] = take(L.state_doubles * 8);
+  // small scratch: doubles then ints
+  const size_t nd = (2 * (size_t)L.cap + 3) + 3 * (size_t)qld + 9 * (size_t)kMaxN + 2 * (size_t)kMaxN +
+                    2 * (size_t)kMaxN * kMaxN + (size_t)qld * L.rmax + (size_t)qld * kRollK;
+  const size_t ni = 6 * (size_t)kMaxN;
+  L.small_bytes = nd * 8 + ni * 4;
+  L.off_small = take(L.small_bytes);
+  L.eig_doubles = 4 * (size_t)L.rmax + 2 * (size_t)L.rmax * L.rmax;
+  L.off_eig = take(L.eig_doubles * 8);
+  L.off_out2 = take(8 * 8);
+  L.off_part = take((size_t)L.partrows * (2 * L.cap + 3) * sizeof(float2));
+  const size_t plane = (size_t)L.npad * L.ldg * esz_of(c.prec);
+  L.off_Lh = take(plane);
+  L.off_Ll = c.prec == ODMD_FP64 ? take(plane) : 0;
+  const size_t snap = (size_t)L.npad * vsz_of(c.prec);
+  L.off_c[0] = take(snap);
+  L.off_c[1] = take(snap);
+  L.off_x = take(snap);
+  L.total = o;
+  return L;
+}
+
+void carve(Ws& ws, const Layout& L, unsigned char* base, const odmd_config& c, int gridA) {
+  ws.n = c.n;
+  ws.npad = L.npad;
+  ws.rmax = L.rmax;
+  ws.cap = L.cap;
+  ws.ldg = L.ldg;
+  ws.prec = (int)c.prec;
+  ws.gridA = gridA;
+  ws.tau = c.trunc_tol;
+  ws.ctl = reinterpret_cast<Ctl*>(base + L.off_ctl);
+  const int qld = L.cap + 1;
+  for (int b = 0; b < 2; ++b) {
+    StateBuf& s = ws.st[b];
+    s.hdr = reinterpret_cast<StateHdr*>(base + L.off_hdr[b]);
+    double* d = reinterpret_cast<double*>(base + L.off_state[b]);
+    s.S = d;
+    d += L.rmax;
+    s.rf = d;
+    d += L.rmax;
+    s.rl = d;
+    d += L.rmax;
+    s.M = d;
+    d += (size_t)L.rmax * L.rmax;
+    s.Q = d;
+    d += (size_t)qld * L.rmax;
+    s.a = d;
+  }
+  double* d = reinterpret_cast<double*>(base + L.off_small);
+  Small& sm = ws.sm;
+  sm.red = d;
+  d += 2 * L.cap + 3;
+  sm.ac = d;
+  d += qld;
+  sm.yext = d;
+  d += qld;
+  sm.qn = d;
+  d += qld;
+  sm.p = d;
+  d += kMaxN;
+  sm.w = d;
+  d += kMaxN;
+  sm.d = d;
+  d += kMaxN;
+  sm.z = d;
+  d += kMaxN;
+  sm.zrot = d;
+  d += kMaxN;
+  sm.rot_c = d;
+  d += kMaxN;
+  sm.rot_s = d;
+  d += kMaxN;
+  sm.mu = d;
+  d += kMaxN;
+  sm.zhat = d;
+  d += kMaxN;
+  sm.sig = d;
+  d += 2 * kMaxN;
+  sm.U = d;
+  d += (size_t)kMaxN * kMaxN;
+  sm.V = d;
+  d += (size_t)kMaxN * kMaxN;
+  sm.QB = d;
+  d += (size_t)qld * L.rmax;
+  sm.coef = d;
+  d += (size_t)qld * kRollK;
+  int* ip = reinterpret_cast<int*>(d);
+  sm.pole = ip;
+  ip += kMaxN;
+  sm.defl = ip;
+  ip += kMaxN;
+  sm.rot_i = ip;
+  ip += kMaxN;
+  sm.rot_j = ip;
+  ip += kMaxN;
+  sm.org = ip;
+  ip += kMaxN;
+  sm.src = ip;
+  double* e = reinterpret_cast<double*>(base + L.off_eig);
+  ws.eig.lre = e;
+  e += L.rmax;
+  ws.eig.lim = e;
+  e += L.rmax;
+  ws.eig.bre = e;
+  e += L.rmax;
+  ws.eig.bim = e;
+  e += L.rmax;
+  ws.eig.Vre = e;
+  e += (size_t)L.rmax * L.rmax;
+  ws.eig.Vim = e;
+  ws.eig.work = nullptr;
+  ws.out2 = reinterpret_cast<double*>(base + L.off_out2);
+  ws.part = reinterpret_cast<float2*>(base + L.off_part);
+  ws.Lh = base + L.off_Lh;
+  ws.Ll = c.prec == ODMD_FP64 ? reinterpret_cast<float*>(base + L.off_Ll) : nullptr;
+  ws.cbuf[0] = base + L.off_c[0];
+  ws.cbuf[1] = base + L.off_c[1];
+  ws.xbuf = base + L.off_x;
+}
+
+odmd_status fail(odmd_t h, odmd_status s, const std::string& msg) {
+  if (h)
+    h->err = msg;
+  else
+    g_err = msg;
+  return s;
+}
+
+odmd_status cuda_fail(odmd_t h, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  return fail(h, ODMD_ERR_CUDA, m);
+}
+
+#define CK(h, call, where)                          \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, where); \
+  } while (0)
+
+// Read and clear the device status word (synchronises the stream).
+odmd_status device_status(odmd_t h) {
+  CK(h, cudaMemcpyAsync(h->pinned + 7, &h->ws.ctl->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream),
+     "status read");
+  CK(h, cudaStreamSynchronize(h->stream), "stream sync");
+  int st = 0;
+  std::memcpy(&st, h->pinned + 7, sizeof(int));
+  if (st == 0) return ODMD_OK;
+  CK(h, cudaMemsetAsync(&h->ws.ctl->status, 0, sizeof(int), h->stream), "status clear");
+  char buf[160];
+  std::snprintf(buf, sizeof buf, "device status 0x%x (%s%s%s%s%s%s)", st, (st & DEV_NONFINITE) ? "non-finite " : "",
+                (st & DEV_TIMEOUT) ? "timeout " : "", (st & DEV_EIG_NOCONV) ? "eig-no-convergence " : "",
+                (st & DEV_EIG_COND) ? "singular-eigenbasis " : "", (st & DEV_SECULAR) ? "secular-no-convergence " : "",
+                (st & DEV_NOMODEL) ? "no-model" : "");
+  if (st & DEV_TIMEOUT) return fail(h, ODMD_ERR_TIMEOUT, buf);
+  if (st & DEV_NOMODEL) return fail(h, ODMD_ERR_STATE, buf);
+  return fail(h, ODMD_ERR_NUMERIC, buf);
+}
+
+odmd_status ensure_eig(odmd_t h) {
+  if (!h->eig_dirty) return ODMD_OK;
+  CK(h, launch_eig(h->ws, h->stream), "eig launch");
+  h->eig_dirty = false;
+  return ODMD_OK;
+}
+
+size_t snap_bytes(const odmd_t h) { return (size_t)h->cfg.n * vsz_of(h->cfg.prec); }
+
+}  // namespace
+
+extern "C" {
+
+odmd_status odmd_config_default(odmd_config* cfg, int64_t n, int32_t r_max) {
+  if (!cfg) return fail(nullptr, ODMD_ERR_ARG, "config is NULL");
+  std::memset(cfg, 0, sizeof *cfg);
+  cfg->n = n;
+  cfg->r_max = r_max;
+  cfg->slack = 16;
+  cfg->trunc_tol = 1e-10;
+  cfg->check_tol = 1e-5;
+  cfg->prec = ODMD_FP64;
+  cfg->refine_every = 0;
+  cfg->flags = 0;
+  return ODMD_OK;
+}
+
+odmd_status odmd_footprint(const odmd_config* cfg, size_t* device_bytes) {
+  std::string why;
+  if (odmd_status s = check_cfg(cfg, why)) return fail(nullptr, s, why);
+  if (!device_bytes) return fail(nullptr, ODMD_ERR_ARG, "device_bytes is NULL");
+  *device_bytes = make_layout(*cfg).total;
+  return ODMD_OK;
+}
+
+odmd_status odmd_create(const odmd_config* cfg, void* workspace_dev, size_t bytes, void* stream, odmd_t* out) {
+  std::string why;
+  if (odmd_status s = check_cfg(cfg, why)) return fail(nullptr, s, why);
+  if (!out) return fail(nullptr, ODMD_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!workspace_dev) return fail(nullptr, ODMD_ERR_ARG, "workspace is NULL");
+  if (reinterpret_cast<uintptr_t>(workspace_dev) % 256 != 0)
+    return fail(nullptr, ODMD_ERR_ARG, "workspace must be 256-byte aligned");
+  const Layout L = make_layout(*cfg);
+  if (bytes < L.total) return fail(nullptr, ODMD_ERR_NOMEM, "workspace smaller than odmd_footprint()");
+  odmd_instance* h = new (std::nothrow) odmd_instance();
+  if (!h) return fail(nullptr, ODMD_ERR_NOMEM, "host allocation failed");
+  h->cfg = *cfg;
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  h->nsnap = 0;
+  h->compactions = 0;
+  h->cur_h = 0;
+  h->curc_h = 0;
+  h->eig_dirty = true;
+  cudaError_t e = cudaGetDevice(&h->device);
+  int sms = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&h->pinned), 8 * sizeof(double));
+  if (e != cudaSuccess) {
+    std::string m = std::string("create: ") + cudaGetErrorString(e);
+    delete h;
+    return fail(nullptr, ODMD_ERR_CUDA, m);
+  }
+  const int64_t ntiles = (cfg->n + kTile - 1) / kTile;
+  int gridA = (int)(ntiles < sms ? ntiles : sms);
+  if (gridA > kPartRows) gridA = kPartRows;
+  if (gridA < 1) gridA = 1;
+  carve(h->ws, L, reinterpret_cast<unsigned char*>(workspace_dev), *cfg, gridA);
+  e = cudaMemsetAsync(workspace_dev, 0, L.total, h->stream);
+  if (e != cudaSuccess) {
+    cudaFreeHost(h->pinned);
+    std::string m = std::string("create memset: ") + cudaGetErrorString(e);
+    delete h;
+    return fail(nullptr, ODMD_ERR_CUDA, m);
+  }
+  *out = h;
+  return ODMD_OK;
+}
+
+odmd_status odmd_update(odmd_t h, const void* x_dev) {
+  if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
+  if (!x_dev) return fail(h, ODMD_ERR_ARG, "x is NULL");
+  const size_t nb = snap_bytes(h);
+  if (h->nsnap == 0) {
+    CK(h, cudaMemcpyAsync(h->ws.cbuf[h->curc_h], x_dev, nb, cudaMemcpyDeviceToDevice, h->stream), "copy u0");
+    CK(h, launch_first(h->ws, h->stream), "first launch");
+    h->nsnap = 1;
+    return ODMD_OK;
+  }
+  CK(h, cudaMemcpyAsync(h->ws.cbuf[h->curc_h ^ 1], x_dev, nb, cudaMemcpyDeviceToDevice, h->stream), "copy x");
+  CK(h, launch_pass_a(h->ws, h->stream), "pass A launch");
+  CK(h, launch_small(h->ws, h->stream), "small solve launch");
+  CK(h, launch_pass_b(h->ws, h->stream), "pass B launch");
+  h->cur_h ^= 1;
+  h->curc_h ^= 1;
+  h->nsnap += 1;
+  h->eig_dirty = true;
+  return ODMD_OK;
+}
+
+odmd_status odmd_predict(odmd_t h, const double* t_host, int32_t k, void* out_dev, int64_t ld) {
+  if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
+  if (k < 0 || (k > 0 && (!t_host || !out_dev))) return fail(h, ODMD_ERR_ARG, "bad t/out/k");
+  if (ld < h->cfg.n) return fail(h, ODMD_ERR_ARG, "ld < n");
+  if (h->nsnap < 2) return fail(h, ODMD_ERR_STATE, "predict needs two snapshots");
+  for (int i = 0; i < k; ++i)
+    if (!(t_host[i] >= 0.0) || !std::isfinite(t_host[i])) return fail(h, ODMD_ERR_ARG, "t must be finite and >= 0");
+  if (odmd_status s = ensure_eig(h)) return s;
+  const size_t vs = (size_t)vsz_of(h->cfg.prec);
+  for (int j0 = 0; j0 < k; j0 += kRollK) {
+    const int kk = (k - j0) < kRollK ? (k - j0) : kRollK;
+    CK(h, launch_coef(h->ws, t_host + j0, kk, h->stream), "coef launch");
+    CK(h, launch_rollout(h->ws, nullptr, kk, static_cast<unsigned char*>(out_dev) + (size_t)j0 * ld * vs, ld, 0,
+                         h->stream),
+       "rollout launch");
+  }
+  return ODMD_OK;
+}
+
+odmd_status odmd_check(odmd_t h, double t, const void* x_fom_dev, double tol, double* rel_err, int32_t* pass) {
+  if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
+  if (!x_fom_dev) return fail(h, ODMD_ERR_ARG, "x_fom is NULL");
+  if (!(t >= 0.0) || !std::isfinite(t)) return fail(h, ODMD_ERR_ARG, "t must be finite and >= 0");
+  if (h->nsnap < 2) return fail(h, ODMD_ERR_STATE, "check needs two snapshots");
+  if (tol <= 0.0) tol = h->cfg.check_tol;
+  CK(h, cudaMemcpyAsync(h->ws.xbuf, x_fom_dev, snap_bytes(h), cudaMemcpyDeviceToDevice, h->stream), "copy x_fom");
+  if (odmd_status s = ensure_eig(h)) return s;
+  CK(h, launch_coef(h->ws, &t, 1, h->stream), "coef launch");
+  CK(h, launch_check(h->ws, h->stream), "check launch");
+  CK(h, cudaMemcpyAsync(h->pinned, h->ws.out2, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "read back");
+  if (odmd_status s = device_status(h)) return s;
+  const double num = h->pinned[0], den = h->pinned[1];
+  double err;
+  if (den == 0.0)
+    err = num == 0.0 ? 0.0 : INFINITY;
+  else
+    err = std::sqrt(num / den);
+  if (rel_err) *rel_err = err;
+  if (pass) *pass = err <= tol ? 1 : 0;
+  return ODMD_OK;
+}
+
+odmd_status odmd_sync(odmd_t h) {
+  if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
+  return device_status(h);
+}
+
+static odmd_status read_hdr(odmd_t h, StateHdr* hdr) {
+  CK(h, cudaMemcpyAsync(h->pinned, h->ws.st[h->cur_h].hdr, sizeof(StateHdr), cudaMemcpyDeviceToHost, h->stream),
+     "header read");
+  if (odmd_status s = device_status(h)) return s;
+  std::memcpy(hdr, h->pinned, sizeof(StateHdr));
+  h->compactions = hdr->compactions;
+  return ODMD_OK;
+}
+
+odmd_status odmd_get_rank(odmd_t h, int32_t* r) {
+  if (!h || !r) return fail(h, ODMD_ERR_ARG, "NULL argument");
+  StateHdr hdr;
+  if (odmd_status s = read_hdr(h, &hdr)) return s;
+  *r = hdr.r;
+  return ODMD_OK;
+}
+
+odmd_status odmd_get_singular_values(odmd_t h, double* s_host, int32_t cap, int32_t* r) {
+  if (!h || !r || (cap > 0 && !s_host)) return fail(h, ODMD_ERR_ARG, "NULL argument");
+  StateHdr hdr;
+  if (odmd_status s = read_hdr(h, &hdr)) return s;
+  *r = hdr.r;
+  const int nc = hdr.r < cap ? hdr.r : cap;
+  if (nc > 0) {
+    CK(h, cudaMemcpy(s_host, h->ws.st[h->cur_h].S, nc * sizeof(double), cudaMemcpyDeviceToHost), "S read");
+  }
+  return ODMD_OK;
+}
+
+odmd_status odmd_get_eigs(odmd_t h, double* re_host, double* im_host, double* amp_host, int32_t cap, int32_t* r) {
+  if (!h || !r || (cap > 0 && (!re_host || !im_host))) return fail(h, ODMD_ERR_ARG, "NULL argument");
+  if (h->nsnap < 2) return fail(h, ODMD_ERR_STATE, "no model yet");
+  if (odmd_status s = ensure_eig(h)) return s;
+  StateHdr hdr;
+  if (odmd_status s = read_hdr(h, &hdr)) return s;
+  *r = hdr.r;
+  const int nc = hdr.r < cap ? hdr.r : cap;
+  if (nc > 0) {
+    CK(h, cudaMemcpy(re_host, h->ws.eig.lre, nc * sizeof(double), cudaMemcpyDeviceToHost), "eig read");
+    CK(h, cudaMemcpy(im_host, h->ws.eig.lim, nc * sizeof(double), cudaMemcpyDeviceToHost), "eig read");
+    if (amp_host) {
+      double br[kMaxR], bi[kMaxR];
+      CK(h, cudaMemcpy(br, h->ws.eig.bre, nc * sizeof(double), cudaMemcpyDeviceToHost), "b read");
+      CK(h, cudaMemcpy(bi, h->ws.eig.bim, nc * sizeof(double), cudaMemcpyDeviceToHost), "b read");
+      for (int i = 0; i < nc; ++i) amp_host[i] = std::hypot(br[i], bi[i]);
+    }
+  }
+  return ODMD_OK;
+}
+
+odmd_status odmd_get_basis(odmd_t h, void* out_dev, int64_t ld, int32_t* r) {
+  if (!h || !out_dev || !r) return fail(h, ODMD_ERR_ARG, "NULL argument");
+  if (ld < h->cfg.n) return fail(h, ODMD_ERR_ARG, "ld < n");
+  StateHdr hdr;
+  if (odmd_status s = read_hdr(h, &hdr)) return s;
+  *r = hdr.r;
+  if (hdr.r == 0) return ODMD_OK;
+  CK(h, launch_basis_coef(h->ws, h->stream), "basis coef launch");
+  CK(h, launch_rollout(h->ws, nullptr, hdr.r, out_dev, ld, 0, h->stream), "basis launch");
+  return device_status(h);
+}
+
+odmd_status odmd_get_counts(odmd_t h, int64_t* snapshots, int64_t* compactions) {
+  if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
+  if (snapshots) *snapshots = h->nsnap;
+  if (compactions) {
+    StateHdr hdr;
+    if (odmd_status s = read_hdr(h, &hdr)) return s;
+    *compactions = hdr.compactions;
+  }
+  return ODMD_OK;
+}
+
+odmd_status odmd_destroy(odmd_t h) {
+  if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  cudaFreeHost(h->pinned);
+  delete h;
+  if (e != cudaSuccess) return fail(nullptr, ODMD_ERR_CUDA, std::string("destroy: ") + cudaGetErrorString(e));
+  return ODMD_OK;
+}
+
+const char* odmd_last_error(odmd_t h) { return h ? h->err.c_str() : g_err.c_str(); }
+
+}  // extern "C"

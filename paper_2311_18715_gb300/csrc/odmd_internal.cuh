@@ -1,0 +1,289 @@
+// Internal definitions shared by the CUDA translation units of libodmd.
+//
+// Numerics: GB300 issues FP32 FMAs ~70x faster than FP64 ones and converts between the
+// two at the FP64 rate, so every pass over the tall basis works on floats: a basis
+// element is an unevaluated sum hi + lo of two floats (48-bit significand) in the
+// FP64-accuracy mode, products are formed exactly with FMA (two-product) and summed
+// with Knuth's two-sum into a hi/lo accumulator.  Only O(r^2)..O(r^3) small solves run
+// in native FP64.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+namespace odmd {
+
+constexpr int kThreads = 256;      // threads of every tall-pass CTA
+constexpr int kTile = 64;          // rows per tile of a tall pass
+constexpr int kStages = 4;         // TMA pipeline depth of a tall pass
+constexpr int kMaxR = 64;          // largest r_max
+constexpr int kMaxSlack = 32;      // largest slack
+constexpr int kMaxCap = kMaxR + kMaxSlack;  // largest number of basis columns r0
+constexpr int kMaxN = kMaxR + 1;   // largest core matrix order r + 1
+constexpr int kRollK = 64;         // horizons (columns) per rollout launch
+
+enum Storage { ST_DD = 0, ST_F32 = 1, ST_BF16 = 2 };
+
+// device status word bits
+enum : int {
+  DEV_NONFINITE = 1,   // a non-finite value reached a reduction or the small solve
+  DEV_TIMEOUT = 2,     // a bounded wait on an mbarrier ran out
+  DEV_EIG_NOCONV = 4,  // the Francis QR iteration did not converge
+  DEV_EIG_COND = 8,    // the eigenvector matrix is singular to working precision
+  DEV_SECULAR = 16,    // a secular-equation root failed to converge
+  DEV_NOMODEL = 32     // predict/check/eig asked for with rank 0
+};
+
+// pass-B modes
+enum : int { PB_NONE = 0, PB_APPEND = 1, PB_COMPACT = 2 };
+
+// Committed small state (two copies, selected by Ctl::cur).
+struct StateHdr {
+  int r;        // rank
+  int r0;       // number of tall-basis columns in use
+  int pairs;    // snapshot pairs ingested
+  int compactions;
+  double cn2;   // ||c||^2 of the latest snapshot c
+};
+
+struct StateBuf {
+  StateHdr* hdr;
+  double* S;    // r_max
+  double* rf;   // r_max   first row of R
+  double* rl;   // r_max   last row of R
+  double* M;    // r_max x r_max, column-major, ld = r_max   (M = L^T U^+ R)
+  double* Q;    // (cap+1) x r_max, column-major, ld = cap+1  (L = L0 Q)
+  double* a;    // cap+1   L0^T c
+};
+
+// Control block: indices of the committed buffers, tickets, status, small scalars.
+struct Ctl {
+  int cur;          // committed StateBuf
+  int cur_c;        // committed snapshot buffer (holds c)
+  int status;       // DEV_* bits
+  unsigned ticket_a, ticket_b, ticket_r;
+  int mode;         // pass-B mode for the update in flight
+  int r0e;          // basis columns after the (optional) append
+  int rnew;         // rank after the update
+  int append;       // 1 if the update appends a column to L0
+  int n;            // core order r + 1
+  int m;            // non-deflated poles of the secular problem
+  int ndefl;        // deflated singular values
+  int nrot;         // Givens rotations used by the deflation
+  int eig_valid;    // eigen-cache matches the committed state
+  int eig_r;        // rank the eigen-cache was built for
+  int pad0;
+  double thr;       // tau * max(sigma_1, ||c||)
+  double rho0;      // norm of the part of c outside span(L0)
+  double rho;       // norm of the part of c outside span(L)
+  double gamma;     // j^T x
+  double check_num, check_den;  // reductions of the credibility check
+  double pad1;
+};
+
+// Scratch of the small solve (single copy).
+struct Small {
+  double* red;      // 2*cap+3 reduced tall sums: s (r0), y (r0), eta, ex, xi
+  double* ac;       // cap+1   corrected projection of c onto L0 (a + s)
+  double* yext;     // cap+1   L0_ext^T x
+  double* qn;       // cap+1   new unit direction in L0_ext coordinates
+  double* p;        // kMaxN   L^T c
+  double* w;        // kMaxN   L^T x
+  double* d;        // kMaxN   poles (ascending) of the secular problem, as singular values
+  double* z;        // kMaxN   weights at those poles
+  int* pole;        // kMaxN   core coordinate of each pole
+  double* zrot;     // kMaxN   z in core coordinates after the deflating rotations
+  int* defl;        // kMaxN   deflated core coordinates
+  int* rot_i;       // kMaxN
+  int* rot_j;
+  double* rot_c;
+  double* rot_s;
+  int* org;         // kMaxN   origin pole of each root
+  double* mu;       // kMaxN   root minus its origin pole (squared units)
+  double* zhat;     // kMaxN   Loewner weights
+  double* sig;      // kMaxN   singular values of the core, descending
+  int* src;         // kMaxN   source of output column j: >=0 root index, <0: -(defl idx)-1
+  double* U;        // kMaxN x kMaxN, column-major   left singular vectors of K (kept)
+  double* V;        // kMaxN x kMaxN                   right singular vectors of K (kept)
+  double* QB;       // (cap+1) x r_max, col-major ld cap+1: pass-B rotation (compaction)
+  double* coef;     // (cap+1) x kRollK rollout coefficients in L0 coordinates
+};
+
+// Eigen-cache.
+struct Eig {
+  double* lre;      // r_max eigenvalues
+  double* lim;
+  double* Vre;      // r_max x r_max eigenvectors (column-major, unit 2-norm)
+  double* Vim;
+  double* bre;      // r_max  b = V^{-1} (S * r_first)
+  double* bim;
+  double* work;     // scratch for the eigensolver: 8 r_max^2 + 16 r_max
+};
+
+struct Ws {
+  int64_t n;        // rows
+  int64_t npad;     // rows rounded up to kTile
+  int rmax, cap, ldg, prec, gridA;
+  double tau;
+  Ctl* ctl;
+  void* Lh;         // hi plane (float) / bf16 plane
+  float* Ll;        // lo plane (FP64 mode only)
+  void* cbuf[2];    // snapshot buffers (npad elements of the snapshot type)
+  void* xbuf;       // scratch snapshot (check input copy)
+  float2* part;     // per-CTA partial sums: gridA x (2*cap+3)
+  StateBuf st[2];
+  Small sm;
+  Eig eig;
+  double* out2;     // 4 doubles for host read-back
+};
+
+// ------------------------------------------------------------------ float-float arithmetic
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Running sum h + l; l collects rounding errors and small cross terms lazily.
+struct Acc {
+  float h, l;
+};
+
+__device__ __forceinline__ Acc acc_zero() { return Acc{0.f, 0.f}; }
+
+// A += (xh + xl) * (yh + yl), dropping xl*yl (2^-48 relative).
+__device__ __forceinline__ void acc_fma(Acc& A, float xh, float xl, float yh, float yl) {
+  float p = __fmul_rn(xh, yh);
+  float pe = __fmaf_rn(xh, yh, -p);
+  pe = __fmaf_rn(xh, yl, pe);
+  pe = __fmaf_rn(xl, yh, pe);
+  float s, e;
+  two_sum(A.h, p, s, e);
+  A.h = s;
+  A.l = __fadd_rn(A.l, __fadd_rn(e, pe));
+}
+
+__device__ __forceinline__ void acc_add(Acc& A, float bh, float bl) {
+  float s, e;
+  two_sum(A.h, bh, s, e);
+  A.h = s;
+  A.l = __fadd_rn(A.l, __fadd_rn(e, bl));
+}
+
+__device__ __forceinline__ Acc acc_norm(Acc A) {
+  float s = __fadd_rn(A.h, A.l);
+  float e = __fsub_rn(A.l, __fsub_rn(s, A.h));
+  return Acc{s, e};
+}
+
+__device__ __forceinline__ void split_double(double x, float& h, float& l) {
+  h = __double2float_rn(x);
+  l = __double2float_rn(x - (double)h);
+}
+
+__device__ __forceinline__ double join_double(float h, float l) { return (double)h + (double)l; }
+
+// ------------------------------------------------------------------ TMA bulk copy + mbarrier
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for an mbarrier phase with a time limit (2 s).  On timeout the status word gets
+// DEV_TIMEOUT and false is returned; the caller skips its compute for that tile.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > 2000000000ull) {
+      atomicOr(status, DEV_TIMEOUT);
+      return false;
+    }
+  }
+}
+
+// After a timeout: give the copies still in flight for stages [li, li + depth) up to
+// 0.5 s in total to land before the CTA leaves, so no copy outlives its shared memory.
+__device__ __forceinline__ void mbar_drain(uint64_t* bars, int stages, int li, int my_tiles) {
+  const uint64_t t0 = global_ns();
+  for (int l = li; l < my_tiles && l < li + stages; ++l) {
+    const uint32_t par = (uint32_t)((l / stages) & 1);
+    while (!mbar_try_wait(&bars[l % stages], par)) {
+      if (global_ns() - t0 > 500000000ull) return;
+    }
+  }
+}
+
+// 1-D bulk copy global -> shared (TMA), completion counted on `bar` in bytes.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// ------------------------------------------------------------------ warp helpers
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ Acc warp_sum_acc(Acc a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    float h = __shfl_xor_sync(0xffffffffu, a.h, o);
+    float l = __shfl_xor_sync(0xffffffffu, a.l, o);
+    acc_add(a, h, l);
+  }
+  return a;
+}
+
+// ------------------------------------------------------------------ launchers (per unit)
+// tall.cu
+cudaError_t launch_pass_a(const Ws& ws, cudaStream_t s);
+cudaError_t launch_pass_b(const Ws& ws, cudaStream_t s);
+cudaError_t launch_first(const Ws& ws, cudaStream_t s);
+cudaError_t launch_rollout(const Ws& ws, const double* coef_src, int kcols, void* out, int64_t ld,
+                           int coef_mode, cudaStream_t s);
+cudaError_t launch_check(const Ws& ws, cudaStream_t s);
+int tall_smem_bytes(int prec);
+// small.cu
+cudaError_t launch_small(const Ws& ws, cudaStream_t s);
+cudaError_t launch_eig(const Ws& ws, cudaStream_t s);
+cudaError_t launch_coef(const Ws& ws, const double* t_host, int k, cudaStream_t s);  // k <= kRollK, t on the host
+cudaError_t launch_basis_coef(const Ws& ws, cudaStream_t s);
+cudaError_t launch_init(const Ws& ws, cudaStream_t s);
+
+}  // namespace odmd

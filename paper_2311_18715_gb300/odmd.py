@@ -1,0 +1,143 @@
+"""Python face of libodmd: torch tensors in, C ABI calls out.
+
+torch provides device memory (the workspace, outputs) and streams; every step of the
+online DMD runs in the CUDA kernels behind include/odmd.h.  There is no CPU path: if
+the library is missing or no GPU is present, construction fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Sequence
+
+import torch
+
+from ._lib import PREC, OdmdConfig, check, load_library
+
+_SNAP_DTYPE = {"fp64": torch.float64, "fp32": torch.float32, "bf16": torch.float32}
+
+
+class OnlineDMD:
+    """Online DMD of a snapshot stream on one GPU (Sec. 2.3 of the paper).
+
+    update(x) appends u^k; predict(ts) returns u(t) = Re(Phi Lambda^t Phi^+ u^0) for the
+    step counts in ts (rows of the result); check(t, x_fom) is the relative-L2
+    credibility test of the hybrid FOM/ROM loop (Sec. 2.2).
+    """
+
+    def __init__(self, n: int, r_max: int, prec: str = "fp64", slack: int = 16,
+                 trunc_tol: float = 1e-10, check_tol: float = 1e-5, refine_every: int = 0,
+                 stream: torch.cuda.Stream | None = None, device: torch.device | int | None = None):
+        if prec not in PREC:
+            raise ValueError(f"prec must be one of {sorted(PREC)}")
+        self._lib = load_library()
+        if not torch.cuda.is_available():
+            raise RuntimeError("OnlineDMD needs a CUDA device")
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        self.n, self.r_max, self.prec = int(n), int(r_max), prec
+        self.dtype = _SNAP_DTYPE[prec]
+        cfg = OdmdConfig()
+        check(self._lib, self._lib.odmd_config_default(C.byref(cfg), self.n, self.r_max))
+        cfg.slack = int(slack)
+        cfg.trunc_tol = float(trunc_tol)
+        cfg.check_tol = float(check_tol)
+        cfg.prec = PREC[prec]
+        cfg.refine_every = int(refine_every)
+        self.cfg = cfg
+        nbytes = C.c_size_t()
+        check(self._lib, self._lib.odmd_footprint(C.byref(cfg), C.byref(nbytes)))
+        self.footprint = int(nbytes.value)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self.workspace = torch.empty(self.footprint, dtype=torch.uint8, device=self.device)
+            h = C.c_void_p()
+            check(self._lib, self._lib.odmd_create(C.byref(cfg), C.c_void_p(self.workspace.data_ptr()),
+                                                   self.footprint, C.c_void_p(self.stream.cuda_stream),
+                                                   C.byref(h)))
+        self._h = h
+
+    # ------------------------------------------------------------------ helpers
+    def _ck(self, status: int) -> None:
+        check(self._lib, status, self._h)
+
+    def _snap(self, x: torch.Tensor, name: str) -> torch.Tensor:
+        if not isinstance(x, torch.Tensor) or x.device != self.device:
+            raise ValueError(f"{name} must be a tensor on {self.device}")
+        if x.dtype != self.dtype or x.numel() != self.n or not x.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous {self.dtype} tensor of {self.n} elements")
+        if self.stream != torch.cuda.current_stream(self.device):
+            x.record_stream(self.stream)
+        return x
+
+    # ------------------------------------------------------------------ API
+    def update(self, x: torch.Tensor) -> None:
+        x = self._snap(x, "x")
+        self._ck(self._lib.odmd_update(self._h, C.c_void_p(x.data_ptr())))
+
+    def predict(self, ts: Sequence[float], out: torch.Tensor | None = None) -> torch.Tensor:
+        """Return a (len(ts), n) tensor whose row j is u(t_j)."""
+        ts = [float(t) for t in ts]
+        k = len(ts)
+        if out is None:
+            out = torch.empty((k, self.n), dtype=self.dtype, device=self.device)
+        elif out.shape != (k, self.n) or out.dtype != self.dtype or not out.is_contiguous():
+            raise ValueError("out must be a contiguous (k, n) tensor of the snapshot dtype")
+        arr = (C.c_double * max(k, 1))(*ts)
+        self._ck(self._lib.odmd_predict(self._h, arr, k, C.c_void_p(out.data_ptr()), self.n))
+        return out
+
+    def check(self, t: float, x_fom: torch.Tensor, tol: float = 0.0) -> tuple[float, bool]:
+        x_fom = self._snap(x_fom, "x_fom")
+        err = C.c_double()
+        ok = C.c_int32()
+        self._ck(self._lib.odmd_check(self._h, float(t), C.c_void_p(x_fom.data_ptr()), float(tol),
+                                      C.byref(err), C.byref(ok)))
+        return float(err.value), bool(ok.value)
+
+    def sync(self) -> None:
+        self._ck(self._lib.odmd_sync(self._h))
+
+    @property
+    def rank(self) -> int:
+        r = C.c_int32()
+        self._ck(self._lib.odmd_get_rank(self._h, C.byref(r)))
+        return int(r.value)
+
+    def singular_values(self) -> list[float]:
+        buf = (C.c_double * self.r_max)()
+        r = C.c_int32()
+        self._ck(self._lib.odmd_get_singular_values(self._h, buf, self.r_max, C.byref(r)))
+        return [buf[i] for i in range(r.value)]
+
+    def eigs(self) -> tuple[list[complex], list[float]]:
+        """DMD eigenvalues and mode amplitudes |b_i| ||Phi e_i||."""
+        re = (C.c_double * self.r_max)()
+        im = (C.c_double * self.r_max)()
+        amp = (C.c_double * self.r_max)()
+        r = C.c_int32()
+        self._ck(self._lib.odmd_get_eigs(self._h, re, im, amp, self.r_max, C.byref(r)))
+        return [complex(re[i], im[i]) for i in range(r.value)], [amp[i] for i in range(r.value)]
+
+    def basis(self) -> torch.Tensor:
+        """The orthonormal basis L = L0 Q as an (r, n) tensor (row i = column i of L)."""
+        out = torch.empty((self.r_max, self.n), dtype=self.dtype, device=self.device)
+        r = C.c_int32()
+        self._ck(self._lib.odmd_get_basis(self._h, C.c_void_p(out.data_ptr()), self.n, C.byref(r)))
+        return out[: r.value]
+
+    def counts(self) -> tuple[int, int]:
+        s = C.c_int64()
+        c = C.c_int64()
+        self._ck(self._lib.odmd_get_counts(self._h, C.byref(s), C.byref(c)))
+        return int(s.value), int(c.value)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._ck(self._lib.odmd_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,154 @@
+"""Device path vs the FP64 oracle, element by element on identical seeded inputs.
+
+Sizes span several 64-row tiles with a ragged tail; slack values exercise both the
+append-only updates and the compaction of the tall basis.  Tolerances (FP64 mode):
+eigenvalues 1e-10 relative for modes with amplitude >= 1e-6 of the largest, rollouts
+1e-9 relative, singular values 1e-10 of sigma_1.
+"""
+import numpy as np
+import pytest
+
+from oracle import BatchDMD, OnlineDMDRef
+from synth import PlantedModes, WakeField
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def match_eigs(a, b):
+    a = list(np.asarray(a, dtype=complex))
+    b = list(np.asarray(b, dtype=complex))
+    worst = 0.0
+    for x in sorted(a, key=lambda z: -abs(z)):
+        d = [abs(x - y) for y in b]
+        i = int(np.argmin(d))
+        worst = max(worst, d[i] / max(abs(x), 1e-300))
+        b.pop(i)
+    return worst
+
+
+def run_pair(X, r_max, slack=16, tau=1e-10, prec="fp64"):
+    import paper_2311_18715_gb300 as pkg
+
+    dev = torch.device("cuda", 0)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    m = pkg.OnlineDMD(X.shape[1], r_max, prec=prec, slack=slack, trunc_tol=tau)
+    ref = OnlineDMDRef(X.shape[1], r_max, tau)
+    Xd = torch.from_numpy(X).to(dev, dt)
+    for k in range(X.shape[0]):
+        m.update(Xd[k])
+        ref.update(X[k].astype(np.float64) if prec == "fp64" else Xd[k].double().cpu().numpy())
+    m.sync()
+    return m, ref
+
+
+def strong_eigs(lam, amp, frac=1e-6):
+    lam = np.asarray(lam)
+    amp = np.asarray(amp)
+    return lam[amp >= frac * amp.max()]
+
+
+@pytest.mark.parametrize("slack", [0, 4, 16])
+def test_planted_modes_4096(slack):
+    g = PlantedModes(4096, sigma=1e-8, seed=0)
+    X = g.snapshots(0, 200)
+    m, ref = run_pair(X, 10, slack=slack)
+    assert m.rank == ref.rank == 10
+    S = np.array(m.singular_values())
+    np.testing.assert_allclose(S, ref.S, rtol=0, atol=1e-10 * ref.S[0])
+    lam, amp = m.eigs()
+    lam_r, V_r, b_r = ref.eig()
+    amp_r = np.abs(b_r) * np.linalg.norm(ref.L @ V_r, axis=0)
+    s_dev = strong_eigs(lam, amp)
+    s_ref = strong_eigs(lam_r, amp_r)
+    assert len(s_dev) == len(s_ref) == 6
+    assert match_eigs(s_dev, s_ref) < 1e-10
+    ts = [0.0, 1.0, 99.5, 199.0, 200.0, 260.0]
+    got = m.predict(ts).cpu().numpy()
+    want = ref.predict(ts).T
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-9
+    for t in (200.0, 201.0):
+        e_dev, _ = m.check(t, torch.from_numpy(g.snapshot(int(t))).cuda())
+        e_ref, _ = ref.check(t, g.snapshot(int(t)))
+        assert abs(e_dev - e_ref) <= 1e-6 * e_ref
+
+
+@pytest.mark.parametrize("n,slack", [(1000, 0), (1000, 3), (777, 16), (64, 2), (33, 5)])
+def test_random_stream_ragged_tiles(n, slack):
+    """Random snapshots, truncation active (r_max < m), rows not a multiple of the tile."""
+    rng = np.random.default_rng(n + slack)
+    X = rng.standard_normal((40, n))
+    X[:, : n // 2] *= 3.0
+    m, ref = run_pair(X, 8, slack=slack)
+    assert m.rank == ref.rank
+    S = np.array(m.singular_values())
+    np.testing.assert_allclose(S, ref.S, rtol=0, atol=1e-10 * ref.S[0])
+    ts = [0.0, 17.0, 39.0, 40.0]
+    got = m.predict(ts).cpu().numpy()
+    want = ref.predict(ts).T
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-9
+    L = m.basis().cpu().numpy().T
+    P = L @ L.T
+    Pr = ref.L @ ref.L.T
+    assert np.max(np.abs(P - Pr)) < 1e-9
+    assert np.max(np.abs(L.T @ L - np.eye(L.shape[1]))) < 1e-12
+
+
+def test_no_truncation_matches_batch_dmd():
+    rng = np.random.default_rng(5)
+    n, steps = 700, 31
+    A = rng.standard_normal((n, n)) / np.sqrt(n)
+    X = np.empty((steps, n))
+    X[0] = rng.standard_normal(n)
+    for k in range(steps - 1):
+        X[k + 1] = A @ X[k] + 0.1 * rng.standard_normal(n)
+    m, ref = run_pair(X, 32, slack=8)
+    B = BatchDMD(X.T, 32)
+    assert m.rank == B.S.shape[0] == steps - 1
+    np.testing.assert_allclose(m.singular_values(), B.S, rtol=1e-11)
+    lam, _ = m.eigs()
+    assert match_eigs(lam, B.lam) < 1e-9
+    got = m.predict([0.0, 12.0, 30.0]).cpu().numpy()
+    want = B.predict([0.0, 12.0, 30.0]).T
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-9
+
+
+def test_wake_field_small_grid():
+    g = WakeField(nx=64, ny=32, sigma=1e-6, seed=0)
+    X = g.snapshots(0, 300)
+    m, ref = run_pair(X, 16, slack=16)
+    assert m.rank == ref.rank
+    np.testing.assert_allclose(m.singular_values(), ref.S, rtol=0, atol=1e-10 * ref.S[0])
+    got = m.predict([300.0, 320.0]).cpu().numpy()
+    want = ref.predict([300.0, 320.0]).T
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-9
+
+
+def test_edge_cases():
+    import paper_2311_18715_gb300 as pkg
+
+    dev = torch.device("cuda", 0)
+    # n = 1: rank one at most
+    m, ref = run_pair(np.array([[1.0], [2.0], [4.0], [8.0]]), 3, slack=0)
+    assert m.rank == 1
+    lam, _ = m.eigs()
+    np.testing.assert_allclose(lam, [2.0], rtol=1e-14)
+    # zero first snapshot: the model starts at u^1, predictions anchored at u^0 = 0
+    g = PlantedModes(200, mus=(1.0,), thetas=(0.05,), sigma=0.0, seed=1)
+    X = g.snapshots(0, 10)
+    X[0] = 0.0
+    m, ref = run_pair(X, 4, slack=2)
+    assert m.rank == ref.rank == 2
+    assert np.max(np.abs(m.predict([5.0]).cpu().numpy())) == 0.0
+    # a repeated snapshot adds no direction
+    a = np.random.default_rng(2).standard_normal(300)
+    m, ref = run_pair(np.stack([a] * 6), 5, slack=1)
+    assert m.rank == 1
+    np.testing.assert_allclose(m.singular_values(), ref.S, rtol=1e-13)
+    # state errors
+    mm = pkg.OnlineDMD(10, 2)
+    with pytest.raises(pkg.OdmdError):
+        mm.predict([1.0])
+    mm.update(torch.zeros(10, dtype=torch.float64, device=dev))
+    with pytest.raises(pkg.OdmdError):
+        mm.check(1.0, torch.zeros(10, dtype=torch.float64, device=dev))
