@@ -34,7 +34,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 struct Layout {
   size_t total;
   size_t off_ctl, off_hdr[2], off_state[2], off_small, off_eig, off_out2, off_part, off_Lh, off_Ll, off_c[2],
-      off_x;
+      off_x, off_e;
   size_t state_doubles, small_bytes, eig_doubles;
   int64_t npad;
   int ldg, cap, rmax, partrows;
@@ -118,6 +118,7 @@ Layout make_layout(const odmd_config& c) {
   L.off_c[0] = take(snap);
   L.off_c[1] = take(snap);
   L.off_x = take(snap);
+  L.off_e = take((size_t)L.npad * sizeof(float2));
   L.total = o;
   return L;
 }
@@ -219,6 +220,7 @@ void carve(Ws& ws, const Layout& L, unsigned char* base, const odmd_config& c, i
   ws.cbuf[0] = base + L.off_c[0];
   ws.cbuf[1] = base + L.off_c[1];
   ws.xbuf = base + L.off_x;
+  ws.ebuf = reinterpret_cast<float2*>(base + L.off_e);
 }
 
 odmd_status fail(odmd_t h, odmd_status s, const std::string& msg) {

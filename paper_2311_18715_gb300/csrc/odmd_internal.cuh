@@ -130,6 +130,7 @@ struct Ws {
   float* Ll;        // lo plane (FP64 mode only)
   void* cbuf[2];    // snapshot buffers (npad elements of the snapshot type)
   void* xbuf;       // scratch snapshot (check input copy)
+  float2* ebuf;     // first-pass residual e = c - L0 a of the update in flight (hi, lo)
   float2* part;     // per-CTA partial sums: gridA x (2*cap+3)
   StateBuf st[2];
   Small sm;

@@ -44,11 +44,12 @@ __device__ __forceinline__ int rows_in(int64_t n, int64_t row0) {
 __host__ __device__ inline int row_bytes(int r0, int esz) { return ((r0 * esz + 15) / 16) * 16; }
 __host__ __device__ inline int row_stride(int rb) { return ((rb / 16) & 1) ? rb : rb + 16; }
 
+// each stage: the basis rows (per plane) and two per-row slots of 8 bytes
 template <int ST>
 __host__ __device__ inline int stage_bytes(int cap) {
   using T = Traits<ST>;
   const int rs = row_stride(row_bytes(cap, T::esz));
-  return kTile * rs * T::planes + 2 * kTile * T::vsz;
+  return kTile * rs * T::planes + 2 * kTile * 8;
 }
 
 // Snapshot element -> float-float
@@ -119,21 +120,21 @@ struct TilePipe {
   int ldg;
   const unsigned char* gLh;
   const unsigned char* gLl;
-  const unsigned char* gc;  // snapshot c (or nullptr)
-  const unsigned char* gx;  // snapshot x (or nullptr)
+  const unsigned char* gc;  // first per-row slot (snapshot c, or the residual e), or nullptr
+  const unsigned char* gx;  // second per-row slot (snapshot x), or nullptr
+  int vc, vx;               // bytes per row of the two slots
 
   __device__ unsigned char* plane_h(int s) const { return base + (size_t)s * stage_sz; }
   __device__ unsigned char* plane_l(int s) const { return plane_h(s) + kTile * rs; }
   __device__ unsigned char* snap_c(int s) const { return plane_h(s) + kTile * rs * T::planes; }
-  __device__ unsigned char* snap_x(int s) const { return snap_c(s) + kTile * T::vsz; }
+  __device__ unsigned char* snap_x(int s) const { return snap_c(s) + kTile * 8; }
 
   // Issue the copies of tile `tile` into stage `s` (called by all lanes of warp 0).
   __device__ void issue(int tile, int s) const {
     const int lane = threadIdx.x & 31;
     const int64_t row0 = (int64_t)tile * kTile;
     const int rows = rows_in(n, row0);
-    const uint32_t bytes = (uint32_t)(rows * rb * T::planes) + (gc ? kTile * T::vsz : 0) +
-                           (gx ? kTile * T::vsz : 0);
+    const uint32_t bytes = (uint32_t)(rows * rb * T::planes) + (gc ? kTile * vc : 0) + (gx ? kTile * vx : 0);
     if (lane == 0) mbar_arrive_expect_tx(&bars[s], bytes);
     __syncwarp();
     if (rb > 0) {
@@ -144,8 +145,8 @@ struct TilePipe {
       }
     }
     if (lane == 0) {
-      if (gc) bulk_g2s(snap_c(s), gc + (size_t)row0 * T::vsz, kTile * T::vsz, &bars[s]);
-      if (gx) bulk_g2s(snap_x(s), gx + (size_t)row0 * T::vsz, kTile * T::vsz, &bars[s]);
+      if (gc) bulk_g2s(snap_c(s), gc + (size_t)row0 * vc, kTile * vc, &bars[s]);
+      if (gx) bulk_g2s(snap_x(s), gx + (size_t)row0 * vx, kTile * vx, &bars[s]);
     }
   }
 };
@@ -195,6 +196,8 @@ __global__ void __launch_bounds__(kThreads) k_pass_a(Ws ws) {
   P.gLl = (const unsigned char*)ws.Ll;
   P.gc = (const unsigned char*)ws.cbuf[curc];
   P.gx = (const unsigned char*)ws.cbuf[curc ^ 1];
+  P.vc = T::vsz;
+  P.vx = T::vsz;
 
   // shared layout: stages | bars | a (hi, lo: kMaxCap+8 each) | e,x (4 x kTile) | red (4 x kTile Acc)
   P.base = smem;
@@ -269,6 +272,8 @@ __global__ void __launch_bounds__(kThreads) k_pass_a(Ws ws) {
         if (t >= rows) {
           e = acc_zero();
           xh_ = xl_ = 0.f;
+        } else {
+          ws.ebuf[row0 + t] = make_float2(e.h, e.l);  // kept for the second Gram-Schmidt pass
         }
         eh[t] = e.h;
         el[t] = e.l;
@@ -391,8 +396,10 @@ __global__ void __launch_bounds__(kThreads) k_pass_b(Ws ws) {
     P.ldg = ws.ldg;
     P.gLh = (const unsigned char*)ws.Lh;
     P.gLl = (const unsigned char*)ws.Ll;
-    P.gc = (const unsigned char*)ws.cbuf[curc];
+    P.gc = (const unsigned char*)ws.ebuf;
     P.gx = nullptr;
+    P.vc = 8;
+    P.vx = 0;
     P.base = smem;
     unsigned char* p = smem + (size_t)kStagesB * P.stage_sz;
     P.bars = reinterpret_cast<uint64_t*>(p);
@@ -408,7 +415,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_b(Ws ws) {
     const int elems_per_chunk = (ST == ST_BF16) ? 8 : 4;
     for (int k = tid; k < kMaxCap + 8; k += kThreads) {
       float h = 0.f, l = 0.f;
-      if (k < r0 && append) split_double(ws.sm.ac[k], h, l);
+      if (k < r0 && append) split_double(ws.sm.red[k], h, l);  // s = L0^T e
       if (k >= P.nch * elems_per_chunk) h = l = 0.f;
       coh[k] = h;
       col[k] = l;
@@ -457,8 +464,9 @@ __global__ void __launch_bounds__(kThreads) k_pass_b(Ws ws) {
           part[sub * kTile + t] = row_dot_partial<ST>(P, s, t, sub, coh, col);
           __syncthreads();
           if (sub == 0) {
-            float ch, cl;
-            load_snap(reinterpret_cast<const snap_t*>(P.snap_c(s)), t, ch, cl);
+            // j0 = (e - L0 s) / rho0: the second Gram-Schmidt pass, applied to the stored e
+            const float2 ev = reinterpret_cast<const float2*>(P.snap_c(s))[t];
+            const float ch = ev.x, cl = ev.y;
             Acc d = part[t];
             acc_add(d, part[kTile + t].h, part[kTile + t].l);
             acc_add(d, part[2 * kTile + t].h, part[2 * kTile + t].l);
@@ -558,6 +566,8 @@ __global__ void __launch_bounds__(kThreads) k_rollout(Ws ws, int kcols, void* ou
   P.gLl = (const unsigned char*)ws.Ll;
   P.gc = CHECK ? (const unsigned char*)ws.xbuf : nullptr;
   P.gx = nullptr;
+  P.vc = T::vsz;
+  P.vx = 0;
   P.base = smem;
   unsigned char* p = smem + (size_t)kStagesR * P.stage_sz;
   P.bars = reinterpret_cast<uint64_t*>(p);
@@ -589,7 +599,7 @@ __global__ void __launch_bounds__(kThreads) k_rollout(Ws ws, int kcols, void* ou
     for (int li = 0; li < min(my_tiles, kStagesR); ++li) P.issue(blockIdx.x + li * G, li);
   }
   // work split: items (t, j); with fewer than 4 columns each dot is split in nsub parts
-  const int nsub = kcols >= 4 ? 1 : (kcols == 1 ? 4 : 2);
+  const int nsub = kcols == 1 ? 4 : (kcols == 2 ? 2 : 1);  // nsub * kTile * kcols <= 4 * kTile when > 1
   Acc num = acc_zero(), den = acc_zero();
 
   for (int li = 0; li < my_tiles; ++li) {

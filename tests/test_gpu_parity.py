@@ -70,7 +70,9 @@ def test_planted_modes_4096(slack):
     for t in (200.0, 201.0):
         e_dev, _ = m.check(t, torch.from_numpy(g.snapshot(int(t))).cuda())
         e_ref, _ = ref.check(t, g.snapshot(int(t)))
-        assert abs(e_dev - e_ref) <= 1e-6 * e_ref
+        # |err_dev - err_ref| <= ||x_dev(t) - x_ref(t)|| / ||x_fom|| (triangle inequality),
+        # so the rollout tolerance bounds it
+        assert abs(e_dev - e_ref) <= 1e-9
 
 
 @pytest.mark.parametrize("n,slack", [(1000, 0), (1000, 3), (777, 16), (64, 2), (33, 5)])
