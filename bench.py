@@ -1,0 +1,422 @@
+#!/usr/bin/env python
+"""Benchmark of the online-DMD hot path (arXiv 2311.18715, Sec. 2.3 / 2.2) on GB300.
+
+Workload: the cylinder-wake-shaped stream on a 512 x 256 grid with (u, v, p) stacked
+(n = 393,216), rank cap 40, FP64-accuracy mode, 2000-snapshot horizon, credibility
+check every 50 steps.  One step is one 50-snapshot block of the hybrid loop: 50 rank-1
+updates, the eigensolve plus a rollout of the next 50 states, and one credibility check
+against the held-out next snapshot.  The model is first brought to steady state (rank
+40) on 100 untimed snapshots.
+
+Timing: inputs resident in HBM; before every update / predict / check a 256 MiB buffer
+is written to flush the 129 MB L2 (untimed); each op is bracketed by CUDA events on the
+handle's stream and the step time is their sum.  `value` = snapshot updates per second
+of step time, summed over ranks (each rank runs an independent replica).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "snapshot updates/s + rollout states/s, HBM GB/s vs roofline; p50/p99 at 1e-6 err"
+NX, NY = 512, 256
+N = 3 * NX * NY
+R_MAX, SLACK, TAU = 40, 16, 1e-10
+BLOCK = 50          # snapshots per step (check interval of the workload)
+PRETRAIN = 100      # untimed snapshots before warm-up
+SIGMA = 1e-6
+L2_FLUSH_BYTES = 256 << 20
+WORKLOAD = (f"cylinder-wake field {NX}x{NY}x3 (n={N}), r_max={R_MAX}, FP64 accuracy, "
+            f"{BLOCK}-snapshot blocks: {BLOCK} updates + {BLOCK}-state rollout + 1 check")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ distributed plumbing
+def dist_setup(n_gpus: int):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if os.environ.get("ODMD_BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+        dist.init_process_group(backend)
+        return rank, world, local, dist
+    return 0, 1, 0, None
+
+
+def max_over_ranks(x: float, dist, device=None) -> float:
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, dist, device=None) -> float:
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ clocks
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={CLOCK_QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sms, maxes, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                maxes.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sms) if sms else None,
+                "sm_max_mhz": max(maxes) if maxes else None,
+                "reasons": sorted(reasons), "samples": len(sms)}
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+class OracleRunner:
+    """The FP64 oracle as it stands, brought to steady state (rank r_max) and then timed
+    on bounded samples of the workload: `sample` updates, a BLOCK-state rollout and one
+    check, extrapolated to a full block (BLOCK x mean update time + rollout + check)."""
+
+    def __init__(self, seed: int = 0):
+        from oracle import OnlineDMDRef
+        from synth import WakeField
+
+        self.gen = WakeField(NX, NY, sigma=SIGMA, seed=seed)
+        self.ref = OnlineDMDRef(N, R_MAX, TAU)
+        self.k = 0
+        for _ in range(R_MAX + 5):
+            self.ref.update(self.gen.snapshot(self.k))
+            self.k += 1
+
+    def step(self, sample: int) -> dict:
+        snaps = [self.gen.snapshot(self.k + j) for j in range(sample + 1)]
+        t0 = time.perf_counter()
+        for j in range(sample):
+            self.ref.update(snaps[j])
+        t_upd = (time.perf_counter() - t0) / sample
+        self.k += sample
+        t0 = time.perf_counter()
+        self.ref.predict([float(self.k + h) for h in range(BLOCK)])
+        t_pred = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        self.ref.check(float(self.k), snaps[sample])
+        t_chk = time.perf_counter() - t0
+        step_s = BLOCK * t_upd + t_pred + t_chk
+        return {"step_s": step_s, "t_update_s": t_upd, "t_predict_s": t_pred, "t_check_s": t_chk,
+                "updates_per_s": BLOCK / step_s, "states_per_s": BLOCK / t_pred, "rank": self.ref.rank}
+
+
+def cpu_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args) -> None:
+    """Reference arm: the FP64 oracle on the host cores, same metric, unit and config."""
+    rank, world, local, dist = dist_setup(args.gpus)
+    if rank != 0:
+        return
+    sample = 6
+    runner = OracleRunner(seed=0)
+    steps = []
+    for i in range(args.warmup + args.steps):
+        r = runner.step(sample)
+        if i >= args.warmup:
+            steps.append(r["step_s"])
+    step_s = statistics.mean(steps)
+    value = BLOCK / step_s
+    desc = (f"each step: {sample} oracle updates at steady state (rank {R_MAX}) + a {BLOCK}-state "
+            f"rollout + 1 check; step time = {BLOCK} x mean update time + rollout + check")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "snapshot updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "n": N, "r_max": R_MAX, "block": BLOCK},
+        "cpu_baseline": {"value": value, "unit": "snapshot updates/s", "cores": cpu_cores(), "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": "snapshot updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args) -> None:
+    rank, world, local, dist = dist_setup(args.gpus)
+    import torch
+
+    import paper_2311_18715_gb300 as pkg
+    from synth import WakeField
+
+    # the CPU leg runs first, before any GPU work, on rank 0 at N = 1 only
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = OracleRunner(seed=0).step(args.cpu_updates)
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pkg.build()
+    gen = WakeField(NX, NY, sigma=SIGMA, seed=rank)
+    K, W = args.steps, args.warmup
+    n_dev = PRETRAIN + (W + K) * BLOCK + 1
+    n_e2e = K * BLOCK + 1
+    host = np.empty((n_dev + n_e2e, N), dtype=np.float64)
+    for k in range(n_dev + n_e2e):
+        host[k] = gen.snapshot(k)
+    Xd = torch.from_numpy(host[:n_dev]).to(dev)
+    Xh = torch.from_numpy(host[n_dev:]).pin_memory()
+    del host
+
+    model = pkg.OnlineDMD(N, R_MAX, prec="fp64", slack=SLACK, trunc_tol=TAU)
+    stream = model.stream
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    out = torch.empty((BLOCK, N), dtype=torch.float64, device=dev)
+    for k in range(PRETRAIN):
+        model.update(Xd[k])
+    model.sync()
+
+    def run_step(k0: int, timed: bool):
+        """One block starting at snapshot k0; returns per-op event pairs."""
+        evs = []
+
+        def op(fn):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            r = fn()
+            b.record(stream)
+            evs.append((a, b))
+            return r
+
+        for i in range(BLOCK):
+            op(lambda: model.update(Xd[k0 + i]))
+        k_next = k0 + BLOCK
+        op(lambda: model.predict([float(k_next + h) for h in range(BLOCK)], out=out))
+        err = op(lambda: model.check(float(k_next), Xd[k_next]))
+        return evs, err
+
+    k = PRETRAIN
+    for _ in range(W):
+        run_step(k, False)
+        k += BLOCK
+    torch.cuda.synchronize()
+    barrier(dist)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    model.profile(True)
+    prof0 = model.profile_read()
+    all_steps = []
+    errs = []
+    t_wall0 = time.perf_counter()
+    for _ in range(K):
+        evs, err = run_step(k, True)
+        all_steps.append(evs)
+        errs.append(err[0])
+        k += BLOCK
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    barrier(dist)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    prof = model.profile_read()
+    model.profile(False)
+
+    upd_ms, pred_ms, chk_ms, step_ms = [], [], [], []
+    for evs in all_steps:
+        times = [a.elapsed_time(b) for a, b in evs]
+        upd_ms.extend(times[:BLOCK])
+        pred_ms.append(times[BLOCK])
+        chk_ms.append(times[BLOCK + 1])
+        step_ms.append(sum(times))
+    total_s = sum(step_ms) / 1e3
+    total_s_max = max_over_ranks(total_s, dist, dev)
+    units = sum_over_ranks(float(BLOCK * K), dist, dev)
+    value = units / total_s_max
+    states_s = sum_over_ranks(float(BLOCK * K), dist, dev) / max_over_ranks(sum(pred_ms) / 1e3, dist, dev)
+
+    # ---- roofline of the dominant kernel class (live event timing)
+    hbm, peak_kind = _peaks()
+    classes = ["pass_a", "small", "pass_b", "eig", "coef", "rollout", "check"]
+    ms_tot = {c: prof[c][0] for c in classes}
+    launches = {c: prof[c][1] - prof0[c][1] for c in classes}
+    groups = {"pass_a": K * BLOCK, "small": K * BLOCK, "pass_b": K * BLOCK, "eig": K, "coef": 2 * K,
+              "rollout": K, "check": K}
+    mean_r0 = prof["mean_r0"]
+    dom = max(classes, key=lambda c: ms_tot[c])
+    w, v = 8, 8  # bytes per basis element (hi + lo floats) and per snapshot element (double)
+    bytes_per = {
+        # pass A streams the r0 active basis columns and the snapshots c and x
+        "pass_a": N * mean_r0 * w + 2 * N * v,
+        # the rollout streams the basis once and writes BLOCK states
+        "rollout": N * mean_r0 * w + BLOCK * N * v,
+        "check": N * mean_r0 * w + N * v,
+    }
+    roof = None
+    if dom in bytes_per:
+        per_launch_ms = ms_tot[dom] / max(groups[dom], 1)
+        achieved = bytes_per[dom] / (per_launch_ms * 1e-3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
+                "bytes_per_launch": bytes_per[dom], "ms_per_launch": per_launch_ms}
+    pa_ms = ms_tot["pass_a"] / max(groups["pass_a"], 1)
+    pass_a_roof = {"achieved": bytes_per["pass_a"] / (pa_ms * 1e-3) / 1e9, "peak": hbm,
+                   "frac": bytes_per["pass_a"] / (pa_ms * 1e-3) / 1e9 / hbm, "ms_per_launch": pa_ms}
+    if roof is None:
+        roof = dict(pass_a_roof, kernel="pass_a", bound="hbm", unit="GB/s", traffic=None,
+                    peak_kind=peak_kind, note=f"dominant class is {dom}")
+
+    # ---- end to end through the public API with host buffers
+    x_stage = torch.empty(N, dtype=torch.float64, device=dev)
+    out_h = torch.empty((BLOCK, N), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    barrier(dist)
+    t0 = time.perf_counter()
+    ke = 0
+    for _ in range(K):
+        with torch.cuda.stream(stream):
+            for i in range(BLOCK):
+                x_stage.copy_(Xh[ke], non_blocking=True)
+                model.update(x_stage)
+                ke += 1
+            model.predict([float(k + h) for h in range(BLOCK)], out=out)
+            out_h.copy_(out, non_blocking=True)
+            x_stage.copy_(Xh[ke], non_blocking=True)
+            model.check(float(k + BLOCK), x_stage)
+        k += BLOCK
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    barrier(dist)
+    e2e_value = sum_over_ranks(float(BLOCK * K), dist, dev) / e2e_s
+
+    model.sync()
+    n_launch = int(sum(launches.values()))
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "snapshot updates/s", "n_gpus": world,
+            "steps": K, "warmup": W, "ms_per_step": sum(step_ms) / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32x2 (double-float basis, 48-bit significand) + f64 small solves",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N, "r_max": R_MAX, "slack": SLACK, "trunc_tol": TAU,
+                       "block": BLOCK, "pretrain": PRETRAIN, "noise_std": SIGMA,
+                       "l2": "256 MiB buffer written before every update/predict/check (untimed)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "rollout_states_per_s": states_s,
+            "latency_ms": {"update_p50": float(np.percentile(upd_ms, 50)),
+                           "update_p99": float(np.percentile(upd_ms, 99)),
+                           "predict50_p50": float(np.percentile(pred_ms, 50)),
+                           "check_p50": float(np.percentile(chk_ms, 50))},
+            "check_rel_err_last": errs[-1],
+            "kernel_ms_per_step": {c: ms_tot[c] / K for c in classes},
+            "mean_r0": mean_r0,
+            "roofline": roof,
+            "pass_a_roofline": pass_a_roof,
+            "wall_s_timed": t_wall,
+            "e2e": {"value": e2e_value, "unit": "snapshot updates/s",
+                    "h2d_bytes_per_step": (BLOCK + 1) * N * 8, "d2h_bytes_per_step": BLOCK * N * 8 + 16},
+            "gpu_launches": n_launch,
+            "clocks": clocks,
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = {"value": cpu["updates_per_s"], "unit": "snapshot updates/s",
+                                    "cores": cpu_cores(), "kind": "oracle",
+                                    "sample": f"{args.cpu_updates} oracle updates at steady state (rank "
+                                              f"{cpu['rank']}) + a {BLOCK}-state rollout + 1 check; step = "
+                                              f"{BLOCK} x update + rollout + check",
+                                    "rollout_states_per_s": cpu["states_per_s"]}
+        print(json.dumps(line), flush=True)
+    model.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-updates", type=int, default=60, help="oracle updates timed for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

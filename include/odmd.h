@@ -133,6 +133,32 @@ odmd_status odmd_get_basis(odmd_t h, void* out_dev, int64_t ld, int32_t* r);
 /* Number of snapshots received and number of compactions performed (host counters). */
 odmd_status odmd_get_counts(odmd_t h, int64_t* snapshots, int64_t* compactions);
 
+/* Kernel classes for odmd_profile_read. */
+typedef enum {
+  ODMD_K_PASS_A = 0,   /* tall projection/residual pass of an update */
+  ODMD_K_SMALL = 1,    /* small solves of an update (5 kernels) */
+  ODMD_K_PASS_B = 2,   /* tall append or compaction pass of an update */
+  ODMD_K_EIG = 3,      /* eigensolve of the reduced operator */
+  ODMD_K_COEF = 4,     /* modal coefficients of a rollout or check */
+  ODMD_K_ROLLOUT = 5,  /* tall rollout pass (predict, basis export) */
+  ODMD_K_CHECK = 6,    /* tall fused credibility-check pass */
+  ODMD_K_FIRST = 7,    /* norm of the first snapshot */
+  ODMD_K_COUNT = 8
+} odmd_kernel_class;
+
+/* Observability: when enabled (nonzero), every kernel group the handle enqueues is
+ * bracketed by CUDA events on the handle's stream, and the time between them is
+ * accumulated per class; enabling (or disabling) resets the accumulators.  This adds
+ * two event records per group and nothing else. */
+odmd_status odmd_profile_enable(odmd_t h, int32_t enable);
+
+/* Read the accumulators (synchronises).  ms_total[c] and launches[c] for the first
+ * `cap` classes (host arrays; either may be NULL): event time summed over the profiled
+ * groups and the number of kernels launched since the handle was created.  mean_r0
+ * (may be NULL) receives the mean number of basis columns r0 streamed by the profiled
+ * pass-A launches. */
+odmd_status odmd_profile_read(odmd_t h, double* ms_total, int64_t* launches, int32_t cap, double* mean_r0);
+
 /* Release the handle (synchronises first).  The workspace is the caller's again. */
 odmd_status odmd_destroy(odmd_t h);
 

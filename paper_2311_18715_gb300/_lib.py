@@ -15,7 +15,9 @@ EXPORTED = [
     "odmd_config_default", "odmd_footprint", "odmd_create", "odmd_update", "odmd_predict",
     "odmd_check", "odmd_sync", "odmd_get_rank", "odmd_get_singular_values", "odmd_get_eigs",
     "odmd_get_basis", "odmd_get_counts", "odmd_destroy", "odmd_last_error",
+    "odmd_profile_enable", "odmd_profile_read",
 ]
+KERNEL_CLASSES = ["pass_a", "small", "pass_b", "eig", "coef", "rollout", "check", "first"]
 
 
 class OdmdConfig(C.Structure):
@@ -65,6 +67,8 @@ def load_library(path: str | None = None) -> C.CDLL:
         "odmd_get_basis": [vp, vp, i64, C.POINTER(i32)],
         "odmd_get_counts": [vp, C.POINTER(i64), C.POINTER(i64)],
         "odmd_destroy": [vp],
+        "odmd_profile_enable": [vp, i32],
+        "odmd_profile_read": [vp, C.POINTER(dbl), C.POINTER(i64), i32, C.POINTER(dbl)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "../../include/odmd.h"
 #include "odmd_internal.cuh"
@@ -23,6 +24,17 @@ struct odmd_instance {
   bool eig_dirty;
   double* pinned;      // 8 doubles of pinned host memory for read-backs
   std::string err;
+  // observability
+  bool prof_on;
+  double prof_ms[ODMD_K_COUNT];
+  long long launches[ODMD_K_COUNT];
+  struct Pending {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  unsigned long long r0_base[2];  // device pass-A counters at enable time
 };
 
 namespace {
@@ -261,9 +273,52 @@ odmd_status device_status(odmd_t h) {
   return fail(h, ODMD_ERR_NUMERIC, buf);
 }
 
+// Bracket a kernel group with events when profiling; count its kernels always.
+struct ProfScope {
+  odmd_t h;
+  int cls;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ProfScope(odmd_t h_, int cls_, int kernels) : h(h_), cls(cls_) {
+    h->launches[cls] += kernels;
+    if (!h->prof_on) return;
+    a = take();
+    b = take();
+    if (a) cudaEventRecord(a, h->stream);
+  }
+  cudaEvent_t take() {
+    if (!h->pool.empty()) {
+      cudaEvent_t e = h->pool.back();
+      h->pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+  }
+  ~ProfScope() {
+    if (!h->prof_on || !a || !b) return;
+    cudaEventRecord(b, h->stream);
+    h->pending.push_back({cls, a, b});
+  }
+};
+
+void prof_collect(odmd_t h) {
+  for (auto& p : h->pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess)
+      h->prof_ms[p.cls] += ms;
+    h->pool.push_back(p.a);
+    h->pool.push_back(p.b);
+  }
+  h->pending.clear();
+}
+
 odmd_status ensure_eig(odmd_t h) {
   if (!h->eig_dirty) return ODMD_OK;
-  CK(h, launch_eig(h->ws, h->stream), "eig launch");
+  {
+    ProfScope ps(h, ODMD_K_EIG, 1);
+    CK(h, launch_eig(h->ws, h->stream), "eig launch");
+  }
   h->eig_dirty = false;
   return ODMD_OK;
 }
@@ -315,6 +370,12 @@ odmd_status odmd_create(const odmd_config* cfg, void* workspace_dev, size_t byte
   h->cur_h = 0;
   h->curc_h = 0;
   h->eig_dirty = true;
+  h->prof_on = false;
+  for (int i = 0; i < ODMD_K_COUNT; ++i) {
+    h->prof_ms[i] = 0.0;
+    h->launches[i] = 0;
+  }
+  h->r0_base[0] = h->r0_base[1] = 0;
   cudaError_t e = cudaGetDevice(&h->device);
   int sms = 0;
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
@@ -346,14 +407,24 @@ odmd_status odmd_update(odmd_t h, const void* x_dev) {
   const size_t nb = snap_bytes(h);
   if (h->nsnap == 0) {
     CK(h, cudaMemcpyAsync(h->ws.cbuf[h->curc_h], x_dev, nb, cudaMemcpyDeviceToDevice, h->stream), "copy u0");
+    ProfScope ps(h, ODMD_K_FIRST, 1);
     CK(h, launch_first(h->ws, h->stream), "first launch");
     h->nsnap = 1;
     return ODMD_OK;
   }
   CK(h, cudaMemcpyAsync(h->ws.cbuf[h->curc_h ^ 1], x_dev, nb, cudaMemcpyDeviceToDevice, h->stream), "copy x");
-  CK(h, launch_pass_a(h->ws, h->stream), "pass A launch");
-  CK(h, launch_small(h->ws, h->stream), "small solve launch");
-  CK(h, launch_pass_b(h->ws, h->stream), "pass B launch");
+  {
+    ProfScope ps(h, ODMD_K_PASS_A, 1);
+    CK(h, launch_pass_a(h->ws, h->stream), "pass A launch");
+  }
+  {
+    ProfScope ps(h, ODMD_K_SMALL, 5);
+    CK(h, launch_small(h->ws, h->stream), "small solve launch");
+  }
+  {
+    ProfScope ps(h, ODMD_K_PASS_B, 1);
+    CK(h, launch_pass_b(h->ws, h->stream), "pass B launch");
+  }
   h->cur_h ^= 1;
   h->curc_h ^= 1;
   h->nsnap += 1;
@@ -372,7 +443,11 @@ odmd_status odmd_predict(odmd_t h, const double* t_host, int32_t k, void* out_de
   const size_t vs = (size_t)vsz_of(h->cfg.prec);
   for (int j0 = 0; j0 < k; j0 += kRollK) {
     const int kk = (k - j0) < kRollK ? (k - j0) : kRollK;
-    CK(h, launch_coef(h->ws, t_host + j0, kk, h->stream), "coef launch");
+    {
+      ProfScope ps(h, ODMD_K_COEF, 1);
+      CK(h, launch_coef(h->ws, t_host + j0, kk, h->stream), "coef launch");
+    }
+    ProfScope ps(h, ODMD_K_ROLLOUT, 1);
     CK(h, launch_rollout(h->ws, nullptr, kk, static_cast<unsigned char*>(out_dev) + (size_t)j0 * ld * vs, ld, 0,
                          h->stream),
        "rollout launch");
@@ -388,8 +463,14 @@ odmd_status odmd_check(odmd_t h, double t, const void* x_fom_dev, double tol, do
   if (tol <= 0.0) tol = h->cfg.check_tol;
   CK(h, cudaMemcpyAsync(h->ws.xbuf, x_fom_dev, snap_bytes(h), cudaMemcpyDeviceToDevice, h->stream), "copy x_fom");
   if (odmd_status s = ensure_eig(h)) return s;
-  CK(h, launch_coef(h->ws, &t, 1, h->stream), "coef launch");
-  CK(h, launch_check(h->ws, h->stream), "check launch");
+  {
+    ProfScope ps(h, ODMD_K_COEF, 1);
+    CK(h, launch_coef(h->ws, &t, 1, h->stream), "coef launch");
+  }
+  {
+    ProfScope ps(h, ODMD_K_CHECK, 1);
+    CK(h, launch_check(h->ws, h->stream), "check launch");
+  }
   CK(h, cudaMemcpyAsync(h->pinned, h->ws.out2, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "read back");
   if (odmd_status s = device_status(h)) return s;
   const double num = h->pinned[0], den = h->pinned[1];
@@ -465,8 +546,14 @@ odmd_status odmd_get_basis(odmd_t h, void* out_dev, int64_t ld, int32_t* r) {
   if (odmd_status s = read_hdr(h, &hdr)) return s;
   *r = hdr.r;
   if (hdr.r == 0) return ODMD_OK;
-  CK(h, launch_basis_coef(h->ws, h->stream), "basis coef launch");
-  CK(h, launch_rollout(h->ws, nullptr, hdr.r, out_dev, ld, 0, h->stream), "basis launch");
+  {
+    ProfScope ps(h, ODMD_K_COEF, 1);
+    CK(h, launch_basis_coef(h->ws, h->stream), "basis coef launch");
+  }
+  {
+    ProfScope ps(h, ODMD_K_ROLLOUT, 1);
+    CK(h, launch_rollout(h->ws, nullptr, hdr.r, out_dev, ld, 0, h->stream), "basis launch");
+  }
   return device_status(h);
 }
 
@@ -481,9 +568,47 @@ odmd_status odmd_get_counts(odmd_t h, int64_t* snapshots, int64_t* compactions) 
   return ODMD_OK;
 }
 
+static odmd_status read_prof_counters(odmd_t h, unsigned long long* out2) {
+  CK(h, cudaMemcpyAsync(h->pinned, &h->ws.ctl->prof_r0_sum, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                        h->stream),
+     "profile counters");
+  CK(h, cudaStreamSynchronize(h->stream), "stream sync");
+  std::memcpy(out2, h->pinned, 2 * sizeof(unsigned long long));
+  return ODMD_OK;
+}
+
+odmd_status odmd_profile_enable(odmd_t h, int32_t enable) {
+  if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
+  prof_collect(h);
+  for (int i = 0; i < ODMD_K_COUNT; ++i) h->prof_ms[i] = 0.0;
+  if (odmd_status s = read_prof_counters(h, h->r0_base)) return s;
+  h->prof_on = enable != 0;
+  return ODMD_OK;
+}
+
+odmd_status odmd_profile_read(odmd_t h, double* ms_total, int64_t* launches, int32_t cap, double* mean_r0) {
+  if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
+  if (odmd_status s = device_status(h)) return s;
+  prof_collect(h);
+  const int nc = cap < ODMD_K_COUNT ? cap : ODMD_K_COUNT;
+  for (int i = 0; i < nc; ++i) {
+    if (ms_total) ms_total[i] = h->prof_ms[i];
+    if (launches) launches[i] = h->launches[i];
+  }
+  if (mean_r0) {
+    unsigned long long now[2];
+    if (odmd_status s = read_prof_counters(h, now)) return s;
+    const unsigned long long na = now[1] - h->r0_base[1];
+    *mean_r0 = na ? (double)(now[0] - h->r0_base[0]) / (double)na : 0.0;
+  }
+  return ODMD_OK;
+}
+
 odmd_status odmd_destroy(odmd_t h) {
   if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
   cudaError_t e = cudaStreamSynchronize(h->stream);
+  prof_collect(h);
+  for (cudaEvent_t ev : h->pool) cudaEventDestroy(ev);
   cudaFreeHost(h->pinned);
   delete h;
   if (e != cudaSuccess) return fail(nullptr, ODMD_ERR_CUDA, std::string("destroy: ") + cudaGetErrorString(e));

@@ -79,6 +79,8 @@ struct Ctl {
   double gamma;     // j^T x
   double check_num, check_den;  // reductions of the credibility check
   double pad1;
+  unsigned long long prof_r0_sum;  // sum of r0 over pass-A launches (for roofline accounting)
+  unsigned long long prof_a;       // number of pass-A launches
 };
 
 // Scratch of the small solve (single copy).

@@ -362,7 +362,11 @@ __global__ void __launch_bounds__(kThreads) k_pass_a(Ws ws) {
     if (!isfinite(val)) atomicOr(&ctl->status, DEV_NONFINITE);
     ws.sm.red[v] = val;
   }
-  if (tid == 0) ctl->ticket_a = 0u;
+  if (tid == 0) {
+    ctl->ticket_a = 0u;
+    ctl->prof_r0_sum += (unsigned long long)r0;
+    ctl->prof_a += 1ull;
+  }
 }
 
 // ---------------------------------------------------------------------------------------

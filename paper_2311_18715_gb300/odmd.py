@@ -131,6 +131,22 @@ class OnlineDMD:
         self._ck(self._lib.odmd_get_counts(self._h, C.byref(s), C.byref(c)))
         return int(s.value), int(c.value)
 
+    def profile(self, enable: bool = True) -> None:
+        """Start (or stop) per-kernel-class event timing; resets the accumulators."""
+        self._ck(self._lib.odmd_profile_enable(self._h, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        """{class: (ms_total, kernels_launched)} plus 'mean_r0' of the profiled pass-A launches."""
+        from ._lib import KERNEL_CLASSES
+        nk = len(KERNEL_CLASSES)
+        ms = (C.c_double * nk)()
+        nl = (C.c_int64 * nk)()
+        r0 = C.c_double()
+        self._ck(self._lib.odmd_profile_read(self._h, ms, nl, nk, C.byref(r0)))
+        out = {KERNEL_CLASSES[i]: (ms[i], int(nl[i])) for i in range(nk)}
+        out["mean_r0"] = r0.value
+        return out
+
     def close(self) -> None:
         if getattr(self, "_h", None):
             self._ck(self._lib.odmd_destroy(self._h))
