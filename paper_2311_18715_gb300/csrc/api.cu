@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "../../include/odmd.h"
 #include "odmd_internal.cuh"
 
@@ -35,6 +37,7 @@ struct odmd_instance {
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> pool;
   unsigned long long r0_base[2];  // device pass-A counters at enable time
+  std::vector<CUtensorMap> maps_host;  // source of the tensor maps copied into the workspace
 };
 
 namespace {
@@ -46,7 +49,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 struct Layout {
   size_t total;
   size_t off_ctl, off_hdr[2], off_state[2], off_small, off_eig, off_out2, off_part, off_Lh, off_Ll, off_c[2],
-      off_x, off_e;
+      off_x, off_e, off_maps;
   size_t state_doubles, small_bytes, eig_doubles;
   int64_t npad;
   int ldg, cap, rmax, partrows;
@@ -97,7 +100,8 @@ Layout make_layout(const odmd_config& c) {
   Layout L{};
   L.cap = c.r_max + c.slack;
   L.rmax = c.r_max;
-  L.ldg = (int)align_up((size_t)L.cap, 8);
+  // row stride: an odd number of 16-byte chunks, the widest TMA box
+  L.ldg = box_chunks(L.cap, esz_of(c.prec)) * 16 / esz_of(c.prec);
   L.npad = (int64_t)align_up((size_t)c.n, kTile);
   L.partrows = kPartRows;
   const int qld = L.cap + 1;
@@ -108,6 +112,7 @@ Layout make_layout(const odmd_config& c) {
     return at;
   };
   L.off_ctl = take(sizeof(Ctl));
+  L.off_maps = take(2 * kMaxMaps * sizeof(CUtensorMap));
   L.off_hdr[0] = take(sizeof(StateHdr));
   L.off_hdr[1] = take(sizeof(StateHdr));
   L.state_doubles = 3 * (size_t)L.rmax + (size_t)L.rmax * L.rmax + (size_t)qld * L.rmax + qld;
@@ -134,6 +139,8 @@ Layout make_layout(const odmd_config& c) {
   L.total = o;
   return L;
 }
+
+odmd_status fail(odmd_t h, odmd_status s, const std::string& msg);
 
 void carve(Ws& ws, const Layout& L, unsigned char* base, const odmd_config& c, int gridA) {
   ws.n = c.n;
@@ -233,6 +240,45 @@ void carve(Ws& ws, const Layout& L, unsigned char* base, const odmd_config& c, i
   ws.cbuf[1] = base + L.off_c[1];
   ws.xbuf = base + L.off_x;
   ws.ebuf = reinterpret_cast<float2*>(base + L.off_e);
+  ws.maps = reinterpret_cast<const CUtensorMap*>(base + L.off_maps);
+}
+
+// 2-D tile maps of the basis planes: dims {ldg, npad}, box {(2k+1) chunks, kTile rows}.
+odmd_status encode_maps(odmd_t h, const Layout& L) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+      return fail(h, ODMD_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const int esz = esz_of(h->cfg.prec);
+  const int planes = h->cfg.prec == ODMD_FP64 ? 2 : 1;
+  const int maxc = box_chunks(L.cap, esz);
+  h->maps_host.assign(2 * kMaxMaps, CUtensorMap{});
+  const CUtensorMapDataType dt = h->cfg.prec == ODMD_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  for (int pl = 0; pl < planes; ++pl) {
+    void* gaddr = pl == 0 ? h->ws.Lh : (void*)h->ws.Ll;
+    for (int k = 0; k < kMaxMaps; ++k) {
+      const int c = 2 * k + 1;
+      if (c > maxc) break;
+      const cuuint64_t dims[2] = {(cuuint64_t)L.ldg, (cuuint64_t)L.npad};
+      const cuuint64_t strides[1] = {(cuuint64_t)L.ldg * esz};
+      const cuuint32_t box[2] = {(cuuint32_t)(c * 16 / esz), (cuuint32_t)kTile};
+      const cuuint32_t estr[2] = {1, 1};
+      CUresult r = encode(&h->maps_host[pl * kMaxMaps + k], dt, 2, gaddr, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) {
+        char buf[96];
+        std::snprintf(buf, sizeof buf, "cuTensorMapEncodeTiled failed (%d) for box %d", (int)r, c);
+        return fail(h, ODMD_ERR_CUDA, buf);
+      }
+    }
+  }
+  return ODMD_OK;
 }
 
 odmd_status fail(odmd_t h, odmd_status s, const std::string& msg) {
@@ -323,6 +369,8 @@ odmd_status ensure_eig(odmd_t h) {
   return ODMD_OK;
 }
 
+void* base_of(odmd_t h, const Layout&) { return const_cast<CUtensorMap*>(h->ws.maps); }
+
 size_t snap_bytes(const odmd_t h) { return (size_t)h->cfg.n * vsz_of(h->cfg.prec); }
 
 }  // namespace
@@ -391,9 +439,20 @@ odmd_status odmd_create(const odmd_config* cfg, void* workspace_dev, size_t byte
   if (gridA < 1) gridA = 1;
   carve(h->ws, L, reinterpret_cast<unsigned char*>(workspace_dev), *cfg, gridA);
   e = cudaMemsetAsync(workspace_dev, 0, L.total, h->stream);
+  if (e == cudaSuccess) {
+    if (encode_maps(h, L) != ODMD_OK) {
+      std::string m = h->err;
+      cudaFreeHost(h->pinned);
+      delete h;
+      return fail(nullptr, ODMD_ERR_CUDA, m);
+    }
+    e = cudaMemcpyAsync(base_of(h, L), h->maps_host.data(), h->maps_host.size() * sizeof(CUtensorMap),
+                        cudaMemcpyHostToDevice, h->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     cudaFreeHost(h->pinned);
-    std::string m = std::string("create memset: ") + cudaGetErrorString(e);
+    std::string m = std::string("create: ") + cudaGetErrorString(e);
     delete h;
     return fail(nullptr, ODMD_ERR_CUDA, m);
   }

@@ -8,6 +8,7 @@
 // in native FP64.
 #pragma once
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
@@ -20,6 +21,7 @@ constexpr int kMaxR = 64;          // largest r_max
 constexpr int kMaxSlack = 32;      // largest slack
 constexpr int kMaxCap = kMaxR + kMaxSlack;  // largest number of basis columns r0
 constexpr int kMaxN = kMaxR + 1;   // largest core matrix order r + 1
+constexpr int kMaxMaps = 13;       // tensor maps per plane: box widths of 1, 3, ..., 25 chunks
 constexpr int kRollK = 64;         // horizons (columns) per rollout launch
 
 enum Storage { ST_DD = 0, ST_F32 = 1, ST_BF16 = 2 };
@@ -122,6 +124,14 @@ struct Eig {
   double* work;     // scratch for the eigensolver: 8 r_max^2 + 16 r_max
 };
 
+// Box width (in 16-byte chunks, always odd) used for r0 active columns of esz bytes:
+// an odd number of chunks per shared-memory row keeps row-wise float4 reads and
+// column-wise scalar reads of a dense TMA tile free of bank conflicts.
+__host__ __device__ inline int box_chunks(int r0, int esz) {
+  int c = (r0 * esz + 15) / 16;
+  return (c & 1) ? c : c + 1;
+}
+
 struct Ws {
   int64_t n;        // rows
   int64_t npad;     // rows rounded up to kTile
@@ -133,6 +143,8 @@ struct Ws {
   void* cbuf[2];    // snapshot buffers (npad elements of the snapshot type)
   void* xbuf;       // scratch snapshot (check input copy)
   float2* ebuf;     // first-pass residual e = c - L0 a of the update in flight (hi, lo)
+  const CUtensorMap* maps;  // [plane][k]: 2-D tile maps of the basis planes, box of
+                            // (2k+1) chunks x kTile rows; plane 1 only in FP64 mode
   float2* part;     // per-CTA partial sums: gridA x (2*cap+3)
   StateBuf st[2];
   Small sm;
@@ -244,6 +256,15 @@ __device__ __forceinline__ void mbar_drain(uint64_t* bars, int stages, int li, i
       if (global_ns() - t0 > 500000000ull) return;
     }
   }
+}
+
+// 2-D tiled TMA load of box (x, y) of `map` into shared memory, counted on `bar`.
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+      : "memory");
 }
 
 // 1-D bulk copy global -> shared (TMA), completion counted on `bar` in bytes.

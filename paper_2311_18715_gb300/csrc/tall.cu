@@ -41,15 +41,14 @@ __device__ __forceinline__ int rows_in(int64_t n, int64_t row0) {
   return d < kTile ? (int)d : kTile;
 }
 
-__host__ __device__ inline int row_bytes(int r0, int esz) { return ((r0 * esz + 15) / 16) * 16; }
-__host__ __device__ inline int row_stride(int rb) { return ((rb / 16) & 1) ? rb : rb + 16; }
 
-// each stage: the basis rows (per plane) and two per-row slots of 8 bytes
+// each stage: the basis rows (per plane, widest box) and two per-row slots of 8 bytes;
+// every part starts on a 1024-byte boundary (TMA tile destinations need 128).
 template <int ST>
 __host__ __device__ inline int stage_bytes(int cap) {
   using T = Traits<ST>;
-  const int rs = row_stride(row_bytes(cap, T::esz));
-  return kTile * rs * T::planes + 2 * kTile * 8;
+  const int rs_max = 16 * box_chunks(cap, T::esz);
+  return kTile * rs_max * T::planes + 2 * kTile * 8;
 }
 
 // Snapshot element -> float-float
@@ -109,45 +108,58 @@ __device__ __forceinline__ void load_elem(const unsigned char* plane_h, const un
   }
 }
 
-// Shared-memory pipeline over the row tiles owned by this CTA.
+// Shared-memory pipeline over the row tiles owned by this CTA.  Each tile is one 2-D
+// TMA load per basis plane (box: the active chunks of kTile rows) plus 1-D bulk copies
+// of the per-row slots, all completing on the stage's mbarrier.
 template <int ST>
 struct TilePipe {
   using T = Traits<ST>;
-  unsigned char* base;  // kStagesUsed stages
+  unsigned char* base;
   uint64_t* bars;
-  int stages, stage_sz, rb, rs, nch;
+  int stages, stage_sz, rs, nch, plane_off;
   int64_t n;
-  int ldg;
-  const unsigned char* gLh;
-  const unsigned char* gLl;
+  const CUtensorMap* mh;    // map of the hi (or only) plane for the current box, or nullptr
+  const CUtensorMap* ml;    // map of the lo plane (FP64 mode)
   const unsigned char* gc;  // first per-row slot (snapshot c, or the residual e), or nullptr
   const unsigned char* gx;  // second per-row slot (snapshot x), or nullptr
   int vc, vx;               // bytes per row of the two slots
 
+  __device__ void setup(const Ws& ws, int r0, int nstages) {
+    stages = nstages;
+    stage_sz = stage_bytes<ST>(ws.cap);
+    plane_off = kTile * 16 * box_chunks(ws.cap, T::esz);
+    n = ws.n;
+    if (r0 > 0) {
+      const int c = box_chunks(r0, T::esz);
+      rs = 16 * c;
+      nch = c;
+      mh = ws.maps + (c - 1) / 2;
+      ml = (T::planes == 2) ? ws.maps + kMaxMaps + (c - 1) / 2 : nullptr;
+    } else {
+      rs = 16;
+      nch = 0;
+      mh = ml = nullptr;
+    }
+    gc = gx = nullptr;
+    vc = vx = 0;
+  }
   __device__ unsigned char* plane_h(int s) const { return base + (size_t)s * stage_sz; }
-  __device__ unsigned char* plane_l(int s) const { return plane_h(s) + kTile * rs; }
-  __device__ unsigned char* snap_c(int s) const { return plane_h(s) + kTile * rs * T::planes; }
+  __device__ unsigned char* plane_l(int s) const { return plane_h(s) + plane_off; }
+  __device__ unsigned char* snap_c(int s) const { return plane_h(s) + plane_off * T::planes; }
   __device__ unsigned char* snap_x(int s) const { return snap_c(s) + kTile * 8; }
 
-  // Issue the copies of tile `tile` into stage `s` (called by all lanes of warp 0).
+  // Issue the copies of tile `tile` into stage `s` (called by one thread).
   __device__ void issue(int tile, int s) const {
-    const int lane = threadIdx.x & 31;
-    const int64_t row0 = (int64_t)tile * kTile;
-    const int rows = rows_in(n, row0);
-    const uint32_t bytes = (uint32_t)(rows * rb * T::planes) + (gc ? kTile * vc : 0) + (gx ? kTile * vx : 0);
-    if (lane == 0) mbar_arrive_expect_tx(&bars[s], bytes);
-    __syncwarp();
-    if (rb > 0) {
-      for (int i = lane; i < rows; i += 32) {
-        const size_t off = (size_t)(row0 + i) * ldg * T::esz;
-        bulk_g2s(plane_h(s) + i * rs, gLh + off, rb, &bars[s]);
-        if constexpr (T::planes == 2) bulk_g2s(plane_l(s) + i * rs, gLl + off, rb, &bars[s]);
-      }
+    const int row0 = tile * kTile;
+    const uint32_t bytes = (mh ? (uint32_t)(kTile * rs * T::planes) : 0u) + (gc ? kTile * vc : 0) +
+                           (gx ? kTile * vx : 0);
+    mbar_arrive_expect_tx(&bars[s], bytes);
+    if (mh) {
+      tma_load_2d(plane_h(s), mh, 0, row0, &bars[s]);
+      if (T::planes == 2) tma_load_2d(plane_l(s), ml, 0, row0, &bars[s]);
     }
-    if (lane == 0) {
-      if (gc) bulk_g2s(snap_c(s), gc + (size_t)row0 * vc, kTile * vc, &bars[s]);
-      if (gx) bulk_g2s(snap_x(s), gx + (size_t)row0 * vx, kTile * vx, &bars[s]);
-    }
+    if (gc) bulk_g2s(snap_c(s), gc + (size_t)row0 * vc, kTile * vc, &bars[s]);
+    if (gx) bulk_g2s(snap_x(s), gx + (size_t)row0 * vx, kTile * vx, &bars[s]);
   }
 };
 
@@ -177,7 +189,7 @@ template <int ST>
 __global__ void __launch_bounds__(kThreads) k_pass_a(Ws ws) {
   using T = Traits<ST>;
   using snap_t = typename T::snap_t;
-  extern __shared__ __align__(128) unsigned char smem[];
+  extern __shared__ __align__(1024) unsigned char smem[];
   Ctl* ctl = ws.ctl;
   const int cur = ctl->cur, curc = ctl->cur_c;
   const StateBuf st = ws.st[cur];
@@ -185,15 +197,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_a(Ws ws) {
   const int tid = threadIdx.x;
 
   TilePipe<ST> P;
-  P.stages = kStages;
-  P.stage_sz = stage_bytes<ST>(ws.cap);
-  P.rb = row_bytes(r0, T::esz);
-  P.rs = row_stride(row_bytes(ws.cap, T::esz));
-  P.nch = P.rb / 16;
-  P.n = ws.n;
-  P.ldg = ws.ldg;
-  P.gLh = (const unsigned char*)ws.Lh;
-  P.gLl = (const unsigned char*)ws.Ll;
+  P.setup(ws, r0, kStages);
   P.gc = (const unsigned char*)ws.cbuf[curc];
   P.gx = (const unsigned char*)ws.cbuf[curc ^ 1];
   P.vc = T::vsz;
@@ -230,7 +234,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_a(Ws ws) {
   const int64_t ntiles = (ws.n + kTile - 1) / kTile;
   const int G = gridDim.x;
   const int my_tiles = (int)((ntiles - blockIdx.x + G - 1) / G);
-  if (tid < 32) {
+  if (tid == 0) {
     for (int li = 0; li < min(my_tiles, kStages); ++li) P.issue(blockIdx.x + li * G, li);
   }
 
@@ -297,7 +301,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_a(Ws ws) {
       }
     }
     __syncthreads();
-    if (tid < 32 && li + kStages < my_tiles) P.issue(blockIdx.x + (li + kStages) * G, s);
+    if (tid == 0 && li + kStages < my_tiles) P.issue(blockIdx.x + (li + kStages) * G, s);
   }
 
   // ---- per-CTA partials
@@ -378,7 +382,7 @@ template <int ST>
 __global__ void __launch_bounds__(kThreads) k_pass_b(Ws ws) {
   using T = Traits<ST>;
   using snap_t = typename T::snap_t;
-  extern __shared__ __align__(128) unsigned char smem[];
+  extern __shared__ __align__(1024) unsigned char smem[];
   Ctl* ctl = ws.ctl;
   const int tid = threadIdx.x;
   const int mode = ctl->mode;
@@ -391,19 +395,9 @@ __global__ void __launch_bounds__(kThreads) k_pass_b(Ws ws) {
 
   if (mode != PB_NONE) {
     TilePipe<ST> P;
-    P.stages = kStagesB;
-    P.stage_sz = stage_bytes<ST>(ws.cap);
-    P.rb = row_bytes(r0, T::esz);
-    P.rs = row_stride(row_bytes(ws.cap, T::esz));
-    P.nch = P.rb / 16;
-    P.n = ws.n;
-    P.ldg = ws.ldg;
-    P.gLh = (const unsigned char*)ws.Lh;
-    P.gLl = (const unsigned char*)ws.Ll;
+    P.setup(ws, r0, kStagesB);
     P.gc = (const unsigned char*)ws.ebuf;
-    P.gx = nullptr;
     P.vc = 8;
-    P.vx = 0;
     P.base = smem;
     unsigned char* p = smem + (size_t)kStagesB * P.stage_sz;
     P.bars = reinterpret_cast<uint64_t*>(p);
@@ -444,7 +438,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_b(Ws ws) {
 
     const int64_t ntiles = (ws.n + kTile - 1) / kTile;
     const int my_tiles = (int)((ntiles - blockIdx.x + G - 1) / G);
-    if (tid < 32) {
+    if (tid == 0) {
       for (int li = 0; li < min(my_tiles, kStagesB); ++li) P.issue(blockIdx.x + li * G, li);
     }
     const int t = tid & 63, sub = tid >> 6;
@@ -520,7 +514,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_b(Ws ws) {
         }
       }
       __syncthreads();
-      if (tid < 32 && li + kStagesB < my_tiles) P.issue(blockIdx.x + (li + kStagesB) * G, s);
+      if (tid == 0 && li + kStagesB < my_tiles) P.issue(blockIdx.x + (li + kStagesB) * G, s);
     }
   }
 
@@ -550,7 +544,7 @@ template <int ST, bool CHECK>
 __global__ void __launch_bounds__(kThreads) k_rollout(Ws ws, int kcols, void* out, int64_t ld) {
   using T = Traits<ST>;
   using snap_t = typename T::snap_t;
-  extern __shared__ __align__(128) unsigned char smem[];
+  extern __shared__ __align__(1024) unsigned char smem[];
   Ctl* ctl = ws.ctl;
   const int tid = threadIdx.x;
   const int cur = ctl->cur;
@@ -559,19 +553,9 @@ __global__ void __launch_bounds__(kThreads) k_rollout(Ws ws, int kcols, void* ou
   const int G = gridDim.x;
 
   TilePipe<ST> P;
-  P.stages = kStagesR;
-  P.stage_sz = stage_bytes<ST>(ws.cap);
-  P.rb = row_bytes(r0, T::esz);
-  P.rs = row_stride(row_bytes(ws.cap, T::esz));
-  P.nch = P.rb / 16;
-  P.n = ws.n;
-  P.ldg = ws.ldg;
-  P.gLh = (const unsigned char*)ws.Lh;
-  P.gLl = (const unsigned char*)ws.Ll;
+  P.setup(ws, r0, kStagesR);
   P.gc = CHECK ? (const unsigned char*)ws.xbuf : nullptr;
-  P.gx = nullptr;
   P.vc = T::vsz;
-  P.vx = 0;
   P.base = smem;
   unsigned char* p = smem + (size_t)kStagesR * P.stage_sz;
   P.bars = reinterpret_cast<uint64_t*>(p);
@@ -599,7 +583,7 @@ __global__ void __launch_bounds__(kThreads) k_rollout(Ws ws, int kcols, void* ou
 
   const int64_t ntiles = (ws.n + kTile - 1) / kTile;
   const int my_tiles = (int)((ntiles - blockIdx.x + G - 1) / G);
-  if (tid < 32) {
+  if (tid == 0) {
     for (int li = 0; li < min(my_tiles, kStagesR); ++li) P.issue(blockIdx.x + li * G, li);
   }
   // work split: items (t, j); with fewer than 4 columns each dot is split in nsub parts
@@ -685,7 +669,7 @@ __global__ void __launch_bounds__(kThreads) k_rollout(Ws ws, int kcols, void* ou
       }
     }
     __syncthreads();
-    if (tid < 32 && li + kStagesR < my_tiles) P.issue(blockIdx.x + (li + kStagesR) * G, s);
+    if (tid == 0 && li + kStagesR < my_tiles) P.issue(blockIdx.x + (li + kStagesR) * G, s);
   }
 
   if constexpr (CHECK) {

@@ -46,7 +46,7 @@ def test_footprint_and_argument_checks_on_host():
     nb = C.c_size_t()
     assert lib.odmd_footprint(C.byref(cfg), C.byref(nb)) == 0
     # two float planes of N x ceil8(r_max+slack) plus three snapshot buffers dominate
-    plane = 393216 * 56 * 4
+    plane = 393216 * 60 * 4  # row stride: 56 columns rounded up to an odd number of 16-byte chunks
     assert 2 * plane < nb.value < 2 * plane + 3 * 393216 * 8 + (8 << 20)
     bad = OdmdConfig()
     lib.odmd_config_default(C.byref(bad), 100, 65)
