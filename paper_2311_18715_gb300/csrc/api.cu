@@ -116,16 +116,16 @@ Layout make_layout(const odmd_config& c) {
   L.off_hdr[0] = take(sizeof(StateHdr));
   L.off_hdr[1] = take(sizeof(StateHdr));
   L.state_doubles = 3 * (size_t)L.rmax + (size_t)L.rmax * L.rmax + (size_t)qld * L.rmax + qld;
-  L.off_state[0] = take(L.state_doubles * 8);
-  L.off_state[1] = take(L.state_doubles * 8);
-  // small scratch: doubles then ints
-  const size_t nd = (2 * (size_t)L.cap + 3) + 3 * (size_t)qld + 9 * (size_t)kMaxN + 2 * (size_t)kMaxN +
+  L.off_state[0] = take(L.state_doubles * sizeof(float2));
+  L.off_state[1] = take(L.state_doubles * sizeof(float2));
+  // small scratch: double-floats then ints
+  const size_t nd = (2 * (size_t)L.cap + 3) + 3 * (size_t)qld + 10 * (size_t)kMaxN + 2 * (size_t)kMaxN +
                     2 * (size_t)kMaxN * kMaxN + (size_t)qld * L.rmax + (size_t)qld * kRollK;
   const size_t ni = 6 * (size_t)kMaxN;
-  L.small_bytes = nd * 8 + ni * 4;
+  L.small_bytes = nd * sizeof(float2) + ni * 4;
   L.off_small = take(L.small_bytes);
   L.eig_doubles = 4 * (size_t)L.rmax + 2 * (size_t)L.rmax * L.rmax;
-  L.off_eig = take(L.eig_doubles * 8);
+  L.off_eig = take(L.eig_doubles * sizeof(float2));
   L.off_out2 = take(8 * 8);
   L.off_part = take((size_t)L.partrows * (2 * L.cap + 3) * sizeof(float2));
   const size_t plane = (size_t)L.npad * L.ldg * esz_of(c.prec);
@@ -150,13 +150,14 @@ void carve(Ws& ws, const Layout& L, unsigned char* base, const odmd_config& c, i
   ws.ldg = L.ldg;
   ws.prec = (int)c.prec;
   ws.gridA = gridA;
-  ws.tau = c.trunc_tol;
+  ws.tau_h = (float)c.trunc_tol;
+  ws.tau_l = (float)(c.trunc_tol - (double)ws.tau_h);
   ws.ctl = reinterpret_cast<Ctl*>(base + L.off_ctl);
   const int qld = L.cap + 1;
   for (int b = 0; b < 2; ++b) {
     StateBuf& s = ws.st[b];
     s.hdr = reinterpret_cast<StateHdr*>(base + L.off_hdr[b]);
-    double* d = reinterpret_cast<double*>(base + L.off_state[b]);
+    float2* d = reinterpret_cast<float2*>(base + L.off_state[b]);
     s.S = d;
     d += L.rmax;
     s.rf = d;
@@ -169,7 +170,7 @@ void carve(Ws& ws, const Layout& L, unsigned char* base, const odmd_config& c, i
     d += (size_t)qld * L.rmax;
     s.a = d;
   }
-  double* d = reinterpret_cast<double*>(base + L.off_small);
+  float2* d = reinterpret_cast<float2*>(base + L.off_small);
   Small& sm = ws.sm;
   sm.red = d;
   d += 2 * L.cap + 3;
@@ -187,7 +188,7 @@ void carve(Ws& ws, const Layout& L, unsigned char* base, const odmd_config& c, i
   d += kMaxN;
   sm.z = d;
   d += kMaxN;
-  sm.zrot = d;
+  sm.dc = d;
   d += kMaxN;
   sm.rot_c = d;
   d += kMaxN;
@@ -219,7 +220,7 @@ void carve(Ws& ws, const Layout& L, unsigned char* base, const odmd_config& c, i
   sm.org = ip;
   ip += kMaxN;
   sm.src = ip;
-  double* e = reinterpret_cast<double*>(base + L.off_eig);
+  float2* e = reinterpret_cast<float2*>(base + L.off_eig);
   ws.eig.lre = e;
   e += L.rmax;
   ws.eig.lim = e;
@@ -231,8 +232,7 @@ void carve(Ws& ws, const Layout& L, unsigned char* base, const odmd_config& c, i
   ws.eig.Vre = e;
   e += (size_t)L.rmax * L.rmax;
   ws.eig.Vim = e;
-  ws.eig.work = nullptr;
-  ws.out2 = reinterpret_cast<double*>(base + L.off_out2);
+  ws.out2 = reinterpret_cast<float2*>(base + L.off_out2);
   ws.part = reinterpret_cast<float2*>(base + L.off_part);
   ws.Lh = base + L.off_Lh;
   ws.Ll = c.prec == ODMD_FP64 ? reinterpret_cast<float*>(base + L.off_Ll) : nullptr;
@@ -370,6 +370,8 @@ odmd_status ensure_eig(odmd_t h) {
 }
 
 void* base_of(odmd_t h, const Layout&) { return const_cast<CUtensorMap*>(h->ws.maps); }
+
+double join(float2 v) { return (double)v.x + (double)v.y; }
 
 size_t snap_bytes(const odmd_t h) { return (size_t)h->cfg.n * vsz_of(h->cfg.prec); }
 
@@ -530,9 +532,11 @@ odmd_status odmd_check(odmd_t h, double t, const void* x_fom_dev, double tol, do
     ProfScope ps(h, ODMD_K_CHECK, 1);
     CK(h, launch_check(h->ws, h->stream), "check launch");
   }
-  CK(h, cudaMemcpyAsync(h->pinned, h->ws.out2, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "read back");
+  CK(h, cudaMemcpyAsync(h->pinned, h->ws.out2, 2 * sizeof(float2), cudaMemcpyDeviceToHost, h->stream), "read back");
   if (odmd_status s = device_status(h)) return s;
-  const double num = h->pinned[0], den = h->pinned[1];
+  float2 nd[2];
+  std::memcpy(nd, h->pinned, sizeof nd);
+  const double num = join(nd[0]), den = join(nd[1]);
   double err;
   if (den == 0.0)
     err = num == 0.0 ? 0.0 : INFINITY;
@@ -572,7 +576,9 @@ odmd_status odmd_get_singular_values(odmd_t h, double* s_host, int32_t cap, int3
   *r = hdr.r;
   const int nc = hdr.r < cap ? hdr.r : cap;
   if (nc > 0) {
-    CK(h, cudaMemcpy(s_host, h->ws.st[h->cur_h].S, nc * sizeof(double), cudaMemcpyDeviceToHost), "S read");
+    float2 buf[kMaxR];
+    CK(h, cudaMemcpy(buf, h->ws.st[h->cur_h].S, nc * sizeof(float2), cudaMemcpyDeviceToHost), "S read");
+    for (int i = 0; i < nc; ++i) s_host[i] = join(buf[i]);
   }
   return ODMD_OK;
 }
@@ -586,13 +592,17 @@ odmd_status odmd_get_eigs(odmd_t h, double* re_host, double* im_host, double* am
   *r = hdr.r;
   const int nc = hdr.r < cap ? hdr.r : cap;
   if (nc > 0) {
-    CK(h, cudaMemcpy(re_host, h->ws.eig.lre, nc * sizeof(double), cudaMemcpyDeviceToHost), "eig read");
-    CK(h, cudaMemcpy(im_host, h->ws.eig.lim, nc * sizeof(double), cudaMemcpyDeviceToHost), "eig read");
+    float2 br[kMaxR], bi[kMaxR];
+    CK(h, cudaMemcpy(br, h->ws.eig.lre, nc * sizeof(float2), cudaMemcpyDeviceToHost), "eig read");
+    CK(h, cudaMemcpy(bi, h->ws.eig.lim, nc * sizeof(float2), cudaMemcpyDeviceToHost), "eig read");
+    for (int i = 0; i < nc; ++i) {
+      re_host[i] = join(br[i]);
+      im_host[i] = join(bi[i]);
+    }
     if (amp_host) {
-      double br[kMaxR], bi[kMaxR];
-      CK(h, cudaMemcpy(br, h->ws.eig.bre, nc * sizeof(double), cudaMemcpyDeviceToHost), "b read");
-      CK(h, cudaMemcpy(bi, h->ws.eig.bim, nc * sizeof(double), cudaMemcpyDeviceToHost), "b read");
-      for (int i = 0; i < nc; ++i) amp_host[i] = std::hypot(br[i], bi[i]);
+      CK(h, cudaMemcpy(br, h->ws.eig.bre, nc * sizeof(float2), cudaMemcpyDeviceToHost), "b read");
+      CK(h, cudaMemcpy(bi, h->ws.eig.bim, nc * sizeof(float2), cudaMemcpyDeviceToHost), "b read");
+      for (int i = 0; i < nc; ++i) amp_host[i] = std::hypot(join(br[i]), join(bi[i]));
     }
   }
   return ODMD_OK;

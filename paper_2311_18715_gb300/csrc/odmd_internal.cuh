@@ -39,23 +39,26 @@ enum : int {
 // pass-B modes
 enum : int { PB_NONE = 0, PB_APPEND = 1, PB_COMPACT = 2 };
 
+// Small quantities are stored as double-float pairs (float2: hi, lo); see dd.cuh.
+
 // Committed small state (two copies, selected by Ctl::cur).
 struct StateHdr {
   int r;        // rank
   int r0;       // number of tall-basis columns in use
   int pairs;    // snapshot pairs ingested
   int compactions;
-  double cn2;   // ||c||^2 of the latest snapshot c
+  float2 cn2;   // ||c||^2 of the latest snapshot c
+  float2 pad;
 };
 
 struct StateBuf {
   StateHdr* hdr;
-  double* S;    // r_max
-  double* rf;   // r_max   first row of R
-  double* rl;   // r_max   last row of R
-  double* M;    // r_max x r_max, column-major, ld = r_max   (M = L^T U^+ R)
-  double* Q;    // (cap+1) x r_max, column-major, ld = cap+1  (L = L0 Q)
-  double* a;    // cap+1   L0^T c
+  float2* S;    // r_max   singular values
+  float2* rf;   // r_max   first row of R
+  float2* rl;   // r_max   last row of R
+  float2* M;    // r_max x r_max, column-major, ld = r_max   (M = L^T U^+ R)
+  float2* Q;    // (cap+1) x r_max, column-major, ld = cap+1  (L = L0 Q)
+  float2* a;    // cap+1   L0^T c
 };
 
 // Control block: indices of the committed buffers, tickets, status, small scalars.
@@ -74,54 +77,52 @@ struct Ctl {
   int nrot;         // Givens rotations used by the deflation
   int eig_valid;    // eigen-cache matches the committed state
   int eig_r;        // rank the eigen-cache was built for
-  int pad0;
-  double thr;       // tau * max(sigma_1, ||c||)
-  double rho0;      // norm of the part of c outside span(L0)
-  double rho;       // norm of the part of c outside span(L)
-  double gamma;     // j^T x
-  double check_num, check_den;  // reductions of the credibility check
-  double pad1;
+  int scale_exp;    // the core matrix is scaled by 2^-scale_exp for the secular solve
+  float2 thr;       // tau * max(sigma_1, ||c||)
+  float2 rho0;      // norm of the part of c outside span(L0)
+  float2 rho;       // norm of the part of c outside span(L)
+  float2 gamma;     // j^T x
+  float2 check_num, check_den;  // reductions of the credibility check
   unsigned long long prof_r0_sum;  // sum of r0 over pass-A launches (for roofline accounting)
   unsigned long long prof_a;       // number of pass-A launches
 };
 
 // Scratch of the small solve (single copy).
 struct Small {
-  double* red;      // 2*cap+3 reduced tall sums: s (r0), y (r0), eta, ex, xi
-  double* ac;       // cap+1   corrected projection of c onto L0 (a + s)
-  double* yext;     // cap+1   L0_ext^T x
-  double* qn;       // cap+1   new unit direction in L0_ext coordinates
-  double* p;        // kMaxN   L^T c
-  double* w;        // kMaxN   L^T x
-  double* d;        // kMaxN   poles (ascending) of the secular problem, as singular values
-  double* z;        // kMaxN   weights at those poles
+  float2* red;      // 2*cap+3 reduced tall sums: s (r0), y (r0), eta, ex, xi
+  float2* ac;       // cap+1   corrected projection of c onto L0 (a + s)
+  float2* yext;     // cap+1   L0_ext^T x
+  float2* qn;       // cap+1   new unit direction in L0_ext coordinates
+  float2* p;        // kMaxN   L^T c
+  float2* w;        // kMaxN   L^T x
+  float2* d;        // kMaxN   poles (ascending) of the secular problem, as scaled singular values
+  float2* z;        // kMaxN   scaled weights at those poles
   int* pole;        // kMaxN   core coordinate of each pole
-  double* zrot;     // kMaxN   z in core coordinates after the deflating rotations
+  float2* dc;       // kMaxN   scaled diagonal of the core in core coordinates (S, 0)
   int* defl;        // kMaxN   deflated core coordinates
   int* rot_i;       // kMaxN
   int* rot_j;
-  double* rot_c;
-  double* rot_s;
+  float2* rot_c;
+  float2* rot_s;
   int* org;         // kMaxN   origin pole of each root
-  double* mu;       // kMaxN   root minus its origin pole (squared units)
-  double* zhat;     // kMaxN   Loewner weights
-  double* sig;      // kMaxN   singular values of the core, descending
+  float2* mu;       // kMaxN   root minus its origin pole (scaled, squared units)
+  float2* zhat;     // kMaxN   Loewner weights
+  float2* sig;      // 2 kMaxN singular values of the core: roots, then the sorted list
   int* src;         // kMaxN   source of output column j: >=0 root index, <0: -(defl idx)-1
-  double* U;        // kMaxN x kMaxN, column-major   left singular vectors of K (kept)
-  double* V;        // kMaxN x kMaxN                   right singular vectors of K (kept)
-  double* QB;       // (cap+1) x r_max, col-major ld cap+1: pass-B rotation (compaction)
-  double* coef;     // (cap+1) x kRollK rollout coefficients in L0 coordinates
+  float2* U;        // kMaxN x kMaxN, column-major   left singular vectors of K (kept)
+  float2* V;        // kMaxN x kMaxN                   right singular vectors of K (kept)
+  float2* QB;       // (cap+1) x r_max, col-major ld cap+1: pass-B rotation (compaction)
+  float2* coef;     // (cap+1) x kRollK rollout coefficients in L0 coordinates
 };
 
 // Eigen-cache.
 struct Eig {
-  double* lre;      // r_max eigenvalues
-  double* lim;
-  double* Vre;      // r_max x r_max eigenvectors (column-major, unit 2-norm)
-  double* Vim;
-  double* bre;      // r_max  b = V^{-1} (S * r_first)
-  double* bim;
-  double* work;     // scratch for the eigensolver: 8 r_max^2 + 16 r_max
+  float2* lre;      // r_max eigenvalues
+  float2* lim;
+  float2* Vre;      // r_max x r_max eigenvectors (column-major, unit 2-norm)
+  float2* Vim;
+  float2* bre;      // r_max  b = V^{-1} (S * r_first)
+  float2* bim;
 };
 
 // Box width (in 16-byte chunks, always odd) used for r0 active columns of esz bytes:
@@ -136,7 +137,7 @@ struct Ws {
   int64_t n;        // rows
   int64_t npad;     // rows rounded up to kTile
   int rmax, cap, ldg, prec, gridA;
-  double tau;
+  float tau_h, tau_l;  // truncation tolerance as a double-float
   Ctl* ctl;
   void* Lh;         // hi plane (float) / bf16 plane
   float* Ll;        // lo plane (FP64 mode only)
@@ -149,7 +150,7 @@ struct Ws {
   StateBuf st[2];
   Small sm;
   Eig eig;
-  double* out2;     // 4 doubles for host read-back
+  float2* out2;     // 4 double-floats for host read-back
 };
 
 // ------------------------------------------------------------------ float-float arithmetic

@@ -1,4 +1,5 @@
-// Small dense solves of the online DMD update and of the eigen-cache, FP64.
+// Small dense solves of the online DMD update and of the eigen-cache, in double-float
+// arithmetic (dd.cuh) on the FP32 pipes.
 //
 // Update (Sec. 2.3, Brand's rank-1 append in product form L = L0 Q):
 //   k_prep     reduced tall sums -> projection p = L^T c, new direction, core matrix
@@ -15,170 +16,236 @@
 // Appl. 16, 1995).  Every difference d_i^2 - lambda is formed as (d_i - d_o)(d_i + d_o)
 // - mu with lambda = d_o^2 + mu and d_o the nearer pole, which keeps the singular vectors
 // orthogonal to working accuracy.  Negligible z_i and nearly equal d_i are deflated first
-// (a Givens rotation merges the weights of two equal poles).
+// (a Givens rotation merges the weights of two equal poles).  K is scaled by a power of
+// two so that its largest entry lies in [1/2, 1).
 //
 // Eigensolve (lazy, Sec. 2.3: A~ = V Lambda V^{-1}, b = Phi^+ u^0): balancing by powers of
 // two, Householder reduction to Hessenberg form, Francis double-shift QR with Schur
 // vectors (Golub and Van Loan, Matrix Computations, Ch. 7), eigenvectors of the
 // quasi-triangular factor by back substitution, then b from a complex LU solve.
+#include "dd.cuh"
 #include "odmd_internal.cuh"
 
 namespace odmd {
 
-constexpr double kEps = 1.1102230246251565e-16;  // 2^-53
+constexpr float kEpsDD = 7.105427357601002e-15f;  // 2^-47, a safe bound on the unit roundoff
+
+__device__ __forceinline__ dd LD(const float2* p, size_t i) { return dd_of(p[i]); }
+__device__ __forceinline__ void STd(float2* p, size_t i, dd v) { p[i] = f2_of(v); }
+__device__ __forceinline__ dd dzero() { return dd{0.f, 0.f}; }
+
+// sum over the 4 adjacent lanes of a group (every lane of the warp must call it)
+__device__ __forceinline__ dd group4_sum(dd a) {
+  a = a + dd_shfl_xor(a, 1);
+  return a + dd_shfl_xor(a, 2);
+}
+
+// out[j] = sum_{i < nrows} A[j*lda + i] v[i] for j < ncols (4 threads per output).
+// Called by every thread of a 256-thread block; A, v, out in shared or global memory.
+__device__ void colsum(float2* out, const float2* A, int lda, const float2* v, int nrows, int ncols) {
+  const int tid = threadIdx.x;
+  for (int base = 0; base < 4 * ncols; base += 256) {
+    const int item = base + tid;
+    const int j = item >> 2, sub = item & 3;
+    dd acc = dzero();
+    if (j < ncols)
+      for (int i = sub; i < nrows; i += 4) acc = dd_fma(LD(A, (size_t)j * lda + i), LD(v, i), acc);
+    acc = group4_sum(acc);
+    if (j < ncols && sub == 0) out[j] = f2_of(acc);
+  }
+}
+
+// out[i] = sum_{j < ncols} A[j*lda + i] v[j] for i < nrows (4 threads per output)
+__device__ void rowsum(float2* out, const float2* A, int lda, const float2* v, int ncols, int nrows) {
+  const int tid = threadIdx.x;
+  for (int base = 0; base < 4 * nrows; base += 256) {
+    const int item = base + tid;
+    const int i = item >> 2, sub = item & 3;
+    dd acc = dzero();
+    if (i < nrows)
+      for (int j = sub; j < ncols; j += 4) acc = dd_fma(LD(A, (size_t)j * lda + i), LD(v, j), acc);
+    acc = group4_sum(acc);
+    if (i < nrows && sub == 0) out[i] = f2_of(acc);
+  }
+}
+
+// block-wide sum for 256 threads; every thread gets the result
+__device__ dd block_sum256(dd a, float2* scratch8) {
+  a = dd_warp_sum(a);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) scratch8[warp] = f2_of(a);
+  __syncthreads();
+  dd t = dzero();
+  for (int w = 0; w < 8; ++w) t = t + LD(scratch8, w);
+  return t;
+}
 
 // ---------------------------------------------------------------------------------------
 // k_prep
 // ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_prep(Ws ws) {
+constexpr int kPrepThreads = 256;
+
+__global__ void __launch_bounds__(kPrepThreads) k_prep(Ws ws) {
+  extern __shared__ __align__(16) float2 psm[];
   Ctl* ctl = ws.ctl;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int cur = ctl->cur;
   const StateBuf st = ws.st[cur];
   const int r = st.hdr->r, r0 = st.hdr->r0, qld = ws.cap + 1;
-  const double* red = ws.sm.red;
-  __shared__ double ac[kMaxCap + 1], yext[kMaxCap + 1], z[kMaxCap + 1], p[kMaxN], p2[kMaxN];
-  __shared__ double sc[8];
-  __shared__ double dd[kMaxN], zc[kMaxN];
+  float2* sQ = psm;  // r columns of Q, ld qld
+  float2* ac = sQ + (size_t)qld * kMaxR;
+  float2* yx = ac + qld;
+  float2* z = yx + qld;
+  float2* t1 = z + qld;
+  float2* p = t1 + qld;
+  float2* p2 = p + kMaxN;
+  __shared__ float2 red8[8];
+  __shared__ float2 sc[4];
+  __shared__ int isc[4];
+  __shared__ float2 dsc[kMaxN], zsc[kMaxN];
+  __shared__ int defl[kMaxN];
+  const float2* red = ws.sm.red;
 
-  for (int i = tid; i < r0; i += 128) {
-    ac[i] = st.a[i] + red[i];
-    yext[i] = red[r0 + i];
+  for (int idx = tid; idx < r * qld; idx += kPrepThreads) sQ[idx] = st.Q[idx];
+  for (int i = tid; i < r0; i += kPrepThreads) {
+    ac[i] = f2_of(LD(st.a, i) + LD(red, i));
+    yx[i] = red[r0 + i];
   }
   __syncthreads();
-  if (tid == 0) {
-    double ssq = 0.0, sy = 0.0;
-    for (int i = 0; i < r0; ++i) {
-      ssq = fma(red[i], red[i], ssq);
-      sy = fma(red[i], red[r0 + i], sy);
+  if (warp == 0) {
+    dd ssq = dzero(), sy = dzero();
+    for (int i = lane; i < r0; i += 32) {
+      const dd si = LD(red, i);
+      ssq = dd_fma(si, si, ssq);
+      sy = dd_fma(si, LD(red, r0 + i), sy);
     }
-    const double eta = red[2 * r0], ex = red[2 * r0 + 1];
-    const double rho0 = sqrt(fmax(eta - ssq, 0.0));
-    const double cn = sqrt(fmax(st.hdr->cn2, 0.0));
-    const double sig1 = r > 0 ? st.S[0] : 0.0;
-    const double thr = ws.tau * fmax(sig1, cn);
-    const int append = rho0 > thr ? 1 : 0;
-    ctl->thr = thr;
-    ctl->rho0 = rho0;
-    ctl->append = append;
-    ctl->r0e = r0 + append;
-    if (append) {
-      ac[r0] = rho0;
-      yext[r0] = (ex - sy) / rho0;
+    ssq = dd_warp_sum(ssq);
+    sy = dd_warp_sum(sy);
+    if (lane == 0) {
+      const dd eta = LD(red, 2 * r0), ex = LD(red, 2 * r0 + 1);
+      dd rho0sq = eta - ssq;
+      if (rho0sq.h < 0.f) rho0sq = dzero();
+      const dd rho0 = dd_sqrt(rho0sq);
+      const dd cn = dd_sqrt(dd_of(st.hdr->cn2));
+      const dd sig1 = r > 0 ? LD(st.S, 0) : dzero();
+      const dd thr = dd{ws.tau_h, ws.tau_l} * dd_max(sig1, cn);
+      const int append = dd_gt(rho0, thr) ? 1 : 0;
+      ctl->thr = f2_of(thr);
+      ctl->rho0 = f2_of(rho0);
+      ctl->append = append;
+      ctl->r0e = r0 + append;
+      if (append) {
+        ac[r0] = f2_of(rho0);
+        yx[r0] = f2_of(dd_div(ex - sy, rho0));
+      }
+      isc[0] = append;
+      sc[0] = f2_of(thr);
     }
-    sc[0] = append;
   }
   __syncthreads();
-  const int append = (int)sc[0];
+  const int append = isc[0];
   const int r0e = r0 + append;
-  // p = Q^T ac (Q has r0 rows; the appended coordinate is outside span(L))
-  for (int j = tid; j < r; j += 128) {
-    double acc = 0.0;
-    for (int i = 0; i < r0; ++i) acc = fma(st.Q[(size_t)j * qld + i], ac[i], acc);
-    p[j] = acc;
-  }
+  const dd thr = dd_of(sc[0]);
+  // p = Q^T ac   (Q has r0 rows; the appended coordinate lies outside span(L))
+  colsum(p, sQ, qld, ac, r0, r);
   __syncthreads();
-  for (int i = tid; i < r0e; i += 128) {
-    double acc = ac[i];
-    if (i < r0)
-      for (int j = 0; j < r; ++j) acc = fma(-st.Q[(size_t)j * qld + i], p[j], acc);
-    z[i] = acc;
-  }
+  // z = ac - Q p
+  rowsum(t1, sQ, qld, p, r, r0);
   __syncthreads();
-  // second Gram-Schmidt pass in the small space
-  for (int j = tid; j < r; j += 128) {
-    double acc = 0.0;
-    for (int i = 0; i < r0; ++i) acc = fma(st.Q[(size_t)j * qld + i], z[i], acc);
-    p2[j] = acc;
-  }
+  for (int i = tid; i < r0e; i += kPrepThreads) z[i] = i < r0 ? f2_of(LD(ac, i) - LD(t1, i)) : ac[i];
   __syncthreads();
-  for (int i = tid; i < r0; i += 128) {
-    double acc = z[i];
-    for (int j = 0; j < r; ++j) acc = fma(-st.Q[(size_t)j * qld + i], p2[j], acc);
-    z[i] = acc;
-  }
-  for (int j = tid; j < r; j += 128) p[j] += p2[j];
+  // second Gram-Schmidt pass in the small space: p2 = Q^T z, z -= Q p2, p += p2
+  colsum(p2, sQ, qld, z, r0, r);
   __syncthreads();
-  if (tid == 0) {
-    double zz = 0.0;
-    for (int i = 0; i < r0e; ++i) zz = fma(z[i], z[i], zz);
-    double rho = sqrt(zz);
-    if (!(rho > ctl->thr)) rho = 0.0;
-    sc[1] = rho;
-    ctl->rho = rho;
-  }
+  rowsum(t1, sQ, qld, p2, r, r0);
   __syncthreads();
-  const double rho = sc[1];
-  for (int i = tid; i < r0e; i += 128) {
-    ws.sm.qn[i] = rho > 0.0 ? z[i] / rho : 0.0;
-    ws.sm.yext[i] = yext[i];
+  for (int i = tid; i < r0; i += kPrepThreads) z[i] = f2_of(LD(z, i) - LD(t1, i));
+  for (int j = tid; j < r; j += kPrepThreads) p[j] = f2_of(LD(p, j) + LD(p2, j));
+  __syncthreads();
+  dd zz = dzero();
+  for (int i = tid; i < r0e; i += kPrepThreads) zz = dd_fma(LD(z, i), LD(z, i), zz);
+  zz = block_sum256(zz, red8);
+  dd rho = dd_sqrt(zz);
+  if (!dd_gt(rho, thr)) rho = dzero();
+  const dd inv_rho = rho.h > 0.f ? dd_div(dd_of(1.f), rho) : dzero();
+  // w = Q^T y (uses the un-extended y); gamma = qn . yext
+  colsum(ws.sm.w, sQ, qld, yx, r0, r);
+  dd g = dzero();
+  for (int i = tid; i < r0e; i += kPrepThreads) {
+    const dd q = LD(z, i) * inv_rho;
+    STd(ws.sm.qn, i, q);
+    ws.sm.yext[i] = yx[i];
     if (i < r0) ws.sm.ac[i] = ac[i];
+    g = dd_fma(q, LD(yx, i), g);
   }
-  // w = L^T x = Q^T y
-  for (int j = tid; j < r; j += 128) {
-    double acc = 0.0;
-    for (int i = 0; i < r0; ++i) acc = fma(st.Q[(size_t)j * qld + i], yext[i], acc);
-    ws.sm.w[j] = acc;
-    ws.sm.p[j] = p[j];
-  }
-  __syncthreads();
+  g = block_sum256(g, red8);
+  for (int j = tid; j < r; j += kPrepThreads) ws.sm.p[j] = p[j];
   if (tid == 0) {
-    double g = 0.0;
-    if (rho > 0.0)
-      for (int i = 0; i < r0e; ++i) g = fma(z[i] / rho, yext[i], g);
-    ctl->gamma = g;
-    // ---- secular problem of K = [[diag(S), p], [0, rho]], n = r + 1
+    ctl->rho = f2_of(rho);
+    ctl->gamma = f2_of(g);
+  }
+  // ---- secular problem of K = [[diag(S), p], [0, rho]], n = r + 1, scaled to max 1
+  if (warp == 0) {
     const int n = r + 1;
-    double zmax = 0.0;
-    for (int i = 0; i < n; ++i) {
-      dd[i] = i < r ? st.S[i] : 0.0;
-      zc[i] = i < r ? p[i] : rho;
-      zmax = fmax(zmax, fabs(zc[i]));
+    dd mx = dzero();
+    for (int i = lane; i < n; i += 32) {
+      const dd zi = i < r ? LD(p, i) : rho;
+      mx = dd_max(mx, dd_abs(zi));
+      if (i == 0 && r > 0) mx = dd_max(mx, LD(st.S, 0));
     }
-    const double tol = 8.0 * kEps * fmax(r > 0 ? dd[0] : 0.0, zmax);
-    int* defl = ws.sm.defl;
-    int ndefl = 0, nrot = 0;
-    bool isdefl[kMaxN];
-    for (int i = 0; i < n; ++i) {
-      isdefl[i] = !(fabs(zc[i]) > tol);
-      if (isdefl[i]) zc[i] = 0.0;
+    mx = dd_warp_max(mx);
+    int e = 0;
+    if (mx.h > 0.f) frexpf(mx.h, &e);
+    const float tol = 8.f * kEpsDD;  // in scaled units
+    for (int i = lane; i < n; i += 32) {
+      const dd di = i < r ? dd_ldexp(LD(st.S, i), -e) : dzero();
+      const dd zi = dd_ldexp(i < r ? LD(p, i) : rho, -e);
+      dsc[i] = f2_of(di);
+      const bool small = !(fabsf(zi.h) > tol);
+      zsc[i] = small ? make_float2(0.f, 0.f) : f2_of(zi);
+      defl[i] = small ? 1 : 0;
+      STd(ws.sm.dc, i, di);
     }
-    // merge nearly equal poles (coordinate r, the pole at 0, is never merged)
-    int last = -1;
-    for (int i = 0; i < r; ++i) {
-      if (isdefl[i]) continue;
-      if (last >= 0 && dd[last] - dd[i] <= tol) {
-        const double h = hypot(zc[last], zc[i]);
-        const double c = zc[last] / h, s = zc[i] / h;
-        zc[last] = h;
-        zc[i] = 0.0;
-        isdefl[i] = true;
-        ws.sm.rot_i[nrot] = last;
-        ws.sm.rot_j[nrot] = i;
-        ws.sm.rot_c[nrot] = c;
-        ws.sm.rot_s[nrot] = s;
-        ++nrot;
-      } else {
-        last = i;
+    __syncwarp();
+    if (lane == 0) {
+      // merge nearly equal poles (the pole at 0, coordinate r, is never merged)
+      int nrot = 0, last = -1;
+      for (int i = 0; i < r; ++i) {
+        if (defl[i]) continue;
+        if (last >= 0 && (dd_of(dsc[last]) - dd_of(dsc[i])).h <= tol) {
+          const dd zl = dd_of(zsc[last]), zi = dd_of(zsc[i]);
+          const dd h = dd_sqrt(zl * zl + zi * zi);
+          ws.sm.rot_i[nrot] = last;
+          ws.sm.rot_j[nrot] = i;
+          STd(ws.sm.rot_c, nrot, dd_div(zl, h));
+          STd(ws.sm.rot_s, nrot, dd_div(zi, h));
+          ++nrot;
+          zsc[last] = f2_of(h);
+          zsc[i] = make_float2(0.f, 0.f);
+          defl[i] = 1;
+        } else {
+          last = i;
+        }
       }
-    }
-    int m = 0;
-    for (int i = n - 1; i >= 0; --i) {  // ascending poles
-      if (isdefl[i]) {
-        defl[ndefl++] = i;
-      } else {
-        ws.sm.pole[m] = i;
-        ws.sm.d[m] = dd[i];
-        ws.sm.z[m] = zc[i];
-        ++m;
+      int m = 0, nd = 0;
+      for (int i = n - 1; i >= 0; --i) {  // ascending poles
+        if (defl[i]) {
+          ws.sm.defl[nd++] = i;
+        } else {
+          ws.sm.pole[m] = i;
+          ws.sm.d[m] = dsc[i];
+          ws.sm.z[m] = zsc[i];
+          ++m;
+        }
       }
+      ctl->n = n;
+      ctl->m = m;
+      ctl->ndefl = nd;
+      ctl->nrot = nrot;
+      ctl->scale_exp = e;
+      if (!dd_isfinite(rho) || !dd_isfinite(mx)) atomicOr(&ctl->status, DEV_NONFINITE);
     }
-    for (int i = 0; i < n; ++i) ws.sm.zrot[i] = zc[i];
-    ctl->n = n;
-    ctl->m = m;
-    ctl->ndefl = ndefl;
-    ctl->nrot = nrot;
-    if (!isfinite(tol) || !isfinite(rho)) atomicOr(&ctl->status, DEV_NONFINITE);
   }
 }
 
@@ -186,31 +253,32 @@ __global__ void __launch_bounds__(128) k_prep(Ws ws) {
 // k_roots: root j of 1 + sum_i z_i^2/(d_i^2 - lambda) = 0 in (d_j^2, d_{j+1}^2)
 // ---------------------------------------------------------------------------------------
 struct SecSums {
-  double psi, dpsi, phi, dphi;
+  dd psi, dpsi, phi, dphi;
 };
 
 // sums over poles i <= j (psi) and i > j (phi) at lambda = d_o^2 + mu
-__device__ SecSums sec_eval(const double* d, const double* z, int m, int j, int o, double mu) {
-  SecSums s{0.0, 0.0, 0.0, 0.0};
+__device__ SecSums sec_eval(const float2* d, const float2* z, int m, int j, int o, dd mu) {
+  SecSums s{dzero(), dzero(), dzero(), dzero()};
   const int lane = threadIdx.x & 31;
-  const double dob = d[o];
+  const dd dob = LD(d, o);
   for (int i = lane; i < m; i += 32) {
-    const double del = (d[i] - dob) * (d[i] + dob) - mu;  // d_i^2 - lambda
-    const double zi = z[i];
-    const double t = zi / del;
-    const double term = zi * t, dterm = t * t;
+    const dd di = LD(d, i);
+    const dd del = (di - dob) * (di + dob) - mu;  // d_i^2 - lambda
+    const dd zi = LD(z, i);
+    const dd t = dd_div(zi, del);
+    const dd term = zi * t, dterm = t * t;
     if (i <= j) {
-      s.psi += term;
-      s.dpsi += dterm;
+      s.psi = s.psi + term;
+      s.dpsi = s.dpsi + dterm;
     } else {
-      s.phi += term;
-      s.dphi += dterm;
+      s.phi = s.phi + term;
+      s.dphi = s.dphi + dterm;
     }
   }
-  s.psi = warp_sum_d(s.psi);
-  s.dpsi = warp_sum_d(s.dpsi);
-  s.phi = warp_sum_d(s.phi);
-  s.dphi = warp_sum_d(s.dphi);
+  s.psi = dd_warp_sum(s.psi);
+  s.dpsi = dd_warp_sum(s.dpsi);
+  s.phi = dd_warp_sum(s.phi);
+  s.dphi = dd_warp_sum(s.dphi);
   return s;
 }
 
@@ -219,91 +287,94 @@ __global__ void __launch_bounds__(32) k_roots(Ws ws) {
   const int m = ctl->m;
   const int j = blockIdx.x;
   if (j >= m) return;
-  const double* d = ws.sm.d;
-  const double* z = ws.sm.z;
+  const float2* d = ws.sm.d;
+  const float2* z = ws.sm.z;
   const int lane = threadIdx.x;
-  double zsq = 0.0;
-  for (int i = lane; i < m; i += 32) zsq = fma(z[i], z[i], zsq);
-  zsq = warp_sum_d(zsq);
+  dd zsq = dzero();
+  for (int i = lane; i < m; i += 32) zsq = dd_fma(LD(z, i), LD(z, i), zsq);
+  zsq = dd_warp_sum(zsq);
   if (m == 1) {
     if (lane == 0) {
       ws.sm.org[0] = 0;
-      ws.sm.mu[0] = zsq;
-      ws.sm.sig[0] = sqrt(d[0] * d[0] + zsq);
+      STd(ws.sm.mu, 0, zsq);
+      STd(ws.sm.sig, 0, dd_sqrt(LD(d, 0) * LD(d, 0) + zsq));
     }
     return;
   }
   int o;
-  double lo, hi;  // bracket of mu, relative to d_o^2
-  double A, B;    // left and right pole relative to d_o^2 (B unused for the last root)
+  dd lo, hi, A, B;  // bracket of mu and the neighbouring poles, relative to d_o^2
   const bool last = (j == m - 1);
   if (!last) {
-    const double gap = (d[j + 1] - d[j]) * (d[j + 1] + d[j]);
-    const double mid = 0.5 * gap;
-    SecSums s = sec_eval(d, z, m, j, j, mid);
-    if (1.0 + s.psi + s.phi >= 0.0) {
+    const dd dj = LD(d, j), dj1 = LD(d, j + 1);
+    const dd gap = (dj1 - dj) * (dj1 + dj);
+    const dd mid = gap * 0.5f;
+    const SecSums s = sec_eval(d, z, m, j, j, mid);
+    if ((dd_of(1.f) + s.psi + s.phi).h >= 0.f) {
       o = j;
-      lo = 0.0;
+      lo = dzero();
       hi = mid;
-      A = 0.0;
+      A = dzero();
       B = gap;
     } else {
       o = j + 1;
       lo = -mid;
-      hi = 0.0;
+      hi = dzero();
       A = -gap;
-      B = 0.0;
+      B = dzero();
     }
   } else {
     o = j;
-    lo = 0.0;
+    lo = dzero();
     hi = zsq;
-    A = 0.0;
-    B = 0.0;
+    A = dzero();
+    B = dzero();
   }
-  double mu = 0.5 * (lo + hi);
+  dd mu = (lo + hi) * 0.5f;
   bool conv = false;
-  for (int it = 0; it < 64; ++it) {
+  for (int it = 0; it < 80; ++it) {
     const SecSums s = sec_eval(d, z, m, j, o, mu);
-    const double f = 1.0 + s.psi + s.phi;
-    if (f < 0.0)
+    const dd f = dd_of(1.f) + s.psi + s.phi;
+    if (f.h < 0.f)
       lo = mu;
     else
       hi = mu;
-    const double ftol = 8.0 * kEps * (double)m * (1.0 + fabs(s.psi) + fabs(s.phi));
-    if (fabs(f) <= ftol) {
+    const float ftol = 8.f * kEpsDD * (float)m * (1.f + fabsf(s.psi.h) + fabsf(s.phi.h));
+    if (fabsf(f.h) <= ftol) {
       conv = true;
       break;
     }
     // two-pole rational model of f matching value and slope at mu
-    const double c1 = s.dpsi * (A - mu) * (A - mu);
-    const double a1 = s.psi - s.dpsi * (A - mu);
-    double x;
+    const dd Am = A - mu;
+    const dd c1 = s.dpsi * Am * Am;
+    const dd a1 = s.psi - s.dpsi * Am;
+    dd x;
     if (!last) {
-      const double c2 = s.dphi * (B - mu) * (B - mu);
-      const double a2 = s.phi - s.dphi * (B - mu);
-      const double C = 1.0 + a1 + a2;
+      const dd Bm = B - mu;
+      const dd c2 = s.dphi * Bm * Bm;
+      const dd a2 = s.phi - s.dphi * Bm;
+      const dd C = dd_of(1.f) + a1 + a2;
       // C (A-x)(B-x) + c1 (B-x) + c2 (A-x) = 0
-      const double qa = C;
-      const double qb = -(C * (A + B) + c1 + c2);
-      const double qc = C * A * B + c1 * B + c2 * A;
-      if (fabs(qa) <= kEps * (fabs(qb) + fabs(qc))) {
-        x = -qc / qb;
+      const dd qb = -(C * (A + B) + c1 + c2);
+      const dd qc = C * A * B + c1 * B + c2 * A;
+      if (fabsf(C.h) <= kEpsDD * (fabsf(qb.h) + fabsf(qc.h))) {
+        x = dd_div(-qc, qb);
       } else {
-        const double disc = fmax(qb * qb - 4.0 * qa * qc, 0.0);
-        const double q = -0.5 * (qb + copysign(sqrt(disc), qb));
-        const double x1 = q / qa, x2 = qc / q;
-        const bool in1 = x1 > lo && x1 < hi, in2 = x2 > lo && x2 < hi;
-        x = in1 && !in2 ? x1 : (in2 && !in1 ? x2 : (fabs(x1 - mu) < fabs(x2 - mu) ? x1 : x2));
+        const dd disc = qb * qb - C * qc * 4.f;
+        const dd sq = dd_sqrt(disc.h > 0.f ? disc : dzero());
+        const dd q = (qb.h >= 0.f ? qb + sq : qb - sq) * -0.5f;
+        const dd x1 = dd_div(q, C), x2 = dd_div(qc, q);
+        const bool in1 = dd_gt(x1, lo) && dd_lt(x1, hi), in2 = dd_gt(x2, lo) && dd_lt(x2, hi);
+        x = in1 && !in2 ? x1 : (in2 && !in1 ? x2 : (dd_lt(dd_abs(x1 - mu), dd_abs(x2 - mu)) ? x1 : x2));
       }
     } else {
-      const double C = 1.0 + a1 + s.phi;
-      x = C > 0.0 ? A + c1 / C : 0.5 * (lo + hi);
+      const dd C = dd_of(1.f) + a1 + s.phi;
+      x = C.h > 0.f ? A + dd_div(c1, C) : (lo + hi) * 0.5f;
     }
-    if (!(x > lo && x < hi)) x = 0.5 * (lo + hi);
-    const double step = fabs(x - mu);
+    if (!(dd_gt(x, lo) && dd_lt(x, hi))) x = (lo + hi) * 0.5f;
+    const dd step = dd_abs(x - mu);
     mu = x;
-    if (step <= 4.0 * kEps * fabs(mu) || hi - lo <= 4.0 * kEps * fmax(fabs(lo), fabs(hi))) {
+    if (step.h <= 4.f * kEpsDD * fabsf(mu.h) ||
+        (hi - lo).h <= 4.f * kEpsDD * fmaxf(fabsf(lo.h), fabsf(hi.h))) {
       conv = true;
       break;
     }
@@ -311,8 +382,11 @@ __global__ void __launch_bounds__(32) k_roots(Ws ws) {
   if (lane == 0) {
     if (!conv) atomicOr(&ctl->status, DEV_SECULAR);
     ws.sm.org[j] = o;
-    ws.sm.mu[j] = mu;
-    ws.sm.sig[j] = sqrt(fmax(d[o] * d[o] + mu, 0.0));
+    STd(ws.sm.mu, j, mu);
+    const dd dob = LD(d, o);
+    dd lam = dob * dob + mu;
+    if (lam.h < 0.f) lam = dzero();
+    STd(ws.sm.sig, j, dd_sqrt(lam));
   }
 }
 
@@ -322,65 +396,70 @@ __global__ void __launch_bounds__(32) k_roots(Ws ws) {
 // ---------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(32) k_zhat(Ws ws) {
   Ctl* ctl = ws.ctl;
-  const int m = ctl->m, n = ctl->n;
+  const int m = ctl->m;
   const int lane = threadIdx.x;
   if (blockIdx.x == kMaxN) {
-    // order: roots (sig[0..m)) and deflated values (d at coordinate defl[k]); descending
-    const StateBuf st = ws.st[ctl->cur];
-    const int r = st.hdr->r;
-    const int ndefl = ctl->ndefl;
-    __shared__ double val[kMaxN];
+    // order roots (sig[0..m)) and deflated values (scaled diagonal at defl[k]), descending
+    const int nd = ctl->ndefl;
+    __shared__ float2 val[kMaxN];
     __shared__ int code[kMaxN];
-    const int tot = m + ndefl;  // == n
+    const int tot = m + nd;
     for (int e = lane; e < tot; e += 32) {
       if (e < m) {
         val[e] = ws.sm.sig[e];
         code[e] = e;
       } else {
         const int c = ws.sm.defl[e - m];
-        val[e] = c < r ? st.S[c] : 0.0;
+        val[e] = ws.sm.dc[c];
         code[e] = -c - 1;
       }
     }
     __syncwarp();
-    double vmax = 0.0;
-    for (int e = 0; e < tot; ++e) vmax = fmax(vmax, val[e]);
-    const double cut = ws.tau * vmax;
+    dd vmax = dzero();
+    for (int e = 0; e < tot; ++e) vmax = dd_max(vmax, LD(val, e));
+    const dd cut = dd{ws.tau_h, ws.tau_l} * vmax;
     for (int e = lane; e < tot; e += 32) {
       int pos = 0;
-      for (int f = 0; f < tot; ++f) pos += (val[f] > val[e]) || (val[f] == val[e] && f < e);
+      const dd ve = LD(val, e);
+      for (int f = 0; f < tot; ++f) {
+        const dd vf = LD(val, f);
+        pos += dd_gt(vf, ve) || (vf.h == ve.h && vf.l == ve.l && f < e);
+      }
       ws.sm.src[pos] = code[e];
-      ws.sm.sig[kMaxN + pos] = val[e];  // sorted copy after the root slots
+      ws.sm.sig[kMaxN + pos] = val[e];
     }
     if (lane == 0) {
       int keep = 0;
-      if (vmax > 0.0)
-        for (int e = 0; e < tot; ++e) keep += val[e] > cut;
+      if (vmax.h > 0.f)
+        for (int e = 0; e < tot; ++e) keep += dd_gt(LD(val, e), cut);
       ctl->rnew = min(keep, ws.rmax);
-      (void)n;
     }
     return;
   }
   const int i = blockIdx.x;
   if (i >= m) return;
-  const double* d = ws.sm.d;
-  const double di = d[i];
-  double prod = 1.0;
+  const float2* d = ws.sm.d;
+  const dd di = LD(d, i);
+  dd prod = dd_of(1.f);
   for (int k = lane; k < m; k += 32) {
-    const int o = ws.sm.org[k];
-    const double lam_m_di = ws.sm.mu[k] - (di - d[o]) * (di + d[o]);  // lambda_k - d_i^2
-    double f;
-    if (k == m - 1)
+    const dd dko = LD(d, ws.sm.org[k]);
+    const dd lam_m_di = LD(ws.sm.mu, k) - (di - dko) * (di + dko);  // lambda_k - d_i^2
+    dd f;
+    if (k == m - 1) {
       f = lam_m_di;
-    else if (k < i)
-      f = lam_m_di / ((d[k] - di) * (d[k] + di));
-    else
-      f = lam_m_di / ((d[k + 1] - di) * (d[k + 1] + di));
-    prod *= f;
+    } else {
+      const dd dk = LD(d, k < i ? k : k + 1);
+      f = dd_div(lam_m_di, (dk - di) * (dk + di));
+    }
+    prod = prod * f;
   }
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) prod *= __shfl_xor_sync(0xffffffffu, prod, off);
-  if (lane == 0) ws.sm.zhat[i] = copysign(sqrt(fmax(prod, 0.0)), ws.sm.z[i]);
+  for (int off = 16; off > 0; off >>= 1) prod = prod * dd_shfl_xor(prod, off);
+  if (lane == 0) {
+    dd zh = dd_sqrt(prod.h > 0.f ? prod : dzero());
+    if (ws.sm.z[i].x < 0.f) zh = -zh;
+    STd(ws.sm.zhat, i, zh);
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -392,59 +471,61 @@ __global__ void __launch_bounds__(64) k_vectors(Ws ws) {
   if (j >= ctl->rnew) return;
   const int n = ctl->n, m = ctl->m, r = n - 1;
   const int tid = threadIdx.x;
-  __shared__ double u[kMaxN], v[kMaxN], red[4];
+  __shared__ float2 u[kMaxN], v[kMaxN], red[4];
   for (int i = tid; i < n; i += 64) {
-    u[i] = 0.0;
-    v[i] = 0.0;
+    u[i] = make_float2(0.f, 0.f);
+    v[i] = make_float2(0.f, 0.f);
   }
   __syncthreads();
   const int code = ws.sm.src[j];
   if (code >= 0) {
-    const double* d = ws.sm.d;
-    const int o = ws.sm.org[code];
-    const double mu = ws.sm.mu[code];
+    const float2* d = ws.sm.d;
+    const dd dob = LD(d, ws.sm.org[code]);
+    const dd mu = LD(ws.sm.mu, code);
     for (int i = tid; i < m; i += 64) {
-      const double del = (d[i] - d[o]) * (d[i] + d[o]) - mu;  // d_i^2 - lambda
-      const double ui = ws.sm.zhat[i] / del;
+      const dd di = LD(d, i);
+      const dd del = (di - dob) * (di + dob) - mu;  // d_i^2 - lambda
+      const dd ui = dd_div(LD(ws.sm.zhat, i), del);
       const int c = ws.sm.pole[i];
-      u[c] = ui;
-      if (c < r) v[c] = d[i] * ui;
+      u[c] = f2_of(ui);
+      if (c < r) v[c] = f2_of(di * ui);
     }
     __syncthreads();
-    if (tid == 0) v[r] = -1.0;
+    if (tid == 0) v[r] = make_float2(-1.f, 0.f);
     __syncthreads();
-    double su = 0.0, sv = 0.0;
+    dd su = dzero(), sv = dzero();
     for (int i = tid; i < n; i += 64) {
-      su = fma(u[i], u[i], su);
-      sv = fma(v[i], v[i], sv);
+      su = dd_fma(LD(u, i), LD(u, i), su);
+      sv = dd_fma(LD(v, i), LD(v, i), sv);
     }
-    su = warp_sum_d(su);
-    sv = warp_sum_d(sv);
+    su = dd_warp_sum(su);
+    sv = dd_warp_sum(sv);
     if ((tid & 31) == 0) {
-      red[(tid >> 5) * 2] = su;
-      red[(tid >> 5) * 2 + 1] = sv;
+      red[(tid >> 5) * 2] = f2_of(su);
+      red[(tid >> 5) * 2 + 1] = f2_of(sv);
     }
     __syncthreads();
-    const double iu = 1.0 / sqrt(red[0] + red[2]), iv = 1.0 / sqrt(red[1] + red[3]);
+    const dd iu = dd_div(dd_of(1.f), dd_sqrt(LD(red, 0) + LD(red, 2)));
+    const dd iv = dd_div(dd_of(1.f), dd_sqrt(LD(red, 1) + LD(red, 3)));
     for (int i = tid; i < n; i += 64) {
-      u[i] *= iu;
-      v[i] *= iv;
+      u[i] = f2_of(LD(u, i) * iu);
+      v[i] = f2_of(LD(v, i) * iv);
     }
   } else if (tid == 0) {
     const int c = -code - 1;
-    u[c] = 1.0;
-    v[c] = 1.0;
+    u[c] = make_float2(1.f, 0.f);
+    v[c] = make_float2(1.f, 0.f);
   }
   __syncthreads();
   if (tid == 0) {
     for (int t = ctl->nrot - 1; t >= 0; --t) {
       const int a = ws.sm.rot_i[t], b = ws.sm.rot_j[t];
-      const double c = ws.sm.rot_c[t], s = ws.sm.rot_s[t];
-      const double ua = u[a], ub = u[b], va = v[a], vb = v[b];
-      u[a] = c * ua - s * ub;
-      u[b] = s * ua + c * ub;
-      v[a] = c * va - s * vb;
-      v[b] = s * va + c * vb;
+      const dd c = LD(ws.sm.rot_c, t), s = LD(ws.sm.rot_s, t);
+      const dd ua = LD(u, a), ub = LD(u, b), va = LD(v, a), vb = LD(v, b);
+      u[a] = f2_of(c * ua - s * ub);
+      u[b] = f2_of(s * ua + c * ub);
+      v[a] = f2_of(c * va - s * vb);
+      v[b] = f2_of(s * va + c * vb);
     }
   }
   __syncthreads();
@@ -459,9 +540,11 @@ __global__ void __launch_bounds__(64) k_vectors(Ws ws) {
 //   M'    = U'^T [[M, w], [rho r_last^T, gamma]] V'
 //   Q'    = [[Q, q_n(0:r0)], [0, q_n(r0)]] U'     (rows: L0 coordinates incl. the append)
 //   r_first' = [r_first, 0] V'  (= last row of V' when c is u^0),  r_last' = V'[r, :]
-//   S' = sigma'[0:rnew];  a' = L0'^T x
+//   S' = sigma'[0:rnew] (unscaled);  a' = L0'^T x
 // ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_apply(Ws ws) {
+constexpr int kApplyThreads = 256;
+
+__global__ void __launch_bounds__(kApplyThreads) k_apply(Ws ws) {
   Ctl* ctl = ws.ctl;
   const int j = blockIdx.x;
   const int rnew = ctl->rnew;
@@ -472,7 +555,6 @@ __global__ void __launch_bounds__(128) k_apply(Ws ws) {
   const int r0e = ctl->r0e;
   const int cap = ws.cap, qld = cap + 1, rm = ws.rmax;
   const bool compact = r0e > cap;
-  const double rho = ctl->rho, gamma = ctl->gamma;
   if (j == 0 && tid == 0) {
     nx.hdr->r = rnew;
     nx.hdr->r0 = compact ? rnew : r0e;
@@ -482,287 +564,381 @@ __global__ void __launch_bounds__(128) k_apply(Ws ws) {
     ctl->mode = compact ? PB_COMPACT : (ctl->append ? PB_APPEND : PB_NONE);
   }
   if (!compact && j == 0)
-    for (int i = tid; i < r0e; i += 128) nx.a[i] = ws.sm.yext[i];
+    for (int i = tid; i < r0e; i += kApplyThreads) nx.a[i] = ws.sm.yext[i];
   if (j >= rnew) return;
-  __shared__ double v[kMaxN], u[kMaxN], bv[kMaxN], qcol[kMaxCap + 1];
-  for (int i = tid; i < n; i += 128) {
+  const dd rho = dd_of(ctl->rho), gamma = dd_of(ctl->gamma);
+  __shared__ float2 v[kMaxN], u[kMaxN], bv[kMaxN], qcol[kMaxCap + 1], rlv[2];
+  for (int i = tid; i < n; i += kApplyThreads) {
     v[i] = ws.sm.V[(size_t)j * kMaxN + i];
     u[i] = ws.sm.U[(size_t)j * kMaxN + i];
   }
   __syncthreads();
-  // B v
-  for (int i = tid; i < n; i += 128) {
-    double acc;
-    if (i < r) {
-      acc = ws.sm.w[i] * v[r];
-      for (int k = 0; k < r; ++k) acc = fma(st.M[(size_t)k * rm + i], v[k], acc);
-    } else {
-      acc = gamma * v[r];
-      double t = 0.0;
-      for (int k = 0; k < r; ++k) t = fma(st.rl[k], v[k], t);
-      acc = fma(rho, t, acc);
-    }
-    bv[i] = acc;
+  // B v, rows 0..r-1: M v[0:r] + w v_r  (4 threads per row; r <= 64 rows)
+  {
+    const int i = tid >> 2, sub = tid & 3;
+    dd acc = dzero();
+    if (i < r)
+      for (int k = sub; k < r; k += 4) acc = dd_fma(LD(st.M, (size_t)k * rm + i), LD(v, k), acc);
+    acc = group4_sum(acc);
+    if (i < r && sub == 0) bv[i] = f2_of(dd_fma(LD(ws.sm.w, i), LD(v, r), acc));
   }
-  // Q' column j (rows 0..r0e-1)
-  for (int i = tid; i < r0e; i += 128) {
-    double acc = ws.sm.qn[i] * u[r];
+  // row r: rho (r_last . v[0:r]) + gamma v_r   (warp 7)
+  if ((tid >> 5) == 7) {
+    const int lane = tid & 31;
+    dd t = dzero();
+    for (int k = lane; k < r; k += 32) t = dd_fma(LD(st.rl, k), LD(v, k), t);
+    t = dd_warp_sum(t);
+    if (lane == 0) rlv[0] = f2_of(t);
+  }
+  // Q' column j (rows 0..r0e-1): Q u[0:r] + qn u_r
+  for (int base = 0; base < 4 * r0e; base += kApplyThreads) {
+    const int item = base + tid;
+    const int i = item >> 2, sub = item & 3;
+    dd acc = dzero();
     if (i < r0)
-      for (int k = 0; k < r; ++k) acc = fma(st.Q[(size_t)k * qld + i], u[k], acc);
-    qcol[i] = acc;
+      for (int k = sub; k < r; k += 4) acc = dd_fma(LD(st.Q, (size_t)k * qld + i), LD(u, k), acc);
+    acc = group4_sum(acc);
+    if (i < r0e && sub == 0) qcol[i] = f2_of(dd_fma(LD(ws.sm.qn, i), LD(u, r), acc));
   }
   __syncthreads();
-  // M' column j
-  for (int i = tid; i < rnew; i += 128) {
-    double acc = 0.0;
-    for (int l = 0; l < n; ++l) acc = fma(ws.sm.U[(size_t)i * kMaxN + l], bv[l], acc);
-    nx.M[(size_t)j * rm + i] = acc;
+  if (tid == 0) bv[r] = f2_of(dd_fma(rho, LD(rlv, 0), gamma * LD(v, r)));
+  __syncthreads();
+  // M' column j: U'^T (B v)   (4 threads per output row i < rnew)
+  {
+    const int i = tid >> 2, sub = tid & 3;
+    dd acc = dzero();
+    if (i < rnew)
+      for (int l = sub; l < n; l += 4) acc = dd_fma(LD(ws.sm.U, (size_t)i * kMaxN + l), LD(bv, l), acc);
+    acc = group4_sum(acc);
+    if (i < rnew && sub == 0) nx.M[(size_t)j * rm + i] = f2_of(acc);
   }
   if (compact) {
-    for (int i = tid; i < r0e; i += 128) ws.sm.QB[(size_t)j * qld + i] = qcol[i];
-    for (int i = tid; i < rnew; i += 128) nx.Q[(size_t)j * qld + i] = (i == j) ? 1.0 : 0.0;
+    for (int i = tid; i < r0e; i += kApplyThreads) ws.sm.QB[(size_t)j * qld + i] = qcol[i];
+    for (int i = tid; i < rnew; i += kApplyThreads)
+      nx.Q[(size_t)j * qld + i] = make_float2(i == j ? 1.f : 0.f, 0.f);
   } else {
-    for (int i = tid; i < r0e; i += 128) nx.Q[(size_t)j * qld + i] = qcol[i];
+    for (int i = tid; i < r0e; i += kApplyThreads) nx.Q[(size_t)j * qld + i] = qcol[i];
   }
-  if (tid == 0) {
-    double rf = 0.0;
-    if (st.hdr->pairs == 0) {
-      rf = v[r];
-    } else {
-      for (int k = 0; k < r; ++k) rf = fma(st.rf[k], v[k], rf);
-    }
-    nx.rf[j] = rf;
-    nx.rl[j] = v[r];
-    nx.S[j] = ws.sm.sig[kMaxN + j];
-    if (compact) {
-      double a = 0.0;
-      for (int i = 0; i < r0e; ++i) a = fma(qcol[i], ws.sm.yext[i], a);
-      nx.a[j] = a;
+  // r_first', r_last', S', a' (compaction)  -- warp 0
+  if (tid < 32) {
+    const int lane = tid;
+    dd rf = dzero();
+    if (st.hdr->pairs != 0)
+      for (int k = lane; k < r; k += 32) rf = dd_fma(LD(st.rf, k), LD(v, k), rf);
+    rf = dd_warp_sum(rf);
+    dd a = dzero();
+    if (compact)
+      for (int i = lane; i < r0e; i += 32) a = dd_fma(LD(qcol, i), LD(ws.sm.yext, i), a);
+    a = dd_warp_sum(a);
+    if (lane == 0) {
+      nx.rf[j] = st.hdr->pairs == 0 ? v[r] : f2_of(rf);
+      nx.rl[j] = v[r];
+      STd(nx.S, j, dd_ldexp(LD(ws.sm.sig, kMaxN + j), ctl->scale_exp));
+      if (compact) STd(nx.a, j, a);
     }
   }
 }
 
 // ---------------------------------------------------------------------------------------
-// eigensolver (one warp; scalar decisions are computed identically by every lane)
+// eigensolver (one CTA of 128 threads).  Scalars are computed identically by every
+// thread from shared data; row/column updates are split across the threads.
 // ---------------------------------------------------------------------------------------
 constexpr int kLD = kMaxR + 1;
+constexpr int kEigThreads = 128;
 
 struct EigSmem {
-  double H[kMaxR * kLD];   // Hessenberg / quasi-triangular Schur factor T, row-major
-  double Z[kMaxR * kLD];   // Schur vectors, row-major
-  double Xr[kMaxR * kLD];  // eigenvectors of T, X[i][j] = component i of vector j
-  double Xi[kMaxR * kLD];
-  double scale[kMaxR];
-  double wr[kMaxR], wi[kMaxR];
+  float2 H[kMaxR * kLD];   // Hessenberg / quasi-triangular Schur factor T, row-major
+  float2 Z[kMaxR * kLD];   // Schur vectors, row-major
+  float2 Xr[kMaxR * kLD];  // eigenvectors of T, X[i][j] = component i of vector j
+  float2 Xi[kMaxR * kLD];
+  float scale[kMaxR];      // balancing (powers of two)
+  float2 wr[kMaxR], wi[kMaxR];
+  float2 v[kMaxR];         // reflector / scratch
+  float2 tmp[kMaxR];
 };
 
-__device__ __forceinline__ void warp_sync() { __syncwarp(0xffffffffu); }
+__device__ __forceinline__ dd HH(const float2* A, int i, int k) { return dd_of(A[i * kLD + k]); }
 
-// Householder reflector (I - beta v v^T) a = alpha e1 with v[0] = 1 (len 2 or 3).
-__device__ __forceinline__ double house_small(const double* a, int len, double* v) {
-  double sigma = 0.0;
-  for (int i = 1; i < len; ++i) sigma = fma(a[i], a[i], sigma);
-  v[0] = 1.0;
-  for (int i = 1; i < len; ++i) v[i] = 0.0;
-  if (sigma == 0.0) return 0.0;
-  const double x0 = a[0];
-  const double mu = sqrt(x0 * x0 + sigma);
-  const double v0 = x0 <= 0.0 ? x0 - mu : -sigma / (x0 + mu);
-  const double beta = 2.0 * v0 * v0 / (sigma + v0 * v0);
-  for (int i = 1; i < len; ++i) v[i] = a[i] / v0;
-  return beta;
-}
-
-// rows i0..i0+len-1, columns c0..cn-1 of row-major A: A <- (I - beta v v^T) A
-__device__ __forceinline__ void refl_left(double* A, int i0, int len, int c0, int cn, const double* v, double beta) {
-  for (int c = c0 + (int)threadIdx.x; c < cn; c += 32) {
-    double s = 0.0;
-    for (int i = 0; i < len; ++i) s = fma(v[i], A[(i0 + i) * kLD + c], s);
-    s *= beta;
-    for (int i = 0; i < len; ++i) A[(i0 + i) * kLD + c] = fma(-s, v[i], A[(i0 + i) * kLD + c]);
+// rows i0..i0+len-1 of A, columns c0..cn-1: A <- A - beta v (v^T A)
+__device__ void refl_left(float2* A, int i0, int len, int c0, int cn, const dd* v, dd beta) {
+  for (int c = c0 + (int)threadIdx.x; c < cn; c += kEigThreads) {
+    dd s = dzero();
+    for (int i = 0; i < len; ++i) s = dd_fma(v[i], HH(A, i0 + i, c), s);
+    s = s * beta;
+    for (int i = 0; i < len; ++i) A[(i0 + i) * kLD + c] = f2_of(HH(A, i0 + i, c) - s * v[i]);
   }
 }
 
-// rows 0..rn-1, columns j0..j0+len-1: A <- A (I - beta v v^T)
-__device__ __forceinline__ void refl_right(double* A, int rn, int j0, int len, const double* v, double beta) {
-  for (int row = (int)threadIdx.x; row < rn; row += 32) {
-    double s = 0.0;
-    for (int i = 0; i < len; ++i) s = fma(A[row * kLD + j0 + i], v[i], s);
-    s *= beta;
-    for (int i = 0; i < len; ++i) A[row * kLD + j0 + i] = fma(-s, v[i], A[row * kLD + j0 + i]);
+// rows rs..rn-1 (split over nth threads), columns j0..j0+len-1: A <- A - (A v) beta v^T
+__device__ void refl_right(float2* A, int rs, int rn, int j0, int len, const dd* v, dd beta, int tid, int nth) {
+  for (int row = rs + tid; row < rn; row += nth) {
+    dd s = dzero();
+    for (int i = 0; i < len; ++i) s = dd_fma(HH(A, row, j0 + i), v[i], s);
+    s = s * beta;
+    for (int i = 0; i < len; ++i) A[row * kLD + j0 + i] = f2_of(HH(A, row, j0 + i) - s * v[i]);
   }
 }
 
-__global__ void __launch_bounds__(32) k_eig(Ws ws) {
+// Power of two that brings the largest |a_i| into [1/2, 1) (0 for a zero vector).  The
+// double-float format has the exponent range of FP32, so reflector inputs are scaled
+// before squaring; a reflector is unchanged when its vector is scaled.
+__device__ __forceinline__ int scale_exp_of(const dd* a, int len) {
+  float mx = 0.f;
+  for (int i = 0; i < len; ++i) mx = fmaxf(mx, fabsf(a[i].h));
+  int e = 0;
+  if (mx > 0.f) frexpf(mx, &e);
+  return e;
+}
+
+// Reflector (I - beta v v^T) a = -sign(a0) ||a|| e1 for len 2 or 3, unnormalised v
+// (of the scaled input).
+__device__ __forceinline__ dd house3(const dd* a_in, int len, dd* v) {
+  const int e = scale_exp_of(a_in, len);
+  dd a[3];
+  for (int i = 0; i < len; ++i) a[i] = dd_ldexp(a_in[i], -e);
+  dd sig = dzero();
+  for (int i = 1; i < len; ++i) sig = dd_fma(a[i], a[i], sig);
+  for (int i = 0; i < len; ++i) v[i] = a[i];
+  if (sig.h == 0.f) return dzero();
+  const dd mu = dd_sqrt(dd_fma(a[0], a[0], sig));
+  const dd ax = dd_abs(a[0]);
+  v[0] = a[0].h >= 0.f ? a[0] + mu : a[0] - mu;  // a0 + sign(a0) mu
+  return dd_div(dd_of(1.f), mu * (mu + ax));      // 2 / (v^T v)
+}
+
+__global__ void __launch_bounds__(kEigThreads) k_eig(Ws ws) {
   extern __shared__ __align__(16) unsigned char esm[];
   EigSmem& E = *reinterpret_cast<EigSmem*>(esm);
   Ctl* ctl = ws.ctl;
-  const int lane = threadIdx.x;
+  const int tid = threadIdx.x;
   const StateBuf st = ws.st[ctl->cur];
   const int r = st.hdr->r, rm = ws.rmax;
+  __shared__ float2 nrm_s[1];
+  __shared__ int piv_s;
   if (r == 0) {
-    if (lane == 0) {
+    if (tid == 0) {
       atomicOr(&ctl->status, DEV_NOMODEL);
       ctl->eig_r = 0;
       ctl->eig_valid = 1;
     }
     return;
   }
-  double* H = E.H;
-  double* Z = E.Z;
+  float2* H = E.H;
+  float2* Z = E.Z;
   // A~ = M diag(S)^-1
-  for (int idx = lane; idx < r * r; idx += 32) {
+  for (int idx = tid; idx < r * r; idx += kEigThreads) {
     const int i = idx / r, k = idx % r;
-    H[i * kLD + k] = st.M[(size_t)k * rm + i] / st.S[k];
-    Z[i * kLD + k] = (i == k) ? 1.0 : 0.0;
+    H[i * kLD + k] = f2_of(dd_div(LD(st.M, (size_t)k * rm + i), LD(st.S, k)));
+    Z[i * kLD + k] = make_float2(i == k ? 1.f : 0.f, 0.f);
   }
-  for (int i = lane; i < r; i += 32) E.scale[i] = 1.0;
-  warp_sync();
+  for (int i = tid; i < r; i += kEigThreads) E.scale[i] = 1.f;
+  __syncthreads();
 
-  // ---- balancing: D^-1 A D with D a diagonal of powers of two (row/column 1-norms)
-  for (int sweep = 0; sweep < 64; ++sweep) {
-    bool changed = false;
-    for (int i = 0; i < r; ++i) {
-      double c = 0.0, rr = 0.0;
-      for (int k = lane; k < r; k += 32)
-        if (k != i) {
-          c += fabs(H[k * kLD + i]);
-          rr += fabs(H[i * kLD + k]);
+  // ---- balancing by powers of two (row/column 1-norms from the hi parts), warp 0
+  if (tid < 32) {
+    const int lane = tid;
+    for (int sweep = 0; sweep < 40; ++sweep) {
+      bool changed = false;
+      for (int i = 0; i < r; ++i) {
+        float c = 0.f, rr = 0.f;
+        for (int k = lane; k < r; k += 32)
+          if (k != i) {
+            c += fabsf(H[k * kLD + i].x);
+            rr += fabsf(H[i * kLD + k].x);
+          }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          c += __shfl_xor_sync(0xffffffffu, c, o);
+          rr += __shfl_xor_sync(0xffffffffu, rr, o);
         }
-      c = warp_sum_d(c);
-      rr = warp_sum_d(rr);
-      if (c == 0.0 || rr == 0.0) continue;
-      const double s = c + rr;
-      double f = 1.0, g = rr / 2.0;
-      while (c < g && f < 1e18) {
-        f *= 2.0;
-        c *= 4.0;
+        if (c == 0.f || rr == 0.f) continue;
+        const float s = c + rr;
+        float f = 1.f, g = rr * 0.5f;
+        while (c < g && f < 1e18f) {
+          f *= 2.f;
+          c *= 4.f;
+        }
+        g = rr * 2.f;
+        while (c >= g && f > 1e-18f) {
+          f *= 0.5f;
+          c *= 0.25f;
+        }
+        if ((c + rr) / f < 0.95f * s) {
+          changed = true;
+          const float inv = 1.f / f;  // exact: f is a power of two
+          for (int k = lane; k < r; k += 32) {
+            const float2 a = H[i * kLD + k];
+            H[i * kLD + k] = make_float2(a.x * inv, a.y * inv);
+          }
+          __syncwarp();
+          for (int k = lane; k < r; k += 32) {
+            const float2 a = H[k * kLD + i];
+            H[k * kLD + i] = make_float2(a.x * f, a.y * f);
+          }
+          if (lane == 0) E.scale[i] *= f;
+          __syncwarp();
+        }
       }
-      g = rr * 2.0;
-      while (c >= g && f > 1e-18) {
-        f /= 2.0;
-        c /= 4.0;
-      }
-      if ((c + rr) / f < 0.95 * s) {
-        changed = true;
-        for (int k = lane; k < r; k += 32) H[i * kLD + k] /= f;
-        warp_sync();
-        for (int k = lane; k < r; k += 32) H[k * kLD + i] *= f;
-        if (lane == 0) E.scale[i] *= f;
-        warp_sync();
-      }
+      if (!changed) break;
     }
-    if (!changed) break;
   }
-  warp_sync();
+  __syncthreads();
 
   // ---- Householder reduction to upper Hessenberg form, Z accumulates the reflectors
-  {
-    double* v = E.wr;  // scratch (length r)
-    for (int k = 0; k + 2 < r; ++k) {
-      const int len = r - k - 1;
-      double sigma = 0.0;
-      for (int i = 1; i < len; ++i) sigma = fma(H[(k + 1 + i) * kLD + k], H[(k + 1 + i) * kLD + k], sigma);
-      if (sigma == 0.0) continue;
-      const double x0 = H[(k + 1) * kLD + k];
-      const double mu = sqrt(x0 * x0 + sigma);
-      const double v0 = x0 <= 0.0 ? x0 - mu : -sigma / (x0 + mu);
-      const double beta = 2.0 * v0 * v0 / (sigma + v0 * v0);
-      warp_sync();
-      for (int i = lane; i < len; i += 32) v[i] = i == 0 ? 1.0 : H[(k + 1 + i) * kLD + k] / v0;
-      warp_sync();
-      refl_left(H, k + 1, len, k, r, v, beta);
-      warp_sync();
-      refl_right(H, r, k + 1, len, v, beta);
-      refl_right(Z, r, k + 1, len, v, beta);
-      warp_sync();
-      if (lane == 0) {
-        H[(k + 1) * kLD + k] = mu;
-        for (int i = k + 2; i < r; ++i) H[i * kLD + k] = 0.0;
+  __shared__ int col_exp;
+  for (int k = 0; k + 2 < r; ++k) {
+    const int len = r - k - 1;
+    if (tid < 32) {
+      float mx = 0.f;
+      for (int i = tid; i < len; i += 32) mx = fmaxf(mx, fabsf(H[(k + 1 + i) * kLD + k].x));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      int e = 0;
+      if (mx > 0.f) frexpf(mx, &e);
+      dd sg = dzero();
+      for (int i = 1 + tid; i < len; i += 32) {
+        const dd hs = dd_ldexp(HH(H, k + 1 + i, k), -e);
+        sg = dd_fma(hs, hs, sg);
       }
-      warp_sync();
+      sg = dd_warp_sum(sg);
+      if (tid == 0) {
+        E.tmp[0] = f2_of(sg);
+        col_exp = e;
+      }
     }
+    __syncthreads();
+    const dd sigma = dd_of(E.tmp[0]);
+    const int ce = col_exp;
+    if (sigma.h == 0.f) {
+      __syncthreads();
+      continue;
+    }
+    // reflector of the column scaled by 2^-ce (v scaled alike; the reflector is the same)
+    const dd x0 = dd_ldexp(HH(H, k + 1, k), -ce);
+    const dd mu = dd_sqrt(dd_fma(x0, x0, sigma));
+    const dd v0 = x0.h >= 0.f ? x0 + mu : x0 - mu;
+    const dd beta = dd_div(dd_of(1.f), mu * (mu + dd_abs(x0)));
+    for (int i = tid; i < len; i += kEigThreads)
+      E.v[i] = i == 0 ? f2_of(v0) : f2_of(dd_ldexp(HH(H, k + 1 + i, k), -ce));
+    __syncthreads();
+    // left: rows k+1.., columns k..r-1
+    for (int c = k + tid; c < r; c += kEigThreads) {
+      dd s = dzero();
+      for (int i = 0; i < len; ++i) s = dd_fma(LD(E.v, i), HH(H, k + 1 + i, c), s);
+      s = s * beta;
+      for (int i = 0; i < len; ++i) H[(k + 1 + i) * kLD + c] = f2_of(HH(H, k + 1 + i, c) - s * LD(E.v, i));
+    }
+    __syncthreads();
+    // right on H and Z (rows 0..r-1): threads 0..63 -> H, 64..127 -> Z
+    {
+      float2* A = tid < 64 ? H : Z;
+      for (int row = tid & 63; row < r; row += 64) {
+        dd s = dzero();
+        for (int i = 0; i < len; ++i) s = dd_fma(HH(A, row, k + 1 + i), LD(E.v, i), s);
+        s = s * beta;
+        for (int i = 0; i < len; ++i) A[row * kLD + k + 1 + i] = f2_of(HH(A, row, k + 1 + i) - s * LD(E.v, i));
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      H[(k + 1) * kLD + k] = f2_of(dd_ldexp(x0.h >= 0.f ? -mu : mu, ce));
+      for (int i = k + 2; i < r; ++i) H[i * kLD + k] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();
   }
 
   // ---- Francis double-shift QR (Golub & Van Loan, Alg. 7.5.1 with deflation)
-  double norm = 0.0;
-  for (int idx = lane; idx < r * r; idx += 32) norm += fabs(H[(idx / r) * kLD + idx % r]);
-  norm = warp_sum_d(norm);
+  // Deflation: a subdiagonal entry is negligible next to its diagonal neighbours, or
+  // next to ||H||_F (double-float rounding leaves absolute noise of order eps ||H||,
+  // which a purely local test could wait on forever; both are within backward error).
+  float fro = 0.f;
+  for (int idx = 0; idx < r * r; ++idx) {
+    const float hv = H[(idx / r) * kLD + idx % r].x;
+    fro = fmaf(hv, hv, fro);
+  }
+  const float gtol = 2.f * kEpsDD * sqrtf(fro);
   int hi = r - 1, iter = 0, total = 0;
   bool failed = false;
   while (hi >= 0) {
     int l = hi;
     while (l > 0) {
-      double s = fabs(H[(l - 1) * kLD + l - 1]) + fabs(H[l * kLD + l]);
-      if (s == 0.0) s = norm;
-      if (fabs(H[l * kLD + l - 1]) <= kEps * s) break;
+      const float s = fabsf(H[(l - 1) * kLD + l - 1].x) + fabsf(H[l * kLD + l].x);
+      const float sub = fabsf(H[l * kLD + l - 1].x);
+      if (sub <= kEpsDD * s || sub <= gtol) break;
       --l;
     }
-    warp_sync();
-    if (l > 0 && lane == 0) H[l * kLD + l - 1] = 0.0;
-    warp_sync();
+    __syncthreads();
+    if (l > 0 && tid == 0) H[l * kLD + l - 1] = make_float2(0.f, 0.f);
+    __syncthreads();
     if (l == hi) {
-      if (lane == 0) {
+      if (tid == 0) {
         E.wr[hi] = H[hi * kLD + hi];
-        E.wi[hi] = 0.0;
+        E.wi[hi] = make_float2(0.f, 0.f);
       }
-      warp_sync();
+      __syncthreads();
       --hi;
       iter = 0;
       continue;
     }
     if (l == hi - 1) {
-      const double a = H[(hi - 1) * kLD + hi - 1], b = H[(hi - 1) * kLD + hi];
-      const double c = H[hi * kLD + hi - 1], d = H[hi * kLD + hi];
-      const double p = 0.5 * (a - d);
-      const double disc = p * p + b * c;
-      warp_sync();
-      if (disc >= 0.0) {
+      const dd a = HH(H, hi - 1, hi - 1), b = HH(H, hi - 1, hi);
+      const dd c = HH(H, hi, hi - 1), d = HH(H, hi, hi);
+      const dd p = (a - d) * 0.5f;
+      const dd disc = dd_fma(p, p, b * c);
+      __syncthreads();
+      if (disc.h >= 0.f) {
         // real pair: rotate the block to upper triangular form
-        const double sq = sqrt(disc);
-        const double l1 = 0.5 * (a + d) + copysign(sq, p);
-        double ur = b, vr = l1 - a;
-        const double ur2 = l1 - d, vr2 = c;
-        if (fabs(ur2) + fabs(vr2) > fabs(ur) + fabs(vr)) {
+        const dd sq = dd_sqrt(disc);
+        const dd l1 = (a + d) * 0.5f + (p.h >= 0.f ? sq : -sq);
+        dd ur = b, vr = l1 - a;
+        const dd ur2 = l1 - d, vr2 = c;
+        if (fabsf(ur2.h) + fabsf(vr2.h) > fabsf(ur.h) + fabsf(vr.h)) {
           ur = ur2;
           vr = vr2;
         }
-        const double nn = hypot(ur, vr);
-        double cs = 1.0, sn = 0.0;
-        if (nn > 0.0) {
-          cs = ur / nn;
-          sn = vr / nn;
+        {
+          const dd uv[2] = {ur, vr};
+          const int e2 = scale_exp_of(uv, 2);
+          ur = dd_ldexp(ur, -e2);
+          vr = dd_ldexp(vr, -e2);
         }
-        for (int col = hi - 1 + lane; col < r; col += 32) {
-          const double x1 = H[(hi - 1) * kLD + col], x2 = H[hi * kLD + col];
-          H[(hi - 1) * kLD + col] = cs * x1 + sn * x2;
-          H[hi * kLD + col] = -sn * x1 + cs * x2;
+        const dd nn = dd_sqrt(ur * ur + vr * vr);
+        dd cs = dd_of(1.f), sn = dzero();
+        if (nn.h > 0.f) {
+          cs = dd_div(ur, nn);
+          sn = dd_div(vr, nn);
         }
-        warp_sync();
-        for (int row = lane; row <= hi; row += 32) {
-          const double x1 = H[row * kLD + hi - 1], x2 = H[row * kLD + hi];
-          H[row * kLD + hi - 1] = cs * x1 + sn * x2;
-          H[row * kLD + hi] = -sn * x1 + cs * x2;
+        for (int col = hi - 1 + tid; col < r; col += kEigThreads) {
+          const dd x1 = HH(H, hi - 1, col), x2 = HH(H, hi, col);
+          H[(hi - 1) * kLD + col] = f2_of(cs * x1 + sn * x2);
+          H[hi * kLD + col] = f2_of(cs * x2 - sn * x1);
         }
-        for (int row = lane; row < r; row += 32) {
-          const double x1 = Z[row * kLD + hi - 1], x2 = Z[row * kLD + hi];
-          Z[row * kLD + hi - 1] = cs * x1 + sn * x2;
-          Z[row * kLD + hi] = -sn * x1 + cs * x2;
+        __syncthreads();
+        {
+          float2* A = tid < 64 ? H : Z;
+          const int rn = tid < 64 ? hi + 1 : r;
+          for (int row = tid & 63; row < rn; row += 64) {
+            const dd x1 = HH(A, row, hi - 1), x2 = HH(A, row, hi);
+            A[row * kLD + hi - 1] = f2_of(cs * x1 + sn * x2);
+            A[row * kLD + hi] = f2_of(cs * x2 - sn * x1);
+          }
         }
-        warp_sync();
-        if (lane == 0) {
-          H[hi * kLD + hi - 1] = 0.0;
+        __syncthreads();
+        if (tid == 0) {
+          H[hi * kLD + hi - 1] = make_float2(0.f, 0.f);
           E.wr[hi - 1] = H[(hi - 1) * kLD + hi - 1];
           E.wr[hi] = H[hi * kLD + hi];
-          E.wi[hi - 1] = 0.0;
-          E.wi[hi] = 0.0;
+          E.wi[hi - 1] = make_float2(0.f, 0.f);
+          E.wi[hi] = make_float2(0.f, 0.f);
         }
-      } else if (lane == 0) {
-        E.wr[hi - 1] = E.wr[hi] = 0.5 * (a + d);
-        E.wi[hi - 1] = sqrt(-disc);
-        E.wi[hi] = -sqrt(-disc);
+      } else if (tid == 0) {
+        const dd re = (a + d) * 0.5f, im = dd_sqrt(-disc);
+        E.wr[hi - 1] = f2_of(re);
+        E.wr[hi] = f2_of(re);
+        E.wi[hi - 1] = f2_of(im);
+        E.wi[hi] = f2_of(-im);
       }
-      warp_sync();
+      __syncthreads();
       hi -= 2;
       iter = 0;
       continue;
@@ -772,226 +948,239 @@ __global__ void __launch_bounds__(32) k_eig(Ws ws) {
       break;
     }
     ++iter;
-    double ssum, tprod;
+    dd ssum, tprod;
     if (iter % 11 == 10) {  // exceptional shift
-      const double s = fabs(H[hi * kLD + hi - 1]) + fabs(H[(hi - 1) * kLD + hi - 2]);
-      const double h = 0.75 * s + H[hi * kLD + hi];
-      ssum = 2.0 * h;
-      tprod = h * h + 0.4375 * s * s;
+      const dd s = dd_abs(HH(H, hi, hi - 1)) + dd_abs(HH(H, hi - 1, hi - 2));
+      const dd h = s * 0.75f + HH(H, hi, hi);
+      ssum = h * 2.f;
+      tprod = dd_fma(h, h, s * s * 0.4375f);
     } else {
-      ssum = H[(hi - 1) * kLD + hi - 1] + H[hi * kLD + hi];
-      tprod = H[(hi - 1) * kLD + hi - 1] * H[hi * kLD + hi] - H[(hi - 1) * kLD + hi] * H[hi * kLD + hi - 1];
+      ssum = HH(H, hi - 1, hi - 1) + HH(H, hi, hi);
+      tprod = HH(H, hi - 1, hi - 1) * HH(H, hi, hi) - HH(H, hi - 1, hi) * HH(H, hi, hi - 1);
     }
-    double x = H[l * kLD + l] * H[l * kLD + l] + H[l * kLD + l + 1] * H[(l + 1) * kLD + l] -
-               ssum * H[l * kLD + l] + tprod;
-    double y = H[(l + 1) * kLD + l] * (H[l * kLD + l] + H[(l + 1) * kLD + l + 1] - ssum);
-    double zz = H[(l + 1) * kLD + l] * H[(l + 2) * kLD + l + 1];
+    const dd hll = HH(H, l, l), hl1l = HH(H, l + 1, l);
+    dd x = hll * hll + HH(H, l, l + 1) * hl1l - ssum * hll + tprod;
+    dd y = hl1l * (hll + HH(H, l + 1, l + 1) - ssum);
+    dd zz = hl1l * HH(H, l + 2, l + 1);
     for (int k = l; k <= hi - 2; ++k) {
-      double a3[3] = {x, y, zz}, v[3];
-      const double beta = house_small(a3, 3, v);
-      warp_sync();
-      if (beta != 0.0) {
+      const dd a3[3] = {x, y, zz};
+      dd v[3];
+      const dd beta = house3(a3, 3, v);
+      __syncthreads();
+      if (beta.h != 0.f) {
         refl_left(H, k, 3, max(l, k - 1), r, v, beta);
-        warp_sync();
-        refl_right(H, min(k + 4, hi + 1), k, 3, v, beta);
-        refl_right(Z, r, k, 3, v, beta);
-        warp_sync();
-        if (k > l && lane == 0) {
-          H[(k + 1) * kLD + k - 1] = 0.0;
-          H[(k + 2) * kLD + k - 1] = 0.0;
+        __syncthreads();
+        {
+          float2* A = tid < 64 ? H : Z;
+          const int rn = tid < 64 ? min(k + 4, hi + 1) : r;
+          refl_right(A, 0, rn, k, 3, v, beta, tid & 63, 64);
         }
-        warp_sync();
+        __syncthreads();
+        if (k > l && tid == 0) {
+          H[(k + 1) * kLD + k - 1] = make_float2(0.f, 0.f);
+          H[(k + 2) * kLD + k - 1] = make_float2(0.f, 0.f);
+        }
+        __syncthreads();
       }
-      x = H[(k + 1) * kLD + k];
-      y = H[(k + 2) * kLD + k];
-      if (k < hi - 2) zz = H[(k + 3) * kLD + k];
+      x = HH(H, k + 1, k);
+      y = HH(H, k + 2, k);
+      if (k < hi - 2) zz = HH(H, k + 3, k);
     }
     {
-      double a2[2] = {x, y}, v[3];
-      const double beta = house_small(a2, 2, v);
-      warp_sync();
-      if (beta != 0.0) {
+      const dd a2[2] = {x, y};
+      dd v[3];
+      const dd beta = house3(a2, 2, v);
+      __syncthreads();
+      if (beta.h != 0.f) {
         refl_left(H, hi - 1, 2, max(l, hi - 2), r, v, beta);
-        warp_sync();
-        refl_right(H, hi + 1, hi - 1, 2, v, beta);
-        refl_right(Z, r, hi - 1, 2, v, beta);
-        warp_sync();
-        if (hi - 2 >= l && lane == 0) H[hi * kLD + hi - 2] = 0.0;
-        warp_sync();
+        __syncthreads();
+        {
+          float2* A = tid < 64 ? H : Z;
+          const int rn = tid < 64 ? hi + 1 : r;
+          refl_right(A, 0, rn, hi - 1, 2, v, beta, tid & 63, 64);
+        }
+        __syncthreads();
+        if (hi - 2 >= l && tid == 0) H[hi * kLD + hi - 2] = make_float2(0.f, 0.f);
+        __syncthreads();
       }
     }
   }
   if (failed) {
-    if (lane == 0) {
+    if (tid == 0) {
       atomicOr(&ctl->status, DEV_EIG_NOCONV);
       ctl->eig_r = r;
       ctl->eig_valid = 1;
     }
     return;
   }
-  warp_sync();
+  __syncthreads();
 
-  // ---- eigenvectors of T by back substitution: column j of X solves (T - lambda_j) x = 0
-  // (x_j = 1 for a real eigenvalue; for a complex pair (j, j+1) with wi[j] > 0 the block's
-  // own eigenvector [b; lambda - a] starts the substitution; column j+1 is its conjugate).
-  double tnorm = 0.0;
-  for (int idx = lane; idx < r * r; idx += 32) tnorm = fmax(tnorm, fabs(H[(idx / r) * kLD + idx % r]));
-  for (int o = 16; o > 0; o >>= 1) tnorm = fmax(tnorm, __shfl_xor_sync(0xffffffffu, tnorm, o));
-  const double smin = fmax(kEps * tnorm, 1e-290);
-  for (int j = lane; j < r; j += 32) {  // each lane owns whole eigenvectors
-    const double lr = E.wr[j], li = E.wi[j];
-    if (li < 0.0) continue;
-    double* xr = E.Xr + j;
-    double* xi = E.Xi + j;
+  // ---- eigenvectors of T by back substitution (one thread per eigenvector); column j
+  // solves (T - lambda_j) x = 0: x_j = 1 for a real eigenvalue; for a complex pair
+  // (j, j+1) with wi[j] > 0 the block's eigenvector starts the substitution and column
+  // j+1 receives the conjugate afterwards.
+  float tnorm = 0.f;
+  for (int idx = 0; idx < r * r; ++idx) tnorm = fmaxf(tnorm, fabsf(H[(idx / r) * kLD + idx % r].x));
+  const float smin = fmaxf(kEpsDD * tnorm, 1e-30f);
+  for (int j = tid; j < r; j += kEigThreads) {
+    const cdd lam{dd_of(E.wr[j]), dd_of(E.wi[j])};
+    if (lam.im.h < 0.f) continue;
     for (int i = 0; i < r; ++i) {
-      xr[i * kLD] = 0.0;
-      xi[i * kLD] = 0.0;
+      E.Xr[i * kLD + j] = make_float2(0.f, 0.f);
+      E.Xi[i * kLD + j] = make_float2(0.f, 0.f);
     }
-    if (li == 0.0) {
-      xr[j * kLD] = 1.0;
+    if (lam.im.h == 0.f) {
+      E.Xr[j * kLD + j] = make_float2(1.f, 0.f);
     } else {
-      const double a = H[j * kLD + j], b = H[j * kLD + j + 1];
-      const double c = H[(j + 1) * kLD + j], d = H[(j + 1) * kLD + j + 1];
-      if (fabs(b) >= fabs(c)) {
-        xr[j * kLD] = b;
-        xr[(j + 1) * kLD] = lr - a;
-        xi[(j + 1) * kLD] = li;
+      const dd a = HH(H, j, j), b = HH(H, j, j + 1), c = HH(H, j + 1, j), d = HH(H, j + 1, j + 1);
+      if (fabsf(b.h) >= fabsf(c.h)) {
+        E.Xr[j * kLD + j] = f2_of(b);
+        E.Xr[(j + 1) * kLD + j] = f2_of(lam.re - a);
+        E.Xi[(j + 1) * kLD + j] = f2_of(lam.im);
       } else {
-        xr[j * kLD] = lr - d;
-        xi[j * kLD] = li;
-        xr[(j + 1) * kLD] = c;
+        E.Xr[j * kLD + j] = f2_of(lam.re - d);
+        E.Xi[j * kLD + j] = f2_of(lam.im);
+        E.Xr[(j + 1) * kLD + j] = f2_of(c);
       }
     }
     int i = j - 1;
     while (i >= 0) {
-      const bool pair = (i > 0) && H[i * kLD + i - 1] != 0.0;
+      const bool pair = (i > 0) && H[i * kLD + i - 1].x != 0.f;
       const int i0 = pair ? i - 1 : i;
-      double rr0 = 0.0, ri0 = 0.0, rr1 = 0.0, ri1 = 0.0;
+      cdd r1{dzero(), dzero()}, r0v{dzero(), dzero()};
       for (int k = i + 1; k < r; ++k) {
-        rr1 -= H[i * kLD + k] * xr[k * kLD];
-        ri1 -= H[i * kLD + k] * xi[k * kLD];
+        const cdd xk{HH(E.Xr, k, j), HH(E.Xi, k, j)};
+        const dd h1 = HH(H, i, k);
+        r1 = r1 - cdd{h1 * xk.re, h1 * xk.im};
         if (pair) {
-          rr0 -= H[i0 * kLD + k] * xr[k * kLD];
-          ri0 -= H[i0 * kLD + k] * xi[k * kLD];
+          const dd h0 = HH(H, i0, k);
+          r0v = r0v - cdd{h0 * xk.re, h0 * xk.im};
         }
       }
       if (!pair) {
-        double dr = H[i * kLD + i] - lr, di = -li;
-        if (fabs(dr) + fabs(di) < smin) dr = smin;
-        const double den = dr * dr + di * di;
-        xr[i * kLD] = (rr1 * dr + ri1 * di) / den;
-        xi[i * kLD] = (ri1 * dr - rr1 * di) / den;
+        cdd den{HH(H, i, i) - lam.re, -lam.im};
+        if (fabsf(den.re.h) + fabsf(den.im.h) < smin) den.re = dd_of(smin);
+        const cdd xi = cdd_div(r1, den);
+        E.Xr[i * kLD + j] = f2_of(xi.re);
+        E.Xi[i * kLD + j] = f2_of(xi.im);
         i -= 1;
       } else {
-        const double ar = H[i0 * kLD + i0] - lr, ai = -li;
-        const double br = H[i0 * kLD + i], cr = H[i * kLD + i0];
-        const double dr = H[i * kLD + i] - lr, di = -li;
-        double detr = ar * dr - ai * di - br * cr;
-        const double deti = ar * di + ai * dr;
-        if (fabs(detr) + fabs(deti) < smin * tnorm) detr = smin * tnorm;
-        const double dn = detr * detr + deti * deti;
-        const double n0r = rr0 * dr - ri0 * di - br * rr1;
-        const double n0i = rr0 * di + ri0 * dr - br * ri1;
-        const double n1r = ar * rr1 - ai * ri1 - cr * rr0;
-        const double n1i = ar * ri1 + ai * rr1 - cr * ri0;
-        xr[i0 * kLD] = (n0r * detr + n0i * deti) / dn;
-        xi[i0 * kLD] = (n0i * detr - n0r * deti) / dn;
-        xr[i * kLD] = (n1r * detr + n1i * deti) / dn;
-        xi[i * kLD] = (n1i * detr - n1r * deti) / dn;
+        // [[a - lam, b], [c, d - lam]] [x0; x1] = [r0; r1]
+        const cdd am{HH(H, i0, i0) - lam.re, -lam.im};
+        const cdd dm{HH(H, i, i) - lam.re, -lam.im};
+        const dd bb = HH(H, i0, i), cc = HH(H, i, i0);
+        cdd det = am * dm - cdd{bb * cc, dzero()};
+        if (fabsf(det.re.h) + fabsf(det.im.h) < smin * tnorm) det.re = dd_of(smin * tnorm);
+        const cdd n0 = r0v * dm - cdd{bb * r1.re, bb * r1.im};
+        const cdd n1 = am * r1 - cdd{cc * r0v.re, cc * r0v.im};
+        const cdd x0 = cdd_div(n0, det), x1 = cdd_div(n1, det);
+        E.Xr[i0 * kLD + j] = f2_of(x0.re);
+        E.Xi[i0 * kLD + j] = f2_of(x0.im);
+        E.Xr[i * kLD + j] = f2_of(x1.re);
+        E.Xi[i * kLD + j] = f2_of(x1.im);
         i -= 2;
       }
-      double mx = 0.0;
-      for (int k = 0; k < r; ++k) mx = fmax(mx, fabs(xr[k * kLD]) + fabs(xi[k * kLD]));
-      if (mx > 1e100) {
+      float mx = 0.f;
+      for (int k = 0; k < r; ++k) mx = fmaxf(mx, fabsf(E.Xr[k * kLD + j].x) + fabsf(E.Xi[k * kLD + j].x));
+      if (mx > 1e8f) {
+        int e = 0;
+        frexpf(mx, &e);
         for (int k = 0; k < r; ++k) {
-          xr[k * kLD] /= mx;
-          xi[k * kLD] /= mx;
+          E.Xr[k * kLD + j] = f2_of(dd_ldexp(HH(E.Xr, k, j), -e));
+          E.Xi[k * kLD + j] = f2_of(dd_ldexp(HH(E.Xi, k, j), -e));
         }
       }
     }
   }
-  warp_sync();
+  __syncthreads();
   // ---- V = D Z X, unit 2-norm columns; conjugate partners
-  double* Vre = ws.eig.Vre;
-  double* Vim = ws.eig.Vim;
+  float2* Vre = ws.eig.Vre;
+  float2* Vim = ws.eig.Vim;
   for (int j = 0; j < r; ++j) {
-    const double li = E.wi[j];
-    if (li < 0.0) continue;
-    double nrm = 0.0;
-    for (int row = lane; row < r; row += 32) {
-      double sr = 0.0, si = 0.0;
+    if (E.wi[j].x < 0.f) continue;
+    for (int row = tid; row < r; row += kEigThreads) {
+      dd sr = dzero(), si = dzero();
       for (int k = 0; k < r; ++k) {
-        sr = fma(Z[row * kLD + k], E.Xr[k * kLD + j], sr);
-        si = fma(Z[row * kLD + k], E.Xi[k * kLD + j], si);
+        sr = dd_fma(HH(Z, row, k), HH(E.Xr, k, j), sr);
+        si = dd_fma(HH(Z, row, k), HH(E.Xi, k, j), si);
       }
-      sr *= E.scale[row];
-      si *= E.scale[row];
-      Vre[(size_t)j * rm + row] = sr;
-      Vim[(size_t)j * rm + row] = si;
-      nrm += sr * sr + si * si;
+      E.tmp[row] = f2_of(sr * E.scale[row]);
+      E.v[row] = f2_of(si * E.scale[row]);
     }
-    nrm = warp_sum_d(nrm);
-    const double inv = nrm > 0.0 ? 1.0 / sqrt(nrm) : 0.0;
-    for (int row = lane; row < r; row += 32) {
-      Vre[(size_t)j * rm + row] *= inv;
-      Vim[(size_t)j * rm + row] *= inv;
-      if (li > 0.0) {
-        Vre[(size_t)(j + 1) * rm + row] = Vre[(size_t)j * rm + row];
-        Vim[(size_t)(j + 1) * rm + row] = -Vim[(size_t)j * rm + row];
+    __syncthreads();
+    if (tid < 32) {
+      dd nrm = dzero();
+      for (int row = tid; row < r; row += 32)
+        nrm = dd_fma(LD(E.tmp, row), LD(E.tmp, row), dd_fma(LD(E.v, row), LD(E.v, row), nrm));
+      nrm = dd_warp_sum(nrm);
+      if (tid == 0) nrm_s[0] = f2_of(nrm.h > 0.f ? dd_div(dd_of(1.f), dd_sqrt(nrm)) : dzero());
+    }
+    __syncthreads();
+    const dd inv = dd_of(nrm_s[0]);
+    for (int row = tid; row < r; row += kEigThreads) {
+      const dd re = LD(E.tmp, row) * inv, im = LD(E.v, row) * inv;
+      Vre[(size_t)j * rm + row] = f2_of(re);
+      Vim[(size_t)j * rm + row] = f2_of(im);
+      if (E.wi[j].x > 0.f) {
+        Vre[(size_t)(j + 1) * rm + row] = f2_of(re);
+        Vim[(size_t)(j + 1) * rm + row] = f2_of(-im);
       }
     }
+    __syncthreads();
   }
-  for (int j = lane; j < r; j += 32) {
+  for (int j = tid; j < r; j += kEigThreads) {
     ws.eig.lre[j] = E.wr[j];
     ws.eig.lim[j] = E.wi[j];
   }
-  __threadfence_block();
-  warp_sync();
+  __syncthreads();
 
   // ---- b = V^{-1} (S * r_first): complex Gaussian elimination with partial pivoting
-  double* Ar = E.H;
-  double* Ai = E.Z;
-  double* br = E.Xr;
-  double* bi = E.Xi;
-  for (int idx = lane; idx < r * r; idx += 32) {
+  float2* Ar = E.H;
+  float2* Ai = E.Z;
+  float2* br = E.tmp;
+  float2* bi = E.v;
+  for (int idx = tid; idx < r * r; idx += kEigThreads) {
     const int i = idx / r, k = idx % r;
     Ar[i * kLD + k] = Vre[(size_t)k * rm + i];
     Ai[i * kLD + k] = Vim[(size_t)k * rm + i];
   }
-  for (int i = lane; i < r; i += 32) {
-    br[i] = st.S[i] * st.rf[i];
-    bi[i] = 0.0;
+  for (int i = tid; i < r; i += kEigThreads) {
+    br[i] = f2_of(LD(st.S, i) * LD(st.rf, i));
+    bi[i] = make_float2(0.f, 0.f);
   }
-  warp_sync();
-  double amax = 0.0;
-  for (int idx = lane; idx < r * r; idx += 32)
-    amax = fmax(amax, hypot(Ar[(idx / r) * kLD + idx % r], Ai[(idx / r) * kLD + idx % r]));
-  for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  __syncthreads();
+  float amax = 0.f;
+  for (int idx = 0; idx < r * r; ++idx)
+    amax = fmaxf(amax, fabsf(Ar[(idx / r) * kLD + idx % r].x) + fabsf(Ai[(idx / r) * kLD + idx % r].x));
   bool singular = false;
   for (int k = 0; k < r; ++k) {
-    int piv = k;
-    double pv = 0.0;
-    for (int i = k; i < r; ++i) {
-      const double a = hypot(Ar[i * kLD + k], Ai[i * kLD + k]);
-      if (a > pv) {
-        pv = a;
-        piv = i;
+    if (tid == 0) {
+      int piv = k;
+      float pv = 0.f;
+      for (int i = k; i < r; ++i) {
+        const float a = fabsf(Ar[i * kLD + k].x) + fabsf(Ai[i * kLD + k].x);
+        if (a > pv) {
+          pv = a;
+          piv = i;
+        }
       }
+      piv_s = pv > 0.f ? piv : -1;
+      if (pv <= 1e-13f * amax) singular = true;
     }
-    if (pv <= 1e-14 * amax) singular = true;
-    if (pv == 0.0) break;
-    warp_sync();
+    __syncthreads();
+    const int piv = piv_s;
+    if (piv < 0) break;
     if (piv != k) {
-      for (int c = lane; c < r; c += 32) {
-        double t = Ar[k * kLD + c];
+      for (int c = tid; c < r; c += kEigThreads) {
+        float2 t = Ar[k * kLD + c];
         Ar[k * kLD + c] = Ar[piv * kLD + c];
         Ar[piv * kLD + c] = t;
         t = Ai[k * kLD + c];
         Ai[k * kLD + c] = Ai[piv * kLD + c];
         Ai[piv * kLD + c] = t;
       }
-      if (lane == 0) {
-        double t = br[k];
+      if (tid == 0) {
+        float2 t = br[k];
         br[k] = br[piv];
         br[piv] = t;
         t = bi[k];
@@ -999,39 +1188,47 @@ __global__ void __launch_bounds__(32) k_eig(Ws ws) {
         bi[piv] = t;
       }
     }
-    warp_sync();
-    const double pr = Ar[k * kLD + k], pi = Ai[k * kLD + k];
-    const double pd = pr * pr + pi * pi;
-    for (int i = k + 1 + lane; i < r; i += 32) {
-      const double ar = Ar[i * kLD + k], ai = Ai[i * kLD + k];
-      const double fr = (ar * pr + ai * pi) / pd, fi = (ai * pr - ar * pi) / pd;
-      for (int c = k; c < r; ++c) {
-        const double xr = Ar[k * kLD + c], xi = Ai[k * kLD + c];
-        Ar[i * kLD + c] -= fr * xr - fi * xi;
-        Ai[i * kLD + c] -= fr * xi + fi * xr;
-      }
-      const double yr = br[k], yi = bi[k];
-      br[i] -= fr * yr - fi * yi;
-      bi[i] -= fr * yi + fi * yr;
+    __syncthreads();
+    const cdd pk{HH(Ar, k, k), HH(Ai, k, k)};
+    // multipliers of rows k+1.. (one thread per row), then the updates split by column
+    for (int i = k + 1 + tid; i < r; i += kEigThreads) {
+      const cdd f = cdd_div(cdd{HH(Ar, i, k), HH(Ai, i, k)}, pk);
+      Ar[i * kLD + k] = f2_of(f.re);
+      Ai[i * kLD + k] = f2_of(f.im);
     }
-    warp_sync();
-  }
-  if (lane == 0) {
-    for (int i = r - 1; i >= 0; --i) {
-      double sr = br[i], si = bi[i];
-      for (int c = i + 1; c < r; ++c) {
-        sr -= Ar[i * kLD + c] * br[c] - Ai[i * kLD + c] * bi[c];
-        si -= Ar[i * kLD + c] * bi[c] + Ai[i * kLD + c] * br[c];
+    __syncthreads();
+    const int rows = r - k - 1, cols = r - k;  // columns k+1..r-1 plus the right-hand side
+    for (int idx = tid; idx < rows * cols; idx += kEigThreads) {
+      const int i = k + 1 + idx / cols, cc = idx % cols;
+      const cdd f{HH(Ar, i, k), HH(Ai, i, k)};
+      if (cc < cols - 1) {
+        const int c = k + 1 + cc;
+        const cdd x{HH(Ar, k, c), HH(Ai, k, c)};
+        const cdd y = cdd{HH(Ar, i, c), HH(Ai, i, c)} - f * x;
+        Ar[i * kLD + c] = f2_of(y.re);
+        Ai[i * kLD + c] = f2_of(y.im);
+      } else {
+        const cdd x{LD(br, k), LD(bi, k)};
+        const cdd y = cdd{LD(br, i), LD(bi, i)} - f * x;
+        br[i] = f2_of(y.re);
+        bi[i] = f2_of(y.im);
       }
-      const double pr = Ar[i * kLD + i], pi = Ai[i * kLD + i];
-      const double pd = pr * pr + pi * pi;
-      br[i] = pd > 0.0 ? (sr * pr + si * pi) / pd : 0.0;
-      bi[i] = pd > 0.0 ? (si * pr - sr * pi) / pd : 0.0;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    for (int i = r - 1; i >= 0; --i) {
+      cdd s{LD(br, i), LD(bi, i)};
+      for (int c = i + 1; c < r; ++c) s = s - cdd{HH(Ar, i, c), HH(Ai, i, c)} * cdd{LD(br, c), LD(bi, c)};
+      const cdd pv{HH(Ar, i, i), HH(Ai, i, i)};
+      const cdd x = (pv.re.h != 0.f || pv.im.h != 0.f) ? cdd_div(s, pv) : cdd{dzero(), dzero()};
+      br[i] = f2_of(x.re);
+      bi[i] = f2_of(x.im);
     }
     for (int i = 0; i < r; ++i) {
       ws.eig.bre[i] = br[i];
       ws.eig.bim[i] = bi[i];
-      if (!isfinite(br[i]) || !isfinite(bi[i])) singular = true;
+      if (!isfinite(br[i].x) || !isfinite(bi[i].x)) singular = true;
     }
     if (singular) atomicOr(&ctl->status, DEV_EIG_COND);
     ctl->eig_r = r;
@@ -1041,10 +1238,22 @@ __global__ void __launch_bounds__(32) k_eig(Ws ws) {
 
 // ---------------------------------------------------------------------------------------
 // rollout coefficients: coef[:, j] = Q Re(V Lambda^{t_j} b)  (r0 values, L0 coordinates)
+// Lambda^t: for integer t by binary powering in complex double-float; otherwise from
+// |lambda|^t and t arg(lambda) in FP64 (principal branch).
 // ---------------------------------------------------------------------------------------
 struct TArr {
   double t[kRollK];
 };
+
+__device__ cdd cpow_int(cdd base, long long e) {
+  cdd res{dd_of(1.f), dzero()};
+  while (e > 0) {
+    if (e & 1) res = res * base;
+    e >>= 1;
+    if (e) base = base * base;
+  }
+  return res;
+}
 
 __global__ void __launch_bounds__(64) k_coef(Ws ws, TArr ts, int k) {
   Ctl* ctl = ws.ctl;
@@ -1053,42 +1262,44 @@ __global__ void __launch_bounds__(64) k_coef(Ws ws, TArr ts, int k) {
   const StateBuf st = ws.st[ctl->cur];
   const int r = st.hdr->r, r0 = st.hdr->r0, rm = ws.rmax, qld = ws.cap + 1;
   const int tid = threadIdx.x;
-  __shared__ double gr[kMaxR], gi[kMaxR], c[kMaxR];
+  __shared__ float2 gr[kMaxR], gi[kMaxR], c[kMaxR];
   const double t = ts.t[j];
+  const bool integral = (t == floor(t)) && t < 9.0e15;
   for (int l = tid; l < r; l += 64) {
-    const double lr = ws.eig.lre[l], li = ws.eig.lim[l];
-    const double b_r = ws.eig.bre[l], b_i = ws.eig.bim[l];
-    double pr, pi;  // lambda^t on the principal branch
+    const cdd lam{LD(ws.eig.lre, l), LD(ws.eig.lim, l)};
+    const cdd b{LD(ws.eig.bre, l), LD(ws.eig.bim, l)};
+    cdd pw;
     if (t == 0.0) {
-      pr = 1.0;
-      pi = 0.0;
-    } else if (lr == 0.0 && li == 0.0) {
-      pr = 0.0;
-      pi = 0.0;
+      pw = cdd{dd_of(1.f), dzero()};
+    } else if (lam.re.h == 0.f && lam.im.h == 0.f) {
+      pw = cdd{dzero(), dzero()};
+    } else if (integral) {
+      pw = cpow_int(lam, (long long)t);
     } else {
+      const double lr = dd_to_double(lam.re), li = dd_to_double(lam.im);
       const double mag = pow(hypot(lr, li), t);
       double sn, cs;
       sincos(t * atan2(li, lr), &sn, &cs);
-      pr = mag * cs;
-      pi = mag * sn;
+      pw = cdd{dd_from_double(mag * cs), dd_from_double(mag * sn)};
     }
-    gr[l] = pr * b_r - pi * b_i;
-    gi[l] = pr * b_i + pi * b_r;
+    const cdd g = pw * b;
+    gr[l] = f2_of(g.re);
+    gi[l] = f2_of(g.im);
   }
   __syncthreads();
   for (int i = tid; i < r; i += 64) {
-    double acc = 0.0;
+    dd acc = dzero();
     for (int l = 0; l < r; ++l) {
-      acc = fma(ws.eig.Vre[(size_t)l * rm + i], gr[l], acc);
-      acc = fma(-ws.eig.Vim[(size_t)l * rm + i], gi[l], acc);
+      acc = dd_fma(LD(ws.eig.Vre, (size_t)l * rm + i), LD(gr, l), acc);
+      acc = acc - LD(ws.eig.Vim, (size_t)l * rm + i) * LD(gi, l);
     }
-    c[i] = acc;
+    c[i] = f2_of(acc);
   }
   __syncthreads();
   for (int i = tid; i < r0; i += 64) {
-    double acc = 0.0;
-    for (int l = 0; l < r; ++l) acc = fma(st.Q[(size_t)l * qld + i], c[l], acc);
-    ws.sm.coef[(size_t)j * qld + i] = acc;
+    dd acc = dzero();
+    for (int l = 0; l < r; ++l) acc = dd_fma(LD(st.Q, (size_t)l * qld + i), LD(c, l), acc);
+    ws.sm.coef[(size_t)j * qld + i] = f2_of(acc);
   }
 }
 
@@ -1103,12 +1314,20 @@ __global__ void __launch_bounds__(64) k_basis_coef(Ws ws) {
 }
 
 // ---------------------------------------------------------------------------------------
+static int prep_smem(const Ws& ws) {
+  const int qld = ws.cap + 1;
+  return (int)sizeof(float2) * (qld * kMaxR + 4 * qld + 2 * kMaxN);
+}
+
 cudaError_t launch_small(const Ws& ws, cudaStream_t s) {
-  k_prep<<<1, 128, 0, s>>>(ws);
+  const int ps = prep_smem(ws);
+  cudaError_t e = cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, ps);
+  if (e != cudaSuccess) return e;
+  k_prep<<<1, kPrepThreads, ps, s>>>(ws);
   k_roots<<<kMaxN, 32, 0, s>>>(ws);
   k_zhat<<<kMaxN + 1, 32, 0, s>>>(ws);
   k_vectors<<<kMaxN, 64, 0, s>>>(ws);
-  k_apply<<<kMaxN, 128, 0, s>>>(ws);
+  k_apply<<<kMaxN, kApplyThreads, 0, s>>>(ws);
   return cudaGetLastError();
 }
 
@@ -1116,7 +1335,7 @@ cudaError_t launch_eig(const Ws& ws, cudaStream_t s) {
   const int bytes = (int)sizeof(EigSmem);
   cudaError_t e = cudaFuncSetAttribute(k_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return e;
-  k_eig<<<1, 32, bytes, s>>>(ws);
+  k_eig<<<1, kEigThreads, bytes, s>>>(ws);
   return cudaGetLastError();
 }
 

@@ -14,6 +14,7 @@
 //
 // Reductions are deterministic: per-CTA partials in a fixed order, then the last CTA to
 // finish (atomic ticket) sums them in CTA order.
+#include "dd.cuh"
 #include "odmd_internal.cuh"
 
 namespace odmd {
@@ -220,7 +221,10 @@ __global__ void __launch_bounds__(kThreads) k_pass_a(Ws ws) {
   const int elems_per_chunk = (ST == ST_BF16) ? 8 : 4;
   for (int k = tid; k < kMaxCap + 8; k += kThreads) {
     float h = 0.f, l = 0.f;
-    if (k < r0) split_double(st.a[k], h, l);
+    if (k < r0) {
+      h = st.a[k].x;
+      l = st.a[k].y;
+    }
     if (k >= P.nch * elems_per_chunk) h = l = 0.f;
     coh[k] = h;
     col[k] = l;
@@ -362,9 +366,8 @@ __global__ void __launch_bounds__(kThreads) k_pass_a(Ws ws) {
       acc_add(sum, f.x, f.y);
     }
     sum = acc_norm(sum);
-    const double val = join_double(sum.h, sum.l);
-    if (!isfinite(val)) atomicOr(&ctl->status, DEV_NONFINITE);
-    ws.sm.red[v] = val;
+    if (!isfinite(sum.h) || !isfinite(sum.l)) atomicOr(&ctl->status, DEV_NONFINITE);
+    ws.sm.red[v] = make_float2(sum.h, sum.l);
   }
   if (tid == 0) {
     ctl->ticket_a = 0u;
@@ -413,21 +416,27 @@ __global__ void __launch_bounds__(kThreads) k_pass_b(Ws ws) {
     const int elems_per_chunk = (ST == ST_BF16) ? 8 : 4;
     for (int k = tid; k < kMaxCap + 8; k += kThreads) {
       float h = 0.f, l = 0.f;
-      if (k < r0 && append) split_double(ws.sm.red[k], h, l);  // s = L0^T e
+      if (k < r0 && append) {  // s = L0^T e
+        h = ws.sm.red[k].x;
+        l = ws.sm.red[k].y;
+      }
       if (k >= P.nch * elems_per_chunk) h = l = 0.f;
       coh[k] = h;
       col[k] = l;
     }
     float ih = 0.f, il = 0.f;  // 1/rho0
-    if (append) split_double(1.0 / ctl->rho0, ih, il);
+    if (append) {
+      const dd inv = dd_div(dd_of(1.f), dd_of(ctl->rho0));
+      ih = inv.h;
+      il = inv.l;
+    }
     const int r0e = r0 + append;
     if (mode == PB_COMPACT) {
       for (int idx = tid; idx < r0e * rnew; idx += kThreads) {
         const int k = idx / rnew, j = idx % rnew;
-        float h, l;
-        split_double(ws.sm.QB[(size_t)j * (ws.cap + 1) + k], h, l);
-        qbh[k * rnew + j] = h;
-        qbl[k * rnew + j] = l;
+        const float2 q = ws.sm.QB[(size_t)j * (ws.cap + 1) + k];
+        qbh[k * rnew + j] = q.x;
+        qbl[k * rnew + j] = q.y;
       }
     }
     if (tid == 0) {
@@ -570,7 +579,11 @@ __global__ void __launch_bounds__(kThreads) k_rollout(Ws ws, int kcols, void* ou
   for (int idx = tid; idx < (kMaxCap + 8) * kcols; idx += kThreads) {
     const int k = idx / kcols, j = idx % kcols;
     float h = 0.f, l = 0.f;
-    if (k < r0) split_double(ws.sm.coef[(size_t)j * (ws.cap + 1) + k], h, l);
+    if (k < r0) {
+      const float2 q = ws.sm.coef[(size_t)j * (ws.cap + 1) + k];
+      h = q.x;
+      l = q.y;
+    }
     if (k >= kpad) h = l = 0.f;
     cfh[idx] = h;
     cfl[idx] = l;
@@ -709,11 +722,10 @@ __global__ void __launch_bounds__(kThreads) k_rollout(Ws ws, int kcols, void* ou
       }
       a = acc_norm(a);
       b = acc_norm(b);
-      const double nm = join_double(a.h, a.l), dn = join_double(b.h, b.l);
-      ctl->check_num = nm;
-      ctl->check_den = dn;
-      ws.out2[0] = nm;
-      ws.out2[1] = dn;
+      ctl->check_num = make_float2(a.h, a.l);
+      ctl->check_den = make_float2(b.h, b.l);
+      ws.out2[0] = make_float2(a.h, a.l);
+      ws.out2[1] = make_float2(b.h, b.l);
       ctl->ticket_r = 0u;
     }
   }
@@ -751,7 +763,7 @@ __global__ void __launch_bounds__(kThreads) k_first(Ws ws) {
   double tot = 0.0;
   for (int b = 0; b < (int)gridDim.x; ++b) tot += __ldcg(reinterpret_cast<const double*>(ws.part) + b);
   if (!isfinite(tot)) atomicOr(&ctl->status, DEV_NONFINITE);
-  ws.st[ctl->cur].hdr->cn2 = tot;
+  ws.st[ctl->cur].hdr->cn2 = f2_of(dd_from_double(tot));
   ctl->ticket_a = 0u;
 }
 

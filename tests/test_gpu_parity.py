@@ -39,6 +39,7 @@ def run_pair(X, r_max, slack=16, tau=1e-10, prec="fp64"):
         m.update(Xd[k])
         ref.update(X[k].astype(np.float64) if prec == "fp64" else Xd[k].double().cpu().numpy())
     m.sync()
+    m.eigs()  # surfaces any eigensolver status before predictions are compared
     return m, ref
 
 
