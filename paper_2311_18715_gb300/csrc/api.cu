@@ -38,6 +38,24 @@ struct odmd_instance {
   std::vector<cudaEvent_t> pool;
   unsigned long long r0_base[2];  // device pass-A counters at enable time
   std::vector<CUtensorMap> maps_host;  // source of the tensor maps copied into the workspace
+  // CUDA graphs of the update sequence, per snapshot-buffer parity and profiling mode:
+  // ingest -> pass A -> small solves (5 kernels) -> pass B; the only argument that changes
+  // between calls is the snapshot pointer of the ingest node.
+  struct UpdGraph {
+    cudaGraph_t graph = nullptr;      // kept alive: its node handles address the exec's nodes
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t ingest = nullptr;
+    cudaKernelNodeParams kp{};
+    const void* src = nullptr;
+    void* dst = nullptr;
+    int64_t n = 0;
+    void* args[3] = {nullptr, nullptr, nullptr};
+    cudaGraphNode_t ev[6] = {};
+    cudaEvent_t ph[6] = {};           // events recorded by the nodes at capture (kept alive)
+  };
+  UpdGraph ug[2][2];
+  cudaStream_t cap = nullptr;
+  bool use_graphs = true;
 };
 
 namespace {
@@ -324,13 +342,15 @@ struct ProfScope {
   odmd_t h;
   int cls;
   cudaEvent_t a = nullptr, b = nullptr;
+  bool graph_recorded = false;  // the events are recorded by graph nodes
   ProfScope(odmd_t h_, int cls_, int kernels) : h(h_), cls(cls_) {
     h->launches[cls] += kernels;
     if (!h->prof_on) return;
     a = take();
     b = take();
-    if (a) cudaEventRecord(a, h->stream);
+    if (a && kernels > 0) cudaEventRecord(a, h->stream);
   }
+  void defer() { graph_recorded = true; }
   cudaEvent_t take() {
     if (!h->pool.empty()) {
       cudaEvent_t e = h->pool.back();
@@ -343,7 +363,7 @@ struct ProfScope {
   }
   ~ProfScope() {
     if (!h->prof_on || !a || !b) return;
-    cudaEventRecord(b, h->stream);
+    if (!graph_recorded) cudaEventRecord(b, h->stream);
     h->pending.push_back({cls, a, b});
   }
 };
@@ -357,6 +377,73 @@ void prof_collect(odmd_t h) {
     h->pool.push_back(p.b);
   }
   h->pending.clear();
+}
+
+// Capture the update sequence for snapshot-buffer parity `par` (the new snapshot goes to
+// cbuf[par ^ 1]); with `prof`, event-record nodes bracket the three kernel groups.
+odmd_status build_update_graph(odmd_t h, int par, int prof) {
+  odmd_instance::UpdGraph& G = h->ug[par][prof];
+  if (G.exec) return ODMD_OK;
+  cudaEvent_t* ph = G.ph;
+  if (prof)
+    for (int i = 0; i < 6; ++i) CK(h, cudaEventCreate(&ph[i]), "graph events");
+  cudaGraph_t graph = nullptr;
+  CK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+  cudaError_t e = launch_ingest(h->ws, h->ws.cbuf[par], h->ws.cbuf[par ^ 1], h->cap);
+  if (e == cudaSuccess && prof) e = cudaEventRecordWithFlags(ph[0], h->cap, cudaEventRecordExternal);
+  if (e == cudaSuccess) e = launch_pass_a(h->ws, h->cap);
+  if (e == cudaSuccess && prof) e = cudaEventRecordWithFlags(ph[1], h->cap, cudaEventRecordExternal);
+  if (e == cudaSuccess && prof) e = cudaEventRecordWithFlags(ph[2], h->cap, cudaEventRecordExternal);
+  if (e == cudaSuccess) e = launch_small(h->ws, h->cap);
+  if (e == cudaSuccess && prof) e = cudaEventRecordWithFlags(ph[3], h->cap, cudaEventRecordExternal);
+  if (e == cudaSuccess && prof) e = cudaEventRecordWithFlags(ph[4], h->cap, cudaEventRecordExternal);
+  if (e == cudaSuccess) e = launch_pass_b(h->ws, h->cap);
+  if (e == cudaSuccess && prof) e = cudaEventRecordWithFlags(ph[5], h->cap, cudaEventRecordExternal);
+  cudaError_t e2 = cudaStreamEndCapture(h->cap, &graph);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_fail(h, e, "update graph capture");
+  }
+  size_t nn = 0;
+  CK(h, cudaGraphGetNodes(graph, nullptr, &nn), "graph nodes");
+  std::vector<cudaGraphNode_t> nodes(nn);
+  CK(h, cudaGraphGetNodes(graph, nodes.data(), &nn), "graph nodes");
+  const void* ingest_fn = ingest_kernel(h->ws.prec);
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType t;
+    CK(h, cudaGraphNodeGetType(nd, &t), "node type");
+    if (t == cudaGraphNodeTypeKernel) {
+      cudaKernelNodeParams kp{};
+      CK(h, cudaGraphKernelNodeGetParams(nd, &kp), "node params");
+      if (kp.func == ingest_fn) {
+        G.ingest = nd;
+        G.kp = kp;
+      }
+    } else if (t == cudaGraphNodeTypeEventRecord) {
+      cudaEvent_t ev;
+      CK(h, cudaGraphEventRecordNodeGetEvent(nd, &ev), "node event");
+      for (int i = 0; i < 6; ++i)
+        if (ev == ph[i]) G.ev[i] = nd;
+    }
+  }
+  if (!G.ingest) {
+    cudaGraphDestroy(graph);
+    return fail(h, ODMD_ERR_CUDA, "update graph: ingest node not found");
+  }
+  e = cudaGraphInstantiate(&G.exec, graph, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    G.exec = nullptr;
+    return cuda_fail(h, e, "update graph instantiate");
+  }
+  G.graph = graph;
+  G.args[0] = &G.src;
+  G.args[1] = &G.dst;
+  G.args[2] = &G.n;
+  G.kp.kernelParams = G.args;
+  G.kp.extra = nullptr;
+  return ODMD_OK;
 }
 
 odmd_status ensure_eig(odmd_t h) {
@@ -430,6 +517,7 @@ odmd_status odmd_create(const odmd_config* cfg, void* workspace_dev, size_t byte
   int sms = 0;
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&h->pinned), 8 * sizeof(double));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     std::string m = std::string("create: ") + cudaGetErrorString(e);
     delete h;
@@ -440,11 +528,14 @@ odmd_status odmd_create(const odmd_config* cfg, void* workspace_dev, size_t byte
   if (gridA > kPartRows) gridA = kPartRows;
   if (gridA < 1) gridA = 1;
   carve(h->ws, L, reinterpret_cast<unsigned char*>(workspace_dev), *cfg, gridA);
-  e = cudaMemsetAsync(workspace_dev, 0, L.total, h->stream);
+  if (e == cudaSuccess) e = prepare_tall(h->ws);
+  if (e == cudaSuccess) e = prepare_small(h->ws);
+  if (e == cudaSuccess) e = cudaMemsetAsync(workspace_dev, 0, L.total, h->stream);
   if (e == cudaSuccess) {
     if (encode_maps(h, L) != ODMD_OK) {
       std::string m = h->err;
       cudaFreeHost(h->pinned);
+      cudaStreamDestroy(h->cap);
       delete h;
       return fail(nullptr, ODMD_ERR_CUDA, m);
     }
@@ -454,6 +545,7 @@ odmd_status odmd_create(const odmd_config* cfg, void* workspace_dev, size_t byte
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     cudaFreeHost(h->pinned);
+    cudaStreamDestroy(h->cap);
     std::string m = std::string("create: ") + cudaGetErrorString(e);
     delete h;
     return fail(nullptr, ODMD_ERR_CUDA, m);
@@ -465,26 +557,70 @@ odmd_status odmd_create(const odmd_config* cfg, void* workspace_dev, size_t byte
 odmd_status odmd_update(odmd_t h, const void* x_dev) {
   if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
   if (!x_dev) return fail(h, ODMD_ERR_ARG, "x is NULL");
-  const size_t nb = snap_bytes(h);
   if (h->nsnap == 0) {
-    CK(h, cudaMemcpyAsync(h->ws.cbuf[h->curc_h], x_dev, nb, cudaMemcpyDeviceToDevice, h->stream), "copy u0");
+    CK(h, launch_ingest(h->ws, x_dev, h->ws.cbuf[h->curc_h], h->stream), "copy u0");
     ProfScope ps(h, ODMD_K_FIRST, 1);
     CK(h, launch_first(h->ws, h->stream), "first launch");
     h->nsnap = 1;
     return ODMD_OK;
   }
-  CK(h, cudaMemcpyAsync(h->ws.cbuf[h->curc_h ^ 1], x_dev, nb, cudaMemcpyDeviceToDevice, h->stream), "copy x");
-  {
-    ProfScope ps(h, ODMD_K_PASS_A, 1);
-    CK(h, launch_pass_a(h->ws, h->stream), "pass A launch");
+  bool graphed = false;
+  if (h->use_graphs) {
+    const int par = h->curc_h, prof = h->prof_on ? 1 : 0;
+    if (odmd_status st = build_update_graph(h, par, prof)) return st;
+    odmd_instance::UpdGraph& G = h->ug[par][prof];
+    G.src = x_dev;
+    G.dst = h->ws.cbuf[par ^ 1];
+    G.n = h->cfg.n;
+    CK(h, cudaGraphExecKernelNodeSetParams(G.exec, G.ingest, &G.kp), "graph ingest params");
+    bool ok = true;
+    if (prof) {
+      // point the graph's event nodes at fresh pool events (on failure this update runs
+      // through the plain launch path below)
+      cudaEvent_t evs[6] = {};
+      for (int i = 0; i < 6 && ok; ++i) {
+        if (!h->pool.empty()) {
+          evs[i] = h->pool.back();
+          h->pool.pop_back();
+        } else if (cudaEventCreate(&evs[i]) != cudaSuccess) {
+          evs[i] = nullptr;
+        }
+        if (!evs[i] || !G.ev[i] ||
+            cudaGraphExecEventRecordNodeSetEvent(G.exec, G.ev[i], evs[i]) != cudaSuccess)
+          ok = false;
+      }
+      cudaGetLastError();
+      if (ok) {
+        h->pending.push_back({ODMD_K_PASS_A, evs[0], evs[1]});
+        h->pending.push_back({ODMD_K_SMALL, evs[2], evs[3]});
+        h->pending.push_back({ODMD_K_PASS_B, evs[4], evs[5]});
+      } else {
+        for (cudaEvent_t ev : evs)
+          if (ev) h->pool.push_back(ev);
+      }
+    }
+    if (ok) {
+      CK(h, cudaGraphLaunch(G.exec, h->stream), "update graph launch");
+      h->launches[ODMD_K_PASS_A] += 1;
+      h->launches[ODMD_K_SMALL] += 5;
+      h->launches[ODMD_K_PASS_B] += 1;
+      graphed = true;
+    }
   }
-  {
-    ProfScope ps(h, ODMD_K_SMALL, 5);
-    CK(h, launch_small(h->ws, h->stream), "small solve launch");
-  }
-  {
-    ProfScope ps(h, ODMD_K_PASS_B, 1);
-    CK(h, launch_pass_b(h->ws, h->stream), "pass B launch");
+  if (!graphed) {
+    CK(h, launch_ingest(h->ws, x_dev, h->ws.cbuf[h->curc_h ^ 1], h->stream), "copy x");
+    {
+      ProfScope ps(h, ODMD_K_PASS_A, 1);
+      CK(h, launch_pass_a(h->ws, h->stream), "pass A launch");
+    }
+    {
+      ProfScope ps(h, ODMD_K_SMALL, 5);
+      CK(h, launch_small(h->ws, h->stream), "small solve launch");
+    }
+    {
+      ProfScope ps(h, ODMD_K_PASS_B, 1);
+      CK(h, launch_pass_b(h->ws, h->stream), "pass B launch");
+    }
   }
   h->cur_h ^= 1;
   h->curc_h ^= 1;
@@ -522,7 +658,7 @@ odmd_status odmd_check(odmd_t h, double t, const void* x_fom_dev, double tol, do
   if (!(t >= 0.0) || !std::isfinite(t)) return fail(h, ODMD_ERR_ARG, "t must be finite and >= 0");
   if (h->nsnap < 2) return fail(h, ODMD_ERR_STATE, "check needs two snapshots");
   if (tol <= 0.0) tol = h->cfg.check_tol;
-  CK(h, cudaMemcpyAsync(h->ws.xbuf, x_fom_dev, snap_bytes(h), cudaMemcpyDeviceToDevice, h->stream), "copy x_fom");
+  CK(h, launch_ingest(h->ws, x_fom_dev, h->ws.xbuf, h->stream), "copy x_fom");
   if (odmd_status s = ensure_eig(h)) return s;
   {
     ProfScope ps(h, ODMD_K_COEF, 1);
@@ -678,6 +814,14 @@ odmd_status odmd_destroy(odmd_t h) {
   cudaError_t e = cudaStreamSynchronize(h->stream);
   prof_collect(h);
   for (cudaEvent_t ev : h->pool) cudaEventDestroy(ev);
+  for (auto& row : h->ug)
+    for (auto& g : row) {
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      if (g.graph) cudaGraphDestroy(g.graph);
+      for (cudaEvent_t ev : g.ph)
+        if (ev) cudaEventDestroy(ev);
+    }
+  if (h->cap) cudaStreamDestroy(h->cap);
   cudaFreeHost(h->pinned);
   delete h;
   if (e != cudaSuccess) return fail(nullptr, ODMD_ERR_CUDA, std::string("destroy: ") + cudaGetErrorString(e));

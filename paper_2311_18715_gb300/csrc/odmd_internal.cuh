@@ -141,8 +141,8 @@ struct Ws {
   Ctl* ctl;
   void* Lh;         // hi plane (float) / bf16 plane
   float* Ll;        // lo plane (FP64 mode only)
-  void* cbuf[2];    // snapshot buffers (npad elements of the snapshot type)
-  void* xbuf;       // scratch snapshot (check input copy)
+  void* cbuf[2];    // snapshot buffers (npad elements: float pairs in FP64 mode, else floats)
+  void* xbuf;       // scratch snapshot (check input copy), same format
   float2* ebuf;     // first-pass residual e = c - L0 a of the update in flight (hi, lo)
   const CUtensorMap* maps;  // [plane][k]: 2-D tile maps of the basis planes, box of
                             // (2k+1) chunks x kTile rows; plane 1 only in FP64 mode
@@ -300,6 +300,10 @@ __device__ __forceinline__ Acc warp_sum_acc(Acc a) {
 cudaError_t launch_pass_a(const Ws& ws, cudaStream_t s);
 cudaError_t launch_pass_b(const Ws& ws, cudaStream_t s);
 cudaError_t launch_first(const Ws& ws, cudaStream_t s);
+cudaError_t launch_ingest(const Ws& ws, const void* src, void* dst, cudaStream_t s);  // snapshot -> workspace
+const void* ingest_kernel(int prec);  // the kernel launch_ingest uses (graph node lookup)
+cudaError_t prepare_tall(const Ws& ws);
+cudaError_t prepare_small(const Ws& ws);
 cudaError_t launch_rollout(const Ws& ws, const double* coef_src, int kcols, void* out, int64_t ld,
                            int coef_mode, cudaStream_t s);
 cudaError_t launch_check(const Ws& ws, cudaStream_t s);

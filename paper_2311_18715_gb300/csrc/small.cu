@@ -329,9 +329,71 @@ __global__ void __launch_bounds__(32) k_roots(Ws ws) {
     A = dzero();
     B = dzero();
   }
+  // ---- stage 1, FP32: locate the root to ~1e-7 relative (cheap), keeping the bracket
   dd mu = (lo + hi) * 0.5f;
+  {
+    const float dof = LD(d, o).h;
+    const float Af = A.h, Bf = B.h;
+    float lof = lo.h, hif = hi.h, muf = mu.h;
+    for (int it = 0; it < 40; ++it) {
+      float psi = 0.f, dpsi = 0.f, phi = 0.f, dphi = 0.f;
+      for (int i = lane; i < m; i += 32) {
+        const float di = d[i].x, zi = z[i].x;
+        const float del = (di - dof) * (di + dof) - muf;
+        const float t = zi / del;
+        if (i <= j) {
+          psi = fmaf(zi, t, psi);
+          dpsi = fmaf(t, t, dpsi);
+        } else {
+          phi = fmaf(zi, t, phi);
+          dphi = fmaf(t, t, dphi);
+        }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        psi += __shfl_xor_sync(0xffffffffu, psi, off);
+        dpsi += __shfl_xor_sync(0xffffffffu, dpsi, off);
+        phi += __shfl_xor_sync(0xffffffffu, phi, off);
+        dphi += __shfl_xor_sync(0xffffffffu, dphi, off);
+      }
+      const float f = 1.f + psi + phi;
+      if (f < 0.f)
+        lof = muf;
+      else
+        hif = muf;
+      if (fabsf(f) <= 16.f * 6e-8f * (1.f + fabsf(psi) + fabsf(phi))) break;
+      const float Am = Af - muf, c1 = dpsi * Am * Am, a1 = psi - dpsi * Am;
+      float x;
+      if (!last) {
+        const float Bm = Bf - muf, c2 = dphi * Bm * Bm, a2 = phi - dphi * Bm;
+        const float C = 1.f + a1 + a2;
+        const float qb = -(C * (Af + Bf) + c1 + c2), qc = C * Af * Bf + c1 * Bf + c2 * Af;
+        if (fabsf(C) <= 1e-7f * (fabsf(qb) + fabsf(qc))) {
+          x = -qc / qb;
+        } else {
+          const float sq = sqrtf(fmaxf(qb * qb - 4.f * C * qc, 0.f));
+          const float q = -0.5f * (qb >= 0.f ? qb + sq : qb - sq);
+          const float x1 = q / C, x2 = qc / q;
+          const bool in1 = x1 > lof && x1 < hif, in2 = x2 > lof && x2 < hif;
+          x = in1 && !in2 ? x1 : (in2 && !in1 ? x2 : (fabsf(x1 - muf) < fabsf(x2 - muf) ? x1 : x2));
+        }
+      } else {
+        const float C = 1.f + a1 + phi;
+        x = C > 0.f ? Af + c1 / C : 0.5f * (lof + hif);
+      }
+      if (!(x > lof && x < hif)) x = 0.5f * (lof + hif);
+      const float step = fabsf(x - muf);
+      muf = x;
+      if (step <= 4e-7f * fabsf(muf) || hif - lof <= 4e-7f * fmaxf(fabsf(lof), fabsf(hif))) break;
+    }
+    // FP32 cannot resolve poles closer than ~1e-7 relative: keep its root only when it is
+    // finite and strictly inside the double-float bracket
+    const dd cand = dd_of(muf);
+    if (isfinite(muf) && dd_gt(cand, lo) && dd_lt(cand, hi)) mu = cand;
+  }
+  // ---- stage 2, double-float: polish inside the original bracket (bisection fallback)
   bool conv = false;
-  for (int it = 0; it < 80; ++it) {
+  for (int it = 0; it < 100; ++it) {
     const SecSums s = sec_eval(d, z, m, j, o, mu);
     const dd f = dd_of(1.f) + s.psi + s.phi;
     if (f.h < 0.f)
@@ -1319,10 +1381,14 @@ static int prep_smem(const Ws& ws) {
   return (int)sizeof(float2) * (qld * kMaxR + 4 * qld + 2 * kMaxN);
 }
 
+cudaError_t prepare_small(const Ws& ws) {
+  cudaError_t e = cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, prep_smem(ws));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(EigSmem));
+}
+
 cudaError_t launch_small(const Ws& ws, cudaStream_t s) {
   const int ps = prep_smem(ws);
-  cudaError_t e = cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, ps);
-  if (e != cudaSuccess) return e;
   k_prep<<<1, kPrepThreads, ps, s>>>(ws);
   k_roots<<<kMaxN, 32, 0, s>>>(ws);
   k_zhat<<<kMaxN + 1, 32, 0, s>>>(ws);
@@ -1333,8 +1399,6 @@ cudaError_t launch_small(const Ws& ws, cudaStream_t s) {
 
 cudaError_t launch_eig(const Ws& ws, cudaStream_t s) {
   const int bytes = (int)sizeof(EigSmem);
-  cudaError_t e = cudaFuncSetAttribute(k_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e != cudaSuccess) return e;
   k_eig<<<1, kEigThreads, bytes, s>>>(ws);
   return cudaGetLastError();
 }

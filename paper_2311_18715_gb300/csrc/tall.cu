@@ -21,20 +21,26 @@ namespace odmd {
 
 template <int ST>
 struct Traits;
+// snap_t: the caller's snapshot element; stored_t: the workspace copy of a snapshot (a
+// double is kept as a float pair so the tall passes need no FP64 instruction); vsz: bytes
+// of stored_t.
 template <>
 struct Traits<ST_DD> {
   static constexpr int planes = 2, esz = 4, vsz = 8;
   using snap_t = double;
+  using stored_t = float2;
 };
 template <>
 struct Traits<ST_F32> {
   static constexpr int planes = 1, esz = 4, vsz = 4;
   using snap_t = float;
+  using stored_t = float;
 };
 template <>
 struct Traits<ST_BF16> {
   static constexpr int planes = 1, esz = 2, vsz = 4;
   using snap_t = float;
+  using stored_t = float;
 };
 
 __device__ __forceinline__ int rows_in(int64_t n, int64_t row0) {
@@ -52,9 +58,10 @@ __host__ __device__ inline int stage_bytes(int cap) {
   return kTile * rs_max * T::planes + 2 * kTile * 8;
 }
 
-// Snapshot element -> float-float
-__device__ __forceinline__ void load_snap(const double* p, int i, float& h, float& l) {
-  split_double(p[i], h, l);
+// Stored snapshot element -> float-float
+__device__ __forceinline__ void load_snap(const float2* p, int i, float& h, float& l) {
+  h = p[i].x;
+  l = p[i].y;
 }
 __device__ __forceinline__ void load_snap(const float* p, int i, float& h, float& l) {
   h = p[i];
@@ -164,15 +171,15 @@ struct TilePipe {
   }
 };
 
-// Phase 1: 4 threads per row (thread = sub*64 + t) form partial row dots with the
+// Phase 1: NSUB threads per row (thread = sub*64 + t) form partial row dots with the
 // coefficient vector (float-float, zero-padded to whole chunks) held in shared memory.
-template <int ST>
+template <int ST, int NSUB = 4>
 __device__ __forceinline__ Acc row_dot_partial(const TilePipe<ST>& P, int s, int t, int sub, const float* coh,
                                                const float* col) {
   Acc acc = acc_zero();
   const unsigned char* ph = P.plane_h(s);
   const unsigned char* pl = P.plane_l(s);
-  for (int q = sub; q < P.nch; q += 4) {
+  for (int q = sub; q < P.nch; q += NSUB) {
     float h[8], l[8];
     const int e = load_chunk<ST>(ph, pl, P.rs, t, q, h, l);
 #pragma unroll
@@ -184,10 +191,12 @@ __device__ __forceinline__ Acc row_dot_partial(const TilePipe<ST>& P, int s, int
 }
 
 // ---------------------------------------------------------------------------------------
-// pass A
+// pass A (512 threads: 8 per row in phase 1, 512 / r0 row groups in phase 2)
 // ---------------------------------------------------------------------------------------
+constexpr int kThreadsA = 512;
+constexpr int kSubA = kThreadsA / kTile;
 template <int ST>
-__global__ void __launch_bounds__(kThreads) k_pass_a(Ws ws) {
+__global__ void __launch_bounds__(kThreadsA) k_pass_a(Ws ws) {
   using T = Traits<ST>;
   using snap_t = typename T::snap_t;
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -215,11 +224,11 @@ __global__ void __launch_bounds__(kThreads) k_pass_a(Ws ws) {
   float* el = eh + kTile;
   float* xh = el + kTile;
   float* xl = xh + kTile;
-  Acc* part = reinterpret_cast<Acc*>(xl + kTile);       // [4][kTile]
-  Acc* colacc = part + 4 * kTile;                        // [256][2] group accumulators
+  Acc* part = reinterpret_cast<Acc*>(xl + kTile);       // [kSubA][kTile]
+  Acc* colacc = part + kSubA * kTile;                    // [kThreadsA][2] group accumulators
 
   const int elems_per_chunk = (ST == ST_BF16) ? 8 : 4;
-  for (int k = tid; k < kMaxCap + 8; k += kThreads) {
+  for (int k = tid; k < kMaxCap + 8; k += kThreadsA) {
     float h = 0.f, l = 0.f;
     if (k < r0) {
       h = st.a[k].x;
@@ -244,7 +253,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_a(Ws ws) {
 
   const int t = tid & 63, sub = tid >> 6;
   const int ncol = max(r0, 1);
-  const int G2 = kThreads / ncol;
+  const int G2 = kThreadsA / ncol;
   const int kcol = tid % ncol, grp = tid / ncol;
   const bool col_active = (r0 > 0) && grp < G2;
   Acc S_acc = acc_zero(), Y_acc = acc_zero();
@@ -264,16 +273,15 @@ __global__ void __launch_bounds__(kThreads) k_pass_a(Ws ws) {
     }
     {
       // phase 1: residual e_t = c_t - L0_t . a
-      part[sub * kTile + t] = row_dot_partial<ST>(P, s, t, sub, coh, col);
+      part[sub * kTile + t] = row_dot_partial<ST, kSubA>(P, s, t, sub, coh, col);
       __syncthreads();
       if (sub == 0) {
         float ch, cl, xh_, xl_;
-        load_snap(reinterpret_cast<const snap_t*>(P.snap_c(s)), t, ch, cl);
-        load_snap(reinterpret_cast<const snap_t*>(P.snap_x(s)), t, xh_, xl_);
+        load_snap(reinterpret_cast<const typename T::stored_t*>(P.snap_c(s)), t, ch, cl);
+        load_snap(reinterpret_cast<const typename T::stored_t*>(P.snap_x(s)), t, xh_, xl_);
         Acc d = part[t];
-        acc_add(d, part[kTile + t].h, part[kTile + t].l);
-        acc_add(d, part[2 * kTile + t].h, part[2 * kTile + t].l);
-        acc_add(d, part[3 * kTile + t].h, part[3 * kTile + t].l);
+#pragma unroll
+        for (int q = 1; q < kSubA; ++q) acc_add(d, part[q * kTile + t].h, part[q * kTile + t].l);
         Acc e = Acc{ch, cl};
         acc_add(e, -d.h, -d.l);
         e = acc_norm(e);
@@ -358,16 +366,28 @@ __global__ void __launch_bounds__(kThreads) k_pass_a(Ws ws) {
   __syncthreads();
   if (ticket != (unsigned)(G - 1)) return;
   __threadfence();
+  // 4 adjacent lanes per value, each summing every 4th CTA, then a fixed-order combine
   const int nv = 2 * r0 + 3;
-  for (int v = tid; v < nv; v += kThreads) {
+  for (int base = 0; base < 4 * nv; base += kThreadsA) {
+    const int item = base + tid;
+    const int v = item >> 2, q = item & 3;
     Acc sum = acc_zero();
-    for (int b = 0; b < G; ++b) {
-      const float2 f = __ldcg(ws.part + (size_t)b * stride + v);
-      acc_add(sum, f.x, f.y);
+    if (v < nv)
+      for (int b = q; b < G; b += 4) {
+        const float2 f = __ldcg(ws.part + (size_t)b * stride + v);
+        acc_add(sum, f.x, f.y);
+      }
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) {
+      const float h = __shfl_xor_sync(0xffffffffu, sum.h, o);
+      const float l = __shfl_xor_sync(0xffffffffu, sum.l, o);
+      acc_add(sum, h, l);
     }
-    sum = acc_norm(sum);
-    if (!isfinite(sum.h) || !isfinite(sum.l)) atomicOr(&ctl->status, DEV_NONFINITE);
-    ws.sm.red[v] = make_float2(sum.h, sum.l);
+    if (v < nv && q == 0) {
+      sum = acc_norm(sum);
+      if (!isfinite(sum.h) || !isfinite(sum.l)) atomicOr(&ctl->status, DEV_NONFINITE);
+      ws.sm.red[v] = make_float2(sum.h, sum.l);
+    }
   }
   if (tid == 0) {
     ctl->ticket_a = 0u;
@@ -636,7 +656,7 @@ __global__ void __launch_bounds__(kThreads) k_rollout(Ws ws, int kcols, void* ou
             acc = acc_norm(acc);
             if constexpr (CHECK) {
               float fh, fl;
-              load_snap(reinterpret_cast<const snap_t*>(P.snap_c(s)), tt, fh, fl);
+              load_snap(reinterpret_cast<const typename T::stored_t*>(P.snap_c(s)), tt, fh, fl);
               Acc d = acc;
               acc_add(d, -fh, -fl);
               d = acc_norm(d);
@@ -664,7 +684,7 @@ __global__ void __launch_bounds__(kThreads) k_rollout(Ws ws, int kcols, void* ou
           if (tt < rows) {
             if constexpr (CHECK) {
               float fh, fl;
-              load_snap(reinterpret_cast<const snap_t*>(P.snap_c(s)), tt, fh, fl);
+              load_snap(reinterpret_cast<const typename T::stored_t*>(P.snap_c(s)), tt, fh, fl);
               Acc d = acc;
               acc_add(d, -fh, -fl);
               d = acc_norm(d);
@@ -734,13 +754,16 @@ __global__ void __launch_bounds__(kThreads) k_rollout(Ws ws, int kcols, void* ou
 // ---------------------------------------------------------------------------------------
 // first snapshot: ||u^0||^2 into the committed state
 // ---------------------------------------------------------------------------------------
-template <typename snap_t>
+__device__ __forceinline__ double stored_to_double(float2 v) { return (double)v.x + (double)v.y; }
+__device__ __forceinline__ double stored_to_double(float v) { return (double)v; }
+
+template <typename stored_t>
 __global__ void __launch_bounds__(kThreads) k_first(Ws ws) {
   Ctl* ctl = ws.ctl;
-  const snap_t* c = reinterpret_cast<const snap_t*>(ws.cbuf[ctl->cur_c]);
+  const stored_t* c = reinterpret_cast<const stored_t*>(ws.cbuf[ctl->cur_c]);
   double acc = 0.0;  // N FP64 FMAs once per stream: negligible
   for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < ws.n; i += (int64_t)gridDim.x * kThreads) {
-    const double v = (double)c[i];
+    const double v = stored_to_double(c[i]);
     acc = fma(v, v, acc);
   }
   acc = warp_sum_d(acc);
@@ -772,7 +795,7 @@ __global__ void __launch_bounds__(kThreads) k_first(Ws ws) {
 // ---------------------------------------------------------------------------------------
 static int smem_a(int prec, int cap) {
   const int sb = prec == ST_DD ? stage_bytes<ST_DD>(cap) : prec == ST_F32 ? stage_bytes<ST_F32>(cap) : stage_bytes<ST_BF16>(cap);
-  return kStages * sb + 8 * kStages + 2 * (kMaxCap + 8) * 4 + 4 * kTile * 4 + 4 * kTile * 8 + 2 * kThreads * 8;
+  return kStages * sb + 8 * kStages + 2 * (kMaxCap + 8) * 4 + 4 * kTile * 4 + kSubA * kTile * 8 + 2 * kThreadsA * 8;
 }
 static int smem_b(int prec, int cap) {
   const int sb = prec == ST_DD ? stage_bytes<ST_DD>(cap) : prec == ST_F32 ? stage_bytes<ST_F32>(cap) : stage_bytes<ST_BF16>(cap);
@@ -791,39 +814,55 @@ static cudaError_t prep_attr(K kern, int bytes) {
   return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-cudaError_t launch_pass_a(const Ws& ws, cudaStream_t s) {
-  const int sm = smem_a(ws.prec, ws.cap);
-  cudaError_t e;
+// Raise the dynamic shared-memory limit of every tall kernel once (not inside launches,
+// which may be captured into a graph).
+cudaError_t prepare_tall(const Ws& ws) {
+  const int cap = ws.cap;
+  cudaError_t e = cudaSuccess;
   switch (ws.prec) {
     case ST_DD:
-      if ((e = prep_attr(k_pass_a<ST_DD>, sm))) return e;
-      k_pass_a<ST_DD><<<ws.gridA, kThreads, sm, s>>>(ws);
+      if ((e = prep_attr(k_pass_a<ST_DD>, smem_a(ST_DD, cap)))) return e;
+      if ((e = prep_attr(k_pass_b<ST_DD>, smem_b(ST_DD, cap)))) return e;
+      if ((e = prep_attr(k_rollout<ST_DD, false>, smem_r(ST_DD, cap)))) return e;
+      return prep_attr(k_rollout<ST_DD, true>, smem_r(ST_DD, cap));
+    case ST_F32:
+      if ((e = prep_attr(k_pass_a<ST_F32>, smem_a(ST_F32, cap)))) return e;
+      if ((e = prep_attr(k_pass_b<ST_F32>, smem_b(ST_F32, cap)))) return e;
+      if ((e = prep_attr(k_rollout<ST_F32, false>, smem_r(ST_F32, cap)))) return e;
+      return prep_attr(k_rollout<ST_F32, true>, smem_r(ST_F32, cap));
+    default:
+      if ((e = prep_attr(k_pass_a<ST_BF16>, smem_a(ST_BF16, cap)))) return e;
+      if ((e = prep_attr(k_pass_b<ST_BF16>, smem_b(ST_BF16, cap)))) return e;
+      if ((e = prep_attr(k_rollout<ST_BF16, false>, smem_r(ST_BF16, cap)))) return e;
+      return prep_attr(k_rollout<ST_BF16, true>, smem_r(ST_BF16, cap));
+  }
+}
+
+cudaError_t launch_pass_a(const Ws& ws, cudaStream_t s) {
+  const int sm = smem_a(ws.prec, ws.cap);
+  switch (ws.prec) {
+    case ST_DD:
+      k_pass_a<ST_DD><<<ws.gridA, kThreadsA, sm, s>>>(ws);
       break;
     case ST_F32:
-      if ((e = prep_attr(k_pass_a<ST_F32>, sm))) return e;
-      k_pass_a<ST_F32><<<ws.gridA, kThreads, sm, s>>>(ws);
+      k_pass_a<ST_F32><<<ws.gridA, kThreadsA, sm, s>>>(ws);
       break;
     default:
-      if ((e = prep_attr(k_pass_a<ST_BF16>, sm))) return e;
-      k_pass_a<ST_BF16><<<ws.gridA, kThreads, sm, s>>>(ws);
+      k_pass_a<ST_BF16><<<ws.gridA, kThreadsA, sm, s>>>(ws);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_pass_b(const Ws& ws, cudaStream_t s) {
   const int sm = smem_b(ws.prec, ws.cap);
-  cudaError_t e;
   switch (ws.prec) {
     case ST_DD:
-      if ((e = prep_attr(k_pass_b<ST_DD>, sm))) return e;
       k_pass_b<ST_DD><<<ws.gridA, kThreads, sm, s>>>(ws);
       break;
     case ST_F32:
-      if ((e = prep_attr(k_pass_b<ST_F32>, sm))) return e;
       k_pass_b<ST_F32><<<ws.gridA, kThreads, sm, s>>>(ws);
       break;
     default:
-      if ((e = prep_attr(k_pass_b<ST_BF16>, sm))) return e;
       k_pass_b<ST_BF16><<<ws.gridA, kThreads, sm, s>>>(ws);
   }
   return cudaGetLastError();
@@ -832,27 +871,60 @@ cudaError_t launch_pass_b(const Ws& ws, cudaStream_t s) {
 cudaError_t launch_first(const Ws& ws, cudaStream_t s) {
   const int grid = 64;  // the partial buffer always holds at least 64 rows
   if (ws.prec == ST_DD)
-    k_first<double><<<grid, kThreads, 0, s>>>(ws);
+    k_first<float2><<<grid, kThreads, 0, s>>>(ws);
   else
     k_first<float><<<grid, kThreads, 0, s>>>(ws);
   return cudaGetLastError();
 }
 
+// Copy a caller's double snapshot into the workspace as float pairs (all SMs; the only
+// FP64 instructions a snapshot meets).
+__global__ void __launch_bounds__(kThreads) k_ingest_dd(const double* __restrict__ src, float2* __restrict__ dst,
+                                                        int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+    float h, l;
+    split_double(src[i], h, l);
+    dst[i] = make_float2(h, l);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_ingest_f32(const float* __restrict__ src, float* __restrict__ dst,
+                                                         int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
+    dst[i] = src[i];
+}
+
+static int ingest_grid(const Ws& ws) {
+  const int64_t blocks = (ws.n + kThreads - 1) / kThreads;
+  return (int)(blocks < 4 * 152 ? blocks : 4 * 152);
+}
+
+cudaError_t launch_ingest(const Ws& ws, const void* src, void* dst, cudaStream_t s) {
+  if (ws.prec == ST_DD)
+    k_ingest_dd<<<ingest_grid(ws), kThreads, 0, s>>>(reinterpret_cast<const double*>(src),
+                                                     reinterpret_cast<float2*>(dst), ws.n);
+  else
+    k_ingest_f32<<<ingest_grid(ws), kThreads, 0, s>>>(reinterpret_cast<const float*>(src),
+                                                      reinterpret_cast<float*>(dst), ws.n);
+  return cudaGetLastError();
+}
+
+const void* ingest_kernel(int prec) {
+  return prec == ST_DD ? reinterpret_cast<const void*>(&k_ingest_dd) : reinterpret_cast<const void*>(&k_ingest_f32);
+}
+
+
 // coef_mode unused here (coefficients are always read from ws.sm.coef)
 cudaError_t launch_rollout(const Ws& ws, const double*, int kcols, void* out, int64_t ld, int, cudaStream_t s) {
   const int sm = smem_r(ws.prec, ws.cap);
-  cudaError_t e;
   switch (ws.prec) {
     case ST_DD:
-      if ((e = prep_attr(k_rollout<ST_DD, false>, sm))) return e;
       k_rollout<ST_DD, false><<<ws.gridA, kThreads, sm, s>>>(ws, kcols, out, ld);
       break;
     case ST_F32:
-      if ((e = prep_attr(k_rollout<ST_F32, false>, sm))) return e;
       k_rollout<ST_F32, false><<<ws.gridA, kThreads, sm, s>>>(ws, kcols, out, ld);
       break;
     default:
-      if ((e = prep_attr(k_rollout<ST_BF16, false>, sm))) return e;
       k_rollout<ST_BF16, false><<<ws.gridA, kThreads, sm, s>>>(ws, kcols, out, ld);
   }
   return cudaGetLastError();
@@ -860,18 +932,14 @@ cudaError_t launch_rollout(const Ws& ws, const double*, int kcols, void* out, in
 
 cudaError_t launch_check(const Ws& ws, cudaStream_t s) {
   const int sm = smem_r(ws.prec, ws.cap);
-  cudaError_t e;
   switch (ws.prec) {
     case ST_DD:
-      if ((e = prep_attr(k_rollout<ST_DD, true>, sm))) return e;
       k_rollout<ST_DD, true><<<ws.gridA, kThreads, sm, s>>>(ws, 1, nullptr, 0);
       break;
     case ST_F32:
-      if ((e = prep_attr(k_rollout<ST_F32, true>, sm))) return e;
       k_rollout<ST_F32, true><<<ws.gridA, kThreads, sm, s>>>(ws, 1, nullptr, 0);
       break;
     default:
-      if ((e = prep_attr(k_rollout<ST_BF16, true>, sm))) return e;
       k_rollout<ST_BF16, true><<<ws.gridA, kThreads, sm, s>>>(ws, 1, nullptr, 0);
   }
   return cudaGetLastError();
