@@ -133,7 +133,7 @@ Layout make_layout(const odmd_config& c) {
   L.off_maps = take(2 * kMaxMaps * sizeof(CUtensorMap));
   L.off_hdr[0] = take(sizeof(StateHdr));
   L.off_hdr[1] = take(sizeof(StateHdr));
-  L.state_doubles = 3 * (size_t)L.rmax + (size_t)L.rmax * L.rmax + (size_t)qld * L.rmax + qld;
+  L.state_doubles = 3 * (size_t)L.rmax + (size_t)L.rmax * L.rmax + (size_t)qld * L.rmax + 2 * (size_t)qld;
   L.off_state[0] = take(L.state_doubles * sizeof(float2));
   L.off_state[1] = take(L.state_doubles * sizeof(float2));
   // small scratch: double-floats then ints
@@ -187,6 +187,8 @@ void carve(Ws& ws, const Layout& L, unsigned char* base, const odmd_config& c, i
     s.Q = d;
     d += (size_t)qld * L.rmax;
     s.a = d;
+    d += qld;
+    s.ps = d;
   }
   float2* d = reinterpret_cast<float2*>(base + L.off_small);
   Small& sm = ws.sm;
@@ -446,6 +448,15 @@ odmd_status build_update_graph(odmd_t h, int par, int prof) {
   return ODMD_OK;
 }
 
+// Write the column appended by the last update if the next tall pass has not yet done
+// so (the kernel returns at once when nothing is pending).
+odmd_status flush_pending(odmd_t h) {
+  if (h->nsnap < 2) return ODMD_OK;
+  ProfScope ps(h, ODMD_K_PASS_B, 1);
+  CK(h, launch_flush(h->ws, h->stream), "flush launch");
+  return ODMD_OK;
+}
+
 odmd_status ensure_eig(odmd_t h) {
   if (!h->eig_dirty) return ODMD_OK;
   {
@@ -637,6 +648,7 @@ odmd_status odmd_predict(odmd_t h, const double* t_host, int32_t k, void* out_de
   for (int i = 0; i < k; ++i)
     if (!(t_host[i] >= 0.0) || !std::isfinite(t_host[i])) return fail(h, ODMD_ERR_ARG, "t must be finite and >= 0");
   if (odmd_status s = ensure_eig(h)) return s;
+  if (odmd_status s = flush_pending(h)) return s;
   const size_t vs = (size_t)vsz_of(h->cfg.prec);
   for (int j0 = 0; j0 < k; j0 += kRollK) {
     const int kk = (k - j0) < kRollK ? (k - j0) : kRollK;
@@ -664,6 +676,7 @@ odmd_status odmd_check(odmd_t h, double t, const void* x_fom_dev, double tol, do
     ProfScope ps(h, ODMD_K_COEF, 1);
     CK(h, launch_coef(h->ws, &t, 1, h->stream), "coef launch");
   }
+  if (odmd_status s = flush_pending(h)) return s;
   {
     ProfScope ps(h, ODMD_K_CHECK, 1);
     CK(h, launch_check(h->ws, h->stream), "check launch");
@@ -751,6 +764,7 @@ odmd_status odmd_get_basis(odmd_t h, void* out_dev, int64_t ld, int32_t* r) {
   if (odmd_status s = read_hdr(h, &hdr)) return s;
   *r = hdr.r;
   if (hdr.r == 0) return ODMD_OK;
+  if (odmd_status s = flush_pending(h)) return s;
   {
     ProfScope ps(h, ODMD_K_COEF, 1);
     CK(h, launch_basis_coef(h->ws, h->stream), "basis coef launch");

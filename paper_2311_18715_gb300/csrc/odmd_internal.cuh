@@ -47,8 +47,10 @@ struct StateHdr {
   int r0;       // number of tall-basis columns in use
   int pairs;    // snapshot pairs ingested
   int compactions;
+  int pend;     // 1: column r0-1 of L0 is not yet written (formed by the next tall pass)
+  int pad_i;
   float2 cn2;   // ||c||^2 of the latest snapshot c
-  float2 pad;
+  float2 pinv;  // 1/rho0 of the pending column
 };
 
 struct StateBuf {
@@ -59,6 +61,7 @@ struct StateBuf {
   float2* M;    // r_max x r_max, column-major, ld = r_max   (M = L^T U^+ R)
   float2* Q;    // (cap+1) x r_max, column-major, ld = cap+1  (L = L0 Q)
   float2* a;    // cap+1   L0^T c
+  float2* ps;   // cap+1   coefficients s of the pending column: (e - L0 s) / rho0
 };
 
 // Control block: indices of the committed buffers, tickets, status, small scalars.
@@ -299,6 +302,7 @@ __device__ __forceinline__ Acc warp_sum_acc(Acc a) {
 // tall.cu
 cudaError_t launch_pass_a(const Ws& ws, cudaStream_t s);
 cudaError_t launch_pass_b(const Ws& ws, cudaStream_t s);
+cudaError_t launch_flush(const Ws& ws, cudaStream_t s);  // write a pending basis column
 cudaError_t launch_first(const Ws& ws, cudaStream_t s);
 cudaError_t launch_ingest(const Ws& ws, const void* src, void* dst, cudaStream_t s);  // snapshot -> workspace
 const void* ingest_kernel(int prec);  // the kernel launch_ingest uses (graph node lookup)

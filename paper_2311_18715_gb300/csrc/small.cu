@@ -391,48 +391,76 @@ __global__ void __launch_bounds__(32) k_roots(Ws ws) {
     const dd cand = dd_of(muf);
     if (isfinite(muf) && dd_gt(cand, lo) && dd_lt(cand, hi)) mu = cand;
   }
-  // ---- stage 2, double-float: polish inside the original bracket (bisection fallback)
+  // ---- stage 2: f in double-float, derivatives and the model step in FP32.  The model is
+  // solved for the correction delta = x - mu (shifted poles A - mu, B - mu), so an FP32
+  // step applied to a double-float mu converges like Newton to double-float accuracy.
   bool conv = false;
   for (int it = 0; it < 100; ++it) {
-    const SecSums s = sec_eval(d, z, m, j, o, mu);
-    const dd f = dd_of(1.f) + s.psi + s.phi;
+    dd psi = dzero(), phi = dzero();
+    float dpsi = 0.f, dphi = 0.f;
+    {
+      const dd dob = LD(d, o);
+      for (int i = lane; i < m; i += 32) {
+        const dd di = LD(d, i);
+        const dd del = (di - dob) * (di + dob) - mu;  // d_i^2 - lambda
+        const dd zi = LD(z, i);
+        // t = z / del: FP32 reciprocal, then one correction of the quotient
+        const float rc = __frcp_rn(del.h);
+        const float t0 = __fmul_rn(zi.h, rc);
+        const dd rem = zi - del * t0;
+        const dd t = fast_two_sum(t0, __fmul_rn(rem.h, rc));
+        const dd term = zi * t;
+        const float dterm = t.h * t.h;
+        if (i <= j) {
+          psi = psi + term;
+          dpsi += dterm;
+        } else {
+          phi = phi + term;
+          dphi += dterm;
+        }
+      }
+      psi = dd_warp_sum(psi);
+      phi = dd_warp_sum(phi);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        dpsi += __shfl_xor_sync(0xffffffffu, dpsi, off);
+        dphi += __shfl_xor_sync(0xffffffffu, dphi, off);
+      }
+    }
+    const dd f = dd_of(1.f) + psi + phi;
     if (f.h < 0.f)
       lo = mu;
     else
       hi = mu;
-    const float ftol = 8.f * kEpsDD * (float)m * (1.f + fabsf(s.psi.h) + fabsf(s.phi.h));
+    const float ftol = 8.f * kEpsDD * (float)m * (1.f + fabsf(psi.h) + fabsf(phi.h));
     if (fabsf(f.h) <= ftol) {
       conv = true;
       break;
     }
-    // two-pole rational model of f matching value and slope at mu
-    const dd Am = A - mu;
-    const dd c1 = s.dpsi * Am * Am;
-    const dd a1 = s.psi - s.dpsi * Am;
-    dd x;
+    // Two-pole model written around mu with f explicit, so that FP32 coefficients give a
+    // step accurate relative to itself:  f + psi' a d/(a - d) + phi' b d/(b - d) = 0,
+    // with the neighbouring poles at a = A - mu and b = B - mu and the unknown d = x - mu.
+    const float fh = f.h;
+    const float a = (A - mu).h;
+    float delta;
     if (!last) {
-      const dd Bm = B - mu;
-      const dd c2 = s.dphi * Bm * Bm;
-      const dd a2 = s.phi - s.dphi * Bm;
-      const dd C = dd_of(1.f) + a1 + a2;
-      // C (A-x)(B-x) + c1 (B-x) + c2 (A-x) = 0
-      const dd qb = -(C * (A + B) + c1 + c2);
-      const dd qc = C * A * B + c1 * B + c2 * A;
-      if (fabsf(C.h) <= kEpsDD * (fabsf(qb.h) + fabsf(qc.h))) {
-        x = dd_div(-qc, qb);
-      } else {
-        const dd disc = qb * qb - C * qc * 4.f;
-        const dd sq = dd_sqrt(disc.h > 0.f ? disc : dzero());
-        const dd q = (qb.h >= 0.f ? qb + sq : qb - sq) * -0.5f;
-        const dd x1 = dd_div(q, C), x2 = dd_div(qc, q);
-        const bool in1 = dd_gt(x1, lo) && dd_lt(x1, hi), in2 = dd_gt(x2, lo) && dd_lt(x2, hi);
-        x = in1 && !in2 ? x1 : (in2 && !in1 ? x2 : (dd_lt(dd_abs(x1 - mu), dd_abs(x2 - mu)) ? x1 : x2));
-      }
+      const float b = (B - mu).h;
+      const float Qa = fh - dpsi * a - dphi * b;
+      const float Qb = a * b * (dpsi + dphi) - fh * (a + b);
+      const float Qc = fh * a * b;
+      const float disc = fmaxf(Qb * Qb - 4.f * Qa * Qc, 0.f);
+      const float q = -0.5f * (Qb >= 0.f ? Qb + sqrtf(disc) : Qb - sqrtf(disc));
+      const float d2 = q != 0.f ? Qc / q : 0.f;  // the root that tends to -f / f'
+      const float d1 = Qa != 0.f ? q / Qa : d2;
+      const float lo_s = (lo - mu).h, hi_s = (hi - mu).h;
+      const bool in2 = d2 > lo_s && d2 < hi_s, in1 = d1 > lo_s && d1 < hi_s;
+      delta = in2 ? d2 : (in1 ? d1 : d2);
     } else {
-      const dd C = dd_of(1.f) + a1 + s.phi;
-      x = C.h > 0.f ? A + dd_div(c1, C) : (lo + hi) * 0.5f;
+      const float den = fh - dpsi * a;
+      delta = den != 0.f ? fh * a / den : 0.f;
     }
-    if (!(dd_gt(x, lo) && dd_lt(x, hi))) x = (lo + hi) * 0.5f;
+    dd x = mu + dd_of(delta);
+    if (!isfinite(delta) || !(dd_gt(x, lo) && dd_lt(x, hi))) x = (lo + hi) * 0.5f;
     const dd step = dd_abs(x - mu);
     mu = x;
     if (step.h <= 4.f * kEpsDD * fabsf(mu.h) ||
@@ -606,6 +634,9 @@ __global__ void __launch_bounds__(64) k_vectors(Ws ws) {
 // ---------------------------------------------------------------------------------------
 constexpr int kApplyThreads = 256;
 
+__device__ void apply_column(const Ws& ws, int j, const StateBuf& st, const StateBuf& nx, int r, int r0, int r0e,
+                             bool compact);
+
 __global__ void __launch_bounds__(kApplyThreads) k_apply(Ws ws) {
   Ctl* ctl = ws.ctl;
   const int j = blockIdx.x;
@@ -617,17 +648,47 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(Ws ws) {
   const int r0e = ctl->r0e;
   const int cap = ws.cap, qld = cap + 1, rm = ws.rmax;
   const bool compact = r0e > cap;
+  const int append = ctl->append;
   if (j == 0 && tid == 0) {
     nx.hdr->r = rnew;
     nx.hdr->r0 = compact ? rnew : r0e;
     nx.hdr->pairs = st.hdr->pairs + 1;
     nx.hdr->compactions = st.hdr->compactions + (compact ? 1 : 0);
     nx.hdr->cn2 = ws.sm.red[2 * r0 + 2];
-    ctl->mode = compact ? PB_COMPACT : (ctl->append ? PB_APPEND : PB_NONE);
+    // an appended column is formed by the next tall pass (compaction forms it at once)
+    nx.hdr->pend = (append && !compact) ? 1 : 0;
+    nx.hdr->pinv = append ? f2_of(dd_div(dd_of(1.f), dd_of(ctl->rho0))) : make_float2(0.f, 0.f);
+    ctl->mode = compact ? PB_COMPACT : (append ? PB_APPEND : PB_NONE);
   }
-  if (!compact && j == 0)
-    for (int i = tid; i < r0e; i += kApplyThreads) nx.a[i] = ws.sm.yext[i];
-  if (j >= rnew) return;
+  if (j == 0) {
+    if (!compact)
+      for (int i = tid; i < r0e; i += kApplyThreads) nx.a[i] = ws.sm.yext[i];
+    if (append && !compact)
+      for (int i = tid; i < r0; i += kApplyThreads) nx.ps[i] = ws.sm.red[i];
+  }
+  if (j < rnew) apply_column(ws, j, st, nx, r, r0, r0e, compact);
+  // the last CTA commits the new state and snapshot buffers
+  __shared__ unsigned ticket;
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) ticket = atomicAdd(&ctl->ticket_b, 1u);
+  __syncthreads();
+  if (ticket != gridDim.x - 1) return;
+  if (tid == 0) {
+    __threadfence();
+    ctl->cur = cur ^ 1;
+    ctl->cur_c = ctl->cur_c ^ 1;
+    ctl->eig_valid = 0;
+    ctl->ticket_b = 0u;
+  }
+}
+
+__device__ void apply_column(const Ws& ws, int j, const StateBuf& st, const StateBuf& nx, int r, int r0, int r0e,
+                             bool compact) {
+  Ctl* ctl = ws.ctl;
+  const int tid = threadIdx.x;
+  const int n = r + 1, rnew = ctl->rnew;
+  const int qld = ws.cap + 1, rm = ws.rmax;
   const dd rho = dd_of(ctl->rho), gamma = dd_of(ctl->gamma);
   __shared__ float2 v[kMaxN], u[kMaxN], bv[kMaxN], qcol[kMaxCap + 1], rlv[2];
   for (int i = tid; i < n; i += kApplyThreads) {

@@ -49,13 +49,13 @@ __device__ __forceinline__ int rows_in(int64_t n, int64_t row0) {
 }
 
 
-// each stage: the basis rows (per plane, widest box) and two per-row slots of 8 bytes;
-// every part starts on a 1024-byte boundary (TMA tile destinations need 128).
+// each stage: the basis rows (per plane, widest box) and three per-row slots of 8 bytes;
+// every part starts on a 512-byte boundary (TMA tile destinations need 128).
 template <int ST>
 __host__ __device__ inline int stage_bytes(int cap) {
   using T = Traits<ST>;
   const int rs_max = 16 * box_chunks(cap, T::esz);
-  return kTile * rs_max * T::planes + 2 * kTile * 8;
+  return kTile * rs_max * T::planes + 3 * kTile * 8;
 }
 
 // Stored snapshot element -> float-float
@@ -118,19 +118,20 @@ __device__ __forceinline__ void load_elem(const unsigned char* plane_h, const un
 
 // Shared-memory pipeline over the row tiles owned by this CTA.  Each tile is one 2-D
 // TMA load per basis plane (box: the active chunks of kTile rows) plus 1-D bulk copies
-// of the per-row slots, all completing on the stage's mbarrier.
+// of up to three per-row slots (8 bytes per row each), all completing on the stage's
+// mbarrier.
 template <int ST>
 struct TilePipe {
   using T = Traits<ST>;
+  static constexpr int kSlots = 3;
   unsigned char* base;
   uint64_t* bars;
   int stages, stage_sz, rs, nch, plane_off;
   int64_t n;
   const CUtensorMap* mh;    // map of the hi (or only) plane for the current box, or nullptr
   const CUtensorMap* ml;    // map of the lo plane (FP64 mode)
-  const unsigned char* gc;  // first per-row slot (snapshot c, or the residual e), or nullptr
-  const unsigned char* gx;  // second per-row slot (snapshot x), or nullptr
-  int vc, vx;               // bytes per row of the two slots
+  const unsigned char* g[kSlots];  // per-row slots (or nullptr)
+  int vb[kSlots];                  // bytes per row of each slot
 
   __device__ void setup(const Ws& ws, int r0, int nstages) {
     stages = nstages;
@@ -148,32 +149,67 @@ struct TilePipe {
       nch = 0;
       mh = ml = nullptr;
     }
-    gc = gx = nullptr;
-    vc = vx = 0;
+    for (int i = 0; i < kSlots; ++i) {
+      g[i] = nullptr;
+      vb[i] = 0;
+    }
   }
   __device__ unsigned char* plane_h(int s) const { return base + (size_t)s * stage_sz; }
   __device__ unsigned char* plane_l(int s) const { return plane_h(s) + plane_off; }
-  __device__ unsigned char* snap_c(int s) const { return plane_h(s) + plane_off * T::planes; }
-  __device__ unsigned char* snap_x(int s) const { return snap_c(s) + kTile * 8; }
+  __device__ unsigned char* slot(int s, int i) const { return plane_h(s) + plane_off * T::planes + i * kTile * 8; }
 
   // Issue the copies of tile `tile` into stage `s` (called by one thread).
   __device__ void issue(int tile, int s) const {
     const int row0 = tile * kTile;
-    const uint32_t bytes = (mh ? (uint32_t)(kTile * rs * T::planes) : 0u) + (gc ? kTile * vc : 0) +
-                           (gx ? kTile * vx : 0);
+    uint32_t bytes = mh ? (uint32_t)(kTile * rs * T::planes) : 0u;
+    for (int i = 0; i < kSlots; ++i)
+      if (g[i]) bytes += kTile * vb[i];
     mbar_arrive_expect_tx(&bars[s], bytes);
     if (mh) {
       tma_load_2d(plane_h(s), mh, 0, row0, &bars[s]);
       if (T::planes == 2) tma_load_2d(plane_l(s), ml, 0, row0, &bars[s]);
     }
-    if (gc) bulk_g2s(snap_c(s), gc + (size_t)row0 * vc, kTile * vc, &bars[s]);
-    if (gx) bulk_g2s(snap_x(s), gx + (size_t)row0 * vx, kTile * vx, &bars[s]);
+    for (int i = 0; i < kSlots; ++i)
+      if (g[i]) bulk_g2s(slot(s, i), g[i] + (size_t)row0 * vb[i], kTile * vb[i], &bars[s]);
   }
 };
 
-// Phase 1: NSUB threads per row (thread = sub*64 + t) form partial row dots with the
-// coefficient vector (float-float, zero-padded to whole chunks) held in shared memory.
-template <int ST, int NSUB = 4>
+// A basis element as stored (rounded to the storage format), as a float pair.
+template <int ST>
+__device__ __forceinline__ void round_to_storage(float& h, float& l) {
+  if constexpr (ST == ST_BF16) {
+    h = __bfloat162float(__float2bfloat16_rn(h));
+    l = 0.f;
+  } else if constexpr (ST == ST_F32) {
+    h = h + l;
+    l = 0.f;
+  }
+}
+
+template <int ST>
+__device__ __forceinline__ void store_elem_global(const Ws& ws, size_t o, float h, float l) {
+  if constexpr (ST == ST_BF16) {
+    reinterpret_cast<__nv_bfloat16*>(ws.Lh)[o] = __float2bfloat16_rn(h);
+  } else {
+    reinterpret_cast<float*>(ws.Lh)[o] = h;
+    if constexpr (ST == ST_DD) ws.Ll[o] = l;
+  }
+}
+
+template <int ST>
+__device__ __forceinline__ void store_elem_smem(unsigned char* ph, unsigned char* pl, int rs, int row, int k, float h,
+                                                float l) {
+  if constexpr (ST == ST_BF16) {
+    reinterpret_cast<__nv_bfloat16*>(ph + row * rs)[k] = __float2bfloat16_rn(h);
+  } else {
+    reinterpret_cast<float*>(ph + row * rs)[k] = h;
+    if constexpr (ST == ST_DD) reinterpret_cast<float*>(pl + row * rs)[k] = l;
+  }
+}
+
+// Partial row dot over chunks sub, sub + NSUB, ... of smem row t with a float-float
+// coefficient vector (zero beyond its length).
+template <int ST, int NSUB>
 __device__ __forceinline__ Acc row_dot_partial(const TilePipe<ST>& P, int s, int t, int sub, const float* coh,
                                                const float* col) {
   Acc acc = acc_zero();
@@ -190,55 +226,106 @@ __device__ __forceinline__ Acc row_dot_partial(const TilePipe<ST>& P, int s, int
   return acc;
 }
 
+// Sum over the 8 adjacent lanes of a row group (every lane gets the sum).
+__device__ __forceinline__ Acc group8_sum(Acc a) {
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) {
+    const float h = __shfl_xor_sync(0xffffffffu, a.h, o);
+    const float l = __shfl_xor_sync(0xffffffffu, a.l, o);
+    acc_add(a, h, l);
+  }
+  return a;
+}
+
 // ---------------------------------------------------------------------------------------
-// pass A (512 threads: 8 per row in phase 1, 512 / r0 row groups in phase 2)
+// pass A (512 threads, warp-specialised): the pending column of the previous update (if
+// any) is formed row by row from its stored residual, written to L0 and used at once; then
+//   e = c - L0 a, s = L0^T e, y = L0^T x, ||e||^2, e.x, ||x||^2.
+// Warps 0-7 (producers) form the row dots of tile i+1 (4 lanes per row) while warps 8-15
+// (consumers) sum down the columns of tile i; e and x of a tile pass through one of two
+// shared slots, handed over with named barriers (full: 1,2; empty: 3,4).
 // ---------------------------------------------------------------------------------------
 constexpr int kThreadsA = 512;
-constexpr int kSubA = kThreadsA / kTile;
+constexpr int kHalfA = kThreadsA / 2;
+constexpr int kRowLanesA = kHalfA / kTile;  // 4
+
+__device__ __forceinline__ void named_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void named_arrive(int id, int count) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ Acc group4_acc_sum(Acc a) {
+#pragma unroll
+  for (int o = 1; o < 4; o <<= 1) {
+    const float h = __shfl_xor_sync(0xffffffffu, a.h, o);
+    const float l = __shfl_xor_sync(0xffffffffu, a.l, o);
+    acc_add(a, h, l);
+  }
+  return a;
+}
+
 template <int ST>
 __global__ void __launch_bounds__(kThreadsA) k_pass_a(Ws ws) {
   using T = Traits<ST>;
-  using snap_t = typename T::snap_t;
+  using stored_t = typename T::stored_t;
   extern __shared__ __align__(1024) unsigned char smem[];
   Ctl* ctl = ws.ctl;
   const int cur = ctl->cur, curc = ctl->cur_c;
   const StateBuf st = ws.st[cur];
   const int r0 = st.hdr->r0;
+  const int pend = st.hdr->pend;  // column p = r0 - 1 is formed here
+  const int p = r0 - 1;
   const int tid = threadIdx.x;
+  const bool producer = tid < kHalfA;
+  const int htid = producer ? tid : tid - kHalfA;
 
   TilePipe<ST> P;
   P.setup(ws, r0, kStages);
-  P.gc = (const unsigned char*)ws.cbuf[curc];
-  P.gx = (const unsigned char*)ws.cbuf[curc ^ 1];
-  P.vc = T::vsz;
-  P.vx = T::vsz;
+  P.g[0] = (const unsigned char*)ws.cbuf[curc];
+  P.g[1] = (const unsigned char*)ws.cbuf[curc ^ 1];
+  P.vb[0] = P.vb[1] = T::vsz;
+  if (pend) {
+    P.g[2] = (const unsigned char*)ws.ebuf;  // residual of the previous update
+    P.vb[2] = 8;
+  }
 
-  // shared layout: stages | bars | a (hi, lo: kMaxCap+8 each) | e,x (4 x kTile) | red (4 x kTile Acc)
+  // shared layout: stages | bars | a (hi, lo) | s_prev (hi, lo) | 2 slots of (e, x) | accumulators
   P.base = smem;
-  unsigned char* p = smem + (size_t)kStages * P.stage_sz;
-  P.bars = reinterpret_cast<uint64_t*>(p);
-  p += 8 * kStages;
-  float* coh = reinterpret_cast<float*>(p);
+  unsigned char* sp = smem + (size_t)kStages * P.stage_sz;
+  P.bars = reinterpret_cast<uint64_t*>(sp);
+  sp += 8 * kStages;
+  float* coh = reinterpret_cast<float*>(sp);
   float* col = coh + (kMaxCap + 8);
-  float* eh = col + (kMaxCap + 8);
-  float* el = eh + kTile;
-  float* xh = el + kTile;
-  float* xl = xh + kTile;
-  Acc* part = reinterpret_cast<Acc*>(xl + kTile);       // [kSubA][kTile]
-  Acc* colacc = part + kSubA * kTile;                    // [kThreadsA][2] group accumulators
+  float* csh = col + (kMaxCap + 8);
+  float* csl = csh + (kMaxCap + 8);
+  float4* ex4 = reinterpret_cast<float4*>(csl + (kMaxCap + 8));  // [2][kTile] (eh, el, xh, xl)
+  Acc* colacc = reinterpret_cast<Acc*>(ex4 + 2 * kTile);          // [kHalfA][2]
+  __shared__ int abort_flag;
 
-  const int elems_per_chunk = (ST == ST_BF16) ? 8 : 4;
+  const int epc = (ST == ST_BF16) ? 8 : 4;
+  const int kpad = P.nch * epc;
   for (int k = tid; k < kMaxCap + 8; k += kThreadsA) {
-    float h = 0.f, l = 0.f;
-    if (k < r0) {
+    float h = 0.f, l = 0.f, sh = 0.f, sl = 0.f;
+    if (k < r0 && !(pend && k == p)) {
       h = st.a[k].x;
       l = st.a[k].y;
     }
-    if (k >= P.nch * elems_per_chunk) h = l = 0.f;
+    if (pend && k < p) {
+      sh = st.ps[k].x;
+      sl = st.ps[k].y;
+    }
+    if (k >= kpad) h = l = sh = sl = 0.f;
     coh[k] = h;
     col[k] = l;
+    csh[k] = sh;
+    csl[k] = sl;
   }
+  const float aph = pend ? st.a[p].x : 0.f, apl = pend ? st.a[p].y : 0.f;
+  const float pih = st.hdr->pinv.x, pil = st.hdr->pinv.y;
   if (tid == 0) {
+    abort_flag = 0;
     for (int s = 0; s < kStages; ++s) mbar_init(&P.bars[s], 1);
     mbar_fence_init();
   }
@@ -251,76 +338,129 @@ __global__ void __launch_bounds__(kThreadsA) k_pass_a(Ws ws) {
     for (int li = 0; li < min(my_tiles, kStages); ++li) P.issue(blockIdx.x + li * G, li);
   }
 
-  const int t = tid & 63, sub = tid >> 6;
   const int ncol = max(r0, 1);
-  const int G2 = kThreadsA / ncol;
-  const int kcol = tid % ncol, grp = tid / ncol;
-  const bool col_active = (r0 > 0) && grp < G2;
-  Acc S_acc = acc_zero(), Y_acc = acc_zero();
-  Acc eta = acc_zero(), ex = acc_zero(), xi = acc_zero();
+  const int G2 = kHalfA / ncol;
+  Acc S_acc = acc_zero(), Y_acc = acc_zero(), S2 = acc_zero(), Y2 = acc_zero();
+  Acc eta = acc_zero(), exa = acc_zero(), xi = acc_zero();
 
-  for (int li = 0; li < my_tiles; ++li) {
-    const int s = li % kStages;
-    const uint32_t par = (uint32_t)((li / kStages) & 1);
-    const int tile = blockIdx.x + li * G;
-    const int64_t row0 = (int64_t)tile * kTile;
-    const int rows = rows_in(ws.n, row0);
-    const bool ok = mbar_wait(&P.bars[s], par, &ctl->status);
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) mbar_drain(P.bars, kStages, li, my_tiles);
-      __syncthreads();
-      break;
-    }
-    {
-      // phase 1: residual e_t = c_t - L0_t . a
-      part[sub * kTile + t] = row_dot_partial<ST, kSubA>(P, s, t, sub, coh, col);
-      __syncthreads();
-      if (sub == 0) {
-        float ch, cl, xh_, xl_;
-        load_snap(reinterpret_cast<const typename T::stored_t*>(P.snap_c(s)), t, ch, cl);
-        load_snap(reinterpret_cast<const typename T::stored_t*>(P.snap_x(s)), t, xh_, xl_);
-        Acc d = part[t];
-#pragma unroll
-        for (int q = 1; q < kSubA; ++q) acc_add(d, part[q * kTile + t].h, part[q * kTile + t].l);
-        Acc e = Acc{ch, cl};
-        acc_add(e, -d.h, -d.l);
-        e = acc_norm(e);
-        if (t >= rows) {
-          e = acc_zero();
-          xh_ = xl_ = 0.f;
-        } else {
-          ws.ebuf[row0 + t] = make_float2(e.h, e.l);  // kept for the second Gram-Schmidt pass
+  if (producer) {
+    const int t = htid >> 2, sub = htid & (kRowLanesA - 1);
+    for (int li = 0; li < my_tiles; ++li) {
+      const int s = li % kStages, slot = li & 1;
+      const uint32_t par = (uint32_t)((li / kStages) & 1);
+      const int64_t row0 = (int64_t)(blockIdx.x + li * G) * kTile;
+      const int rows = rows_in(ws.n, row0);
+      if (li >= 2) named_sync(3 + slot, kThreadsA);  // consumers are done with this slot
+      bool ok = !abort_flag;
+      if (ok) ok = mbar_wait(&P.bars[s], par, &ctl->status);
+      if (!ok) abort_flag = 1;
+      if (ok) {
+        Acc da = row_dot_partial<ST, kRowLanesA>(P, s, t, sub, coh, col);
+        Acc ds = acc_zero();
+        if (pend) ds = row_dot_partial<ST, kRowLanesA>(P, s, t, sub, csh, csl);
+        da = group4_acc_sum(da);
+        if (pend) ds = group4_acc_sum(ds);
+        if (sub == 0) {
+          float ch, cl, xh_, xl_;
+          load_snap(reinterpret_cast<const stored_t*>(P.slot(s, 0)), t, ch, cl);
+          load_snap(reinterpret_cast<const stored_t*>(P.slot(s, 1)), t, xh_, xl_);
+          if (pend) {
+            // j = (e_prev - L0[:, :p] s_prev) / rho0, as stored; a_p j joins the row dot
+            const float2 ep = reinterpret_cast<const float2*>(P.slot(s, 2))[t];
+            Acc j = Acc{ep.x, ep.y};
+            acc_add(j, -ds.h, -ds.l);
+            j = acc_norm(j);
+            Acc jj = acc_zero();
+            acc_fma(jj, j.h, j.l, pih, pil);
+            jj = acc_norm(jj);
+            float jh = jj.h, jl = jj.l;
+            round_to_storage<ST>(jh, jl);
+            store_elem_smem<ST>(P.plane_h(s), P.plane_l(s), P.rs, t, p, jh, jl);
+            if (t < rows) store_elem_global<ST>(ws, (size_t)(row0 + t) * ws.ldg + p, jh, jl);
+            acc_fma(da, jh, jl, aph, apl);
+          }
+          Acc e = Acc{ch, cl};
+          acc_add(e, -da.h, -da.l);
+          e = acc_norm(e);
+          if (t >= rows) {
+            e = acc_zero();
+            xh_ = xl_ = 0.f;
+          } else {
+            ws.ebuf[row0 + t] = make_float2(e.h, e.l);  // kept for the second Gram-Schmidt pass
+          }
+          ex4[slot * kTile + t] = make_float4(e.h, e.l, xh_, xl_);
+          acc_fma(eta, e.h, e.l, e.h, e.l);
+          acc_fma(exa, e.h, e.l, xh_, xl_);
+          acc_fma(xi, xh_, xl_, xh_, xl_);
         }
-        eh[t] = e.h;
-        el[t] = e.l;
-        xh[t] = xh_;
-        xl[t] = xl_;
-        acc_fma(eta, e.h, e.l, e.h, e.l);
-        acc_fma(ex, e.h, e.l, xh_, xl_);
-        acc_fma(xi, xh_, xl_, xh_, xl_);
       }
-      __syncthreads();
-      // phase 2: column sums s_k += L_tk e_t, y_k += L_tk x_t
-      if (col_active) {
+      named_arrive(1 + slot, kThreadsA);  // slot (and the stage) ready for the consumers
+    }
+    // balance the empty barriers the consumers arrive on for the last two tiles
+    for (int li = max(my_tiles, 2); li < my_tiles + 2; ++li) named_sync(3 + (li & 1), kThreadsA);
+  } else {
+    const int kcol = htid % ncol, grp = htid / ncol;
+    const bool col_active = (r0 > 0) && grp < G2;
+    for (int li = 0; li < my_tiles; ++li) {
+      const int s = li % kStages, slot = li & 1;
+      const int64_t row0 = (int64_t)(blockIdx.x + li * G) * kTile;
+      const int rows = rows_in(ws.n, row0);
+      named_sync(1 + slot, kThreadsA);  // producers filled the slot
+      // observe the stage's completed phase too, so the TMA writes are visible here
+      if (!abort_flag) mbar_wait(&P.bars[s], (uint32_t)((li / kStages) & 1), &ctl->status);
+      if (!abort_flag && col_active) {
         const unsigned char* ph = P.plane_h(s);
         const unsigned char* pl = P.plane_l(s);
-        for (int tt = grp; tt < rows; tt += G2) {
-          float h, l;
-          load_elem<ST>(ph, pl, P.rs, tt, kcol, h, l);
-          acc_fma(S_acc, h, l, eh[tt], el[tt]);
-          acc_fma(Y_acc, h, l, xh[tt], xl[tt]);
+        const float4* ex = ex4 + slot * kTile;
+        int tt = grp;
+        for (; tt + G2 < rows; tt += 2 * G2) {  // two rows per step: four independent chains
+          float h0, l0, h1, l1;
+          load_elem<ST>(ph, pl, P.rs, tt, kcol, h0, l0);
+          load_elem<ST>(ph, pl, P.rs, tt + G2, kcol, h1, l1);
+          const float4 v0 = ex[tt], v1 = ex[tt + G2];
+          acc_fma(S_acc, h0, l0, v0.x, v0.y);
+          acc_fma(Y_acc, h0, l0, v0.z, v0.w);
+          acc_fma(S2, h1, l1, v1.x, v1.y);
+          acc_fma(Y2, h1, l1, v1.z, v1.w);
+        }
+        if (tt < rows) {
+          float h0, l0;
+          load_elem<ST>(ph, pl, P.rs, tt, kcol, h0, l0);
+          const float4 v0 = ex[tt];
+          acc_fma(S_acc, h0, l0, v0.x, v0.y);
+          acc_fma(Y_acc, h0, l0, v0.z, v0.w);
         }
       }
+      // the consumers are the last readers of the stage: refill it, free the slot
+      if (htid == 0 && !abort_flag && li + kStages < my_tiles) P.issue(blockIdx.x + (li + kStages) * G, s);
+      named_arrive(3 + slot, kThreadsA);
     }
-    __syncthreads();
-    if (tid == 0 && li + kStages < my_tiles) P.issue(blockIdx.x + (li + kStages) * G, s);
+    acc_add(S_acc, S2.h, S2.l);
+    acc_add(Y_acc, Y2.h, Y2.l);
   }
+  __syncthreads();
+  if (abort_flag && tid == 0) mbar_drain(P.bars, kStages, 0, my_tiles);
 
   // ---- per-CTA partials
   const int stride = 2 * ws.cap + 3;
   float2* mypart = ws.part + (size_t)blockIdx.x * stride;
-  colacc[2 * tid] = S_acc;
-  colacc[2 * tid + 1] = Y_acc;
+  if (!producer) {
+    colacc[2 * htid] = S_acc;
+    colacc[2 * htid + 1] = Y_acc;
+  }
+  // scalar sums live in the sub == 0 lanes of the producer warps (others hold zeros)
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    acc_add(eta, __shfl_xor_sync(0xffffffffu, eta.h, o), __shfl_xor_sync(0xffffffffu, eta.l, o));
+    acc_add(exa, __shfl_xor_sync(0xffffffffu, exa.h, o), __shfl_xor_sync(0xffffffffu, exa.l, o));
+    acc_add(xi, __shfl_xor_sync(0xffffffffu, xi.h, o), __shfl_xor_sync(0xffffffffu, xi.l, o));
+  }
+  __shared__ Acc wsc[kThreadsA / 32][3];
+  if ((tid & 31) == 0) {
+    wsc[tid >> 5][0] = eta;
+    wsc[tid >> 5][1] = exa;
+    wsc[tid >> 5][2] = xi;
+  }
   __syncthreads();
   if (tid < r0) {
     Acc sS = acc_zero(), sY = acc_zero();
@@ -334,28 +474,11 @@ __global__ void __launch_bounds__(kThreadsA) k_pass_a(Ws ws) {
     mypart[tid] = make_float2(sS.h, sS.l);
     mypart[r0 + tid] = make_float2(sY.h, sY.l);
   }
-  if (tid < 64) {  // threads with sub == 0 hold the scalar sums (warps 0 and 1)
-    eta = warp_sum_acc(eta);
-    ex = warp_sum_acc(ex);
-    xi = warp_sum_acc(xi);
-  }
-  __syncthreads();
-  if (tid == 32) {
-    part[0] = eta;
-    part[1] = ex;
-    part[2] = xi;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    acc_add(eta, part[0].h, part[0].l);
-    acc_add(ex, part[1].h, part[1].l);
-    acc_add(xi, part[2].h, part[2].l);
-    eta = acc_norm(eta);
-    ex = acc_norm(ex);
-    xi = acc_norm(xi);
-    mypart[2 * r0] = make_float2(eta.h, eta.l);
-    mypart[2 * r0 + 1] = make_float2(ex.h, ex.l);
-    mypart[2 * r0 + 2] = make_float2(xi.h, xi.l);
+  if (tid < 3) {
+    Acc a = acc_zero();
+    for (int w = 0; w < kThreadsA / 32; ++w) acc_add(a, wsc[w][tid].h, wsc[w][tid].l);
+    a = acc_norm(a);
+    mypart[2 * r0 + tid] = make_float2(a.h, a.l);
   }
 
   // ---- last CTA reduces all partials in CTA order
@@ -393,66 +516,80 @@ __global__ void __launch_bounds__(kThreadsA) k_pass_a(Ws ws) {
     ctl->ticket_a = 0u;
     ctl->prof_r0_sum += (unsigned long long)r0;
     ctl->prof_a += 1ull;
+    st.hdr->pend = 0;  // the pending column now exists in L0
   }
 }
 
 // ---------------------------------------------------------------------------------------
-// pass B: append the new column, or compact the basis (fused with the append)
+// pass B: compaction L0 <- [L0, j0] QB (with the update's own new column j0 formed from
+// its residual), or -- FLUSH -- writing a pending column before a predict or check.
 // ---------------------------------------------------------------------------------------
 constexpr int kStagesB = 2;
+constexpr int kRowLanes = 8;
+constexpr int kThreadsB = 512;
 
-template <int ST>
-__global__ void __launch_bounds__(kThreads) k_pass_b(Ws ws) {
+template <int ST, bool FLUSH>
+__global__ void __launch_bounds__(kThreadsB) k_pass_b(Ws ws) {
   using T = Traits<ST>;
-  using snap_t = typename T::snap_t;
   extern __shared__ __align__(1024) unsigned char smem[];
   Ctl* ctl = ws.ctl;
   const int tid = threadIdx.x;
-  const int mode = ctl->mode;
-  const int cur = ctl->cur, curc = ctl->cur_c;
-  const StateBuf st = ws.st[cur];
-  const int r0 = st.hdr->r0;
-  const int append = ctl->append;
-  const int rnew = ctl->rnew;
-  const int G = gridDim.x;
-
-  if (mode != PB_NONE) {
-    TilePipe<ST> P;
-    P.setup(ws, r0, kStagesB);
-    P.gc = (const unsigned char*)ws.ebuf;
-    P.vc = 8;
-    P.base = smem;
-    unsigned char* p = smem + (size_t)kStagesB * P.stage_sz;
-    P.bars = reinterpret_cast<uint64_t*>(p);
-    p += 8 * kStagesB;
-    float* coh = reinterpret_cast<float*>(p);
-    float* col = coh + (kMaxCap + 8);
-    float* jh = col + (kMaxCap + 8);
-    float* jl = jh + kTile;
-    Acc* part = reinterpret_cast<Acc*>(jl + kTile);          // [4][kTile]
-    float* qbh = reinterpret_cast<float*>(part + 4 * kTile);  // [(r0+1)][rnew] hi
-    float* qbl = qbh + (kMaxCap + 1) * kMaxR;
-
-    const int elems_per_chunk = (ST == ST_BF16) ? 8 : 4;
-    for (int k = tid; k < kMaxCap + 8; k += kThreads) {
-      float h = 0.f, l = 0.f;
-      if (k < r0 && append) {  // s = L0^T e
-        h = ws.sm.red[k].x;
-        l = ws.sm.red[k].y;
-      }
-      if (k >= P.nch * elems_per_chunk) h = l = 0.f;
-      coh[k] = h;
-      col[k] = l;
-    }
-    float ih = 0.f, il = 0.f;  // 1/rho0
+  const StateBuf st = ws.st[ctl->cur];
+  int r0, append, rnew;  // r0: columns of L0 that exist; append: form column r0 too
+  float ih = 0.f, il = 0.f;
+  const float2* sco;     // coefficients of the new column: (e - L0[:, :r0] s) / rho0
+  bool work;
+  if constexpr (FLUSH) {
+    work = st.hdr->pend != 0;
+    r0 = st.hdr->r0 - 1;
+    append = 1;
+    rnew = 0;
+    ih = st.hdr->pinv.x;
+    il = st.hdr->pinv.y;
+    sco = st.ps;
+  } else {
+    work = ctl->mode == PB_COMPACT;
+    append = ctl->append;
+    r0 = ctl->r0e - append;
+    rnew = ctl->rnew;
     if (append) {
       const dd inv = dd_div(dd_of(1.f), dd_of(ctl->rho0));
       ih = inv.h;
       il = inv.l;
     }
+    sco = ws.sm.red;
+  }
+  const int G = gridDim.x;
+  if (work) {
+    TilePipe<ST> P;
+    P.setup(ws, r0, kStagesB);
+    P.g[0] = (const unsigned char*)ws.ebuf;
+    P.vb[0] = 8;
+    P.base = smem;
+    unsigned char* sp = smem + (size_t)kStagesB * P.stage_sz;
+    P.bars = reinterpret_cast<uint64_t*>(sp);
+    sp += 8 * kStagesB;
+    float* coh = reinterpret_cast<float*>(sp);
+    float* col = coh + (kMaxCap + 8);
+    float* jh = col + (kMaxCap + 8);
+    float* jl = jh + kTile;
+    float* qbh = jl + kTile;                  // [(r0+1)][rnew] hi
+    float* qbl = qbh + (kMaxCap + 1) * kMaxR;
+
+    const int epc = (ST == ST_BF16) ? 8 : 4;
+    const int kpad = P.nch * epc;
+    for (int k = tid; k < kMaxCap + 8; k += kThreadsB) {
+      float h = 0.f, l = 0.f;
+      if (k < r0 && append && k < kpad) {
+        h = sco[k].x;
+        l = sco[k].y;
+      }
+      coh[k] = h;
+      col[k] = l;
+    }
     const int r0e = r0 + append;
-    if (mode == PB_COMPACT) {
-      for (int idx = tid; idx < r0e * rnew; idx += kThreads) {
+    if (!FLUSH) {
+      for (int idx = tid; idx < r0e * rnew; idx += kThreadsB) {
         const int k = idx / rnew, j = idx % rnew;
         const float2 q = ws.sm.QB[(size_t)j * (ws.cap + 1) + k];
         qbh[k * rnew + j] = q.x;
@@ -470,9 +607,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_b(Ws ws) {
     if (tid == 0) {
       for (int li = 0; li < min(my_tiles, kStagesB); ++li) P.issue(blockIdx.x + li * G, li);
     }
-    const int t = tid & 63, sub = tid >> 6;
-    unsigned char* gh = (unsigned char*)ws.Lh;
-    float* gl = ws.Ll;
+    const int t = tid >> 3, sub = tid & (kRowLanes - 1);
 
     for (int li = 0; li < my_tiles; ++li) {
       const int s = li % kStagesB;
@@ -486,80 +621,58 @@ __global__ void __launch_bounds__(kThreads) k_pass_b(Ws ws) {
         __syncthreads();
         break;
       }
-      {
-        if (append) {
-          part[sub * kTile + t] = row_dot_partial<ST>(P, s, t, sub, coh, col);
-          __syncthreads();
-          if (sub == 0) {
-            // j0 = (e - L0 s) / rho0: the second Gram-Schmidt pass, applied to the stored e
-            const float2 ev = reinterpret_cast<const float2*>(P.snap_c(s))[t];
-            const float ch = ev.x, cl = ev.y;
-            Acc d = part[t];
-            acc_add(d, part[kTile + t].h, part[kTile + t].l);
-            acc_add(d, part[2 * kTile + t].h, part[2 * kTile + t].l);
-            acc_add(d, part[3 * kTile + t].h, part[3 * kTile + t].l);
-            Acc e = Acc{ch, cl};
-            acc_add(e, -d.h, -d.l);
-            e = acc_norm(e);
-            Acc j = acc_zero();
-            acc_fma(j, e.h, e.l, ih, il);
-            j = acc_norm(j);
-            jh[t] = j.h;
-            jl[t] = j.l;
-            if (mode == PB_APPEND && t < rows) {
-              const size_t o = (size_t)(row0 + t) * ws.ldg + r0;
-              if constexpr (ST == ST_BF16) {
-                reinterpret_cast<__nv_bfloat16*>(gh)[o] = __float2bfloat16_rn(j.h);
-              } else {
-                reinterpret_cast<float*>(gh)[o] = j.h;
-                if constexpr (ST == ST_DD) gl[o] = j.l;
-              }
-            }
-          }
-          __syncthreads();
+      if (append) {
+        Acc d = row_dot_partial<ST, kRowLanes>(P, s, t, sub, coh, col);
+        d = group8_sum(d);
+        if (sub == 0) {
+          // j0 = (e - L0 s) / rho0: the second Gram-Schmidt pass, applied to the stored e
+          const float2 ev = reinterpret_cast<const float2*>(P.slot(s, 0))[t];
+          Acc e = Acc{ev.x, ev.y};
+          acc_add(e, -d.h, -d.l);
+          e = acc_norm(e);
+          Acc j = acc_zero();
+          acc_fma(j, e.h, e.l, ih, il);
+          j = acc_norm(j);
+          float h = j.h, l = j.l;
+          round_to_storage<ST>(h, l);
+          jh[t] = h;
+          jl[t] = l;
+          if (FLUSH && t < rows) store_elem_global<ST>(ws, (size_t)(row0 + t) * ws.ldg + r0, h, l);
         }
-        if (mode == PB_COMPACT) {
-          // out[t][j] = sum_k L0[t][k] QB[k][j] + j0_t QB[r0][j]
-          const unsigned char* ph = P.plane_h(s);
-          const unsigned char* pl = P.plane_l(s);
-          for (int idx = tid; idx < rows * rnew; idx += kThreads) {
-            const int tt = idx / rnew, j = idx % rnew;
-            Acc acc = acc_zero();
-            for (int k = 0; k < r0; ++k) {
-              float h, l;
-              load_elem<ST>(ph, pl, P.rs, tt, k, h, l);
-              acc_fma(acc, h, l, qbh[k * rnew + j], qbl[k * rnew + j]);
-            }
-            if (append) acc_fma(acc, jh[tt], jl[tt], qbh[r0 * rnew + j], qbl[r0 * rnew + j]);
-            acc = acc_norm(acc);
-            const size_t o = (size_t)(row0 + tt) * ws.ldg + j;
-            if constexpr (ST == ST_BF16) {
-              reinterpret_cast<__nv_bfloat16*>(gh)[o] = __float2bfloat16_rn(acc.h);
-            } else {
-              reinterpret_cast<float*>(gh)[o] = acc.h;
-              if constexpr (ST == ST_DD) gl[o] = acc.l;
-            }
+        __syncthreads();
+      }
+      if (!FLUSH) {
+        // out[t][j] = sum_k L0[t][k] QB[k][j] + j0_t QB[r0][j]
+        const unsigned char* ph = P.plane_h(s);
+        const unsigned char* pl = P.plane_l(s);
+        for (int idx = tid; idx < rows * rnew; idx += kThreadsB) {
+          const int tt = idx / rnew, j = idx % rnew;
+          Acc acc = acc_zero();
+          for (int k = 0; k < r0; ++k) {
+            float h, l;
+            load_elem<ST>(ph, pl, P.rs, tt, k, h, l);
+            acc_fma(acc, h, l, qbh[k * rnew + j], qbl[k * rnew + j]);
           }
+          if (append) acc_fma(acc, jh[tt], jl[tt], qbh[r0 * rnew + j], qbl[r0 * rnew + j]);
+          acc = acc_norm(acc);
+          store_elem_global<ST>(ws, (size_t)(row0 + tt) * ws.ldg + j, acc.h, acc.l);
         }
       }
       __syncthreads();
       if (tid == 0 && li + kStagesB < my_tiles) P.issue(blockIdx.x + (li + kStagesB) * G, s);
     }
   }
-
-  // ---- last CTA commits the new state
-  __shared__ unsigned ticket;
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) ticket = atomicAdd(&ctl->ticket_b, 1u);
-  __syncthreads();
-  if (ticket != (unsigned)(G - 1)) return;
-  if (tid == 0) {
+  if constexpr (FLUSH) {
+    __shared__ unsigned ticket;
     __threadfence();
-    ctl->cur = cur ^ 1;
-    ctl->cur_c = curc ^ 1;
-    ctl->eig_valid = 0;
-    ctl->ticket_b = 0u;
+    __syncthreads();
+    if (tid == 0) ticket = atomicAdd(&ctl->ticket_b, 1u);
+    __syncthreads();
+    if (ticket != (unsigned)(G - 1)) return;
+    if (tid == 0) {
+      st.hdr->pend = 0;
+      ctl->ticket_b = 0u;
+    }
   }
 }
 
@@ -583,8 +696,10 @@ __global__ void __launch_bounds__(kThreads) k_rollout(Ws ws, int kcols, void* ou
 
   TilePipe<ST> P;
   P.setup(ws, r0, kStagesR);
-  P.gc = CHECK ? (const unsigned char*)ws.xbuf : nullptr;
-  P.vc = T::vsz;
+  if (CHECK) {
+    P.g[0] = (const unsigned char*)ws.xbuf;
+    P.vb[0] = T::vsz;
+  }
   P.base = smem;
   unsigned char* p = smem + (size_t)kStagesR * P.stage_sz;
   P.bars = reinterpret_cast<uint64_t*>(p);
@@ -656,7 +771,7 @@ __global__ void __launch_bounds__(kThreads) k_rollout(Ws ws, int kcols, void* ou
             acc = acc_norm(acc);
             if constexpr (CHECK) {
               float fh, fl;
-              load_snap(reinterpret_cast<const typename T::stored_t*>(P.snap_c(s)), tt, fh, fl);
+              load_snap(reinterpret_cast<const typename T::stored_t*>(P.slot(s, 0)), tt, fh, fl);
               Acc d = acc;
               acc_add(d, -fh, -fl);
               d = acc_norm(d);
@@ -684,7 +799,7 @@ __global__ void __launch_bounds__(kThreads) k_rollout(Ws ws, int kcols, void* ou
           if (tt < rows) {
             if constexpr (CHECK) {
               float fh, fl;
-              load_snap(reinterpret_cast<const typename T::stored_t*>(P.snap_c(s)), tt, fh, fl);
+              load_snap(reinterpret_cast<const typename T::stored_t*>(P.slot(s, 0)), tt, fh, fl);
               Acc d = acc;
               acc_add(d, -fh, -fl);
               d = acc_norm(d);
@@ -793,13 +908,14 @@ __global__ void __launch_bounds__(kThreads) k_first(Ws ws) {
 // ---------------------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------------------
+static int stage_of(int prec, int cap) {
+  return prec == ST_DD ? stage_bytes<ST_DD>(cap) : prec == ST_F32 ? stage_bytes<ST_F32>(cap) : stage_bytes<ST_BF16>(cap);
+}
 static int smem_a(int prec, int cap) {
-  const int sb = prec == ST_DD ? stage_bytes<ST_DD>(cap) : prec == ST_F32 ? stage_bytes<ST_F32>(cap) : stage_bytes<ST_BF16>(cap);
-  return kStages * sb + 8 * kStages + 2 * (kMaxCap + 8) * 4 + 4 * kTile * 4 + kSubA * kTile * 8 + 2 * kThreadsA * 8;
+  return kStages * stage_of(prec, cap) + 8 * kStages + 4 * (kMaxCap + 8) * 4 + 2 * kTile * 16 + 2 * kHalfA * 8;
 }
 static int smem_b(int prec, int cap) {
-  const int sb = prec == ST_DD ? stage_bytes<ST_DD>(cap) : prec == ST_F32 ? stage_bytes<ST_F32>(cap) : stage_bytes<ST_BF16>(cap);
-  return kStagesB * sb + 8 * kStagesB + 2 * (kMaxCap + 8) * 4 + 2 * kTile * 4 + 4 * kTile * 8 +
+  return kStagesB * stage_of(prec, cap) + 8 * kStagesB + 2 * (kMaxCap + 8) * 4 + 2 * kTile * 4 +
          2 * (kMaxCap + 1) * kMaxR * 4;
 }
 static int smem_r(int prec, int cap) {
@@ -822,17 +938,20 @@ cudaError_t prepare_tall(const Ws& ws) {
   switch (ws.prec) {
     case ST_DD:
       if ((e = prep_attr(k_pass_a<ST_DD>, smem_a(ST_DD, cap)))) return e;
-      if ((e = prep_attr(k_pass_b<ST_DD>, smem_b(ST_DD, cap)))) return e;
+      if ((e = prep_attr(k_pass_b<ST_DD, false>, smem_b(ST_DD, cap)))) return e;
+      if ((e = prep_attr(k_pass_b<ST_DD, true>, smem_b(ST_DD, cap)))) return e;
       if ((e = prep_attr(k_rollout<ST_DD, false>, smem_r(ST_DD, cap)))) return e;
       return prep_attr(k_rollout<ST_DD, true>, smem_r(ST_DD, cap));
     case ST_F32:
       if ((e = prep_attr(k_pass_a<ST_F32>, smem_a(ST_F32, cap)))) return e;
-      if ((e = prep_attr(k_pass_b<ST_F32>, smem_b(ST_F32, cap)))) return e;
+      if ((e = prep_attr(k_pass_b<ST_F32, false>, smem_b(ST_F32, cap)))) return e;
+      if ((e = prep_attr(k_pass_b<ST_F32, true>, smem_b(ST_F32, cap)))) return e;
       if ((e = prep_attr(k_rollout<ST_F32, false>, smem_r(ST_F32, cap)))) return e;
       return prep_attr(k_rollout<ST_F32, true>, smem_r(ST_F32, cap));
     default:
       if ((e = prep_attr(k_pass_a<ST_BF16>, smem_a(ST_BF16, cap)))) return e;
-      if ((e = prep_attr(k_pass_b<ST_BF16>, smem_b(ST_BF16, cap)))) return e;
+      if ((e = prep_attr(k_pass_b<ST_BF16, false>, smem_b(ST_BF16, cap)))) return e;
+      if ((e = prep_attr(k_pass_b<ST_BF16, true>, smem_b(ST_BF16, cap)))) return e;
       if ((e = prep_attr(k_rollout<ST_BF16, false>, smem_r(ST_BF16, cap)))) return e;
       return prep_attr(k_rollout<ST_BF16, true>, smem_r(ST_BF16, cap));
   }
@@ -853,20 +972,24 @@ cudaError_t launch_pass_a(const Ws& ws, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_pass_b(const Ws& ws, cudaStream_t s) {
+template <bool FLUSH>
+static cudaError_t pass_b_launch(const Ws& ws, cudaStream_t s) {
   const int sm = smem_b(ws.prec, ws.cap);
   switch (ws.prec) {
     case ST_DD:
-      k_pass_b<ST_DD><<<ws.gridA, kThreads, sm, s>>>(ws);
+      k_pass_b<ST_DD, FLUSH><<<ws.gridA, kThreadsB, sm, s>>>(ws);
       break;
     case ST_F32:
-      k_pass_b<ST_F32><<<ws.gridA, kThreads, sm, s>>>(ws);
+      k_pass_b<ST_F32, FLUSH><<<ws.gridA, kThreadsB, sm, s>>>(ws);
       break;
     default:
-      k_pass_b<ST_BF16><<<ws.gridA, kThreads, sm, s>>>(ws);
+      k_pass_b<ST_BF16, FLUSH><<<ws.gridA, kThreadsB, sm, s>>>(ws);
   }
   return cudaGetLastError();
 }
+
+cudaError_t launch_pass_b(const Ws& ws, cudaStream_t s) { return pass_b_launch<false>(ws, s); }
+cudaError_t launch_flush(const Ws& ws, cudaStream_t s) { return pass_b_launch<true>(ws, s); }
 
 cudaError_t launch_first(const Ws& ws, cudaStream_t s) {
   const int grid = 64;  // the partial buffer always holds at least 64 rows
