@@ -212,16 +212,28 @@ __device__ __forceinline__ void store_elem_smem(unsigned char* ph, unsigned char
 template <int ST, int NSUB>
 __device__ __forceinline__ Acc row_dot_partial(const TilePipe<ST>& P, int s, int t, int sub, const float* coh,
                                                const float* col) {
+  constexpr int E = (ST == ST_BF16) ? 8 : 4;  // elements per 16-byte chunk
   Acc acc = acc_zero();
   const unsigned char* ph = P.plane_h(s);
   const unsigned char* pl = P.plane_l(s);
   for (int q = sub; q < P.nch; q += NSUB) {
-    float h[8], l[8];
-    const int e = load_chunk<ST>(ph, pl, P.rs, t, q, h, l);
+    float h[8], l[8], ch[8], cl[8];
+    load_chunk<ST>(ph, pl, P.rs, t, q, h, l);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      if (i < e) acc_fma(acc, h[i], l[i], coh[q * e + i], col[q * e + i]);
+    for (int i = 0; i < E; i += 4) {
+      const float4 a = *reinterpret_cast<const float4*>(coh + q * E + i);
+      const float4 b = *reinterpret_cast<const float4*>(col + q * E + i);
+      ch[i] = a.x;
+      ch[i + 1] = a.y;
+      ch[i + 2] = a.z;
+      ch[i + 3] = a.w;
+      cl[i] = b.x;
+      cl[i + 1] = b.y;
+      cl[i + 2] = b.z;
+      cl[i + 3] = b.w;
     }
+#pragma unroll
+    for (int i = 0; i < E; ++i) acc_fma(acc, h[i], l[i], ch[i], cl[i]);
   }
   return acc;
 }
@@ -266,6 +278,14 @@ __device__ __forceinline__ Acc group4_acc_sum(Acc a) {
   return a;
 }
 
+// stage memory of pass A, large enough to hold the column accumulators afterwards
+template <int ST>
+__host__ __device__ inline size_t pass_a_region(int stage_sz) {
+  constexpr int kE = (ST == ST_BF16) ? 8 : 4;
+  const size_t a = (size_t)kStages * stage_sz, b = (size_t)2 * kHalfA * kE * sizeof(Acc);
+  return a > b ? a : b;
+}
+
 template <int ST>
 __global__ void __launch_bounds__(kThreadsA) k_pass_a(Ws ws) {
   using T = Traits<ST>;
@@ -291,9 +311,10 @@ __global__ void __launch_bounds__(kThreadsA) k_pass_a(Ws ws) {
     P.vb[2] = 8;
   }
 
-  // shared layout: stages | bars | a (hi, lo) | s_prev (hi, lo) | 2 slots of (e, x) | accumulators
+  // shared layout: stages (reused for the column accumulators at the end) | bars |
+  // a (hi, lo) | s_prev (hi, lo) | 2 slots of (e, x)
   P.base = smem;
-  unsigned char* sp = smem + (size_t)kStages * P.stage_sz;
+  unsigned char* sp = smem + pass_a_region<ST>(P.stage_sz);
   P.bars = reinterpret_cast<uint64_t*>(sp);
   sp += 8 * kStages;
   float* coh = reinterpret_cast<float*>(sp);
@@ -301,7 +322,6 @@ __global__ void __launch_bounds__(kThreadsA) k_pass_a(Ws ws) {
   float* csh = col + (kMaxCap + 8);
   float* csl = csh + (kMaxCap + 8);
   float4* ex4 = reinterpret_cast<float4*>(csl + (kMaxCap + 8));  // [2][kTile] (eh, el, xh, xl)
-  Acc* colacc = reinterpret_cast<Acc*>(ex4 + 2 * kTile);          // [kHalfA][2]
   __shared__ int abort_flag;
 
   const int epc = (ST == ST_BF16) ? 8 : 4;
@@ -338,9 +358,12 @@ __global__ void __launch_bounds__(kThreadsA) k_pass_a(Ws ws) {
     for (int li = 0; li < min(my_tiles, kStages); ++li) P.issue(blockIdx.x + li * G, li);
   }
 
-  const int ncol = max(r0, 1);
-  const int G2 = kHalfA / ncol;
-  Acc S_acc = acc_zero(), Y_acc = acc_zero(), S2 = acc_zero(), Y2 = acc_zero();
+  constexpr int kE = (ST == ST_BF16) ? 8 : 4;  // columns per 16-byte chunk
+  const int nq = max(P.nch, 1);
+  const int G2 = kHalfA / nq;
+  Acc Sacc[kE], Yacc[kE];
+#pragma unroll
+  for (int i = 0; i < kE; ++i) Sacc[i] = Yacc[i] = acc_zero();
   Acc eta = acc_zero(), exa = acc_zero(), xi = acc_zero();
 
   if (producer) {
@@ -399,7 +422,8 @@ __global__ void __launch_bounds__(kThreadsA) k_pass_a(Ws ws) {
     // balance the empty barriers the consumers arrive on for the last two tiles
     for (int li = max(my_tiles, 2); li < my_tiles + 2; ++li) named_sync(3 + (li & 1), kThreadsA);
   } else {
-    const int kcol = htid % ncol, grp = htid / ncol;
+    // consumer thread: chunk cq (E adjacent columns) of rows grp, grp + G2, ...
+    const int cq = htid % nq, grp = htid / nq;
     const bool col_active = (r0 > 0) && grp < G2;
     for (int li = 0; li < my_tiles; ++li) {
       const int s = li % kStages, slot = li & 1;
@@ -412,31 +436,21 @@ __global__ void __launch_bounds__(kThreadsA) k_pass_a(Ws ws) {
         const unsigned char* ph = P.plane_h(s);
         const unsigned char* pl = P.plane_l(s);
         const float4* ex = ex4 + slot * kTile;
-        int tt = grp;
-        for (; tt + G2 < rows; tt += 2 * G2) {  // two rows per step: four independent chains
-          float h0, l0, h1, l1;
-          load_elem<ST>(ph, pl, P.rs, tt, kcol, h0, l0);
-          load_elem<ST>(ph, pl, P.rs, tt + G2, kcol, h1, l1);
-          const float4 v0 = ex[tt], v1 = ex[tt + G2];
-          acc_fma(S_acc, h0, l0, v0.x, v0.y);
-          acc_fma(Y_acc, h0, l0, v0.z, v0.w);
-          acc_fma(S2, h1, l1, v1.x, v1.y);
-          acc_fma(Y2, h1, l1, v1.z, v1.w);
-        }
-        if (tt < rows) {
-          float h0, l0;
-          load_elem<ST>(ph, pl, P.rs, tt, kcol, h0, l0);
-          const float4 v0 = ex[tt];
-          acc_fma(S_acc, h0, l0, v0.x, v0.y);
-          acc_fma(Y_acc, h0, l0, v0.z, v0.w);
+        for (int tt = grp; tt < rows; tt += G2) {
+          float h[8], l[8];
+          load_chunk<ST>(ph, pl, P.rs, tt, cq, h, l);
+          const float4 v = ex[tt];
+#pragma unroll
+          for (int i = 0; i < kE; ++i) {
+            acc_fma(Sacc[i], h[i], l[i], v.x, v.y);
+            acc_fma(Yacc[i], h[i], l[i], v.z, v.w);
+          }
         }
       }
       // the consumers are the last readers of the stage: refill it, free the slot
       if (htid == 0 && !abort_flag && li + kStages < my_tiles) P.issue(blockIdx.x + (li + kStages) * G, s);
       named_arrive(3 + slot, kThreadsA);
     }
-    acc_add(S_acc, S2.h, S2.l);
-    acc_add(Y_acc, Y2.h, Y2.l);
   }
   __syncthreads();
   if (abort_flag && tid == 0) mbar_drain(P.bars, kStages, 0, my_tiles);
@@ -444,9 +458,17 @@ __global__ void __launch_bounds__(kThreadsA) k_pass_a(Ws ws) {
   // ---- per-CTA partials
   const int stride = 2 * ws.cap + 3;
   float2* mypart = ws.part + (size_t)blockIdx.x * stride;
+  // consumer accumulators -> stage memory (idle now): colacc[g][k] for S then Y
+  Acc* cacc = reinterpret_cast<Acc*>(smem);
+  const int ncols_box = nq * kE;
   if (!producer) {
-    colacc[2 * htid] = S_acc;
-    colacc[2 * htid + 1] = Y_acc;
+    const int cq = htid % nq, grp = htid / nq;
+    if (grp < G2)
+#pragma unroll
+      for (int i = 0; i < kE; ++i) {
+        cacc[(size_t)grp * ncols_box + cq * kE + i] = Sacc[i];
+        cacc[(size_t)(G2 + grp) * ncols_box + cq * kE + i] = Yacc[i];
+      }
   }
   // scalar sums live in the sub == 0 lanes of the producer warps (others hold zeros)
 #pragma unroll
@@ -465,7 +487,7 @@ __global__ void __launch_bounds__(kThreadsA) k_pass_a(Ws ws) {
   if (tid < r0) {
     Acc sS = acc_zero(), sY = acc_zero();
     for (int g = 0; g < G2; ++g) {
-      const Acc a1 = colacc[2 * (g * ncol + tid)], a2 = colacc[2 * (g * ncol + tid) + 1];
+      const Acc a1 = cacc[(size_t)g * ncols_box + tid], a2 = cacc[(size_t)(G2 + g) * ncols_box + tid];
       acc_add(sS, a1.h, a1.l);
       acc_add(sY, a2.h, a2.l);
     }
@@ -531,6 +553,7 @@ constexpr int kThreadsB = 512;
 template <int ST, bool FLUSH>
 __global__ void __launch_bounds__(kThreadsB) k_pass_b(Ws ws) {
   using T = Traits<ST>;
+  constexpr int epcC = (ST == ST_BF16) ? 8 : 4;  // basis columns per 16-byte chunk
   extern __shared__ __align__(1024) unsigned char smem[];
   Ctl* ctl = ws.ctl;
   const int tid = threadIdx.x;
@@ -573,8 +596,8 @@ __global__ void __launch_bounds__(kThreadsB) k_pass_b(Ws ws) {
     float* col = coh + (kMaxCap + 8);
     float* jh = col + (kMaxCap + 8);
     float* jl = jh + kTile;
-    float* qbh = jl + kTile;                  // [(r0+1)][rnew] hi
-    float* qbl = qbh + (kMaxCap + 1) * kMaxR;
+    float* qbh = jl + kTile;                  // [(box columns + 1)][rnew padded] hi
+    float* qbl = qbh + (kMaxCap + 9) * kMaxR;
 
     const int epc = (ST == ST_BF16) ? 8 : 4;
     const int kpad = P.nch * epc;
@@ -588,12 +611,18 @@ __global__ void __launch_bounds__(kThreadsB) k_pass_b(Ws ws) {
       col[k] = l;
     }
     const int r0e = r0 + append;
+    const int rnp = (rnew + 3) & ~3;  // output columns padded to whole float4s (zeros)
+    const int kch = P.nch * epc;      // basis columns covered by the box (zero rows of QB beyond r0)
     if (!FLUSH) {
-      for (int idx = tid; idx < r0e * rnew; idx += kThreadsB) {
-        const int k = idx / rnew, j = idx % rnew;
-        const float2 q = ws.sm.QB[(size_t)j * (ws.cap + 1) + k];
-        qbh[k * rnew + j] = q.x;
-        qbl[k * rnew + j] = q.y;
+      for (int idx = tid; idx < (kch + 1) * rnp; idx += kThreadsB) {
+        const int k = idx / rnp, j = idx % rnp;
+        // row kch holds the coefficients of the new column j0 (QB row r0)
+        const int kk = k < kch ? k : r0;
+        float2 q = make_float2(0.f, 0.f);
+        if (j < rnew && ((k < kch && k < r0) || (k == kch && append)))
+          q = ws.sm.QB[(size_t)j * (ws.cap + 1) + kk];
+        qbh[k * rnp + j] = q.x;
+        qbl[k * rnp + j] = q.y;
       }
     }
     if (tid == 0) {
@@ -642,20 +671,43 @@ __global__ void __launch_bounds__(kThreadsB) k_pass_b(Ws ws) {
         __syncthreads();
       }
       if (!FLUSH) {
-        // out[t][j] = sum_k L0[t][k] QB[k][j] + j0_t QB[r0][j]
+        // out[t][j..j+3] = sum_k L0[t][k] QB[k][j..j+3] + j0_t QB[r0][j..j+3]; each thread
+        // one row and 4 adjacent output columns (4 independent accumulators)
         const unsigned char* ph = P.plane_h(s);
         const unsigned char* pl = P.plane_l(s);
-        for (int idx = tid; idx < rows * rnew; idx += kThreadsB) {
-          const int tt = idx / rnew, j = idx % rnew;
-          Acc acc = acc_zero();
-          for (int k = 0; k < r0; ++k) {
-            float h, l;
-            load_elem<ST>(ph, pl, P.rs, tt, k, h, l);
-            acc_fma(acc, h, l, qbh[k * rnew + j], qbl[k * rnew + j]);
+        const int nqo = rnp >> 2;
+        for (int idx = tid; idx < rows * nqo; idx += kThreadsB) {
+          const int tt = idx / nqo, j0c = (idx % nqo) * 4;
+          Acc acc[4] = {acc_zero(), acc_zero(), acc_zero(), acc_zero()};
+          for (int q = 0; q < P.nch; ++q) {
+            float h[8], l[8];
+            load_chunk<ST>(ph, pl, P.rs, tt, q, h, l);
+#pragma unroll
+            for (int i = 0; i < epcC; ++i) {
+              const int k = q * epcC + i;
+              const float4 bh = *reinterpret_cast<const float4*>(qbh + k * rnp + j0c);
+              const float4 bl = *reinterpret_cast<const float4*>(qbl + k * rnp + j0c);
+              acc_fma(acc[0], h[i], l[i], bh.x, bl.x);
+              acc_fma(acc[1], h[i], l[i], bh.y, bl.y);
+              acc_fma(acc[2], h[i], l[i], bh.z, bl.z);
+              acc_fma(acc[3], h[i], l[i], bh.w, bl.w);
+            }
           }
-          if (append) acc_fma(acc, jh[tt], jl[tt], qbh[r0 * rnew + j], qbl[r0 * rnew + j]);
-          acc = acc_norm(acc);
-          store_elem_global<ST>(ws, (size_t)(row0 + tt) * ws.ldg + j, acc.h, acc.l);
+          if (append) {
+            const float4 bh = *reinterpret_cast<const float4*>(qbh + kch * rnp + j0c);
+            const float4 bl = *reinterpret_cast<const float4*>(qbl + kch * rnp + j0c);
+            acc_fma(acc[0], jh[tt], jl[tt], bh.x, bl.x);
+            acc_fma(acc[1], jh[tt], jl[tt], bh.y, bl.y);
+            acc_fma(acc[2], jh[tt], jl[tt], bh.z, bl.z);
+            acc_fma(acc[3], jh[tt], jl[tt], bh.w, bl.w);
+          }
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            if (j0c + c < rnew) {
+              const Acc a = acc_norm(acc[c]);
+              store_elem_global<ST>(ws, (size_t)(row0 + tt) * ws.ldg + j0c + c, a.h, a.l);
+            }
+          }
         }
       }
       __syncthreads();
@@ -912,11 +964,14 @@ static int stage_of(int prec, int cap) {
   return prec == ST_DD ? stage_bytes<ST_DD>(cap) : prec == ST_F32 ? stage_bytes<ST_F32>(cap) : stage_bytes<ST_BF16>(cap);
 }
 static int smem_a(int prec, int cap) {
-  return kStages * stage_of(prec, cap) + 8 * kStages + 4 * (kMaxCap + 8) * 4 + 2 * kTile * 16 + 2 * kHalfA * 8;
+  const size_t region = prec == ST_DD    ? pass_a_region<ST_DD>(stage_of(prec, cap))
+                        : prec == ST_F32 ? pass_a_region<ST_F32>(stage_of(prec, cap))
+                                         : pass_a_region<ST_BF16>(stage_of(prec, cap));
+  return (int)region + 8 * kStages + 4 * (kMaxCap + 8) * 4 + 2 * kTile * 16;
 }
 static int smem_b(int prec, int cap) {
   return kStagesB * stage_of(prec, cap) + 8 * kStagesB + 2 * (kMaxCap + 8) * 4 + 2 * kTile * 4 +
-         2 * (kMaxCap + 1) * kMaxR * 4;
+         2 * (kMaxCap + 9) * kMaxR * 4;
 }
 static int smem_r(int prec, int cap) {
   const int sb = prec == ST_DD ? stage_bytes<ST_DD>(cap) : prec == ST_F32 ? stage_bytes<ST_F32>(cap) : stage_bytes<ST_BF16>(cap);
