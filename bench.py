@@ -401,6 +401,31 @@ def run_ours(args) -> None:
         dist.destroy_process_group()
 
 
+def run_profile_case(args) -> None:
+    """A short untimed run of the bench workload's kernels for profiler captures: the wake
+    stream at full size, `--profile-updates` updates (rank 40 is reached after ~40), one
+    BLOCK-state rollout and one check.  Prints a one-line summary."""
+    import torch
+
+    import paper_2311_18715_gb300 as pkg
+    from synth import WakeField
+
+    dev = torch.device("cuda", 0)
+    pkg.build()
+    gen = WakeField(NX, NY, sigma=SIGMA, seed=0)
+    m = args.profile_updates
+    Xd = torch.from_numpy(np.stack([gen.snapshot(k) for k in range(m + 2)])).to(dev)
+    model = pkg.OnlineDMD(N, R_MAX, prec="fp64", slack=SLACK, trunc_tol=TAU)
+    for k in range(m):
+        model.update(Xd[k])
+    out = model.predict([float(m + h) for h in range(BLOCK)])
+    err = model.check(float(m), Xd[m])
+    model.sync()
+    print(json.dumps({"profile_case": WORKLOAD, "updates": m, "rank": model.rank,
+                      "check_rel_err": err[0], "out_norm": float(out.norm())}), flush=True)
+    model.close()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -409,7 +434,13 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-updates", type=int, default=60, help="oracle updates timed for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="untimed short run of the same kernels, for ncu captures")
+    ap.add_argument("--profile-updates", type=int, default=64)
     args = ap.parse_args()
+    if args.profile_case:
+        run_profile_case(args)
+        return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
