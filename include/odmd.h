@@ -162,6 +162,30 @@ odmd_status odmd_profile_read(odmd_t h, double* ms_total, int64_t* launches, int
 /* Release the handle (synchronises first).  The workspace is the caller's again. */
 odmd_status odmd_destroy(odmd_t h);
 
+/* Credibility check of a prediction the caller already holds, allocating nothing.
+ * The paper has no counterpart: this is a convenience beside odmd_check for callers that
+ * must not allocate device memory -- for example a callback inside a host solver's time
+ * loop whose memory belongs to the solver's own pool allocator, a process under a hard
+ * device-memory cap, or code that must avoid the device-wide synchronisation that
+ * cudaMalloc/cudaFree can cause.  It needs no handle and no workspace.
+ *
+ *   rel_err = ||pred - x_fom|| / ||x_fom||  (0 if both are zero, +inf if only x_fom is),
+ *   pass    = rel_err <= tol  (tol <= 0 selects 1e-5).
+ *
+ * pred_dev, x_fom_dev: device arrays of n doubles on the current device, read only.
+ * n: 1 <= n <= 33,554,432; larger n is rejected with ODMD_ERR_ARG (the scratch is a fixed
+ * 64 KiB device array inside the library, one partial-sum slot per 8192 elements).
+ * stream: cudaStream_t as void* (NULL = legacy default stream); the call synchronises it.
+ * rel_err, pass: host outputs (either may be NULL).  Sums are FP64.  Errors: ODMD_ERR_ARG,
+ * ODMD_ERR_CUDA, ODMD_ERR_NUMERIC (non-finite input); the message is odmd_last_error(NULL).
+ *
+ * The first call on each device looks up the scratch array's device address with that
+ * device current; make that first call before any stream capture on the device.  Every
+ * call in the process shares the one array on a device: calls whose GPU work overlaps
+ * (different streams or threads at the same time) race and may return wrong results. */
+odmd_status odmd_check_noalloc(const double* pred_dev, const double* x_fom_dev, int64_t n, double tol,
+                               void* stream, double* rel_err, int32_t* pass);
+
 /* Message describing the last error on this handle (or the last global error if h is
  * NULL).  The string lives until the next call on the same handle. */
 const char* odmd_last_error(odmd_t h);

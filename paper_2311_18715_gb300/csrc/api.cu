@@ -845,3 +845,7 @@ odmd_status odmd_destroy(odmd_t h) {
 const char* odmd_last_error(odmd_t h) { return h ? h->err.c_str() : g_err.c_str(); }
 
 }  // extern "C"
+
+namespace odmd {
+odmd_status report_global_error(odmd_status s, const std::string& msg) { return fail(nullptr, s, msg); }
+}  // namespace odmd

@@ -7,6 +7,9 @@
 // with Knuth's two-sum into a hi/lo accumulator.  Only O(r^2)..O(r^3) small solves run
 // in native FP64.
 #pragma once
+#include <string>
+
+#include "odmd.h"
 #include <cstdint>
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -318,5 +321,9 @@ cudaError_t launch_eig(const Ws& ws, cudaStream_t s);
 cudaError_t launch_coef(const Ws& ws, const double* t_host, int k, cudaStream_t s);  // k <= kRollK, t on the host
 cudaError_t launch_basis_coef(const Ws& ws, cudaStream_t s);
 cudaError_t launch_init(const Ws& ws, cudaStream_t s);
+
+// Record `msg` as the message of odmd_last_error(NULL) and return `s` (for entry points
+// that have no handle).
+odmd_status report_global_error(odmd_status s, const std::string& msg);
 
 }  // namespace odmd

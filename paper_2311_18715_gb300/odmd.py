@@ -157,3 +157,29 @@ class OnlineDMD:
             self.close()
         except Exception:
             pass
+
+
+def check_noalloc(pred: torch.Tensor, x_fom: torch.Tensor, tol: float = 0.0,
+                  stream: torch.cuda.Stream | None = None) -> tuple[float, bool]:
+    """Relative L2 credibility check of a prediction the caller already holds, through
+    odmd_check_noalloc: no handle, no workspace, and no device allocation in the library.
+
+    For callers that must not allocate device memory (a callback inside a solver's time
+    loop whose memory belongs to the solver's pool, a process under a device-memory cap).
+    pred and x_fom: contiguous float64 CUDA tensors of the same length (at most
+    33,554,432 elements).  Calls whose GPU work overlaps share one scratch array and race.
+    """
+    lib = load_library()
+    for name, t in (("pred", pred), ("x_fom", x_fom)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
+    if pred.numel() != x_fom.numel() or pred.device != x_fom.device:
+        raise ValueError("pred and x_fom must have the same length and device")
+    err = C.c_double()
+    ok = C.c_int32()
+    with torch.cuda.device(pred.device):
+        s = stream if stream is not None else torch.cuda.current_stream(pred.device)
+        check(lib, lib.odmd_check_noalloc(C.c_void_p(pred.data_ptr()), C.c_void_p(x_fom.data_ptr()),
+                                          pred.numel(), float(tol), C.c_void_p(s.cuda_stream),
+                                          C.byref(err), C.byref(ok)))
+    return float(err.value), bool(ok.value)
