@@ -168,6 +168,7 @@ void carve(Ws& ws, const Layout& L, unsigned char* base, const odmd_config& c, i
   ws.ldg = L.ldg;
   ws.prec = (int)c.prec;
   ws.gridA = gridA;
+  ws.stagesA = stages_a((int)c.prec, L.cap);
   ws.tau_h = (float)c.trunc_tol;
   ws.tau_l = (float)(c.trunc_tol - (double)ws.tau_h);
   ws.ctl = reinterpret_cast<Ctl*>(base + L.off_ctl);
@@ -539,6 +540,12 @@ odmd_status odmd_create(const odmd_config* cfg, void* workspace_dev, size_t byte
   if (gridA > kPartRows) gridA = kPartRows;
   if (gridA < 1) gridA = 1;
   carve(h->ws, L, reinterpret_cast<unsigned char*>(workspace_dev), *cfg, gridA);
+  {
+    const int64_t tiles32 = (cfg->n + 31) / 32;
+    int g = (int)(tiles32 < sms ? tiles32 : sms);
+    if (g > kPartRows) g = kPartRows;
+    h->ws.gridPA = g < 1 ? 1 : g;
+  }
   if (e == cudaSuccess) e = prepare_tall(h->ws);
   if (e == cudaSuccess) e = prepare_small(h->ws);
   if (e == cudaSuccess) e = cudaMemsetAsync(workspace_dev, 0, L.total, h->stream);

@@ -20,6 +20,7 @@ namespace odmd {
 constexpr int kThreads = 256;      // threads of every tall-pass CTA
 constexpr int kTile = 64;          // rows per tile of a tall pass
 constexpr int kStages = 4;         // TMA pipeline depth of a tall pass
+
 constexpr int kMaxR = 64;          // largest r_max
 constexpr int kMaxSlack = 32;      // largest slack
 constexpr int kMaxCap = kMaxR + kMaxSlack;  // largest number of basis columns r0
@@ -143,6 +144,8 @@ struct Ws {
   int64_t n;        // rows
   int64_t npad;     // rows rounded up to kTile
   int rmax, cap, ldg, prec, gridA;
+  int stagesA;      // TMA pipeline depth of pass A (as many stages as shared memory holds)
+  int gridPA;       // pass A grid: one CTA per SM, at most one per 32-row tile
   float tau_h, tau_l;  // truncation tolerance as a double-float
   Ctl* ctl;
   void* Lh;         // hi plane (float) / bf16 plane
@@ -196,6 +199,95 @@ __device__ __forceinline__ Acc acc_norm(Acc A) {
   float s = __fadd_rn(A.h, A.l);
   float e = __fsub_rn(A.l, __fsub_rn(s, A.h));
   return Acc{s, e};
+}
+
+// ---- packed pairs: two floats in one 64-bit register pair, operated on by the FP32x2
+// instructions of sm_100 and later (one issue slot for two lanes of work).  The double-float
+// accumulate below performs, lane by lane, exactly the operations of acc_fma, so a packed
+// and a scalar accumulation give bitwise equal results.
+typedef unsigned long long f2x;
+__device__ __forceinline__ f2x f2x_pack(float a, float b) {
+  f2x r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2x_unpack(f2x v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+#ifndef ODMD_SCALAR_PAIRS
+__device__ __forceinline__ f2x add2(f2x a, f2x b) {
+  f2x d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2x sub2(f2x a, f2x b) {
+  f2x d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2x mul2(f2x a, f2x b) {
+  f2x d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2x fma2(f2x a, f2x b, f2x c) {
+  f2x d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+#else
+// the same operations lane by lane on scalar FP32 instructions
+__device__ __forceinline__ f2x add2(f2x a, f2x b) {
+  float a0, a1, b0, b1;
+  f2x_unpack(a, a0, a1);
+  f2x_unpack(b, b0, b1);
+  return f2x_pack(__fadd_rn(a0, b0), __fadd_rn(a1, b1));
+}
+__device__ __forceinline__ f2x sub2(f2x a, f2x b) {
+  float a0, a1, b0, b1;
+  f2x_unpack(a, a0, a1);
+  f2x_unpack(b, b0, b1);
+  return f2x_pack(__fsub_rn(a0, b0), __fsub_rn(a1, b1));
+}
+__device__ __forceinline__ f2x mul2(f2x a, f2x b) {
+  float a0, a1, b0, b1;
+  f2x_unpack(a, a0, a1);
+  f2x_unpack(b, b0, b1);
+  return f2x_pack(__fmul_rn(a0, b0), __fmul_rn(a1, b1));
+}
+__device__ __forceinline__ f2x fma2(f2x a, f2x b, f2x c) {
+  float a0, a1, b0, b1, c0, c1;
+  f2x_unpack(a, a0, a1);
+  f2x_unpack(b, b0, b1);
+  f2x_unpack(c, c0, c1);
+  return f2x_pack(__fmaf_rn(a0, b0, c0), __fmaf_rn(a1, b1, c1));
+}
+#endif
+
+struct Acc2 {
+  f2x h, l;
+};
+__device__ __forceinline__ Acc2 acc2_zero() { return Acc2{0ull, 0ull}; }
+
+// A += (xh + xl) * (yh + yl) in both lanes, given nyh = -yh: the product's rounding error
+// (xh*yh - p) + xh*yl + xl*yh is formed with FMAs and the high part p is added with
+// two-sum, the same steps as acc_fma.
+__device__ __forceinline__ void acc2_fma(Acc2& A, f2x xh, f2x xl, f2x yh, f2x nyh, f2x yl) {
+  const f2x np = mul2(xh, nyh);     // -p
+  f2x pe = fma2(xh, yh, np);        // xh*yh - p
+  pe = fma2(xh, yl, pe);
+  pe = fma2(xl, yh, pe);
+  const f2x s = sub2(A.h, np);      // two-sum of A.h and p
+  const f2x bb = sub2(s, A.h);
+  const f2x e = sub2(sub2(A.h, sub2(s, bb)), add2(np, bb));
+  A.h = s;
+  A.l = add2(A.l, add2(e, pe));
+}
+
+// the two lanes of A as scalar accumulators
+__device__ __forceinline__ void acc2_split(Acc2 A, Acc& a0, Acc& a1) {
+  f2x_unpack(A.h, a0.h, a1.h);
+  f2x_unpack(A.l, a0.l, a1.l);
 }
 
 __device__ __forceinline__ void split_double(double x, float& h, float& l) {
@@ -284,6 +376,22 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
+// The same copy with an L2 eviction-priority hint (a policy from l2_evict_first_policy):
+// data streamed once should not push reused lines (code, small state) out of L2.
+__device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                              uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
+      : "memory");
+}
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
 // ------------------------------------------------------------------ warp helpers
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
@@ -315,6 +423,7 @@ cudaError_t launch_rollout(const Ws& ws, const double* coef_src, int kcols, void
                            int coef_mode, cudaStream_t s);
 cudaError_t launch_check(const Ws& ws, cudaStream_t s);
 int tall_smem_bytes(int prec);
+int stages_a(int prec, int cap);  // pass A pipeline depth for this storage format and cap
 // small.cu
 cudaError_t launch_small(const Ws& ws, cudaStream_t s);
 cudaError_t launch_eig(const Ws& ws, cudaStream_t s);

@@ -8,12 +8,15 @@
 // Each CTA is persistent over row tiles of kTile rows.  A tile of the basis (only the
 // r0 active columns of each row) and the matching snapshot rows are brought into
 // shared memory by TMA bulk copies (one per row and plane) completing on an mbarrier,
-// kStages tiles in flight.  Shared rows are padded to an odd number of 16-byte chunks so
-// that both the row-wise float4 reads (dot products along a row) and the column-wise
-// reads (sums down a column) are free of bank conflicts.
+// several tiles in flight (pass A: as many as shared memory holds).  Shared rows are
+// padded to an odd number of 16-byte chunks so that both the row-wise vector reads (dot
+// products along a row) and the column-wise reads (sums down a column) are free of bank
+// conflicts.
 //
 // Reductions are deterministic: per-CTA partials in a fixed order, then the last CTA to
 // finish (atomic ticket) sums them in CTA order.
+#include <type_traits>
+
 #include "dd.cuh"
 #include "odmd_internal.cuh"
 
@@ -249,47 +252,200 @@ __device__ __forceinline__ Acc group8_sum(Acc a) {
   return a;
 }
 
-// ---------------------------------------------------------------------------------------
-// pass A (512 threads, warp-specialised): the pending column of the previous update (if
-// any) is formed row by row from its stored residual, written to L0 and used at once; then
-//   e = c - L0 a, s = L0^T e, y = L0^T x, ||e||^2, e.x, ||x||^2.
-// Warps 0-7 (producers) form the row dots of tile i+1 (4 lanes per row) while warps 8-15
-// (consumers) sum down the columns of tile i; e and x of a tile pass through one of two
-// shared slots, handed over with named barriers (full: 1,2; empty: 3,4).
-// ---------------------------------------------------------------------------------------
-constexpr int kThreadsA = 512;
-constexpr int kHalfA = kThreadsA / 2;
-constexpr int kRowLanesA = kHalfA / kTile;  // 4
-
-__device__ __forceinline__ void named_sync(int id, int count) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
-}
-__device__ __forceinline__ void named_arrive(int id, int count) {
-  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ Acc group4_acc_sum(Acc a) {
-#pragma unroll
-  for (int o = 1; o < 4; o <<= 1) {
-    const float h = __shfl_xor_sync(0xffffffffu, a.h, o);
-    const float l = __shfl_xor_sync(0xffffffffu, a.l, o);
-    acc_add(a, h, l);
-  }
-  return a;
-}
-
-// stage memory of pass A, large enough to hold the column accumulators afterwards
+// The elements of chunk q of smem row `row` as packed pairs (2 pairs for 4-byte elements,
+// 4 for bf16); lo pairs are zero unless the basis is double-float.
 template <int ST>
-__host__ __device__ inline size_t pass_a_region(int stage_sz) {
-  constexpr int kE = (ST == ST_BF16) ? 8 : 4;
-  const size_t a = (size_t)kStages * stage_sz, b = (size_t)2 * kHalfA * kE * sizeof(Acc);
+__device__ __forceinline__ void load_chunk2(const unsigned char* plane_h, const unsigned char* plane_l, int rs,
+                                            int row, int q, f2x* H, f2x* L) {
+  if constexpr (ST == ST_BF16) {
+    const uint4 v = *reinterpret_cast<const uint4*>(plane_h + row * rs + q * 16);
+    const __nv_bfloat162* b = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float2 f = __bfloat1622float2(b[i]);
+      H[i] = f2x_pack(f.x, f.y);
+      L[i] = 0ull;
+    }
+  } else {
+    const ulonglong2 vh = *reinterpret_cast<const ulonglong2*>(plane_h + row * rs + q * 16);
+    H[0] = vh.x;
+    H[1] = vh.y;
+    if constexpr (ST == ST_DD) {
+      const ulonglong2 vl = *reinterpret_cast<const ulonglong2*>(plane_l + row * rs + q * 16);
+      L[0] = vl.x;
+      L[1] = vl.y;
+    } else {
+      L[0] = L[1] = 0ull;
+    }
+  }
+}
+
+// acc2_fma without the xl*yh term when the basis has no lo part
+template <int ST>
+__device__ __forceinline__ void acc2_fma_basis(Acc2& A, f2x xh, f2x xl, f2x yh, f2x nyh, f2x yl) {
+  if constexpr (ST == ST_DD) {
+    acc2_fma(A, xh, xl, yh, nyh, yl);
+  } else {
+    const f2x np = mul2(xh, nyh);
+    f2x pe = fma2(xh, yh, np);
+    pe = fma2(xh, yl, pe);
+    const f2x s = sub2(A.h, np);
+    const f2x bb = sub2(s, A.h);
+    const f2x e = sub2(sub2(A.h, sub2(s, bb)), add2(np, bb));
+    A.h = s;
+    A.l = add2(A.l, add2(e, pe));
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// pass A: the pending column of the previous update (if any) is formed row by row from
+// its stored residual, written to L0 and used at once; then
+//   e = c - L0 a, s = L0^T e, y = L0^T x, ||e||^2, e.x, ||x||^2.
+// Each CTA streams its 32-row tiles (whole rows of both basis planes, one bulk copy per
+// plane) through a ring of shared stages; the warp that finishes with a stage refills it
+// with the tile ns places ahead.  A warp takes whole tiles: lane i owns row i for the row
+// dots, the pending column and the residual (no exchange between lanes; c, x and the
+// stored residual of the row come in by plain loads issued before the tile's wait), then
+// the lanes switch to owning 16-byte column chunks, 16 lanes per row and two rows at a
+// time, and add the tile into column sums that stay in registers for the whole launch.
+// Column sums meet across lanes, warps and CTAs once, at the end.  The double-float
+// arithmetic runs on packed FP32x2 instructions; the row dots are unrolled for the
+// tile's chunk count.
+// ---------------------------------------------------------------------------------------
+constexpr int kRowsA = 32;                      // rows per tile (one warp)
+constexpr int kWarpsA = 8;                      // compute warps per CTA
+constexpr int kThreadsA = 32 * kWarpsA;
+#ifndef ODMD_PASS_A_MAX_STAGES
+#define ODMD_PASS_A_MAX_STAGES 16
+#endif
+constexpr int kMaxStagesA = ODMD_PASS_A_MAX_STAGES;
+constexpr int kBarBytesA = (8 * kMaxStagesA + 15) / 16 * 16;  // one barrier per stage
+static_assert((kMaxCap + 8) * 4 % 16 == 0, "pass A coefficient arrays must stay 16-byte aligned");
+constexpr int kSmemBudget = 227 * 1024 - 2048;  // dynamic shared memory per CTA, less the static part
+constexpr int kCo = 128;  // length of a coefficient array: zero past r0, so chunk groups may overrun
+
+// one stage: 32 whole rows (the full row pitch) of each basis plane
+template <int ST>
+__host__ __device__ inline int stage_bytes_a(int cap) {
+  using T = Traits<ST>;
+  return kRowsA * 16 * box_chunks(cap, T::esz) * T::planes;
+}
+
+// shared memory of pass A besides its stages: barriers, coefficients, per-warp e/x slots
+__host__ __device__ inline int smem_a_fixed() { return kBarBytesA + 6 * kCo * 4 + kWarpsA * kRowsA * 3 * 16; }
+
+// the column sums of every warp meet in the stage memory at the end
+template <int ST>
+__host__ __device__ inline size_t pass_a_region(int stage_sz, int nstages) {
+  const size_t a = (size_t)nstages * stage_sz, b = (size_t)kWarpsA * 2 * kCo * sizeof(Acc);
   return a > b ? a : b;
 }
 
+// The rows of a 32-row tile are contiguous in both basis planes (row pitch ldg), so a tile
+// is one 1-D bulk copy per plane: two TMA operations per tile, each several KB.
 template <int ST>
-__global__ void __launch_bounds__(kThreadsA) k_pass_a(Ws ws) {
+struct PipeA {
+  using T = Traits<ST>;
+  unsigned char* base;
+  uint64_t* full;
+  int stage_sz, rs, nch, plane_off;
+  const unsigned char* gh;  // hi (or only) plane
+  const unsigned char* gl;  // lo plane (double-float)
+  uint64_t policy;          // L2 evict-first: the planes are streamed once per pass
+  __device__ unsigned char* plane_h(int s) const { return base + (size_t)s * stage_sz; }
+  __device__ unsigned char* plane_l(int s) const { return plane_h(s) + plane_off; }
+  // the copies of tile `tile` into stage s (one thread)
+  __device__ void issue(int tile, int s) const {
+    const size_t off = (size_t)tile * kRowsA * rs;
+    mbar_arrive_expect_tx(&full[s], (uint32_t)(kRowsA * rs * T::planes));
+    bulk_g2s_hint(plane_h(s), gh + off, kRowsA * rs, &full[s], policy);
+    if (T::planes == 2) bulk_g2s_hint(plane_l(s), gl + off, kRowsA * rs, &full[s], policy);
+  }
+};
+
+// Wait (at most 2 s) until the shared tile index *slot equals k.
+__device__ __forceinline__ bool wait_issued(const int* slot, int k, int* status) {
+  const volatile int* v = slot;
+  if (*v == k) return true;
+  const uint64_t t0 = global_ns();
+  while (*v != k) {
+    if (global_ns() - t0 > 2000000000ull) {
+      atomicOr(status, DEV_TIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+
+// Row dots of one smem row (lane t) with the coefficient vectors a and s_prev over NCH
+// chunks, fully unrolled.  The six coefficient arrays (a hi, -a hi, a lo, s hi, -s hi, s lo)
+// are laid out back to back, kCo floats each.
+template <int ST, int NCH>
+__device__ __forceinline__ void row_dots(const unsigned char* ph, const unsigned char* pl, int rs, int t,
+                                         const float* co, Acc2 (&DA)[2], Acc2 (&DS)[2]) {
+  constexpr int kE = (ST == ST_BF16) ? 8 : 4, kP = kE / 2;
+#pragma unroll
+  for (int q = 0; q < NCH; ++q) {
+    f2x H[kP], L[kP];
+    load_chunk2<ST>(ph, pl, rs, t, q, H, L);
+#pragma unroll
+    for (int i = 0; i < kP; i += 2) {
+      const int kk = q * kE + 2 * i;
+      const ulonglong2 ah = *reinterpret_cast<const ulonglong2*>(co + kk);
+      const ulonglong2 an = *reinterpret_cast<const ulonglong2*>(co + kCo + kk);
+      const ulonglong2 al = *reinterpret_cast<const ulonglong2*>(co + 2 * kCo + kk);
+      const ulonglong2 bh = *reinterpret_cast<const ulonglong2*>(co + 3 * kCo + kk);
+      const ulonglong2 bn = *reinterpret_cast<const ulonglong2*>(co + 4 * kCo + kk);
+      const ulonglong2 bl = *reinterpret_cast<const ulonglong2*>(co + 5 * kCo + kk);
+      acc2_fma_basis<ST>(DA[q & 1], H[i], L[i], ah.x, an.x, al.x);
+      acc2_fma_basis<ST>(DS[q & 1], H[i], L[i], bh.x, bn.x, bl.x);
+      acc2_fma_basis<ST>(DA[q & 1], H[i + 1], L[i + 1], ah.y, an.y, al.y);
+      acc2_fma_basis<ST>(DS[q & 1], H[i + 1], L[i + 1], bh.y, bn.y, bl.y);
+    }
+  }
+}
+
+// box widths are odd chunk counts: 1..25 for 4-byte elements, 1..13 for bf16
+template <int ST>
+__device__ __forceinline__ void row_dots_dispatch(int nch, const unsigned char* ph, const unsigned char* pl, int rs,
+                                                  int t, const float* co, Acc2 (&DA)[2], Acc2 (&DS)[2]) {
+#define ODMD_ROW_DOTS_CASE(n) \
+  case n:                     \
+    row_dots<ST, n>(ph, pl, rs, t, co, DA, DS); \
+    break;
+  switch (nch) {
+    ODMD_ROW_DOTS_CASE(1)
+    ODMD_ROW_DOTS_CASE(3)
+    ODMD_ROW_DOTS_CASE(5)
+    ODMD_ROW_DOTS_CASE(7)
+    ODMD_ROW_DOTS_CASE(9)
+    ODMD_ROW_DOTS_CASE(11)
+    ODMD_ROW_DOTS_CASE(13)
+    default:
+      if constexpr (ST != ST_BF16) {
+        switch (nch) {
+          ODMD_ROW_DOTS_CASE(15)
+          ODMD_ROW_DOTS_CASE(17)
+          ODMD_ROW_DOTS_CASE(19)
+          ODMD_ROW_DOTS_CASE(21)
+          ODMD_ROW_DOTS_CASE(23)
+          ODMD_ROW_DOTS_CASE(25)
+          default:
+            break;
+        }
+      }
+  }
+#undef ODMD_ROW_DOTS_CASE
+}
+static_assert(kMaxCap <= 96, "row_dots_dispatch covers box widths up to 25 chunks of 4-byte elements");
+
+template <int ST>
+__global__ void __launch_bounds__(kThreadsA, 1) k_pass_a(Ws ws) {
   using T = Traits<ST>;
   using stored_t = typename T::stored_t;
+  constexpr int kE = (ST == ST_BF16) ? 8 : 4;      // columns per 16-byte chunk
+  constexpr int kP = kE / 2;                        // packed pairs per chunk
+  constexpr int kCS = (ST == ST_BF16) ? 1 : 2;      // chunks a lane owns in the column sums
   extern __shared__ __align__(1024) unsigned char smem[];
   Ctl* ctl = ws.ctl;
   const int cur = ctl->cur, curc = ctl->cur_c;
@@ -297,36 +453,41 @@ __global__ void __launch_bounds__(kThreadsA) k_pass_a(Ws ws) {
   const int r0 = st.hdr->r0;
   const int pend = st.hdr->pend;  // column p = r0 - 1 is formed here
   const int p = r0 - 1;
-  const int tid = threadIdx.x;
-  const bool producer = tid < kHalfA;
-  const int htid = producer ? tid : tid - kHalfA;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int hrow = lane >> 4, cq = lane & 15;  // column phase: row parity and chunk of a lane
+  const int ns = ws.stagesA;
 
-  TilePipe<ST> P;
-  P.setup(ws, r0, kStages);
-  P.g[0] = (const unsigned char*)ws.cbuf[curc];
-  P.g[1] = (const unsigned char*)ws.cbuf[curc ^ 1];
-  P.vb[0] = P.vb[1] = T::vsz;
-  if (pend) {
-    P.g[2] = (const unsigned char*)ws.ebuf;  // residual of the previous update
-    P.vb[2] = 8;
-  }
+  PipeA<ST> P;
+  P.stage_sz = stage_bytes_a<ST>(ws.cap);
+  P.rs = ws.ldg * T::esz;  // = 16 box_chunks(cap): an odd number of 16-byte chunks
+  P.plane_off = kRowsA * P.rs;
+  P.nch = r0 > 0 ? box_chunks(r0, T::esz) : 0;
+  P.gh = reinterpret_cast<const unsigned char*>(ws.Lh);
+  P.gl = reinterpret_cast<const unsigned char*>(ws.Ll);
+  // per-row vectors come in by plain loads, issued before the tile's wait: c, x, the stored
+  // residual of the previous update
+  const stored_t* cvec = reinterpret_cast<const stored_t*>(ws.cbuf[curc]);
+  const stored_t* xvec = reinterpret_cast<const stored_t*>(ws.cbuf[curc ^ 1]);
 
-  // shared layout: stages (reused for the column accumulators at the end) | bars |
-  // a (hi, lo) | s_prev (hi, lo) | 2 slots of (e, x)
+  // shared layout: stages | one barrier per stage | coefficients a and s_prev (hi, -hi, lo
+  // each) | per-warp e/x slots: 3 packed pairs per row (eh, eh, el, el), (-eh, -eh, xh, xh),
+  // (xl, xl, -xh, -xh)
   P.base = smem;
-  unsigned char* sp = smem + pass_a_region<ST>(P.stage_sz);
-  P.bars = reinterpret_cast<uint64_t*>(sp);
-  sp += 8 * kStages;
+  unsigned char* sp = smem + pass_a_region<ST>(P.stage_sz, ns);
+  P.full = reinterpret_cast<uint64_t*>(sp);
+  sp += kBarBytesA;
   float* coh = reinterpret_cast<float*>(sp);
-  float* col = coh + (kMaxCap + 8);
-  float* csh = col + (kMaxCap + 8);
-  float* csl = csh + (kMaxCap + 8);
-  float4* ex4 = reinterpret_cast<float4*>(csl + (kMaxCap + 8));  // [2][kTile] (eh, el, xh, xl)
+  float* con = coh + kCo;
+  float* col = con + kCo;
+  float* csh = col + kCo;
+  float* csn = csh + kCo;
+  float* csl = csn + kCo;
+  float4* ex4 = reinterpret_cast<float4*>(csl + kCo);
   __shared__ int abort_flag;
+  __shared__ int last_issued[kMaxStagesA];  // tile last issued into each stage (for a drain)
 
-  const int epc = (ST == ST_BF16) ? 8 : 4;
-  const int kpad = P.nch * epc;
-  for (int k = tid; k < kMaxCap + 8; k += kThreadsA) {
+  const int kpad = P.nch * kE;
+  for (int k = tid; k < kCo; k += kThreadsA) {
     float h = 0.f, l = 0.f, sh = 0.f, sl = 0.f;
     if (k < r0 && !(pend && k == p)) {
       h = st.a[k].x;
@@ -338,139 +499,203 @@ __global__ void __launch_bounds__(kThreadsA) k_pass_a(Ws ws) {
     }
     if (k >= kpad) h = l = sh = sl = 0.f;
     coh[k] = h;
+    con[k] = -h;
     col[k] = l;
     csh[k] = sh;
+    csn[k] = -sh;
     csl[k] = sl;
   }
   const float aph = pend ? st.a[p].x : 0.f, apl = pend ? st.a[p].y : 0.f;
   const float pih = st.hdr->pinv.x, pil = st.hdr->pinv.y;
-  if (tid == 0) {
-    abort_flag = 0;
-    for (int s = 0; s < kStages; ++s) mbar_init(&P.bars[s], 1);
-    mbar_fence_init();
-  }
-  __syncthreads();
-
-  const int64_t ntiles = (ws.n + kTile - 1) / kTile;
+  const int64_t ntiles = (ws.n + kRowsA - 1) / kRowsA;
   const int G = gridDim.x;
   const int my_tiles = (int)((ntiles - blockIdx.x + G - 1) / G);
+  P.policy = l2_evict_first_policy();
   if (tid == 0) {
-    for (int li = 0; li < min(my_tiles, kStages); ++li) P.issue(blockIdx.x + li * G, li);
-  }
-
-  constexpr int kE = (ST == ST_BF16) ? 8 : 4;  // columns per 16-byte chunk
-  const int nq = max(P.nch, 1);
-  const int G2 = kHalfA / nq;
-  Acc Sacc[kE], Yacc[kE];
-#pragma unroll
-  for (int i = 0; i < kE; ++i) Sacc[i] = Yacc[i] = acc_zero();
-  Acc eta = acc_zero(), exa = acc_zero(), xi = acc_zero();
-
-  if (producer) {
-    const int t = htid >> 2, sub = htid & (kRowLanesA - 1);
-    for (int li = 0; li < my_tiles; ++li) {
-      const int s = li % kStages, slot = li & 1;
-      const uint32_t par = (uint32_t)((li / kStages) & 1);
-      const int64_t row0 = (int64_t)(blockIdx.x + li * G) * kTile;
-      const int rows = rows_in(ws.n, row0);
-      if (li >= 2) named_sync(3 + slot, kThreadsA);  // consumers are done with this slot
-      bool ok = !abort_flag;
-      if (ok) ok = mbar_wait(&P.bars[s], par, &ctl->status);
-      if (!ok) abort_flag = 1;
-      if (ok) {
-        Acc da = row_dot_partial<ST, kRowLanesA>(P, s, t, sub, coh, col);
-        Acc ds = acc_zero();
-        if (pend) ds = row_dot_partial<ST, kRowLanesA>(P, s, t, sub, csh, csl);
-        da = group4_acc_sum(da);
-        if (pend) ds = group4_acc_sum(ds);
-        if (sub == 0) {
-          float ch, cl, xh_, xl_;
-          load_snap(reinterpret_cast<const stored_t*>(P.slot(s, 0)), t, ch, cl);
-          load_snap(reinterpret_cast<const stored_t*>(P.slot(s, 1)), t, xh_, xl_);
-          if (pend) {
-            // j = (e_prev - L0[:, :p] s_prev) / rho0, as stored; a_p j joins the row dot
-            const float2 ep = reinterpret_cast<const float2*>(P.slot(s, 2))[t];
-            Acc j = Acc{ep.x, ep.y};
-            acc_add(j, -ds.h, -ds.l);
-            j = acc_norm(j);
-            Acc jj = acc_zero();
-            acc_fma(jj, j.h, j.l, pih, pil);
-            jj = acc_norm(jj);
-            float jh = jj.h, jl = jj.l;
-            round_to_storage<ST>(jh, jl);
-            store_elem_smem<ST>(P.plane_h(s), P.plane_l(s), P.rs, t, p, jh, jl);
-            if (t < rows) store_elem_global<ST>(ws, (size_t)(row0 + t) * ws.ldg + p, jh, jl);
-            acc_fma(da, jh, jl, aph, apl);
-          }
-          Acc e = Acc{ch, cl};
-          acc_add(e, -da.h, -da.l);
-          e = acc_norm(e);
-          if (t >= rows) {
-            e = acc_zero();
-            xh_ = xl_ = 0.f;
-          } else {
-            ws.ebuf[row0 + t] = make_float2(e.h, e.l);  // kept for the second Gram-Schmidt pass
-          }
-          ex4[slot * kTile + t] = make_float4(e.h, e.l, xh_, xl_);
-          acc_fma(eta, e.h, e.l, e.h, e.l);
-          acc_fma(exa, e.h, e.l, xh_, xl_);
-          acc_fma(xi, xh_, xl_, xh_, xl_);
-        }
-      }
-      named_arrive(1 + slot, kThreadsA);  // slot (and the stage) ready for the consumers
+    abort_flag = 0;
+    for (int s = 0; s < ns; ++s) {
+      mbar_init(&P.full[s], 1);
+      last_issued[s] = -1;
     }
-    // balance the empty barriers the consumers arrive on for the last two tiles
-    for (int li = max(my_tiles, 2); li < my_tiles + 2; ++li) named_sync(3 + (li & 1), kThreadsA);
-  } else {
-    // consumer thread: chunk cq (E adjacent columns) of rows grp, grp + G2, ...
-    const int cq = htid % nq, grp = htid / nq;
-    const bool col_active = (r0 > 0) && grp < G2;
-    for (int li = 0; li < my_tiles; ++li) {
-      const int s = li % kStages, slot = li & 1;
-      const int64_t row0 = (int64_t)(blockIdx.x + li * G) * kTile;
-      const int rows = rows_in(ws.n, row0);
-      named_sync(1 + slot, kThreadsA);  // producers filled the slot
-      // observe the stage's completed phase too, so the TMA writes are visible here
-      if (!abort_flag) mbar_wait(&P.bars[s], (uint32_t)((li / kStages) & 1), &ctl->status);
-      if (!abort_flag && col_active) {
-        const unsigned char* ph = P.plane_h(s);
-        const unsigned char* pl = P.plane_l(s);
-        const float4* ex = ex4 + slot * kTile;
-        for (int tt = grp; tt < rows; tt += G2) {
-          float h[8], l[8];
-          load_chunk<ST>(ph, pl, P.rs, tt, cq, h, l);
-          const float4 v = ex[tt];
-#pragma unroll
-          for (int i = 0; i < kE; ++i) {
-            acc_fma(Sacc[i], h[i], l[i], v.x, v.y);
-            acc_fma(Yacc[i], h[i], l[i], v.z, v.w);
-          }
-        }
-      }
-      // the consumers are the last readers of the stage: refill it, free the slot
-      if (htid == 0 && !abort_flag && li + kStages < my_tiles) P.issue(blockIdx.x + (li + kStages) * G, s);
-      named_arrive(3 + slot, kThreadsA);
+    mbar_fence_init();
+    // the first ns tiles; afterwards the warp that releases a stage refills it
+    for (int k = 0; k < ns && k < my_tiles; ++k) {
+      last_issued[k] = k;
+      P.issue(blockIdx.x + k * G, k);
     }
   }
   __syncthreads();
-  if (abort_flag && tid == 0) mbar_drain(P.bars, kStages, 0, my_tiles);
+
+  Acc2 Sacc[kCS][kP], Yacc[kCS][kP], Sacc2[kCS][kP], Yacc2[kCS][kP];
+#pragma unroll
+  for (int c = 0; c < kCS; ++c)
+#pragma unroll
+    for (int i = 0; i < kP; ++i) Sacc[c][i] = Yacc[c][i] = Sacc2[c][i] = Yacc2[c][i] = acc2_zero();
+  Acc eta = acc_zero(), exa = acc_zero(), xi = acc_zero();
+
+  {
+    float4* ex = ex4 + warp * kRowsA * 3;
+    for (int k = warp; k < my_tiles; k += kWarpsA) {
+      const int s = k % ns;
+      const int64_t row0 = (int64_t)(blockIdx.x + k * G) * kRowsA;
+      const int rows = (int)((ws.n - row0) < kRowsA ? (ws.n - row0) : kRowsA);
+      // rows past n (up to the padded length) read zeros
+      const stored_t cv = cvec[row0 + lane], xv = xvec[row0 + lane];
+      const float2 ep = pend ? ws.ebuf[row0 + lane] : make_float2(0.f, 0.f);
+      // a stage's barrier is waited on by parity, which cannot tell tile k's phase from the
+      // phase two refills earlier: first make sure tile k itself has been issued into it
+      bool ok = !abort_flag;
+      if (ok) ok = wait_issued(&last_issued[s], k, &ctl->status);
+      if (ok) ok = mbar_wait(&P.full[s], (uint32_t)((k / ns) & 1), &ctl->status);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) {
+        abort_flag = 1;
+        break;
+      }
+      const unsigned char* ph = P.plane_h(s);
+      const unsigned char* pl = P.plane_l(s);
+      // ---- row phase: lane = row
+      {
+        const int t = lane;
+        // the chunk count is a compile-time constant in each branch, so the row dot is
+        // straight-line code whose chains the compiler interleaves
+        Acc2 DA[2] = {acc2_zero(), acc2_zero()}, DS[2] = {acc2_zero(), acc2_zero()};
+        row_dots_dispatch<ST>(P.nch, ph, pl, P.rs, t, coh, DA, DS);
+        Acc da, ds, u, v, w;
+        acc2_split(DA[0], da, u);
+        acc2_split(DA[1], v, w);
+        acc_add(da, u.h, u.l);
+        acc_add(da, v.h, v.l);
+        acc_add(da, w.h, w.l);
+        acc2_split(DS[0], ds, u);
+        acc2_split(DS[1], v, w);
+        acc_add(ds, u.h, u.l);
+        acc_add(ds, v.h, v.l);
+        acc_add(ds, w.h, w.l);
+        float ch, cl, xh_, xl_;
+        load_snap(&cv, 0, ch, cl);
+        load_snap(&xv, 0, xh_, xl_);
+        if (pend) {
+          // j = (e_prev - L0[:, :p] s_prev) / rho0, as stored; a_p j joins the row dot
+          Acc j = Acc{ep.x, ep.y};
+          acc_add(j, -ds.h, -ds.l);
+          j = acc_norm(j);
+          Acc jj = acc_zero();
+          acc_fma(jj, j.h, j.l, pih, pil);
+          jj = acc_norm(jj);
+          float jh = jj.h, jl = jj.l;
+          round_to_storage<ST>(jh, jl);
+          store_elem_smem<ST>(P.plane_h(s), P.plane_l(s), P.rs, t, p, jh, jl);
+          if (t < rows) store_elem_global<ST>(ws, (size_t)(row0 + t) * ws.ldg + p, jh, jl);
+          acc_fma(da, jh, jl, aph, apl);
+        }
+        Acc e = Acc{ch, cl};
+        acc_add(e, -da.h, -da.l);
+        e = acc_norm(e);
+        if (t >= rows) {
+          e = acc_zero();
+          xh_ = xl_ = 0.f;
+        } else {
+          ws.ebuf[row0 + t] = make_float2(e.h, e.l);  // kept for the second Gram-Schmidt pass
+        }
+        ex[3 * t] = make_float4(e.h, e.h, e.l, e.l);
+        ex[3 * t + 1] = make_float4(-e.h, -e.h, xh_, xh_);
+        ex[3 * t + 2] = make_float4(xl_, xl_, -xh_, -xh_);
+        acc_fma(eta, e.h, e.l, e.h, e.l);
+        acc_fma(exa, e.h, e.l, xh_, xl_);
+        acc_fma(xi, xh_, xl_, xh_, xl_);
+      }
+      __syncwarp();
+      // ---- column phase: lanes 0-15 take row 2i, lanes 16-31 row 2i + 1; lane owns chunks cq, cq + 16
+      {
+        // all 32 rows, straight-line: rows past the end of the data are zero in the stage and
+        // in the e/x slot, so they add exact zeros.  Lanes whose chunk is past nch read a valid
+        // chunk; their sums land in columns that are never read.
+        const ulonglong2* exv = reinterpret_cast<const ulonglong2*>(ex);
+        auto rows16 = [&](int q, auto cc) {
+          constexpr int c = decltype(cc)::value;
+#pragma unroll 1
+          for (int j0 = 0; j0 < kRowsA / 2; j0 += 4)
+#pragma unroll
+          for (int j1 = 0; j1 < 4; ++j1) {
+            const int j = j0 + j1;
+            const int tt = hrow + 2 * j;
+            const ulonglong2 v0 = exv[3 * tt], v1 = exv[3 * tt + 1], v2 = exv[3 * tt + 2];
+            f2x H[kP], L[kP];
+            load_chunk2<ST>(ph, pl, P.rs, tt, q, H, L);
+#pragma unroll
+            for (int i = 0; i < kP; ++i) {
+              if (j1 & 1) {
+                acc2_fma_basis<ST>(Sacc2[c][i], H[i], L[i], v0.x, v1.x, v0.y);  // e
+                acc2_fma_basis<ST>(Yacc2[c][i], H[i], L[i], v1.y, v2.y, v2.x);  // x
+              } else {
+                acc2_fma_basis<ST>(Sacc[c][i], H[i], L[i], v0.x, v1.x, v0.y);
+                acc2_fma_basis<ST>(Yacc[c][i], H[i], L[i], v1.y, v2.y, v2.x);
+              }
+            }
+          }
+        };
+        rows16(cq < P.nch ? cq : P.nch - 1, std::integral_constant<int, 0>{});
+        if constexpr (kCS > 1) {
+          if (P.nch > 16) rows16(cq + 16 < P.nch ? cq + 16 : P.nch - 1, std::integral_constant<int, kCS - 1>{});
+        }
+      }
+      // this warp is the stage's last reader: refill it with tile k + ns
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0 && k + ns < my_tiles && !abort_flag) {
+        P.issue(blockIdx.x + (k + ns) * G, s);
+        *reinterpret_cast<volatile int*>(&last_issued[s]) = k + ns;
+      }
+    }
+  }
+  __syncthreads();
+  if (abort_flag && tid == 0) {
+    // give the copies still in flight (the last tile issued into each stage) up to 0.5 s
+    const uint64_t t0 = global_ns();
+    for (int st_ = 0; st_ < ns; ++st_) {
+      const int k = last_issued[st_];
+      if (k < 0) continue;
+      while (!mbar_try_wait(&P.full[st_], (uint32_t)((k / ns) & 1)))
+        if (global_ns() - t0 > 500000000ull) break;
+    }
+  }
+  __syncthreads();
 
   // ---- per-CTA partials
   const int stride = 2 * ws.cap + 3;
   float2* mypart = ws.part + (size_t)blockIdx.x * stride;
-  // consumer accumulators -> stage memory (idle now): colacc[g][k] for S then Y
-  Acc* cacc = reinterpret_cast<Acc*>(smem);
-  const int ncols_box = nq * kE;
-  if (!producer) {
-    const int cq = htid % nq, grp = htid / nq;
-    if (grp < G2)
+  // column sums: lanes cq and cq + 16 of a warp hold the same columns (even / odd rows)
+  Acc* cacc = reinterpret_cast<Acc*>(smem);  // [warp][S | Y][kCo], in the idle stage memory
+  {
 #pragma unroll
-      for (int i = 0; i < kE; ++i) {
-        cacc[(size_t)grp * ncols_box + cq * kE + i] = Sacc[i];
-        cacc[(size_t)(G2 + grp) * ncols_box + cq * kE + i] = Yacc[i];
+    for (int c = 0; c < kCS; ++c)
+#pragma unroll
+      for (int i = 0; i < kP; ++i) {
+        Acc s0, s1, y0, y1, u0, u1;
+        acc2_split(Sacc[c][i], s0, s1);
+        acc2_split(Sacc2[c][i], u0, u1);
+        acc_add(s0, u0.h, u0.l);
+        acc_add(s1, u1.h, u1.l);
+        acc2_split(Yacc[c][i], y0, y1);
+        acc2_split(Yacc2[c][i], u0, u1);
+        acc_add(y0, u0.h, u0.l);
+        acc_add(y1, u1.h, u1.l);
+        acc_add(s0, __shfl_xor_sync(0xffffffffu, s0.h, 16), __shfl_xor_sync(0xffffffffu, s0.l, 16));
+        acc_add(s1, __shfl_xor_sync(0xffffffffu, s1.h, 16), __shfl_xor_sync(0xffffffffu, s1.l, 16));
+        acc_add(y0, __shfl_xor_sync(0xffffffffu, y0.h, 16), __shfl_xor_sync(0xffffffffu, y0.l, 16));
+        acc_add(y1, __shfl_xor_sync(0xffffffffu, y1.h, 16), __shfl_xor_sync(0xffffffffu, y1.l, 16));
+        const int c0 = (cq + 16 * c) * kE + 2 * i;
+        if (hrow == 0 && c0 < kCo) {
+          Acc* w = cacc + (size_t)warp * 2 * kCo;
+          w[c0] = s0;
+          w[c0 + 1] = s1;
+          w[kCo + c0] = y0;
+          w[kCo + c0 + 1] = y1;
+        }
       }
   }
-  // scalar sums live in the sub == 0 lanes of the producer warps (others hold zeros)
+  // scalar sums live in the row lanes of every warp
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     acc_add(eta, __shfl_xor_sync(0xffffffffu, eta.h, o), __shfl_xor_sync(0xffffffffu, eta.l, o));
@@ -478,16 +703,16 @@ __global__ void __launch_bounds__(kThreadsA) k_pass_a(Ws ws) {
     acc_add(xi, __shfl_xor_sync(0xffffffffu, xi.h, o), __shfl_xor_sync(0xffffffffu, xi.l, o));
   }
   __shared__ Acc wsc[kThreadsA / 32][3];
-  if ((tid & 31) == 0) {
-    wsc[tid >> 5][0] = eta;
-    wsc[tid >> 5][1] = exa;
-    wsc[tid >> 5][2] = xi;
+  if (lane == 0) {
+    wsc[warp][0] = eta;
+    wsc[warp][1] = exa;
+    wsc[warp][2] = xi;
   }
   __syncthreads();
   if (tid < r0) {
     Acc sS = acc_zero(), sY = acc_zero();
-    for (int g = 0; g < G2; ++g) {
-      const Acc a1 = cacc[(size_t)g * ncols_box + tid], a2 = cacc[(size_t)(G2 + g) * ncols_box + tid];
+    for (int w = 0; w < kWarpsA; ++w) {
+      const Acc a1 = cacc[(size_t)w * 2 * kCo + tid], a2 = cacc[(size_t)w * 2 * kCo + kCo + tid];
       acc_add(sS, a1.h, a1.l);
       acc_add(sY, a2.h, a2.l);
     }
@@ -610,7 +835,6 @@ __global__ void __launch_bounds__(kThreadsB) k_pass_b(Ws ws) {
       coh[k] = h;
       col[k] = l;
     }
-    const int r0e = r0 + append;
     const int rnp = (rnew + 3) & ~3;  // output columns padded to whole float4s (zeros)
     const int kch = P.nch * epc;      // basis columns covered by the box (zero rows of QB beyond r0)
     if (!FLUSH) {
@@ -963,11 +1187,23 @@ __global__ void __launch_bounds__(kThreads) k_first(Ws ws) {
 static int stage_of(int prec, int cap) {
   return prec == ST_DD ? stage_bytes<ST_DD>(cap) : prec == ST_F32 ? stage_bytes<ST_F32>(cap) : stage_bytes<ST_BF16>(cap);
 }
+static int stage_a_of(int prec, int cap) {
+  return prec == ST_DD ? stage_bytes_a<ST_DD>(cap) : prec == ST_F32 ? stage_bytes_a<ST_F32>(cap) : stage_bytes_a<ST_BF16>(cap);
+}
+// as many stages as fit in the dynamic shared memory a CTA may have (a deeper ring keeps
+// more HBM reads in flight; a stage is held until its compute warp is done with it)
+int stages_a(int prec, int cap) {
+  const int sz = stage_a_of(prec, cap);
+  int n = (kSmemBudget - smem_a_fixed()) / sz;
+  if (n > kMaxStagesA) n = kMaxStagesA;
+  return n < 2 ? 2 : n;
+}
 static int smem_a(int prec, int cap) {
-  const size_t region = prec == ST_DD    ? pass_a_region<ST_DD>(stage_of(prec, cap))
-                        : prec == ST_F32 ? pass_a_region<ST_F32>(stage_of(prec, cap))
-                                         : pass_a_region<ST_BF16>(stage_of(prec, cap));
-  return (int)region + 8 * kStages + 4 * (kMaxCap + 8) * 4 + 2 * kTile * 16;
+  const int ns = stages_a(prec, cap), sz = stage_a_of(prec, cap);
+  const size_t region = prec == ST_DD    ? pass_a_region<ST_DD>(sz, ns)
+                        : prec == ST_F32 ? pass_a_region<ST_F32>(sz, ns)
+                                         : pass_a_region<ST_BF16>(sz, ns);
+  return (int)region + smem_a_fixed();
 }
 static int smem_b(int prec, int cap) {
   return kStagesB * stage_of(prec, cap) + 8 * kStagesB + 2 * (kMaxCap + 8) * 4 + 2 * kTile * 4 +
@@ -1016,13 +1252,13 @@ cudaError_t launch_pass_a(const Ws& ws, cudaStream_t s) {
   const int sm = smem_a(ws.prec, ws.cap);
   switch (ws.prec) {
     case ST_DD:
-      k_pass_a<ST_DD><<<ws.gridA, kThreadsA, sm, s>>>(ws);
+      k_pass_a<ST_DD><<<ws.gridPA, kThreadsA, sm, s>>>(ws);
       break;
     case ST_F32:
-      k_pass_a<ST_F32><<<ws.gridA, kThreadsA, sm, s>>>(ws);
+      k_pass_a<ST_F32><<<ws.gridPA, kThreadsA, sm, s>>>(ws);
       break;
     default:
-      k_pass_a<ST_BF16><<<ws.gridA, kThreadsA, sm, s>>>(ws);
+      k_pass_a<ST_BF16><<<ws.gridPA, kThreadsA, sm, s>>>(ws);
   }
   return cudaGetLastError();
 }
