@@ -378,13 +378,14 @@ __device__ __forceinline__ bool wait_issued(const int* slot, int k, int* status)
 }
 
 // Row dots of one smem row (lane t) with the coefficient vectors a and s_prev over NCH
-// chunks, fully unrolled.  The six coefficient arrays (a hi, -a hi, a lo, s hi, -s hi, s lo)
+// chunks (a compile-time count).  The six coefficient arrays (a hi, -a hi, a lo, s hi, -s hi, s lo)
 // are laid out back to back, kCo floats each.
 template <int ST, int NCH>
 __device__ __forceinline__ void row_dots(const unsigned char* ph, const unsigned char* pl, int rs, int t,
                                          const float* co, Acc2 (&DA)[2], Acc2 (&DS)[2]) {
   constexpr int kE = (ST == ST_BF16) ? 8 : 4, kP = kE / 2;
-#pragma unroll
+  // two chunks per loop body: fully unrolled row dots stall on instruction fetch
+#pragma unroll 2
   for (int q = 0; q < NCH; ++q) {
     f2x H[kP], L[kP];
     load_chunk2<ST>(ph, pl, rs, t, q, H, L);
