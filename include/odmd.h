@@ -28,7 +28,7 @@
  *   (non-finite input, a solver that did not converge) is recorded on the device and
  *   reported by the next synchronising call.
  * - A handle is not thread-safe; different handles may be used concurrently.
- * - Snapshot element type: double for ODMD_FP64, float for ODMD_FP32 and ODMD_BF16.
+ * - Snapshot element type: double for ODMD_FP64, float for ODMD_FP32.
  *   Snapshots are contiguous vectors of n elements.
  */
 #ifndef ODMD_H
@@ -58,7 +58,8 @@ typedef enum {
  *   ODMD_FP64: basis as an unevaluated sum of two floats (hi + lo, 48-bit significand),
  *              snapshots and outputs double.
  *   ODMD_FP32: basis float, snapshots and outputs float.
- *   ODMD_BF16: basis bfloat16, snapshots and outputs float.
+ *   ODMD_BF16: reserved; rejected with ODMD_ERR_ARG (a bfloat16 basis cannot stay
+ *              orthonormal to the accuracy the rank-1 update assumes).
  * The small solves (core SVD, operator update, eigensolve) are FP64 in every mode. */
 typedef enum { ODMD_FP64 = 0, ODMD_FP32 = 1, ODMD_BF16 = 2 } odmd_precision;
 

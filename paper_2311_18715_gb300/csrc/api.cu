@@ -103,6 +103,12 @@ odmd_status check_cfg(const odmd_config* c, std::string& why) {
     why = "unknown precision";
     return ODMD_ERR_ARG;
   }
+  if (c->prec == ODMD_BF16) {
+    // an 8-bit significand cannot hold the basis orthonormal to the accuracy the rank-1
+    // update assumes (measured: ||L^T L - I|| reaches ~1 at the first truncation)
+    why = "ODMD_BF16 basis storage is not supported by the rank-1 update; use ODMD_FP32";
+    return ODMD_ERR_ARG;
+  }
   if (c->flags != 0) {
     why = "flags must be 0";
     return ODMD_ERR_ARG;

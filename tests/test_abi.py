@@ -55,4 +55,8 @@ def test_footprint_and_argument_checks_on_host():
     lib.odmd_config_default(C.byref(bad), 100, 8)
     bad.trunc_tol = 1e-16
     assert lib.odmd_footprint(C.byref(bad), C.byref(nb)) == 1
+    lib.odmd_config_default(C.byref(bad), 100, 8)
+    bad.prec = 2  # ODMD_BF16: refused, with the reason
+    assert lib.odmd_footprint(C.byref(bad), C.byref(nb)) == 1
+    assert b"BF16" in lib.odmd_last_error(None)
     assert lib.odmd_update(None, None) == 1
