@@ -37,6 +37,10 @@ BLOCK = 50          # snapshots per step (check interval of the workload)
 PRETRAIN = 100      # untimed snapshots before warm-up
 SIGMA = 1e-6
 L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes (read + write) per launch from one ncu capture of the current kernels
+# (profiles/pass_a_wake_n393216_r40.md); pass A copies whole rows, so its traffic does not
+# depend on r0.  Kernels without a capture report null.
+TRAFFIC = {"pass_a": 213.7e6}
 WORKLOAD = (f"cylinder-wake field {NX}x{NY}x3 (n={N}), r_max={R_MAX}, FP64 accuracy, "
             f"{BLOCK}-snapshot blocks: {BLOCK} updates + {BLOCK}-state rollout + 1 check")
 
@@ -327,13 +331,13 @@ def run_ours(args) -> None:
         per_launch_ms = ms_tot[dom] / max(groups[dom], 1)
         achieved = bytes_per[dom] / (per_launch_ms * 1e-3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
+                "frac": achieved / hbm, "traffic": TRAFFIC.get(dom), "peak_kind": peak_kind,
                 "bytes_per_launch": bytes_per[dom], "ms_per_launch": per_launch_ms}
     pa_ms = ms_tot["pass_a"] / max(groups["pass_a"], 1)
     pass_a_roof = {"achieved": bytes_per["pass_a"] / (pa_ms * 1e-3) / 1e9, "peak": hbm,
                    "frac": bytes_per["pass_a"] / (pa_ms * 1e-3) / 1e9 / hbm, "ms_per_launch": pa_ms}
     if roof is None:
-        roof = dict(pass_a_roof, kernel="pass_a", bound="hbm", unit="GB/s", traffic=None,
+        roof = dict(pass_a_roof, kernel="pass_a", bound="hbm", unit="GB/s", traffic=TRAFFIC["pass_a"],
                     peak_kind=peak_kind, note=f"dominant class is {dom}")
 
     # ---- end to end through the public API with host buffers
