@@ -112,6 +112,20 @@ odmd_status odmd_predict(odmd_t h, const double* t_host, int32_t k, void* out_de
 odmd_status odmd_check(odmd_t h, double t, const void* x_fom_dev, double tol,
                        double* rel_err, int32_t* pass);
 
+/* One step of the hybrid FOM/ROM loop (Sec. 2.1, Fig. 1) for the step t = number of
+ * snapshots received so far.  x_fom_dev: the FOM's state at step t (device, n elements of
+ * the snapshot type).  If a model exists, the ROM predicts u(t) and the credibility test of
+ * Sec. 2.2 compares it with x_fom (rel_err as in odmd_check; tol <= 0 selects check_tol);
+ * a credible prediction is taken as the new state, otherwise the FOM state is.  The state
+ * taken is written to state_out_dev (device, n elements, must not alias x_fom_dev) and
+ * appended to the model as the next snapshot, so the pairs stay contiguous (an accepted
+ * prediction updates the DMD as a FOM state would).  Before a model exists the FOM state is
+ * taken.  *accepted (host, may be NULL): 1 if the prediction was taken; *rel_err (host, may
+ * be NULL): the distance measured, +inf when no model existed.  Synchronises the stream
+ * for the test; the update itself is asynchronous. */
+odmd_status odmd_hybrid_step(odmd_t h, const void* x_fom_dev, double tol, void* state_out_dev,
+                             int32_t* accepted, double* rel_err);
+
 /* Wait for the handle's stream and report any recorded device-side error. */
 odmd_status odmd_sync(odmd_t h);
 

@@ -709,6 +709,36 @@ odmd_status odmd_check(odmd_t h, double t, const void* x_fom_dev, double tol, do
   return ODMD_OK;
 }
 
+odmd_status odmd_hybrid_step(odmd_t h, const void* x_fom_dev, double tol, void* state_out_dev, int32_t* accepted,
+                             double* rel_err) {
+  if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
+  if (!x_fom_dev || !state_out_dev) return fail(h, ODMD_ERR_ARG, "x_fom and state_out must not be NULL");
+  if (state_out_dev == x_fom_dev) return fail(h, ODMD_ERR_ARG, "state_out must not alias x_fom");
+  int32_t acc = 0;
+  double err = INFINITY;
+  const double t = (double)h->nsnap;  // the step about to be taken, counted from u^0
+  if (h->nsnap >= 2) {
+    odmd_status s = odmd_check(h, t, x_fom_dev, tol, &err, &acc);
+    if (s == ODMD_ERR_STATE) {  // no model yet (every snapshot so far was zero): the FOM decides
+      acc = 0;
+      err = INFINITY;
+    } else if (s != ODMD_OK) {
+      return s;
+    }
+  }
+  if (acc) {
+    if (odmd_status s = odmd_predict(h, &t, 1, state_out_dev, h->cfg.n)) return s;
+  } else {
+    CK(h, cudaMemcpyAsync(state_out_dev, x_fom_dev, snap_bytes(h), cudaMemcpyDeviceToDevice, h->stream),
+       "copy the FOM state");
+  }
+  // the state taken, accepted prediction or FOM state, joins the snapshot stream
+  if (odmd_status s = odmd_update(h, state_out_dev)) return s;
+  if (accepted) *accepted = acc;
+  if (rel_err) *rel_err = err;
+  return ODMD_OK;
+}
+
 odmd_status odmd_sync(odmd_t h) {
   if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
   return device_status(h);

@@ -94,6 +94,21 @@ class OnlineDMD:
                                       C.byref(err), C.byref(ok)))
         return float(err.value), bool(ok.value)
 
+    def hybrid_step(self, x_fom: torch.Tensor, tol: float = 0.0,
+                    out: torch.Tensor | None = None) -> tuple[torch.Tensor, bool, float]:
+        """One step of the hybrid FOM/ROM loop (odmd_hybrid_step): returns the state taken
+        (the ROM prediction if it passes the credibility test against x_fom, else x_fom),
+        whether the prediction was accepted, and the relative error measured."""
+        x_fom = self._snap(x_fom, "x_fom")
+        if out is None:
+            out = torch.empty(self.n, dtype=self.dtype, device=self.device)
+        out = self._snap(out, "out")
+        acc = C.c_int32()
+        err = C.c_double()
+        self._ck(self._lib.odmd_hybrid_step(self._h, C.c_void_p(x_fom.data_ptr()), float(tol),
+                                            C.c_void_p(out.data_ptr()), C.byref(acc), C.byref(err)))
+        return out, bool(acc.value), float(err.value)
+
     def sync(self) -> None:
         self._ck(self._lib.odmd_sync(self._h))
 
