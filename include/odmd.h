@@ -126,6 +126,17 @@ odmd_status odmd_check(odmd_t h, double t, const void* x_fom_dev, double tol,
 odmd_status odmd_hybrid_step(odmd_t h, const void* x_fom_dev, double tol, void* state_out_dev,
                              int32_t* accepted, double* rel_err);
 
+/* Many instances in one call (independent simulations, Sec. 2.1 per instance):
+ * odmd_update_batch is odmd_update(hs[i], xs[i]) for i < count, and odmd_predict_batch is
+ * odmd_predict(hs[i], ts[i], ks[i], outs[i], lds[i]); each instance's work is enqueued on
+ * its own handle's stream, so instances created on different streams run concurrently on
+ * the GPU (the update of one instance is a single CUDA-graph launch).  Handles must be
+ * distinct within a call.  On the first failing instance the call stops and returns that
+ * status; odmd_last_error(NULL) names the instance.  Earlier instances stay updated. */
+odmd_status odmd_update_batch(odmd_t* hs, const void* const* xs, int32_t count);
+odmd_status odmd_predict_batch(odmd_t* hs, const double* const* ts, const int32_t* ks, void* const* outs,
+                               const int64_t* lds, int32_t count);
+
 /* Wait for the handle's stream and report any recorded device-side error. */
 odmd_status odmd_sync(odmd_t h);
 

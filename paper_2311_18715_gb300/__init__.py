@@ -6,14 +6,15 @@ The C ABI lives in include/odmd.h and libodmd.so (built in-tree by ``build()``);
 from ._build import build
 from ._lib import EXPORTED, OdmdError, load_library
 
-__all__ = ["build", "load_library", "OdmdError", "EXPORTED", "OnlineDMD", "check_noalloc"]
+__all__ = ["build", "load_library", "OdmdError", "EXPORTED", "OnlineDMD", "check_noalloc", "update_batch",
+           "predict_batch"]
 
 
 def __getattr__(name):
     if name == "OnlineDMD":
         from .odmd import OnlineDMD
         return OnlineDMD
-    if name == "check_noalloc":
-        from .odmd import check_noalloc
-        return check_noalloc
+    if name in ("check_noalloc", "update_batch", "predict_batch"):
+        from . import odmd
+        return getattr(odmd, name)
     raise AttributeError(name)

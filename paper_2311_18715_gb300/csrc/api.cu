@@ -739,6 +739,33 @@ odmd_status odmd_hybrid_step(odmd_t h, const void* x_fom_dev, double tol, void* 
   return ODMD_OK;
 }
 
+odmd_status odmd_update_batch(odmd_t* hs, const void* const* xs, int32_t count) {
+  if (count < 0 || (count > 0 && (!hs || !xs))) return fail(nullptr, ODMD_ERR_ARG, "update_batch: bad arguments");
+  for (int32_t i = 0; i < count; ++i) {
+    if (!hs[i]) return fail(nullptr, ODMD_ERR_ARG, "update_batch: handle " + std::to_string(i) + " is NULL");
+    for (int32_t j = 0; j < i; ++j)
+      if (hs[j] == hs[i])
+        return fail(nullptr, ODMD_ERR_ARG, "update_batch: handle " + std::to_string(i) + " repeats handle " +
+                                               std::to_string(j));
+  }
+  for (int32_t i = 0; i < count; ++i)
+    if (odmd_status s = odmd_update(hs[i], xs[i]))
+      return fail(nullptr, s, "update_batch: instance " + std::to_string(i) + ": " + hs[i]->err);
+  return ODMD_OK;
+}
+
+odmd_status odmd_predict_batch(odmd_t* hs, const double* const* ts, const int32_t* ks, void* const* outs,
+                               const int64_t* lds, int32_t count) {
+  if (count < 0 || (count > 0 && (!hs || !ts || !ks || !outs || !lds)))
+    return fail(nullptr, ODMD_ERR_ARG, "predict_batch: bad arguments");
+  for (int32_t i = 0; i < count; ++i)
+    if (!hs[i]) return fail(nullptr, ODMD_ERR_ARG, "predict_batch: handle " + std::to_string(i) + " is NULL");
+  for (int32_t i = 0; i < count; ++i)
+    if (odmd_status s = odmd_predict(hs[i], ts[i], ks[i], outs[i], lds[i]))
+      return fail(nullptr, s, "predict_batch: instance " + std::to_string(i) + ": " + hs[i]->err);
+  return ODMD_OK;
+}
+
 odmd_status odmd_sync(odmd_t h) {
   if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
   return device_status(h);

@@ -198,3 +198,33 @@ def check_noalloc(pred: torch.Tensor, x_fom: torch.Tensor, tol: float = 0.0,
                                           pred.numel(), float(tol), C.c_void_p(s.cuda_stream),
                                           C.byref(err), C.byref(ok)))
     return float(err.value), bool(ok.value)
+
+
+def update_batch(models: Sequence[OnlineDMD], xs: Sequence[torch.Tensor]) -> None:
+    """odmd_update_batch: append xs[i] to models[i] for every i in one call; instances on
+    different streams run concurrently."""
+    if len(models) != len(xs):
+        raise ValueError("models and xs differ in length")
+    lib = load_library()
+    xs = [m._snap(x, f"xs[{i}]") for i, (m, x) in enumerate(zip(models, xs))]
+    k = len(models)
+    hs = (C.c_void_p * max(k, 1))(*[m._h for m in models])
+    ps = (C.c_void_p * max(k, 1))(*[x.data_ptr() for x in xs])
+    check(lib, lib.odmd_update_batch(hs, ps, k))
+
+
+def predict_batch(models: Sequence[OnlineDMD], ts: Sequence[Sequence[float]]) -> list[torch.Tensor]:
+    """odmd_predict_batch: predictions of every model at its own step counts."""
+    if len(models) != len(ts):
+        raise ValueError("models and ts differ in length")
+    lib = load_library()
+    k = len(models)
+    outs = [torch.empty((len(t), m.n), dtype=m.dtype, device=m.device) for m, t in zip(models, ts)]
+    tarrs = [(C.c_double * max(len(t), 1))(*[float(v) for v in t]) for t in ts]
+    hs = (C.c_void_p * max(k, 1))(*[m._h for m in models])
+    tp = (C.POINTER(C.c_double) * max(k, 1))(*[C.cast(a, C.POINTER(C.c_double)) for a in tarrs])
+    ks = (C.c_int32 * max(k, 1))(*[len(t) for t in ts])
+    op = (C.c_void_p * max(k, 1))(*[o.data_ptr() for o in outs])
+    lds = (C.c_int64 * max(k, 1))(*[m.n for m in models])
+    check(lib, lib.odmd_predict_batch(hs, tp, ks, op, lds, k))
+    return outs
