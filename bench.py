@@ -430,6 +430,197 @@ def run_profile_case(args) -> None:
     model.close()
 
 
+class DeviceStream:
+    """A separable synthetic stream (fixed fields times scalar time coefficients) drawn on
+    the device: x_k = coefficients(k) @ fields + sigma * noise_k, with torch's generator
+    seeded per step for the noise.  Same fields and coefficients as the host generator;
+    the noise differs from the host's draw (these runs are measured, not checked)."""
+
+    def __init__(self, gen, device, dtype):
+        import torch
+
+        self.gen, self.device, self.dtype = gen, device, dtype
+        self.fields = torch.from_numpy(np.ascontiguousarray(gen.fields)).to(device)
+        self.g = torch.Generator(device=device)
+
+    def draw(self, k: int, out):
+        import torch
+
+        c = torch.from_numpy(np.asarray(self.gen.coefficients(k), dtype=np.float64)).to(self.device)
+        x = c @ self.fields
+        if self.gen.sigma > 0.0:
+            self.g.manual_seed(1_000_003 * (self.gen.seed + 1) + k)
+            x += self.gen.sigma * torch.randn(x.shape[0], generator=self.g, device=self.device,
+                                              dtype=torch.float64)
+        out.copy_(x.to(self.dtype))
+        return out
+
+
+def run_fp32_large(args) -> None:
+    """The mixed-precision wake configuration: a 2048 x 1024 grid of (u, v, p) (n = 6,291,456),
+    r_max 64, basis in FP32 storage with compensated arithmetic, FP32 snapshots; the same
+    50-snapshot blocks as the default workload, timed the same way."""
+    import torch
+
+    import paper_2311_18715_gb300 as pkg
+    from synth import WakeField
+
+    dev = torch.device("cuda", 0)
+    pkg.build()
+    gen = WakeField(2048, 1024, sigma=SIGMA, seed=0)
+    n, r_max = gen.n, 64
+    ds = DeviceStream(gen, dev, torch.float32)
+    model = pkg.OnlineDMD(n, r_max, prec="fp32", slack=SLACK, trunc_tol=TAU)
+    stream = model.stream
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    x = torch.empty(n, dtype=torch.float32, device=dev)
+    out = torch.empty((BLOCK, n), dtype=torch.float32, device=dev)
+    pre = 80
+    for k in range(pre):
+        model.update(ds.draw(k, x))
+    model.sync()
+    k = pre
+    upd, pred, step = [], [], []
+    sampler = ClockSampler(0)
+    for it in range(args.warmup + args.steps):
+        timed = it >= args.warmup
+        if timed and it == args.warmup:
+            sampler.start()
+            model.profile(True)
+        st = 0.0
+        for i in range(BLOCK):
+            ds.draw(k + i, x)
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            model.update(x)
+            b.record(stream)
+            b.synchronize()
+            if timed:
+                upd.append(a.elapsed_time(b))
+            st += a.elapsed_time(b)
+        k += BLOCK
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        model.predict([float(k + h) for h in range(BLOCK)], out=out)
+        b.record(stream)
+        b.synchronize()
+        if timed:
+            pred.append(a.elapsed_time(b))
+            step.append(st + a.elapsed_time(b))
+    clocks = sampler.stop()
+    prof = model.profile_read()
+    model.profile(False)
+    hbm, peak_kind = _peaks()
+    K = args.steps
+    pa_ms = prof["pass_a"][0] / (K * BLOCK)
+    bytes_pa = n * prof["mean_r0"] * 4 + 2 * n * 4
+    line = {
+        "metric": METRIC, "value": BLOCK * K / (sum(step) / 1e3), "unit": "snapshot updates/s", "n_gpus": 1,
+        "steps": K, "warmup": args.warmup, "ms_per_step": sum(step) / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 basis (compensated accumulation) + double-float small solves",
+        "data": "synthetic (fields and coefficients of the wake generator, drawn on the device)",
+        "config": {"workload": f"cylinder-wake field 2048x1024x3 (n={n}), r_max={r_max}, FP32 storage, "
+                               f"{BLOCK}-snapshot blocks: {BLOCK} updates + {BLOCK}-state rollout",
+                   "n": n, "r_max": r_max, "slack": SLACK, "pretrain": pre,
+                   "l2": "256 MiB buffer written before every update/predict (untimed)"},
+        "rollout_states_per_s": BLOCK * K / (sum(pred) / 1e3),
+        "latency_ms": {"update_p50": float(np.percentile(upd, 50)), "update_p99": float(np.percentile(upd, 99))},
+        "mean_r0": prof["mean_r0"],
+        "roofline": {"kernel": "pass_a", "bound": "hbm", "achieved": bytes_pa / (pa_ms * 1e-3) / 1e9, "peak": hbm,
+                     "unit": "GB/s", "frac": bytes_pa / (pa_ms * 1e-3) / 1e9 / hbm, "traffic": None,
+                     "peak_kind": peak_kind, "bytes_per_launch": bytes_pa, "ms_per_launch": pa_ms},
+        "kernel_ms_per_step": {c: prof[c][0] / K for c in ("pass_a", "small", "pass_b", "eig", "coef", "rollout")},
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    model.close()
+
+
+def run_batched(args) -> None:
+    """64 independent instances, n uniform in [50k, 2M], r_max uniform in {8..64}, FP32
+    storage, each a random planted-mode stream (2-8 pairs, noise std 1e-8) on its own CUDA
+    stream; a step is one odmd_update_batch over all instances."""
+    import torch
+
+    import paper_2311_18715_gb300 as pkg
+    from synth import RandomPlanted
+
+    dev = torch.device("cuda", 0)
+    pkg.build()
+    rng = np.random.default_rng(0)
+    count = 64
+    ns = rng.integers(50_000, 2_000_001, count)
+    rs = rng.integers(8, 65, count)
+    streams, models, bufs = [], [], []
+    for i in range(count):
+        gen = RandomPlanted(int(ns[i]), seed=100 + i)
+        streams.append(DeviceStream(gen, dev, torch.float32))
+        models.append(pkg.OnlineDMD(int(ns[i]), int(rs[i]), prec="fp32", slack=16, trunc_tol=TAU,
+                                    stream=torch.cuda.Stream()))
+        bufs.append(torch.empty(int(ns[i]), dtype=torch.float32, device=dev))
+    pre = 70
+    for k in range(pre):
+        for s, b in zip(streams, bufs):
+            s.draw(k, b)
+        torch.cuda.synchronize()
+        pkg.update_batch(models, bufs)
+    for m in models:
+        m.sync()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    join = torch.cuda.current_stream()
+    times = []
+    sampler = ClockSampler(0)
+    k = pre
+    for it in range(args.warmup + args.steps):
+        for s, b in zip(streams, bufs):
+            s.draw(k, b)
+        flush.zero_()
+        torch.cuda.synchronize()
+        a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if it == args.warmup:
+            sampler.start()
+        a.record(join)
+        for m in models:
+            m.stream.wait_event(a)
+        pkg.update_batch(models, bufs)
+        for m in models:
+            e = torch.cuda.Event()
+            e.record(m.stream)
+            join.wait_event(e)
+        b_.record(join)
+        b_.synchronize()
+        if it >= args.warmup:
+            times.append(a.elapsed_time(b_))
+        k += 1
+    clocks = sampler.stop()
+    r0 = [m.rank for m in models]
+    hbm, peak_kind = _peaks()
+    step_ms = float(np.mean(times))
+    # pass A streams each basis once per update (FP32: 4 bytes per element) and two snapshots
+    bytes_step = float(sum(int(n) * (int(r) * 4 + 8) for n, r in zip(ns, r0)))
+    line = {
+        "metric": METRIC, "value": count / (step_ms * 1e-3), "unit": "snapshot updates/s (sum over instances)",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 basis (compensated accumulation) + double-float small solves",
+        "data": "synthetic (random planted-mode streams drawn on the device)",
+        "config": {"workload": f"{count} instances, n in [50k, 2M], r_max in [8, 64], FP32 storage, one "
+                               "odmd_update_batch per step, each instance on its own stream",
+                   "instances": count, "sum_n": int(ns.sum()), "pretrain": pre,
+                   "l2": "256 MiB buffer written before every step (untimed)"},
+        "latency_ms": {"step_p50": float(np.percentile(times, 50)), "step_p99": float(np.percentile(times, 99))},
+        "roofline": {"kernel": "update step (all instances)", "bound": "hbm", "achieved": bytes_step / (step_ms * 1e-3) / 1e9,
+                     "peak": hbm, "unit": "GB/s", "frac": bytes_step / (step_ms * 1e-3) / 1e9 / hbm, "traffic": None,
+                     "peak_kind": peak_kind, "bytes_per_step": bytes_step,
+                     "note": "pass-A bytes of every instance at its current rank over the whole step time"},
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    for m in models:
+        m.close()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -441,6 +632,8 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="untimed short run of the same kernels, for ncu captures")
     ap.add_argument("--profile-updates", type=int, default=64)
+    ap.add_argument("--config", choices=["wake", "fp32-large", "batched"], default="wake",
+                    help="wake: the headline workload; fp32-large and batched: extra measured configurations")
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args)
@@ -449,6 +642,10 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "fp32-large":
+        run_fp32_large(args)
+    elif args.config == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 

@@ -1437,13 +1437,16 @@ __global__ void __launch_bounds__(64) k_basis_coef(Ws ws) {
 }
 
 // ---------------------------------------------------------------------------------------
-static int prep_smem(const Ws& ws) {
-  const int qld = ws.cap + 1;
+static int prep_smem_cap(int cap) {
+  const int qld = cap + 1;
   return (int)sizeof(float2) * (qld * kMaxR + 4 * qld + 2 * kMaxN);
 }
+static int prep_smem(const Ws& ws) { return prep_smem_cap(ws.cap); }
 
-cudaError_t prepare_small(const Ws& ws) {
-  cudaError_t e = cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, prep_smem(ws));
+// The shared-memory limit is a property of the kernel, shared by every handle in the
+// process: set it for the largest cap any handle can have.
+cudaError_t prepare_small(const Ws&) {
+  cudaError_t e = cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, prep_smem_cap(kMaxCap));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(EigSmem));
 }

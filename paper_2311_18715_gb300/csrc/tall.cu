@@ -1222,30 +1222,44 @@ static cudaError_t prep_attr(K kern, int bytes) {
   return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
+// Largest dynamic shared memory a kernel of this precision needs over every cap a handle
+// can have (pass A's ring depth varies with the row width, so the largest cap is not
+// always the largest request)
+template <typename F>
+static int max_over_caps(F f) {
+  int m = 0;
+  for (int cap = 1; cap <= kMaxCap; ++cap) m = f(cap) > m ? f(cap) : m;
+  return m;
+}
+
 // Raise the dynamic shared-memory limit of every tall kernel once (not inside launches,
-// which may be captured into a graph).
+// which may be captured into a graph).  The limit is a property of the kernel, shared by
+// every handle in the process, so it is set for every cap a handle can have.
 cudaError_t prepare_tall(const Ws& ws) {
-  const int cap = ws.cap;
+  const int p = ws.prec;
+  const int sa = max_over_caps([p](int c) { return smem_a(p, c); });
+  const int sb = max_over_caps([p](int c) { return smem_b(p, c); });
+  const int sr = max_over_caps([p](int c) { return smem_r(p, c); });
   cudaError_t e = cudaSuccess;
-  switch (ws.prec) {
+  switch (p) {
     case ST_DD:
-      if ((e = prep_attr(k_pass_a<ST_DD>, smem_a(ST_DD, cap)))) return e;
-      if ((e = prep_attr(k_pass_b<ST_DD, false>, smem_b(ST_DD, cap)))) return e;
-      if ((e = prep_attr(k_pass_b<ST_DD, true>, smem_b(ST_DD, cap)))) return e;
-      if ((e = prep_attr(k_rollout<ST_DD, false>, smem_r(ST_DD, cap)))) return e;
-      return prep_attr(k_rollout<ST_DD, true>, smem_r(ST_DD, cap));
+      if ((e = prep_attr(k_pass_a<ST_DD>, sa))) return e;
+      if ((e = prep_attr(k_pass_b<ST_DD, false>, sb))) return e;
+      if ((e = prep_attr(k_pass_b<ST_DD, true>, sb))) return e;
+      if ((e = prep_attr(k_rollout<ST_DD, false>, sr))) return e;
+      return prep_attr(k_rollout<ST_DD, true>, sr);
     case ST_F32:
-      if ((e = prep_attr(k_pass_a<ST_F32>, smem_a(ST_F32, cap)))) return e;
-      if ((e = prep_attr(k_pass_b<ST_F32, false>, smem_b(ST_F32, cap)))) return e;
-      if ((e = prep_attr(k_pass_b<ST_F32, true>, smem_b(ST_F32, cap)))) return e;
-      if ((e = prep_attr(k_rollout<ST_F32, false>, smem_r(ST_F32, cap)))) return e;
-      return prep_attr(k_rollout<ST_F32, true>, smem_r(ST_F32, cap));
+      if ((e = prep_attr(k_pass_a<ST_F32>, sa))) return e;
+      if ((e = prep_attr(k_pass_b<ST_F32, false>, sb))) return e;
+      if ((e = prep_attr(k_pass_b<ST_F32, true>, sb))) return e;
+      if ((e = prep_attr(k_rollout<ST_F32, false>, sr))) return e;
+      return prep_attr(k_rollout<ST_F32, true>, sr);
     default:
-      if ((e = prep_attr(k_pass_a<ST_BF16>, smem_a(ST_BF16, cap)))) return e;
-      if ((e = prep_attr(k_pass_b<ST_BF16, false>, smem_b(ST_BF16, cap)))) return e;
-      if ((e = prep_attr(k_pass_b<ST_BF16, true>, smem_b(ST_BF16, cap)))) return e;
-      if ((e = prep_attr(k_rollout<ST_BF16, false>, smem_r(ST_BF16, cap)))) return e;
-      return prep_attr(k_rollout<ST_BF16, true>, smem_r(ST_BF16, cap));
+      if ((e = prep_attr(k_pass_a<ST_BF16>, sa))) return e;
+      if ((e = prep_attr(k_pass_b<ST_BF16, false>, sb))) return e;
+      if ((e = prep_attr(k_pass_b<ST_BF16, true>, sb))) return e;
+      if ((e = prep_attr(k_rollout<ST_BF16, false>, sr))) return e;
+      return prep_attr(k_rollout<ST_BF16, true>, sr);
   }
 }
 

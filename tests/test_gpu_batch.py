@@ -23,6 +23,9 @@ def test_batch_calls_equal_single_calls():
     torch.cuda.synchronize()
     batch = [pkg.OnlineDMD(n, r, slack=4, stream=torch.cuda.Stream()) for n, r in SHAPES]
     single = [pkg.OnlineDMD(n, r, slack=4) for n, r in SHAPES]
+    # a small instance created last: the kernels' shared-memory limits are per process, so
+    # creating it must not shrink what the larger instances above need
+    tiny = pkg.OnlineDMD(100, 2, slack=0)
     for k in range(steps):
         pkg.update_batch(batch, [d[k] for d in data])
         for m, d in zip(single, data):
@@ -34,6 +37,7 @@ def test_batch_calls_equal_single_calls():
         assert m.rank == s.rank
         assert np.array_equal(np.array(m.singular_values()), np.array(s.singular_values()))
         assert torch.equal(g, s.predict(t))
+    tiny.close()
     ref = OnlineDMDRef(SHAPES[2][0], SHAPES[2][1], 1e-10)
     for k in range(steps):
         ref.update(data[2][k].cpu().numpy())
