@@ -442,22 +442,29 @@ __global__ void __launch_bounds__(32) k_roots(Ws ws) {
     // with the neighbouring poles at a = A - mu and b = B - mu and the unknown d = x - mu.
     const float fh = f.h;
     const float a = (A - mu).h;
+    const float b = last ? 0.f : (B - mu).h;
+    // the unknown is scaled by a power of two so that the model's coefficients stay inside
+    // the FP32 exponent range: offsets between clustered tiny singular values square to
+    // 1e-23 and their products to 1e-46, below the smallest float
+    int ex = 0;
+    frexpf(fmaxf(fabsf(a), fabsf(b)), &ex);
+    const float sc = ldexpf(1.f, ex), as = ldexpf(a, -ex), bs = ldexpf(b, -ex);
+    const float ps = dpsi * sc, hs = dphi * sc;
     float delta;
     if (!last) {
-      const float b = (B - mu).h;
-      const float Qa = fh - dpsi * a - dphi * b;
-      const float Qb = a * b * (dpsi + dphi) - fh * (a + b);
-      const float Qc = fh * a * b;
+      const float Qa = fh - ps * as - hs * bs;
+      const float Qb = as * bs * (ps + hs) - fh * (as + bs);
+      const float Qc = fh * as * bs;
       const float disc = fmaxf(Qb * Qb - 4.f * Qa * Qc, 0.f);
       const float q = -0.5f * (Qb >= 0.f ? Qb + sqrtf(disc) : Qb - sqrtf(disc));
       const float d2 = q != 0.f ? Qc / q : 0.f;  // the root that tends to -f / f'
       const float d1 = Qa != 0.f ? q / Qa : d2;
-      const float lo_s = (lo - mu).h, hi_s = (hi - mu).h;
+      const float lo_s = ldexpf((lo - mu).h, -ex), hi_s = ldexpf((hi - mu).h, -ex);
       const bool in2 = d2 > lo_s && d2 < hi_s, in1 = d1 > lo_s && d1 < hi_s;
-      delta = in2 ? d2 : (in1 ? d1 : d2);
+      delta = ldexpf(in2 ? d2 : (in1 ? d1 : d2), ex);
     } else {
-      const float den = fh - dpsi * a;
-      delta = den != 0.f ? fh * a / den : 0.f;
+      const float den = fh - ps * as;
+      delta = den != 0.f ? ldexpf(fh * as / den, ex) : 0.f;
     }
     dd x = mu + dd_of(delta);
     if (!isfinite(delta) || !(dd_gt(x, lo) && dd_lt(x, hi))) x = (lo + hi) * 0.5f;

@@ -217,3 +217,28 @@ def test_edge_cases():
     mm.update(torch.zeros(10, dtype=torch.float64, device=dev))
     with pytest.raises(pkg.OdmdError):
         mm.check(1.0, torch.zeros(10, dtype=torch.float64, device=dev))
+
+
+def test_clustered_tiny_singular_values():
+    """A random planted-mode stream whose noise singular values sit ~1e-10 below the
+    largest, packed with relative gaps ~1e-4: offsets between such poles square to 1e-23,
+    and a secular-equation step formed in FP32 without rescaling underflowed and stalled.
+    The stream is drawn on the device (noise from torch's seeded generator) and handed to
+    the oracle as the same bytes."""
+    n, r_max = 1637390, 34
+    gen = RandomPlanted(n, seed=1010)
+    fields = torch.from_numpy(gen.fields).cuda()
+    g = torch.Generator(device="cuda")
+    X = []
+    for k in range(125):
+        c = torch.from_numpy(np.asarray(gen.coefficients(k))).cuda()
+        g.manual_seed(1_000_003 * (gen.seed + 1) + k)
+        X.append(c @ fields + gen.sigma * torch.randn(n, generator=g, device="cuda", dtype=torch.float64))
+    X = torch.stack(X).cpu().numpy()
+    del fields
+    m, ref = run_pair(X, r_max, slack=16)
+    assert m.rank == ref.rank
+    np.testing.assert_allclose(m.singular_values(), ref.S, rtol=0, atol=1e-10 * ref.S[0])
+    got = m.predict([125.0]).cpu().numpy()
+    want = ref.predict([125.0]).T
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-9
