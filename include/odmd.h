@@ -72,7 +72,8 @@ typedef struct {
                            singular values <= tau*sigma_1 are dropped.  1e-13 <= tau < 1 */
   double check_tol;     /* default tolerance of odmd_check (Sec. 3 uses 1e-5) */
   odmd_precision prec;  /* basis storage, see above */
-  int32_t refine_every; /* re-orthonormalise L0 every this many compactions (0: never) */
+  int32_t refine_every; /* refine orthogonality after every this many pairs (0: never);
+                           see odmd_refine */
   uint32_t flags;       /* reserved, must be 0 */
 } odmd_config;
 
@@ -136,6 +137,17 @@ odmd_status odmd_hybrid_step(odmd_t h, const void* x_fom_dev, double tol, void* 
 odmd_status odmd_update_batch(odmd_t* hs, const void* const* xs, int32_t count);
 odmd_status odmd_predict_batch(odmd_t* hs, const double* const* ts, const int32_t* ks, void* const* outs,
                                const int64_t* lds, int32_t count);
+
+/* Orthogonality refinement (no counterpart in the paper: it keeps L^T L = I over long
+ * streams, where rounding in every rank-1 update lets it drift, most of all with FP32
+ * storage).  One pass over the basis forms C = L^T L; with C = R^T R (Cholesky) and
+ * R diag(S) = U_s Sigma V_s^T the basis becomes L R^-1 U_s, orthonormal to working
+ * accuracy, and S, the rows of the right factor and the reduced operator are rotated to
+ * match, so the factorisation of the snapshots and the span of L are unchanged.  Runs
+ * automatically after every refine_every-th snapshot pair when refine_every > 0 (which
+ * also reserves its scratch in the workspace); otherwise this call returns
+ * ODMD_ERR_STATE.  Asynchronous. */
+odmd_status odmd_refine(odmd_t h);
 
 /* Wait for the handle's stream and report any recorded device-side error. */
 odmd_status odmd_sync(odmd_t h);

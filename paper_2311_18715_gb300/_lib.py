@@ -16,7 +16,7 @@ EXPORTED = [
     "odmd_check", "odmd_sync", "odmd_get_rank", "odmd_get_singular_values", "odmd_get_eigs",
     "odmd_get_basis", "odmd_get_counts", "odmd_destroy", "odmd_last_error",
     "odmd_profile_enable", "odmd_profile_read", "odmd_check_noalloc", "odmd_hybrid_step",
-    "odmd_update_batch", "odmd_predict_batch",
+    "odmd_update_batch", "odmd_predict_batch", "odmd_refine",
 ]
 KERNEL_CLASSES = ["pass_a", "small", "pass_b", "eig", "coef", "rollout", "check", "first"]
 
@@ -64,6 +64,7 @@ def load_library(path: str | None = None) -> C.CDLL:
         "odmd_check_noalloc": [vp, vp, i64, dbl, vp, C.POINTER(dbl), C.POINTER(i32)],
         "odmd_hybrid_step": [vp, vp, dbl, vp, C.POINTER(i32), C.POINTER(dbl)],
         "odmd_update_batch": [C.POINTER(vp), C.POINTER(vp), i32],
+        "odmd_refine": [vp],
         "odmd_predict_batch": [C.POINTER(vp), C.POINTER(C.POINTER(dbl)), C.POINTER(i32), C.POINTER(vp),
                                C.POINTER(i64), i32],
         "odmd_sync": [vp],

@@ -66,6 +66,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Layout {
   size_t total;
+  size_t off_gpart = 0, off_rscr = 0;  // refinement scratch (refine_every > 0 only)
   size_t off_ctl, off_hdr[2], off_state[2], off_small, off_eig, off_out2, off_part, off_Lh, off_Ll, off_c[2],
       off_x, off_e, off_maps;
   size_t state_doubles, small_bytes, eig_doubles;
@@ -152,6 +153,11 @@ Layout make_layout(const odmd_config& c) {
   L.off_eig = take(L.eig_doubles * sizeof(float2));
   L.off_out2 = take(8 * 8);
   L.off_part = take((size_t)L.partrows * (2 * L.cap + 3) * sizeof(float2));
+  if (c.refine_every > 0) {
+    L.off_gpart = take((size_t)kGramCtas * L.cap * (L.cap + 1) / 2 * sizeof(float2));
+    L.off_rscr = take(((size_t)L.cap * L.cap + (size_t)L.cap * L.rmax + 6 * (size_t)L.rmax * L.rmax + 2 * (size_t)L.rmax) *
+                      sizeof(float2));
+  }
   const size_t plane = (size_t)L.npad * L.ldg * esz_of(c.prec);
   L.off_Lh = take(plane);
   L.off_Ll = c.prec == ODMD_FP64 ? take(plane) : 0;
@@ -261,6 +267,8 @@ void carve(Ws& ws, const Layout& L, unsigned char* base, const odmd_config& c, i
   ws.eig.Vim = e;
   ws.out2 = reinterpret_cast<float2*>(base + L.off_out2);
   ws.part = reinterpret_cast<float2*>(base + L.off_part);
+  ws.gpart = L.off_gpart ? reinterpret_cast<float2*>(base + L.off_gpart) : nullptr;
+  ws.rscr = L.off_rscr ? reinterpret_cast<float2*>(base + L.off_rscr) : nullptr;
   ws.Lh = base + L.off_Lh;
   ws.Ll = c.prec == ODMD_FP64 ? reinterpret_cast<float*>(base + L.off_Ll) : nullptr;
   ws.cbuf[0] = base + L.off_c[0];
@@ -650,6 +658,8 @@ odmd_status odmd_update(odmd_t h, const void* x_dev) {
   h->curc_h ^= 1;
   h->nsnap += 1;
   h->eig_dirty = true;
+  // periodic orthogonality refinement, every refine_every snapshot pairs
+  if (h->cfg.refine_every > 0 && (h->nsnap - 1) % h->cfg.refine_every == 0) return odmd_refine(h);
   return ODMD_OK;
 }
 
@@ -706,6 +716,17 @@ odmd_status odmd_check(odmd_t h, double t, const void* x_fom_dev, double tol, do
     err = std::sqrt(num / den);
   if (rel_err) *rel_err = err;
   if (pass) *pass = err <= tol ? 1 : 0;
+  return ODMD_OK;
+}
+
+odmd_status odmd_refine(odmd_t h) {
+  if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
+  if (!h->ws.gpart) return fail(h, ODMD_ERR_STATE, "refinement scratch not reserved: create with refine_every > 0");
+  if (h->nsnap < 2) return ODMD_OK;  // no basis yet
+  if (odmd_status s = flush_pending(h)) return s;
+  CK(h, launch_refine(h->ws, h->stream), "refine launch");
+  h->cur_h ^= 1;
+  h->eig_dirty = true;
   return ODMD_OK;
 }
 

@@ -27,6 +27,7 @@ constexpr int kMaxCap = kMaxR + kMaxSlack;  // largest number of basis columns r
 constexpr int kMaxN = kMaxR + 1;   // largest core matrix order r + 1
 constexpr int kMaxMaps = 13;       // tensor maps per plane: box widths of 1, 3, ..., 25 chunks
 constexpr int kRollK = 64;         // horizons (columns) per rollout launch
+constexpr int kGramCtas = 128;     // CTAs of the Gram pass of the orthogonality refinement
 
 enum Storage { ST_DD = 0, ST_F32 = 1, ST_BF16 = 2 };
 
@@ -156,6 +157,8 @@ struct Ws {
   const CUtensorMap* maps;  // [plane][k]: 2-D tile maps of the basis planes, box of
                             // (2k+1) chunks x kTile rows; plane 1 only in FP64 mode
   float2* part;     // per-CTA partial sums: gridA x (2*cap+3)
+  float2* gpart;    // refinement: per-CTA Gram partials, kGramCtas x cap(cap+1)/2 (or null)
+  float2* rscr;     // refinement: small matrices (or null)
   StateBuf st[2];
   Small sm;
   Eig eig;
@@ -426,6 +429,7 @@ int tall_smem_bytes(int prec);
 int stages_a(int prec, int cap);  // pass A pipeline depth for this storage format and cap
 // small.cu
 cudaError_t launch_small(const Ws& ws, cudaStream_t s);
+cudaError_t launch_refine(const Ws& ws, cudaStream_t s);  // Gram pass + small refinement
 cudaError_t launch_eig(const Ws& ws, cudaStream_t s);
 cudaError_t launch_coef(const Ws& ws, const double* t_host, int k, cudaStream_t s);  // k <= kRollK, t on the host
 cudaError_t launch_basis_coef(const Ws& ws, cudaStream_t s);

@@ -109,6 +109,10 @@ class OnlineDMD:
                                             C.c_void_p(out.data_ptr()), C.byref(acc), C.byref(err)))
         return out, bool(acc.value), float(err.value)
 
+    def refine(self) -> None:
+        """odmd_refine: restore L^T L = I now (needs refine_every > 0 at construction)."""
+        self._ck(self._lib.odmd_refine(self._h))
+
     def sync(self) -> None:
         self._ck(self._lib.odmd_sync(self._h))
 

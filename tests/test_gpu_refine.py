@@ -1,0 +1,88 @@
+"""Orthogonality refinement (odmd_refine; refine_every > 0 runs it periodically).
+
+What it must preserve and restore: the span of L (projector difference at rounding level),
+the singular values, the predictions; and L^T L = I to working accuracy afterwards.  With
+FP32 storage, where the drift is largest, the refined run must be at least as orthogonal
+as the plain one and still match the FP64 oracle at the FP32 bars."""
+import numpy as np
+import pytest
+
+from oracle import OnlineDMDRef
+from synth import PlantedModes, WakeField
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _run(X, r_max, slack, prec, refine_every):
+    import paper_2311_18715_gb300 as pkg
+
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    m = pkg.OnlineDMD(X.shape[1], r_max, prec=prec, slack=slack, refine_every=refine_every)
+    Xd = torch.from_numpy(X).cuda().to(dt)
+    for k in range(X.shape[0]):
+        m.update(Xd[k])
+    m.sync()
+    return m, Xd
+
+
+def _orth(m):
+    L = m.basis().double().cpu().numpy().T
+    return L, float(np.max(np.abs(L.T @ L - np.eye(L.shape[1]))))
+
+
+def _signal_projector(L, p):
+    # columns come sorted by singular value; the first p span the planted (signal) modes,
+    # well separated from the noise directions, whose span rounding may rotate
+    return L[:, :p] @ L[:, :p].T
+
+
+def test_refinement_preserves_the_model_fp64():
+    X = PlantedModes(4096, sigma=1e-8, seed=0).snapshots(0, 150)   # planted rank 6
+    a, _ = _run(X, 10, 4, "fp64", 0)
+    b, _ = _run(X, 10, 4, "fp64", 7)
+    La, oa = _orth(a)
+    Lb, ob = _orth(b)
+    # Gram sums over n = 4096 rows: rounding of order sqrt(n) * eps, plus the two CGS2
+    # appends after the last periodic refinement
+    assert ob <= 1e-13, (oa, ob)
+    assert np.max(np.abs(_signal_projector(La, 6) - _signal_projector(Lb, 6))) <= 1e-12
+    Sa = np.array(a.singular_values())
+    np.testing.assert_allclose(b.singular_values(), Sa, rtol=0, atol=1e-10 * Sa[0])
+    ts = [0.0, 75.5, 149.0, 180.0]
+    pa, pb = a.predict(ts).cpu().numpy(), b.predict(ts).cpu().numpy()
+    assert np.linalg.norm(pa - pb) / np.linalg.norm(pa) <= 1e-9
+    # an explicit call on top of the periodic ones changes nothing beyond rounding
+    b.refine()
+    np.testing.assert_allclose(b.singular_values(), Sa, rtol=0, atol=1e-10 * Sa[0])
+    Lc, oc = _orth(b)
+    assert oc <= 1e-13
+    assert np.max(np.abs(_signal_projector(Lc, 6) - _signal_projector(Lb, 6))) <= 1e-12
+    pc = b.predict(ts).cpu().numpy()
+    assert np.linalg.norm(pc - pb) / np.linalg.norm(pb) <= 1e-9
+
+
+def test_refinement_fp32_storage_against_oracle():
+    X = WakeField(64, 32, sigma=1e-6, seed=0).snapshots(0, 300)
+    plain, _ = _run(X, 16, 16, "fp32", 0)
+    refd, Xd = _run(X, 16, 16, "fp32", 10)
+    _, o_plain = _orth(plain)
+    _, o_ref = _orth(refd)
+    assert o_ref <= max(o_plain, 1e-7)
+    ref = OnlineDMDRef(X.shape[1], 16, 1e-10)
+    for k in range(X.shape[0]):
+        ref.update(Xd[k].double().cpu().numpy())
+    S = np.array(refd.singular_values())
+    assert np.max(np.abs(S - ref.S)) <= 1e-6 * ref.S[0]
+    ts = [300.0, 320.0]
+    got = refd.predict(ts).double().cpu().numpy()
+    want = ref.predict(ts).T
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) <= 1e-5
+
+
+def test_refine_needs_reserved_scratch():
+    import paper_2311_18715_gb300 as pkg
+
+    m = pkg.OnlineDMD(100, 4)
+    with pytest.raises(pkg.OdmdError):
+        m.refine()
