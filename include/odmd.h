@@ -181,7 +181,8 @@ typedef enum {
   ODMD_K_ROLLOUT = 5,  /* tall rollout pass (predict, basis export) */
   ODMD_K_CHECK = 6,    /* tall fused credibility-check pass */
   ODMD_K_FIRST = 7,    /* norm of the first snapshot */
-  ODMD_K_COUNT = 8
+  ODMD_K_REFINE = 8,   /* orthogonality refinement (Gram pass + 4 small kernels) */
+  ODMD_K_COUNT = 9
 } odmd_kernel_class;
 
 /* Observability: when enabled (nonzero), every kernel group the handle enqueues is

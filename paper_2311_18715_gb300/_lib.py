@@ -18,7 +18,7 @@ EXPORTED = [
     "odmd_profile_enable", "odmd_profile_read", "odmd_check_noalloc", "odmd_hybrid_step",
     "odmd_update_batch", "odmd_predict_batch", "odmd_refine",
 ]
-KERNEL_CLASSES = ["pass_a", "small", "pass_b", "eig", "coef", "rollout", "check", "first"]
+KERNEL_CLASSES = ["pass_a", "small", "pass_b", "eig", "coef", "rollout", "check", "first", "refine"]
 
 
 class OdmdConfig(C.Structure):

@@ -155,8 +155,7 @@ Layout make_layout(const odmd_config& c) {
   L.off_part = take((size_t)L.partrows * (2 * L.cap + 3) * sizeof(float2));
   if (c.refine_every > 0) {
     L.off_gpart = take((size_t)kGramCtas * L.cap * (L.cap + 1) / 2 * sizeof(float2));
-    L.off_rscr = take(((size_t)L.cap * L.cap + (size_t)L.cap * L.rmax + 6 * (size_t)L.rmax * L.rmax + 2 * (size_t)L.rmax) *
-                      sizeof(float2));
+    L.off_rscr = take(((size_t)L.cap * L.cap + 3 * (size_t)L.rmax * L.rmax + 2 * (size_t)L.rmax + 2) * sizeof(float2));
   }
   const size_t plane = (size_t)L.npad * L.ldg * esz_of(c.prec);
   L.off_Lh = take(plane);
@@ -559,9 +558,12 @@ odmd_status odmd_create(const odmd_config* cfg, void* workspace_dev, size_t byte
     int g = (int)(tiles32 < sms ? tiles32 : sms);
     if (g > kPartRows) g = kPartRows;
     h->ws.gridPA = g < 1 ? 1 : g;
+    h->ws.gridG = 2 * sms < kGramCtas ? 2 * sms : kGramCtas;
+    if (h->ws.gridG < 1) h->ws.gridG = 1;
   }
   if (e == cudaSuccess) e = prepare_tall(h->ws);
   if (e == cudaSuccess) e = prepare_small(h->ws);
+  if (e == cudaSuccess && cfg->refine_every > 0) e = prepare_refine();
   if (e == cudaSuccess) e = cudaMemsetAsync(workspace_dev, 0, L.total, h->stream);
   if (e == cudaSuccess) {
     if (encode_maps(h, L) != ODMD_OK) {
@@ -724,7 +726,10 @@ odmd_status odmd_refine(odmd_t h) {
   if (!h->ws.gpart) return fail(h, ODMD_ERR_STATE, "refinement scratch not reserved: create with refine_every > 0");
   if (h->nsnap < 2) return ODMD_OK;  // no basis yet
   if (odmd_status s = flush_pending(h)) return s;
-  CK(h, launch_refine(h->ws, h->stream), "refine launch");
+  {
+    ProfScope ps(h, ODMD_K_REFINE, 5);
+    CK(h, launch_refine(h->ws, h->cur_h, h->stream), "refine launch");
+  }
   h->cur_h ^= 1;
   h->eig_dirty = true;
   return ODMD_OK;

@@ -27,7 +27,7 @@ constexpr int kMaxCap = kMaxR + kMaxSlack;  // largest number of basis columns r
 constexpr int kMaxN = kMaxR + 1;   // largest core matrix order r + 1
 constexpr int kMaxMaps = 13;       // tensor maps per plane: box widths of 1, 3, ..., 25 chunks
 constexpr int kRollK = 64;         // horizons (columns) per rollout launch
-constexpr int kGramCtas = 128;     // CTAs of the Gram pass of the orthogonality refinement
+constexpr int kGramCtas = 304;     // most CTAs of the Gram pass of the orthogonality refinement
 
 enum Storage { ST_DD = 0, ST_F32 = 1, ST_BF16 = 2 };
 
@@ -147,6 +147,7 @@ struct Ws {
   int rmax, cap, ldg, prec, gridA;
   int stagesA;      // TMA pipeline depth of pass A (as many stages as shared memory holds)
   int gridPA;       // pass A grid: one CTA per SM, at most one per 32-row tile
+  int gridG;        // Gram pass grid: two CTAs per SM, at most kGramCtas
   float tau_h, tau_l;  // truncation tolerance as a double-float
   Ctl* ctl;
   void* Lh;         // hi plane (float) / bf16 plane
@@ -429,7 +430,8 @@ int tall_smem_bytes(int prec);
 int stages_a(int prec, int cap);  // pass A pipeline depth for this storage format and cap
 // small.cu
 cudaError_t launch_small(const Ws& ws, cudaStream_t s);
-cudaError_t launch_refine(const Ws& ws, cudaStream_t s);  // Gram pass + small refinement
+cudaError_t prepare_refine();
+cudaError_t launch_refine(const Ws& ws, int cur, cudaStream_t s);  // Gram pass + small refinement
 cudaError_t launch_eig(const Ws& ws, cudaStream_t s);
 cudaError_t launch_coef(const Ws& ws, const double* t_host, int k, cudaStream_t s);  // k <= kRollK, t on the host
 cudaError_t launch_basis_coef(const Ws& ws, cudaStream_t s);

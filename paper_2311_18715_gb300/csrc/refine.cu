@@ -2,9 +2,11 @@
 // the invariant L^T L = I over long streams (rounding in every rank-1 update lets it drift,
 // most of all with FP32 storage of L0).
 //
-//   C = L^T L = Q^T (L0^T L0) Q           (k_gram: the Gram matrix of L0, one pass over N)
+//   C = L^T L = Q^T (L0^T L0) Q           (k_gram + k_gram_sum: the Gram matrix of L0, one
+//                                          pass over N; k_refine_c: the two small products)
 //   C = R^T R                              (Cholesky, R upper triangular)
-//   R diag(S) = U_s Sigma V_s^T            (one-sided Jacobi SVD; R ~ I so one or two sweeps)
+//   R diag(S) = U_s Sigma V_s^T            (one-sided Jacobi SVD; R ~ I, so one sweep rotates
+//                                          and a second confirms)
 //
 // and, since U^- ~ L S W^T = (L R^-1)(R S) W^T = (L R^-1 U_s) Sigma (W V_s)^T,
 //
@@ -12,21 +14,34 @@
 //   M <- (R^-1 U_s)^T M V_s                (M = L^T U^+ W with the new L and W)
 //
 // L0 itself is not rewritten; the carried projection a = L0^T c and the coefficients of a
-// pending column are in L0 coordinates and stay as they are.  Both kernels work in
-// double-float arithmetic.
+// pending column are in L0 coordinates and stay as they are.  All arithmetic is
+// double-float.  The state moves to the other state buffer like an update does, so the
+// host's mirror of the committed buffer flips once per call whatever happens: when the
+// rank is still 0 or the Cholesky factorisation fails (a non-positive pivot sets
+// DEV_NONFINITE), the state is copied unchanged.
 #include "dd.cuh"
 #include "odmd_internal.cuh"
 
 namespace odmd {
 
+// ---------------------------------------------------------------- Gram pass G = L0^T L0
+// A CTA streams 32-row tiles of L0 through shared memory.  The upper triangle of G is cut
+// into 4 x 4 column blocks; a thread owns one block (two when there are more blocks than
+// threads) and, when there are few blocks, a residue class of the tile's rows, so every
+// thread has work for any r0.  A block is 16 double-float accumulations per row, done two
+// at a time by the FP32x2 instructions.
 constexpr int kGramThreads = 256;
 constexpr int kGramRows = 32;
-constexpr int kGramMaxPairs = (kMaxCap * (kMaxCap + 1) / 2 + kGramThreads - 1) / kGramThreads;
-constexpr int kRefineThreads = 256;
+constexpr int kGramLd = kMaxCap + 4;  // floats per shared row (rows stay 16-byte aligned)
+constexpr int kGramItems = 2;         // blocks per thread at most: ceil(B(B+1)/2 / 256), B = 24
+constexpr int kRefineThreads = 512;
+constexpr int kRefineLd = kMaxR;      // leading dimension of the small matrices in shared memory
+static_assert((kMaxCap / 4 + 1) * (kMaxCap / 4) / 2 <= kGramItems * kGramThreads, "Gram blocks per thread");
+static_assert(kMaxCap <= 128 && kMaxR <= 64, "refinement kernels size their CTAs for these limits");
 
 __device__ __forceinline__ int gram_pairs(int r0) { return r0 * (r0 + 1) / 2; }
-
-// pair p of the upper triangle (row-major: (0,0), (0,1), .., (0,r0-1), (1,1), ..) -> (i, k)
+// index of (i, k), i <= k, in the row-major upper triangle (0,0), (0,1), .., (0,r0-1), (1,1), ..
+__device__ __forceinline__ int gram_index(int i, int k, int r0) { return i * r0 - i * (i - 1) / 2 + (k - i); }
 __device__ __forceinline__ void gram_pair(int p, int r0, int& i, int& k) {
   i = 0;
   while (p >= r0 - i) {
@@ -36,310 +51,554 @@ __device__ __forceinline__ void gram_pair(int p, int r0, int& i, int& k) {
   k = i + p;
 }
 
+struct GramTile {
+  float h[kGramRows][kGramLd], l[kGramRows][kGramLd];
+};
+union GramSmem {
+  GramTile t;
+  float2 red[kGramThreads][16];
+};
+
 template <int ST>
-__device__ __forceinline__ void load_basis(const Ws& ws, size_t o, float& h, float& l) {
-  if constexpr (ST == ST_BF16) {
-    h = __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(ws.Lh)[o]);
-    l = 0.f;
+__device__ __forceinline__ void gram_row(Acc2 (&A)[8], const GramTile& t, int row, int bi, int bk) {
+  const float4 xh = *reinterpret_cast<const float4*>(&t.h[row][4 * bi]);
+  const float4 yh = *reinterpret_cast<const float4*>(&t.h[row][4 * bk]);
+  const f2x y0 = f2x_pack(yh.x, yh.y), y1 = f2x_pack(yh.z, yh.w);
+  const f2x ny0 = sub2(0ull, y0), ny1 = sub2(0ull, y1);
+  const float xs[4] = {xh.x, xh.y, xh.z, xh.w};
+  if constexpr (ST == ST_DD) {
+    const float4 xl = *reinterpret_cast<const float4*>(&t.l[row][4 * bi]);
+    const float4 yl = *reinterpret_cast<const float4*>(&t.l[row][4 * bk]);
+    const f2x l0 = f2x_pack(yl.x, yl.y), l1 = f2x_pack(yl.z, yl.w);
+    const float xls[4] = {xl.x, xl.y, xl.z, xl.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const f2x xb = f2x_pack(xs[i], xs[i]), xlb = f2x_pack(xls[i], xls[i]);
+      acc2_fma(A[2 * i], xb, xlb, y0, ny0, l0);
+      acc2_fma(A[2 * i + 1], xb, xlb, y1, ny1, l1);
+    }
   } else {
-    h = reinterpret_cast<const float*>(ws.Lh)[o];
-    l = (ST == ST_DD) ? ws.Ll[o] : 0.f;
+    // FP32 storage: the low parts are zero, so only the product's own rounding error
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const f2x xb = f2x_pack(xs[i], xs[i]);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const f2x y = h ? y1 : y0, ny = h ? ny1 : ny0;
+        Acc2& a = A[2 * i + h];
+        const f2x np = mul2(xb, ny);
+        const f2x pe = fma2(xb, y, np);
+        const f2x s = sub2(a.h, np);
+        const f2x bb = sub2(s, a.h);
+        const f2x e = sub2(sub2(a.h, sub2(s, bb)), add2(np, bb));
+        a.h = s;
+        a.l = add2(a.l, add2(e, pe));
+      }
+    }
   }
 }
 
-// G = L0^T L0 (upper triangle), per-CTA partial sums in fixed order, written to ws.gpart
-template <int ST>
-__global__ void __launch_bounds__(kGramThreads) k_gram(Ws ws) {
-  const int r0 = ws.st[ws.ctl->cur].hdr->r0;
-  const int np = gram_pairs(r0);
-  const int tid = threadIdx.x;
-  __shared__ float th[kGramRows][kMaxCap + 1], tl[kGramRows][kMaxCap + 1];
-  int pi[kGramMaxPairs], pk[kGramMaxPairs];
-  Acc acc[kGramMaxPairs];
+__device__ __forceinline__ void acc2_renorm(Acc2& a) {
+  const f2x s = add2(a.h, a.l);
+  a.l = sub2(a.l, sub2(s, a.h));
+  a.h = s;
+}
+
+// element e = 4 i + 2 h + lane of a block: row 4 bi + i, column 4 bk + 2 h + lane
+__device__ __forceinline__ void block_values(const Acc2 (&A)[8], float2 (&v)[16]) {
 #pragma unroll
-  for (int q = 0; q < kGramMaxPairs; ++q) {
-    const int p = tid + kGramThreads * q;
-    pi[q] = pk[q] = 0;
-    if (p < np) gram_pair(p, r0, pi[q], pk[q]);
-    acc[q] = acc_zero();
+  for (int q = 0; q < 8; ++q) {
+    Acc a0, a1;
+    acc2_split(A[q], a0, a1);
+    a0 = acc_norm(a0);
+    a1 = acc_norm(a1);
+    v[2 * q] = make_float2(a0.h, a0.l);
+    v[2 * q + 1] = make_float2(a1.h, a1.l);
   }
+}
+
+__device__ __forceinline__ void block_of(int b, int B, int& bi, int& bk) {
+  bi = 0;
+  while (b >= B - bi) {
+    b -= B - bi;
+    ++bi;
+  }
+  bk = bi + b;
+}
+
+template <int ST>
+__global__ void __launch_bounds__(kGramThreads, 2) k_gram(Ws ws, int cur) {
+  const int r0 = ws.st[cur].hdr->r0;
+  if (r0 < 1) return;
+  const int B = (r0 + 3) >> 2, nb = B * (B + 1) / 2;
+  int nsub = kGramThreads / nb;
+  nsub = nsub < 1 ? 1 : (nsub > kGramRows ? kGramRows : nsub);
+  const int items = nb * nsub;
+  const int tid = threadIdx.x;
+  __shared__ __align__(16) GramSmem sm;
+  int bi[kGramItems], bk[kGramItems], sb[kGramItems];
+  Acc2 acc[kGramItems][8];
+#pragma unroll
+  for (int q = 0; q < kGramItems; ++q) {
+    const int it = tid + kGramThreads * q;
+    bi[q] = bk[q] = 0;
+    sb[q] = kGramRows;  // no rows: inactive
+    if (it < items) {
+      block_of(it % nb, B, bi[q], bk[q]);
+      sb[q] = it / nb;
+    }
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc[q][e] = acc2_zero();
+  }
+  const int w = 4 * B;
   const int64_t ntiles = (ws.n + kGramRows - 1) / kGramRows;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t row0 = tile * kGramRows;
     __syncthreads();
-    for (int idx = tid; idx < kGramRows * r0; idx += kGramThreads) {
-      const int t = idx / r0, c = idx % r0;
+    for (int idx = tid; idx < kGramRows * w; idx += kGramThreads) {
+      const int t = idx / w, c = idx - t * w;
       float h = 0.f, l = 0.f;
-      if (row0 + t < ws.n) load_basis<ST>(ws, (size_t)(row0 + t) * ws.ldg + c, h, l);
-      th[t][c] = h;
-      tl[t][c] = l;
+      if (c < r0 && row0 + t < ws.n) {
+        const size_t o = (size_t)(row0 + t) * ws.ldg + c;
+        h = reinterpret_cast<const float*>(ws.Lh)[o];
+        if constexpr (ST == ST_DD) l = ws.Ll[o];
+      }
+      sm.t.h[t][c] = h;
+      if constexpr (ST == ST_DD) sm.t.l[t][c] = l;
     }
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < kGramMaxPairs; ++q) {
-      if (tid + kGramThreads * q < np) {
-        const int i = pi[q], k = pk[q];
-        for (int t = 0; t < kGramRows; ++t) acc_fma(acc[q], th[t][i], tl[t][i], th[t][k], tl[t][k]);
-      }
+    for (int q = 0; q < kGramItems; ++q) {
+      for (int t = sb[q]; t < kGramRows; t += nsub) gram_row<ST>(acc[q], sm.t, t, bi[q], bk[q]);
+      // fold the low word back once per tile: left to grow over the hundreds of rows a
+      // thread adds, its own FP32 rounding dominates the error of the diagonal sums
+#pragma unroll
+      for (int e = 0; e < 8; ++e) acc2_renorm(acc[q][e]);
     }
   }
   const size_t stride = (size_t)ws.cap * (ws.cap + 1) / 2;
+  float2* out = ws.gpart + (size_t)blockIdx.x * stride;
+  if (nsub == 1) {
 #pragma unroll
-  for (int q = 0; q < kGramMaxPairs; ++q) {
-    const int p = tid + kGramThreads * q;
-    if (p < np) {
-      const Acc a = acc_norm(acc[q]);
-      ws.gpart[(size_t)blockIdx.x * stride + p] = make_float2(a.h, a.l);
+    for (int q = 0; q < kGramItems; ++q) {
+      if (tid + kGramThreads * q >= items) continue;
+      float2 v[16];
+      block_values(acc[q], v);
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        const int ci = 4 * bi[q] + (e >> 2), ck = 4 * bk[q] + (e & 3);
+        if (ci <= ck && ck < r0) out[gram_index(ci, ck, r0)] = v[e];
+      }
     }
+    return;
+  }
+  // several row classes per block (then items <= kGramThreads): add them in class order
+  __syncthreads();
+  if (tid < items) {
+    float2 v[16];
+    block_values(acc[0], v);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) sm.red[tid][e] = v[e];
+  }
+  __syncthreads();
+  for (int o = tid; o < nb * 16; o += kGramThreads) {
+    const int b = o >> 4, e = o & 15;
+    int i0, k0;
+    block_of(b, B, i0, k0);
+    const int ci = 4 * i0 + (e >> 2), ck = 4 * k0 + (e & 3);
+    if (!(ci <= ck && ck < r0)) continue;
+    dd a = dd_of(0.f);
+    for (int s = 0; s < nsub; ++s) a = a + dd_of(sm.red[s * nb + b][e]);
+    out[gram_index(ci, ck, r0)] = f2_of(a);
   }
 }
 
 // Matrices of the refinement in the scratch region (double-float pairs, column-major):
-//   G cap x cap | T1 cap x rmax | C, R, T, V, W, M2: rmax x rmax | sig: rmax | perm: rmax ints
+//   G cap x cap (ld cap) | C, W, V: rmax x rmax (ld rmax) | sig: rmax | perm: rmax ints, flag
 struct RefineScratch {
-  float2 *G, *T1, *C, *R, *T, *V, *W, *M2, *sig;
-  int* perm;
+  float2 *G, *C, *W, *V, *sig;
+  int *perm, *flag;
 };
 
-__device__ RefineScratch refine_scratch(const Ws& ws) {
+__device__ __forceinline__ RefineScratch refine_scratch(const Ws& ws) {
   RefineScratch s;
   const size_t cap = ws.cap, rm = ws.rmax;
   float2* p = ws.rscr;
   s.G = p;
   p += cap * cap;
-  s.T1 = p;
-  p += cap * rm;
   s.C = p;
-  p += rm * rm;
-  s.R = p;
-  p += rm * rm;
-  s.T = p;
-  p += rm * rm;
-  s.V = p;
   p += rm * rm;
   s.W = p;
   p += rm * rm;
-  s.M2 = p;
+  s.V = p;
   p += rm * rm;
   s.sig = p;
   p += rm;
   s.perm = reinterpret_cast<int*>(p);
+  s.flag = s.perm + rm;
   return s;
 }
 
-__device__ __forceinline__ dd ld2(const float2* a, size_t i) { return dd{a[i].x, a[i].y}; }
-__device__ __forceinline__ dd dzero() { return dd{0.f, 0.f}; }
 __device__ __forceinline__ void st2(float2* a, size_t i, dd v) { a[i] = make_float2(v.h, v.l); }
+// a += x y, folding the low word back every 8 terms (sums of up to cap terms)
+__device__ __forceinline__ void acc_fma_k(Acc& a, float2 x, float2 y, int k) {
+  acc_fma(a, x.x, x.y, y.x, y.y);
+  if ((k & 7) == 7) a = acc_norm(a);
+}
+__device__ __forceinline__ dd acc_dd(Acc a) {
+  a = acc_norm(a);
+  return dd{a.h, a.l};
+}
 
-__global__ void __launch_bounds__(kRefineThreads) k_refine(Ws ws, int nblocks) {
-  Ctl* ctl = ws.ctl;
-  const int cur = ctl->cur;
-  const StateBuf st = ws.st[cur], nx = ws.st[cur ^ 1];
-  const int r = st.hdr->r, r0 = st.hdr->r0;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (r < 1 || r0 < r) return;
-  const int cap = ws.cap, rm = ws.rmax, qld = cap + 1;
-  const RefineScratch S = refine_scratch(ws);
-  __shared__ int bad;
-  if (tid == 0) bad = 0;
-
-  // G: sum the per-CTA partials in CTA order, mirror the upper triangle
-  const int np = gram_pairs(r0);
-  const size_t stride = (size_t)cap * (cap + 1) / 2;
-  for (int p = tid; p < np; p += kRefineThreads) {
-    dd s = dzero();
-    for (int b = 0; b < nblocks; ++b) s = s + ld2(ws.gpart, (size_t)b * stride + p);
+// G: a warp per pair; lane L adds partials L, L + 32, .. in order, then a butterfly over the
+// lanes (double-float addition is symmetric, so every lane ends with the same value).  The
+// tree keeps the rounding of the sum of a few hundred partials at a few units of 2^-48.
+constexpr int kSumThreads = 256;
+__global__ void __launch_bounds__(kSumThreads) k_gram_sum(Ws ws, int cur, int nblocks) {
+  const int r0 = ws.st[cur].hdr->r0;
+  const int p = blockIdx.x * (kSumThreads / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (p >= gram_pairs(r0)) return;  // whole warps leave together
+  const size_t stride = (size_t)ws.cap * (ws.cap + 1) / 2;
+  dd a = dd_of(0.f);
+  for (int b = lane; b < nblocks; b += 32) a = a + dd_of(__ldcg(ws.gpart + (size_t)b * stride + p));
+  a = dd_warp_sum(a);
+  if (lane == 0) {
     int i, k;
     gram_pair(p, r0, i, k);
-    st2(S.G, (size_t)k * cap + i, s);
-    st2(S.G, (size_t)i * cap + k, s);
-  }
-  __syncthreads();
-  // T1 = G Q  (r0 x r),  C = Q^T T1  (r x r)
-  for (int o = tid; o < r0 * r; o += kRefineThreads) {
-    const int a = o % r0, j = o / r0;
-    dd s = dzero();
-    for (int b = 0; b < r0; ++b) s = dd_fma(ld2(S.G, (size_t)b * cap + a), ld2(st.Q, (size_t)j * qld + b), s);
-    st2(S.T1, (size_t)j * cap + a, s);
-  }
-  __syncthreads();
-  for (int o = tid; o < r * r; o += kRefineThreads) {
-    const int i = o % r, j = o / r;
-    dd s = dzero();
-    for (int a = 0; a < r0; ++a) s = dd_fma(ld2(st.Q, (size_t)i * qld + a), ld2(S.T1, (size_t)j * cap + a), s);
-    st2(S.C, (size_t)j * rm + i, s);
-  }
-  __syncthreads();
-  // Cholesky C = R^T R, column by column (R upper triangular, column-major)
-  for (int o = tid; o < r * r; o += kRefineThreads) st2(S.R, (size_t)(o / r) * rm + (o % r), dzero());
-  __syncthreads();
-  for (int j = 0; j < r; ++j) {
-    if (tid == 0) {
-      dd d = ld2(S.C, (size_t)j * rm + j);
-      for (int k = 0; k < j; ++k) {
-        const dd rk = ld2(S.R, (size_t)j * rm + k);
-        d = d - rk * rk;
-      }
-      if (!(d.h > 0.f) || !dd_isfinite(d)) {
-        bad = 1;
-        d = dd_of(1.f);
-      }
-      st2(S.R, (size_t)j * rm + j, dd_sqrt(d));
-    }
-    __syncthreads();
-    const dd rjj = ld2(S.R, (size_t)j * rm + j);
-    for (int i = j + 1 + tid; i < r; i += kRefineThreads) {
-      dd s = ld2(S.C, (size_t)i * rm + j);
-      for (int k = 0; k < j; ++k) s = s - ld2(S.R, (size_t)j * rm + k) * ld2(S.R, (size_t)i * rm + k);
-      st2(S.R, (size_t)i * rm + j, dd_div(s, rjj));
-    }
-    __syncthreads();
-  }
-  if (bad) {
-    if (tid == 0) atomicOr(&ctl->status, DEV_NONFINITE);
-    return;
-  }
-  // T = R diag(S), V = I
-  for (int o = tid; o < r * r; o += kRefineThreads) {
-    const int i = o % r, j = o / r;
-    st2(S.T, (size_t)j * rm + i, ld2(S.R, (size_t)j * rm + i) * ld2(st.S, j));
-    st2(S.V, (size_t)j * rm + i, dd_of(i == j ? 1.f : 0.f));
-  }
-  __syncthreads();
-  // one-sided Jacobi on the columns of T (warp 0; rows split over the lanes)
-  if (warp == 0) {
-    const float tol = 4.f * 7.105427357601002e-15f;
-    for (int sweep = 0; sweep < 12; ++sweep) {
-      int rotated = 0;
-      for (int p = 0; p < r - 1; ++p)
-        for (int q = p + 1; q < r; ++q) {
-          dd al = dzero(), be = dzero(), ga = dzero();
-          for (int i = lane; i < r; i += 32) {
-            const dd tp = ld2(S.T, (size_t)p * rm + i), tq = ld2(S.T, (size_t)q * rm + i);
-            al = dd_fma(tp, tp, al);
-            be = dd_fma(tq, tq, be);
-            ga = dd_fma(tp, tq, ga);
-          }
-          al = dd_warp_sum(al);
-          be = dd_warp_sum(be);
-          ga = dd_warp_sum(ga);
-          if (!(fabsf(ga.h) > tol * sqrtf(al.h) * sqrtf(be.h))) continue;
-          ++rotated;
-          // rotation zeroing the (p, q) inner product: zeta = (be - al) / (2 ga)
-          const dd zeta = dd_div(be - al, ga * 2.f);
-          const dd one = dd_of(1.f);
-          const dd tt = dd_div(zeta.h >= 0.f ? one : -one, dd_abs(zeta) + dd_sqrt(one + zeta * zeta));
-          const dd c = dd_div(one, dd_sqrt(one + tt * tt)), sn = c * tt;
-          for (int i = lane; i < r; i += 32) {
-            const dd tp = ld2(S.T, (size_t)p * rm + i), tq = ld2(S.T, (size_t)q * rm + i);
-            st2(S.T, (size_t)p * rm + i, c * tp - sn * tq);
-            st2(S.T, (size_t)q * rm + i, sn * tp + c * tq);
-            const dd vp = ld2(S.V, (size_t)p * rm + i), vq = ld2(S.V, (size_t)q * rm + i);
-            st2(S.V, (size_t)p * rm + i, c * vp - sn * vq);
-            st2(S.V, (size_t)q * rm + i, sn * vp + c * vq);
-          }
-          __syncwarp();
-        }
-      if (rotated == 0) break;
-    }
-    // singular values (column norms) and their descending order
-    for (int j = 0; j < r; ++j) {
-      dd s = dzero();
-      for (int i = lane; i < r; i += 32) {
-        const dd t = ld2(S.T, (size_t)j * rm + i);
-        s = dd_fma(t, t, s);
-      }
-      s = dd_warp_sum(s);
-      if (lane == 0) st2(S.sig, j, dd_sqrt(s));
-    }
-    __syncwarp();
-    if (lane == 0) {
-      for (int j = 0; j < r; ++j) S.perm[j] = j;
-      for (int j = 0; j < r; ++j) {
-        int best = j;
-        for (int k = j + 1; k < r; ++k)
-          if (dd_gt(ld2(S.sig, S.perm[k]), ld2(S.sig, S.perm[best]))) best = k;
-        const int t = S.perm[j];
-        S.perm[j] = S.perm[best];
-        S.perm[best] = t;
-      }
-    }
-  }
-  __syncthreads();
-  // U_s = T Sigma^-1 (in place), then W = R^-1 U_s by back substitution (a thread per column)
-  for (int o = tid; o < r * r; o += kRefineThreads) {
-    const int i = o % r, j = o / r;
-    st2(S.T, (size_t)j * rm + i, dd_div(ld2(S.T, (size_t)j * rm + i), ld2(S.sig, j)));
-  }
-  __syncthreads();
-  for (int j = tid; j < r; j += kRefineThreads)
-    for (int i = r - 1; i >= 0; --i) {
-      dd s = ld2(S.T, (size_t)j * rm + i);
-      for (int k = i + 1; k < r; ++k) s = s - ld2(S.R, (size_t)k * rm + i) * ld2(S.W, (size_t)j * rm + k);
-      st2(S.W, (size_t)j * rm + i, dd_div(s, ld2(S.R, (size_t)i * rm + i)));
-    }
-  __syncthreads();
-  // M2 = M V
-  for (int o = tid; o < r * r; o += kRefineThreads) {
-    const int i = o % r, j = o / r;
-    dd s = dzero();
-    for (int k = 0; k < r; ++k) s = dd_fma(ld2(st.M, (size_t)k * rm + i), ld2(S.V, (size_t)j * rm + k), s);
-    st2(S.M2, (size_t)j * rm + i, s);
-  }
-  __syncthreads();
-  // the new state, columns in descending order of Sigma
-  for (int o = tid; o < r * r; o += kRefineThreads) {
-    const int i = o % r, j = o / r;
-    const int pi_ = S.perm[i], pj = S.perm[j];
-    dd s = dzero();
-    for (int k = 0; k < r; ++k) s = dd_fma(ld2(S.W, (size_t)pi_ * rm + k), ld2(S.M2, (size_t)pj * rm + k), s);
-    st2(nx.M, (size_t)j * rm + i, s);
-  }
-  for (int o = tid; o < r0 * r; o += kRefineThreads) {
-    const int a = o % r0, j = o / r0, pj = S.perm[j];
-    dd s = dzero();
-    for (int k = 0; k < r; ++k) s = dd_fma(ld2(st.Q, (size_t)k * qld + a), ld2(S.W, (size_t)pj * rm + k), s);
-    st2(nx.Q, (size_t)j * qld + a, s);
-  }
-  for (int j = tid; j < r; j += kRefineThreads) {
-    const int pj = S.perm[j];
-    dd f = dzero(), l = dzero();
-    for (int k = 0; k < r; ++k) {
-      const dd v = ld2(S.V, (size_t)pj * rm + k);
-      f = dd_fma(ld2(st.rf, k), v, f);
-      l = dd_fma(ld2(st.rl, k), v, l);
-    }
-    st2(nx.rf, j, f);
-    st2(nx.rl, j, l);
-    nx.S[j] = S.sig[pj];
-  }
-  for (int i = tid; i < qld; i += kRefineThreads) {
-    nx.a[i] = st.a[i];
-    nx.ps[i] = st.ps[i];
-  }
-  if (tid == 0) *nx.hdr = *st.hdr;
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) {
-    ctl->cur = cur ^ 1;
-    ctl->eig_valid = 0;
+    const RefineScratch S = refine_scratch(ws);
+    S.G[(size_t)k * ws.cap + i] = f2_of(a);
+    S.G[(size_t)i * ws.cap + k] = f2_of(a);
   }
 }
 
-cudaError_t launch_refine(const Ws& ws, cudaStream_t s) {
+// C = Q^T G Q, one column per CTA: t = G Q[:, j] in shared memory, then C[:, j] = Q^T t
+__global__ void __launch_bounds__(128) k_refine_c(Ws ws, int cur) {
+  const StateBuf st = ws.st[cur];
+  const int r = st.hdr->r, r0 = st.hdr->r0, j = blockIdx.x;
+  if (r < 1 || r0 < r || j >= r) return;
+  const int cap = ws.cap, qld = cap + 1, tid = threadIdx.x;
+  const RefineScratch S = refine_scratch(ws);
+  __shared__ float2 t[kMaxCap];
+  for (int a = tid; a < r0; a += 128) {
+    Acc s = acc_zero();
+    for (int b = 0; b < r0; ++b) acc_fma_k(s, S.G[(size_t)b * cap + a], st.Q[(size_t)j * qld + b], b);
+    s = acc_norm(s);
+    t[a] = make_float2(s.h, s.l);
+  }
+  __syncthreads();
+  for (int i = tid; i < r; i += 128) {
+    Acc s = acc_zero();
+    for (int a = 0; a < r0; ++a) acc_fma_k(s, st.Q[(size_t)i * qld + a], t[a], a);
+    s = acc_norm(s);
+    S.C[(size_t)j * ws.rmax + i] = make_float2(s.h, s.l);
+  }
+}
+
+// ------------------------------------------------- Cholesky, Jacobi SVD, R^-1 U_s (one CTA)
+struct RefineSmem {
+  float2 R[kMaxR * kRefineLd], T[kMaxR * kRefineLd], V[kMaxR * kRefineLd];
+  float2 sig[kMaxR], dinv[kMaxR];
+  int perm[kMaxR];
+  int rot[32];
+  int bad;
+};
+
+__device__ __forceinline__ dd half_sum(dd a, unsigned mask) {
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) a = a + dd{__shfl_xor_sync(mask, a.h, o), __shfl_xor_sync(mask, a.l, o)};
+  return a;
+}
+
+__global__ void __launch_bounds__(kRefineThreads) k_refine(Ws ws, int cur) {
+  const StateBuf st = ws.st[cur];
+  const int r = st.hdr->r, r0 = st.hdr->r0;
+  const int tid = threadIdx.x;
+  const RefineScratch S = refine_scratch(ws);
+  if (r < 1 || r0 < r) {
+    if (tid == 0) *S.flag = 2;  // no basis yet: the state is carried over as it is
+    return;
+  }
+  extern __shared__ __align__(16) unsigned char refine_smem_raw[];
+  RefineSmem& sm = *reinterpret_cast<RefineSmem*>(refine_smem_raw);
+  constexpr int ld = kRefineLd;
+  const int rm = ws.rmax;
+  if (tid == 0) sm.bad = 0;
+  if (tid < 32) sm.rot[tid] = 0;
+  for (int o = tid; o < r * r; o += kRefineThreads) {
+    const int i = o % r, k = o / r;
+    sm.R[k * ld + i] = S.C[(size_t)k * rm + i];
+  }
+  __syncthreads();
+
+  // Cholesky C = R^T R, right-looking on the upper triangle.  Step j subtracts
+  // a_ji a_jk / a_jj from the trailing block; the rows are scaled by 1/sqrt(a_jj) at the end
+  // (row j is not touched after step j), so a step needs one barrier.
+  for (int j = 0; j < r; ++j) {
+    const dd d = dd_of(sm.R[j * ld + j]);
+    if (!(d.h > 0.f) || !dd_isfinite(d)) {
+      if (tid == 0) sm.bad = 1;
+      break;  // every thread reads the same pivot and leaves here
+    }
+    const dd dinv = dd_div(dd_of(1.f), d);
+    const int w = r - j - 1;
+    for (int o = tid; o < w * w; o += kRefineThreads) {
+      const int i = j + 1 + o % w, k = j + 1 + o / w;
+      if (i > k) continue;
+      const dd f = dd_of(sm.R[i * ld + j]) * dinv;
+      const dd v = dd_of(sm.R[k * ld + i]) - f * dd_of(sm.R[k * ld + j]);
+      sm.R[k * ld + i] = f2_of(v);
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  if (sm.bad) {
+    if (tid == 0) *S.flag = 1;
+    return;
+  }
+  // row scaling (a_jj -> sqrt(a_jj), a_jk -> a_jk / sqrt(a_jj)), zero below the diagonal;
+  // T = R diag(S), V = I
+  for (int j = tid; j < r; j += kRefineThreads) sm.dinv[j] = f2_of(dd_sqrt(dd_of(sm.R[j * ld + j])));
+  __syncthreads();
+  for (int o = tid; o < r * r; o += kRefineThreads) {
+    const int i = o % r, k = o / r;
+    dd v = dd_of(0.f);
+    if (i == k)
+      v = dd_of(sm.dinv[i]);
+    else if (i < k)
+      v = dd_div(dd_of(sm.R[k * ld + i]), dd_of(sm.dinv[i]));
+    sm.R[k * ld + i] = f2_of(v);
+  }
+  __syncthreads();
+  for (int o = tid; o < r * r; o += kRefineThreads) {
+    const int i = o % r, k = o / r;
+    sm.T[k * ld + i] = f2_of(dd_of(sm.R[k * ld + i]) * dd_of(st.S[k]));
+    sm.V[k * ld + i] = make_float2(i == k ? 1.f : 0.f, 0.f);
+  }
+  __syncthreads();
+
+  // One-sided Jacobi on the columns of T, round-robin order: each round rotates m/2
+  // disjoint column pairs at once, a half-warp per pair with the rows split over its
+  // 16 lanes.  A sweep is m - 1 rounds; the sweeps stop when one rotates nothing.
+  {
+    const int m = r + (r & 1);
+    const int hw = tid >> 4, hl = tid & 15;
+    const unsigned mask = (tid & 16) ? 0xffff0000u : 0x0000ffffu;
+    const float tol = 4.f * 7.105427357601002e-15f;
+    for (int sweep = 0; sweep < 16; ++sweep) {
+      int rotated = 0;
+      for (int k = 0; k < m - 1; ++k) {
+        for (int pi = hw; pi < m / 2; pi += kRefineThreads / 16) {
+          int a = k, b = m - 1;
+          if (pi > 0) {
+            a = (k + pi) % (m - 1);
+            b = (k - pi + m - 1) % (m - 1);
+          }
+          const int p = a < b ? a : b, q = a < b ? b : a;
+          if (q >= r) continue;  // the dummy column of an odd r
+          Acc al = acc_zero(), be = acc_zero(), ga = acc_zero();
+          for (int i = hl; i < r; i += 16) {
+            const float2 tp = sm.T[p * ld + i], tq = sm.T[q * ld + i];
+            acc_fma(al, tp.x, tp.y, tp.x, tp.y);
+            acc_fma(be, tq.x, tq.y, tq.x, tq.y);
+            acc_fma(ga, tp.x, tp.y, tq.x, tq.y);
+          }
+          const dd A = half_sum(acc_dd(al), mask), Bv = half_sum(acc_dd(be), mask), G = half_sum(acc_dd(ga), mask);
+          if (!(fabsf(G.h) > tol * sqrtf(A.h) * sqrtf(Bv.h))) continue;
+          ++rotated;
+          // rotation zeroing the (p, q) inner product: zeta = (be - al) / (2 ga),
+          // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1 / sqrt(1 + t^2), s = c t.
+          // For |zeta| >= 2^26, t = ga / (be - al) and c = 1 to double-float accuracy.
+          const dd diff = Bv - A;
+          dd c, s;
+          if (fabsf(diff.h) >= 134217728.f * fabsf(G.h)) {
+            c = dd_of(1.f);
+            s = dd_div(G, diff);
+          } else {
+            const dd one = dd_of(1.f);
+            const dd zeta = dd_div(diff, G * 2.f);
+            const dd t = dd_div(zeta.h >= 0.f ? one : -one, dd_abs(zeta) + dd_sqrt(one + zeta * zeta));
+            c = dd_div(one, dd_sqrt(one + t * t));
+            s = c * t;
+          }
+          for (int i = hl; i < r; i += 16) {
+            const dd tp = dd_of(sm.T[p * ld + i]), tq = dd_of(sm.T[q * ld + i]);
+            sm.T[p * ld + i] = f2_of(c * tp - s * tq);
+            sm.T[q * ld + i] = f2_of(s * tp + c * tq);
+            const dd vp = dd_of(sm.V[p * ld + i]), vq = dd_of(sm.V[q * ld + i]);
+            sm.V[p * ld + i] = f2_of(c * vp - s * vq);
+            sm.V[q * ld + i] = f2_of(s * vp + c * vq);
+          }
+        }
+        __syncthreads();
+      }
+      if (rotated && hl == 0) atomicAdd(&sm.rot[sweep], 1);
+      __syncthreads();
+      if (sm.rot[sweep] == 0) break;
+    }
+  }
+
+  // singular values (column norms, a half-warp per column), descending order by rank count
+  {
+    const int hw = tid >> 4, hl = tid & 15;
+    const unsigned mask = (tid & 16) ? 0xffff0000u : 0x0000ffffu;
+    for (int j = hw; j < r; j += kRefineThreads / 16) {
+      Acc s = acc_zero();
+      for (int i = hl; i < r; i += 16) {
+        const float2 t = sm.T[j * ld + i];
+        acc_fma(s, t.x, t.y, t.x, t.y);
+      }
+      const dd n = dd_sqrt(half_sum(acc_dd(s), mask));
+      if (hl == 0) {
+        sm.sig[j] = f2_of(n);
+        if (!(n.h > 0.f) || !dd_isfinite(n)) sm.bad = 1;
+      }
+    }
+  }
+  __syncthreads();
+  if (sm.bad) {
+    if (tid == 0) *S.flag = 1;
+    return;
+  }
+  for (int j = tid; j < r; j += kRefineThreads) {
+    const dd sj = dd_of(sm.sig[j]);
+    int rank = 0;
+    for (int k = 0; k < r; ++k) {
+      const dd sk = dd_of(sm.sig[k]);
+      rank += dd_gt(sk, sj) || (!dd_lt(sk, sj) && k < j);
+    }
+    sm.perm[rank] = j;
+  }
+  // U_s = T Sigma^-1 in place; 1 / R_ii
+  for (int o = tid; o < r * r; o += kRefineThreads) {
+    const int i = o % r, k = o / r;
+    sm.T[k * ld + i] = f2_of(dd_div(dd_of(sm.T[k * ld + i]), dd_of(sm.sig[k])));
+  }
+  for (int i = tid; i < r; i += kRefineThreads) sm.dinv[i] = f2_of(dd_div(dd_of(1.f), dd_of(sm.R[i * ld + i])));
+  __syncthreads();
+  // W = R^-1 U_s in place, column-oriented back substitution: step i removes the final
+  // row i (its unscaled value times 1/R_ii) from the rows above; rows are scaled at the end
+  for (int i = r - 1; i > 0; --i) {
+    const dd di = dd_of(sm.dinv[i]);
+    for (int o = tid; o < i * r; o += kRefineThreads) {
+      const int k = o % i, j = o / i;
+      const dd u = dd_of(sm.T[j * ld + i]) * di;
+      sm.T[j * ld + k] = f2_of(dd_of(sm.T[j * ld + k]) - dd_of(sm.R[i * ld + k]) * u);
+    }
+    __syncthreads();
+  }
+  for (int o = tid; o < r * r; o += kRefineThreads) {
+    const int i = o % r, j = o / r;
+    st2(S.W, (size_t)j * rm + i, dd_of(sm.T[j * ld + i]) * dd_of(sm.dinv[i]));
+    S.V[(size_t)j * rm + i] = sm.V[j * ld + i];
+  }
+  for (int j = tid; j < r; j += kRefineThreads) {
+    S.sig[j] = sm.sig[j];
+    S.perm[j] = sm.perm[j];
+  }
+  if (tid == 0) *S.flag = 0;
+}
+
+// --------------------------------------------------- the new state, one column per CTA
+// Column j takes Sigma's j-th largest value: pj = perm[j].
+//   M'[:, j] = W[:, perm]^T (M V[:, pj]),  Q'[:, j] = Q W[:, pj]
+// CTA 0 also writes S, r_first, r_last, copies a, ps and the header, and commits.
+__global__ void __launch_bounds__(128) k_refine_out(Ws ws, int cur) {
+  const StateBuf st = ws.st[cur], nx = ws.st[cur ^ 1];
+  const int r = st.hdr->r, r0 = st.hdr->r0, rm = ws.rmax, qld = ws.cap + 1;
+  const int j = blockIdx.x, tid = threadIdx.x;
+  const RefineScratch S = refine_scratch(ws);
+  const int flag = *S.flag;
+  if (flag != 0) {
+    // carried over unchanged (flag 2) or refused (flag 1: a non-positive pivot)
+    if (j < r) {
+      for (int i = tid; i < r; i += 128) nx.M[(size_t)j * rm + i] = st.M[(size_t)j * rm + i];
+      for (int a = tid; a < r0; a += 128) nx.Q[(size_t)j * qld + a] = st.Q[(size_t)j * qld + a];
+    }
+    if (j == 0) {
+      for (int i = tid; i < r; i += 128) {
+        nx.S[i] = st.S[i];
+        nx.rf[i] = st.rf[i];
+        nx.rl[i] = st.rl[i];
+      }
+    }
+  } else if (j < r) {
+    __shared__ float2 m2[kMaxR];
+    const int pj = S.perm[j];
+    for (int i = tid; i < r; i += 128) {
+      Acc s = acc_zero();
+      for (int k = 0; k < r; ++k) acc_fma_k(s, st.M[(size_t)k * rm + i], S.V[(size_t)pj * rm + k], k);
+      s = acc_norm(s);
+      m2[i] = make_float2(s.h, s.l);
+    }
+    __syncthreads();
+    for (int i = tid; i < r; i += 128) {
+      const int pi = S.perm[i];
+      Acc s = acc_zero();
+      for (int k = 0; k < r; ++k) acc_fma_k(s, S.W[(size_t)pi * rm + k], m2[k], k);
+      s = acc_norm(s);
+      nx.M[(size_t)j * rm + i] = make_float2(s.h, s.l);
+    }
+    for (int a = tid; a < r0; a += 128) {
+      Acc s = acc_zero();
+      for (int k = 0; k < r; ++k) acc_fma_k(s, st.Q[(size_t)k * qld + a], S.W[(size_t)pj * rm + k], k);
+      s = acc_norm(s);
+      nx.Q[(size_t)j * qld + a] = make_float2(s.h, s.l);
+    }
+    if (j == 0) {
+      for (int jj = tid; jj < r; jj += 128) {
+        const int pjj = S.perm[jj];
+        Acc f = acc_zero(), l = acc_zero();
+        for (int k = 0; k < r; ++k) {
+          const float2 v = S.V[(size_t)pjj * rm + k];
+          acc_fma_k(f, st.rf[k], v, k);
+          acc_fma_k(l, st.rl[k], v, k);
+        }
+        f = acc_norm(f);
+        l = acc_norm(l);
+        nx.rf[jj] = make_float2(f.h, f.l);
+        nx.rl[jj] = make_float2(l.h, l.l);
+        nx.S[jj] = S.sig[pjj];
+      }
+    }
+  }
+  if (j == 0) {
+    for (int i = tid; i < qld; i += 128) {
+      nx.a[i] = st.a[i];
+      nx.ps[i] = st.ps[i];
+    }
+    if (tid == 0) {
+      *nx.hdr = *st.hdr;
+      // the kernels of this call take the committed buffer from their argument, so the
+      // switch can be made before the other CTAs finish
+      ws.ctl->cur = cur ^ 1;
+      ws.ctl->eig_valid = 0;
+      if (flag == 1) atomicOr(&ws.ctl->status, DEV_NONFINITE);
+    }
+  }
+}
+
+int refine_smem_bytes() { return (int)sizeof(RefineSmem); }
+
+cudaError_t prepare_refine() {
+  return cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, refine_smem_bytes());
+}
+
+cudaError_t launch_refine(const Ws& ws, int cur, cudaStream_t s) {
   switch (ws.prec) {
     case ST_DD:
-      k_gram<ST_DD><<<kGramCtas, kGramThreads, 0, s>>>(ws);
+      k_gram<ST_DD><<<ws.gridG, kGramThreads, 0, s>>>(ws, cur);
       break;
     case ST_F32:
-      k_gram<ST_F32><<<kGramCtas, kGramThreads, 0, s>>>(ws);
+      k_gram<ST_F32><<<ws.gridG, kGramThreads, 0, s>>>(ws, cur);
       break;
     default:
-      k_gram<ST_BF16><<<kGramCtas, kGramThreads, 0, s>>>(ws);
+      return cudaErrorInvalidValue;  // BF16 storage is refused when a handle is created
   }
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_refine<<<1, kRefineThreads, 0, s>>>(ws, kGramCtas);
+  const int np = ws.cap * (ws.cap + 1) / 2, per = kSumThreads / 32;
+  k_gram_sum<<<(np + per - 1) / per, kSumThreads, 0, s>>>(ws, cur, ws.gridG);
+  k_refine_c<<<ws.rmax, 128, 0, s>>>(ws, cur);
+  k_refine<<<1, kRefineThreads, refine_smem_bytes(), s>>>(ws, cur);
+  k_refine_out<<<ws.rmax, 128, 0, s>>>(ws, cur);
   return cudaGetLastError();
 }
 
