@@ -87,6 +87,7 @@ __device__ dd block_sum256(dd a, float2* scratch8) {
 constexpr int kPrepThreads = 256;
 
 __global__ void __launch_bounds__(kPrepThreads) k_prep(Ws ws) {
+  pdl_wait();
   extern __shared__ __align__(16) float2 psm[];
   Ctl* ctl = ws.ctl;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -283,6 +284,7 @@ __device__ SecSums sec_eval(const float2* d, const float2* z, int m, int j, int 
 }
 
 __global__ void __launch_bounds__(32) k_roots(Ws ws) {
+  pdl_wait();
   Ctl* ctl = ws.ctl;
   const int m = ctl->m;
   const int j = blockIdx.x;
@@ -492,6 +494,7 @@ __global__ void __launch_bounds__(32) k_roots(Ws ws) {
 // paired so every factor is O(1).  Block kMaxN orders all singular values of K.
 // ---------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(32) k_zhat(Ws ws) {
+  pdl_wait();
   Ctl* ctl = ws.ctl;
   const int m = ctl->m;
   const int lane = threadIdx.x;
@@ -563,6 +566,7 @@ __global__ void __launch_bounds__(32) k_zhat(Ws ws) {
 // k_vectors: kept column j -> u_j, v_j (core coordinates 0..r; r is the p/rho column)
 // ---------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(64) k_vectors(Ws ws) {
+  pdl_wait();
   Ctl* ctl = ws.ctl;
   const int j = blockIdx.x;
   if (j >= ctl->rnew) return;
@@ -645,6 +649,7 @@ __device__ void apply_column(const Ws& ws, int j, const StateBuf& st, const Stat
                              bool compact);
 
 __global__ void __launch_bounds__(kApplyThreads) k_apply(Ws ws) {
+  pdl_wait();
   Ctl* ctl = ws.ctl;
   const int j = blockIdx.x;
   const int rnew = ctl->rnew;
@@ -1460,12 +1465,12 @@ cudaError_t prepare_small(const Ws&) {
 
 cudaError_t launch_small(const Ws& ws, cudaStream_t s) {
   const int ps = prep_smem(ws);
-  k_prep<<<1, kPrepThreads, ps, s>>>(ws);
-  k_roots<<<kMaxN, 32, 0, s>>>(ws);
-  k_zhat<<<kMaxN + 1, 32, 0, s>>>(ws);
-  k_vectors<<<kMaxN, 64, 0, s>>>(ws);
-  k_apply<<<kMaxN, kApplyThreads, 0, s>>>(ws);
-  return cudaGetLastError();
+  cudaError_t e = launch_dependent(k_prep, 1, kPrepThreads, ps, s, ws);
+  if (e == cudaSuccess) e = launch_dependent(k_roots, kMaxN, 32, 0, s, ws);
+  if (e == cudaSuccess) e = launch_dependent(k_zhat, kMaxN + 1, 32, 0, s, ws);
+  if (e == cudaSuccess) e = launch_dependent(k_vectors, kMaxN, 64, 0, s, ws);
+  if (e == cudaSuccess) e = launch_dependent(k_apply, kMaxN, kApplyThreads, 0, s, ws);
+  return e;
 }
 
 cudaError_t launch_eig(const Ws& ws, cudaStream_t s) {

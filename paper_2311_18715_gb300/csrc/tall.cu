@@ -442,6 +442,7 @@ static_assert(kMaxCap <= 96, "row_dots_dispatch covers box widths up to 25 chunk
 
 template <int ST>
 __global__ void __launch_bounds__(kThreadsA, 1) k_pass_a(Ws ws) {
+  pdl_wait();
   using T = Traits<ST>;
   using stored_t = typename T::stored_t;
   constexpr int kE = (ST == ST_BF16) ? 8 : 4;      // columns per 16-byte chunk
@@ -778,6 +779,7 @@ constexpr int kThreadsB = 512;
 
 template <int ST, bool FLUSH>
 __global__ void __launch_bounds__(kThreadsB) k_pass_b(Ws ws) {
+  pdl_wait();
   using T = Traits<ST>;
   constexpr int epcC = (ST == ST_BF16) ? 8 : 4;  // basis columns per 16-byte chunk
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -1267,15 +1269,12 @@ cudaError_t launch_pass_a(const Ws& ws, cudaStream_t s) {
   const int sm = smem_a(ws.prec, ws.cap);
   switch (ws.prec) {
     case ST_DD:
-      k_pass_a<ST_DD><<<ws.gridPA, kThreadsA, sm, s>>>(ws);
-      break;
+      return launch_dependent(k_pass_a<ST_DD>, ws.gridPA, kThreadsA, sm, s, ws);
     case ST_F32:
-      k_pass_a<ST_F32><<<ws.gridPA, kThreadsA, sm, s>>>(ws);
-      break;
+      return launch_dependent(k_pass_a<ST_F32>, ws.gridPA, kThreadsA, sm, s, ws);
     default:
-      k_pass_a<ST_BF16><<<ws.gridPA, kThreadsA, sm, s>>>(ws);
+      return launch_dependent(k_pass_a<ST_BF16>, ws.gridPA, kThreadsA, sm, s, ws);
   }
-  return cudaGetLastError();
 }
 
 template <bool FLUSH>
@@ -1283,15 +1282,12 @@ static cudaError_t pass_b_launch(const Ws& ws, cudaStream_t s) {
   const int sm = smem_b(ws.prec, ws.cap);
   switch (ws.prec) {
     case ST_DD:
-      k_pass_b<ST_DD, FLUSH><<<ws.gridA, kThreadsB, sm, s>>>(ws);
-      break;
+      return launch_dependent(k_pass_b<ST_DD, FLUSH>, ws.gridA, kThreadsB, sm, s, ws);
     case ST_F32:
-      k_pass_b<ST_F32, FLUSH><<<ws.gridA, kThreadsB, sm, s>>>(ws);
-      break;
+      return launch_dependent(k_pass_b<ST_F32, FLUSH>, ws.gridA, kThreadsB, sm, s, ws);
     default:
-      k_pass_b<ST_BF16, FLUSH><<<ws.gridA, kThreadsB, sm, s>>>(ws);
+      return launch_dependent(k_pass_b<ST_BF16, FLUSH>, ws.gridA, kThreadsB, sm, s, ws);
   }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_pass_b(const Ws& ws, cudaStream_t s) { return pass_b_launch<false>(ws, s); }
@@ -1310,6 +1306,7 @@ cudaError_t launch_first(const Ws& ws, cudaStream_t s) {
 // FP64 instructions a snapshot meets).
 __global__ void __launch_bounds__(kThreads) k_ingest_dd(const double* __restrict__ src, float2* __restrict__ dst,
                                                         int64_t n) {
+  pdl_wait();
   for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
     float h, l;
     split_double(src[i], h, l);
@@ -1319,6 +1316,7 @@ __global__ void __launch_bounds__(kThreads) k_ingest_dd(const double* __restrict
 
 __global__ void __launch_bounds__(kThreads) k_ingest_f32(const float* __restrict__ src, float* __restrict__ dst,
                                                          int64_t n) {
+  pdl_wait();
   for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
     dst[i] = src[i];
 }
