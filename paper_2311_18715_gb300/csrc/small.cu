@@ -40,8 +40,34 @@ __device__ __forceinline__ dd group4_sum(dd a) {
   return a + dd_shfl_xor(a, 2);
 }
 
+// sum_{t < cnt} A[a0 + t as] B[b0 + t bs] in double-float.  The sums are short and their
+// operands sit in L2 or shared memory, so the loads are issued 8 at a time ahead of the
+// arithmetic, and even and odd terms go to two accumulators (added at the end).
+__device__ __forceinline__ dd dot_dd(const float2* A, size_t a0, size_t as, const float2* B, size_t b0, size_t bs,
+                                     int cnt) {
+  dd acc0 = dzero(), acc1 = dzero();
+  for (int t0 = 0; t0 < cnt; t0 += 8) {
+    float2 a[8], b[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const bool ok = t0 + t < cnt;
+      a[t] = ok ? A[a0 + (size_t)(t0 + t) * as] : make_float2(0.f, 0.f);
+      b[t] = ok ? B[b0 + (size_t)(t0 + t) * bs] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int t = 0; t < 8; t += 2) {
+      acc0 = dd_fma(dd_of(a[t]), dd_of(b[t]), acc0);
+      acc1 = dd_fma(dd_of(a[t + 1]), dd_of(b[t + 1]), acc1);
+    }
+  }
+  return acc0 + acc1;
+}
+
+// terms t = sub, sub + 4, .. below n: how many
+__device__ __forceinline__ int count4(int sub, int n) { return n > sub ? (n - sub + 3) >> 2 : 0; }
+
 // out[j] = sum_{i < nrows} A[j*lda + i] v[i] for j < ncols (4 threads per output).
-// Called by every thread of a 256-thread block; A, v, out in shared or global memory.
+// Called by every thread of a 256-thread block; A, v, out in shared memory.
 __device__ void colsum(float2* out, const float2* A, int lda, const float2* v, int nrows, int ncols) {
   const int tid = threadIdx.x;
   for (int base = 0; base < 4 * ncols; base += 256) {
@@ -262,7 +288,10 @@ __device__ SecSums sec_eval(const float2* d, const float2* z, int m, int j, int 
   SecSums s{dzero(), dzero(), dzero(), dzero()};
   const int lane = threadIdx.x & 31;
   const dd dob = LD(d, o);
-  for (int i = lane; i < m; i += 32) {
+  #pragma unroll
+  for (int q_ = 0; q_ < (kMaxN + 31) / 32; ++q_) {
+    const int i = lane + 32 * q_;
+    if (i >= m) break;
     const dd di = LD(d, i);
     const dd del = (di - dob) * (di + dob) - mu;  // d_i^2 - lambda
     const dd zi = LD(z, i);
@@ -339,7 +368,10 @@ __global__ void __launch_bounds__(32) k_roots(Ws ws) {
     float lof = lo.h, hif = hi.h, muf = mu.h;
     for (int it = 0; it < 40; ++it) {
       float psi = 0.f, dpsi = 0.f, phi = 0.f, dphi = 0.f;
-      for (int i = lane; i < m; i += 32) {
+      #pragma unroll
+  for (int q_ = 0; q_ < (kMaxN + 31) / 32; ++q_) {
+    const int i = lane + 32 * q_;
+    if (i >= m) break;
         const float di = d[i].x, zi = z[i].x;
         const float del = (di - dof) * (di + dof) - muf;
         const float t = zi / del;
@@ -402,7 +434,10 @@ __global__ void __launch_bounds__(32) k_roots(Ws ws) {
     float dpsi = 0.f, dphi = 0.f;
     {
       const dd dob = LD(d, o);
-      for (int i = lane; i < m; i += 32) {
+      #pragma unroll
+  for (int q_ = 0; q_ < (kMaxN + 31) / 32; ++q_) {
+    const int i = lane + 32 * q_;
+    if (i >= m) break;
         const dd di = LD(d, i);
         const dd del = (di - dob) * (di + dob) - mu;  // d_i^2 - lambda
         const dd zi = LD(z, i);
@@ -541,7 +576,10 @@ __global__ void __launch_bounds__(32) k_zhat(Ws ws) {
   const float2* d = ws.sm.d;
   const dd di = LD(d, i);
   dd prod = dd_of(1.f);
-  for (int k = lane; k < m; k += 32) {
+  #pragma unroll
+  for (int q_ = 0; q_ < (kMaxN + 31) / 32; ++q_) {
+    const int k = lane + 32 * q_;
+    if (k >= m) break;
     const dd dko = LD(d, ws.sm.org[k]);
     const dd lam_m_di = LD(ws.sm.mu, k) - (di - dko) * (di + dko);  // lambda_k - d_i^2
     dd f;
@@ -712,8 +750,7 @@ __device__ void apply_column(const Ws& ws, int j, const StateBuf& st, const Stat
   {
     const int i = tid >> 2, sub = tid & 3;
     dd acc = dzero();
-    if (i < r)
-      for (int k = sub; k < r; k += 4) acc = dd_fma(LD(st.M, (size_t)k * rm + i), LD(v, k), acc);
+    if (i < r) acc = dot_dd(st.M, (size_t)sub * rm + i, (size_t)4 * rm, v, sub, 4, count4(sub, r));
     acc = group4_sum(acc);
     if (i < r && sub == 0) bv[i] = f2_of(dd_fma(LD(ws.sm.w, i), LD(v, r), acc));
   }
@@ -721,7 +758,7 @@ __device__ void apply_column(const Ws& ws, int j, const StateBuf& st, const Stat
   if ((tid >> 5) == 7) {
     const int lane = tid & 31;
     dd t = dzero();
-    for (int k = lane; k < r; k += 32) t = dd_fma(LD(st.rl, k), LD(v, k), t);
+    if (lane < r) t = dot_dd(st.rl, lane, 32, v, lane, 32, (r - lane + 31) >> 5);
     t = dd_warp_sum(t);
     if (lane == 0) rlv[0] = f2_of(t);
   }
@@ -730,8 +767,7 @@ __device__ void apply_column(const Ws& ws, int j, const StateBuf& st, const Stat
     const int item = base + tid;
     const int i = item >> 2, sub = item & 3;
     dd acc = dzero();
-    if (i < r0)
-      for (int k = sub; k < r; k += 4) acc = dd_fma(LD(st.Q, (size_t)k * qld + i), LD(u, k), acc);
+    if (i < r0) acc = dot_dd(st.Q, (size_t)sub * qld + i, (size_t)4 * qld, u, sub, 4, count4(sub, r));
     acc = group4_sum(acc);
     if (i < r0e && sub == 0) qcol[i] = f2_of(dd_fma(LD(ws.sm.qn, i), LD(u, r), acc));
   }
@@ -742,8 +778,7 @@ __device__ void apply_column(const Ws& ws, int j, const StateBuf& st, const Stat
   {
     const int i = tid >> 2, sub = tid & 3;
     dd acc = dzero();
-    if (i < rnew)
-      for (int l = sub; l < n; l += 4) acc = dd_fma(LD(ws.sm.U, (size_t)i * kMaxN + l), LD(bv, l), acc);
+    if (i < rnew) acc = dot_dd(ws.sm.U, (size_t)i * kMaxN + sub, 4, bv, sub, 4, count4(sub, n));
     acc = group4_sum(acc);
     if (i < rnew && sub == 0) nx.M[(size_t)j * rm + i] = f2_of(acc);
   }

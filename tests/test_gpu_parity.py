@@ -140,41 +140,48 @@ def test_wake_full_size_bench_configuration():
 
     With r_max below the number of noise directions, which noise direction each update
     drops hinges on rounding-level differences between nearly equal noise singular values,
-    so results are only as reproducible as the problem is conditioned (reading A11).  The
-    test measures that conditioning: the oracle run again on inputs perturbed by 1e-16
-    relative moves the strong eigenvalues and the rollouts by d_eig and d_pred.  A
-    computation with unit roundoff 2^-47 (the device's double-float) instead of 2^-53 is
-    expected to differ by up to 2^6 times as much, so the bars are max(1e-10, 64 d_eig)
-    for eigenvalues and max(1e-9, 64 d_pred) for rollouts.  The noise-subspace modes
-    (amplitude ~1e-6 of the largest here, noise std 1e-6) are excluded by an amplitude
-    threshold of 1e-3 of the largest, ~1000x above the relative noise amplitude."""
+    and the strong eigenvalues move with the noise directions kept, so results are only as
+    reproducible as this branch choice (reading A11).  The FP64 oracle alone shows it: runs
+    on inputs perturbed by 1e-16 relative differ by 1e-11..4e-11 in the strong
+    eigenvalues, and from ~1e-13 upward the change grows in proportion to the
+    perturbation.  The device's double-float rounding over 120 updates acts like an input
+    perturbation of about sqrt(120) * 2^-47 * 10 (operations per basis element per update)
+    = 8e-13, so the test measures the oracle's change d under a 1e-12 relative
+    perturbation of its inputs (the larger of two) and bars the device at
+    max(1e-10, 4 d) for the strong eigenvalues and max(1e-9, 4 d) for rollouts and check
+    errors.  The noise-subspace modes (amplitude ~1e-6 of the largest here, noise std
+    1e-6) are excluded by an amplitude threshold of 1e-3 of the largest, ~1000x above the
+    relative noise amplitude."""
     g = WakeField(512, 256, sigma=1e-6, seed=0)
     X = g.snapshots(0, 120)
     m, ref = run_pair(X, 40, slack=16)
-    ref2 = OnlineDMDRef(X.shape[1], 40, 1e-10)
-    Xp = X * (1.0 + 1e-16 * np.random.default_rng(1).standard_normal(X.shape))
-    for k in range(Xp.shape[0]):
-        ref2.update(Xp[k])
+    perturbed = []
+    for seed in (1, 2):
+        rp = OnlineDMDRef(X.shape[1], 40, 1e-10)
+        Xp = X * (1.0 + 1e-12 * np.random.default_rng(seed).standard_normal(X.shape))
+        for k in range(Xp.shape[0]):
+            rp.update(Xp[k])
+        perturbed.append(rp)
     assert m.rank == ref.rank == 40
     np.testing.assert_allclose(m.singular_values(), ref.S, rtol=0, atol=1e-10 * ref.S[0])
 
     s_ref = _strong(ref, 1e-3)
-    d_eig = match_eigs(s_ref, _strong(ref2, 1e-3))
+    d_eig = max(match_eigs(s_ref, _strong(rp, 1e-3)) for rp in perturbed)
     lam, amp = m.eigs()
     s_dev = strong_eigs(lam, amp, 1e-3)
     assert len(s_dev) == len(s_ref) >= 7
-    assert match_eigs(s_dev, s_ref) <= max(1e-10, 64 * d_eig), (match_eigs(s_dev, s_ref), d_eig)
+    assert match_eigs(s_dev, s_ref) <= max(1e-10, 4 * d_eig), (match_eigs(s_dev, s_ref), d_eig)
 
     ts = [120.0, 150.0]
     want = ref.predict(ts).T
-    d_pred = np.linalg.norm(ref2.predict(ts).T - want) / np.linalg.norm(want)
+    d_pred = max(np.linalg.norm(rp.predict(ts).T - want) for rp in perturbed) / np.linalg.norm(want)
     got = m.predict(ts).cpu().numpy()
     err = np.linalg.norm(got - want) / np.linalg.norm(want)
-    assert err <= max(1e-9, 64 * d_pred), (err, d_pred)
+    assert err <= max(1e-9, 4 * d_pred), (err, d_pred)
     x_fom = g.snapshot(125)
     e_dev, _ = m.check(125.0, torch.from_numpy(x_fom).cuda())
     e_ref, _ = ref.check(125.0, x_fom)
-    assert abs(e_dev - e_ref) <= max(1e-9, 64 * d_pred)
+    assert abs(e_dev - e_ref) <= max(1e-9, 4 * d_pred)
 
 
 def test_many_tiles_per_cta_small_rank():
