@@ -297,6 +297,56 @@ __device__ __forceinline__ void acc2_fma_basis(Acc2& A, f2x xh, f2x xl, f2x yh, 
   }
 }
 
+// acc[r][c] += sum_k L0[t0 + 32 r][k] B[k][j0 + 2c .. j0 + 2c + 1]  (r < R, c < 4) over the
+// nch chunks of the stage's rows, double-float.  B is in shared memory as three planes
+// (hi, lo, -hi) with row stride ldb floats (a multiple of 4) and j0 a multiple of 8, so a
+// column pair loads as a ready FP32x2 operand; a row element is broadcast to both lanes.
+// A warp's lanes take consecutive rows, which keeps the row reads free of bank conflicts.
+template <int ST, int R>
+__device__ __forceinline__ void tile_dot8(const unsigned char* ph, const unsigned char* pl, int rs, int t0, int nch,
+                                          const float* bh, const float* bl, const float* bn, int ldb, int j0,
+                                          Acc2 (&A)[R][4]) {
+  constexpr int E = (ST == ST_BF16) ? 8 : 4;
+#pragma unroll 1
+  for (int q = 0; q < nch; ++q) {
+    float h[R][8], l[R][8];
+#pragma unroll
+    for (int r = 0; r < R; ++r) load_chunk<ST>(ph, pl, rs, t0 + 32 * r, q, h[r], l[r]);
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const int o = (q * E + i) * ldb + j0;
+      const float4 h0 = *reinterpret_cast<const float4*>(bh + o), h1 = *reinterpret_cast<const float4*>(bh + o + 4);
+      const float4 l0 = *reinterpret_cast<const float4*>(bl + o), l1 = *reinterpret_cast<const float4*>(bl + o + 4);
+      const float4 n0 = *reinterpret_cast<const float4*>(bn + o), n1 = *reinterpret_cast<const float4*>(bn + o + 4);
+      const f2x yh[4] = {f2x_pack(h0.x, h0.y), f2x_pack(h0.z, h0.w), f2x_pack(h1.x, h1.y), f2x_pack(h1.z, h1.w)};
+      const f2x yl[4] = {f2x_pack(l0.x, l0.y), f2x_pack(l0.z, l0.w), f2x_pack(l1.x, l1.y), f2x_pack(l1.z, l1.w)};
+      const f2x yn[4] = {f2x_pack(n0.x, n0.y), f2x_pack(n0.z, n0.w), f2x_pack(n1.x, n1.y), f2x_pack(n1.z, n1.w)};
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const f2x xb = f2x_pack(h[r][i], h[r][i]);
+        const f2x xl = f2x_pack(l[r][i], l[r][i]);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc2_fma_basis<ST>(A[r][c], xb, xl, yh[c], yn[c], yl[c]);
+      }
+    }
+  }
+}
+
+// one extra term: acc[r][c] += x[r] B[k][j0 + 2c ..] (the appended column of a compaction)
+template <int ST, int R>
+__device__ __forceinline__ void tile_dot8_term(const float (&xh)[R], const float (&xl)[R], const float* bh,
+                                               const float* bl, const float* bn, int o, Acc2 (&A)[R][4]) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const f2x yh = f2x_pack(bh[o + 2 * c], bh[o + 2 * c + 1]);
+    const f2x yl = f2x_pack(bl[o + 2 * c], bl[o + 2 * c + 1]);
+    const f2x yn = f2x_pack(bn[o + 2 * c], bn[o + 2 * c + 1]);
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      acc2_fma(A[r][c], f2x_pack(xh[r], xh[r]), f2x_pack(xl[r], xl[r]), yh, yn, yl);
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // pass A: the pending column of the previous update (if any) is formed row by row from
 // its stored residual, written to L0 and used at once; then
@@ -825,7 +875,8 @@ __global__ void __launch_bounds__(kThreadsB) k_pass_b(Ws ws) {
     float* jh = col + (kMaxCap + 8);
     float* jl = jh + kTile;
     float* qbh = jl + kTile;                  // [(box columns + 1)][rnew padded] hi
-    float* qbl = qbh + (kMaxCap + 9) * kMaxR;
+    float* qbl = qbh + (kMaxCap + 9) * kMaxR;  // lo
+    float* qbn = qbl + (kMaxCap + 9) * kMaxR;  // -hi
 
     const int epc = (ST == ST_BF16) ? 8 : 4;
     const int kpad = P.nch * epc;
@@ -838,7 +889,7 @@ __global__ void __launch_bounds__(kThreadsB) k_pass_b(Ws ws) {
       coh[k] = h;
       col[k] = l;
     }
-    const int rnp = (rnew + 3) & ~3;  // output columns padded to whole float4s (zeros)
+    const int rnp = (rnew + 7) & ~7;  // output columns padded to whole groups of 8 (zeros)
     const int kch = P.nch * epc;      // basis columns covered by the box (zero rows of QB beyond r0)
     if (!FLUSH) {
       for (int idx = tid; idx < (kch + 1) * rnp; idx += kThreadsB) {
@@ -850,6 +901,7 @@ __global__ void __launch_bounds__(kThreadsB) k_pass_b(Ws ws) {
           q = ws.sm.QB[(size_t)j * (ws.cap + 1) + kk];
         qbh[k * rnp + j] = q.x;
         qbl[k * rnp + j] = q.y;
+        qbn[k * rnp + j] = -q.x;
       }
     }
     if (tid == 0) {
@@ -898,45 +950,70 @@ __global__ void __launch_bounds__(kThreadsB) k_pass_b(Ws ws) {
         __syncthreads();
       }
       if (!FLUSH) {
-        // out[t][j..j+3] = sum_k L0[t][k] QB[k][j..j+3] + j0_t QB[r0][j..j+3]; each thread
-        // one row and 4 adjacent output columns (4 independent accumulators)
+        // out[t][j] = sum_k L0[t][k] QB[k][j] + j0_t QB[r0][j]; a thread takes one row and
+        // 8 adjacent output columns, the lanes of a warp consecutive rows
         const unsigned char* ph = P.plane_h(s);
         const unsigned char* pl = P.plane_l(s);
-        const int nqo = rnp >> 2;
-        for (int idx = tid; idx < rows * nqo; idx += kThreadsB) {
-          const int tt = idx / nqo, j0c = (idx % nqo) * 4;
-          Acc acc[4] = {acc_zero(), acc_zero(), acc_zero(), acc_zero()};
-          for (int q = 0; q < P.nch; ++q) {
-            float h[8], l[8];
-            load_chunk<ST>(ph, pl, P.rs, tt, q, h, l);
+        const int ngrp = rnp >> 3;
+        // results go through shared memory so that whole rows of the new L0 are written at
+        // once: the stage just read holds them, [t][rnew] hi then (double-float) lo, which
+        // fits because a stage holds kTile rows of at least cap elements per plane
+        float* oh = reinterpret_cast<float*>(P.plane_h(s));
+        float* ol = oh + kTile * rnew;
+        float2 res[4][2];
+        const bool mine = tid < kTile * ngrp;
+        const int tt = tid % kTile, j0c = (tid / kTile) * 8;
+        if (mine) {
+          Acc2 acc[1][4];
 #pragma unroll
-            for (int i = 0; i < epcC; ++i) {
-              const int k = q * epcC + i;
-              const float4 bh = *reinterpret_cast<const float4*>(qbh + k * rnp + j0c);
-              const float4 bl = *reinterpret_cast<const float4*>(qbl + k * rnp + j0c);
-              acc_fma(acc[0], h[i], l[i], bh.x, bl.x);
-              acc_fma(acc[1], h[i], l[i], bh.y, bl.y);
-              acc_fma(acc[2], h[i], l[i], bh.z, bl.z);
-              acc_fma(acc[3], h[i], l[i], bh.w, bl.w);
-            }
-          }
+          for (int c = 0; c < 4; ++c) acc[0][c] = acc2_zero();
+          tile_dot8<ST, 1>(ph, pl, P.rs, tt, P.nch, qbh, qbl, qbn, rnp, j0c, acc);
           if (append) {
-            const float4 bh = *reinterpret_cast<const float4*>(qbh + kch * rnp + j0c);
-            const float4 bl = *reinterpret_cast<const float4*>(qbl + kch * rnp + j0c);
-            acc_fma(acc[0], jh[tt], jl[tt], bh.x, bl.x);
-            acc_fma(acc[1], jh[tt], jl[tt], bh.y, bl.y);
-            acc_fma(acc[2], jh[tt], jl[tt], bh.z, bl.z);
-            acc_fma(acc[3], jh[tt], jl[tt], bh.w, bl.w);
+            const float xh[1] = {jh[tt]}, xl[1] = {jl[tt]};
+            tile_dot8_term<ST, 1>(xh, xl, qbh, qbl, qbn, kch * rnp + j0c, acc);
           }
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
-            if (j0c + c < rnew) {
-              const Acc a = acc_norm(acc[c]);
-              store_elem_global<ST>(ws, (size_t)(row0 + tt) * ws.ldg + j0c + c, a.h, a.l);
+            Acc a[2];
+            acc2_split(acc[0][c], a[0], a[1]);
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+              const Acc v = acc_norm(a[e]);
+              res[c][e] = make_float2(v.h, v.l);
             }
           }
         }
+        if constexpr (ST == ST_BF16) {
+          if (mine && tt < rows)
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+              for (int e = 0; e < 2; ++e) {
+                const int col = j0c + 2 * c + e;
+                if (col < rnew) store_elem_global<ST>(ws, (size_t)(row0 + tt) * ws.ldg + col, res[c][e].x, 0.f);
+              }
+        } else {
+          __syncthreads();  // every thread is done reading the stage
+          if (mine)
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+              for (int e = 0; e < 2; ++e) {
+                const int col = j0c + 2 * c + e;
+                if (col < rnew) {
+                  oh[tt * rnew + col] = res[c][e].x;
+                  if constexpr (ST == ST_DD) ol[tt * rnew + col] = res[c][e].y;
+                }
+              }
+          __syncthreads();
+          for (int idx = tid; idx < rows * rnew; idx += kThreadsB) {
+            const int t = idx / rnew, col = idx - t * rnew;
+            store_elem_global<ST>(ws, (size_t)(row0 + t) * ws.ldg + col, oh[idx], ST == ST_DD ? ol[idx] : 0.f);
+          }
+        }
       }
+      // the stage is refilled by TMA (async proxy) after generic reads and writes
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
       if (tid == 0 && li + kStagesB < my_tiles) P.issue(blockIdx.x + (li + kStagesB) * G, s);
     }
@@ -983,17 +1060,22 @@ __global__ void __launch_bounds__(kThreads) k_rollout(Ws ws, int kcols, void* ou
   unsigned char* p = smem + (size_t)kStagesR * P.stage_sz;
   P.bars = reinterpret_cast<uint64_t*>(p);
   p += 8 * kStagesR;
-  // coefficients, float-float, layout [k][kcols]; rows padded to whole chunks with zeros
+  // coefficients, float-float, layout [k][ldc] in three planes (hi, lo, -hi); rows padded to
+  // whole chunks with zeros.  From 3 columns on, a thread computes 2 rows x 8 columns and
+  // the rows are padded to groups of 8 columns (ldc); below that, ldc = kcols.
   const int epc = (ST == ST_BF16) ? 8 : 4;
   const int kpad = P.nch * epc;
+  const bool tiled = !CHECK && kcols >= 3;
+  const int ldc = tiled ? (kcols + 7) & ~7 : kcols;
   float* cfh = reinterpret_cast<float*>(p);
   float* cfl = cfh + (kMaxCap + 8) * kRollK;
-  Acc* part = reinterpret_cast<Acc*>(cfl + (kMaxCap + 8) * kRollK);  // [4][kTile]
+  float* cfn = cfl + (kMaxCap + 8) * kRollK;
+  Acc* part = reinterpret_cast<Acc*>(cfn + (kMaxCap + 8) * kRollK);  // [4][kTile]
 
-  for (int idx = tid; idx < (kMaxCap + 8) * kcols; idx += kThreads) {
-    const int k = idx / kcols, j = idx % kcols;
+  for (int idx = tid; idx < (kMaxCap + 8) * ldc; idx += kThreads) {
+    const int k = idx / ldc, j = idx % ldc;
     float h = 0.f, l = 0.f;
-    if (k < r0) {
+    if (k < r0 && j < kcols) {
       const float2 q = ws.sm.coef[(size_t)j * (ws.cap + 1) + k];
       h = q.x;
       l = q.y;
@@ -1001,6 +1083,7 @@ __global__ void __launch_bounds__(kThreads) k_rollout(Ws ws, int kcols, void* ou
     if (k >= kpad) h = l = 0.f;
     cfh[idx] = h;
     cfl[idx] = l;
+    cfn[idx] = -h;
   }
   if (tid == 0) {
     for (int s = 0; s < kStagesR; ++s) mbar_init(&P.bars[s], 1);
@@ -1032,7 +1115,40 @@ __global__ void __launch_bounds__(kThreads) k_rollout(Ws ws, int kcols, void* ou
     {
       const unsigned char* ph = P.plane_h(s);
       const unsigned char* pl = P.plane_l(s);
-      const int items = kTile * kcols * nsub;
+      if (tiled) {
+        // lanes take rows lane and lane + 32 of the tile, a warp one group of 8 columns
+        snap_t* o = reinterpret_cast<snap_t*>(out);
+        for (int it = tid; it < 32 * (ldc >> 3); it += kThreads) {
+          const int t0 = it & 31, j0 = (it >> 5) * 8;
+          Acc2 acc[2][4];
+#pragma unroll
+          for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[r][c] = acc2_zero();
+          tile_dot8<ST, 2>(ph, pl, P.rs, t0, P.nch, cfh, cfl, cfn, ldc, j0, acc);
+#pragma unroll
+          for (int r = 0; r < 2; ++r) {
+            const int tt = t0 + 32 * r;
+            if (tt >= rows) continue;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              Acc a[2];
+              acc2_split(acc[r][c], a[0], a[1]);
+#pragma unroll
+              for (int e = 0; e < 2; ++e) {
+                const int j = j0 + 2 * c + e;
+                if (j >= kcols) continue;
+                const Acc v = acc_norm(a[e]);
+                if constexpr (ST == ST_DD)
+                  o[(size_t)j * ld + row0 + tt] = join_double(v.h, v.l);
+                else
+                  o[(size_t)j * ld + row0 + tt] = v.h + v.l;
+              }
+            }
+          }
+        }
+      }
+      const int items = tiled ? 0 : kTile * kcols * nsub;
       for (int it = tid; it < items; it += kThreads) {
         const int tt = it % kTile;
         const int rest = it / kTile;
@@ -1210,11 +1326,11 @@ static int smem_a(int prec, int cap) {
 }
 static int smem_b(int prec, int cap) {
   return kStagesB * stage_of(prec, cap) + 8 * kStagesB + 2 * (kMaxCap + 8) * 4 + 2 * kTile * 4 +
-         2 * (kMaxCap + 9) * kMaxR * 4;
+         3 * (kMaxCap + 9) * kMaxR * 4;
 }
 static int smem_r(int prec, int cap) {
   const int sb = prec == ST_DD ? stage_bytes<ST_DD>(cap) : prec == ST_F32 ? stage_bytes<ST_F32>(cap) : stage_bytes<ST_BF16>(cap);
-  return kStagesR * sb + 8 * kStagesR + 2 * (kMaxCap + 8) * kRollK * 4 + 4 * kTile * 8;
+  return kStagesR * sb + 8 * kStagesR + 3 * (kMaxCap + 8) * kRollK * 4 + 4 * kTile * 8;
 }
 
 int tall_smem_bytes(int prec) { return smem_a(prec, kMaxCap); }
