@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(Ws ws) {
   float2* t1 = z + qld;
   float2* p = t1 + qld;
   float2* p2 = p + kMaxN;
-  __shared__ float2 red8[8];
+  __shared__ float2 red8[16];
   __shared__ float2 sc[4];
   __shared__ int isc[4];
   __shared__ float2 dsc[kMaxN], zsc[kMaxN];
@@ -140,7 +140,27 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(Ws ws) {
     yx[i] = red[r0 + i];
   }
   __syncthreads();
-  if (warp == 0) {
+  // p = Q^T ac and w = Q^T y in one pass (4 threads per column j < r; Q has r0 rows, the
+  // appended coordinate lies outside span(L)); one warp with no column work meanwhile
+  // decides whether the residual is appended (rho0 against the truncation threshold)
+  {
+    const int j = tid >> 2, sub = tid & 3;
+    dd ap = dzero(), aw = dzero();
+    if (j < r)
+      for (int i = sub; i < r0; i += 4) {
+        const dd q = LD(sQ, (size_t)j * qld + i);
+        ap = dd_fma(q, LD(ac, i), ap);
+        aw = dd_fma(q, LD(yx, i), aw);
+      }
+    ap = group4_sum(ap);
+    aw = group4_sum(aw);
+    if (j < r && sub == 0) {
+      p[j] = f2_of(ap);
+      ws.sm.w[j] = f2_of(aw);
+    }
+  }
+  const int dwarp = 4 * r <= kPrepThreads - 32 ? 7 : 0;  // a warp without columns when there is one
+  if (warp == dwarp) {
     dd ssq = dzero(), sy = dzero();
     for (int i = lane; i < r0; i += 32) {
       const dd si = LD(red, i);
@@ -174,40 +194,61 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(Ws ws) {
   const int append = isc[0];
   const int r0e = r0 + append;
   const dd thr = dd_of(sc[0]);
-  // p = Q^T ac   (Q has r0 rows; the appended coordinate lies outside span(L))
-  colsum(p, sQ, qld, ac, r0, r);
-  __syncthreads();
-  // z = ac - Q p
-  rowsum(t1, sQ, qld, p, r, r0);
-  __syncthreads();
-  for (int i = tid; i < r0e; i += kPrepThreads) z[i] = i < r0 ? f2_of(LD(ac, i) - LD(t1, i)) : ac[i];
+  // z = ac - Q p (rows < r0; the appended coordinate is ac itself)
+  for (int base = 0; base < 4 * r0e; base += kPrepThreads) {
+    const int i = (base + tid) >> 2, sub = tid & 3;
+    dd acc = dzero();
+    if (i < r0)
+      for (int j = sub; j < r; j += 4) acc = dd_fma(LD(sQ, (size_t)j * qld + i), LD(p, j), acc);
+    acc = group4_sum(acc);
+    if (i < r0e && sub == 0) z[i] = i < r0 ? f2_of(LD(ac, i) - acc) : ac[i];
+  }
   __syncthreads();
   // second Gram-Schmidt pass in the small space: p2 = Q^T z, z -= Q p2, p += p2
   colsum(p2, sQ, qld, z, r0, r);
   __syncthreads();
-  rowsum(t1, sQ, qld, p2, r, r0);
+  for (int base = 0; base < 4 * r0; base += kPrepThreads) {
+    const int i = (base + tid) >> 2, sub = tid & 3;
+    dd acc = dzero();
+    if (i < r0)
+      for (int j = sub; j < r; j += 4) acc = dd_fma(LD(sQ, (size_t)j * qld + i), LD(p2, j), acc);
+    acc = group4_sum(acc);
+    if (i < r0 && sub == 0) z[i] = f2_of(LD(z, i) - acc);
+  }
+  for (int j = tid; j < r; j += kPrepThreads) {
+    p[j] = f2_of(LD(p, j) + LD(p2, j));
+    ws.sm.p[j] = p[j];
+  }
   __syncthreads();
-  for (int i = tid; i < r0; i += kPrepThreads) z[i] = f2_of(LD(z, i) - LD(t1, i));
-  for (int j = tid; j < r; j += kPrepThreads) p[j] = f2_of(LD(p, j) + LD(p2, j));
+  // ||z||^2 and z . y in one block reduction; rho = ||z||, gamma = q_n . y = (z . y) / rho
+  dd zz = dzero(), zy = dzero();
+  for (int i = tid; i < r0e; i += kPrepThreads) {
+    const dd zi = LD(z, i);
+    zz = dd_fma(zi, zi, zz);
+    zy = dd_fma(zi, LD(yx, i), zy);
+  }
+  zz = dd_warp_sum(zz);
+  zy = dd_warp_sum(zy);
+  if (lane == 0) {
+    red8[warp] = f2_of(zz);
+    red8[8 + warp] = f2_of(zy);
+  }
   __syncthreads();
-  dd zz = dzero();
-  for (int i = tid; i < r0e; i += kPrepThreads) zz = dd_fma(LD(z, i), LD(z, i), zz);
-  zz = block_sum256(zz, red8);
+  zz = dzero();
+  zy = dzero();
+  for (int w8 = 0; w8 < 8; ++w8) {
+    zz = zz + LD(red8, w8);
+    zy = zy + LD(red8, 8 + w8);
+  }
   dd rho = dd_sqrt(zz);
   if (!dd_gt(rho, thr)) rho = dzero();
   const dd inv_rho = rho.h > 0.f ? dd_div(dd_of(1.f), rho) : dzero();
-  // w = Q^T y (uses the un-extended y); gamma = qn . yext
-  colsum(ws.sm.w, sQ, qld, yx, r0, r);
-  dd g = dzero();
+  const dd g = zy * inv_rho;
   for (int i = tid; i < r0e; i += kPrepThreads) {
-    const dd q = LD(z, i) * inv_rho;
-    STd(ws.sm.qn, i, q);
+    STd(ws.sm.qn, i, LD(z, i) * inv_rho);
     ws.sm.yext[i] = yx[i];
     if (i < r0) ws.sm.ac[i] = ac[i];
-    g = dd_fma(q, LD(yx, i), g);
   }
-  g = block_sum256(g, red8);
-  for (int j = tid; j < r; j += kPrepThreads) ws.sm.p[j] = p[j];
   if (tid == 0) {
     ctl->rho = f2_of(rho);
     ctl->gamma = f2_of(g);
