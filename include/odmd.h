@@ -198,6 +198,24 @@ odmd_status odmd_profile_enable(odmd_t h, int32_t enable);
  * pass-A launches. */
 odmd_status odmd_profile_read(odmd_t h, double* ms_total, int64_t* launches, int32_t cap, double* mean_r0);
 
+/* Checkpoint / resume (the survey's NEXT-3; the paper has no counterpart).
+ *
+ * odmd_checkpoint_size: bytes of a checkpoint of this handle (host memory).
+ * odmd_save: synchronises, then writes the model's whole state into host_buf (bytes >=
+ *   odmd_checkpoint_size): a header (magic, version, n, r_max, precision, slack, snapshot
+ *   count, FNV-1a checksum over 8-byte words) followed by the raw device state -- control block, committed
+ *   state buffers with the small scratch, rows 0..n-1 of the tall factor, both snapshot
+ *   slots and the stored residual.  The host buffer is the caller's; nothing is kept.
+ * odmd_load: restores such a checkpoint into a handle created with the same n, r_max,
+ *   precision and slack (trunc_tol, check_tol and refine_every are the new handle's), on
+ *   a device of the same kind.  Updates, predictions and checks then continue exactly as
+ *   they would have in the saved handle.  Errors: ODMD_ERR_ARG for a NULL pointer, a
+ *   short or truncated buffer, a foreign or corrupted checkpoint (bad magic, version or
+ *   checksum) or a different configuration; ODMD_ERR_CUDA. */
+odmd_status odmd_checkpoint_size(odmd_t h, size_t* bytes);
+odmd_status odmd_save(odmd_t h, void* host_buf, size_t bytes);
+odmd_status odmd_load(odmd_t h, const void* host_buf, size_t bytes);
+
 /* Release the handle (synchronises first).  The workspace is the caller's again. */
 odmd_status odmd_destroy(odmd_t h);
 

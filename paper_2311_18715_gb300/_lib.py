@@ -16,7 +16,8 @@ EXPORTED = [
     "odmd_check", "odmd_sync", "odmd_get_rank", "odmd_get_singular_values", "odmd_get_eigs",
     "odmd_get_basis", "odmd_get_counts", "odmd_destroy", "odmd_last_error",
     "odmd_profile_enable", "odmd_profile_read", "odmd_check_noalloc", "odmd_hybrid_step",
-    "odmd_update_batch", "odmd_predict_batch", "odmd_refine",
+    "odmd_update_batch", "odmd_predict_batch", "odmd_refine", "odmd_checkpoint_size", "odmd_save",
+    "odmd_load",
 ]
 KERNEL_CLASSES = ["pass_a", "small", "pass_b", "eig", "coef", "rollout", "check", "first", "refine"]
 
@@ -65,6 +66,9 @@ def load_library(path: str | None = None) -> C.CDLL:
         "odmd_hybrid_step": [vp, vp, dbl, vp, C.POINTER(i32), C.POINTER(dbl)],
         "odmd_update_batch": [C.POINTER(vp), C.POINTER(vp), i32],
         "odmd_refine": [vp],
+        "odmd_checkpoint_size": [vp, C.POINTER(C.c_size_t)],
+        "odmd_save": [vp, vp, C.c_size_t],
+        "odmd_load": [vp, vp, C.c_size_t],
         "odmd_predict_batch": [C.POINTER(vp), C.POINTER(C.POINTER(dbl)), C.POINTER(i32), C.POINTER(vp),
                                C.POINTER(i64), i32],
         "odmd_sync": [vp],

@@ -735,6 +735,161 @@ odmd_status odmd_refine(odmd_t h) {
   return ODMD_OK;
 }
 
+// ---- checkpoint / resume
+// A checkpoint is a header followed by the raw bytes of every part of the workspace that
+// survives from one call to the next: the control block, the two committed-state buffers
+// with the small and eigen scratch after them, the rows 0..n-1 of the tall factor L0
+// (each plane), both snapshot slots and the stored residual.  The tensor maps (they hold
+// device addresses) and the per-call scratch are not saved.  A checkpoint loads into any
+// handle created with the same n, r_max, precision and slack on a device of the same
+// kind; the resumed model then continues bit for bit as the saved one would have.
+namespace {
+struct CkptHeader {
+  char magic[8];
+  uint32_t version, header_bytes;
+  int64_t n;
+  int32_t r_max, prec, slack, cap, ldg, ctl_bytes;
+  int64_t nsnap;
+  int32_t cur_h, curc_h;
+  uint64_t region[6];  // bytes: control block, state block, L0 hi rows, L0 lo rows, snapshots, residual
+  uint64_t checksum;   // FNV-1a (8-byte words) over the regions
+};
+constexpr char kCkptMagic[8] = {'O', 'D', 'M', 'D', 'C', 'K', 'P', '1'};
+
+struct CkptRegion {
+  size_t off, bytes;
+};
+
+void ckpt_regions(const odmd_t h, CkptRegion out[7]) {
+  const Layout L = make_layout(h->cfg);
+  const size_t n = (size_t)h->cfg.n;
+  const size_t row = (size_t)L.ldg * esz_of(h->cfg.prec);
+  const size_t snap = n * vsz_of(h->cfg.prec);
+  out[0] = {L.off_ctl, sizeof(Ctl)};
+  out[1] = {L.off_hdr[0], L.off_part - L.off_hdr[0]};
+  out[2] = {L.off_Lh, n * row};
+  out[3] = {L.off_Ll, h->cfg.prec == ODMD_FP64 ? n * row : 0};
+  out[4] = {L.off_c[0], snap};
+  out[5] = {L.off_c[1], snap};
+  out[6] = {L.off_e, n * sizeof(float2)};
+}
+
+// FNV-1a over 8-byte little-endian words (then the tail bytes)
+uint64_t fnv1a(uint64_t hsh, const unsigned char* p, size_t bytes) {
+  size_t i = 0;
+  for (; i + 8 <= bytes; i += 8) {
+    uint64_t w;
+    std::memcpy(&w, p + i, 8);
+    hsh ^= w;
+    hsh *= 1099511628211ull;
+  }
+  for (; i < bytes; ++i) {
+    hsh ^= p[i];
+    hsh *= 1099511628211ull;
+  }
+  return hsh;
+}
+
+size_t ckpt_bytes(const odmd_t h) {
+  CkptRegion R[7];
+  ckpt_regions(h, R);
+  size_t b = sizeof(CkptHeader);
+  for (const CkptRegion& r : R) b += r.bytes;
+  return b;
+}
+}  // namespace
+
+odmd_status odmd_checkpoint_size(odmd_t h, size_t* bytes) {
+  if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
+  if (!bytes) return fail(h, ODMD_ERR_ARG, "bytes must not be NULL");
+  *bytes = ckpt_bytes(h);
+  return ODMD_OK;
+}
+
+odmd_status odmd_save(odmd_t h, void* host_buf, size_t bytes) {
+  if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
+  if (!host_buf) return fail(h, ODMD_ERR_ARG, "host buffer must not be NULL");
+  const size_t need = ckpt_bytes(h);
+  if (bytes < need) return fail(h, ODMD_ERR_ARG, "checkpoint buffer of " + std::to_string(bytes) +
+                                                   " bytes is smaller than the " + std::to_string(need) + " needed");
+  CK(h, cudaStreamSynchronize(h->stream), "save: sync");
+  CkptRegion R[7];
+  ckpt_regions(h, R);
+  const Layout L = make_layout(h->cfg);
+  CkptHeader hd{};
+  std::memcpy(hd.magic, kCkptMagic, 8);
+  hd.version = 1;
+  hd.header_bytes = sizeof(CkptHeader);
+  hd.n = h->cfg.n;
+  hd.r_max = h->cfg.r_max;
+  hd.prec = h->cfg.prec;
+  hd.slack = h->cfg.slack;
+  hd.cap = L.cap;
+  hd.ldg = L.ldg;
+  hd.ctl_bytes = (int32_t)sizeof(Ctl);
+  hd.nsnap = h->nsnap;
+  hd.cur_h = h->cur_h;
+  hd.curc_h = h->curc_h;
+  hd.region[0] = R[0].bytes;
+  hd.region[1] = R[1].bytes;
+  hd.region[2] = R[2].bytes;
+  hd.region[3] = R[3].bytes;
+  hd.region[4] = R[4].bytes + R[5].bytes;
+  hd.region[5] = R[6].bytes;
+  unsigned char* out = static_cast<unsigned char*>(host_buf) + sizeof(CkptHeader);
+  const unsigned char* base = reinterpret_cast<const unsigned char*>(h->ws.ctl) - L.off_ctl;  // workspace start
+  uint64_t hsh = 1469598103934665603ull;
+  for (const CkptRegion& r : R) {
+    if (r.bytes) CK(h, cudaMemcpy(out, base + r.off, r.bytes, cudaMemcpyDeviceToHost), "save: copy");
+    hsh = fnv1a(hsh, out, r.bytes);
+    out += r.bytes;
+  }
+  hd.checksum = hsh;
+  std::memcpy(host_buf, &hd, sizeof hd);
+  return ODMD_OK;
+}
+
+odmd_status odmd_load(odmd_t h, const void* host_buf, size_t bytes) {
+  if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
+  if (!host_buf) return fail(h, ODMD_ERR_ARG, "host buffer must not be NULL");
+  if (bytes < sizeof(CkptHeader)) return fail(h, ODMD_ERR_ARG, "checkpoint shorter than its header");
+  CkptHeader hd;
+  std::memcpy(&hd, host_buf, sizeof hd);
+  if (std::memcmp(hd.magic, kCkptMagic, 8) != 0 || hd.version != 1 || hd.header_bytes != sizeof(CkptHeader))
+    return fail(h, ODMD_ERR_ARG, "not a checkpoint of this library version");
+  const Layout L = make_layout(h->cfg);
+  if (hd.n != h->cfg.n || hd.r_max != h->cfg.r_max || hd.prec != h->cfg.prec || hd.slack != h->cfg.slack ||
+      hd.cap != L.cap || hd.ldg != L.ldg || hd.ctl_bytes != (int32_t)sizeof(Ctl))
+    return fail(h, ODMD_ERR_ARG, "checkpoint of a different configuration (n, r_max, precision or slack)");
+  if (bytes < ckpt_bytes(h)) return fail(h, ODMD_ERR_ARG, "checkpoint truncated");
+  CkptRegion R[7];
+  ckpt_regions(h, R);
+  if (hd.region[0] != R[0].bytes || hd.region[1] != R[1].bytes || hd.region[2] != R[2].bytes ||
+      hd.region[3] != R[3].bytes || hd.region[4] != R[4].bytes + R[5].bytes || hd.region[5] != R[6].bytes)
+    return fail(h, ODMD_ERR_ARG, "checkpoint regions do not match this handle's layout");
+  const unsigned char* in = static_cast<const unsigned char*>(host_buf) + sizeof(CkptHeader);
+  uint64_t hsh = 1469598103934665603ull;
+  {
+    const unsigned char* p = in;
+    for (const CkptRegion& r : R) {
+      hsh = fnv1a(hsh, p, r.bytes);
+      p += r.bytes;
+    }
+  }
+  if (hsh != hd.checksum) return fail(h, ODMD_ERR_ARG, "checkpoint checksum mismatch (corrupted data)");
+  CK(h, cudaStreamSynchronize(h->stream), "load: sync");
+  unsigned char* base = reinterpret_cast<unsigned char*>(h->ws.ctl) - L.off_ctl;
+  for (const CkptRegion& r : R) {
+    if (r.bytes) CK(h, cudaMemcpy(base + r.off, in, r.bytes, cudaMemcpyHostToDevice), "load: copy");
+    in += r.bytes;
+  }
+  h->nsnap = hd.nsnap;
+  h->cur_h = hd.cur_h;
+  h->curc_h = hd.curc_h;
+  h->eig_dirty = true;
+  return ODMD_OK;
+}
+
 odmd_status odmd_hybrid_step(odmd_t h, const void* x_fom_dev, double tol, void* state_out_dev, int32_t* accepted,
                              double* rel_err) {
   if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");

@@ -113,6 +113,20 @@ class OnlineDMD:
         """odmd_refine: restore L^T L = I now (needs refine_every > 0 at construction)."""
         self._ck(self._lib.odmd_refine(self._h))
 
+    def save(self) -> bytes:
+        """odmd_save: the model's whole state as a host checkpoint (synchronises)."""
+        nb = C.c_size_t()
+        self._ck(self._lib.odmd_checkpoint_size(self._h, C.byref(nb)))
+        buf = C.create_string_buffer(nb.value)
+        self._ck(self._lib.odmd_save(self._h, buf, nb.value))
+        return buf.raw
+
+    def load(self, checkpoint: bytes) -> None:
+        """odmd_load: continue from a checkpoint of a handle with the same n, r_max,
+        precision and slack."""
+        buf = C.create_string_buffer(bytes(checkpoint), len(checkpoint))
+        self._ck(self._lib.odmd_load(self._h, buf, len(checkpoint)))
+
     def sync(self) -> None:
         self._ck(self._lib.odmd_sync(self._h))
 

@@ -60,3 +60,7 @@ def test_footprint_and_argument_checks_on_host():
     assert lib.odmd_footprint(C.byref(bad), C.byref(nb)) == 1
     assert b"BF16" in lib.odmd_last_error(None)
     assert lib.odmd_update(None, None) == 1
+    # checkpoint entry points refuse a NULL handle before touching the device
+    assert lib.odmd_checkpoint_size(None, None) == 1
+    assert lib.odmd_save(None, None, 0) == 1
+    assert lib.odmd_load(None, None, 0) == 1
