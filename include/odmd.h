@@ -198,6 +198,34 @@ odmd_status odmd_profile_enable(odmd_t h, int32_t enable);
  * pass-A launches. */
 odmd_status odmd_profile_read(odmd_t h, double* ms_total, int64_t* launches, int32_t cap, double* mean_r0);
 
+/* One step of the hybrid FOM/ROM loop with the paper's own credibility test (Sec. 2.2:
+ * the residual of the FOM's discrete system at the predicted state; the survey's NEXT-4).
+ *
+ * The step taken is t = number of snapshots received so far.  With a model, the library
+ * predicts u(t) into state_out_dev and calls residual(user, t, state_out_dev, r_dev, b_dev,
+ * stream): the caller's host function enqueues on `stream` (the handle's stream, a
+ * cudaStream_t) the work that writes the right-hand side b of the FOM's step t into b_dev
+ * and the residual r = b - A u of the predicted state into r_dev, and returns 0 (nonzero
+ * reports a failure).  The library then forms ||r|| / ||b|| on the device (FP64 sums) and
+ * accepts the prediction when it is <= tol (tol <= 0: the handle's check_tol).  Without a
+ * model, or when the prediction is refused, it calls fom(user, t, state_out_dev, stream),
+ * which enqueues the FOM's solve of step t into state_out_dev.  The state taken joins the
+ * snapshot stream (odmd_update).  The callbacks keep whatever history their FOM needs:
+ * before the call, state_out_dev holds nothing the library reads.
+ *
+ * state_out_dev, r_dev, b_dev: three distinct device buffers of n elements of the snapshot
+ * type (double for ODMD_FP64, float for ODMD_FP32), owned by the caller.  accepted (1 if
+ * the prediction was taken) and rel_res (the relative residual, +inf when no prediction
+ * was made) are host outputs, either may be NULL.  Synchronises once per step with a
+ * model.  Errors: ODMD_ERR_ARG (NULL or aliased pointers), ODMD_ERR_STATE (a callback
+ * returned nonzero), ODMD_ERR_CUDA, ODMD_ERR_NUMERIC (non-finite residual). */
+typedef int32_t (*odmd_residual_fn)(void* user, int64_t step, const void* u_dev, void* r_dev, void* b_dev,
+                                    void* stream);
+typedef int32_t (*odmd_fom_fn)(void* user, int64_t step, void* u_dev, void* stream);
+odmd_status odmd_hybrid_step_residual(odmd_t h, odmd_residual_fn residual, odmd_fom_fn fom, void* user, double tol,
+                                      void* state_out_dev, void* r_dev, void* b_dev, int32_t* accepted,
+                                      double* rel_res);
+
 /* Checkpoint / resume (the survey's NEXT-3; the paper has no counterpart).
  *
  * odmd_checkpoint_size: bytes of a checkpoint of this handle (host memory).

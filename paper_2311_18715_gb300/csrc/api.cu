@@ -920,6 +920,43 @@ odmd_status odmd_hybrid_step(odmd_t h, const void* x_fom_dev, double tol, void* 
   return ODMD_OK;
 }
 
+odmd_status odmd_hybrid_step_residual(odmd_t h, odmd_residual_fn residual, odmd_fom_fn fom, void* user, double tol,
+                                      void* state_out_dev, void* r_dev, void* b_dev, int32_t* accepted,
+                                      double* rel_res) {
+  if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
+  if (!residual || !fom) return fail(h, ODMD_ERR_ARG, "the residual and FOM callbacks must not be NULL");
+  if (!state_out_dev || !r_dev || !b_dev) return fail(h, ODMD_ERR_ARG, "state_out, r and b must not be NULL");
+  if (state_out_dev == r_dev || state_out_dev == b_dev || r_dev == b_dev)
+    return fail(h, ODMD_ERR_ARG, "state_out, r and b must be three different buffers");
+  if (tol <= 0.0) tol = h->cfg.check_tol;
+  const int64_t step = h->nsnap;  // the step about to be taken, counted from u^0
+  int32_t acc = 0;
+  double rel = INFINITY;
+  if (h->nsnap >= 2) {
+    const double t = (double)step;
+    odmd_status s = odmd_predict(h, &t, 1, state_out_dev, h->cfg.n);
+    if (s != ODMD_OK && s != ODMD_ERR_STATE) return s;
+    if (s == ODMD_OK) {  // (ODMD_ERR_STATE: no model yet, every snapshot so far was zero)
+      if (residual(user, step, state_out_dev, r_dev, b_dev, h->stream) != 0)
+        return fail(h, ODMD_ERR_STATE, "residual callback reported a failure");
+      CK(h, launch_norm_ratio(h->ws, r_dev, b_dev, h->stream), "residual norm launch");
+      CK(h, cudaMemcpyAsync(h->pinned, h->ws.out2, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+         "read back");
+      if (odmd_status s2 = device_status(h)) return s2;
+      const double num = h->pinned[0], den = h->pinned[1];
+      rel = den > 0.0 ? std::sqrt(num / den) : (num == 0.0 ? 0.0 : INFINITY);
+      acc = rel <= tol ? 1 : 0;
+    }
+  }
+  if (!acc && fom(user, step, state_out_dev, h->stream) != 0)
+    return fail(h, ODMD_ERR_STATE, "FOM callback reported a failure");
+  // the state taken, accepted prediction or FOM state, joins the snapshot stream
+  if (odmd_status s = odmd_update(h, state_out_dev)) return s;
+  if (accepted) *accepted = acc;
+  if (rel_res) *rel_res = rel;
+  return ODMD_OK;
+}
+
 odmd_status odmd_update_batch(odmd_t* hs, const void* const* xs, int32_t count) {
   if (count < 0 || (count > 0 && (!hs || !xs))) return fail(nullptr, ODMD_ERR_ARG, "update_batch: bad arguments");
   for (int32_t i = 0; i < count; ++i) {

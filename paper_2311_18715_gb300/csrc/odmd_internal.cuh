@@ -454,6 +454,7 @@ int stages_a(int prec, int cap);  // pass A pipeline depth for this storage form
 // small.cu
 cudaError_t launch_small(const Ws& ws, cudaStream_t s);
 cudaError_t prepare_refine();
+cudaError_t launch_norm_ratio(const Ws& ws, const void* r, const void* b, cudaStream_t s);  // sum r^2, sum b^2 -> out2
 cudaError_t launch_refine(const Ws& ws, int cur, cudaStream_t s);  // Gram pass + small refinement
 cudaError_t launch_eig(const Ws& ws, cudaStream_t s);
 cudaError_t launch_coef(const Ws& ws, const double* t_host, int k, cudaStream_t s);  // k <= kRollK, t on the host

@@ -113,6 +113,48 @@ class OnlineDMD:
         """odmd_refine: restore L^T L = I now (needs refine_every > 0 at construction)."""
         self._ck(self._lib.odmd_refine(self._h))
 
+    def hybrid_step_residual(self, residual, fom, state_out: torch.Tensor, r: torch.Tensor, b: torch.Tensor,
+                             tol: float = 0.0) -> tuple[bool, float]:
+        """odmd_hybrid_step_residual: one hybrid step with the residual credibility test.
+
+        residual(step) must fill r with b - A u and b with the right-hand side of the FOM's
+        step for the predicted state held in state_out; fom(step) must write the FOM's state
+        of that step into state_out.  Both run on this model's stream (torch work inside
+        them is enqueued there).  Returns (accepted, relative residual)."""
+        from ._lib import FOM_FN, RESIDUAL_FN
+        for tns in (state_out, r, b):
+            if tns.shape != (self.n,) or tns.dtype != self.dtype or not tns.is_contiguous():
+                raise ValueError("state_out, r and b must be contiguous (n,) tensors of the snapshot dtype")
+        failure = []
+
+        def _res(user, step, u, rr, bb, stream):
+            try:
+                with torch.cuda.stream(self.stream):
+                    residual(int(step))
+                return 0
+            except Exception as e:  # reported to the library as a failed callback
+                failure.append(e)
+                return 1
+
+        def _fom(user, step, u, stream):
+            try:
+                with torch.cuda.stream(self.stream):
+                    fom(int(step))
+                return 0
+            except Exception as e:
+                failure.append(e)
+                return 1
+
+        cres, cfom = RESIDUAL_FN(_res), FOM_FN(_fom)
+        acc, rel = C.c_int32(), C.c_double()
+        st = self._lib.odmd_hybrid_step_residual(self._h, cres, cfom, None, float(tol),
+                                                 C.c_void_p(state_out.data_ptr()), C.c_void_p(r.data_ptr()),
+                                                 C.c_void_p(b.data_ptr()), C.byref(acc), C.byref(rel))
+        if failure:
+            raise failure[0]
+        self._ck(st)
+        return bool(acc.value), float(rel.value)
+
     def save(self) -> bytes:
         """odmd_save: the model's whole state as a host checkpoint (synchronises)."""
         nb = C.c_size_t()

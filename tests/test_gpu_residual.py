@@ -1,0 +1,147 @@
+"""The hybrid step with the residual credibility test (odmd_hybrid_step_residual; Sec. 2.2
+of the paper, the survey's NEXT-4) against the same controller written with the oracle.
+
+The FOM stand-in is a linear implicit step, so that A u = b exists: forced diffusion on a
+periodic grid, (I - alpha Lap) u_{k+1} = u_k + f_{k+1}, with f periodic in time, solved
+exactly through the FFT.  A prediction u is credible when ||b - A u|| / ||b|| <= tol; the
+FOM solve is called only for the steps whose prediction is refused.  The stream is a finite
+sum of exponentials (three decaying modes and the forced response oscillating at the
+forcing frequency), so once the model holds them the relative residual drops from ~1 to
+far below tol = 1e-7, and device and oracle take the same decisions.
+"""
+import numpy as np
+import pytest
+
+from oracle import OnlineDMDRef
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+NX, NY, ALPHA, PERIOD = 48, 40, 0.3, 40.0
+
+
+def _fields():
+    """Initial field, forcing shapes and the FFT symbol of I - alpha Lap.  The forced Fourier
+    modes start on their periodic steady state Re(W e^{i w k}), W = (s1 - i s2) e^{iw} /
+    (den e^{iw} - 1) mode by mode, so the stream is 3 decaying modes plus one oscillating
+    pair in 5 independent directions: a linear map reproduces it exactly.  (Started from
+    zero instead, the forced modes would also carry decaying transients in the same
+    directions, 8 exponentials in 6 directions, and no DMD could fit them to better than
+    ~1e-7.)"""
+    x = 2 * np.pi * np.arange(NX)[:, None] / NX
+    y = 2 * np.pi * np.arange(NY)[None, :] / NY
+    s1 = np.cos(x) + 0.3 * np.sin(2 * y)
+    s2 = 0.7 * np.cos(x + 2 * y)
+    p = np.arange(NX)[:, None]
+    q = np.arange(NY)[None, :]
+    den = 1.0 + ALPHA * (4 * np.sin(np.pi * p / NX) ** 2 + 4 * np.sin(np.pi * q / NY) ** 2)
+    e = np.exp(2j * np.pi / PERIOD)
+    W = np.fft.ifft2(np.fft.fft2(s1 - 1j * s2) * e / (den * e - 1.0))
+    u0 = np.cos(x + y) + 0.5 * np.sin(2 * x - y) + 0.25 * np.cos(3 * y) + W.real
+    return u0, s1, s2, den
+
+
+def _force(s1, s2, k):
+    w = 2 * np.pi * k / PERIOD
+    return s1 * np.cos(w) + s2 * np.sin(w)
+
+
+def oracle_hybrid(steps, r_max, tol):
+    u0, s1, s2, den = _fields()
+    A = lambda u: u - ALPHA * (np.roll(u, 1, 0) + np.roll(u, -1, 0) + np.roll(u, 1, 1) + np.roll(u, -1, 1) - 4 * u)
+    ref = OnlineDMDRef(NX * NY, r_max, 1e-10)
+    prev = u0.copy()
+    ref.update(prev.ravel())
+    accepted, rels, taken = [], [], []
+    for k in range(1, steps):
+        b = prev + _force(s1, s2, k)
+        ok, rel = False, np.inf
+        if k >= 2 and ref.rank > 0:
+            u = ref.predict([float(k)])[:, 0].reshape(NX, NY)
+            rel = np.linalg.norm(b - A(u)) / np.linalg.norm(b)
+            ok = rel <= tol
+        if not ok:
+            u = np.fft.ifft2(np.fft.fft2(b) / den).real
+        ref.update(u.ravel())
+        prev = u
+        accepted.append(bool(ok))
+        rels.append(rel)
+        taken.append(u.ravel().copy())
+    return ref, accepted, rels, np.array(taken)
+
+
+def test_residual_step_matches_oracle_controller():
+    import paper_2311_18715_gb300 as pkg
+
+    steps, r_max, tol = 120, 12, 1e-7
+    ref, acc_ref, rel_ref, taken_ref = oracle_hybrid(steps, r_max, tol)
+    u0, s1, s2, den = _fields()
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    s1d, s2d, dend = dev(s1), dev(s2), dev(den)
+    m = pkg.OnlineDMD(NX * NY, r_max, trunc_tol=1e-10, slack=8)
+    state = dev(u0.ravel()).clone()
+    r = torch.empty_like(state)
+    b = torch.empty_like(state)
+    prev = state.clone().view(NX, NY)
+    m.update(state)
+    fom_calls = [0]
+
+    def force(k):
+        w = 2 * np.pi * k / PERIOD
+        return s1d * np.cos(w) + s2d * np.sin(w)
+
+    def A(u):
+        return u - ALPHA * (torch.roll(u, 1, 0) + torch.roll(u, -1, 0) + torch.roll(u, 1, 1) + torch.roll(u, -1, 1)
+                            - 4 * u)
+
+    def residual(k):
+        bb = prev + force(k)
+        b.copy_(bb.view(-1))
+        r.copy_((bb - A(state.view(NX, NY))).view(-1))
+
+    def fom(k):
+        fom_calls[0] += 1
+        state.copy_(torch.fft.ifft2(torch.fft.fft2(prev + force(k)) / dend).real.reshape(-1))
+
+    acc, rels, taken = [], [], []
+    for k in range(1, steps):
+        ok, rel = m.hybrid_step_residual(residual, fom, state, r, b, tol)
+        prev.copy_(state.view(NX, NY))
+        acc.append(ok)
+        rels.append(rel)
+        taken.append(state.cpu().numpy().copy())
+    assert acc == acc_ref
+    assert fom_calls[0] == len(acc) - sum(acc)
+    assert sum(acc) >= 0.8 * len(acc)      # the ROM replaces most FOM solves
+    # a prediction within 1e-9 of the oracle's (the rollout parity bar) moves the relative
+    # residual by at most ||A|| 1e-9 per side, ||A|| <= 1 + 8 alpha = 3.4
+    for e, er in zip(rels, rel_ref):
+        assert (np.isinf(e) and np.isinf(er)) or abs(e - er) <= 1e-8 + 1e-6 * er
+        assert np.isinf(er) or abs(er - tol) > 1e-3 * tol   # no near-tie in the decisions
+    # the implicit operator has ||A^-1|| <= 1, so a state taken with residual <= tol is within
+    # tol ||b|| of the FOM's state from the same previous one, and differences do not grow
+    taken = np.array(taken)
+    diff = np.linalg.norm(taken - taken_ref, axis=1) / np.linalg.norm(taken_ref, axis=1)
+    assert diff.max() <= 4 * tol, diff.max()
+
+
+def test_residual_step_callback_failures_are_reported():
+    import paper_2311_18715_gb300 as pkg
+
+    m = pkg.OnlineDMD(64, 4)
+    s = torch.ones(64, dtype=torch.float64, device="cuda")
+    r, b = torch.empty_like(s), torch.empty_like(s)
+
+    def fom(k):
+        s.mul_(0.9)
+
+    def bad_residual(k):
+        raise RuntimeError("residual not available")
+
+    for _ in range(2):
+        ok, rel = m.hybrid_step_residual(bad_residual, fom, s, r, b)  # no model yet: FOM only
+        assert not ok and np.isinf(rel)
+    with pytest.raises(RuntimeError):
+        m.hybrid_step_residual(bad_residual, fom, s, r, b)
+    with pytest.raises(pkg.OdmdError):
+        m.hybrid_step_residual(bad_residual, fom, s, s, b)  # aliased buffers are refused
