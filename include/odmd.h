@@ -226,6 +226,34 @@ odmd_status odmd_hybrid_step_residual(odmd_t h, odmd_residual_fn residual, odmd_
                                       void* state_out_dev, void* r_dev, void* b_dev, int32_t* accepted,
                                       double* rel_res);
 
+/* The hybrid loop up to t_final with the convergence exit of Sec. 2.1 (the survey's NEXT-1):
+ * steps t = (snapshots so far) .. t_final are taken with odmd_hybrid_step_residual (same
+ * callbacks, buffers and tol).  Every check_every-th step, once a model exists, the DMD
+ * eigenvalues of the modes that carry the field (amplitude >= 1e-6 of the largest) are
+ * compared with those of the previous check; the paper does not define convergence, and
+ * the reading taken is: conv_checks consecutive checks with the rank unchanged and every
+ * such eigenvalue within conv_tol of the nearest one of the previous check.  Then the
+ * remaining steps are skipped and u(t_final) is predicted into state_out_dev directly.
+ * Otherwise state_out_dev ends holding the state taken at t_final.
+ *
+ * prev_dev: a fourth device buffer of n elements (caller's): on entry it must hold the
+ * state taken at the step before the first one of the run; after every step the library
+ * copies the state taken into it, so the callbacks of step t read u(t-1) there (state_out
+ * holds the prediction of step t while they run).
+ *
+ * report (host, may be NULL): steps taken, FOM calls, accepted predictions, whether the
+ * model converged, the step at which it did (-1 if not) and the steps skipped.  Errors:
+ * those of odmd_hybrid_step_residual; ODMD_ERR_ARG for t_final before the next step,
+ * check_every or conv_checks < 1, conv_tol <= 0. */
+typedef struct {
+  int64_t steps, fom_calls, accepted;
+  int32_t converged, pad;
+  int64_t converged_at, skipped;
+} odmd_run_report;
+odmd_status odmd_hybrid_run(odmd_t h, odmd_residual_fn residual, odmd_fom_fn fom, void* user, double tol,
+                            int64_t t_final, int32_t check_every, int32_t conv_checks, double conv_tol,
+                            void* state_out_dev, void* prev_dev, void* r_dev, void* b_dev, odmd_run_report* report);
+
 /* Checkpoint / resume (the survey's NEXT-3; the paper has no counterpart).
  *
  * odmd_checkpoint_size: bytes of a checkpoint of this handle (host memory).

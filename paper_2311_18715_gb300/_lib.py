@@ -17,11 +17,16 @@ EXPORTED = [
     "odmd_get_basis", "odmd_get_counts", "odmd_destroy", "odmd_last_error",
     "odmd_profile_enable", "odmd_profile_read", "odmd_check_noalloc", "odmd_hybrid_step",
     "odmd_update_batch", "odmd_predict_batch", "odmd_refine", "odmd_checkpoint_size", "odmd_save",
-    "odmd_load", "odmd_hybrid_step_residual",
+    "odmd_load", "odmd_hybrid_step_residual", "odmd_hybrid_run",
 ]
 # host callbacks of odmd_hybrid_step_residual: (user, step, u, r, b, stream) and (user, step, u, stream)
 RESIDUAL_FN = C.CFUNCTYPE(C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p)
 FOM_FN = C.CFUNCTYPE(C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p)
+
+
+class RunReport(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("fom_calls", C.c_int64), ("accepted", C.c_int64), ("converged", C.c_int32),
+                ("pad", C.c_int32), ("converged_at", C.c_int64), ("skipped", C.c_int64)]
 KERNEL_CLASSES = ["pass_a", "small", "pass_b", "eig", "coef", "rollout", "check", "first", "refine"]
 
 
@@ -74,6 +79,8 @@ def load_library(path: str | None = None) -> C.CDLL:
         "odmd_load": [vp, vp, C.c_size_t],
         "odmd_hybrid_step_residual": [vp, RESIDUAL_FN, FOM_FN, vp, C.c_double, vp, vp, vp, C.POINTER(i32),
                                       C.POINTER(C.c_double)],
+        "odmd_hybrid_run": [vp, RESIDUAL_FN, FOM_FN, vp, C.c_double, C.c_int64, i32, i32, C.c_double, vp, vp, vp,
+                            vp, C.POINTER(RunReport)],
         "odmd_predict_batch": [C.POINTER(vp), C.POINTER(C.POINTER(dbl)), C.POINTER(i32), C.POINTER(vp),
                                C.POINTER(i64), i32],
         "odmd_sync": [vp],

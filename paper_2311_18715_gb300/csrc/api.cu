@@ -957,6 +957,98 @@ odmd_status odmd_hybrid_step_residual(odmd_t h, odmd_residual_fn residual, odmd_
   return ODMD_OK;
 }
 
+namespace {
+// DMD eigenvalues of the modes that carry the field (amplitude >= 1e-6 of the largest, the
+// threshold below which parity of noise-subspace modes is not asked), host copies
+odmd_status strong_eigs(odmd_t h, std::vector<double>& re, std::vector<double>& im, int32_t* rank) {
+  double lr[kMaxR], li[kMaxR], am[kMaxR];
+  if (odmd_status s = odmd_get_eigs(h, lr, li, am, kMaxR, rank)) return s;
+  double amax = 0.0;
+  for (int i = 0; i < *rank; ++i) amax = am[i] > amax ? am[i] : amax;
+  re.clear();
+  im.clear();
+  for (int i = 0; i < *rank; ++i)
+    if (am[i] >= 1e-6 * amax) {
+      re.push_back(lr[i]);
+      im.push_back(li[i]);
+    }
+  return ODMD_OK;
+}
+
+// largest distance from an eigenvalue of one set to the nearest of the other (both ways)
+double eig_shift(const std::vector<double>& ar, const std::vector<double>& ai, const std::vector<double>& br,
+                 const std::vector<double>& bi) {
+  double worst = 0.0;
+  for (int pass = 0; pass < 2; ++pass) {
+    const auto& xr = pass ? br : ar;
+    const auto& xi = pass ? bi : ai;
+    const auto& yr = pass ? ar : br;
+    const auto& yi = pass ? ai : bi;
+    for (size_t i = 0; i < xr.size(); ++i) {
+      double best = INFINITY;
+      for (size_t j = 0; j < yr.size(); ++j) best = std::fmin(best, std::hypot(xr[i] - yr[j], xi[i] - yi[j]));
+      worst = std::fmax(worst, best);
+    }
+  }
+  return worst;
+}
+}  // namespace
+
+odmd_status odmd_hybrid_run(odmd_t h, odmd_residual_fn residual, odmd_fom_fn fom, void* user, double tol,
+                            int64_t t_final, int32_t check_every, int32_t conv_checks, double conv_tol,
+                            void* state_out_dev, void* prev_dev, void* r_dev, void* b_dev, odmd_run_report* report) {
+  if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
+  if (!prev_dev || prev_dev == state_out_dev || prev_dev == r_dev || prev_dev == b_dev)
+    return fail(h, ODMD_ERR_ARG, "prev must be a buffer of its own");
+  if (t_final < h->nsnap) return fail(h, ODMD_ERR_ARG, "t_final lies before the next step");
+  if (check_every < 1 || conv_checks < 1 || !(conv_tol > 0.0))
+    return fail(h, ODMD_ERR_ARG, "check_every and conv_checks must be >= 1 and conv_tol > 0");
+  odmd_run_report rep{};
+  rep.converged_at = -1;
+  std::vector<double> pre, pim, cre, cim;
+  int32_t prank = -1, streak = 0;
+  while (h->nsnap <= t_final) {
+    const int64_t t = h->nsnap;
+    int32_t acc = 0;
+    if (odmd_status s = odmd_hybrid_step_residual(h, residual, fom, user, tol, state_out_dev, r_dev, b_dev, &acc,
+                                                  nullptr))
+      return s;
+    ++rep.steps;
+    rep.accepted += acc;
+    rep.fom_calls += acc ? 0 : 1;
+    if (t == t_final) break;
+    // the callbacks of the next step see the state taken at this one
+    CK(h, cudaMemcpyAsync(prev_dev, state_out_dev, snap_bytes(h), cudaMemcpyDeviceToDevice, h->stream),
+       "copy the state taken");
+    if (t % check_every != 0 || h->nsnap < 2) continue;
+    // convergence (reading of Sec. 2.1, whose criterion is not given): conv_checks consecutive
+    // checks with the rank unchanged and no strong eigenvalue moved by more than conv_tol
+    int32_t rank = 0;
+    odmd_status s = strong_eigs(h, cre, cim, &rank);
+    if (s == ODMD_ERR_STATE) {  // no model yet
+      prank = -1;
+      streak = 0;
+      continue;
+    }
+    if (s) return s;
+    const bool same = rank == prank && cre.size() == pre.size() && eig_shift(cre, cim, pre, pim) <= conv_tol;
+    streak = same ? streak + 1 : 0;
+    pre.swap(cre);
+    pim.swap(cim);
+    prank = rank;
+    if (streak >= conv_checks) {
+      const double tf = (double)t_final;
+      if (odmd_status s2 = odmd_predict(h, &tf, 1, state_out_dev, h->cfg.n)) return s2;
+      rep.converged = 1;
+      rep.converged_at = t;
+      rep.skipped = t_final - t;
+      break;
+    }
+  }
+  if (report) *report = rep;
+  return ODMD_OK;
+}
+
 odmd_status odmd_update_batch(odmd_t* hs, const void* const* xs, int32_t count) {
   if (count < 0 || (count > 0 && (!hs || !xs))) return fail(nullptr, ODMD_ERR_ARG, "update_batch: bad arguments");
   for (int32_t i = 0; i < count; ++i) {

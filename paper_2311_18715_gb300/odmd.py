@@ -113,19 +113,8 @@ class OnlineDMD:
         """odmd_refine: restore L^T L = I now (needs refine_every > 0 at construction)."""
         self._ck(self._lib.odmd_refine(self._h))
 
-    def hybrid_step_residual(self, residual, fom, state_out: torch.Tensor, r: torch.Tensor, b: torch.Tensor,
-                             tol: float = 0.0) -> tuple[bool, float]:
-        """odmd_hybrid_step_residual: one hybrid step with the residual credibility test.
-
-        residual(step) must fill r with b - A u and b with the right-hand side of the FOM's
-        step for the predicted state held in state_out; fom(step) must write the FOM's state
-        of that step into state_out.  Both run on this model's stream (torch work inside
-        them is enqueued there).  Returns (accepted, relative residual)."""
+    def _callbacks(self, residual, fom, failure):
         from ._lib import FOM_FN, RESIDUAL_FN
-        for tns in (state_out, r, b):
-            if tns.shape != (self.n,) or tns.dtype != self.dtype or not tns.is_contiguous():
-                raise ValueError("state_out, r and b must be contiguous (n,) tensors of the snapshot dtype")
-        failure = []
 
         def _res(user, step, u, rr, bb, stream):
             try:
@@ -145,7 +134,44 @@ class OnlineDMD:
                 failure.append(e)
                 return 1
 
-        cres, cfom = RESIDUAL_FN(_res), FOM_FN(_fom)
+        return RESIDUAL_FN(_res), FOM_FN(_fom)
+
+    def _check_bufs(self, *tensors):
+        for tns in tensors:
+            if tns.shape != (self.n,) or tns.dtype != self.dtype or not tns.is_contiguous():
+                raise ValueError("state buffers must be contiguous (n,) tensors of the snapshot dtype")
+
+    def hybrid_run(self, residual, fom, state_out: torch.Tensor, prev: torch.Tensor, r: torch.Tensor,
+                   b: torch.Tensor, t_final: int, tol: float = 0.0, check_every: int = 10, conv_checks: int = 3,
+                   conv_tol: float = 1e-8) -> dict:
+        """odmd_hybrid_run: hybrid steps up to t_final with the convergence exit (callbacks as
+        in hybrid_step_residual; prev holds the state taken at the previous step, refreshed by
+        the library after every step).  Returns the run report as a dict."""
+        from ._lib import RunReport
+        self._check_bufs(state_out, prev, r, b)
+        failure = []
+        cres, cfom = self._callbacks(residual, fom, failure)
+        rep = RunReport()
+        st = self._lib.odmd_hybrid_run(self._h, cres, cfom, None, float(tol), int(t_final), int(check_every),
+                                       int(conv_checks), float(conv_tol), C.c_void_p(state_out.data_ptr()),
+                                       C.c_void_p(prev.data_ptr()), C.c_void_p(r.data_ptr()),
+                                       C.c_void_p(b.data_ptr()), C.byref(rep))
+        if failure:
+            raise failure[0]
+        self._ck(st)
+        return {f: getattr(rep, f) for f, _ in RunReport._fields_ if f != "pad"}
+
+    def hybrid_step_residual(self, residual, fom, state_out: torch.Tensor, r: torch.Tensor, b: torch.Tensor,
+                             tol: float = 0.0) -> tuple[bool, float]:
+        """odmd_hybrid_step_residual: one hybrid step with the residual credibility test.
+
+        residual(step) must fill r with b - A u and b with the right-hand side of the FOM's
+        step for the predicted state held in state_out; fom(step) must write the FOM's state
+        of that step into state_out.  Both run on this model's stream (torch work inside
+        them is enqueued there).  Returns (accepted, relative residual)."""
+        self._check_bufs(state_out, r, b)
+        failure = []
+        cres, cfom = self._callbacks(residual, fom, failure)
         acc, rel = C.c_int32(), C.c_double()
         st = self._lib.odmd_hybrid_step_residual(self._h, cres, cfom, None, float(tol),
                                                  C.c_void_p(state_out.data_ptr()), C.c_void_p(r.data_ptr()),

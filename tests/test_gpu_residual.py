@@ -145,3 +145,111 @@ def test_residual_step_callback_failures_are_reported():
         m.hybrid_step_residual(bad_residual, fom, s, r, b)
     with pytest.raises(pkg.OdmdError):
         m.hybrid_step_residual(bad_residual, fom, s, s, b)  # aliased buffers are refused
+
+
+def _strong(ref):
+    lam, V, b = ref.eig()
+    amp = np.abs(b) * np.linalg.norm(ref.L @ V, axis=0)
+    return lam[amp >= 1e-6 * amp.max()]
+
+
+def _shift(a, b):
+    if len(a) == 0 or len(b) == 0:
+        return np.inf
+    d = np.abs(a[:, None] - b[None, :])
+    return max(d.min(axis=1).max(), d.min(axis=0).max())
+
+
+def oracle_run(t_final, r_max, tol, check_every, conv_checks, conv_tol):
+    """The hybrid loop with the convergence exit, as odmd_hybrid_run states it."""
+    u0, s1, s2, den = _fields()
+    A = lambda u: u - ALPHA * (np.roll(u, 1, 0) + np.roll(u, -1, 0) + np.roll(u, 1, 1) + np.roll(u, -1, 1) - 4 * u)
+    ref = OnlineDMDRef(NX * NY, r_max, 1e-10)
+    prev = u0.copy()
+    ref.update(prev.ravel())
+    rep = dict(steps=0, fom_calls=0, accepted=0, converged=0, converged_at=-1, skipped=0)
+    pl, prank, streak = None, -1, 0
+    for t in range(1, t_final + 1):
+        b = prev + _force(s1, s2, t)
+        ok = False
+        if t >= 2 and ref.rank > 0:
+            u = ref.predict([float(t)])[:, 0].reshape(NX, NY)
+            ok = np.linalg.norm(b - A(u)) / np.linalg.norm(b) <= tol
+        if not ok:
+            u = np.fft.ifft2(np.fft.fft2(b) / den).real
+        ref.update(u.ravel())
+        prev = u
+        rep["steps"] += 1
+        rep["accepted"] += int(ok)
+        rep["fom_calls"] += int(not ok)
+        if t == t_final:
+            break
+        if t % check_every != 0:
+            continue
+        lam = _strong(ref)
+        same = ref.rank == prank and pl is not None and len(lam) == len(pl) and _shift(lam, pl) <= conv_tol
+        streak = streak + 1 if same else 0
+        pl, prank = lam, ref.rank
+        if streak >= conv_checks:
+            prev = ref.predict([float(t_final)])[:, 0].reshape(NX, NY)
+            rep.update(converged=1, converged_at=t, skipped=t_final - t)
+            break
+    return rep, prev.ravel()
+
+
+def _device_run(t_final, r_max, tol, check_every, conv_checks, conv_tol):
+    import paper_2311_18715_gb300 as pkg
+
+    u0, s1, s2, den = _fields()
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    s1d, s2d, dend = dev(s1), dev(s2), dev(den)
+    m = pkg.OnlineDMD(NX * NY, r_max, trunc_tol=1e-10, slack=8)
+    state = dev(u0.ravel()).clone()
+    m.update(state)
+    prev = state.clone()
+    r, b = torch.empty_like(state), torch.empty_like(state)
+
+    def force(k):
+        w = 2 * np.pi * k / PERIOD
+        return s1d * np.cos(w) + s2d * np.sin(w)
+
+    def A(u):
+        return u - ALPHA * (torch.roll(u, 1, 0) + torch.roll(u, -1, 0) + torch.roll(u, 1, 1) + torch.roll(u, -1, 1)
+                            - 4 * u)
+
+    def residual(k):
+        bb = prev.view(NX, NY) + force(k)
+        b.copy_(bb.view(-1))
+        r.copy_((bb - A(state.view(NX, NY))).view(-1))
+
+    def fom(k):
+        state.copy_(torch.fft.ifft2(torch.fft.fft2(prev.view(NX, NY) + force(k)) / dend).real.reshape(-1))
+
+    rep = m.hybrid_run(residual, fom, state, prev, r, b, t_final, tol, check_every, conv_checks, conv_tol)
+    return rep, state.cpu().numpy()
+
+
+def test_hybrid_run_converges_and_jumps_like_the_oracle():
+    args = (400, 12, 1e-7, 10, 3, 1e-8)
+    rep, final = _device_run(*args)
+    rep_ref, final_ref = oracle_run(*args)
+    assert rep == rep_ref, (rep, rep_ref)
+    assert rep["converged"] == 1 and rep["skipped"] >= 300   # most of the run is skipped
+    # u(t_final) is extrapolated 360 steps from the model at convergence: an eigenvalue
+    # difference at the 1e-10 parity bar becomes ~360 x 1e-10 = 3.6e-8 of the field
+    np.testing.assert_allclose(final, final_ref, rtol=0, atol=1e-7 * np.abs(final_ref).max())
+    # against the FOM itself, stepped all the way to t_final
+    u0, s1, s2, den = _fields()
+    u = u0.copy()
+    for t in range(1, args[0] + 1):
+        u = np.fft.ifft2(np.fft.fft2(u + _force(s1, s2, t)) / den).real
+    # the oracle's own jump lands within 3e-9 of the stepped FOM; the device adds the above
+    assert np.linalg.norm(final - u.ravel()) / np.linalg.norm(u) < 2e-7
+
+
+def test_hybrid_run_without_convergence_steps_to_t_final():
+    args = (60, 12, 1e-7, 10, 3, 1e-300)   # a tolerance nothing meets: no jump
+    rep, final = _device_run(*args)
+    rep_ref, final_ref = oracle_run(*args)
+    assert rep == rep_ref and rep["converged"] == 0 and rep["steps"] == 60
+    np.testing.assert_allclose(final, final_ref, rtol=0, atol=4e-7 * np.abs(final_ref).max())
