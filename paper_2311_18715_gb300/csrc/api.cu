@@ -481,6 +481,25 @@ odmd_status ensure_eig(odmd_t h) {
   return ODMD_OK;
 }
 
+// Integer horizons (the common case: states at time steps) take the coefficients from powers
+// of the reduced operator, A~^t (S * r_first), which equals V Lambda^t b exactly; any other
+// horizon takes them from the eigen-cache.
+bool integer_horizons(const double* t, int k) {
+  for (int i = 0; i < k; ++i)
+    if (!(t[i] == std::floor(t[i])) || t[i] > 1e12) return false;
+  return true;
+}
+
+odmd_status launch_coefficients(odmd_t h, const double* t, int k, bool by_powers) {
+  ProfScope ps(h, ODMD_K_COEF, 1);
+  if (by_powers) {
+    CK(h, launch_coef_pow(h->ws, t, k, h->stream), "coef launch");
+  } else {
+    CK(h, launch_coef(h->ws, t, k, h->stream), "coef launch");
+  }
+  return ODMD_OK;
+}
+
 void* base_of(odmd_t h, const Layout&) { return const_cast<CUtensorMap*>(h->ws.maps); }
 
 double join(float2 v) { return (double)v.x + (double)v.y; }
@@ -672,15 +691,14 @@ odmd_status odmd_predict(odmd_t h, const double* t_host, int32_t k, void* out_de
   if (h->nsnap < 2) return fail(h, ODMD_ERR_STATE, "predict needs two snapshots");
   for (int i = 0; i < k; ++i)
     if (!(t_host[i] >= 0.0) || !std::isfinite(t_host[i])) return fail(h, ODMD_ERR_ARG, "t must be finite and >= 0");
-  if (odmd_status s = ensure_eig(h)) return s;
+  const bool by_powers = integer_horizons(t_host, k);
+  if (!by_powers)
+    if (odmd_status s = ensure_eig(h)) return s;
   if (odmd_status s = flush_pending(h)) return s;
   const size_t vs = (size_t)vsz_of(h->cfg.prec);
   for (int j0 = 0; j0 < k; j0 += kRollK) {
     const int kk = (k - j0) < kRollK ? (k - j0) : kRollK;
-    {
-      ProfScope ps(h, ODMD_K_COEF, 1);
-      CK(h, launch_coef(h->ws, t_host + j0, kk, h->stream), "coef launch");
-    }
+    if (odmd_status s = launch_coefficients(h, t_host + j0, kk, by_powers)) return s;
     ProfScope ps(h, ODMD_K_ROLLOUT, 1);
     CK(h, launch_rollout(h->ws, nullptr, kk, static_cast<unsigned char*>(out_dev) + (size_t)j0 * ld * vs, ld, 0,
                          h->stream),
@@ -696,11 +714,10 @@ odmd_status odmd_check(odmd_t h, double t, const void* x_fom_dev, double tol, do
   if (h->nsnap < 2) return fail(h, ODMD_ERR_STATE, "check needs two snapshots");
   if (tol <= 0.0) tol = h->cfg.check_tol;
   CK(h, launch_ingest(h->ws, x_fom_dev, h->ws.xbuf, h->stream), "copy x_fom");
-  if (odmd_status s = ensure_eig(h)) return s;
-  {
-    ProfScope ps(h, ODMD_K_COEF, 1);
-    CK(h, launch_coef(h->ws, &t, 1, h->stream), "coef launch");
-  }
+  const bool by_powers = integer_horizons(&t, 1);
+  if (!by_powers)
+    if (odmd_status s = ensure_eig(h)) return s;
+  if (odmd_status s = launch_coefficients(h, &t, 1, by_powers)) return s;
   if (odmd_status s = flush_pending(h)) return s;
   {
     ProfScope ps(h, ODMD_K_CHECK, 1);
@@ -920,6 +937,8 @@ odmd_status odmd_hybrid_step(odmd_t h, const void* x_fom_dev, double tol, void* 
   return ODMD_OK;
 }
 
+static odmd_status read_hdr(odmd_t h, StateHdr* hdr);
+
 odmd_status odmd_hybrid_step_residual(odmd_t h, odmd_residual_fn residual, odmd_fom_fn fom, void* user, double tol,
                                       void* state_out_dev, void* r_dev, void* b_dev, int32_t* accepted,
                                       double* rel_res) {
@@ -932,21 +951,21 @@ odmd_status odmd_hybrid_step_residual(odmd_t h, odmd_residual_fn residual, odmd_
   const int64_t step = h->nsnap;  // the step about to be taken, counted from u^0
   int32_t acc = 0;
   double rel = INFINITY;
-  if (h->nsnap >= 2) {
+  StateHdr hdr{};
+  if (h->nsnap >= 2)
+    if (odmd_status s = read_hdr(h, &hdr)) return s;
+  if (h->nsnap >= 2 && hdr.r > 0) {  // (rank 0: no model yet, every snapshot so far was zero)
     const double t = (double)step;
-    odmd_status s = odmd_predict(h, &t, 1, state_out_dev, h->cfg.n);
-    if (s != ODMD_OK && s != ODMD_ERR_STATE) return s;
-    if (s == ODMD_OK) {  // (ODMD_ERR_STATE: no model yet, every snapshot so far was zero)
-      if (residual(user, step, state_out_dev, r_dev, b_dev, h->stream) != 0)
-        return fail(h, ODMD_ERR_STATE, "residual callback reported a failure");
-      CK(h, launch_norm_ratio(h->ws, r_dev, b_dev, h->stream), "residual norm launch");
-      CK(h, cudaMemcpyAsync(h->pinned, h->ws.out2, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
-         "read back");
-      if (odmd_status s2 = device_status(h)) return s2;
-      const double num = h->pinned[0], den = h->pinned[1];
-      rel = den > 0.0 ? std::sqrt(num / den) : (num == 0.0 ? 0.0 : INFINITY);
-      acc = rel <= tol ? 1 : 0;
-    }
+    if (odmd_status s = odmd_predict(h, &t, 1, state_out_dev, h->cfg.n)) return s;
+    if (residual(user, step, state_out_dev, r_dev, b_dev, h->stream) != 0)
+      return fail(h, ODMD_ERR_STATE, "residual callback reported a failure");
+    CK(h, launch_norm_ratio(h->ws, r_dev, b_dev, h->stream), "residual norm launch");
+    CK(h, cudaMemcpyAsync(h->pinned, h->ws.out2, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+       "read back");
+    if (odmd_status s = device_status(h)) return s;
+    const double num = h->pinned[0], den = h->pinned[1];
+    rel = den > 0.0 ? std::sqrt(num / den) : (num == 0.0 ? 0.0 : INFINITY);
+    acc = rel <= tol ? 1 : 0;
   }
   if (!acc && fom(user, step, state_out_dev, h->stream) != 0)
     return fail(h, ODMD_ERR_STATE, "FOM callback reported a failure");

@@ -458,6 +458,7 @@ cudaError_t launch_norm_ratio(const Ws& ws, const void* r, const void* b, cudaSt
 cudaError_t launch_refine(const Ws& ws, int cur, cudaStream_t s);  // Gram pass + small refinement
 cudaError_t launch_eig(const Ws& ws, cudaStream_t s);
 cudaError_t launch_coef(const Ws& ws, const double* t_host, int k, cudaStream_t s);  // k <= kRollK, t on the host
+cudaError_t launch_coef_pow(const Ws& ws, const double* t_host, int k, cudaStream_t s);  // integer t only
 cudaError_t launch_basis_coef(const Ws& ws, cudaStream_t s);
 cudaError_t launch_init(const Ws& ws, cudaStream_t s);
 

@@ -1455,6 +1455,9 @@ __global__ void __launch_bounds__(kEigThreads) k_eig(Ws ws) {
 struct TArr {
   double t[kRollK];
 };
+struct TOrd {
+  int i[kRollK];
+};
 
 __device__ cdd cpow_int(cdd base, long long e) {
   cdd res{dd_of(1.f), dzero()};
@@ -1514,6 +1517,108 @@ __global__ void __launch_bounds__(64) k_coef(Ws ws, TArr ts, int k) {
   }
 }
 
+// Rollout coefficients for integer horizons without the eigensolve: with A~ = V Lambda V^-1
+// and b = V^-1 y, y = S * r_first = L^T u^0,  V Lambda^t b = A~^t y  exactly, so
+// coef[:, j] = Q A~^{t_j} y.  The horizons are taken in ascending order (ord): the vector
+// advances by single products with A~ over short gaps and by binary powering (repeated
+// squaring of A~, applied to the vector on set bits) over long ones.  Double-float
+// throughout; one CTA.
+constexpr int kPowThreads = 256;
+constexpr int kPowDirect = 8;  // gaps up to this many steps: repeated products
+
+struct PowSmem {
+  float2 A[kMaxR * kMaxR];   // A~, row-major
+  float2 P[kMaxR * kMaxR];   // current power of A~
+  float2 T[kMaxR * kMaxR];   // scratch of a squaring
+  float2 c[kMaxR], w[kMaxR];
+};
+
+// out = B v (B row-major r x r in shared memory), 4 threads per row
+__device__ __forceinline__ void pow_matvec(const float2* B, const float2* v, float2* out, int r) {
+  const int tid = threadIdx.x;
+  for (int base = 0; base < 4 * r; base += kPowThreads) {
+    const int i = (base + tid) >> 2, sub = tid & 3;
+    dd acc = dzero();
+    if (i < r)
+      for (int l = sub; l < r; l += 4) acc = dd_fma(LD(B, (size_t)i * kMaxR + l), LD(v, l), acc);
+    acc = group4_sum(acc);
+    if (i < r && sub == 0) out[i] = f2_of(acc);
+  }
+}
+
+__global__ void __launch_bounds__(kPowThreads) k_coef_pow(Ws ws, TArr ts, TOrd ord, int k) {
+  extern __shared__ __align__(16) unsigned char pow_raw[];
+  PowSmem& S = *reinterpret_cast<PowSmem*>(pow_raw);
+  Ctl* ctl = ws.ctl;
+  const StateBuf st = ws.st[ctl->cur];
+  const int r = st.hdr->r, r0 = st.hdr->r0, rm = ws.rmax, qld = ws.cap + 1;
+  const int tid = threadIdx.x;
+  if (r == 0) {
+    if (tid == 0) atomicOr(&ctl->status, DEV_NOMODEL);
+    return;
+  }
+  for (int idx = tid; idx < r * r; idx += kPowThreads) {
+    const int i = idx / r, l = idx % r;
+    S.A[i * kMaxR + l] = f2_of(dd_div(LD(st.M, (size_t)l * rm + i), LD(st.S, l)));
+  }
+  for (int l = tid; l < r; l += kPowThreads) S.c[l] = f2_of(LD(st.S, l) * LD(st.rf, l));
+  __syncthreads();
+  long long tcur = 0;
+  for (int q = 0; q < k; ++q) {
+    const int j = ord.i[q];
+    long long d = (long long)ts.t[j] - tcur;
+    tcur += d;
+    if (d <= kPowDirect) {
+      for (; d > 0; --d) {
+        pow_matvec(S.A, S.c, S.w, r);
+        __syncthreads();
+        for (int l = tid; l < r; l += kPowThreads) S.c[l] = S.w[l];
+        __syncthreads();
+      }
+    } else {
+      for (int idx = tid; idx < r * r; idx += kPowThreads) S.P[(idx / r) * kMaxR + idx % r] = S.A[(idx / r) * kMaxR + idx % r];
+      __syncthreads();
+      while (d > 0) {
+        if (d & 1) {
+          pow_matvec(S.P, S.c, S.w, r);
+          __syncthreads();
+          for (int l = tid; l < r; l += kPowThreads) S.c[l] = S.w[l];
+          __syncthreads();
+        }
+        d >>= 1;
+        if (d) {  // P <- P P
+          for (int base = 0; base < 4 * r * r; base += kPowThreads) {
+            const int e = (base + tid) >> 2, sub = tid & 3;
+            const int i = e / r, jj = e % r;
+            dd acc = dzero();
+            if (e < r * r)
+              for (int l = sub; l < r; l += 4) acc = dd_fma(LD(S.P, (size_t)i * kMaxR + l), LD(S.P, (size_t)l * kMaxR + jj), acc);
+            acc = group4_sum(acc);
+            if (e < r * r && sub == 0) S.T[i * kMaxR + jj] = f2_of(acc);
+          }
+          __syncthreads();
+          for (int idx = tid; idx < r * r; idx += kPowThreads) S.P[(idx / r) * kMaxR + idx % r] = S.T[(idx / r) * kMaxR + idx % r];
+          __syncthreads();
+        }
+      }
+    }
+    // coef[:, j] = Q c  (4 threads per row of Q)
+    for (int base = 0; base < 4 * r0; base += kPowThreads) {
+      const int i = (base + tid) >> 2, sub = tid & 3;
+      dd acc = dzero();
+      if (i < r0)
+        for (int l = sub; l < r; l += 4) acc = dd_fma(LD(st.Q, (size_t)l * qld + i), LD(S.c, l), acc);
+      acc = group4_sum(acc);
+      if (i < r0 && sub == 0) ws.sm.coef[(size_t)j * qld + i] = f2_of(acc);
+    }
+  }
+  if (tid == 0) {
+    bool bad = false;
+    for (int l = 0; l < r; ++l) bad |= !dd_isfinite(LD(S.c, l));
+    if (bad) atomicOr(&ctl->status, DEV_NONFINITE);
+  }
+}
+
 // basis export coefficients: coef[:, j] = Q[:, j]
 __global__ void __launch_bounds__(64) k_basis_coef(Ws ws) {
   Ctl* ctl = ws.ctl;
@@ -1536,7 +1641,9 @@ static int prep_smem(const Ws& ws) { return prep_smem_cap(ws.cap); }
 cudaError_t prepare_small(const Ws&) {
   cudaError_t e = cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, prep_smem_cap(kMaxCap));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(EigSmem));
+  e = cudaFuncSetAttribute(k_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(EigSmem));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_coef_pow, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PowSmem));
 }
 
 cudaError_t launch_small(const Ws& ws, cudaStream_t s) {
@@ -1559,6 +1666,28 @@ cudaError_t launch_coef(const Ws& ws, const double* t_host, int k, cudaStream_t 
   TArr ta;
   for (int i = 0; i < kRollK; ++i) ta.t[i] = i < k ? t_host[i] : 0.0;
   k_coef<<<k, 64, 0, s>>>(ws, ta, k);
+  return cudaGetLastError();
+}
+
+// integer horizons only (the caller checks): coefficients by powers of A~, no eigensolve
+cudaError_t launch_coef_pow(const Ws& ws, const double* t_host, int k, cudaStream_t s) {
+  TArr ta;
+  TOrd ord;
+  for (int i = 0; i < kRollK; ++i) {
+    ta.t[i] = i < k ? t_host[i] : 0.0;
+    ord.i[i] = i;
+  }
+  // ascending order of the horizons (insertion sort of at most kRollK indices, stable)
+  for (int a = 1; a < k; ++a) {
+    const int v = ord.i[a];
+    int b = a - 1;
+    while (b >= 0 && ta.t[ord.i[b]] > ta.t[v]) {
+      ord.i[b + 1] = ord.i[b];
+      --b;
+    }
+    ord.i[b + 1] = v;
+  }
+  k_coef_pow<<<1, kPowThreads, sizeof(PowSmem), s>>>(ws, ta, ord, k);
   return cudaGetLastError();
 }
 
