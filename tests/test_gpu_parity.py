@@ -249,3 +249,26 @@ def test_clustered_tiny_singular_values():
     got = m.predict([125.0]).cpu().numpy()
     want = ref.predict([125.0]).T
     assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-9
+
+
+@pytest.mark.parametrize("stream", ["planted", "wake"])
+def test_powers_and_eigen_paths_agree(stream):
+    """Integer horizons take their coefficients from powers of the reduced operator, any
+    other horizon from the eigen-cache (V Lambda^t b); both are the same quantity (reading
+    A21).  A call with only integer horizons takes the first path, the same horizons with
+    a fractional one added take the second: both must match each other and the oracle."""
+    if stream == "planted":
+        X = PlantedModes(4096, sigma=1e-8, seed=0).snapshots(0, 200)
+        r_max, ts = 10, [0.0, 1.0, 150.0, 199.0, 200.0, 260.0]
+    else:
+        X = WakeField(nx=64, ny=32, sigma=1e-6, seed=0).snapshots(0, 300)
+        r_max, ts = 16, [0.0, 299.0, 300.0, 301.0, 320.0]
+    m, ref = run_pair(X, r_max, slack=4)
+    by_powers = m.predict(ts).cpu().numpy()
+    by_eigen = m.predict(ts + [0.5]).cpu().numpy()[: len(ts)]
+    want = ref.predict(ts).T
+    for got in (by_powers, by_eigen):
+        for j in range(len(ts)):
+            assert np.linalg.norm(got[j] - want[j]) / np.linalg.norm(want[j]) < 1e-9, (stream, ts[j])
+    scale = np.linalg.norm(want, axis=1)
+    assert np.max(np.linalg.norm(by_powers - by_eigen, axis=1) / scale) < 1e-10
