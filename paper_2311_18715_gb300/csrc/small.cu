@@ -1530,7 +1530,8 @@ struct PowSmem {
   float2 A[kMaxR * kMaxR];   // A~, row-major
   float2 P[kMaxR * kMaxR];   // current power of A~
   float2 T[kMaxR * kMaxR];   // scratch of a squaring
-  float2 c[kMaxR], w[kMaxR];
+  float2 v[2][kMaxR];        // the vector, ping-pong
+  float2 C[kRollK * kMaxR];  // A~^{t_j} y for every horizon j (row j)
 };
 
 // out = B v (B row-major r x r in shared memory), 4 threads per row
@@ -1561,8 +1562,9 @@ __global__ void __launch_bounds__(kPowThreads) k_coef_pow(Ws ws, TArr ts, TOrd o
     const int i = idx / r, l = idx % r;
     S.A[i * kMaxR + l] = f2_of(dd_div(LD(st.M, (size_t)l * rm + i), LD(st.S, l)));
   }
-  for (int l = tid; l < r; l += kPowThreads) S.c[l] = f2_of(LD(st.S, l) * LD(st.rf, l));
+  for (int l = tid; l < r; l += kPowThreads) S.v[0][l] = f2_of(LD(st.S, l) * LD(st.rf, l));
   __syncthreads();
+  int cur = 0;  // S.v[cur] holds the vector
   long long tcur = 0;
   for (int q = 0; q < k; ++q) {
     const int j = ord.i[q];
@@ -1570,9 +1572,8 @@ __global__ void __launch_bounds__(kPowThreads) k_coef_pow(Ws ws, TArr ts, TOrd o
     tcur += d;
     if (d <= kPowDirect) {
       for (; d > 0; --d) {
-        pow_matvec(S.A, S.c, S.w, r);
-        __syncthreads();
-        for (int l = tid; l < r; l += kPowThreads) S.c[l] = S.w[l];
+        pow_matvec(S.A, S.v[cur], S.v[cur ^ 1], r);
+        cur ^= 1;
         __syncthreads();
       }
     } else {
@@ -1580,9 +1581,8 @@ __global__ void __launch_bounds__(kPowThreads) k_coef_pow(Ws ws, TArr ts, TOrd o
       __syncthreads();
       while (d > 0) {
         if (d & 1) {
-          pow_matvec(S.P, S.c, S.w, r);
-          __syncthreads();
-          for (int l = tid; l < r; l += kPowThreads) S.c[l] = S.w[l];
+          pow_matvec(S.P, S.v[cur], S.v[cur ^ 1], r);
+          cur ^= 1;
           __syncthreads();
         }
         d >>= 1;
@@ -1602,19 +1602,23 @@ __global__ void __launch_bounds__(kPowThreads) k_coef_pow(Ws ws, TArr ts, TOrd o
         }
       }
     }
-    // coef[:, j] = Q c  (4 threads per row of Q)
-    for (int base = 0; base < 4 * r0; base += kPowThreads) {
-      const int i = (base + tid) >> 2, sub = tid & 3;
-      dd acc = dzero();
-      if (i < r0)
-        for (int l = sub; l < r; l += 4) acc = dd_fma(LD(st.Q, (size_t)l * qld + i), LD(S.c, l), acc);
-      acc = group4_sum(acc);
-      if (i < r0 && sub == 0) ws.sm.coef[(size_t)j * qld + i] = f2_of(acc);
-    }
+    for (int l = tid; l < r; l += kPowThreads) S.C[j * kMaxR + l] = S.v[cur][l];
+    // (read only after the barrier that ends the next step, or the final one)
+  }
+  __syncthreads();
+  // coef[:, j] = Q C[j] for every horizon at once (4 threads per output)
+  for (int base = 0; base < 4 * r0 * k; base += kPowThreads) {
+    const int e = (base + tid) >> 2, sub = tid & 3;
+    const int i = e % r0, j = e / r0;
+    dd acc = dzero();
+    if (e < r0 * k)
+      for (int l = sub; l < r; l += 4) acc = dd_fma(LD(st.Q, (size_t)l * qld + i), LD(S.C, (size_t)j * kMaxR + l), acc);
+    acc = group4_sum(acc);
+    if (e < r0 * k && sub == 0) ws.sm.coef[(size_t)j * qld + i] = f2_of(acc);
   }
   if (tid == 0) {
     bool bad = false;
-    for (int l = 0; l < r; ++l) bad |= !dd_isfinite(LD(S.c, l));
+    for (int l = 0; l < r; ++l) bad |= !dd_isfinite(LD(S.v[cur], l));
     if (bad) atomicOr(&ctl->status, DEV_NONFINITE);
   }
 }
