@@ -342,19 +342,29 @@ def run_ours(args) -> None:
 
     # ---- end to end through the public API with host buffers
     x_stage = torch.empty(N, dtype=torch.float64, device=dev)
-    out_h = torch.empty((BLOCK, N), dtype=torch.float64).pin_memory()
+    # the predicted states go back to pinned host memory on a side stream, so the read-back
+    # of one block overlaps the updates of the next (two device and two host buffers)
+    outs = [out, torch.empty_like(out)]
+    outs_h = [torch.empty((BLOCK, N), dtype=torch.float64).pin_memory() for _ in range(2)]
+    d2h = torch.cuda.Stream(dev)
+    done = [torch.cuda.Event(), torch.cuda.Event()]
     torch.cuda.synchronize()
     barrier(dist)
     t0 = time.perf_counter()
     ke = 0
-    for _ in range(K):
+    for blk in range(K):
+        b = blk & 1
         with torch.cuda.stream(stream):
-            for i in range(BLOCK):
-                x_stage.copy_(Xh[ke], non_blocking=True)
-                model.update(x_stage)
-                ke += 1
-            model.predict([float(k + h) for h in range(BLOCK)], out=out)
-            out_h.copy_(out, non_blocking=True)
+            # the block's snapshots straight from pinned host memory through the C ABI
+            # (odmd_update_host: copies on the handle's copy stream overlap the updates)
+            model.update_host(Xh[ke:ke + BLOCK])
+            ke += BLOCK
+            stream.wait_event(done[b])  # the read-back of this buffer two blocks ago is over
+            model.predict([float(k + h) for h in range(BLOCK)], out=outs[b])
+            d2h.wait_stream(stream)
+            with torch.cuda.stream(d2h):
+                outs_h[b].copy_(outs[b], non_blocking=True)
+                done[b].record(d2h)
             x_stage.copy_(Xh[ke], non_blocking=True)
             model.check(float(k + BLOCK), x_stage)
         k += BLOCK

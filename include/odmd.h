@@ -127,6 +127,17 @@ odmd_status odmd_check(odmd_t h, double t, const void* x_fom_dev, double tol,
 odmd_status odmd_hybrid_step(odmd_t h, const void* x_fom_dev, double tol, void* state_out_dev,
                              int32_t* accepted, double* rel_err);
 
+/* Append `count` snapshots read from host memory: snapshot k (n elements of the snapshot
+ * type, double for ODMD_FP64 and float for ODMD_FP32) starts at element k*ld of host
+ * (ld >= n).  Each is copied into one of two staging slots of the workspace on a copy
+ * stream of the handle's own, and odmd_update runs on it once its copy has arrived; a slot
+ * is refilled only after the update that read it, so with pinned host memory the copy of
+ * snapshot k+1 overlaps the update of snapshot k.  Returns once the work is enqueued
+ * (pageable host memory is copied before the call returns); a pinned buffer must stay
+ * valid until the handle's stream has finished it (odmd_sync).  Errors: ODMD_ERR_ARG,
+ * ODMD_ERR_CUDA, and those of odmd_update. */
+odmd_status odmd_update_host(odmd_t h, const void* host, int64_t count, int64_t ld);
+
 /* Many instances in one call (independent simulations, Sec. 2.1 per instance):
  * odmd_update_batch is odmd_update(hs[i], xs[i]) for i < count, and odmd_predict_batch is
  * odmd_predict(hs[i], ts[i], ks[i], outs[i], lds[i]); each instance's work is enqueued on

@@ -17,7 +17,7 @@ EXPORTED = [
     "odmd_get_basis", "odmd_get_counts", "odmd_destroy", "odmd_last_error",
     "odmd_profile_enable", "odmd_profile_read", "odmd_check_noalloc", "odmd_hybrid_step",
     "odmd_update_batch", "odmd_predict_batch", "odmd_refine", "odmd_checkpoint_size", "odmd_save",
-    "odmd_load", "odmd_hybrid_step_residual", "odmd_hybrid_run",
+    "odmd_load", "odmd_hybrid_step_residual", "odmd_hybrid_run", "odmd_update_host",
 ]
 # host callbacks of odmd_hybrid_step_residual: (user, step, u, r, b, stream) and (user, step, u, stream)
 RESIDUAL_FN = C.CFUNCTYPE(C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p)
@@ -77,6 +77,7 @@ def load_library(path: str | None = None) -> C.CDLL:
         "odmd_checkpoint_size": [vp, C.POINTER(C.c_size_t)],
         "odmd_save": [vp, vp, C.c_size_t],
         "odmd_load": [vp, vp, C.c_size_t],
+        "odmd_update_host": [vp, vp, C.c_int64, C.c_int64],
         "odmd_hybrid_step_residual": [vp, RESIDUAL_FN, FOM_FN, vp, C.c_double, vp, vp, vp, C.POINTER(i32),
                                       C.POINTER(C.c_double)],
         "odmd_hybrid_run": [vp, RESIDUAL_FN, FOM_FN, vp, C.c_double, C.c_int64, i32, i32, C.c_double, vp, vp, vp,

@@ -56,6 +56,13 @@ struct odmd_instance {
   UpdGraph ug[2][2];
   cudaStream_t cap = nullptr;
   bool use_graphs = true;
+  // odmd_update_host: two staging slots in the workspace, filled on a copy stream of their
+  // own; a slot is refilled only after the update that read it
+  unsigned char* stage[2] = {nullptr, nullptr};
+  cudaStream_t copy = nullptr;
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
+  bool stage_used[2] = {false, false};
+  int stage_next = 0;
 };
 
 namespace {
@@ -67,6 +74,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 struct Layout {
   size_t total;
   size_t off_gpart = 0, off_rscr = 0;  // refinement scratch (refine_every > 0 only)
+  size_t off_stage[2] = {0, 0};  // staging of snapshots read from host memory
   size_t off_ctl, off_hdr[2], off_state[2], off_small, off_eig, off_out2, off_part, off_Lh, off_Ll, off_c[2],
       off_x, off_e, off_maps;
   size_t state_doubles, small_bytes, eig_doubles;
@@ -165,6 +173,8 @@ Layout make_layout(const odmd_config& c) {
   L.off_c[1] = take(snap);
   L.off_x = take(snap);
   L.off_e = take((size_t)L.npad * sizeof(float2));
+  L.off_stage[0] = take(snap);
+  L.off_stage[1] = take(snap);
   L.total = o;
   return L;
 }
@@ -572,6 +582,8 @@ odmd_status odmd_create(const odmd_config* cfg, void* workspace_dev, size_t byte
   if (gridA > kPartRows) gridA = kPartRows;
   if (gridA < 1) gridA = 1;
   carve(h->ws, L, reinterpret_cast<unsigned char*>(workspace_dev), *cfg, gridA);
+  h->stage[0] = reinterpret_cast<unsigned char*>(workspace_dev) + L.off_stage[0];
+  h->stage[1] = reinterpret_cast<unsigned char*>(workspace_dev) + L.off_stage[1];
   {
     const int64_t tiles32 = (cfg->n + 31) / 32;
     int g = (int)(tiles32 < sms ? tiles32 : sms);
@@ -1068,6 +1080,34 @@ odmd_status odmd_hybrid_run(odmd_t h, odmd_residual_fn residual, odmd_fom_fn fom
   return ODMD_OK;
 }
 
+odmd_status odmd_update_host(odmd_t h, const void* host, int64_t count, int64_t ld) {
+  if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
+  if (count < 0 || (count > 0 && !host)) return fail(h, ODMD_ERR_ARG, "bad host buffer or count");
+  if (ld < h->cfg.n) return fail(h, ODMD_ERR_ARG, "ld < n");
+  if (!h->copy) {
+    CK(h, cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking), "copy stream");
+    for (int b = 0; b < 2; ++b) {
+      CK(h, cudaEventCreateWithFlags(&h->ev_copied[b], cudaEventDisableTiming), "staging events");
+      CK(h, cudaEventCreateWithFlags(&h->ev_used[b], cudaEventDisableTiming), "staging events");
+    }
+  }
+  const size_t esz = (size_t)vsz_of(h->cfg.prec), bytes = (size_t)h->cfg.n * esz;
+  const unsigned char* src = static_cast<const unsigned char*>(host);
+  for (int64_t k = 0; k < count; ++k) {
+    const int b = h->stage_next;
+    if (h->stage_used[b]) CK(h, cudaStreamWaitEvent(h->copy, h->ev_used[b], 0), "wait for the slot");
+    CK(h, cudaMemcpyAsync(h->stage[b], src + (size_t)k * (size_t)ld * esz, bytes, cudaMemcpyHostToDevice, h->copy),
+       "host copy");
+    CK(h, cudaEventRecord(h->ev_copied[b], h->copy), "record copy");
+    CK(h, cudaStreamWaitEvent(h->stream, h->ev_copied[b], 0), "wait for the copy");
+    if (odmd_status s = odmd_update(h, h->stage[b])) return s;
+    CK(h, cudaEventRecord(h->ev_used[b], h->stream), "record use");
+    h->stage_used[b] = true;
+    h->stage_next ^= 1;
+  }
+  return ODMD_OK;
+}
+
 odmd_status odmd_update_batch(odmd_t* hs, const void* const* xs, int32_t count) {
   if (count < 0 || (count > 0 && (!hs || !xs))) return fail(nullptr, ODMD_ERR_ARG, "update_batch: bad arguments");
   for (int32_t i = 0; i < count; ++i) {
@@ -1235,6 +1275,11 @@ odmd_status odmd_destroy(odmd_t h) {
         if (ev) cudaEventDestroy(ev);
     }
   if (h->cap) cudaStreamDestroy(h->cap);
+  for (int b = 0; b < 2; ++b) {
+    if (h->ev_copied[b]) cudaEventDestroy(h->ev_copied[b]);
+    if (h->ev_used[b]) cudaEventDestroy(h->ev_used[b]);
+  }
+  if (h->copy) cudaStreamDestroy(h->copy);
   cudaFreeHost(h->pinned);
   delete h;
   if (e != cudaSuccess) return fail(nullptr, ODMD_ERR_CUDA, std::string("destroy: ") + cudaGetErrorString(e));

@@ -181,6 +181,16 @@ class OnlineDMD:
         self._ck(st)
         return bool(acc.value), float(rel.value)
 
+    def update_host(self, X: torch.Tensor) -> None:
+        """odmd_update_host: append the rows of a host (CPU) tensor X (count x n, the snapshot
+        dtype) as snapshots; the copies overlap the updates when X is in pinned memory, which
+        must then stay alive until sync()."""
+        if X.device.type != "cpu" or X.dtype != self.dtype or X.dim() != 2 or X.shape[1] != self.n:
+            raise ValueError("X must be a CPU (count, n) tensor of the snapshot dtype")
+        if X.stride(1) != 1:
+            raise ValueError("X rows must be contiguous")
+        self._ck(self._lib.odmd_update_host(self._h, C.c_void_p(X.data_ptr()), X.shape[0], X.stride(0)))
+
     def save(self) -> bytes:
         """odmd_save: the model's whole state as a host checkpoint (synchronises)."""
         nb = C.c_size_t()

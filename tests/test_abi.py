@@ -45,9 +45,10 @@ def test_footprint_and_argument_checks_on_host():
     assert lib.odmd_config_default(C.byref(cfg), 393216, 40) == 0
     nb = C.c_size_t()
     assert lib.odmd_footprint(C.byref(cfg), C.byref(nb)) == 0
-    # two float planes of N x ceil8(r_max+slack) plus three snapshot buffers dominate
+    # two float planes of N x ceil8(r_max+slack) dominate; then six n-element buffers of 8
+    # bytes (two snapshot slots, the check input, the stored residual, two host-staging slots)
     plane = 393216 * 60 * 4  # row stride: 56 columns rounded up to an odd number of 16-byte chunks
-    assert 2 * plane < nb.value < 2 * plane + 3 * 393216 * 8 + (8 << 20)
+    assert 2 * plane < nb.value < 2 * plane + 6 * 393216 * 8 + (8 << 20)
     bad = OdmdConfig()
     lib.odmd_config_default(C.byref(bad), 100, 65)
     assert lib.odmd_footprint(C.byref(bad), C.byref(nb)) == 1  # ODMD_ERR_ARG
