@@ -210,7 +210,7 @@ odmd_status odmd_profile_enable(odmd_t h, int32_t enable);
 odmd_status odmd_profile_read(odmd_t h, double* ms_total, int64_t* launches, int32_t cap, double* mean_r0);
 
 /* One step of the hybrid FOM/ROM loop with the paper's own credibility test (Sec. 2.2:
- * the residual of the FOM's discrete system at the predicted state; the survey's NEXT-4).
+ * the residual of the FOM's discrete system at the predicted state).
  *
  * The step taken is t = number of snapshots received so far.  With a model, the library
  * predicts u(t) into state_out_dev and calls residual(user, t, state_out_dev, r_dev, b_dev,
@@ -237,7 +237,7 @@ odmd_status odmd_hybrid_step_residual(odmd_t h, odmd_residual_fn residual, odmd_
                                       void* state_out_dev, void* r_dev, void* b_dev, int32_t* accepted,
                                       double* rel_res);
 
-/* The hybrid loop up to t_final with the convergence exit of Sec. 2.1 (the survey's NEXT-1):
+/* The hybrid loop up to t_final with the convergence exit of Sec. 2.1:
  * steps t = (snapshots so far) .. t_final are taken with odmd_hybrid_step_residual (same
  * callbacks, buffers and tol).  Every check_every-th step, once a model exists, the DMD
  * eigenvalues of the modes that carry the field (amplitude >= 1e-6 of the largest) are
@@ -265,7 +265,7 @@ odmd_status odmd_hybrid_run(odmd_t h, odmd_residual_fn residual, odmd_fom_fn fom
                             int64_t t_final, int32_t check_every, int32_t conv_checks, double conv_tol,
                             void* state_out_dev, void* prev_dev, void* r_dev, void* b_dev, odmd_run_report* report);
 
-/* Checkpoint / resume (the survey's NEXT-3; the paper has no counterpart).
+/* Checkpoint / resume (the paper has no counterpart).
  *
  * odmd_checkpoint_size: bytes of a checkpoint of this handle (host memory).
  * odmd_save: synchronises, then writes the model's whole state into host_buf (bytes >=

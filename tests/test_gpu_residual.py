@@ -1,5 +1,5 @@
 """The hybrid step with the residual credibility test (odmd_hybrid_step_residual; Sec. 2.2
-of the paper, the survey's NEXT-4) against the same controller written with the oracle.
+of the paper) against the same controller written with the oracle.
 
 The FOM stand-in is a linear implicit step, so that A u = b exists: forced diffusion on a
 periodic grid, (I - alpha Lap) u_{k+1} = u_k + f_{k+1}, with f periodic in time, solved

@@ -1,4 +1,4 @@
-"""Spectrum and probe checks on the device model (the survey's NEXT-3 spectrum check).
+"""Spectrum and probe checks on the device model.
 
 The synthetic cylinder wake sheds at Strouhal number St = 0.22 (Sec. 3 of the paper):
 its shedding harmonics have per-step eigenvalues exp(+-i 2 pi St h dt), h = 1, 2, 3.
