@@ -1525,11 +1525,14 @@ __global__ void __launch_bounds__(64) k_coef(Ws ws, TArr ts, int k) {
 // throughout; one CTA.
 constexpr int kPowThreads = 256;
 constexpr int kPowDirect = 8;  // gaps up to this many steps: repeated products
+// row stride of the r x r matrices: one element more than kMaxR, so that the rows a warp
+// reads at the same column fall in different shared-memory banks
+constexpr int kPowLd = kMaxR + 1;
 
 struct PowSmem {
-  float2 A[kMaxR * kMaxR];   // A~, row-major
-  float2 P[kMaxR * kMaxR];   // current power of A~
-  float2 T[kMaxR * kMaxR];   // scratch of a squaring
+  float2 A[kMaxR * kPowLd];  // A~, row-major
+  float2 P[kMaxR * kPowLd];  // current power of A~
+  float2 T[kMaxR * kPowLd];  // scratch of a squaring
   float2 v[2][kMaxR];        // the vector, ping-pong
   float2 C[kRollK * kMaxR];  // A~^{t_j} y for every horizon j (row j)
 };
@@ -1541,7 +1544,7 @@ __device__ __forceinline__ void pow_matvec(const float2* B, const float2* v, flo
     const int i = (base + tid) >> 2, sub = tid & 3;
     dd acc = dzero();
     if (i < r)
-      for (int l = sub; l < r; l += 4) acc = dd_fma(LD(B, (size_t)i * kMaxR + l), LD(v, l), acc);
+      for (int l = sub; l < r; l += 4) acc = dd_fma(LD(B, (size_t)i * kPowLd + l), LD(v, l), acc);
     acc = group4_sum(acc);
     if (i < r && sub == 0) out[i] = f2_of(acc);
   }
@@ -1560,7 +1563,7 @@ __global__ void __launch_bounds__(kPowThreads) k_coef_pow(Ws ws, TArr ts, TOrd o
   }
   for (int idx = tid; idx < r * r; idx += kPowThreads) {
     const int i = idx / r, l = idx % r;
-    S.A[i * kMaxR + l] = f2_of(dd_div(LD(st.M, (size_t)l * rm + i), LD(st.S, l)));
+    S.A[i * kPowLd + l] = f2_of(dd_div(LD(st.M, (size_t)l * rm + i), LD(st.S, l)));
   }
   for (int l = tid; l < r; l += kPowThreads) S.v[0][l] = f2_of(LD(st.S, l) * LD(st.rf, l));
   __syncthreads();
@@ -1577,7 +1580,7 @@ __global__ void __launch_bounds__(kPowThreads) k_coef_pow(Ws ws, TArr ts, TOrd o
         __syncthreads();
       }
     } else {
-      for (int idx = tid; idx < r * r; idx += kPowThreads) S.P[(idx / r) * kMaxR + idx % r] = S.A[(idx / r) * kMaxR + idx % r];
+      for (int idx = tid; idx < r * r; idx += kPowThreads) S.P[(idx / r) * kPowLd + idx % r] = S.A[(idx / r) * kPowLd + idx % r];
       __syncthreads();
       while (d > 0) {
         if (d & 1) {
@@ -1592,12 +1595,12 @@ __global__ void __launch_bounds__(kPowThreads) k_coef_pow(Ws ws, TArr ts, TOrd o
             const int i = e / r, jj = e % r;
             dd acc = dzero();
             if (e < r * r)
-              for (int l = sub; l < r; l += 4) acc = dd_fma(LD(S.P, (size_t)i * kMaxR + l), LD(S.P, (size_t)l * kMaxR + jj), acc);
+              for (int l = sub; l < r; l += 4) acc = dd_fma(LD(S.P, (size_t)i * kPowLd + l), LD(S.P, (size_t)l * kPowLd + jj), acc);
             acc = group4_sum(acc);
-            if (e < r * r && sub == 0) S.T[i * kMaxR + jj] = f2_of(acc);
+            if (e < r * r && sub == 0) S.T[i * kPowLd + jj] = f2_of(acc);
           }
           __syncthreads();
-          for (int idx = tid; idx < r * r; idx += kPowThreads) S.P[(idx / r) * kMaxR + idx % r] = S.T[(idx / r) * kMaxR + idx % r];
+          for (int idx = tid; idx < r * r; idx += kPowThreads) S.P[(idx / r) * kPowLd + idx % r] = S.T[(idx / r) * kPowLd + idx % r];
           __syncthreads();
         }
       }
