@@ -1523,7 +1523,7 @@ __global__ void __launch_bounds__(64) k_coef(Ws ws, TArr ts, int k) {
 // advances by single products with A~ over short gaps and by binary powering (repeated
 // squaring of A~, applied to the vector on set bits) over long ones.  Double-float
 // throughout; one CTA.
-constexpr int kPowThreads = 256;
+constexpr int kPowThreads = 1024;  // eight warps per scheduler hide the latency of the dependent double-float sums
 constexpr int kPowDirect = 8;  // gaps up to this many steps: repeated products
 // row stride of the r x r matrices: one element more than kMaxR, so that the rows a warp
 // reads at the same column fall in different shared-memory banks
