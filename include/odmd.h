@@ -253,9 +253,10 @@ odmd_status odmd_hybrid_step_residual(odmd_t h, odmd_residual_fn residual, odmd_
  * holds the prediction of step t while they run).
  *
  * report (host, may be NULL): steps taken, FOM calls, accepted predictions, whether the
- * model converged, the step at which it did (-1 if not) and the steps skipped.  Errors:
- * those of odmd_hybrid_step_residual; ODMD_ERR_ARG for t_final before the next step,
- * check_every or conv_checks < 1, conv_tol <= 0. */
+ * model converged, the step at which it did (-1 if not) and the steps skipped.  A check
+ * whose eigensolve fails (no convergence, ill-conditioned eigenbasis) counts as not
+ * converged.  Errors: those of odmd_hybrid_step_residual; ODMD_ERR_ARG for t_final before
+ * the next step, check_every or conv_checks < 1, conv_tol <= 0. */
 typedef struct {
   int64_t steps, fom_calls, accepted;
   int32_t converged, pad;

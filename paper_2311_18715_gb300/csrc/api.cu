@@ -1056,7 +1056,9 @@ odmd_status odmd_hybrid_run(odmd_t h, odmd_residual_fn residual, odmd_fom_fn fom
     // checks with the rank unchanged and no strong eigenvalue moved by more than conv_tol
     int32_t rank = 0;
     odmd_status s = strong_eigs(h, cre, cim, &rank);
-    if (s == ODMD_ERR_STATE) {  // no model yet
+    if (s == ODMD_ERR_STATE || s == ODMD_ERR_NUMERIC) {
+      // no model yet, or an eigensolve that did not converge or met an ill-conditioned
+      // eigenbasis: not converged at this check; the run goes on
       prank = -1;
       streak = 0;
       continue;
