@@ -231,3 +231,19 @@ def test_check_special_cases():
     assert abs(err - 2.0) < 1e-14 and not ok
     err, ok = o.check(31.0, g.clean(31.0), 1e-5)
     assert err < 1e-10 and ok
+
+
+def test_integer_horizons_equal_powers_of_the_reduced_operator():
+    """Reading A21: for integer t, Phi Lambda^t Phi^+ u0 = L A~^t (S * r_first), the
+    identity V Lambda^t V^-1 = A~^t with b = V^-1 (S * r_first).  The oracle's eigen-based
+    rollout must equal the plain matrix power, on a stream whose operator has a complex
+    pair, a decaying mode and a neutral one."""
+    g = PlantedModes(600, mus=(1.0, 0.97, 0.9), thetas=(0.013, 0.071, 0.2), sigma=0.0, seed=5)
+    X = g.snapshots(0, 40)
+    o = run_online(X.T, r_max=12, tau=1e-12)
+    A = o.reduced_operator()
+    y = o.S * o.r_first
+    for t in (0, 1, 7, 39, 40, 111):
+        direct = o.L @ (np.linalg.matrix_power(A, t) @ y)
+        via_eig = o.predict([float(t)])[:, 0]
+        assert np.linalg.norm(direct - via_eig) <= 1e-9 * np.linalg.norm(via_eig), t
