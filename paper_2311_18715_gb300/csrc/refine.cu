@@ -572,6 +572,7 @@ __global__ void __launch_bounds__(128) k_refine_out(Ws ws, int cur) {
       // switch can be made before the other CTAs finish
       ws.ctl->cur = cur ^ 1;
       ws.ctl->eig_valid = 0;
+      ws.ctl->model_ver += 1ull;
       if (flag == 1) atomicOr(&ws.ctl->status, DEV_NONFINITE);
     }
   }

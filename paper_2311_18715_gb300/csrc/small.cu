@@ -770,6 +770,7 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(Ws ws) {
     ctl->cur = cur ^ 1;
     ctl->cur_c = ctl->cur_c ^ 1;
     ctl->eig_valid = 0;
+    ctl->model_ver += 1ull;
     ctl->ticket_b = 0u;
   }
 }
@@ -1565,10 +1566,15 @@ __global__ void __launch_bounds__(kPowThreads) k_coef_pow(Ws ws, TArr ts, TOrd o
     const int i = idx / r, l = idx % r;
     S.A[i * kPowLd + l] = f2_of(dd_div(LD(st.M, (size_t)l * rm + i), LD(st.S, l)));
   }
-  for (int l = tid; l < r; l += kPowThreads) S.v[0][l] = f2_of(LD(st.S, l) * LD(st.rf, l));
+  // start from the vector of the previous call when it belongs to this model and to a
+  // horizon not after the first one asked for (a check right after a predict)
+  const unsigned long long ver = ctl->model_ver;
+  const bool reuse = k > 0 && ctl->pc_ver == ver + 1ull && ctl->pc_t <= ts.t[ord.i[0]];
+  long long tcur = reuse ? (long long)ctl->pc_t : 0;
+  for (int l = tid; l < r; l += kPowThreads)
+    S.v[0][l] = reuse ? ws.sm.pc[l] : f2_of(LD(st.S, l) * LD(st.rf, l));
   __syncthreads();
   int cur = 0;  // S.v[cur] holds the vector
-  long long tcur = 0;
   for (int q = 0; q < k; ++q) {
     const int j = ord.i[q];
     long long d = (long long)ts.t[j] - tcur;
@@ -1618,6 +1624,13 @@ __global__ void __launch_bounds__(kPowThreads) k_coef_pow(Ws ws, TArr ts, TOrd o
       for (int l = sub; l < r; l += 4) acc = dd_fma(LD(st.Q, (size_t)l * qld + i), LD(S.C, (size_t)j * kMaxR + l), acc);
     acc = group4_sum(acc);
     if (e < r0 * k && sub == 0) ws.sm.coef[(size_t)j * qld + i] = f2_of(acc);
+  }
+  if (k > 0) {
+    for (int l = tid; l < r; l += kPowThreads) ws.sm.pc[l] = S.v[cur][l];
+    if (tid == 0) {
+      ctl->pc_t = (double)tcur;
+      ctl->pc_ver = ver + 1ull;
+    }
   }
   if (tid == 0) {
     bool bad = false;
