@@ -153,7 +153,7 @@ Layout make_layout(const odmd_config& c) {
   L.off_state[1] = take(L.state_doubles * sizeof(float2));
   // small scratch: double-floats then ints
   const size_t nd = (2 * (size_t)L.cap + 3) + 3 * (size_t)qld + 10 * (size_t)kMaxN + 2 * (size_t)kMaxN +
-                    2 * (size_t)kMaxN * kMaxN + (size_t)qld * L.rmax + (size_t)qld * kRollK + (size_t)kMaxN;
+                    2 * (size_t)kMaxN * kMaxN + (size_t)qld * L.rmax + (size_t)qld * kRollK + 2 * (size_t)kMaxN;
   const size_t ni = 6 * (size_t)kMaxN;
   L.small_bytes = nd * sizeof(float2) + ni * 4;
   L.off_small = take(L.small_bytes);
@@ -251,7 +251,7 @@ void carve(Ws& ws, const Layout& L, unsigned char* base, const odmd_config& c, i
   sm.coef = d;
   d += (size_t)qld * kRollK;
   sm.pc = d;
-  d += kMaxN;
+  d += 2 * kMaxN;
   int* ip = reinterpret_cast<int*>(d);
   sm.pole = ip;
   ip += kMaxN;

@@ -94,8 +94,8 @@ struct Ctl {
   unsigned long long prof_r0_sum;  // sum of r0 over pass-A launches (for roofline accounting)
   unsigned long long prof_a;       // number of pass-A launches
   unsigned long long model_ver;    // advanced by every commit of a new model (update, refinement)
-  unsigned long long pc_ver;       // model_ver + 1 of the vector in Small::pc (0: none)
-  double pc_t;                     // its horizon
+  unsigned long long pc_ver;       // model_ver + 1 of the vectors in Small::pc (0: none)
+  double pc_t[2];                  // their horizons: the first and the last of the call that made them
 };
 
 // Scratch of the small solve (single copy).
@@ -124,7 +124,7 @@ struct Small {
   float2* V;        // kMaxN x kMaxN                   right singular vectors of K (kept)
   float2* QB;       // (cap+1) x r_max, col-major ld cap+1: pass-B rotation (compaction)
   float2* coef;     // (cap+1) x kRollK rollout coefficients in L0 coordinates
-  float2* pc;       // kMaxN: A~^{pc_t} y of the model of version pc_ver - 1 (see Ctl)
+  float2* pc;       // 2 x kMaxN: A~^{pc_t[s]} y, s = 0, 1, of the model of version pc_ver - 1 (see Ctl)
 };
 
 // Eigen-cache.

@@ -1566,13 +1566,19 @@ __global__ void __launch_bounds__(kPowThreads) k_coef_pow(Ws ws, TArr ts, TOrd o
     const int i = idx / r, l = idx % r;
     S.A[i * kPowLd + l] = f2_of(dd_div(LD(st.M, (size_t)l * rm + i), LD(st.S, l)));
   }
-  // start from the vector of the previous call when it belongs to this model and to a
-  // horizon not after the first one asked for (a check right after a predict)
+  // start from a vector of the previous call when it belongs to this model: the latest of
+  // its first and last horizons that is not after the first one asked for (a check of the
+  // first or of the next state after a predict needs no powering)
   const unsigned long long ver = ctl->model_ver;
-  const bool reuse = k > 0 && ctl->pc_ver == ver + 1ull && ctl->pc_t <= ts.t[ord.i[0]];
-  long long tcur = reuse ? (long long)ctl->pc_t : 0;
+  int slot = -1;
+  if (k > 0 && ctl->pc_ver == ver + 1ull) {
+    const double t0 = ts.t[ord.i[0]];
+    for (int q = 0; q < 2; ++q)
+      if (ctl->pc_t[q] <= t0 && (slot < 0 || ctl->pc_t[q] > ctl->pc_t[slot])) slot = q;
+  }
+  long long tcur = slot >= 0 ? (long long)ctl->pc_t[slot] : 0;
   for (int l = tid; l < r; l += kPowThreads)
-    S.v[0][l] = reuse ? ws.sm.pc[l] : f2_of(LD(st.S, l) * LD(st.rf, l));
+    S.v[0][l] = slot >= 0 ? ws.sm.pc[slot * kMaxN + l] : f2_of(LD(st.S, l) * LD(st.rf, l));
   __syncthreads();
   int cur = 0;  // S.v[cur] holds the vector
   for (int q = 0; q < k; ++q) {
@@ -1612,6 +1618,12 @@ __global__ void __launch_bounds__(kPowThreads) k_coef_pow(Ws ws, TArr ts, TOrd o
       }
     }
     for (int l = tid; l < r; l += kPowThreads) S.C[j * kMaxR + l] = S.v[cur][l];
+    if (q == 0) {
+      const long long tf = tcur;
+      __syncthreads();  // slot 0 may be the vector this call started from
+      for (int l = tid; l < r; l += kPowThreads) ws.sm.pc[l] = S.v[cur][l];
+      if (tid == 0) ctl->pc_t[0] = (double)tf;
+    }
     // (read only after the barrier that ends the next step, or the final one)
   }
   __syncthreads();
@@ -1626,9 +1638,9 @@ __global__ void __launch_bounds__(kPowThreads) k_coef_pow(Ws ws, TArr ts, TOrd o
     if (e < r0 * k && sub == 0) ws.sm.coef[(size_t)j * qld + i] = f2_of(acc);
   }
   if (k > 0) {
-    for (int l = tid; l < r; l += kPowThreads) ws.sm.pc[l] = S.v[cur][l];
+    for (int l = tid; l < r; l += kPowThreads) ws.sm.pc[kMaxN + l] = S.v[cur][l];
     if (tid == 0) {
-      ctl->pc_t = (double)tcur;
+      ctl->pc_t[1] = (double)tcur;
       ctl->pc_ver = ver + 1ull;
     }
   }

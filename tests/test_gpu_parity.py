@@ -272,3 +272,30 @@ def test_powers_and_eigen_paths_agree(stream):
             assert np.linalg.norm(got[j] - want[j]) / np.linalg.norm(want[j]) < 1e-9, (stream, ts[j])
     scale = np.linalg.norm(want, axis=1)
     assert np.max(np.linalg.norm(by_powers - by_eigen, axis=1) / scale) < 1e-10
+
+
+def test_powers_path_resumes_from_earlier_calls():
+    """Integer-horizon calls start from the vector A~^t y that the previous call of the same
+    model left at its first or last horizon, when that horizon is not after the first one
+    asked for; a new snapshot or a refinement makes a new model and the vectors stale.  Every
+    call must agree with the oracle and with a call that started from t = 0."""
+    X = WakeField(nx=64, ny=32, sigma=1e-6, seed=1).snapshots(0, 301)
+    m, ref = run_pair(X[:300], 16, slack=4)
+    ts = [float(t) for t in range(300, 350)]
+    first = m.predict(ts).cpu().numpy()                   # from t = 0
+    want = ref.predict(ts).T
+    scale = np.linalg.norm(want, axis=1)
+    assert np.max(np.linalg.norm(first - want, axis=1) / scale) < 1e-9
+    xs = torch.from_numpy(np.ascontiguousarray(want)).cuda()
+    for t in (300.0, 349.0, 360.0, 305.0, 300.0):         # first horizon, last, later, earlier
+        j = int(t) - 300
+        x_t = xs[j] if j < len(ts) else torch.from_numpy(np.ascontiguousarray(ref.predict([t])[:, 0])).cuda()
+        err, _ = m.check(t, x_t)
+        assert err < 1e-9, t
+    again = m.predict(ts[5:]).cpu().numpy()               # resumes from t = 305 or 300
+    assert np.max(np.linalg.norm(again - first[5:], axis=1) / scale[5:]) < 1e-11
+    m.update(torch.from_numpy(X[300]).cuda())             # a new model: no reuse
+    ref.update(X[300])
+    got = m.predict(ts[1:]).cpu().numpy()
+    want2 = ref.predict(ts[1:]).T
+    assert np.max(np.linalg.norm(got - want2, axis=1) / np.linalg.norm(want2, axis=1)) < 1e-9
