@@ -27,12 +27,12 @@ def match_eigs(a, b):
     return worst
 
 
-def run_pair(X, r_max, slack=16, tau=1e-10, prec="fp64"):
+def run_pair(X, r_max, slack=16, tau=1e-10, prec="fp64", refine_every=0):
     import paper_2311_18715_gb300 as pkg
 
     dev = torch.device("cuda", 0)
     dt = torch.float64 if prec == "fp64" else torch.float32
-    m = pkg.OnlineDMD(X.shape[1], r_max, prec=prec, slack=slack, trunc_tol=tau)
+    m = pkg.OnlineDMD(X.shape[1], r_max, prec=prec, slack=slack, trunc_tol=tau, refine_every=refine_every)
     ref = OnlineDMDRef(X.shape[1], r_max, tau)
     Xd = torch.from_numpy(X).to(dev, dt)
     for k in range(X.shape[0]):
@@ -299,3 +299,46 @@ def test_powers_path_resumes_from_earlier_calls():
     got = m.predict(ts[1:]).cpu().numpy()
     want2 = ref.predict(ts[1:]).T
     assert np.max(np.linalg.norm(got - want2, axis=1) / np.linalg.norm(want2, axis=1)) < 1e-9
+
+
+def _driven_linear_stream(n, steps, seed):
+    """A damped random linear system driven by noise, x_{k+1} = 0.97 A x_k + 0.3 xi_k with
+    A Gaussian / sqrt(n): every snapshot adds a direction, so the rank reaches any r_max
+    and the truncation and compaction run at every update."""
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((n, n)) / np.sqrt(n) * 0.97
+    X = np.empty((steps, n))
+    X[0] = rng.standard_normal(n)
+    for k in range(steps - 1):
+        X[k + 1] = A @ X[k] + 0.3 * rng.standard_normal(n)
+    return X
+
+
+@pytest.mark.parametrize("slack", [32, 0])
+def test_largest_rank_and_slack(slack):
+    """r_max and slack at their limits (64 and 32: 96 basis columns, the widest tiles and
+    the largest core and reduced operator), n = 4999 rows (a ragged last tile), 140
+    snapshots with more than 64 active directions.  The oracle's own response to a 1e-12
+    relative perturbation of the snapshots is 5e-14 of sigma_1 in the singular values,
+    3e-12 relative in the predictions and 3e-14 in the projector, far below the bars.
+    Predictions take two launches (65 horizons); the refinement runs at its largest size."""
+    X = _driven_linear_stream(4999, 140, 11)
+    m, ref = run_pair(X, 64, slack=slack, refine_every=1000)  # scratch reserved, refined only on demand
+    assert m.rank == ref.rank == 64
+    np.testing.assert_allclose(np.array(m.singular_values()), ref.S, rtol=0, atol=1e-10 * ref.S[0])
+    L = m.basis().cpu().numpy().T
+    assert np.max(np.abs(L @ L.T - ref.L @ ref.L.T)) < 1e-9
+    assert np.max(np.abs(L.T @ L - np.eye(64))) < 1e-12
+    ts = [float(t) for t in range(0, 130, 2)]
+    want = ref.predict(ts).T
+    for got in (m.predict(ts).cpu().numpy(), m.predict(ts[:-1] + [128.5]).cpu().numpy()[:-1]):
+        k = got.shape[0]
+        assert np.linalg.norm(got - want[:k]) / np.linalg.norm(want[:k]) < 1e-9
+    err, _ = m.check(139.0, torch.from_numpy(X[139]).cuda())
+    assert abs(err - ref.check(139.0, X[139])[0]) < 1e-9
+    m.refine()
+    np.testing.assert_allclose(np.array(m.singular_values()), ref.S, rtol=0, atol=1e-10 * ref.S[0])
+    L = m.basis().cpu().numpy().T
+    assert np.max(np.abs(L.T @ L - np.eye(64))) < 1e-13
+    got = m.predict(ts).cpu().numpy()
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-9
