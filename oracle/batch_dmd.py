@@ -44,3 +44,31 @@ class BatchDMD:
 
     def projector(self) -> np.ndarray:
         return self.L @ self.L.T
+
+
+class BatchPairDMD:
+    """Exact DMD of paired matrices X -> Y, from the definition (Sec. 2.3 with arbitrary
+    pairs): truncated SVD X = L S R^T by LAPACK, A~_r = L^T Y R S^{-1}, and a prediction
+    from a state u as Phi Lambda^t Phi^+ u with Phi^+ = pinv(Phi) taken literally."""
+
+    def __init__(self, X: np.ndarray, Y: np.ndarray, r_max: int, trunc_tol: float = 1e-10):
+        X = np.asarray(X, dtype=np.float64)
+        Y = np.asarray(Y, dtype=np.float64)
+        Lf, sf, Rt = np.linalg.svd(X, full_matrices=False)
+        keep = int(np.count_nonzero(sf > trunc_tol * sf[0]))
+        keep = max(1, min(keep, r_max))
+        self.L = Lf[:, :keep]
+        self.S = sf[:keep]
+        self.R = Rt[:keep, :].T
+        self.Atilde = self.L.T @ Y @ self.R / self.S[None, :]
+        self.lam, self.V = np.linalg.eig(self.Atilde)
+        self.Phi = self.L @ self.V
+
+    def predict_from(self, u, ts) -> np.ndarray:
+        b = np.linalg.pinv(self.Phi) @ np.asarray(u, dtype=np.float64).reshape(-1)
+        cols = []
+        for t in np.atleast_1d(np.asarray(ts, dtype=np.float64)):
+            lt = np.ones_like(self.lam) if t == 0 else np.where(
+                self.lam != 0, np.exp(t * np.log(np.where(self.lam != 0, self.lam, 1))), 0)
+            cols.append((self.Phi @ (lt * b)).real)
+        return np.stack(cols, axis=1)
