@@ -1,0 +1,59 @@
+/* A plain C99 client of include/odmd.h: the header compiles as strict C, the library links
+ * and its host-side entry points (configuration, workspace size, argument checks, error
+ * strings) answer without a GPU.  Prints "ok" and exits 0, or names the first failure. */
+#include <stdio.h>
+#include <string.h>
+
+#include "odmd.h"
+
+#define EXPECT(cond)                                               \
+  do {                                                             \
+    if (!(cond)) {                                                 \
+      fprintf(stderr, "abi_host: failed %s (line %d)\n", #cond, __LINE__); \
+      return 1;                                                    \
+    }                                                              \
+  } while (0)
+
+int main(void) {
+  odmd_config cfg;
+  size_t bytes = 0, small = 0;
+  double s[4];
+  int32_t r = -1;
+  const char* msg;
+
+  EXPECT(odmd_config_default(&cfg, 393216, 40) == ODMD_OK);
+  EXPECT(cfg.n == 393216 && cfg.r_max == 40 && cfg.prec == ODMD_FP64 && cfg.flags == 0u);
+  EXPECT(odmd_footprint(&cfg, &bytes) == ODMD_OK);
+  /* two float planes of N x (r_max + slack) columns at least */
+  EXPECT(bytes > (size_t)2 * 393216 * (size_t)(cfg.r_max + cfg.slack) * 4);
+
+  EXPECT(odmd_config_default(&cfg, 1000, 8) == ODMD_OK);
+  EXPECT(odmd_footprint(&cfg, &small) == ODMD_OK);
+  EXPECT(small > 0 && small < bytes);
+
+  /* out-of-range configurations are refused with the reason */
+  EXPECT(odmd_config_default(&cfg, 1000, 65) == ODMD_OK);
+  EXPECT(odmd_footprint(&cfg, &small) == ODMD_ERR_ARG);
+  msg = odmd_last_error(NULL);
+  EXPECT(msg != NULL && strstr(msg, "r_max") != NULL);
+  EXPECT(odmd_config_default(&cfg, 0, 8) == ODMD_OK && cfg.n == 0);  /* filled, checked later */
+  EXPECT(odmd_footprint(&cfg, &small) == ODMD_ERR_ARG);
+  EXPECT(odmd_config_default(NULL, 10, 8) == ODMD_ERR_ARG);
+  EXPECT(odmd_config_default(&cfg, 1000, 8) == ODMD_OK);
+  cfg.flags = 1u;
+  EXPECT(odmd_footprint(&cfg, &small) == ODMD_ERR_ARG);
+  EXPECT(odmd_footprint(NULL, &small) == ODMD_ERR_ARG);
+
+  /* every handle call refuses a NULL handle before it touches the device */
+  EXPECT(odmd_update(NULL, NULL) == ODMD_ERR_ARG);
+  EXPECT(odmd_predict(NULL, NULL, 0, NULL, 0) == ODMD_ERR_ARG);
+  EXPECT(odmd_get_rank(NULL, &r) == ODMD_ERR_ARG);
+  EXPECT(odmd_get_singular_values(NULL, s, 4, &r) == ODMD_ERR_ARG);
+  EXPECT(odmd_checkpoint_size(NULL, &small) == ODMD_ERR_ARG);
+  EXPECT(odmd_destroy(NULL) == ODMD_ERR_ARG);
+  msg = odmd_last_error(NULL);
+  EXPECT(msg != NULL && strstr(msg, "NULL") != NULL);
+
+  printf("ok\n");
+  return 0;
+}

@@ -65,3 +65,28 @@ def test_footprint_and_argument_checks_on_host():
     assert lib.odmd_checkpoint_size(None, None) == 1
     assert lib.odmd_save(None, None, 0) == 1
     assert lib.odmd_load(None, None, 0) == 1
+
+
+def test_plain_c_client_compiles_links_and_runs():
+    """include/odmd.h is strict C99 (-pedantic -Werror) and a C program linked against
+    libodmd.so gets answers from its host-side entry points without a GPU."""
+    import shutil
+    import subprocess
+    import tempfile
+
+    import paper_2311_18715_gb300 as pkg
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    pkg.build()
+    libdir = os.path.dirname(pkg.load_library()._name)
+    with tempfile.TemporaryDirectory() as tmp:
+        exe = os.path.join(tmp, "abi_host")
+        cmd = [cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+               os.path.join(ROOT, "tests", "c", "abi_host.c"), "-L", libdir, "-lodmd", "-Wl,-rpath," + libdir,
+               "-o", exe]
+        res = subprocess.run(cmd, capture_output=True, text=True)
+        assert res.returncode == 0, res.stderr
+        run = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+        assert run.returncode == 0 and run.stdout.strip() == "ok", run.stderr
