@@ -433,27 +433,36 @@ odmd_status build_update_graph(odmd_t h, int par, int prof) {
     if (graph) cudaGraphDestroy(graph);
     return cuda_fail(h, e, "update graph capture");
   }
+  // find the ingest node (its source pointer changes every update) and the event nodes;
+  // the captured graph is released on every way out that does not keep it
   size_t nn = 0;
-  CK(h, cudaGraphGetNodes(graph, nullptr, &nn), "graph nodes");
-  std::vector<cudaGraphNode_t> nodes(nn);
-  CK(h, cudaGraphGetNodes(graph, nodes.data(), &nn), "graph nodes");
+  e = cudaGraphGetNodes(graph, nullptr, &nn);
+  std::vector<cudaGraphNode_t> nodes(e == cudaSuccess ? nn : 0);
+  if (e == cudaSuccess) e = cudaGraphGetNodes(graph, nodes.data(), &nn);
   const void* ingest_fn = ingest_kernel(h->ws.prec);
-  for (cudaGraphNode_t nd : nodes) {
+  for (size_t i = 0; e == cudaSuccess && i < nodes.size(); ++i) {
+    cudaGraphNode_t nd = nodes[i];
     cudaGraphNodeType t;
-    CK(h, cudaGraphNodeGetType(nd, &t), "node type");
+    e = cudaGraphNodeGetType(nd, &t);
+    if (e != cudaSuccess) break;
     if (t == cudaGraphNodeTypeKernel) {
       cudaKernelNodeParams kp{};
-      CK(h, cudaGraphKernelNodeGetParams(nd, &kp), "node params");
-      if (kp.func == ingest_fn) {
+      e = cudaGraphKernelNodeGetParams(nd, &kp);
+      if (e == cudaSuccess && kp.func == ingest_fn) {
         G.ingest = nd;
         G.kp = kp;
       }
     } else if (t == cudaGraphNodeTypeEventRecord) {
       cudaEvent_t ev;
-      CK(h, cudaGraphEventRecordNodeGetEvent(nd, &ev), "node event");
-      for (int i = 0; i < 6; ++i)
-        if (ev == ph[i]) G.ev[i] = nd;
+      e = cudaGraphEventRecordNodeGetEvent(nd, &ev);
+      for (int k = 0; e == cudaSuccess && k < 6; ++k)
+        if (ev == ph[k]) G.ev[k] = nd;
     }
+  }
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    G.ingest = nullptr;
+    return cuda_fail(h, e, "update graph nodes");
   }
   if (!G.ingest) {
     cudaGraphDestroy(graph);
@@ -576,6 +585,7 @@ odmd_status odmd_create(const odmd_config* cfg, void* workspace_dev, size_t byte
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     std::string m = std::string("create: ") + cudaGetErrorString(e);
+    if (h->pinned) cudaFreeHost(h->pinned);
     delete h;
     return fail(nullptr, ODMD_ERR_CUDA, m);
   }
