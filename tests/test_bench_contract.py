@@ -1,6 +1,6 @@
 """The benchmark's command-line contract on CPU: the reference arm (the FP64 oracle on the
-host cores) prints one JSON line with the keys and units of the device arm, and the
-warm-up floor is enforced."""
+host cores) prints one JSON line with the keys and units of the device arm, alone or under
+torchrun, and the warm-up floor is enforced."""
 import json
 import os
 import subprocess
@@ -40,3 +40,19 @@ def test_warmup_below_three_is_refused():
     res = _bench("--impl", "reference", "--steps", "1", "--warmup", "2", timeout=120)
     assert res.returncode != 0
     assert "warmup" in res.stderr
+
+
+def test_reference_arm_under_torchrun_prints_once():
+    """Launched as the multi-rank benchmark is (torchrun, one process per rank; gloo here),
+    the reference arm runs on rank 0 alone: exactly one JSON line, with n_gpus = 2, and every
+    rank exits 0."""
+    env = dict(os.environ, ODMD_BENCH_BACKEND="gloo", MASTER_ADDR="127.0.0.1")
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", "29531", os.path.join(ROOT, "bench.py"),
+           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "3"]
+    res = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+    assert res.returncode == 0, res.stderr[-2000:]
+    lines = [l for l in res.stdout.splitlines() if l.strip().startswith("{")]
+    assert len(lines) == 1, res.stdout
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
