@@ -57,6 +57,10 @@ def _mutations():
     def pow_shift(lam, t):
         return orig_pow(lam, t + 1.0)
 
+    def gs_once(L, c, p):
+        # classical Gram-Schmidt applied once: the correction s = L^T e is never taken
+        return p, c - L @ p
+
     return [
         ("operator_update", op_sign),
         ("operator_update", op_drop_w),
@@ -67,10 +71,11 @@ def _mutations():
         ("core_matrix", core_transposed),
         ("new_direction", dir_unnormalised),
         ("powers", staticmethod(pow_shift)),
+        ("orthogonalise_cgs2", gs_once),
     ]
 
 
-@pytest.mark.parametrize("idx", range(9))
+@pytest.mark.parametrize("idx", range(10))
 def test_planted_mistake_is_caught(idx, monkeypatch):
     name, bad = _mutations()[idx]
     if name == "powers":
