@@ -4,8 +4,9 @@
 Workload: the cylinder-wake-shaped stream on a 512 x 256 grid with (u, v, p) stacked
 (n = 393,216), rank cap 40, FP64-accuracy mode, 2000-snapshot horizon, credibility
 check every 50 steps.  One step is one 50-snapshot block of the hybrid loop: 50 rank-1
-updates, the eigensolve plus a rollout of the next 50 states, and one credibility check
-against the held-out next snapshot.  The model is first brought to steady state (rank
+updates, a rollout of the next 50 states (integer horizons: coefficients by powers of the
+reduced operator, no eigensolve), and one credibility check against the held-out next
+snapshot.  The model is first brought to steady state (rank
 40) on 100 untimed snapshots.
 
 Timing: inputs resident in HBM; before every update / predict / check a 256 MiB buffer
