@@ -44,6 +44,37 @@ int main(void) {
   EXPECT(odmd_footprint(&cfg, &small) == ODMD_ERR_ARG);
   EXPECT(odmd_footprint(NULL, &small) == ODMD_ERR_ARG);
 
+  /* every limit the header states is enforced */
+  {
+    odmd_config c;
+    EXPECT(odmd_config_default(&c, 2147483648LL, 8) == ODMD_OK);
+    EXPECT(odmd_footprint(&c, &small) == ODMD_ERR_ARG); /* n above 2^31 - 1 */
+    EXPECT(odmd_config_default(&c, 1000, 0) == ODMD_OK);
+    EXPECT(odmd_footprint(&c, &small) == ODMD_ERR_ARG); /* r_max below 1 */
+    EXPECT(odmd_config_default(&c, 1000, 64) == ODMD_OK);
+    EXPECT(odmd_footprint(&c, &small) == ODMD_OK);      /* r_max 64 is the top */
+    c.slack = 33;
+    EXPECT(odmd_footprint(&c, &small) == ODMD_ERR_ARG); /* slack above 32 */
+    c.slack = -1;
+    EXPECT(odmd_footprint(&c, &small) == ODMD_ERR_ARG);
+    c.slack = 32;
+    EXPECT(odmd_footprint(&c, &small) == ODMD_OK);
+    c.trunc_tol = 1e-14;
+    EXPECT(odmd_footprint(&c, &small) == ODMD_ERR_ARG); /* tau below 1e-13 */
+    c.trunc_tol = 1.0;
+    EXPECT(odmd_footprint(&c, &small) == ODMD_ERR_ARG); /* tau not below 1 */
+    c.trunc_tol = 1e-10;
+    c.prec = (odmd_precision)3;
+    EXPECT(odmd_footprint(&c, &small) == ODMD_ERR_ARG); /* no such precision */
+    c.prec = ODMD_BF16;
+    EXPECT(odmd_footprint(&c, &small) == ODMD_ERR_ARG); /* refused, with the reason */
+    c.prec = ODMD_FP32;
+    c.refine_every = -1;
+    EXPECT(odmd_footprint(&c, &small) == ODMD_ERR_ARG);
+    c.refine_every = 10;
+    EXPECT(odmd_footprint(&c, &small) == ODMD_OK);
+  }
+
   /* every handle call refuses a NULL handle before it touches the device */
   EXPECT(odmd_update(NULL, NULL) == ODMD_ERR_ARG);
   EXPECT(odmd_predict(NULL, NULL, 0, NULL, 0) == ODMD_ERR_ARG);
