@@ -75,6 +75,19 @@ int main(void) {
     EXPECT(odmd_footprint(&c, &small) == ODMD_OK);
   }
 
+  /* the allocation-free check refuses bad arguments before it touches the device (the
+   * pointers below are never dereferenced: each call fails its argument checks first) */
+  {
+    const double* fake = (const double*)(uintptr_t)256;
+    double err = 0.0;
+    int32_t pass = 0;
+    EXPECT(odmd_check_noalloc(NULL, fake, 10, 1e-5, NULL, &err, &pass) == ODMD_ERR_ARG);
+    EXPECT(odmd_check_noalloc(fake, fake, 0, 1e-5, NULL, &err, &pass) == ODMD_ERR_ARG);
+    EXPECT(odmd_check_noalloc(fake, fake, 33554433, 1e-5, NULL, &err, &pass) == ODMD_ERR_ARG);
+    msg = odmd_last_error(NULL);
+    EXPECT(msg != NULL && strstr(msg, "33554432") != NULL);
+  }
+
   /* every handle call refuses a NULL handle before it touches the device */
   EXPECT(odmd_update(NULL, NULL) == ODMD_ERR_ARG);
   EXPECT(odmd_predict(NULL, NULL, 0, NULL, 0) == ODMD_ERR_ARG);
