@@ -56,3 +56,35 @@ def test_reference_arm_under_torchrun_prints_once():
     assert len(lines) == 1, res.stdout
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+
+
+def test_clock_sampler_reads_median_clock_and_throttle_reasons(tmp_path):
+    """The clocks object of the JSON line: median SM clock under load, the maximum, and every
+    throttle reason seen active (the names the rejection rule checks)."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class _Proc:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    s = bench.ClockSampler(0)
+    s.path = str(tmp_path / "clocks.csv")
+    lines = [
+        "0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1390.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1200.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "garbled line",
+        "0, 1500, 2070, 1400.0, 0x0000000000000008, Active, Not Active, Not Active, Not Active",
+    ]
+    with open(s.path, "w") as f:
+        f.write("\n".join(lines) + "\n")
+    s.proc = _Proc()
+    s.f = open(os.devnull, "w")
+    c = s.stop()
+    assert c["samples"] == 4
+    assert c["sm_mhz"] == 2025.0 and c["sm_max_mhz"] == 2070.0
+    assert c["reasons"] == ["hw_slowdown", "sw_power_cap"]
