@@ -90,3 +90,39 @@ def test_plain_c_client_compiles_links_and_runs():
         assert res.returncode == 0, res.stderr
         run = subprocess.run([exe], capture_output=True, text=True, timeout=60)
         assert run.returncode == 0 and run.stdout.strip() == "ok", run.stderr
+
+
+def test_library_exports_nothing_the_header_does_not_declare():
+    """Every odmd_* function symbol libodmd.so defines is declared in include/odmd.h (and the
+    other way round), so nothing undocumented is part of the ABI."""
+    import shutil
+    import subprocess
+
+    import paper_2311_18715_gb300 as pkg
+
+    nm = shutil.which("nm")
+    if nm is None:
+        pytest.skip("no nm")
+    pkg.build()
+    path = pkg.load_library()._name
+    out = subprocess.run([nm, "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    exported = {parts[2] for parts in (l.split() for l in out.splitlines())
+                if len(parts) == 3 and parts[1] == "T" and parts[2].startswith("odmd_")}
+    assert exported == declared_functions()
+
+
+def test_header_compiles_as_cplusplus():
+    import shutil
+    import subprocess
+    import tempfile
+
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    with tempfile.TemporaryDirectory() as tmp:
+        src = os.path.join(tmp, "h.cc")
+        with open(src, "w") as f:
+            f.write('#include "odmd.h"\nint main() { odmd_config c; return odmd_config_default(&c, 10, 2); }\n')
+        res = subprocess.run([cxx, "-std=c++17", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
+                              "-I", os.path.join(ROOT, "include"), src], capture_output=True, text=True)
+        assert res.returncode == 0, res.stderr
