@@ -349,6 +349,22 @@ odmd_status odmd_pairs_predict(odmd_pairs_t h, const double* u_dev, const double
 /* Rank r and the min(r, cap) singular values of X, descending (synchronises). */
 odmd_status odmd_pairs_get_singular_values(odmd_pairs_t h, double* s_host, int32_t cap, int32_t* r);
 
+/* Step `step` of the hybrid loop of Sec. 2 (Fig. 1) in the FOM-only reading, with the
+ * paper's residual test (Sec. 2.2).  On entry state_dev holds u^{k-1}; on return u^k.
+ * With a model, next_dev receives the prediction L A~ L^T u^{k-1} and
+ * residual(user, step, next_dev, r_dev, b_dev, stream) enqueues the FOM's residual
+ * r = b - A u of it and its right-hand side b (state_dev still holds u^{k-1}); the
+ * prediction is taken, without updating the model, when ||r|| / ||b|| <= tol (tol <= 0:
+ * 1e-5, Sec. 3).  Otherwise next_dev receives u^{k-1}, fom(user, step, next_dev, stream)
+ * enqueues the FOM's solve into it in place, and the pair (u^{k-1}, u^k) updates the model.
+ * Four distinct device buffers of n doubles, owned by the caller; accepted and rel_res
+ * (+inf without a prediction) are host outputs, either may be NULL.  Synchronises.
+ * Errors: ODMD_ERR_ARG (NULL or aliased buffers), ODMD_ERR_STATE (a callback returned
+ * nonzero), ODMD_ERR_NUMERIC (non-finite residual), ODMD_ERR_CUDA. */
+odmd_status odmd_pairs_hybrid_step_residual(odmd_pairs_t h, odmd_residual_fn residual, odmd_fom_fn fom, void* user,
+                                            double tol, int64_t step, double* state_dev, double* next_dev,
+                                            double* r_dev, double* b_dev, int32_t* accepted, double* rel_res);
+
 /* Pairs appended so far (host counter, no synchronisation). */
 odmd_status odmd_pairs_get_count(odmd_pairs_t h, int64_t* pairs);
 

@@ -684,6 +684,56 @@ __global__ void k_pr_rollout(PWs w, int k, double* out, int64_t ld) {
   }
 }
 
+// ||r||^2 and ||b||^2 in double (the relative residual of the hybrid step), per-CTA partials
+// in part, then the last CTA sums them in CTA order into aux (as doubles, bytes 32..47)
+__global__ void __launch_bounds__(kThreads) k_pr_norms(PWs w, const double* r, const double* b) {
+  __shared__ double sh[2][kWarps];
+  __shared__ unsigned ticket;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double sr = 0.0, sb = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + tid; i < w.n; i += (int64_t)gridDim.x * kThreads) {
+    sr = fma(r[i], r[i], sr);
+    sb = fma(b[i], b[i], sb);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    sb += __shfl_xor_sync(0xffffffffu, sb, o);
+  }
+  if (lane == 0) {
+    sh[0][warp] = sr;
+    sh[1][warp] = sb;
+  }
+  __syncthreads();
+  double* mine = reinterpret_cast<double*>(w.part + (size_t)blockIdx.x * kPart);
+  if (tid == 0) {
+    double a = 0.0, c = 0.0;
+    for (int k = 0; k < kWarps; ++k) {
+      a += sh[0][k];
+      c += sh[1][k];
+    }
+    mine[0] = a;
+    mine[1] = c;
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) ticket = atomicAdd(&w.hdr->ticket, 1u);
+  __syncthreads();
+  if (ticket != (unsigned)(gridDim.x - 1)) return;
+  __threadfence();
+  if (tid == 0) {
+    double a = 0.0, c = 0.0;
+    for (int k = 0; k < (int)gridDim.x; ++k) {
+      const double* pk = reinterpret_cast<const double*>(w.part + (size_t)k * kPart);
+      a += __ldcg(pk);
+      c += __ldcg(pk + 1);
+    }
+    double* out = reinterpret_cast<double*>(w.aux + 4);
+    out[0] = a;
+    out[1] = c;
+    w.hdr->ticket = 0u;
+  }
+}
+
 }  // namespace pairs
 }  // namespace odmd
 
@@ -931,6 +981,52 @@ odmd_status odmd_pairs_get_singular_values(odmd_pairs_t h, double* s_host, int32
 odmd_status odmd_pairs_get_count(odmd_pairs_t h, int64_t* pairs) {
   if (!h || !pairs) return pfail(h, ODMD_ERR_ARG, "handle and pairs must not be NULL");
   *pairs = h->pairs;
+  return ODMD_OK;
+}
+
+odmd_status odmd_pairs_hybrid_step_residual(odmd_pairs_t h, odmd_residual_fn residual, odmd_fom_fn fom, void* user,
+                                            double tol, int64_t step, double* state_dev, double* next_dev,
+                                            double* r_dev, double* b_dev, int32_t* accepted, double* rel_res) {
+  if (!h) return pfail(nullptr, ODMD_ERR_ARG, "handle is NULL");
+  if (!residual || !fom) return pfail(h, ODMD_ERR_ARG, "the residual and FOM callbacks must not be NULL");
+  if (!state_dev || !next_dev || !r_dev || !b_dev) return pfail(h, ODMD_ERR_ARG, "state, next, r and b must not be NULL");
+  const double* bufs[4] = {state_dev, next_dev, r_dev, b_dev};
+  for (int i = 0; i < 4; ++i)
+    for (int j = i + 1; j < 4; ++j)
+      if (bufs[i] == bufs[j]) return pfail(h, ODMD_ERR_ARG, "state, next, r and b must be four different buffers");
+  if (!(tol > 0.0)) tol = 1e-5;  // Sec. 3's tolerance
+  const size_t bytes = (size_t)h->w.n * sizeof(double);
+  Hdr hd;
+  PCK(h, cudaStreamSynchronize(h->stream), "sync");
+  PCK(h, cudaMemcpy(&hd, h->w.hdr, sizeof hd, cudaMemcpyDeviceToHost), "read rank");
+  int32_t acc = 0;
+  double rel = INFINITY;
+  if (hd.r > 0) {
+    const double one = 1.0;
+    if (odmd_status s = odmd_pairs_predict(h, state_dev, &one, 1, next_dev, h->w.n)) return s;
+    if (residual(user, step, next_dev, r_dev, b_dev, h->stream) != 0)
+      return pfail(h, ODMD_ERR_STATE, "residual callback reported a failure");
+    k_pr_norms<<<h->w.grid, kThreads, 0, h->stream>>>(h->w, r_dev, b_dev);
+    PCK(h, cudaGetLastError(), "residual norm launch");
+    double nd[2];
+    PCK(h, cudaMemcpyAsync(nd, reinterpret_cast<double*>(h->w.aux + 4), sizeof nd, cudaMemcpyDeviceToHost, h->stream),
+        "read back");
+    PCK(h, cudaStreamSynchronize(h->stream), "sync");
+    if (!std::isfinite(nd[0]) || !std::isfinite(nd[1])) return pfail(h, ODMD_ERR_NUMERIC, "non-finite residual");
+    rel = nd[1] > 0.0 ? std::sqrt(nd[0] / nd[1]) : (nd[0] == 0.0 ? 0.0 : INFINITY);
+    acc = rel <= tol ? 1 : 0;
+  }
+  if (acc) {
+    PCK(h, cudaMemcpyAsync(state_dev, next_dev, bytes, cudaMemcpyDeviceToDevice, h->stream), "take the prediction");
+  } else {
+    // the FOM's step starts from u^{k-1}; the pair (u^{k-1}, u^k) updates the model
+    PCK(h, cudaMemcpyAsync(next_dev, state_dev, bytes, cudaMemcpyDeviceToDevice, h->stream), "FOM input");
+    if (fom(user, step, next_dev, h->stream) != 0) return pfail(h, ODMD_ERR_STATE, "FOM callback reported a failure");
+    if (odmd_status s = odmd_pairs_update(h, state_dev, next_dev)) return s;
+    PCK(h, cudaMemcpyAsync(state_dev, next_dev, bytes, cudaMemcpyDeviceToDevice, h->stream), "take the FOM state");
+  }
+  if (accepted) *accepted = acc;
+  if (rel_res) *rel_res = rel;
   return ODMD_OK;
 }
 

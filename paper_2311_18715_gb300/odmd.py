@@ -387,6 +387,46 @@ class OnlineDMDPairs:
                                                             C.c_void_p(out.data_ptr()), self.n), self._h)
         return out
 
+    def hybrid_step_residual(self, residual, fom, step: int, state: torch.Tensor, nxt: torch.Tensor,
+                             r: torch.Tensor, b: torch.Tensor, tol: float = 0.0) -> tuple[bool, float]:
+        """odmd_pairs_hybrid_step_residual: one step of the FOM-only hybrid loop.  residual(step)
+        fills r and b for the prediction in nxt (state still holds the previous state);
+        fom(step) advances nxt in place from the previous state.  Returns (accepted, relative
+        residual)."""
+        from ._lib import FOM_FN, RESIDUAL_FN
+
+        for t, name in ((state, "state"), (nxt, "next"), (r, "r"), (b, "b")):
+            self._vec(t, name)
+        failure = []
+
+        def _res(user, st, u, rr, bb, stream):
+            try:
+                with torch.cuda.stream(self.stream):
+                    residual(int(st))
+                return 0
+            except Exception as e:
+                failure.append(e)
+                return 1
+
+        def _fom(user, st, u, stream):
+            try:
+                with torch.cuda.stream(self.stream):
+                    fom(int(st))
+                return 0
+            except Exception as e:
+                failure.append(e)
+                return 1
+
+        cres, cfom = RESIDUAL_FN(_res), FOM_FN(_fom)
+        acc, rel = C.c_int32(), C.c_double()
+        st = self._lib.odmd_pairs_hybrid_step_residual(
+            self._h, cres, cfom, None, float(tol), int(step), C.c_void_p(state.data_ptr()),
+            C.c_void_p(nxt.data_ptr()), C.c_void_p(r.data_ptr()), C.c_void_p(b.data_ptr()), C.byref(acc), C.byref(rel))
+        if failure:
+            raise failure[0]
+        self._check(self._lib, st, self._h)
+        return bool(acc.value), float(rel.value)
+
     def singular_values(self) -> list[float]:
         buf = (C.c_double * self.r_max)()
         r = C.c_int32()

@@ -128,3 +128,46 @@ def test_hybrid_loop_with_fom_only_updates():
     assert fom_steps == want_fom
     assert np.linalg.norm(state.cpu().numpy() - want_states[-1]) <= 1e-9 * np.linalg.norm(u0)
     np.testing.assert_allclose(np.array(dev.singular_values()), ref.S, rtol=0, atol=1e-10 * ref.S[0])
+
+
+def test_hybrid_step_residual_through_the_abi():
+    """The same loop through odmd_pairs_hybrid_step_residual: the residual of the explicit
+    linear FOM u_k = A u_{k-1} is r = b - u with b = A u_{k-1}, so the relative residual is
+    the prediction's relative error; every fourth step the callback returns r = b (relative
+    residual 1), which sends the step to the FOM.  Step for step as the oracle's loop."""
+    n, tol, steps = 4096, 1e-6, 80
+    Ar, B = _low_rank_map(n, 6, 4)
+    A = Ar + 0.3 * (np.eye(n) - B @ B.T)
+    rng = np.random.default_rng(5)
+    u0 = B @ rng.standard_normal(6) + 1e-3 * rng.standard_normal(n)
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+    want_states, want_fom, ref = hybrid_fom_updates(
+        lambda k, u: A @ u, lambda k, prev, pred: k % 4 != 0 and rel(pred, A @ prev) <= tol, u0, steps, 16)
+    import paper_2311_18715_gb300 as pkg
+
+    dev = pkg.OnlineDMDPairs(n, 16)
+    Ad = torch.from_numpy(A).cuda()
+    state = torch.from_numpy(u0).cuda().clone()
+    nxt, r, b = (torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(3))
+
+    def residual(k):
+        b.copy_(Ad @ state)
+        if k % 4 == 0:
+            r.copy_(b)
+        else:
+            torch.sub(b, nxt, out=r)
+
+    def fom(k):
+        nxt.copy_(Ad @ nxt)
+
+    fom_steps = []
+    for k in range(1, steps + 1):
+        acc, _ = dev.hybrid_step_residual(residual, fom, k, state, nxt, r, b, tol)
+        if not acc:
+            fom_steps.append(k)
+    assert fom_steps == want_fom
+    assert np.linalg.norm(state.cpu().numpy() - want_states[-1]) <= 1e-9 * np.linalg.norm(u0)
+    np.testing.assert_allclose(np.array(dev.singular_values()), ref.S, rtol=0, atol=1e-10 * ref.S[0])
