@@ -653,6 +653,79 @@ def run_fp32_large(args) -> None:
     model.close()
 
 
+def run_pairs(args) -> None:
+    """The FOM-only hybrid reading: an online DMD fed pairs (x, y) that share no snapshot
+    (x_k, x_{k+1} for even k of the wake stream, n = 393,216, r_max 40), then predictions of
+    50 states from the latest y; updates timed one by one behind the L2 flush."""
+    import torch
+
+    import paper_2311_18715_gb300 as pkg
+    from synth import WakeField
+
+    dev = torch.device("cuda", 0)
+    pkg.build()
+    gen = WakeField(NX, NY, sigma=SIGMA, seed=0)
+    n = gen.n
+    ds = DeviceStream(gen, dev, torch.float64)
+    model = pkg.OnlineDMDPairs(n, R_MAX, trunc_tol=TAU)
+    stream = model.stream
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    x = torch.empty(n, dtype=torch.float64, device=dev)
+    y = torch.empty(n, dtype=torch.float64, device=dev)
+    out = torch.empty((BLOCK, n), dtype=torch.float64, device=dev)
+    pre = 2 * (R_MAX + 10)
+    k = 0
+    while k < pre:
+        model.update(ds.draw(k, x), ds.draw(k + 1, y))
+        k += 2
+    upd, pred, step = [], [], []
+    sampler = ClockSampler(0)
+    for it in range(args.warmup + args.steps):
+        timed = it >= args.warmup
+        if timed and it == args.warmup:
+            sampler.start()
+        st = 0.0
+        for i in range(BLOCK):
+            ds.draw(k, x)
+            ds.draw(k + 1, y)
+            k += 2
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            model.update(x, y)
+            b.record(stream)
+            b.synchronize()
+            if timed:
+                upd.append(a.elapsed_time(b))
+            st += a.elapsed_time(b)
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        model.predict(y, [float(h) for h in range(1, BLOCK + 1)], out=out)
+        b.record(stream)
+        b.synchronize()
+        if timed:
+            pred.append(a.elapsed_time(b))
+            step.append(st + a.elapsed_time(b))
+    clocks = sampler.stop()
+    K = args.steps
+    line = {
+        "metric": METRIC, "value": BLOCK * K / (sum(step) / 1e3), "unit": "snapshot pair updates/s", "n_gpus": 1,
+        "steps": K, "warmup": args.warmup, "ms_per_step": sum(step) / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32x2 (double-float rows) + double-float small solves",
+        "data": "synthetic (fields and coefficients of the wake generator, drawn on the device)",
+        "config": {"workload": f"FOM-only updates: pairs (x_k, x_k+1), k even, of the cylinder-wake field "
+                               f"(n={n}), r_max={R_MAX}, {BLOCK} pairs + {BLOCK}-state prediction per step",
+                   "n": n, "r_max": R_MAX, "l2": "256 MiB buffer written before every update/predict (untimed)"},
+        "predict50_ms_p50": float(np.percentile(pred, 50)),
+        "latency_ms": {"update_p50": float(np.percentile(upd, 50)), "update_p99": float(np.percentile(upd, 99))},
+        "rank": model.rank,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    model.close()
+
+
 def run_batched(args) -> None:
     """64 independent instances, n uniform in [50k, 2M], r_max uniform in {8..64}, FP32
     storage, each a random planted-mode stream (2-8 pairs, noise std 1e-8) on its own CUDA
@@ -799,7 +872,7 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="untimed short run of the same kernels, for ncu captures")
     ap.add_argument("--profile-updates", type=int, default=64)
-    ap.add_argument("--config", choices=["wake", "fp32-large", "batched", "serving", "hybrid"], default="wake",
+    ap.add_argument("--config", choices=["wake", "fp32-large", "batched", "serving", "hybrid", "pairs"], default="wake",
                     help="wake: the headline workload; fp32-large and batched: extra measured configurations")
     args = ap.parse_args()
     if args.profile_case:
@@ -815,6 +888,8 @@ def main():
         run_batched(args)
     elif args.config == "hybrid":
         run_hybrid(args)
+    elif args.config == "pairs":
+        run_pairs(args)
     elif args.config == "serving":
         run_serving(args)
     else:

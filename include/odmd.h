@@ -315,6 +315,65 @@ odmd_status odmd_check_noalloc(const double* pred_dev, const double* x_fom_dev, 
  * NULL).  The string lives until the next call on the same handle. */
 const char* odmd_last_error(odmd_t h);
 
+/* ---------------------------------------------------------------- pairs (FOM-only updates)
+ * Online DMD fed snapshot pairs (x, y = FOM(x)) that need not be contiguous: the hybrid
+ * loop of Sec. 2 (Fig. 1) in the reading where only FOM steps update the model, so the
+ * state a FOM step starts from may be an accepted DMD state rather than the previous
+ * pair's y.  Sec. 2.3's matrices become X = [x_1 .. x_m] ~ L S R^T, Y = [y_1 .. y_m],
+ * A~_r = L^T Y R S^{-1}; the handle keeps L and P = Y R (N x r each, double-float rows), S
+ * and M = L^T P.  Snapshots, states and outputs are double, length n, contiguous, on the
+ * device of the handle; FP64 accuracy only.  Errors are read with odmd_pairs_last_error.
+ */
+typedef struct odmd_pairs_instance* odmd_pairs_t;
+
+/* Device bytes a pairs handle of length n and rank cap r_max (1..64) needs. */
+odmd_status odmd_pairs_footprint(int64_t n, int32_t r_max, size_t* device_bytes);
+
+/* Create a handle on a caller-owned workspace (256-byte aligned, at least
+ * odmd_pairs_footprint bytes; the library allocates no device memory).  trunc_tol is tau
+ * of odmd_config (a new direction enters iff rho > tau max(sigma_1, ||x||); singular values
+ * <= tau sigma_1 are dropped), in [1e-13, 1).  stream: a cudaStream_t as void*. */
+odmd_status odmd_pairs_create(int64_t n, int32_t r_max, double trunc_tol, void* workspace_dev, size_t bytes,
+                              void* stream, odmd_pairs_t* out);
+
+/* Append the pair (x, y): X gains x, Y gains y (asynchronous; a numerical failure of the
+ * update is reported by the next synchronising call, and the model is then unchanged). */
+odmd_status odmd_pairs_update(odmd_pairs_t h, const double* x_dev, const double* y_dev);
+
+/* out[:, j] = L A~^{t_j} L^T u for k <= 64 integer horizons t_j in [0, 1e12] (steps after
+ * the state u); column j at out + j*ld, ld >= n.  Synchronises the stream.
+ * ODMD_ERR_STATE before the first pair with a nonzero x. */
+odmd_status odmd_pairs_predict(odmd_pairs_t h, const double* u_dev, const double* t_host, int32_t k, double* out_dev,
+                               int64_t ld);
+
+/* Rank r and the min(r, cap) singular values of X, descending (synchronises). */
+odmd_status odmd_pairs_get_singular_values(odmd_pairs_t h, double* s_host, int32_t cap, int32_t* r);
+
+/* Step `step` of the hybrid loop of Sec. 2 (Fig. 1) in the FOM-only reading, with the
+ * paper's residual test (Sec. 2.2).  On entry state_dev holds u^{k-1}; on return u^k.
+ * With a model, next_dev receives the prediction L A~ L^T u^{k-1} and
+ * residual(user, step, next_dev, r_dev, b_dev, stream) enqueues the FOM's residual
+ * r = b - A u of it and its right-hand side b (state_dev still holds u^{k-1}); the
+ * prediction is taken, without updating the model, when ||r|| / ||b|| <= tol (tol <= 0:
+ * 1e-5, Sec. 3).  Otherwise next_dev receives u^{k-1}, fom(user, step, next_dev, stream)
+ * enqueues the FOM's solve into it in place, and the pair (u^{k-1}, u^k) updates the model.
+ * Four distinct device buffers of n doubles, owned by the caller; accepted and rel_res
+ * (+inf without a prediction) are host outputs, either may be NULL.  Synchronises.
+ * Errors: ODMD_ERR_ARG (NULL or aliased buffers), ODMD_ERR_STATE (a callback returned
+ * nonzero), ODMD_ERR_NUMERIC (non-finite residual), ODMD_ERR_CUDA. */
+odmd_status odmd_pairs_hybrid_step_residual(odmd_pairs_t h, odmd_residual_fn residual, odmd_fom_fn fom, void* user,
+                                            double tol, int64_t step, double* state_dev, double* next_dev,
+                                            double* r_dev, double* b_dev, int32_t* accepted, double* rel_res);
+
+/* Pairs appended so far (host counter, no synchronisation). */
+odmd_status odmd_pairs_get_count(odmd_pairs_t h, int64_t* pairs);
+
+/* Message of the last failure on h (or of a call that had no handle when h is NULL). */
+const char* odmd_pairs_last_error(odmd_pairs_t h);
+
+/* Release the handle (synchronises first); the workspace is the caller's again. */
+odmd_status odmd_pairs_destroy(odmd_pairs_t h);
+
 #ifdef __cplusplus
 }
 #endif

@@ -6,14 +6,17 @@ The C ABI lives in include/odmd.h and libodmd.so (built in-tree by ``build()``);
 from ._build import build
 from ._lib import EXPORTED, OdmdError, load_library
 
-__all__ = ["build", "load_library", "OdmdError", "EXPORTED", "OnlineDMD", "check_noalloc", "update_batch",
-           "predict_batch"]
+__all__ = ["build", "load_library", "OdmdError", "EXPORTED", "OnlineDMD", "OnlineDMDPairs", "check_noalloc",
+           "update_batch", "predict_batch"]
 
 
 def __getattr__(name):
     if name == "OnlineDMD":
         from .odmd import OnlineDMD
         return OnlineDMD
+    if name == "OnlineDMDPairs":
+        from .odmd import OnlineDMDPairs
+        return OnlineDMDPairs
     if name in ("check_noalloc", "update_batch", "predict_batch"):
         from . import odmd
         return getattr(odmd, name)

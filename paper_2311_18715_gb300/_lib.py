@@ -18,6 +18,9 @@ EXPORTED = [
     "odmd_profile_enable", "odmd_profile_read", "odmd_check_noalloc", "odmd_hybrid_step",
     "odmd_update_batch", "odmd_predict_batch", "odmd_refine", "odmd_checkpoint_size", "odmd_save",
     "odmd_load", "odmd_hybrid_step_residual", "odmd_hybrid_run", "odmd_update_host",
+    "odmd_pairs_footprint", "odmd_pairs_create", "odmd_pairs_update", "odmd_pairs_predict",
+    "odmd_pairs_get_singular_values", "odmd_pairs_get_count", "odmd_pairs_last_error", "odmd_pairs_destroy",
+    "odmd_pairs_hybrid_step_residual",
 ]
 # host callbacks of odmd_hybrid_step_residual: (user, step, u, r, b, stream) and (user, step, u, stream)
 RESIDUAL_FN = C.CFUNCTYPE(C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p)
@@ -93,6 +96,15 @@ def load_library(path: str | None = None) -> C.CDLL:
         "odmd_destroy": [vp],
         "odmd_profile_enable": [vp, i32],
         "odmd_profile_read": [vp, C.POINTER(dbl), C.POINTER(i64), i32, C.POINTER(dbl)],
+        "odmd_pairs_footprint": [i64, i32, C.POINTER(C.c_size_t)],
+        "odmd_pairs_create": [i64, i32, dbl, vp, C.c_size_t, vp, C.POINTER(vp)],
+        "odmd_pairs_update": [vp, vp, vp],
+        "odmd_pairs_predict": [vp, vp, C.POINTER(dbl), i32, vp, i64],
+        "odmd_pairs_get_singular_values": [vp, C.POINTER(dbl), i32, C.POINTER(i32)],
+        "odmd_pairs_get_count": [vp, C.POINTER(i64)],
+        "odmd_pairs_destroy": [vp],
+        "odmd_pairs_hybrid_step_residual": [vp, RESIDUAL_FN, FOM_FN, vp, dbl, i64, vp, vp, vp, vp, C.POINTER(i32),
+                                            C.POINTER(dbl)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -100,6 +112,8 @@ def load_library(path: str | None = None) -> C.CDLL:
         f.restype = C.c_int
     lib.odmd_last_error.argtypes = [vp]
     lib.odmd_last_error.restype = C.c_char_p
+    lib.odmd_pairs_last_error.argtypes = [vp]
+    lib.odmd_pairs_last_error.restype = C.c_char_p
     if path is None:
         _lib = lib
     return lib
@@ -108,4 +122,10 @@ def load_library(path: str | None = None) -> C.CDLL:
 def check(lib, status: int, handle=None) -> None:
     if status != ODMD_OK:
         msg = lib.odmd_last_error(handle)
+        raise OdmdError(status, msg.decode() if msg else "")
+
+
+def check_pairs(lib, status: int, handle=None) -> None:
+    if status != ODMD_OK:
+        msg = lib.odmd_pairs_last_error(handle)
         raise OdmdError(status, msg.decode() if msg else "")

@@ -324,3 +324,133 @@ def predict_batch(models: Sequence[OnlineDMD], ts: Sequence[Sequence[float]]) ->
     lds = (C.c_int64 * max(k, 1))(*[m.n for m in models])
     check(lib, lib.odmd_predict_batch(hs, tp, ks, op, lds, k))
     return outs
+
+
+class OnlineDMDPairs:
+    """Online DMD fed (x, y) snapshot pairs that need not be contiguous: the hybrid loop of
+    Sec. 2 (Fig. 1) in the reading where only FOM steps update the model (y = FOM(x), x the
+    state the FOM started from, a DMD state whenever the step before it was accepted).
+
+    update(x, y) appends the pair; predict(u, ts) returns L A~^t L^T u for integer step
+    counts t after the state u (rows of the result).  FP64 accuracy; double tensors.
+    """
+
+    def __init__(self, n: int, r_max: int, trunc_tol: float = 1e-10,
+                 stream: torch.cuda.Stream | None = None, device: torch.device | int | None = None):
+        from ._lib import check_pairs
+
+        self._check = check_pairs
+        self._lib = load_library()
+        if not torch.cuda.is_available():
+            raise RuntimeError("OnlineDMDPairs needs a CUDA device")
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        self.n, self.r_max = int(n), int(r_max)
+        nbytes = C.c_size_t()
+        check_pairs(self._lib, self._lib.odmd_pairs_footprint(self.n, self.r_max, C.byref(nbytes)))
+        self.footprint = int(nbytes.value)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self.workspace = torch.empty(self.footprint, dtype=torch.uint8, device=self.device)
+            h = C.c_void_p()
+            check_pairs(self._lib, self._lib.odmd_pairs_create(
+                self.n, self.r_max, float(trunc_tol), C.c_void_p(self.workspace.data_ptr()), self.footprint,
+                C.c_void_p(self.stream.cuda_stream), C.byref(h)))
+        self._h = h
+
+    def _vec(self, x: torch.Tensor, name: str) -> torch.Tensor:
+        if not isinstance(x, torch.Tensor) or x.device != self.device:
+            raise ValueError(f"{name} must be a tensor on {self.device}")
+        if x.dtype != torch.float64 or x.numel() != self.n or not x.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous float64 tensor of {self.n} elements")
+        if self.stream != torch.cuda.current_stream(self.device):
+            x.record_stream(self.stream)
+        return x
+
+    def update(self, x: torch.Tensor, y: torch.Tensor) -> None:
+        """odmd_pairs_update: X gains x, Y gains y."""
+        x, y = self._vec(x, "x"), self._vec(y, "y")
+        self._check(self._lib, self._lib.odmd_pairs_update(self._h, C.c_void_p(x.data_ptr()),
+                                                           C.c_void_p(y.data_ptr())), self._h)
+
+    def predict(self, u: torch.Tensor, ts: Sequence[float], out: torch.Tensor | None = None) -> torch.Tensor:
+        """odmd_pairs_predict: row j is L A~^{t_j} L^T u (integer t_j >= 0, at most 64)."""
+        u = self._vec(u, "u")
+        ts = [float(t) for t in ts]
+        k = len(ts)
+        if out is None:
+            out = torch.empty((k, self.n), dtype=torch.float64, device=self.device)
+        if out.shape != (k, self.n) or out.dtype != torch.float64 or not out.is_contiguous():
+            raise ValueError("out must be a contiguous (len(ts), n) float64 tensor")
+        tarr = (C.c_double * max(k, 1))(*ts)
+        self._check(self._lib, self._lib.odmd_pairs_predict(self._h, C.c_void_p(u.data_ptr()), tarr, k,
+                                                            C.c_void_p(out.data_ptr()), self.n), self._h)
+        return out
+
+    def hybrid_step_residual(self, residual, fom, step: int, state: torch.Tensor, nxt: torch.Tensor,
+                             r: torch.Tensor, b: torch.Tensor, tol: float = 0.0) -> tuple[bool, float]:
+        """odmd_pairs_hybrid_step_residual: one step of the FOM-only hybrid loop.  residual(step)
+        fills r and b for the prediction in nxt (state still holds the previous state);
+        fom(step) advances nxt in place from the previous state.  Returns (accepted, relative
+        residual)."""
+        from ._lib import FOM_FN, RESIDUAL_FN
+
+        for t, name in ((state, "state"), (nxt, "next"), (r, "r"), (b, "b")):
+            self._vec(t, name)
+        failure = []
+
+        def _res(user, st, u, rr, bb, stream):
+            try:
+                with torch.cuda.stream(self.stream):
+                    residual(int(st))
+                return 0
+            except Exception as e:
+                failure.append(e)
+                return 1
+
+        def _fom(user, st, u, stream):
+            try:
+                with torch.cuda.stream(self.stream):
+                    fom(int(st))
+                return 0
+            except Exception as e:
+                failure.append(e)
+                return 1
+
+        cres, cfom = RESIDUAL_FN(_res), FOM_FN(_fom)
+        acc, rel = C.c_int32(), C.c_double()
+        st = self._lib.odmd_pairs_hybrid_step_residual(
+            self._h, cres, cfom, None, float(tol), int(step), C.c_void_p(state.data_ptr()),
+            C.c_void_p(nxt.data_ptr()), C.c_void_p(r.data_ptr()), C.c_void_p(b.data_ptr()), C.byref(acc), C.byref(rel))
+        if failure:
+            raise failure[0]
+        self._check(self._lib, st, self._h)
+        return bool(acc.value), float(rel.value)
+
+    def singular_values(self) -> list[float]:
+        buf = (C.c_double * self.r_max)()
+        r = C.c_int32()
+        self._check(self._lib, self._lib.odmd_pairs_get_singular_values(self._h, buf, self.r_max, C.byref(r)),
+                    self._h)
+        return [buf[i] for i in range(r.value)]
+
+    @property
+    def rank(self) -> int:
+        return len(self.singular_values())
+
+    @property
+    def pairs(self) -> int:
+        n = C.c_int64()
+        self._check(self._lib, self._lib.odmd_pairs_get_count(self._h, C.byref(n)), self._h)
+        return int(n.value)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._check(self._lib, self._lib.odmd_pairs_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
