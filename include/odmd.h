@@ -374,6 +374,17 @@ const char* odmd_pairs_last_error(odmd_pairs_t h);
 /* Release the handle (synchronises first); the workspace is the caller's again. */
 odmd_status odmd_pairs_destroy(odmd_pairs_t h);
 
+/* ---------------------------------------------------------------- tensor-core self-test
+ * The paper has no counterpart: a check of the hardware building block under the
+ * split-precision tall x small products (bfloat16 tcgen05.mma into an FP32 accumulator in
+ * tensor memory, canonical K-major shared-memory layout without swizzle).  One CTA forms
+ * D = reps * A B with A 128 x 64 (row-major bfloat16 bits), B given as 64 rows of 64 (row
+ * n holds column n of the 64 x 64 factor) and D 128 x 64 floats, row-major; all three and
+ * the status word are device pointers owned by the caller.  1 <= reps <= 4096.
+ * Synchronises the device.  Errors: ODMD_ERR_ARG, ODMD_ERR_CUDA, ODMD_ERR_TIMEOUT (the
+ * product did not complete within the bounded wait; *status_dev is then nonzero). */
+odmd_status odmd_tc_selftest(const void* a_dev, const void* b_dev, void* d_dev, int32_t* status_dev, int32_t reps);
+
 #ifdef __cplusplus
 }
 #endif
