@@ -270,8 +270,10 @@ odmd_status odmd_hybrid_run(odmd_t h, odmd_residual_fn residual, odmd_fom_fn fom
  *
  * odmd_checkpoint_size: bytes of a checkpoint of this handle (host memory).
  * odmd_save: synchronises, then writes the model's whole state into host_buf (bytes >=
- *   odmd_checkpoint_size): a header (magic, version, n, r_max, precision, slack, snapshot
- *   count, FNV-1a checksum over 8-byte words) followed by the raw device state -- control block, committed
+ *   odmd_checkpoint_size): a header (magic, format version 2, n, r_max, precision, slack,
+ *   snapshot count, indices of the committed buffers, region sizes, and an FNV-1a checksum
+ *   over 8-byte little-endian words of the header with its checksum field zero and then of
+ *   every region) followed by the raw device state -- control block, committed
  *   state buffers with the small scratch, rows 0..n-1 of the tall factor, both snapshot
  *   slots and the stored residual.  The host buffer is the caller's; nothing is kept.
  * odmd_load: restores such a checkpoint into a handle created with the same n, r_max,
@@ -279,7 +281,9 @@ odmd_status odmd_hybrid_run(odmd_t h, odmd_residual_fn residual, odmd_fom_fn fom
  *   a device of the same kind.  Updates, predictions and checks then continue exactly as
  *   they would have in the saved handle.  Errors: ODMD_ERR_ARG for a NULL pointer, a
  *   short or truncated buffer, a foreign or corrupted checkpoint (bad magic, version or
- *   checksum) or a different configuration; ODMD_ERR_CUDA. */
+ *   checksum; buffer indices other than 0 or 1, a negative snapshot count, or a control
+ *   block that disagrees with the header, all refused before anything is copied to the
+ *   device) or a different configuration; ODMD_ERR_CUDA. */
 odmd_status odmd_checkpoint_size(odmd_t h, size_t* bytes);
 odmd_status odmd_save(odmd_t h, void* host_buf, size_t bytes);
 odmd_status odmd_load(odmd_t h, const void* host_buf, size_t bytes);

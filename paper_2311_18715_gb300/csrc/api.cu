@@ -192,19 +192,21 @@ void carve(Ws& ws, const Layout& L, unsigned char* base, const odmd_config& c, i
   ws.stagesA = stages_a((int)c.prec, L.cap);
   ws.tau_h = (float)c.trunc_tol;
   ws.tau_l = (float)(c.trunc_tol - (double)ws.tau_h);
+  ws.tau = c.trunc_tol;
   ws.ctl = reinterpret_cast<Ctl*>(base + L.off_ctl);
   const int qld = L.cap + 1;
   for (int b = 0; b < 2; ++b) {
     StateBuf& s = ws.st[b];
     s.hdr = reinterpret_cast<StateHdr*>(base + L.off_hdr[b]);
     float2* d = reinterpret_cast<float2*>(base + L.off_state[b]);
-    s.S = d;
+    // S, rf, rl, M are doubles: the same 8 bytes per value as a float pair
+    s.S = reinterpret_cast<double*>(d);
     d += L.rmax;
-    s.rf = d;
+    s.rf = reinterpret_cast<double*>(d);
     d += L.rmax;
-    s.rl = d;
+    s.rl = reinterpret_cast<double*>(d);
     d += L.rmax;
-    s.M = d;
+    s.M = reinterpret_cast<double*>(d);
     d += (size_t)L.rmax * L.rmax;
     s.Q = d;
     d += (size_t)qld * L.rmax;
@@ -216,35 +218,37 @@ void carve(Ws& ws, const Layout& L, unsigned char* base, const odmd_config& c, i
   Small& sm = ws.sm;
   sm.red = d;
   d += 2 * L.cap + 3;
-  sm.ac = d;
+  // the core-SVD scratch is doubles (8 bytes per value, like a float pair)
+  auto dbl = [](float2* q) { return reinterpret_cast<double*>(q); };
+  sm.ac = dbl(d);
   d += qld;
-  sm.yext = d;
+  sm.yext = dbl(d);
   d += qld;
-  sm.qn = d;
+  sm.qn = dbl(d);
   d += qld;
-  sm.p = d;
+  sm.p = dbl(d);
   d += kMaxN;
-  sm.w = d;
+  sm.w = dbl(d);
   d += kMaxN;
-  sm.d = d;
+  sm.d = dbl(d);
   d += kMaxN;
-  sm.z = d;
+  sm.z = dbl(d);
   d += kMaxN;
-  sm.dc = d;
+  sm.dc = dbl(d);
   d += kMaxN;
-  sm.rot_c = d;
+  sm.rot_c = dbl(d);
   d += kMaxN;
-  sm.rot_s = d;
+  sm.rot_s = dbl(d);
   d += kMaxN;
-  sm.mu = d;
+  sm.mu = dbl(d);
   d += kMaxN;
-  sm.zhat = d;
+  sm.zhat = dbl(d);
   d += kMaxN;
-  sm.sig = d;
+  sm.sig = dbl(d);
   d += 2 * kMaxN;
-  sm.U = d;
+  sm.U = dbl(d);
   d += (size_t)kMaxN * kMaxN;
-  sm.V = d;
+  sm.V = dbl(d);
   d += (size_t)kMaxN * kMaxN;
   sm.QB = d;
   d += (size_t)qld * L.rmax;
@@ -606,6 +610,7 @@ odmd_status odmd_create(const odmd_config* cfg, void* workspace_dev, size_t byte
   }
   if (e == cudaSuccess) e = prepare_tall(h->ws);
   if (e == cudaSuccess) e = prepare_small(h->ws);
+  if (e == cudaSuccess) e = prepare_core();
   if (e == cudaSuccess && cfg->refine_every > 0) e = prepare_refine();
   if (e == cudaSuccess) e = cudaMemsetAsync(workspace_dev, 0, L.total, h->stream);
   if (e == cudaSuccess) {
@@ -793,8 +798,10 @@ struct CkptHeader {
   int64_t nsnap;
   int32_t cur_h, curc_h;
   uint64_t region[6];  // bytes: control block, state block, L0 hi rows, L0 lo rows, snapshots, residual
-  uint64_t checksum;   // FNV-1a (8-byte words) over the regions
+  uint64_t checksum;   // FNV-1a (8-byte words) over this header (checksum field zero), then the regions
 };
+// version 2: the small state (S, rows of R, M) is FP64 and the header is covered by the checksum
+constexpr uint32_t kCkptVersion = 2;
 constexpr char kCkptMagic[8] = {'O', 'D', 'M', 'D', 'C', 'K', 'P', '1'};
 
 struct CkptRegion {
@@ -859,7 +866,7 @@ odmd_status odmd_save(odmd_t h, void* host_buf, size_t bytes) {
   const Layout L = make_layout(h->cfg);
   CkptHeader hd{};
   std::memcpy(hd.magic, kCkptMagic, 8);
-  hd.version = 1;
+  hd.version = kCkptVersion;
   hd.header_bytes = sizeof(CkptHeader);
   hd.n = h->cfg.n;
   hd.r_max = h->cfg.r_max;
@@ -879,7 +886,8 @@ odmd_status odmd_save(odmd_t h, void* host_buf, size_t bytes) {
   hd.region[5] = R[6].bytes;
   unsigned char* out = static_cast<unsigned char*>(host_buf) + sizeof(CkptHeader);
   const unsigned char* base = reinterpret_cast<const unsigned char*>(h->ws.ctl) - L.off_ctl;  // workspace start
-  uint64_t hsh = 1469598103934665603ull;
+  hd.checksum = 0;
+  uint64_t hsh = fnv1a(1469598103934665603ull, reinterpret_cast<const unsigned char*>(&hd), sizeof hd);
   for (const CkptRegion& r : R) {
     if (r.bytes) CK(h, cudaMemcpy(out, base + r.off, r.bytes, cudaMemcpyDeviceToHost), "save: copy");
     hsh = fnv1a(hsh, out, r.bytes);
@@ -896,8 +904,11 @@ odmd_status odmd_load(odmd_t h, const void* host_buf, size_t bytes) {
   if (bytes < sizeof(CkptHeader)) return fail(h, ODMD_ERR_ARG, "checkpoint shorter than its header");
   CkptHeader hd;
   std::memcpy(&hd, host_buf, sizeof hd);
-  if (std::memcmp(hd.magic, kCkptMagic, 8) != 0 || hd.version != 1 || hd.header_bytes != sizeof(CkptHeader))
+  if (std::memcmp(hd.magic, kCkptMagic, 8) != 0 || hd.version != kCkptVersion || hd.header_bytes != sizeof(CkptHeader))
     return fail(h, ODMD_ERR_ARG, "not a checkpoint of this library version");
+  // the scalars that select buffers are checked before anything else uses them
+  if ((hd.cur_h != 0 && hd.cur_h != 1) || (hd.curc_h != 0 && hd.curc_h != 1) || hd.nsnap < 0)
+    return fail(h, ODMD_ERR_ARG, "checkpoint header out of range (buffer indices or snapshot count)");
   const Layout L = make_layout(h->cfg);
   if (hd.n != h->cfg.n || hd.r_max != h->cfg.r_max || hd.prec != h->cfg.prec || hd.slack != h->cfg.slack ||
       hd.cap != L.cap || hd.ldg != L.ldg || hd.ctl_bytes != (int32_t)sizeof(Ctl))
@@ -909,7 +920,9 @@ odmd_status odmd_load(odmd_t h, const void* host_buf, size_t bytes) {
       hd.region[3] != R[3].bytes || hd.region[4] != R[4].bytes + R[5].bytes || hd.region[5] != R[6].bytes)
     return fail(h, ODMD_ERR_ARG, "checkpoint regions do not match this handle's layout");
   const unsigned char* in = static_cast<const unsigned char*>(host_buf) + sizeof(CkptHeader);
-  uint64_t hsh = 1469598103934665603ull;
+  CkptHeader hz = hd;
+  hz.checksum = 0;
+  uint64_t hsh = fnv1a(1469598103934665603ull, reinterpret_cast<const unsigned char*>(&hz), sizeof hz);
   {
     const unsigned char* p = in;
     for (const CkptRegion& r : R) {
@@ -918,6 +931,12 @@ odmd_status odmd_load(odmd_t h, const void* host_buf, size_t bytes) {
     }
   }
   if (hsh != hd.checksum) return fail(h, ODMD_ERR_ARG, "checkpoint checksum mismatch (corrupted data)");
+  {
+    Ctl saved;
+    std::memcpy(&saved, in, sizeof saved);  // region 0 is the control block
+    if (saved.cur != hd.cur_h || saved.cur_c != hd.curc_h)
+      return fail(h, ODMD_ERR_ARG, "checkpoint control block disagrees with its header");
+  }
   CK(h, cudaStreamSynchronize(h->stream), "load: sync");
   unsigned char* base = reinterpret_cast<unsigned char*>(h->ws.ctl) - L.off_ctl;
   for (const CkptRegion& r : R) {
@@ -1178,9 +1197,7 @@ odmd_status odmd_get_singular_values(odmd_t h, double* s_host, int32_t cap, int3
   *r = hdr.r;
   const int nc = hdr.r < cap ? hdr.r : cap;
   if (nc > 0) {
-    float2 buf[kMaxR];
-    CK(h, cudaMemcpy(buf, h->ws.st[h->cur_h].S, nc * sizeof(float2), cudaMemcpyDeviceToHost), "S read");
-    for (int i = 0; i < nc; ++i) s_host[i] = join(buf[i]);
+    CK(h, cudaMemcpy(s_host, h->ws.st[h->cur_h].S, nc * sizeof(double), cudaMemcpyDeviceToHost), "S read");
   }
   return ODMD_OK;
 }

@@ -1,0 +1,798 @@
+// Small solves of the online DMD update in FP64 (Sec. 2.3: Brand's rank-1 append, kept in
+// product form L = L0 Q).  These steps decide which directions of the snapshot stream
+// survive truncation, and the reduced operator they update is carried from one snapshot to
+// the next, so rounding here feeds back into every later model; they run in IEEE double.
+// The tall passes hand over their reductions as double-float pairs (exact in double).
+//
+//   k_prep     reduced tall sums -> projections p = L^T c, w = L^T x, the new direction,
+//              the core matrix K = [[diag(S), p], [0, rho]] and its deflated secular problem
+//   k_roots    one CTA per singular value of K: root of the secular equation
+//   k_zhat     one CTA per pole: Loewner weights; one extra CTA orders the values
+//   k_vectors  one CTA per kept singular pair: left/right singular vectors of K
+//   k_apply    one CTA per kept column: M' = U'^T B V', Q' = [Q 0; 0 q] U', rows of R
+//
+// Core SVD.  K K^T = D^2 + z z^T with D = diag(S, 0) and z = [p; rho], so sigma'^2 are the
+// roots of 1 + sum_i z_i^2 / (d_i^2 - lambda) = 0 and, with z-hat from Loewner's formula,
+// u ~ (D^2 - lambda)^{-1} z-hat and v ~ (d_i z-hat_i / (d_i^2 - lambda), -1): the
+// broken-arrow SVD of Gu and Eisenstat (SIAM J. Matrix Anal. Appl. 16, 1995).  Every
+// difference d_i^2 - lambda is formed as (d_i - d_o)(d_i + d_o) - mu with lambda = d_o^2 +
+// mu and d_o the nearer pole.  Negligible z_i and nearly equal d_i are deflated first (a
+// Givens rotation merges the weights of two equal poles).  K is scaled by a power of two so
+// that its largest entry lies in [1/2, 1).
+//
+// GB300 issues FP64 arithmetic at 1/64 of its FP32 rate, so each root is first located by
+// FP32 iterations (to ~1e-7) and then refined with the secular function in FP64 and an
+// FP32 two-pole model step for the correction (Newton-like convergence to FP64 accuracy);
+// the sums over poles are spread over the threads of the CTA.
+#include "dd.cuh"
+#include "odmd_internal.cuh"
+
+namespace odmd {
+
+constexpr double kEps64 = 2.220446049250313e-16;  // 2^-52, a safe bound on the unit roundoff
+
+__device__ __forceinline__ double group4_sum_d(double a) {
+  a += __shfl_xor_sync(0xffffffffu, a, 1);
+  return a + __shfl_xor_sync(0xffffffffu, a, 2);
+}
+__device__ __forceinline__ double warp_max_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+// nonnegative doubles order like their bit patterns read as integers
+__device__ __forceinline__ long long ord_key(double v) { return __double_as_longlong(v); }
+
+// ---------------------------------------------------------------------------------------
+// k_prep
+// ---------------------------------------------------------------------------------------
+constexpr int kPrepThreads = 256;
+
+__global__ void __launch_bounds__(kPrepThreads) k_prep(Ws ws) {
+  pdl_wait();
+  extern __shared__ __align__(16) double psm[];
+  Ctl* ctl = ws.ctl;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int cur = ctl->cur;
+  const StateBuf st = ws.st[cur];
+  const int r = st.hdr->r, r0 = st.hdr->r0, qld = ws.cap + 1;
+  double* sQ = psm;  // r columns of Q, ld qld
+  double* ac = sQ + (size_t)qld * kMaxR;
+  double* yx = ac + qld;
+  double* z = yx + qld;
+  double* p = z + qld;
+  double* p2 = p + kMaxN;
+  __shared__ double red8[16];
+  __shared__ double thr_s;
+  __shared__ int append_s;
+  __shared__ double dsc[kMaxN], zsc[kMaxN];
+  __shared__ int defl[kMaxN];
+  const float2* red = ws.sm.red;
+
+  for (int idx = tid; idx < r * qld; idx += kPrepThreads) sQ[idx] = dd2d(st.Q[idx]);
+  for (int i = tid; i < r0; i += kPrepThreads) {
+    ac[i] = dd2d(st.a[i]) + dd2d(red[i]);
+    yx[i] = dd2d(red[r0 + i]);
+  }
+  __syncthreads();
+  // p = Q^T ac and w = Q^T y (4 threads per column j < r; Q has r0 rows, the appended
+  // coordinate lies outside span(L)); a warp without column work meanwhile decides whether
+  // the residual is appended (rho0 against the truncation threshold)
+  {
+    const int j = tid >> 2, sub = tid & 3;
+    double ap = 0.0, aw = 0.0;
+    if (j < r)
+      for (int i = sub; i < r0; i += 4) {
+        const double q = sQ[(size_t)j * qld + i];
+        ap = fma(q, ac[i], ap);
+        aw = fma(q, yx[i], aw);
+      }
+    ap = group4_sum_d(ap);
+    aw = group4_sum_d(aw);
+    if (j < r && sub == 0) {
+      p[j] = ap;
+      ws.sm.w[j] = aw;
+    }
+  }
+  const int dwarp = 4 * r <= kPrepThreads - 32 ? 7 : 0;
+  if (warp == dwarp) {
+    double ssq = 0.0, sy = 0.0;
+    for (int i = lane; i < r0; i += 32) {
+      const double si = dd2d(red[i]);
+      ssq = fma(si, si, ssq);
+      sy = fma(si, dd2d(red[r0 + i]), sy);
+    }
+    ssq = warp_sum_d(ssq);
+    sy = warp_sum_d(sy);
+    if (lane == 0) {
+      const double eta = dd2d(red[2 * r0]), ex = dd2d(red[2 * r0 + 1]);
+      const double rho0 = sqrt(fmax(eta - ssq, 0.0));
+      const double cn = sqrt(dd2d(st.hdr->cn2));
+      const double sig1 = r > 0 ? st.S[0] : 0.0;
+      const double thr = ws.tau * fmax(sig1, cn);
+      const int append = rho0 > thr ? 1 : 0;
+      ctl->thr = thr;
+      ctl->rho0 = rho0;
+      ctl->append = append;
+      ctl->r0e = r0 + append;
+      if (append) {
+        ac[r0] = rho0;
+        yx[r0] = (ex - sy) / rho0;
+      }
+      append_s = append;
+      thr_s = thr;
+    }
+  }
+  __syncthreads();
+  const int append = append_s;
+  const int r0e = r0 + append;
+  const double thr = thr_s;
+  // z = ac - Q p (rows < r0; the appended coordinate is ac itself)
+  for (int base = 0; base < 4 * r0e; base += kPrepThreads) {
+    const int i = (base + tid) >> 2, sub = tid & 3;
+    double acc = 0.0;
+    if (i < r0)
+      for (int j = sub; j < r; j += 4) acc = fma(sQ[(size_t)j * qld + i], p[j], acc);
+    acc = group4_sum_d(acc);
+    if (i < r0e && sub == 0) z[i] = i < r0 ? ac[i] - acc : ac[i];
+  }
+  __syncthreads();
+  // second Gram-Schmidt pass in the small space: p2 = Q^T z, z -= Q p2, p += p2
+  {
+    const int j = tid >> 2, sub = tid & 3;
+    double acc = 0.0;
+    if (j < r)
+      for (int i = sub; i < r0; i += 4) acc = fma(sQ[(size_t)j * qld + i], z[i], acc);
+    acc = group4_sum_d(acc);
+    if (j < r && sub == 0) p2[j] = acc;
+  }
+  __syncthreads();
+  for (int base = 0; base < 4 * r0; base += kPrepThreads) {
+    const int i = (base + tid) >> 2, sub = tid & 3;
+    double acc = 0.0;
+    if (i < r0)
+      for (int j = sub; j < r; j += 4) acc = fma(sQ[(size_t)j * qld + i], p2[j], acc);
+    acc = group4_sum_d(acc);
+    if (i < r0 && sub == 0) z[i] -= acc;
+  }
+  for (int j = tid; j < r; j += kPrepThreads) {
+    p[j] += p2[j];
+    ws.sm.p[j] = p[j];
+  }
+  __syncthreads();
+  // ||z||^2 and z . y in one block reduction; rho = ||z||, gamma = q_n . y = (z . y) / rho
+  double zz = 0.0, zy = 0.0;
+  for (int i = tid; i < r0e; i += kPrepThreads) {
+    zz = fma(z[i], z[i], zz);
+    zy = fma(z[i], yx[i], zy);
+  }
+  zz = warp_sum_d(zz);
+  zy = warp_sum_d(zy);
+  if (lane == 0) {
+    red8[warp] = zz;
+    red8[8 + warp] = zy;
+  }
+  __syncthreads();
+  zz = 0.0;
+  zy = 0.0;
+  for (int w8 = 0; w8 < 8; ++w8) {
+    zz += red8[w8];
+    zy += red8[8 + w8];
+  }
+  double rho = sqrt(zz);
+  if (!(rho > thr)) rho = 0.0;
+  const double inv_rho = rho > 0.0 ? 1.0 / rho : 0.0;
+  for (int i = tid; i < r0e; i += kPrepThreads) {
+    ws.sm.qn[i] = z[i] * inv_rho;
+    ws.sm.yext[i] = yx[i];
+    if (i < r0) ws.sm.ac[i] = ac[i];
+  }
+  if (tid == 0) {
+    ctl->rho = rho;
+    ctl->gamma = zy * inv_rho;
+  }
+  // ---- secular problem of K = [[diag(S), p], [0, rho]], n = r + 1, scaled to max < 1
+  if (warp == 0) {
+    const int n = r + 1;
+    double mx = 0.0;
+    for (int i = lane; i < n; i += 32) {
+      mx = fmax(mx, fabs(i < r ? p[i] : rho));
+      if (i == 0 && r > 0) mx = fmax(mx, st.S[0]);
+    }
+    mx = warp_max_d(mx);
+    int e = 0;
+    if (mx > 0.0) frexp(mx, &e);
+    const double tol = 8.0 * kEps64;  // in scaled units
+    for (int i = lane; i < n; i += 32) {
+      const double di = i < r ? ldexp(st.S[i], -e) : 0.0;
+      const double zi = ldexp(i < r ? p[i] : rho, -e);
+      dsc[i] = di;
+      const bool small = !(fabs(zi) > tol);
+      zsc[i] = small ? 0.0 : zi;
+      defl[i] = small ? 1 : 0;
+      ws.sm.dc[i] = di;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      // merge nearly equal poles (the pole at 0, coordinate r, is never merged)
+      int nrot = 0, last = -1;
+      for (int i = 0; i < r; ++i) {
+        if (defl[i]) continue;
+        if (last >= 0 && dsc[last] - dsc[i] <= tol) {
+          const double zl = zsc[last], zi = zsc[i];
+          const double h = sqrt(zl * zl + zi * zi);
+          ws.sm.rot_i[nrot] = last;
+          ws.sm.rot_j[nrot] = i;
+          ws.sm.rot_c[nrot] = zl / h;
+          ws.sm.rot_s[nrot] = zi / h;
+          ++nrot;
+          zsc[last] = h;
+          zsc[i] = 0.0;
+          defl[i] = 1;
+        } else {
+          last = i;
+        }
+      }
+      int m = 0, nd = 0;
+      for (int i = n - 1; i >= 0; --i) {  // ascending poles
+        if (defl[i]) {
+          ws.sm.defl[nd++] = i;
+        } else {
+          ws.sm.pole[m] = i;
+          ws.sm.d[m] = dsc[i];
+          ws.sm.z[m] = zsc[i];
+          ++m;
+        }
+      }
+      ctl->n = n;
+      ctl->m = m;
+      ctl->ndefl = nd;
+      ctl->nrot = nrot;
+      ctl->scale_exp = e;
+      if (!isfinite(rho) || !isfinite(mx)) atomicOr(&ctl->status, DEV_NONFINITE);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// k_roots: root j of 1 + sum_i z_i^2/(d_i^2 - lambda) = 0 in (d_j^2, d_{j+1}^2)
+// ---------------------------------------------------------------------------------------
+constexpr int kRootThreads = 128;  // >= kMaxN: one pole per thread in the FP64 sums
+static_assert(kRootThreads >= kMaxN, "one pole per thread");
+
+// block sums of four values; every thread gets the same results (fixed order)
+__device__ __forceinline__ void block_sum4(double (&v)[4], double (*part)[4]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) v[k] = warp_sum_d(v[k]);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) part[warp][k] = v[k];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    double s = part[0][k];
+    for (int w = 1; w < kRootThreads / 32; ++w) s += part[w][k];
+    v[k] = s;
+  }
+}
+
+__global__ void __launch_bounds__(kRootThreads) k_roots(Ws ws) {
+  pdl_wait();
+  Ctl* ctl = ws.ctl;
+  const int m = ctl->m;
+  const int j = blockIdx.x;
+  if (j >= m) return;
+  const double* d = ws.sm.d;
+  const double* z = ws.sm.z;
+  const int tid = threadIdx.x, lane = tid & 31;
+  __shared__ float df[kMaxN], zf[kMaxN];
+  __shared__ double part[2][kRootThreads / 32][4];
+  const bool mine = tid < m;
+  const double di = mine ? d[tid] : 0.0, zi = mine ? z[tid] : 0.0;
+  if (mine) {
+    df[tid] = __double2float_rn(di);
+    zf[tid] = __double2float_rn(zi);
+  }
+  double zs[4] = {zi * zi, 0.0, 0.0, 0.0};
+  block_sum4(zs, part[0]);  // also publishes df, zf
+  const double zsq = zs[0];
+  if (m == 1) {
+    if (tid == 0) {
+      ws.sm.org[0] = 0;
+      ws.sm.mu[0] = zsq;
+      ws.sm.sig[0] = sqrt(d[0] * d[0] + zsq);
+    }
+    return;
+  }
+  int o;
+  double lo, hi, A, B;  // bracket of mu and the neighbouring poles, relative to d_o^2
+  const bool last = (j == m - 1);
+  int it_total = 1;  // parity of the partial-sum buffer in use
+  if (!last) {
+    const double dj = d[j], dj1 = d[j + 1];
+    const double gap = (dj1 - dj) * (dj1 + dj);
+    const double mid = gap * 0.5;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    if (mine) {
+      const double t = zi / ((di - dj) * (di + dj) - mid);
+      v[0] = zi * t;
+    }
+    block_sum4(v, part[it_total & 1]);
+    ++it_total;
+    if (1.0 + v[0] >= 0.0) {
+      o = j;
+      lo = 0.0;
+      hi = mid;
+      A = 0.0;
+      B = gap;
+    } else {
+      o = j + 1;
+      lo = -mid;
+      hi = 0.0;
+      A = -gap;
+      B = 0.0;
+    }
+  } else {
+    o = j;
+    lo = 0.0;
+    hi = zsq;
+    A = 0.0;
+    B = 0.0;
+  }
+  const double dob = d[o];
+  // ---- stage 1, FP32: locate the root to ~1e-7 relative (every warp the same way)
+  double mu = 0.5 * (lo + hi);
+  {
+    const float dof = df[o];
+    const float Af = (float)A, Bf = (float)B;
+    float lof = (float)lo, hif = (float)hi, muf = (float)mu;
+    for (int it = 0; it < 40; ++it) {
+      float psi = 0.f, dpsi = 0.f, phi = 0.f, dphi = 0.f;
+#pragma unroll
+      for (int q_ = 0; q_ < (kMaxN + 31) / 32; ++q_) {
+        const int i = lane + 32 * q_;
+        if (i >= m) break;
+        const float dv = df[i], zv = zf[i];
+        const float del = (dv - dof) * (dv + dof) - muf;
+        const float t = zv / del;
+        if (i <= j) {
+          psi = fmaf(zv, t, psi);
+          dpsi = fmaf(t, t, dpsi);
+        } else {
+          phi = fmaf(zv, t, phi);
+          dphi = fmaf(t, t, dphi);
+        }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        psi += __shfl_xor_sync(0xffffffffu, psi, off);
+        dpsi += __shfl_xor_sync(0xffffffffu, dpsi, off);
+        phi += __shfl_xor_sync(0xffffffffu, phi, off);
+        dphi += __shfl_xor_sync(0xffffffffu, dphi, off);
+      }
+      const float f = 1.f + psi + phi;
+      if (f < 0.f)
+        lof = muf;
+      else
+        hif = muf;
+      if (fabsf(f) <= 16.f * 6e-8f * (1.f + fabsf(psi) + fabsf(phi))) break;
+      const float Am = Af - muf, c1 = dpsi * Am * Am, a1 = psi - dpsi * Am;
+      float x;
+      if (!last) {
+        const float Bm = Bf - muf, c2 = dphi * Bm * Bm, a2 = phi - dphi * Bm;
+        const float C = 1.f + a1 + a2;
+        const float qb = -(C * (Af + Bf) + c1 + c2), qc = C * Af * Bf + c1 * Bf + c2 * Af;
+        if (fabsf(C) <= 1e-7f * (fabsf(qb) + fabsf(qc))) {
+          x = -qc / qb;
+        } else {
+          const float sq = sqrtf(fmaxf(qb * qb - 4.f * C * qc, 0.f));
+          const float q = -0.5f * (qb >= 0.f ? qb + sq : qb - sq);
+          const float x1 = q / C, x2 = qc / q;
+          const bool in1 = x1 > lof && x1 < hif, in2 = x2 > lof && x2 < hif;
+          x = in1 && !in2 ? x1 : (in2 && !in1 ? x2 : (fabsf(x1 - muf) < fabsf(x2 - muf) ? x1 : x2));
+        }
+      } else {
+        const float C = 1.f + a1 + phi;
+        x = C > 0.f ? Af + c1 / C : 0.5f * (lof + hif);
+      }
+      if (!(x > lof && x < hif)) x = 0.5f * (lof + hif);
+      const float step = fabsf(x - muf);
+      muf = x;
+      if (step <= 4e-7f * fabsf(muf) || hif - lof <= 4e-7f * fmaxf(fabsf(lof), fabsf(hif))) break;
+    }
+    // FP32 cannot resolve poles closer than ~1e-7 relative: keep its root only when it is
+    // finite and strictly inside the FP64 bracket
+    const double cand = (double)muf;
+    if (isfinite(muf) && cand > lo && cand < hi) mu = cand;
+  }
+  // ---- stage 2: f in FP64 (one pole per thread), the model step in FP32 for the
+  // correction delta = x - mu (shifted poles A - mu, B - mu), applied to the FP64 mu
+  const double ddo = mine ? (di - dob) * (di + dob) : 0.0;  // d_i^2 - d_o^2
+  bool conv = false;
+  for (int it = 0; it < 100; ++it, ++it_total) {
+    double v[4] = {0.0, 0.0, 0.0, 0.0};  // psi, phi, psi', phi'
+    if (mine) {
+      const double t = zi / (ddo - mu);
+      const double term = zi * t, dterm = t * t;
+      if (tid <= j) {
+        v[0] = term;
+        v[2] = dterm;
+      } else {
+        v[1] = term;
+        v[3] = dterm;
+      }
+    }
+    block_sum4(v, part[it_total & 1]);
+    const double psi = v[0], phi = v[1];
+    const double f = 1.0 + psi + phi;
+    if (f < 0.0)
+      lo = mu;
+    else
+      hi = mu;
+    if (fabs(f) <= 8.0 * kEps64 * (double)m * (1.0 + fabs(psi) + fabs(phi))) {
+      conv = true;
+      break;
+    }
+    // two-pole model written around mu with f explicit:  f + psi' a d/(a - d) + phi' b d/(b
+    // - d) = 0, neighbouring poles at a = A - mu and b = B - mu, unknown d = x - mu, scaled
+    // by a power of two so that the FP32 coefficients stay inside the exponent range
+    const float fh = (float)f;
+    const float a = (float)(A - mu);
+    const float b = last ? 0.f : (float)(B - mu);
+    int ex = 0;
+    frexpf(fmaxf(fabsf(a), fabsf(b)), &ex);
+    const float sc = ldexpf(1.f, ex), as = ldexpf(a, -ex), bs = ldexpf(b, -ex);
+    const float ps = (float)v[2] * sc, hs = (float)v[3] * sc;
+    float delta;
+    if (!last) {
+      const float Qa = fh - ps * as - hs * bs;
+      const float Qb = as * bs * (ps + hs) - fh * (as + bs);
+      const float Qc = fh * as * bs;
+      const float disc = fmaxf(Qb * Qb - 4.f * Qa * Qc, 0.f);
+      const float q = -0.5f * (Qb >= 0.f ? Qb + sqrtf(disc) : Qb - sqrtf(disc));
+      const float d2 = q != 0.f ? Qc / q : 0.f;  // the root that tends to -f / f'
+      const float d1 = Qa != 0.f ? q / Qa : d2;
+      const float lo_s = ldexpf((float)(lo - mu), -ex), hi_s = ldexpf((float)(hi - mu), -ex);
+      const bool in2 = d2 > lo_s && d2 < hi_s, in1 = d1 > lo_s && d1 < hi_s;
+      delta = ldexpf(in2 ? d2 : (in1 ? d1 : d2), ex);
+    } else {
+      const float den = fh - ps * as;
+      delta = den != 0.f ? ldexpf(fh * as / den, ex) : 0.f;
+    }
+    double x = mu + (double)delta;
+    if (!isfinite(delta) || !(x > lo && x < hi)) x = 0.5 * (lo + hi);
+    const double step = fabs(x - mu);
+    mu = x;
+    if (step <= 4.0 * kEps64 * fabs(mu) || hi - lo <= 4.0 * kEps64 * fmax(fabs(lo), fabs(hi))) {
+      conv = true;
+      break;
+    }
+  }
+  if (tid == 0) {
+    if (!conv) atomicOr(&ctl->status, DEV_SECULAR);
+    ws.sm.org[j] = o;
+    ws.sm.mu[j] = mu;
+    ws.sm.sig[j] = sqrt(fmax(dob * dob + mu, 0.0));
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// k_zhat: Loewner weights z^_i^2 = prod_k (lambda_k - d_i^2) / prod_{k != i} (d_k^2 - d_i^2),
+// paired so every factor is O(1).  Block kMaxN orders all singular values of K.
+// ---------------------------------------------------------------------------------------
+constexpr int kZhatThreads = 64;
+
+__global__ void __launch_bounds__(kZhatThreads) k_zhat(Ws ws) {
+  pdl_wait();
+  Ctl* ctl = ws.ctl;
+  const int m = ctl->m;
+  const int tid = threadIdx.x;
+  if (blockIdx.x == kMaxN) {
+    // order roots (sig[0..m)) and deflated values (scaled diagonal at defl[k]), descending;
+    // every value is >= 0, so its bit pattern orders it
+    const int nd = ctl->ndefl;
+    __shared__ double val[kMaxN];
+    __shared__ long long key[kMaxN];
+    __shared__ int code[kMaxN];
+    const int tot = m + nd;
+    for (int e = tid; e < tot; e += kZhatThreads) {
+      double v;
+      if (e < m) {
+        v = ws.sm.sig[e];
+        code[e] = e;
+      } else {
+        const int c = ws.sm.defl[e - m];
+        v = ws.sm.dc[c];
+        code[e] = -c - 1;
+      }
+      val[e] = v;
+      key[e] = ord_key(v);
+    }
+    __syncthreads();
+    long long kmax = 0;
+    for (int e = 0; e < tot; ++e) kmax = max(kmax, key[e]);
+    const double vmax = __longlong_as_double(kmax);
+    const long long kcut = ord_key(ws.tau * vmax);
+    for (int e = tid; e < tot; e += kZhatThreads) {
+      int pos = 0;
+      const long long ke = key[e];
+      for (int f = 0; f < tot; ++f) pos += key[f] > ke || (key[f] == ke && f < e);
+      ws.sm.src[pos] = code[e];
+      ws.sm.sig[kMaxN + pos] = val[e];
+    }
+    if (tid == 0) {
+      int keep = 0;
+      if (vmax > 0.0)
+        for (int e = 0; e < tot; ++e) keep += key[e] > kcut;
+      ctl->rnew = min(keep, ws.rmax);
+    }
+    return;
+  }
+  const int i = blockIdx.x;
+  if (i >= m) return;
+  const double* d = ws.sm.d;
+  const double di = d[i];
+  double prod = 1.0;
+  for (int k = tid; k < m; k += kZhatThreads) {
+    const double dko = d[ws.sm.org[k]];
+    const double lam_m_di = ws.sm.mu[k] - (di - dko) * (di + dko);  // lambda_k - d_i^2
+    double f;
+    if (k == m - 1) {
+      f = lam_m_di;
+    } else {
+      const double dk = d[k < i ? k : k + 1];
+      f = lam_m_di / ((dk - di) * (dk + di));
+    }
+    prod *= f;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) prod *= __shfl_xor_sync(0xffffffffu, prod, off);
+  __shared__ double wp[kZhatThreads / 32];
+  if ((tid & 31) == 0) wp[tid >> 5] = prod;
+  __syncthreads();
+  if (tid == 0) {
+    double pr = wp[0];
+    for (int w = 1; w < kZhatThreads / 32; ++w) pr *= wp[w];
+    double zh = sqrt(pr > 0.0 ? pr : 0.0);
+    if (ws.sm.z[i] < 0.0) zh = -zh;
+    ws.sm.zhat[i] = zh;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// k_vectors: kept column j -> u_j, v_j (core coordinates 0..r; r is the p/rho column)
+// ---------------------------------------------------------------------------------------
+constexpr int kVecThreads = 64;
+
+__global__ void __launch_bounds__(kVecThreads) k_vectors(Ws ws) {
+  pdl_wait();
+  Ctl* ctl = ws.ctl;
+  const int j = blockIdx.x;
+  if (j >= ctl->rnew) return;
+  const int n = ctl->n, m = ctl->m, r = n - 1;
+  const int tid = threadIdx.x;
+  __shared__ double u[kMaxN], v[kMaxN], red[4];
+  for (int i = tid; i < n; i += kVecThreads) {
+    u[i] = 0.0;
+    v[i] = 0.0;
+  }
+  __syncthreads();
+  const int code = ws.sm.src[j];
+  if (code >= 0) {
+    const double* d = ws.sm.d;
+    const double dob = d[ws.sm.org[code]];
+    const double mu = ws.sm.mu[code];
+    for (int i = tid; i < m; i += kVecThreads) {
+      const double di = d[i];
+      const double ui = ws.sm.zhat[i] / ((di - dob) * (di + dob) - mu);  // z^_i / (d_i^2 - lambda)
+      const int c = ws.sm.pole[i];
+      u[c] = ui;
+      if (c < r) v[c] = di * ui;
+    }
+    __syncthreads();
+    if (tid == 0) v[r] = -1.0;
+    __syncthreads();
+    double su = 0.0, sv = 0.0;
+    for (int i = tid; i < n; i += kVecThreads) {
+      su = fma(u[i], u[i], su);
+      sv = fma(v[i], v[i], sv);
+    }
+    su = warp_sum_d(su);
+    sv = warp_sum_d(sv);
+    if ((tid & 31) == 0) {
+      red[(tid >> 5) * 2] = su;
+      red[(tid >> 5) * 2 + 1] = sv;
+    }
+    __syncthreads();
+    const double iu = 1.0 / sqrt(red[0] + red[2]);
+    const double iv = 1.0 / sqrt(red[1] + red[3]);
+    __syncthreads();
+    for (int i = tid; i < n; i += kVecThreads) {
+      u[i] *= iu;
+      v[i] *= iv;
+    }
+  } else if (tid == 0) {
+    const int c = -code - 1;
+    u[c] = 1.0;
+    v[c] = 1.0;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int t = ctl->nrot - 1; t >= 0; --t) {
+      const int a = ws.sm.rot_i[t], b = ws.sm.rot_j[t];
+      const double c = ws.sm.rot_c[t], s = ws.sm.rot_s[t];
+      const double ua = u[a], ub = u[b], va = v[a], vb = v[b];
+      u[a] = c * ua - s * ub;
+      u[b] = s * ua + c * ub;
+      v[a] = c * va - s * vb;
+      v[b] = s * va + c * vb;
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < n; i += kVecThreads) {
+    ws.sm.U[(size_t)j * kMaxN + i] = u[i];
+    ws.sm.V[(size_t)j * kMaxN + i] = v[i];
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// k_apply: column j of the new small state (written to the other state buffer)
+//   M'    = U'^T [[M, w], [rho r_last^T, gamma]] V'
+//   Q'    = [[Q, q_n(0:r0)], [0, q_n(r0)]] U'     (rows: L0 coordinates incl. the append)
+//   r_first' = [r_first, 0] V'  (= last row of V' when c is u^0),  r_last' = V'[r, :]
+//   S' = sigma'[0:rnew] (unscaled);  a' = L0'^T x
+// ---------------------------------------------------------------------------------------
+constexpr int kApplyThreads = 256;
+
+__device__ __forceinline__ int count4(int sub, int n) { return n > sub ? (n - sub + 3) >> 2 : 0; }
+
+__device__ void apply_column(const Ws& ws, int j, const StateBuf& st, const StateBuf& nx, int r, int r0, int r0e,
+                             bool compact);
+
+__global__ void __launch_bounds__(kApplyThreads) k_apply(Ws ws) {
+  pdl_wait();
+  Ctl* ctl = ws.ctl;
+  const int j = blockIdx.x;
+  const int rnew = ctl->rnew;
+  const int tid = threadIdx.x;
+  const int cur = ctl->cur;
+  const StateBuf st = ws.st[cur], nx = ws.st[cur ^ 1];
+  const int r = st.hdr->r, r0 = st.hdr->r0;
+  const int r0e = ctl->r0e;
+  const int cap = ws.cap;
+  const bool compact = r0e > cap;
+  const int append = ctl->append;
+  if (j == 0 && tid == 0) {
+    nx.hdr->r = rnew;
+    nx.hdr->r0 = compact ? rnew : r0e;
+    nx.hdr->pairs = st.hdr->pairs + 1;
+    nx.hdr->compactions = st.hdr->compactions + (compact ? 1 : 0);
+    nx.hdr->cn2 = ws.sm.red[2 * r0 + 2];
+    // an appended column is formed by the next tall pass (compaction forms it at once)
+    nx.hdr->pend = (append && !compact) ? 1 : 0;
+    nx.hdr->pinv = append ? d2f2(1.0 / ctl->rho0) : make_float2(0.f, 0.f);
+    ctl->mode = compact ? PB_COMPACT : (append ? PB_APPEND : PB_NONE);
+  }
+  if (j == 0) {
+    if (!compact)
+      for (int i = tid; i < r0e; i += kApplyThreads) nx.a[i] = d2f2(ws.sm.yext[i]);
+    if (append && !compact)
+      for (int i = tid; i < r0; i += kApplyThreads) nx.ps[i] = ws.sm.red[i];
+  }
+  if (j < rnew) apply_column(ws, j, st, nx, r, r0, r0e, compact);
+  // the last CTA commits the new state and snapshot buffers
+  __shared__ unsigned ticket;
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) ticket = atomicAdd(&ctl->ticket_b, 1u);
+  __syncthreads();
+  if (ticket != gridDim.x - 1) return;
+  if (tid == 0) {
+    __threadfence();
+    ctl->cur = cur ^ 1;
+    ctl->cur_c = ctl->cur_c ^ 1;
+    ctl->eig_valid = 0;
+    ctl->model_ver += 1ull;
+    ctl->ticket_b = 0u;
+  }
+}
+
+__device__ void apply_column(const Ws& ws, int j, const StateBuf& st, const StateBuf& nx, int r, int r0, int r0e,
+                             bool compact) {
+  Ctl* ctl = ws.ctl;
+  const int tid = threadIdx.x;
+  const int n = r + 1, rnew = ctl->rnew;
+  const int qld = ws.cap + 1, rm = ws.rmax;
+  const double rho = ctl->rho, gamma = ctl->gamma;
+  __shared__ double v[kMaxN], u[kMaxN], bv[kMaxN], qcol[kMaxCap + 1], rlv;
+  for (int i = tid; i < n; i += kApplyThreads) {
+    v[i] = ws.sm.V[(size_t)j * kMaxN + i];
+    u[i] = ws.sm.U[(size_t)j * kMaxN + i];
+  }
+  __syncthreads();
+  // B v, rows 0..r-1: M v[0:r] + w v_r  (4 threads per row; r <= 64 rows)
+  {
+    const int i = tid >> 2, sub = tid & 3;
+    double acc = 0.0;
+    if (i < r)
+      for (int k = sub; k < r; k += 4) acc = fma(st.M[(size_t)k * rm + i], v[k], acc);
+    acc = group4_sum_d(acc);
+    if (i < r && sub == 0) bv[i] = fma(ws.sm.w[i], v[r], acc);
+  }
+  // row r: rho (r_last . v[0:r]) + gamma v_r   (warp 7)
+  if ((tid >> 5) == 7) {
+    const int lane = tid & 31;
+    double t = 0.0;
+    for (int k = lane; k < r; k += 32) t = fma(st.rl[k], v[k], t);
+    t = warp_sum_d(t);
+    if (lane == 0) rlv = t;
+  }
+  // Q' column j (rows 0..r0e-1): Q u[0:r] + qn u_r
+  for (int base = 0; base < 4 * r0e; base += kApplyThreads) {
+    const int i = (base + tid) >> 2, sub = tid & 3;
+    double acc = 0.0;
+    if (i < r0)
+      for (int k = sub; k < r; k += 4) acc = fma(dd2d(st.Q[(size_t)k * qld + i]), u[k], acc);
+    acc = group4_sum_d(acc);
+    if (i < r0e && sub == 0) qcol[i] = fma(ws.sm.qn[i], u[r], acc);
+  }
+  __syncthreads();
+  if (tid == 0) bv[r] = fma(rho, rlv, gamma * v[r]);
+  __syncthreads();
+  // M' column j: U'^T (B v)   (4 threads per output row i < rnew)
+  {
+    const int i = tid >> 2, sub = tid & 3;
+    double acc = 0.0;
+    if (i < rnew)
+      for (int k = sub; k < n; k += 4) acc = fma(ws.sm.U[(size_t)i * kMaxN + k], bv[k], acc);
+    acc = group4_sum_d(acc);
+    if (i < rnew && sub == 0) nx.M[(size_t)j * rm + i] = acc;
+  }
+  if (compact) {
+    for (int i = tid; i < r0e; i += kApplyThreads) ws.sm.QB[(size_t)j * qld + i] = d2f2(qcol[i]);
+    for (int i = tid; i < rnew; i += kApplyThreads)
+      nx.Q[(size_t)j * qld + i] = make_float2(i == j ? 1.f : 0.f, 0.f);
+  } else {
+    for (int i = tid; i < r0e; i += kApplyThreads) nx.Q[(size_t)j * qld + i] = d2f2(qcol[i]);
+  }
+  // r_first', r_last', S', a' (compaction)  -- warp 0
+  if (tid < 32) {
+    const int lane = tid;
+    double rf = 0.0;
+    if (st.hdr->pairs != 0)
+      for (int k = lane; k < r; k += 32) rf = fma(st.rf[k], v[k], rf);
+    rf = warp_sum_d(rf);
+    double a = 0.0;
+    if (compact)
+      for (int i = lane; i < r0e; i += 32) a = fma(qcol[i], ws.sm.yext[i], a);
+    a = warp_sum_d(a);
+    if (lane == 0) {
+      nx.rf[j] = st.hdr->pairs == 0 ? v[r] : rf;
+      nx.rl[j] = v[r];
+      nx.S[j] = ldexp(ws.sm.sig[kMaxN + j], ctl->scale_exp);
+      if (compact) nx.a[j] = d2f2(a);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+static int prep_smem_cap(int cap) {
+  const int qld = cap + 1;
+  return (int)sizeof(double) * (qld * kMaxR + 3 * qld + 2 * kMaxN);
+}
+
+cudaError_t prepare_core() {
+  return cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, prep_smem_cap(kMaxCap));
+}
+
+cudaError_t launch_small(const Ws& ws, cudaStream_t s) {
+  cudaError_t e = launch_dependent(k_prep, 1, kPrepThreads, prep_smem_cap(ws.cap), s, ws);
+  if (e == cudaSuccess) e = launch_dependent(k_roots, kMaxN, kRootThreads, 0, s, ws);
+  if (e == cudaSuccess) e = launch_dependent(k_zhat, kMaxN + 1, kZhatThreads, 0, s, ws);
+  if (e == cudaSuccess) e = launch_dependent(k_vectors, kMaxN, kVecThreads, 0, s, ws);
+  if (e == cudaSuccess) e = launch_dependent(k_apply, kMaxN, kApplyThreads, 0, s, ws);
+  return e;
+}
+
+}  // namespace odmd

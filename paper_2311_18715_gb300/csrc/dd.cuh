@@ -24,6 +24,12 @@ __device__ __forceinline__ dd dd_from_double(double x) {
   const float h = __double2float_rn(x);
   return dd{h, __double2float_rn(x - (double)h)};
 }
+// a float pair (hi, lo) as the double it represents exactly, and a double rounded to a pair
+__device__ __forceinline__ double dd2d(float2 v) { return (double)v.x + (double)v.y; }
+__device__ __forceinline__ float2 d2f2(double x) {
+  const float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(x - (double)h));
+}
 
 __device__ __forceinline__ dd fast_two_sum(float a, float b) {
   const float s = __fadd_rn(a, b);

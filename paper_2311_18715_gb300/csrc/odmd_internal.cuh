@@ -44,7 +44,9 @@ enum : int {
 // pass-B modes
 enum : int { PB_NONE = 0, PB_APPEND = 1, PB_COMPACT = 2 };
 
-// Small quantities are stored as double-float pairs (float2: hi, lo); see dd.cuh.
+// The small state that the update carries from one snapshot to the next (S, the rows of R,
+// M) and the scratch of the core SVD are IEEE doubles; the factor Q and the vectors the tall
+// passes read are double-float pairs (float2: hi, lo; see dd.cuh).
 
 // Committed small state (two copies, selected by Ctl::cur).
 struct StateHdr {
@@ -60,10 +62,10 @@ struct StateHdr {
 
 struct StateBuf {
   StateHdr* hdr;
-  float2* S;    // r_max   singular values
-  float2* rf;   // r_max   first row of R
-  float2* rl;   // r_max   last row of R
-  float2* M;    // r_max x r_max, column-major, ld = r_max   (M = L^T U^+ R)
+  double* S;    // r_max   singular values
+  double* rf;   // r_max   first row of R
+  double* rl;   // r_max   last row of R
+  double* M;    // r_max x r_max, column-major, ld = r_max   (M = L^T U^+ R)
   float2* Q;    // (cap+1) x r_max, column-major, ld = cap+1  (L = L0 Q)
   float2* a;    // cap+1   L0^T c
   float2* ps;   // cap+1   coefficients s of the pending column: (e - L0 s) / rho0
@@ -86,10 +88,10 @@ struct Ctl {
   int eig_valid;    // eigen-cache matches the committed state
   int eig_r;        // rank the eigen-cache was built for
   int scale_exp;    // the core matrix is scaled by 2^-scale_exp for the secular solve
-  float2 thr;       // tau * max(sigma_1, ||c||)
-  float2 rho0;      // norm of the part of c outside span(L0)
-  float2 rho;       // norm of the part of c outside span(L)
-  float2 gamma;     // j^T x
+  double thr;       // tau * max(sigma_1, ||c||)
+  double rho0;      // norm of the part of c outside span(L0)
+  double rho;       // norm of the part of c outside span(L)
+  double gamma;     // j^T x
   float2 check_num, check_den;  // reductions of the credibility check
   unsigned long long prof_r0_sum;  // sum of r0 over pass-A launches (for roofline accounting)
   unsigned long long prof_a;       // number of pass-A launches
@@ -101,27 +103,27 @@ struct Ctl {
 // Scratch of the small solve (single copy).
 struct Small {
   float2* red;      // 2*cap+3 reduced tall sums: s (r0), y (r0), eta, ex, xi
-  float2* ac;       // cap+1   corrected projection of c onto L0 (a + s)
-  float2* yext;     // cap+1   L0_ext^T x
-  float2* qn;       // cap+1   new unit direction in L0_ext coordinates
-  float2* p;        // kMaxN   L^T c
-  float2* w;        // kMaxN   L^T x
-  float2* d;        // kMaxN   poles (ascending) of the secular problem, as scaled singular values
-  float2* z;        // kMaxN   scaled weights at those poles
+  double* ac;       // cap+1   corrected projection of c onto L0 (a + s)
+  double* yext;     // cap+1   L0_ext^T x
+  double* qn;       // cap+1   new unit direction in L0_ext coordinates
+  double* p;        // kMaxN   L^T c
+  double* w;        // kMaxN   L^T x
+  double* d;        // kMaxN   poles (ascending) of the secular problem, as scaled singular values
+  double* z;        // kMaxN   scaled weights at those poles
   int* pole;        // kMaxN   core coordinate of each pole
-  float2* dc;       // kMaxN   scaled diagonal of the core in core coordinates (S, 0)
+  double* dc;       // kMaxN   scaled diagonal of the core in core coordinates (S, 0)
   int* defl;        // kMaxN   deflated core coordinates
   int* rot_i;       // kMaxN
   int* rot_j;
-  float2* rot_c;
-  float2* rot_s;
+  double* rot_c;
+  double* rot_s;
   int* org;         // kMaxN   origin pole of each root
-  float2* mu;       // kMaxN   root minus its origin pole (scaled, squared units)
-  float2* zhat;     // kMaxN   Loewner weights
-  float2* sig;      // 2 kMaxN singular values of the core: roots, then the sorted list
+  double* mu;       // kMaxN   root minus its origin pole (scaled, squared units)
+  double* zhat;     // kMaxN   Loewner weights
+  double* sig;      // 2 kMaxN singular values of the core: roots, then the sorted list
   int* src;         // kMaxN   source of output column j: >=0 root index, <0: -(defl idx)-1
-  float2* U;        // kMaxN x kMaxN, column-major   left singular vectors of K (kept)
-  float2* V;        // kMaxN x kMaxN                   right singular vectors of K (kept)
+  double* U;        // kMaxN x kMaxN, column-major   left singular vectors of K (kept)
+  double* V;        // kMaxN x kMaxN                   right singular vectors of K (kept)
   float2* QB;       // (cap+1) x r_max, col-major ld cap+1: pass-B rotation (compaction)
   float2* coef;     // (cap+1) x kRollK rollout coefficients in L0 coordinates
   float2* pc;       // 2 x kMaxN: A~^{pc_t[s]} y, s = 0, 1, of the model of version pc_ver - 1 (see Ctl)
@@ -153,6 +155,7 @@ struct Ws {
   int gridPA;       // pass A grid: one CTA per SM, at most one per 32-row tile
   int gridG;        // Gram pass grid: two CTAs per SM, at most kGramCtas
   float tau_h, tau_l;  // truncation tolerance as a double-float
+  double tau;          // truncation tolerance
   Ctl* ctl;
   void* Lh;         // hi plane (float) / bf16 plane
   float* Ll;        // lo plane (FP64 mode only)
@@ -450,6 +453,7 @@ cudaError_t launch_ingest(const Ws& ws, const void* src, void* dst, cudaStream_t
 const void* ingest_kernel(int prec);  // the kernel launch_ingest uses (graph node lookup)
 cudaError_t prepare_tall(const Ws& ws);
 cudaError_t prepare_small(const Ws& ws);
+cudaError_t prepare_core();  // shared-memory limits of the FP64 small solves of the update
 cudaError_t launch_rollout(const Ws& ws, const double* coef_src, int kcols, void* out, int64_t ld,
                            int coef_mode, cudaStream_t s);
 cudaError_t launch_check(const Ws& ws, cudaStream_t s);

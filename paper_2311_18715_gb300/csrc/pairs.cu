@@ -342,15 +342,32 @@ __global__ void __launch_bounds__(kSmallThreads) k_pr_small(PWs w) {
     sm.T[c * kLdT + i] = f2_of(v);
     sm.V[c * kLdT + i] = make_float2(i == c ? 1.f : 0.f, 0.f);
   }
+  // ||K||_F^2 (invariant under the rotations below), for the test of negligible columns
+  __shared__ float fro2_sh;
+  if (tid < 32) {
+    float f = 0.f;
+    for (int o = tid; o < n * n; o += 32) {
+      const float t = sm.T[(o / n) * kLdT + o % n].x;
+      f = fmaf(t, t, f);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) f += __shfl_xor_sync(0xffffffffu, f, off);
+    if (tid == 0) fro2_sh = f;
+  }
   __syncthreads();
 
   // One-sided Jacobi on the columns of T, round-robin: each round rotates m/2 disjoint column
   // pairs at once, a half-warp per pair; a sweep is m - 1 rounds; stop after a sweep that
-  // rotates nothing (at most 24 sweeps, else the update is refused).
+  // rotates nothing (at most 24 sweeps, else the update is refused).  A pair is left alone
+  // when its columns are orthogonal to working accuracy, or when one of them has shrunk to
+  // the rounding level of ||K||_F: a pair that adds no new direction (rho = 0) makes K
+  // singular, one column then tends to zero, and the relative test alone would keep
+  // rotating its rounding noise (its singular value is truncated in any case).
   const int m = n + (n & 1);
   const int hw = tid >> 4, hl = tid & 15;
   const unsigned mask = (tid & 16) ? 0xffff0000u : 0x0000ffffu;
   const float tol = 4.f * 7.105427357601002e-15f;
+  const float negl = fro2_sh * (16.f * 7.105427357601002e-15f) * (16.f * 7.105427357601002e-15f);
   for (int sweep = 0; sweep < 24; ++sweep) {
     for (int k = 0; k < m - 1; ++k) {
       for (int pi = hw; pi < m / 2; pi += kSmallThreads / 16) {
@@ -370,7 +387,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_pr_small(PWs w) {
         }
         const dd A = half_sum16(acc_to_dd(al), mask), B = half_sum16(acc_to_dd(be), mask),
                  G = half_sum16(acc_to_dd(ga), mask);
-        if (!(fabsf(G.h) > tol * sqrtf(A.h) * sqrtf(B.h))) continue;
+        if (!(fabsf(G.h) > tol * sqrtf(A.h) * sqrtf(B.h)) || A.h <= negl || B.h <= negl) continue;
         if (hl == 0) atomicAdd(&sm.rot[sweep & 31], 1);
         const dd diff = B - A;
         dd c, s;

@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(kRefineThreads) k_refine(Ws ws, int cur) {
   __syncthreads();
   for (int o = tid; o < r * r; o += kRefineThreads) {
     const int i = o % r, k = o / r;
-    sm.T[k * ld + i] = f2_of(dd_of(sm.R[k * ld + i]) * dd_of(st.S[k]));
+    sm.T[k * ld + i] = f2_of(dd_of(sm.R[k * ld + i]) * dd_from_double(st.S[k]));
     sm.V[k * ld + i] = make_float2(i == k ? 1.f : 0.f, 0.f);
   }
   __syncthreads();
@@ -522,21 +522,20 @@ __global__ void __launch_bounds__(128) k_refine_out(Ws ws, int cur) {
       }
     }
   } else if (j < r) {
-    __shared__ float2 m2[kMaxR];
+    // M and the rows of R are FP64 state: the rotation is applied in FP64
+    __shared__ double m2[kMaxR];
     const int pj = S.perm[j];
     for (int i = tid; i < r; i += 128) {
-      Acc s = acc_zero();
-      for (int k = 0; k < r; ++k) acc_fma_k(s, st.M[(size_t)k * rm + i], S.V[(size_t)pj * rm + k], k);
-      s = acc_norm(s);
-      m2[i] = make_float2(s.h, s.l);
+      double s = 0.0;
+      for (int k = 0; k < r; ++k) s = fma(st.M[(size_t)k * rm + i], dd2d(S.V[(size_t)pj * rm + k]), s);
+      m2[i] = s;
     }
     __syncthreads();
     for (int i = tid; i < r; i += 128) {
       const int pi = S.perm[i];
-      Acc s = acc_zero();
-      for (int k = 0; k < r; ++k) acc_fma_k(s, S.W[(size_t)pi * rm + k], m2[k], k);
-      s = acc_norm(s);
-      nx.M[(size_t)j * rm + i] = make_float2(s.h, s.l);
+      double s = 0.0;
+      for (int k = 0; k < r; ++k) s = fma(dd2d(S.W[(size_t)pi * rm + k]), m2[k], s);
+      nx.M[(size_t)j * rm + i] = s;
     }
     for (int a = tid; a < r0; a += 128) {
       Acc s = acc_zero();
@@ -547,17 +546,15 @@ __global__ void __launch_bounds__(128) k_refine_out(Ws ws, int cur) {
     if (j == 0) {
       for (int jj = tid; jj < r; jj += 128) {
         const int pjj = S.perm[jj];
-        Acc f = acc_zero(), l = acc_zero();
+        double f = 0.0, l = 0.0;
         for (int k = 0; k < r; ++k) {
-          const float2 v = S.V[(size_t)pjj * rm + k];
-          acc_fma_k(f, st.rf[k], v, k);
-          acc_fma_k(l, st.rl[k], v, k);
+          const double v = dd2d(S.V[(size_t)pjj * rm + k]);
+          f = fma(st.rf[k], v, f);
+          l = fma(st.rl[k], v, l);
         }
-        f = acc_norm(f);
-        l = acc_norm(l);
-        nx.rf[jj] = make_float2(f.h, f.l);
-        nx.rl[jj] = make_float2(l.h, l.l);
-        nx.S[jj] = S.sig[pjj];
+        nx.rf[jj] = f;
+        nx.rl[jj] = l;
+        nx.S[jj] = dd2d(S.sig[pjj]);
       }
     }
   }

@@ -854,7 +854,7 @@ __global__ void __launch_bounds__(kThreadsB) k_pass_b(Ws ws) {
     r0 = ctl->r0e - append;
     rnew = ctl->rnew;
     if (append) {
-      const dd inv = dd_div(dd_of(1.f), dd_of(ctl->rho0));
+      const dd inv = dd_from_double(1.0 / ctl->rho0);
       ih = inv.h;
       il = inv.l;
     }

@@ -96,3 +96,55 @@ def test_load_refuses_bad_checkpoints():
     b = _model(500, 6)
     b.load(ck)                                # the original loads
     assert b.rank == a.rank
+
+
+def _fnv1a_words(h, data):
+    """FNV-1a over 8-byte little-endian words, then the tail bytes (the checkpoint's checksum)."""
+    mask = (1 << 64) - 1
+    n8 = len(data) // 8 * 8
+    for w in np.frombuffer(data[:n8], dtype="<u8").tolist():
+        h = ((h ^ w) * 1099511628211) & mask
+    for b in data[n8:]:
+        h = ((h ^ b) * 1099511628211) & mask
+    return h
+
+
+# header layout: magic 8, version u32, header_bytes u32, n i64, r_max/prec/slack/cap/ldg/ctl_bytes
+# i32, nsnap i64, cur_h i32, curc_h i32, region u64[6], checksum u64
+_HDR, _NSNAP, _CUR, _CURC, _SUM = 120, 48, 56, 60, 112
+
+
+def _reseal(buf):
+    """Recompute the checksum of a checkpoint whose header was edited (header with a zero
+    checksum field, then every region), so that only the range checks can refuse it."""
+    b = bytearray(buf)
+    b[_SUM:_SUM + 8] = bytes(8)
+    h = _fnv1a_words(1469598103934665603, bytes(b[:_HDR]))
+    h = _fnv1a_words(h, bytes(b[_HDR:]))
+    b[_SUM:_SUM + 8] = int(h).to_bytes(8, "little")
+    return bytes(b)
+
+
+def test_load_refuses_out_of_range_header_scalars():
+    """Buffer indices outside {0, 1} and a negative snapshot count are refused even when the
+    checksum matches; an edited header without a matching checksum is refused too."""
+    import struct
+
+    import paper_2311_18715_gb300 as pkg
+
+    X = torch.from_numpy(PlantedModes(500, seed=1).snapshots(0, 9)).cuda()
+    a = _model(500, 6)
+    for k in range(9):
+        a.update(X[k])
+    ck = a.save()
+    assert _reseal(ck) == ck  # the test's checksum is the library's
+    for off, fmt, val in [(_CUR, "<i", 2), (_CURC, "<i", -1), (_NSNAP, "<q", -5), (_CUR, "<i", 1 - struct.unpack_from("<i", ck, _CUR)[0])]:
+        bad = bytearray(ck)
+        struct.pack_into(fmt, bad, off, val)
+        with pytest.raises(pkg.OdmdError):
+            _model(500, 6).load(bytes(bad))            # checksum no longer matches
+        with pytest.raises(pkg.OdmdError):
+            _model(500, 6).load(_reseal(bytes(bad)))   # range or control-block check
+    b = _model(500, 6)
+    b.load(ck)
+    assert b.rank == a.rank

@@ -49,6 +49,16 @@ def strong_eigs(lam, amp, frac=1e-6):
     return lam[amp >= frac * amp.max()]
 
 
+def assert_horizons(got, want, bar, what=""):
+    """Every predicted state against the oracle's, relative to that state's own norm, so that
+    one poor horizon cannot hide under larger ones (rows are horizons)."""
+    got, want = np.asarray(got), np.asarray(want)
+    assert got.shape == want.shape, (got.shape, want.shape)
+    for j in range(want.shape[0]):
+        e = np.linalg.norm(got[j] - want[j]) / np.linalg.norm(want[j])
+        assert e < bar, (what, j, e)
+
+
 @pytest.mark.parametrize("slack", [0, 4, 16])
 def test_planted_modes_4096(slack):
     g = PlantedModes(4096, sigma=1e-8, seed=0)
@@ -67,7 +77,7 @@ def test_planted_modes_4096(slack):
     ts = [0.0, 1.0, 99.5, 199.0, 200.0, 260.0]
     got = m.predict(ts).cpu().numpy()
     want = ref.predict(ts).T
-    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-9
+    assert_horizons(got, want, 1e-9)
     for t in (200.0, 201.0):
         e_dev, _ = m.check(t, torch.from_numpy(g.snapshot(int(t))).cuda())
         e_ref, _ = ref.check(t, g.snapshot(int(t)))
@@ -89,7 +99,7 @@ def test_random_stream_ragged_tiles(n, slack):
     ts = [0.0, 17.0, 39.0, 40.0]
     got = m.predict(ts).cpu().numpy()
     want = ref.predict(ts).T
-    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-9
+    assert_horizons(got, want, 1e-9)
     L = m.basis().cpu().numpy().T
     P = L @ L.T
     Pr = ref.L @ ref.L.T
@@ -113,7 +123,7 @@ def test_no_truncation_matches_batch_dmd():
     assert match_eigs(lam, B.lam) < 1e-9
     got = m.predict([0.0, 12.0, 30.0]).cpu().numpy()
     want = B.predict([0.0, 12.0, 30.0]).T
-    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-9
+    assert_horizons(got, want, 1e-9)
 
 
 def test_wake_field_small_grid():
@@ -124,7 +134,7 @@ def test_wake_field_small_grid():
     np.testing.assert_allclose(m.singular_values(), ref.S, rtol=0, atol=1e-10 * ref.S[0])
     got = m.predict([300.0, 320.0]).cpu().numpy()
     want = ref.predict([300.0, 320.0]).T
-    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-9
+    assert_horizons(got, want, 1e-9)
 
 
 def _strong(ref, frac):
@@ -138,50 +148,31 @@ def test_wake_full_size_bench_configuration():
     r_max 40, slack 16): many tiles per CTA, so every stage of the tall pipelines is
     refilled, compactions included.  The oracle runs the same stream at full size.
 
-    With r_max below the number of noise directions, which noise direction each update
-    drops hinges on rounding-level differences between nearly equal noise singular values,
-    and the strong eigenvalues move with the noise directions kept, so results are only as
-    reproducible as this branch choice (reading A11).  The FP64 oracle alone shows it: runs
-    on inputs perturbed by 1e-16 relative differ by 1e-11..4e-11 in the strong
-    eigenvalues, and from ~1e-13 upward the change grows in proportion to the
-    perturbation.  The device's double-float rounding over 120 updates acts like an input
-    perturbation of about sqrt(120) * 2^-47 * 10 (operations per basis element per update)
-    = 8e-13, so the test measures the oracle's change d under a 1e-12 relative
-    perturbation of its inputs (the larger of two) and bars the device at
-    max(1e-10, 4 d) for the strong eigenvalues and max(1e-9, 4 d) for rollouts and check
-    errors.  The noise-subspace modes (amplitude ~1e-6 of the largest here, noise std
-    1e-6) are excluded by an amplitude threshold of 1e-3 of the largest, ~1000x above the
-    relative noise amplitude."""
+    Bars are the FP64 ones as stated, with nothing derived from the device: strong
+    eigenvalues within 1e-10 relative, every predicted state within 1e-9 relative, check
+    errors within 1e-9.  With r_max below the number of noise directions each update chooses
+    among nearly equal noise singular values, and the strong eigenvalues move with the noise
+    directions kept: the FP64 oracle run on inputs perturbed by 1e-16 relative differs from
+    itself by 1e-11..4e-11, so these bars leave room only for FP64-level rounding in the
+    steps that feed back (the core SVD and the operator update run in FP64 on the device).
+    The noise-subspace modes (amplitude ~1e-6 of the largest here, noise std 1e-6) are
+    excluded by an amplitude threshold of 1e-3 of the largest (reading A12)."""
     g = WakeField(512, 256, sigma=1e-6, seed=0)
     X = g.snapshots(0, 120)
     m, ref = run_pair(X, 40, slack=16)
-    perturbed = []
-    for seed in (1, 2):
-        rp = OnlineDMDRef(X.shape[1], 40, 1e-10)
-        Xp = X * (1.0 + 1e-12 * np.random.default_rng(seed).standard_normal(X.shape))
-        for k in range(Xp.shape[0]):
-            rp.update(Xp[k])
-        perturbed.append(rp)
     assert m.rank == ref.rank == 40
     np.testing.assert_allclose(m.singular_values(), ref.S, rtol=0, atol=1e-10 * ref.S[0])
-
     s_ref = _strong(ref, 1e-3)
-    d_eig = max(match_eigs(s_ref, _strong(rp, 1e-3)) for rp in perturbed)
     lam, amp = m.eigs()
     s_dev = strong_eigs(lam, amp, 1e-3)
     assert len(s_dev) == len(s_ref) >= 7
-    assert match_eigs(s_dev, s_ref) <= max(1e-10, 4 * d_eig), (match_eigs(s_dev, s_ref), d_eig)
-
-    ts = [120.0, 150.0]
-    want = ref.predict(ts).T
-    d_pred = max(np.linalg.norm(rp.predict(ts).T - want) for rp in perturbed) / np.linalg.norm(want)
-    got = m.predict(ts).cpu().numpy()
-    err = np.linalg.norm(got - want) / np.linalg.norm(want)
-    assert err <= max(1e-9, 4 * d_pred), (err, d_pred)
+    assert match_eigs(s_dev, s_ref) < 1e-10, match_eigs(s_dev, s_ref)
+    ts = [120.0, 121.0, 135.0, 150.0]
+    assert_horizons(m.predict(ts).cpu().numpy(), ref.predict(ts).T, 1e-9)
     x_fom = g.snapshot(125)
     e_dev, _ = m.check(125.0, torch.from_numpy(x_fom).cuda())
     e_ref, _ = ref.check(125.0, x_fom)
-    assert abs(e_dev - e_ref) <= max(1e-9, 4 * d_pred)
+    assert abs(e_dev - e_ref) <= 1e-9
 
 
 def test_many_tiles_per_cta_small_rank():
@@ -193,7 +184,7 @@ def test_many_tiles_per_cta_small_rank():
     np.testing.assert_allclose(m.singular_values(), ref.S, rtol=0, atol=1e-10 * ref.S[0])
     got = m.predict([40.0, 41.5]).cpu().numpy()
     want = ref.predict([40.0, 41.5]).T
-    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-9
+    assert_horizons(got, want, 1e-9)
 
 
 def test_edge_cases():
@@ -248,7 +239,7 @@ def test_clustered_tiny_singular_values():
     np.testing.assert_allclose(m.singular_values(), ref.S, rtol=0, atol=1e-10 * ref.S[0])
     got = m.predict([125.0]).cpu().numpy()
     want = ref.predict([125.0]).T
-    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-9
+    assert_horizons(got, want, 1e-9)
 
 
 @pytest.mark.parametrize("stream", ["planted", "wake"])
@@ -332,8 +323,7 @@ def test_largest_rank_and_slack(slack):
     ts = [float(t) for t in range(0, 130, 2)]
     want = ref.predict(ts).T
     for got in (m.predict(ts).cpu().numpy(), m.predict(ts[:-1] + [128.5]).cpu().numpy()[:-1]):
-        k = got.shape[0]
-        assert np.linalg.norm(got - want[:k]) / np.linalg.norm(want[:k]) < 1e-9
+        assert_horizons(got, want[: got.shape[0]], 1e-9)
     err, _ = m.check(139.0, torch.from_numpy(X[139]).cuda())
     assert abs(err - ref.check(139.0, X[139])[0]) < 1e-9
     m.refine()
@@ -341,4 +331,4 @@ def test_largest_rank_and_slack(slack):
     L = m.basis().cpu().numpy().T
     assert np.max(np.abs(L.T @ L - np.eye(64))) < 1e-13
     got = m.predict(ts).cpu().numpy()
-    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-9
+    assert_horizons(got, want, 1e-9)
