@@ -147,9 +147,9 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ CPU oracle leg
 class OracleRunner:
-    """The FP64 oracle as it stands, brought to steady state (rank r_max) and then timed
-    on bounded samples of the workload: `sample` updates, a BLOCK-state rollout and one
-    check, extrapolated to a full block (BLOCK x mean update time + rollout + check)."""
+    """The FP64 oracle as it stands, brought to steady state (rank r_max), then timed on
+    whole blocks of the workload: BLOCK updates, a BLOCK-state rollout and one check, each
+    part by time.perf_counter (snapshot generation excluded)."""
 
     def __init__(self, seed: int = 0):
         from oracle import OnlineDMDRef
@@ -162,21 +162,23 @@ class OracleRunner:
             self.ref.update(self.gen.snapshot(self.k))
             self.k += 1
 
-    def step(self, sample: int) -> dict:
-        snaps = [self.gen.snapshot(self.k + j) for j in range(sample + 1)]
-        t0 = time.perf_counter()
-        for j in range(sample):
+    def block(self) -> dict:
+        snaps = [self.gen.snapshot(self.k + j) for j in range(BLOCK + 1)]
+        t_upd = []
+        for j in range(BLOCK):
+            t0 = time.perf_counter()
             self.ref.update(snaps[j])
-        t_upd = (time.perf_counter() - t0) / sample
-        self.k += sample
+            t_upd.append(time.perf_counter() - t0)
+        self.k += BLOCK
         t0 = time.perf_counter()
         self.ref.predict([float(self.k + h) for h in range(BLOCK)])
         t_pred = time.perf_counter() - t0
         t0 = time.perf_counter()
-        self.ref.check(float(self.k), snaps[sample])
+        self.ref.check(float(self.k), snaps[BLOCK])
         t_chk = time.perf_counter() - t0
-        step_s = BLOCK * t_upd + t_pred + t_chk
-        return {"step_s": step_s, "t_update_s": t_upd, "t_predict_s": t_pred, "t_check_s": t_chk,
+        step_s = sum(t_upd) + t_pred + t_chk
+        return {"step_s": step_s, "update_p50_ms": 1e3 * statistics.median(t_upd),
+                "update_p99_ms": 1e3 * float(np.percentile(t_upd, 99)), "predict_s": t_pred, "check_s": t_chk,
                 "updates_per_s": BLOCK / step_s, "states_per_s": BLOCK / t_pred, "rank": self.ref.rank}
 
 
@@ -187,30 +189,90 @@ def cpu_cores() -> int:
         return os.cpu_count() or 1
 
 
+_THREAD_VARS = ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS")
+
+
+def blas_info() -> dict:
+    """The BLAS/LAPACK library NumPy was built against, and the threads it runs with."""
+    info = {"blas": "unknown", "threads": None}
+    try:
+        cfg = np.show_config(mode="dicts")
+        b = cfg["Build Dependencies"]["blas"]
+        info["blas"] = f"{b.get('name')} {b.get('version')}"
+    except Exception:
+        pass
+    try:
+        import threadpoolctl
+
+        pools = threadpoolctl.threadpool_info()
+        if pools:
+            info["threads"] = max(int(p.get("num_threads", 0)) for p in pools)
+    except Exception:
+        pass
+    if info["threads"] is None:
+        env = [os.environ.get(v) for v in _THREAD_VARS if os.environ.get(v)]
+        info["threads"] = int(env[0]) if env else cpu_cores()
+        info["threads_source"] = "environment" if env else "library default (one per core)"
+    return info
+
+
+def oracle_child(threads: int | None, blocks: int) -> dict:
+    """Time the oracle on `blocks` whole blocks in a child process whose BLAS runs with
+    `threads` threads (None: the library's default, one per core)."""
+    env = dict(os.environ)
+    for v in _THREAD_VARS:
+        env.pop(v, None)
+        if threads is not None:
+            env[v] = str(threads)
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-child", str(blocks)]
+    res = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=900)
+    if res.returncode != 0:
+        raise RuntimeError(f"oracle child failed: {res.stderr[-2000:]}")
+    return json.loads(res.stdout.strip().splitlines()[-1])
+
+
+def run_oracle_child(blocks: int) -> None:
+    runner = OracleRunner(seed=0)
+    runs = [runner.block() for _ in range(blocks)]
+    step_s = statistics.mean(r["step_s"] for r in runs)
+    out = {"step_s": step_s, "updates_per_s": BLOCK / step_s,
+           "states_per_s": statistics.mean(r["states_per_s"] for r in runs),
+           "update_p50_ms": statistics.median(r["update_p50_ms"] for r in runs),
+           "rank": runs[-1]["rank"], "blocks": blocks, "cores": cpu_cores()}
+    out.update(blas_info())
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(args) -> None:
-    """Reference arm: the FP64 oracle on the host cores, same metric, unit and config."""
+    """Reference arm: the FP64 oracle on the host cores, same metric, unit and config; each
+    step is one whole block of the workload (no extrapolation)."""
     rank, world, local, dist = dist_setup(args.gpus)
     if rank != 0:
         return
-    sample = 6
     runner = OracleRunner(seed=0)
-    steps = []
+    steps, upd = [], []
+    t_wall0 = time.perf_counter()
     for i in range(args.warmup + args.steps):
-        r = runner.step(sample)
+        r = runner.block()
         if i >= args.warmup:
             steps.append(r["step_s"])
+            upd.append(r["update_p50_ms"])
+    t_wall = time.perf_counter() - t_wall0
     step_s = statistics.mean(steps)
     value = BLOCK / step_s
-    desc = (f"each step: {sample} oracle updates at steady state (rank {R_MAX}) + a {BLOCK}-state "
-            f"rollout + 1 check; step time = {BLOCK} x mean update time + rollout + check")
+    bi = blas_info()
+    desc = (f"each step one whole block: {BLOCK} oracle updates at steady state (rank {R_MAX}), a "
+            f"{BLOCK}-state rollout and 1 check, timed in full ({bi['blas']}, {bi['threads']} BLAS threads)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "snapshot updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "n": N, "r_max": R_MAX, "block": BLOCK},
         "cpu_baseline": {"value": value, "unit": "snapshot updates/s", "cores": cpu_cores(), "kind": "oracle",
-                         "sample": desc},
+                         "sample": desc, "blas": bi["blas"], "threads": bi["threads"],
+                         "update_p50_ms": statistics.median(upd)},
         "e2e": {"value": value, "unit": "snapshot updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s_timed_and_warmup": t_wall,
     }
     print(json.dumps(line), flush=True)
 
@@ -224,9 +286,10 @@ def run_ours(args) -> None:
     from synth import WakeField
 
     # the CPU leg runs first, before any GPU work, on rank 0 at N = 1 only
-    cpu = None
+    cpu = cpu1 = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = OracleRunner(seed=0).step(args.cpu_updates)
+        cpu = oracle_child(None, args.cpu_blocks)
+        cpu1 = oracle_child(1, 1)
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -311,36 +374,41 @@ def run_ours(args) -> None:
     value = units / total_s_max
     states_s = sum_over_ranks(float(BLOCK * K), dist, dev) / max_over_ranks(sum(pred_ms) / 1e3, dist, dev)
 
-    # ---- roofline of the dominant kernel class (live event timing)
+    # ---- roofline (live event timing).  Algorithmic bytes per launch at the model's rank r
+    # (w = 8 bytes per basis element, v = 8 per snapshot element): pass A reads L and the
+    # snapshots c and x, N r w + 2 N v; a whole update moves B_upd = 3 N r w + 3 N v (two
+    # reads and one write of L, three snapshot-sized vectors); a k-state rollout N r w + k N v;
+    # a check N r w + N v.  The product form moves other bytes (pass A streams the r0 >= r
+    # columns of L0; the compaction reads L0 and writes L every ~slack updates): those are
+    # implementation traffic and are not counted as algorithmic.
     hbm, peak_kind = _peaks()
-    classes = ["pass_a", "small", "pass_b", "eig", "coef", "rollout", "check"]
+    classes = ["pass_a", "small", "pass_b", "eig", "coef", "rollout", "check", "gap"]
     ms_tot = {c: prof[c][0] for c in classes}
-    launches = {c: prof[c][1] - prof0[c][1] for c in classes}
+    launches = {c: prof[c][1] - prof0[c][1] for c in classes if c != "gap"}
     groups = {"pass_a": K * BLOCK, "small": K * BLOCK, "pass_b": K * BLOCK, "eig": K, "coef": 2 * K,
-              "rollout": K, "check": K}
+              "rollout": K, "check": K, "gap": 2 * K * BLOCK}
     mean_r0 = prof["mean_r0"]
-    dom = max(classes, key=lambda c: ms_tot[c])
-    w, v = 8, 8  # bytes per basis element (hi + lo floats) and per snapshot element (double)
-    bytes_per = {
-        # pass A streams the r0 active basis columns and the snapshots c and x
-        "pass_a": N * mean_r0 * w + 2 * N * v,
-        # the rollout streams the basis once and writes BLOCK states
-        "rollout": N * mean_r0 * w + BLOCK * N * v,
-        "check": N * mean_r0 * w + N * v,
-    }
-    roof = None
-    if dom in bytes_per:
-        per_launch_ms = ms_tot[dom] / max(groups[dom], 1)
-        achieved = bytes_per[dom] / (per_launch_ms * 1e-3) / 1e9
-        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": TRAFFIC.get(dom), "peak_kind": peak_kind,
-                "bytes_per_launch": bytes_per[dom], "ms_per_launch": per_launch_ms}
-    pa_ms = ms_tot["pass_a"] / max(groups["pass_a"], 1)
-    pass_a_roof = {"achieved": bytes_per["pass_a"] / (pa_ms * 1e-3) / 1e9, "peak": hbm,
-                   "frac": bytes_per["pass_a"] / (pa_ms * 1e-3) / 1e9 / hbm, "ms_per_launch": pa_ms}
-    if roof is None:
-        roof = dict(pass_a_roof, kernel="pass_a", bound="hbm", unit="GB/s", traffic=TRAFFIC["pass_a"],
-                    peak_kind=peak_kind, note=f"dominant class is {dom}")
+    r = model.rank
+    w, v = 8, 8
+    alg = {"pass_a": N * r * w + 2 * N * v, "rollout": N * r * w + BLOCK * N * v, "check": N * r * w + N * v,
+           "update": 3 * N * r * w + 3 * N * v}
+    gap_ms = ms_tot["gap"] / max(groups["gap"], 1)  # one event-to-event interval inside the update graph
+    per_ms = {c: ms_tot[c] / max(groups[c], 1) for c in classes}
+    per_ms["update"] = per_ms["pass_a"] + per_ms["small"] + per_ms["pass_b"]
+
+    def frac(c):
+        gbs = alg[c] / (per_ms[c] * 1e-3) / 1e9
+        return {"achieved_gbs": gbs, "frac": gbs / hbm, "ms_per_launch": per_ms[c], "alg_bytes": alg[c]}
+
+    by_kernel = {c: frac(c) for c in ("pass_a", "rollout", "check", "update")}
+    by_kernel["pass_a"]["ms_per_launch_less_gap"] = per_ms["pass_a"] - gap_ms
+    by_kernel["pass_a"]["frac_less_gap"] = alg["pass_a"] / ((per_ms["pass_a"] - gap_ms) * 1e-3) / 1e9 / hbm
+    dom = max(("pass_a", "rollout", "check"), key=lambda c: ms_tot[c])
+    roof = {"kernel": dom, "bound": "hbm", "achieved": by_kernel[dom]["achieved_gbs"], "peak": hbm, "unit": "GB/s",
+            "frac": by_kernel[dom]["frac"], "traffic": TRAFFIC.get(dom), "peak_kind": peak_kind,
+            "bytes_per_launch": alg[dom], "ms_per_launch": per_ms[dom], "rank": r,
+            "bytes_rule": "algorithmic: N r w + 2 N v at the model's rank r (pass A)" if dom == "pass_a" else
+                          "algorithmic bytes at the model's rank r"}
 
     # ---- end to end through the public API with host buffers
     x_stage = torch.empty(N, dtype=torch.float64, device=dev)
@@ -382,7 +450,7 @@ def run_ours(args) -> None:
             "metric": METRIC, "value": value, "unit": "snapshot updates/s", "n_gpus": world,
             "steps": K, "warmup": W, "ms_per_step": sum(step_ms) / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32x2 (double-float basis, 48-bit significand) + f64 small solves",
+            "dtype": "f32x2 tall passes (double-float basis, 48-bit significand) + f64 core SVD and operator update",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": N, "r_max": R_MAX, "slack": SLACK, "trunc_tol": TAU,
                        "block": BLOCK, "pretrain": PRETRAIN, "noise_std": SIGMA,
@@ -394,10 +462,11 @@ def run_ours(args) -> None:
                            "predict50_p50": float(np.percentile(pred_ms, 50)),
                            "check_p50": float(np.percentile(chk_ms, 50))},
             "check_rel_err_last": errs[-1],
-            "kernel_ms_per_step": {c: ms_tot[c] / K for c in classes},
+            "kernel_ms_per_step": {c: ms_tot[c] / K for c in classes if c != "gap"},
             "mean_r0": mean_r0,
             "roofline": roof,
-            "pass_a_roofline": pass_a_roof,
+            "roofline_by_kernel": by_kernel,
+            "graph_event_gap_ms": gap_ms,
             "wall_s_timed": t_wall,
             "e2e": {"value": e2e_value, "unit": "snapshot updates/s",
                     "h2d_bytes_per_step": (BLOCK + 1) * N * 8, "d2h_bytes_per_step": BLOCK * N * 8 + 16},
@@ -406,11 +475,16 @@ def run_ours(args) -> None:
         }
         if cpu is not None:
             line["cpu_baseline"] = {"value": cpu["updates_per_s"], "unit": "snapshot updates/s",
-                                    "cores": cpu_cores(), "kind": "oracle",
-                                    "sample": f"{args.cpu_updates} oracle updates at steady state (rank "
-                                              f"{cpu['rank']}) + a {BLOCK}-state rollout + 1 check; step = "
-                                              f"{BLOCK} x update + rollout + check",
-                                    "rollout_states_per_s": cpu["states_per_s"]}
+                                    "cores": cpu["cores"], "kind": "oracle",
+                                    "sample": f"{args.cpu_blocks} whole block(s) of the workload timed in full: "
+                                              f"{BLOCK} oracle updates at steady state (rank {cpu['rank']}), a "
+                                              f"{BLOCK}-state rollout and 1 check",
+                                    "blas": cpu["blas"], "threads": cpu["threads"],
+                                    "rollout_states_per_s": cpu["states_per_s"],
+                                    "update_p50_ms": cpu["update_p50_ms"],
+                                    "single_thread": {"value": cpu1["updates_per_s"], "threads": cpu1["threads"],
+                                                      "rollout_states_per_s": cpu1["states_per_s"],
+                                                      "update_p50_ms": cpu1["update_p50_ms"]}}
         print(json.dumps(line), flush=True)
     model.close()
     if dist is not None:
@@ -867,7 +941,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--cpu-updates", type=int, default=60, help="oracle updates timed for cpu_baseline")
+    ap.add_argument("--cpu-blocks", type=int, default=2, help="whole oracle blocks timed for cpu_baseline")
+    ap.add_argument("--oracle-child", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", action="store_true",
                     help="untimed short run of the same kernels, for ncu captures")
@@ -875,6 +950,9 @@ def main():
     ap.add_argument("--config", choices=["wake", "fp32-large", "batched", "serving", "hybrid", "pairs"], default="wake",
                     help="wake: the headline workload; fp32-large and batched: extra measured configurations")
     args = ap.parse_args()
+    if args.oracle_child:
+        run_oracle_child(args.oracle_child)
+        return
     if args.profile_case:
         run_profile_case(args)
         return

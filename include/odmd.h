@@ -193,7 +193,9 @@ typedef enum {
   ODMD_K_CHECK = 6,    /* tall fused credibility-check pass */
   ODMD_K_FIRST = 7,    /* norm of the first snapshot */
   ODMD_K_REFINE = 8,   /* orthogonality refinement (Gram pass + 4 small kernels) */
-  ODMD_K_COUNT = 9
+  ODMD_K_GAP = 9,      /* two event records back to back inside a profiled update graph: the
+                          overhead each bracketed group's time above includes */
+  ODMD_K_COUNT = 10
 } odmd_kernel_class;
 
 /* Observability: when enabled (nonzero), every kernel group the handle enqueues is

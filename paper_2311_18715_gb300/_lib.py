@@ -30,7 +30,7 @@ FOM_FN = C.CFUNCTYPE(C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p)
 class RunReport(C.Structure):
     _fields_ = [("steps", C.c_int64), ("fom_calls", C.c_int64), ("accepted", C.c_int64), ("converged", C.c_int32),
                 ("pad", C.c_int32), ("converged_at", C.c_int64), ("skipped", C.c_int64)]
-KERNEL_CLASSES = ["pass_a", "small", "pass_b", "eig", "coef", "rollout", "check", "first", "refine"]
+KERNEL_CLASSES = ["pass_a", "small", "pass_b", "eig", "coef", "rollout", "check", "first", "refine", "gap"]
 
 
 class OdmdConfig(C.Structure):

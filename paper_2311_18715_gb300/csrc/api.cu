@@ -33,6 +33,7 @@ struct odmd_instance {
   struct Pending {
     int cls;
     cudaEvent_t a, b;
+    bool owned = true;  // false: the events also belong to another entry (returned by that one)
   };
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> pool;
@@ -405,8 +406,10 @@ void prof_collect(odmd_t h) {
     float ms = 0.f;
     if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess)
       h->prof_ms[p.cls] += ms;
-    h->pool.push_back(p.a);
-    h->pool.push_back(p.b);
+    if (p.owned) {
+      h->pool.push_back(p.a);
+      h->pool.push_back(p.b);
+    }
   }
   h->pending.clear();
 }
@@ -676,6 +679,9 @@ odmd_status odmd_update(odmd_t h, const void* x_dev) {
         h->pending.push_back({ODMD_K_PASS_A, evs[0], evs[1]});
         h->pending.push_back({ODMD_K_SMALL, evs[2], evs[3]});
         h->pending.push_back({ODMD_K_PASS_B, evs[4], evs[5]});
+        // the empty intervals between the groups: the graph's own timing overhead
+        h->pending.push_back({ODMD_K_GAP, evs[1], evs[2], false});
+        h->pending.push_back({ODMD_K_GAP, evs[3], evs[4], false});
       } else {
         for (cudaEvent_t ev : evs)
           if (ev) h->pool.push_back(ev);

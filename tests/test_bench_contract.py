@@ -88,3 +88,16 @@ def test_clock_sampler_reads_median_clock_and_throttle_reasons(tmp_path):
     assert c["samples"] == 4
     assert c["sm_mhz"] == 2025.0 and c["sm_max_mhz"] == 2070.0
     assert c["reasons"] == ["hw_slowdown", "sw_power_cap"]
+
+
+def test_oracle_child_times_whole_blocks_with_the_thread_count_set():
+    """The CPU legs time the oracle in a child process whose BLAS thread count is set through
+    the environment (one thread here), on whole blocks of the workload, and report the BLAS
+    library with the threads it ran with."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    d = bench.oracle_child(1, 1)
+    assert d["blocks"] == 1 and d["rank"] == 40
+    assert d["threads"] == 1 and d["blas"] and d["blas"] != "unknown"
+    assert d["updates_per_s"] > 0 and d["states_per_s"] > 0 and d["step_s"] > 0
