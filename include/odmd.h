@@ -290,6 +290,26 @@ odmd_status odmd_checkpoint_size(odmd_t h, size_t* bytes);
 odmd_status odmd_save(odmd_t h, void* host_buf, size_t bytes);
 odmd_status odmd_load(odmd_t h, const void* host_buf, size_t bytes);
 
+/* Row shards (Sec. 2.3: the O(N r) passes of an update are row-local, so the rows split
+ * across GPUs and each pass ends in a reduction of a few values).  The paper has no
+ * multi-GPU counterpart; this is the one-GPU form of a row-sharded run.
+ *
+ * The rows are cut into B row blocks, the same for every pass that ends in a reduction (the
+ * projection/residual pass of an update, the credibility check, the norm of the first
+ * snapshot): block b is rows [rows[b], rows[b+1]) with B and rows from odmd_get_row_blocks
+ * (rows_host: cap >= B + 1 int64 on the host, may be NULL; block boundaries are multiples
+ * of 64 rows).  Each block's partial sums are added in block order.
+ *
+ * odmd_set_row_shards: run every such pass as `shards` launches, shard g taking the
+ * contiguous blocks [g B / shards, (g + 1) B / shards), each launch leaving its per-block
+ * partials in the workspace, followed by one launch that adds all partials in block order
+ * (the exchange a run on `shards` GPUs would make, an all-gather of the per-block partials).
+ * The results are bitwise those of shards = 1 (the default), because every block's partial
+ * and the order of the final sum are the same.  1 <= shards <= B, else ODMD_ERR_ARG.
+ * Synchronises the stream; the captured update graphs are rebuilt on the next update. */
+odmd_status odmd_set_row_shards(odmd_t h, int32_t shards);
+odmd_status odmd_get_row_blocks(odmd_t h, int32_t* blocks, int64_t* rows_host, int32_t cap);
+
 /* Release the handle (synchronises first).  The workspace is the caller's again. */
 odmd_status odmd_destroy(odmd_t h);
 

@@ -20,7 +20,7 @@ EXPORTED = [
     "odmd_load", "odmd_hybrid_step_residual", "odmd_hybrid_run", "odmd_update_host",
     "odmd_pairs_footprint", "odmd_pairs_create", "odmd_pairs_update", "odmd_pairs_predict",
     "odmd_pairs_get_singular_values", "odmd_pairs_get_count", "odmd_pairs_last_error", "odmd_pairs_destroy",
-    "odmd_pairs_hybrid_step_residual", "odmd_tc_selftest",
+    "odmd_pairs_hybrid_step_residual", "odmd_tc_selftest", "odmd_set_row_shards", "odmd_get_row_blocks",
 ]
 # host callbacks of odmd_hybrid_step_residual: (user, step, u, r, b, stream) and (user, step, u, stream)
 RESIDUAL_FN = C.CFUNCTYPE(C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p)
@@ -104,6 +104,8 @@ def load_library(path: str | None = None) -> C.CDLL:
         "odmd_pairs_get_count": [vp, C.POINTER(i64)],
         "odmd_pairs_destroy": [vp],
         "odmd_tc_selftest": [vp, vp, vp, vp, i32],
+        "odmd_set_row_shards": [vp, i32],
+        "odmd_get_row_blocks": [vp, C.POINTER(i32), C.POINTER(i64), i32],
         "odmd_pairs_hybrid_step_residual": [vp, RESIDUAL_FN, FOM_FN, vp, dbl, i64, vp, vp, vp, vp, C.POINTER(i32),
                                             C.POINTER(dbl)],
     }

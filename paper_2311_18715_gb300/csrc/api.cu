@@ -604,10 +604,7 @@ odmd_status odmd_create(const odmd_config* cfg, void* workspace_dev, size_t byte
   h->stage[0] = reinterpret_cast<unsigned char*>(workspace_dev) + L.off_stage[0];
   h->stage[1] = reinterpret_cast<unsigned char*>(workspace_dev) + L.off_stage[1];
   {
-    const int64_t tiles32 = (cfg->n + 31) / 32;
-    int g = (int)(tiles32 < sms ? tiles32 : sms);
-    if (g > kPartRows) g = kPartRows;
-    h->ws.gridPA = g < 1 ? 1 : g;
+    h->ws.shards = 1;
     h->ws.gridG = 2 * sms < kGramCtas ? 2 * sms : kGramCtas;
     if (h->ws.gridG < 1) h->ws.gridG = 1;
   }
@@ -644,7 +641,7 @@ odmd_status odmd_update(odmd_t h, const void* x_dev) {
   if (!x_dev) return fail(h, ODMD_ERR_ARG, "x is NULL");
   if (h->nsnap == 0) {
     CK(h, launch_ingest(h->ws, x_dev, h->ws.cbuf[h->curc_h], h->stream), "copy u0");
-    ProfScope ps(h, ODMD_K_FIRST, 1);
+    ProfScope ps(h, ODMD_K_FIRST, launches_per_reduction(h->ws));
     CK(h, launch_first(h->ws, h->stream), "first launch");
     h->nsnap = 1;
     return ODMD_OK;
@@ -689,7 +686,7 @@ odmd_status odmd_update(odmd_t h, const void* x_dev) {
     }
     if (ok) {
       CK(h, cudaGraphLaunch(G.exec, h->stream), "update graph launch");
-      h->launches[ODMD_K_PASS_A] += 1;
+      h->launches[ODMD_K_PASS_A] += launches_per_reduction(h->ws);
       h->launches[ODMD_K_SMALL] += 5;
       h->launches[ODMD_K_PASS_B] += 1;
       graphed = true;
@@ -698,7 +695,7 @@ odmd_status odmd_update(odmd_t h, const void* x_dev) {
   if (!graphed) {
     CK(h, launch_ingest(h->ws, x_dev, h->ws.cbuf[h->curc_h ^ 1], h->stream), "copy x");
     {
-      ProfScope ps(h, ODMD_K_PASS_A, 1);
+      ProfScope ps(h, ODMD_K_PASS_A, launches_per_reduction(h->ws));
       CK(h, launch_pass_a(h->ws, h->stream), "pass A launch");
     }
     {
@@ -755,7 +752,7 @@ odmd_status odmd_check(odmd_t h, double t, const void* x_fom_dev, double tol, do
   if (odmd_status s = launch_coefficients(h, &t, 1, by_powers)) return s;
   if (odmd_status s = flush_pending(h)) return s;
   {
-    ProfScope ps(h, ODMD_K_CHECK, 1);
+    ProfScope ps(h, ODMD_K_CHECK, launches_per_reduction(h->ws));
     CK(h, launch_check(h->ws, h->stream), "check launch");
   }
   CK(h, cudaMemcpyAsync(h->pinned, h->ws.out2, 2 * sizeof(float2), cudaMemcpyDeviceToHost, h->stream), "read back");
@@ -1299,18 +1296,49 @@ odmd_status odmd_profile_read(odmd_t h, double* ms_total, int64_t* launches, int
   return ODMD_OK;
 }
 
-odmd_status odmd_destroy(odmd_t h) {
-  if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
-  cudaError_t e = cudaStreamSynchronize(h->stream);
-  prof_collect(h);
-  for (cudaEvent_t ev : h->pool) cudaEventDestroy(ev);
+// release the captured update graphs (they are captured again on the next update)
+static void drop_update_graphs(odmd_t h) {
   for (auto& row : h->ug)
     for (auto& g : row) {
       if (g.exec) cudaGraphExecDestroy(g.exec);
       if (g.graph) cudaGraphDestroy(g.graph);
       for (cudaEvent_t ev : g.ph)
         if (ev) cudaEventDestroy(ev);
+      g = odmd_instance::UpdGraph{};
     }
+}
+
+odmd_status odmd_set_row_shards(odmd_t h, int32_t shards) {
+  if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
+  if (shards < 1 || shards > h->ws.gridA)
+    return fail(h, ODMD_ERR_ARG, "shards must lie in [1, " + std::to_string(h->ws.gridA) + "] (the row blocks)");
+  if (shards == h->ws.shards) return ODMD_OK;
+  CK(h, cudaStreamSynchronize(h->stream), "shards: sync");
+  drop_update_graphs(h);
+  h->ws.shards = shards;
+  return ODMD_OK;
+}
+
+odmd_status odmd_get_row_blocks(odmd_t h, int32_t* blocks, int64_t* rows_host, int32_t cap) {
+  if (!h || !blocks) return fail(h, ODMD_ERR_ARG, "NULL argument");
+  const int B = h->ws.gridA;
+  *blocks = B;
+  if (rows_host && cap > 0) {
+    const int64_t T = (h->cfg.n + kTile - 1) / kTile;
+    for (int b = 0; b <= B && b < cap; ++b) {
+      const int64_t r = (int64_t)b * T / B * kTile;
+      rows_host[b] = r < h->cfg.n ? r : h->cfg.n;
+    }
+  }
+  return ODMD_OK;
+}
+
+odmd_status odmd_destroy(odmd_t h) {
+  if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  prof_collect(h);
+  for (cudaEvent_t ev : h->pool) cudaEventDestroy(ev);
+  drop_update_graphs(h);
   if (h->cap) cudaStreamDestroy(h->cap);
   for (int b = 0; b < 2; ++b) {
     if (h->ev_copied[b]) cudaEventDestroy(h->ev_copied[b]);

@@ -152,7 +152,7 @@ struct Ws {
   int64_t npad;     // rows rounded up to kTile
   int rmax, cap, ldg, prec, gridA;
   int stagesA;      // TMA pipeline depth of pass A (as many stages as shared memory holds)
-  int gridPA;       // pass A grid: one CTA per SM, at most one per 32-row tile
+  int shards;       // row shards a reduction pass is split into (1: one launch; see tall.cu)
   int gridG;        // Gram pass grid: two CTAs per SM, at most kGramCtas
   float tau_h, tau_l;  // truncation tolerance as a double-float
   double tau;          // truncation tolerance
@@ -449,6 +449,7 @@ cudaError_t launch_pass_a(const Ws& ws, cudaStream_t s);
 cudaError_t launch_pass_b(const Ws& ws, cudaStream_t s);
 cudaError_t launch_flush(const Ws& ws, cudaStream_t s);  // write a pending basis column
 cudaError_t launch_first(const Ws& ws, cudaStream_t s);
+int launches_per_reduction(const Ws& ws);  // kernel launches of one pass A, check or first-norm
 cudaError_t launch_ingest(const Ws& ws, const void* src, void* dst, cudaStream_t s);  // snapshot -> workspace
 const void* ingest_kernel(int prec);  // the kernel launch_ingest uses (graph node lookup)
 cudaError_t prepare_tall(const Ws& ws);

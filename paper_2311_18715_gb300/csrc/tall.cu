@@ -490,8 +490,60 @@ __device__ __forceinline__ void row_dots_dispatch(int nch, const unsigned char* 
 }
 static_assert(kMaxCap <= 96, "row_dots_dispatch covers box widths up to 25 chunks of 4-byte elements");
 
+// ---------------------------------------------------------------------------------------
+// Row blocks.  Every pass that ends in a reduction over rows (pass A, the check, the norm of
+// the first snapshot) splits the rows the same way: ws.gridA blocks of whole 64-row tiles,
+// block b holding tiles [b T / B, (b + 1) T / B) of the T = ceil(n / 64).  Logical CTA b of a
+// pass works on block b alone and leaves its partial sums in slot b; the partials are then
+// added in block order.  A run split over G row shards (each shard a contiguous range of
+// blocks, as on G GPUs that each hold their rows) therefore computes bitwise the same
+// partials, and folding them in the same order gives bitwise the unsharded result.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void block_tiles64(const Ws& ws, int b, int64_t& t0, int64_t& t1) {
+  const int64_t T = (ws.n + kTile - 1) / kTile;
+  t0 = (int64_t)b * T / ws.gridA;
+  t1 = (int64_t)(b + 1) * T / ws.gridA;
+}
+
+// fold of pass A's per-block partials (one CTA of kThreadsA threads): 4 adjacent lanes per
+// value, each summing every 4th block, then a fixed-order combine
+__device__ void fold_pass_a(const Ws& ws, const StateBuf& st, int r0) {
+  Ctl* ctl = ws.ctl;
+  const int tid = threadIdx.x;
+  const int stride = 2 * ws.cap + 3;
+  const int nv = 2 * r0 + 3;
+  const int B = ws.gridA;
+  for (int base = 0; base < 4 * nv; base += kThreadsA) {
+    const int item = base + tid;
+    const int v = item >> 2, q = item & 3;
+    Acc sum = acc_zero();
+    if (v < nv)
+      for (int b = q; b < B; b += 4) {
+        const float2 f = __ldcg(ws.part + (size_t)b * stride + v);
+        acc_add(sum, f.x, f.y);
+      }
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) {
+      const float h = __shfl_xor_sync(0xffffffffu, sum.h, o);
+      const float l = __shfl_xor_sync(0xffffffffu, sum.l, o);
+      acc_add(sum, h, l);
+    }
+    if (v < nv && q == 0) {
+      sum = acc_norm(sum);
+      if (!isfinite(sum.h) || !isfinite(sum.l)) atomicOr(&ctl->status, DEV_NONFINITE);
+      ws.sm.red[v] = make_float2(sum.h, sum.l);
+    }
+  }
+  if (tid == 0) {
+    ctl->ticket_a = 0u;
+    ctl->prof_r0_sum += (unsigned long long)r0;
+    ctl->prof_a += 1ull;
+    st.hdr->pend = 0;  // the pending column now exists in L0
+  }
+}
+
 template <int ST>
-__global__ void __launch_bounds__(kThreadsA, 1) k_pass_a(Ws ws) {
+__global__ void __launch_bounds__(kThreadsA, 1) k_pass_a(Ws ws, int cta0, int fold) {
   pdl_wait();
   using T = Traits<ST>;
   using stored_t = typename T::stored_t;
@@ -559,9 +611,14 @@ __global__ void __launch_bounds__(kThreadsA, 1) k_pass_a(Ws ws) {
   }
   const float aph = pend ? st.a[p].x : 0.f, apl = pend ? st.a[p].y : 0.f;
   const float pih = st.hdr->pinv.x, pil = st.hdr->pinv.y;
+  // this CTA's row block, in tiles of kRowsA = 32 rows
+  static_assert(kTile == 2 * kRowsA, "a row block is whole 64-row tiles");
+  const int blk = cta0 + blockIdx.x;
+  int64_t b0, b1;
+  block_tiles64(ws, blk, b0, b1);
   const int64_t ntiles = (ws.n + kRowsA - 1) / kRowsA;
-  const int G = gridDim.x;
-  const int my_tiles = (int)((ntiles - blockIdx.x + G - 1) / G);
+  const int64_t tbase = 2 * b0;
+  const int my_tiles = (int)((2 * b1 < ntiles ? 2 * b1 : ntiles) - tbase);
   P.policy = l2_evict_first_policy();
   if (tid == 0) {
     abort_flag = 0;
@@ -573,7 +630,7 @@ __global__ void __launch_bounds__(kThreadsA, 1) k_pass_a(Ws ws) {
     // the first ns tiles; afterwards the warp that releases a stage refills it
     for (int k = 0; k < ns && k < my_tiles; ++k) {
       last_issued[k] = k;
-      P.issue(blockIdx.x + k * G, k);
+      P.issue((int)(tbase + k), k);
     }
   }
   __syncthreads();
@@ -589,7 +646,7 @@ __global__ void __launch_bounds__(kThreadsA, 1) k_pass_a(Ws ws) {
     float4* ex = ex4 + warp * kRowsA * 3;
     for (int k = warp; k < my_tiles; k += kWarpsA) {
       const int s = k % ns;
-      const int64_t row0 = (int64_t)(blockIdx.x + k * G) * kRowsA;
+      const int64_t row0 = (tbase + k) * kRowsA;
       const int rows = (int)((ws.n - row0) < kRowsA ? (ws.n - row0) : kRowsA);
       // rows past n (up to the padded length) read zeros
       const stored_t cv = cvec[row0 + lane], xv = xvec[row0 + lane];
@@ -696,7 +753,7 @@ __global__ void __launch_bounds__(kThreadsA, 1) k_pass_a(Ws ws) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0 && k + ns < my_tiles && !abort_flag) {
-        P.issue(blockIdx.x + (k + ns) * G, s);
+        P.issue((int)(tbase + k + ns), s);
         *reinterpret_cast<volatile int*>(&last_issued[s]) = k + ns;
       }
     }
@@ -716,7 +773,7 @@ __global__ void __launch_bounds__(kThreadsA, 1) k_pass_a(Ws ws) {
 
   // ---- per-CTA partials
   const int stride = 2 * ws.cap + 3;
-  float2* mypart = ws.part + (size_t)blockIdx.x * stride;
+  float2* mypart = ws.part + (size_t)blk * stride;
   // column sums: lanes cq and cq + 16 of a warp hold the same columns (even / odd rows)
   Acc* cacc = reinterpret_cast<Acc*>(smem);  // [warp][S | Y][kCo], in the idle stage memory
   {
@@ -780,43 +837,25 @@ __global__ void __launch_bounds__(kThreadsA, 1) k_pass_a(Ws ws) {
     mypart[2 * r0 + tid] = make_float2(a.h, a.l);
   }
 
-  // ---- last CTA reduces all partials in CTA order
-  __shared__ unsigned ticket;
+  // ---- the CTA that finishes last adds all partials in block order (a sharded run leaves
+  // that to k_fold_a, after every shard's launch)
   __threadfence();
+  if (!fold) return;
+  __shared__ unsigned ticket;
   __syncthreads();
   if (tid == 0) ticket = atomicAdd(&ctl->ticket_a, 1u);
   __syncthreads();
-  if (ticket != (unsigned)(G - 1)) return;
+  if (ticket != gridDim.x - 1) return;
   __threadfence();
-  // 4 adjacent lanes per value, each summing every 4th CTA, then a fixed-order combine
-  const int nv = 2 * r0 + 3;
-  for (int base = 0; base < 4 * nv; base += kThreadsA) {
-    const int item = base + tid;
-    const int v = item >> 2, q = item & 3;
-    Acc sum = acc_zero();
-    if (v < nv)
-      for (int b = q; b < G; b += 4) {
-        const float2 f = __ldcg(ws.part + (size_t)b * stride + v);
-        acc_add(sum, f.x, f.y);
-      }
-#pragma unroll
-    for (int o = 1; o < 4; o <<= 1) {
-      const float h = __shfl_xor_sync(0xffffffffu, sum.h, o);
-      const float l = __shfl_xor_sync(0xffffffffu, sum.l, o);
-      acc_add(sum, h, l);
-    }
-    if (v < nv && q == 0) {
-      sum = acc_norm(sum);
-      if (!isfinite(sum.h) || !isfinite(sum.l)) atomicOr(&ctl->status, DEV_NONFINITE);
-      ws.sm.red[v] = make_float2(sum.h, sum.l);
-    }
-  }
-  if (tid == 0) {
-    ctl->ticket_a = 0u;
-    ctl->prof_r0_sum += (unsigned long long)r0;
-    ctl->prof_a += 1ull;
-    st.hdr->pend = 0;  // the pending column now exists in L0
-  }
+  fold_pass_a(ws, st, r0);
+}
+
+// the fold of pass A after a sharded run (one CTA): the exchange of per-block partials of a
+// row-sharded run, added in block order exactly as the unsharded pass adds them
+__global__ void __launch_bounds__(kThreadsA) k_fold_a(Ws ws) {
+  pdl_wait();
+  const StateBuf st = ws.st[ws.ctl->cur];
+  fold_pass_a(ws, st, st.hdr->r0);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1038,8 +1077,34 @@ __global__ void __launch_bounds__(kThreadsB) k_pass_b(Ws ws) {
 // ---------------------------------------------------------------------------------------
 constexpr int kStagesR = 2;
 
+// fold of the check's per-block partials (one thread): ||L c - x||^2 and ||x||^2
+__device__ void fold_check(const Ws& ws) {
+  Ctl* ctl = ws.ctl;
+  Acc a = acc_zero(), b = acc_zero();
+  for (int blk = 0; blk < ws.gridA; ++blk) {
+    const float2 f1 = __ldcg(ws.part + 2 * blk), f2 = __ldcg(ws.part + 2 * blk + 1);
+    acc_add(a, f1.x, f1.y);
+    acc_add(b, f2.x, f2.y);
+  }
+  a = acc_norm(a);
+  b = acc_norm(b);
+  ctl->check_num = make_float2(a.h, a.l);
+  ctl->check_den = make_float2(b.h, b.l);
+  ws.out2[0] = make_float2(a.h, a.l);
+  ws.out2[1] = make_float2(b.h, b.l);
+  ctl->ticket_r = 0u;
+}
+
+__global__ void __launch_bounds__(32) k_fold_check(Ws ws) {
+  if (threadIdx.x == 0) fold_check(ws);
+}
+
+// Rollout (CHECK = false): out[:, j] = L0 coef[:, j] for j < kcols.  Check (CHECK = true):
+// the partial sums of ||L0 coef[:, 0] - x||^2 and ||x||^2 over this CTA's row block, added
+// in block order by the CTA that finishes last when `fold` is set.  Logical CTA cta0 +
+// blockIdx.x works on that row block.
 template <int ST, bool CHECK>
-__global__ void __launch_bounds__(kThreads) k_rollout(Ws ws, int kcols, void* out, int64_t ld) {
+__global__ void __launch_bounds__(kThreads) k_rollout(Ws ws, int kcols, void* out, int64_t ld, int cta0, int fold) {
   using T = Traits<ST>;
   using snap_t = typename T::snap_t;
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -1048,7 +1113,6 @@ __global__ void __launch_bounds__(kThreads) k_rollout(Ws ws, int kcols, void* ou
   const int cur = ctl->cur;
   const StateBuf st = ws.st[cur];
   const int r0 = st.hdr->r0;
-  const int G = gridDim.x;
 
   TilePipe<ST> P;
   P.setup(ws, r0, kStagesR);
@@ -1091,10 +1155,12 @@ __global__ void __launch_bounds__(kThreads) k_rollout(Ws ws, int kcols, void* ou
   }
   __syncthreads();
 
-  const int64_t ntiles = (ws.n + kTile - 1) / kTile;
-  const int my_tiles = (int)((ntiles - blockIdx.x + G - 1) / G);
+  const int blk = cta0 + blockIdx.x;
+  int64_t tb0, tb1;
+  block_tiles64(ws, blk, tb0, tb1);
+  const int my_tiles = (int)(tb1 - tb0);
   if (tid == 0) {
-    for (int li = 0; li < min(my_tiles, kStagesR); ++li) P.issue(blockIdx.x + li * G, li);
+    for (int li = 0; li < min(my_tiles, kStagesR); ++li) P.issue((int)(tb0 + li), li);
   }
   // work split: items (t, j); with fewer than 4 columns each dot is split in nsub parts
   const int nsub = kcols == 1 ? 4 : (kcols == 2 ? 2 : 1);  // nsub * kTile * kcols <= 4 * kTile when > 1
@@ -1103,8 +1169,7 @@ __global__ void __launch_bounds__(kThreads) k_rollout(Ws ws, int kcols, void* ou
   for (int li = 0; li < my_tiles; ++li) {
     const int s = li % kStagesR;
     const uint32_t par = (uint32_t)((li / kStagesR) & 1);
-    const int tile = blockIdx.x + li * G;
-    const int64_t row0 = (int64_t)tile * kTile;
+    const int64_t row0 = (tb0 + li) * kTile;
     const int rows = rows_in(ws.n, row0);
     const bool ok = mbar_wait(&P.bars[s], par, &ctl->status);
     if (__syncthreads_or(!ok)) {
@@ -1212,7 +1277,7 @@ __global__ void __launch_bounds__(kThreads) k_rollout(Ws ws, int kcols, void* ou
       }
     }
     __syncthreads();
-    if (tid == 0 && li + kStagesR < my_tiles) P.issue(blockIdx.x + (li + kStagesR) * G, s);
+    if (tid == 0 && li + kStagesR < my_tiles) P.issue((int)(tb0 + li + kStagesR), s);
   }
 
   if constexpr (CHECK) {
@@ -1233,30 +1298,19 @@ __global__ void __launch_bounds__(kThreads) k_rollout(Ws ws, int kcols, void* ou
       }
       a = acc_norm(a);
       b = acc_norm(b);
-      ws.part[2 * blockIdx.x] = make_float2(a.h, a.l);
-      ws.part[2 * blockIdx.x + 1] = make_float2(b.h, b.l);
+      ws.part[2 * blk] = make_float2(a.h, a.l);
+      ws.part[2 * blk + 1] = make_float2(b.h, b.l);
     }
-    __shared__ unsigned ticket;
     __threadfence();
+    if (!fold) return;
+    __shared__ unsigned ticket;
     __syncthreads();
     if (tid == 0) ticket = atomicAdd(&ctl->ticket_r, 1u);
     __syncthreads();
-    if (ticket != (unsigned)(G - 1)) return;
+    if (ticket != gridDim.x - 1) return;
     if (tid == 0) {
       __threadfence();
-      Acc a = acc_zero(), b = acc_zero();
-      for (int blk = 0; blk < G; ++blk) {
-        const float2 f1 = __ldcg(ws.part + 2 * blk), f2 = __ldcg(ws.part + 2 * blk + 1);
-        acc_add(a, f1.x, f1.y);
-        acc_add(b, f2.x, f2.y);
-      }
-      a = acc_norm(a);
-      b = acc_norm(b);
-      ctl->check_num = make_float2(a.h, a.l);
-      ctl->check_den = make_float2(b.h, b.l);
-      ws.out2[0] = make_float2(a.h, a.l);
-      ws.out2[1] = make_float2(b.h, b.l);
-      ctl->ticket_r = 0u;
+      fold_check(ws);
     }
   }
 }
@@ -1267,12 +1321,32 @@ __global__ void __launch_bounds__(kThreads) k_rollout(Ws ws, int kcols, void* ou
 __device__ __forceinline__ double stored_to_double(float2 v) { return (double)v.x + (double)v.y; }
 __device__ __forceinline__ double stored_to_double(float v) { return (double)v; }
 
+// fold of the first snapshot's per-block sums of squares (one thread)
+__device__ void fold_first(const Ws& ws) {
+  Ctl* ctl = ws.ctl;
+  double tot = 0.0;
+  for (int b = 0; b < ws.gridA; ++b) tot += __ldcg(reinterpret_cast<const double*>(ws.part) + b);
+  if (!isfinite(tot)) atomicOr(&ctl->status, DEV_NONFINITE);
+  ws.st[ctl->cur].hdr->cn2 = f2_of(dd_from_double(tot));
+  ctl->ticket_a = 0u;
+}
+
+__global__ void __launch_bounds__(32) k_fold_first(Ws ws) {
+  if (threadIdx.x == 0) fold_first(ws);
+}
+
+// ||u^0||^2 over this CTA's row block (logical CTA cta0 + blockIdx.x), in FP64: N FMAs once
+// per stream, negligible
 template <typename stored_t>
-__global__ void __launch_bounds__(kThreads) k_first(Ws ws) {
+__global__ void __launch_bounds__(kThreads) k_first(Ws ws, int cta0, int fold) {
   Ctl* ctl = ws.ctl;
   const stored_t* c = reinterpret_cast<const stored_t*>(ws.cbuf[ctl->cur_c]);
-  double acc = 0.0;  // N FP64 FMAs once per stream: negligible
-  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < ws.n; i += (int64_t)gridDim.x * kThreads) {
+  const int blk = cta0 + blockIdx.x;
+  int64_t t0, t1;
+  block_tiles64(ws, blk, t0, t1);
+  const int64_t i1 = t1 * kTile < ws.n ? t1 * kTile : ws.n;
+  double acc = 0.0;
+  for (int64_t i = t0 * kTile + threadIdx.x; i < i1; i += kThreads) {
     const double v = stored_to_double(c[i]);
     acc = fma(v, v, acc);
   }
@@ -1283,21 +1357,17 @@ __global__ void __launch_bounds__(kThreads) k_first(Ws ws) {
   if (threadIdx.x == 0) {
     double b = 0.0;
     for (int w = 0; w < kThreads / 32; ++w) b += wsum[w];
-    ws.part[blockIdx.x] = make_float2(0.f, 0.f);
-    reinterpret_cast<double*>(ws.part)[blockIdx.x] = b;
+    reinterpret_cast<double*>(ws.part)[blk] = b;
   }
-  __shared__ unsigned ticket;
   __threadfence();
+  if (!fold) return;
+  __shared__ unsigned ticket;
   __syncthreads();
   if (threadIdx.x == 0) ticket = atomicAdd(&ctl->ticket_a, 1u);
   __syncthreads();
-  if (ticket != (unsigned)(gridDim.x - 1) || threadIdx.x != 0) return;
+  if (ticket != gridDim.x - 1 || threadIdx.x != 0) return;
   __threadfence();
-  double tot = 0.0;
-  for (int b = 0; b < (int)gridDim.x; ++b) tot += __ldcg(reinterpret_cast<const double*>(ws.part) + b);
-  if (!isfinite(tot)) atomicOr(&ctl->status, DEV_NONFINITE);
-  ws.st[ctl->cur].hdr->cn2 = f2_of(dd_from_double(tot));
-  ctl->ticket_a = 0u;
+  fold_first(ws);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1381,17 +1451,40 @@ cudaError_t prepare_tall(const Ws& ws) {
   }
 }
 
+// shard g of a run split over ws.shards row shards: row blocks [first, first + count)
+static void shard_blocks(const Ws& ws, int g, int& first, int& count) {
+  first = (int)((int64_t)g * ws.gridA / ws.shards);
+  count = (int)((int64_t)(g + 1) * ws.gridA / ws.shards) - first;
+}
+
+// One launch over every row block (its last CTA folds), or one launch per row shard and
+// then the fold: the sharded run's exchange of per-block partials
+template <typename K, typename F>
+static cudaError_t launch_blocks(K kern, F fold_kern, int threads, int fold_threads, int smem, const Ws& ws,
+                                 cudaStream_t s) {
+  if (ws.shards <= 1) return launch_dependent(kern, ws.gridA, threads, smem, s, ws, 0, 1);
+  for (int g = 0; g < ws.shards; ++g) {
+    int first, count;
+    shard_blocks(ws, g, first, count);
+    const cudaError_t e = launch_dependent(kern, count, threads, smem, s, ws, first, 0);
+    if (e != cudaSuccess) return e;
+  }
+  return launch_dependent(fold_kern, 1, fold_threads, 0, s, ws);
+}
+
 cudaError_t launch_pass_a(const Ws& ws, cudaStream_t s) {
   const int sm = smem_a(ws.prec, ws.cap);
   switch (ws.prec) {
     case ST_DD:
-      return launch_dependent(k_pass_a<ST_DD>, ws.gridPA, kThreadsA, sm, s, ws);
+      return launch_blocks(k_pass_a<ST_DD>, &k_fold_a, kThreadsA, kThreadsA, sm, ws, s);
     case ST_F32:
-      return launch_dependent(k_pass_a<ST_F32>, ws.gridPA, kThreadsA, sm, s, ws);
+      return launch_blocks(k_pass_a<ST_F32>, &k_fold_a, kThreadsA, kThreadsA, sm, ws, s);
     default:
-      return launch_dependent(k_pass_a<ST_BF16>, ws.gridPA, kThreadsA, sm, s, ws);
+      return launch_blocks(k_pass_a<ST_BF16>, &k_fold_a, kThreadsA, kThreadsA, sm, ws, s);
   }
 }
+
+int launches_per_reduction(const Ws& ws) { return ws.shards <= 1 ? 1 : ws.shards + 1; }
 
 template <bool FLUSH>
 static cudaError_t pass_b_launch(const Ws& ws, cudaStream_t s) {
@@ -1410,12 +1503,8 @@ cudaError_t launch_pass_b(const Ws& ws, cudaStream_t s) { return pass_b_launch<f
 cudaError_t launch_flush(const Ws& ws, cudaStream_t s) { return pass_b_launch<true>(ws, s); }
 
 cudaError_t launch_first(const Ws& ws, cudaStream_t s) {
-  const int grid = 64;  // the partial buffer always holds at least 64 rows
-  if (ws.prec == ST_DD)
-    k_first<float2><<<grid, kThreads, 0, s>>>(ws);
-  else
-    k_first<float><<<grid, kThreads, 0, s>>>(ws);
-  return cudaGetLastError();
+  if (ws.prec == ST_DD) return launch_blocks(k_first<float2>, &k_fold_first, kThreads, 32, 0, ws, s);
+  return launch_blocks(k_first<float>, &k_fold_first, kThreads, 32, 0, ws, s);
 }
 
 // Copy a caller's double snapshot into the workspace as float pairs (all SMs; the only
@@ -1462,14 +1551,30 @@ cudaError_t launch_rollout(const Ws& ws, const double*, int kcols, void* out, in
   const int sm = smem_r(ws.prec, ws.cap);
   switch (ws.prec) {
     case ST_DD:
-      k_rollout<ST_DD, false><<<ws.gridA, kThreads, sm, s>>>(ws, kcols, out, ld);
+      k_rollout<ST_DD, false><<<ws.gridA, kThreads, sm, s>>>(ws, kcols, out, ld, 0, 1);
       break;
     case ST_F32:
-      k_rollout<ST_F32, false><<<ws.gridA, kThreads, sm, s>>>(ws, kcols, out, ld);
+      k_rollout<ST_F32, false><<<ws.gridA, kThreads, sm, s>>>(ws, kcols, out, ld, 0, 1);
       break;
     default:
-      k_rollout<ST_BF16, false><<<ws.gridA, kThreads, sm, s>>>(ws, kcols, out, ld);
+      k_rollout<ST_BF16, false><<<ws.gridA, kThreads, sm, s>>>(ws, kcols, out, ld, 0, 1);
   }
+  return cudaGetLastError();
+}
+
+// the check: the kernel's grid, block and shared memory as the rollout's, with kcols = 1
+template <int ST>
+static cudaError_t check_blocks(const Ws& ws, int sm, cudaStream_t s) {
+  if (ws.shards <= 1) {
+    k_rollout<ST, true><<<ws.gridA, kThreads, sm, s>>>(ws, 1, nullptr, 0, 0, 1);
+    return cudaGetLastError();
+  }
+  for (int g = 0; g < ws.shards; ++g) {
+    int first, count;
+    shard_blocks(ws, g, first, count);
+    k_rollout<ST, true><<<count, kThreads, sm, s>>>(ws, 1, nullptr, 0, first, 0);
+  }
+  k_fold_check<<<1, 32, 0, s>>>(ws);
   return cudaGetLastError();
 }
 
@@ -1477,15 +1582,12 @@ cudaError_t launch_check(const Ws& ws, cudaStream_t s) {
   const int sm = smem_r(ws.prec, ws.cap);
   switch (ws.prec) {
     case ST_DD:
-      k_rollout<ST_DD, true><<<ws.gridA, kThreads, sm, s>>>(ws, 1, nullptr, 0);
-      break;
+      return check_blocks<ST_DD>(ws, sm, s);
     case ST_F32:
-      k_rollout<ST_F32, true><<<ws.gridA, kThreads, sm, s>>>(ws, 1, nullptr, 0);
-      break;
+      return check_blocks<ST_F32>(ws, sm, s);
     default:
-      k_rollout<ST_BF16, true><<<ws.gridA, kThreads, sm, s>>>(ws, 1, nullptr, 0);
+      return check_blocks<ST_BF16>(ws, sm, s);
   }
-  return cudaGetLastError();
 }
 
 }  // namespace odmd

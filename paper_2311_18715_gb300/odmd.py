@@ -242,6 +242,18 @@ class OnlineDMD:
         self._ck(self._lib.odmd_get_counts(self._h, C.byref(s), C.byref(c)))
         return int(s.value), int(c.value)
 
+    def set_row_shards(self, shards: int) -> None:
+        """odmd_set_row_shards: run the passes that end in a reduction as `shards` row shards."""
+        self._ck(self._lib.odmd_set_row_shards(self._h, int(shards)))
+
+    def row_blocks(self) -> list[int]:
+        """odmd_get_row_blocks: the B + 1 row boundaries of the row blocks."""
+        b = C.c_int32()
+        self._ck(self._lib.odmd_get_row_blocks(self._h, C.byref(b), None, 0))
+        rows = (C.c_int64 * (b.value + 1))()
+        self._ck(self._lib.odmd_get_row_blocks(self._h, C.byref(b), rows, b.value + 1))
+        return [int(x) for x in rows]
+
     def profile(self, enable: bool = True) -> None:
         """Start (or stop) per-kernel-class event timing; resets the accumulators."""
         self._ck(self._lib.odmd_profile_enable(self._h, 1 if enable else 0))
