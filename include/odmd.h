@@ -60,7 +60,8 @@ typedef enum {
  *   ODMD_FP32: basis float, snapshots and outputs float.
  *   ODMD_BF16: reserved; rejected with ODMD_ERR_ARG (a bfloat16 basis cannot stay
  *              orthonormal to the accuracy the rank-1 update assumes).
- * The small solves (core SVD, operator update, eigensolve) are FP64 in every mode. */
+ * In every mode the core SVD and the operator update of an update are FP64; the eigensolve
+ * and the modal coefficients of predictions are double-float (48-bit significand). */
 typedef enum { ODMD_FP64 = 0, ODMD_FP32 = 1, ODMD_BF16 = 2 } odmd_precision;
 
 typedef struct {
@@ -74,8 +75,14 @@ typedef struct {
   odmd_precision prec;  /* basis storage, see above */
   int32_t refine_every; /* refine orthogonality after every this many pairs (0: never);
                            see odmd_refine */
-  uint32_t flags;       /* reserved, must be 0 */
+  uint32_t flags;       /* 0, or ODMD_CUDA_CORES; other bits are rejected */
 } odmd_config;
+
+/* flags: keep multi-horizon rollouts on the CUDA cores.  By default a prediction of 8 to 64
+ * states with FP64 storage and at most 64 basis columns (r_max + slack <= 64) runs as an
+ * exact split product on the tensor cores; this flag keeps the CUDA-core path (the same
+ * values to the double-float rounding level). */
+#define ODMD_CUDA_CORES 1u
 
 /* Fill *cfg with the defaults for a stream of length n and rank cap r_max:
  * slack 16, trunc_tol 1e-10, check_tol 1e-5, ODMD_FP64, refine_every 0, flags 0. */

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libodmd.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["api.cu", "tall.cu", "small.cu", "core.cu", "check_static.cu", "refine.cu", "residual.cu", "pairs.cu", "tc_selftest.cu"]
+SOURCES = ["api.cu", "tall.cu", "small.cu", "core.cu", "check_static.cu", "refine.cu", "residual.cu", "pairs.cu", "tc_selftest.cu", "split.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

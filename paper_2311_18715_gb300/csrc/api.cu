@@ -57,6 +57,8 @@ struct odmd_instance {
   UpdGraph ug[2][2];
   cudaStream_t cap = nullptr;
   bool use_graphs = true;
+  bool use_tc = true;   // multi-horizon rollouts on the tensor cores where split.cu takes them
+  int sms = 0;          // streaming multiprocessors of the handle's device
   // odmd_update_host: two staging slots in the workspace, filled on a copy stream of their
   // own; a slot is refilled only after the update that read it
   unsigned char* stage[2] = {nullptr, nullptr};
@@ -119,8 +121,8 @@ odmd_status check_cfg(const odmd_config* c, std::string& why) {
     why = "ODMD_BF16 basis storage is not supported by the rank-1 update; use ODMD_FP32";
     return ODMD_ERR_ARG;
   }
-  if (c->flags != 0) {
-    why = "flags must be 0";
+  if ((c->flags & ~ODMD_CUDA_CORES) != 0) {
+    why = "unknown flags (only ODMD_CUDA_CORES is defined)";
     return ODMD_ERR_ARG;
   }
   if (c->refine_every < 0) {
@@ -611,6 +613,9 @@ odmd_status odmd_create(const odmd_config* cfg, void* workspace_dev, size_t byte
   if (e == cudaSuccess) e = prepare_tall(h->ws);
   if (e == cudaSuccess) e = prepare_small(h->ws);
   if (e == cudaSuccess) e = prepare_core();
+  if (e == cudaSuccess) e = prepare_split(h->ws);
+  h->sms = sms;
+  h->use_tc = (cfg->flags & ODMD_CUDA_CORES) == 0;
   if (e == cudaSuccess && cfg->refine_every > 0) e = prepare_refine();
   if (e == cudaSuccess) e = cudaMemsetAsync(workspace_dev, 0, L.total, h->stream);
   if (e == cudaSuccess) {
@@ -732,9 +737,13 @@ odmd_status odmd_predict(odmd_t h, const double* t_host, int32_t k, void* out_de
     const int kk = (k - j0) < kRollK ? (k - j0) : kRollK;
     if (odmd_status s = launch_coefficients(h, t_host + j0, kk, by_powers)) return s;
     ProfScope ps(h, ODMD_K_ROLLOUT, 1);
-    CK(h, launch_rollout(h->ws, nullptr, kk, static_cast<unsigned char*>(out_dev) + (size_t)j0 * ld * vs, ld, 0,
-                         h->stream),
-       "rollout launch");
+    unsigned char* o = static_cast<unsigned char*>(out_dev) + (size_t)j0 * ld * vs;
+    if (h->use_tc && split_rollout_ok(h->ws, kk)) {
+      // eight or more states: the contraction on the tensor cores (split.cu)
+      CK(h, launch_split_rollout(h->ws, kk, reinterpret_cast<double*>(o), ld, h->sms, h->stream), "rollout launch");
+    } else {
+      CK(h, launch_rollout(h->ws, nullptr, kk, o, ld, 0, h->stream), "rollout launch");
+    }
   }
   return ODMD_OK;
 }

@@ -455,6 +455,9 @@ const void* ingest_kernel(int prec);  // the kernel launch_ingest uses (graph no
 cudaError_t prepare_tall(const Ws& ws);
 cudaError_t prepare_small(const Ws& ws);
 cudaError_t prepare_core();  // shared-memory limits of the FP64 small solves of the update
+bool split_rollout_ok(const Ws& ws, int kcols);       // the tensor-core rollout takes this call
+cudaError_t prepare_split(const Ws& ws);
+cudaError_t launch_split_rollout(const Ws& ws, int kcols, double* out, int64_t ld, int sms, cudaStream_t s);
 cudaError_t launch_rollout(const Ws& ws, const double* coef_src, int kcols, void* out, int64_t ld,
                            int coef_mode, cudaStream_t s);
 cudaError_t launch_check(const Ws& ws, cudaStream_t s);
