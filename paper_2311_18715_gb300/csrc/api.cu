@@ -211,7 +211,7 @@ void carve(Ws& ws, const Layout& L, unsigned char* base, const odmd_config& c, i
     d += L.rmax;
     s.M = reinterpret_cast<double*>(d);
     d += (size_t)L.rmax * L.rmax;
-    s.Q = d;
+    s.Q = reinterpret_cast<double*>(d);
     d += (size_t)qld * L.rmax;
     s.a = d;
     d += qld;
@@ -434,7 +434,8 @@ odmd_status build_update_graph(odmd_t h, int par, int prof) {
   if (e == cudaSuccess) e = launch_small(h->ws, h->cap);
   if (e == cudaSuccess && prof) e = cudaEventRecordWithFlags(ph[3], h->cap, cudaEventRecordExternal);
   if (e == cudaSuccess && prof) e = cudaEventRecordWithFlags(ph[4], h->cap, cudaEventRecordExternal);
-  if (e == cudaSuccess) e = launch_pass_b(h->ws, h->cap);
+  if (e == cudaSuccess)
+    e = (h->use_tc && split_compact_ok(h->ws)) ? launch_split_compact(h->ws, h->sms, h->cap) : launch_pass_b(h->ws, h->cap);
   if (e == cudaSuccess && prof) e = cudaEventRecordWithFlags(ph[5], h->cap, cudaEventRecordExternal);
   cudaError_t e2 = cudaStreamEndCapture(h->cap, &graph);
   if (e == cudaSuccess) e = e2;
@@ -709,7 +710,9 @@ odmd_status odmd_update(odmd_t h, const void* x_dev) {
     }
     {
       ProfScope ps(h, ODMD_K_PASS_B, 1);
-      CK(h, launch_pass_b(h->ws, h->stream), "pass B launch");
+      CK(h, (h->use_tc && split_compact_ok(h->ws)) ? launch_split_compact(h->ws, h->sms, h->stream)
+                                                    : launch_pass_b(h->ws, h->stream),
+         "pass B launch");
     }
   }
   h->cur_h ^= 1;

@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(Ws ws) {
   __shared__ int defl[kMaxN];
   const float2* red = ws.sm.red;
 
-  for (int idx = tid; idx < r * qld; idx += kPrepThreads) sQ[idx] = dd2d(st.Q[idx]);
+  for (int idx = tid; idx < r * qld; idx += kPrepThreads) sQ[idx] = st.Q[idx];
   for (int i = tid; i < r0; i += kPrepThreads) {
     ac[i] = dd2d(st.a[i]) + dd2d(red[i]);
     yx[i] = dd2d(red[r0 + i]);
@@ -733,7 +733,7 @@ __device__ void apply_column(const Ws& ws, int j, const StateBuf& st, const Stat
     const int i = (base + tid) >> 2, sub = tid & 3;
     double acc = 0.0;
     if (i < r0)
-      for (int k = sub; k < r; k += 4) acc = fma(dd2d(st.Q[(size_t)k * qld + i]), u[k], acc);
+      for (int k = sub; k < r; k += 4) acc = fma(st.Q[(size_t)k * qld + i], u[k], acc);
     acc = group4_sum_d(acc);
     if (i < r0e && sub == 0) qcol[i] = fma(ws.sm.qn[i], u[r], acc);
   }
@@ -752,9 +752,9 @@ __device__ void apply_column(const Ws& ws, int j, const StateBuf& st, const Stat
   if (compact) {
     for (int i = tid; i < r0e; i += kApplyThreads) ws.sm.QB[(size_t)j * qld + i] = d2f2(qcol[i]);
     for (int i = tid; i < rnew; i += kApplyThreads)
-      nx.Q[(size_t)j * qld + i] = make_float2(i == j ? 1.f : 0.f, 0.f);
+      nx.Q[(size_t)j * qld + i] = i == j ? 1.0 : 0.0;
   } else {
-    for (int i = tid; i < r0e; i += kApplyThreads) nx.Q[(size_t)j * qld + i] = d2f2(qcol[i]);
+    for (int i = tid; i < r0e; i += kApplyThreads) nx.Q[(size_t)j * qld + i] = qcol[i];
   }
   // r_first', r_last', S', a' (compaction)  -- warp 0
   if (tid < 32) {

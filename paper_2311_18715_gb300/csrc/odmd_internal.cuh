@@ -45,8 +45,8 @@ enum : int {
 enum : int { PB_NONE = 0, PB_APPEND = 1, PB_COMPACT = 2 };
 
 // The small state that the update carries from one snapshot to the next (S, the rows of R,
-// M) and the scratch of the core SVD are IEEE doubles; the factor Q and the vectors the tall
-// passes read are double-float pairs (float2: hi, lo; see dd.cuh).
+// M, the factor Q of L = L0 Q) and the scratch of the core SVD are IEEE doubles; the vectors
+// the tall passes read are double-float pairs (float2: hi, lo; see dd.cuh).
 
 // Committed small state (two copies, selected by Ctl::cur).
 struct StateHdr {
@@ -66,7 +66,7 @@ struct StateBuf {
   double* rf;   // r_max   first row of R
   double* rl;   // r_max   last row of R
   double* M;    // r_max x r_max, column-major, ld = r_max   (M = L^T U^+ R)
-  float2* Q;    // (cap+1) x r_max, column-major, ld = cap+1  (L = L0 Q)
+  double* Q;    // (cap+1) x r_max, column-major, ld = cap+1  (L = L0 Q), FP64
   float2* a;    // cap+1   L0^T c
   float2* ps;   // cap+1   coefficients s of the pending column: (e - L0 s) / rho0
 };
@@ -458,6 +458,8 @@ cudaError_t prepare_core();  // shared-memory limits of the FP64 small solves of
 bool split_rollout_ok(const Ws& ws, int kcols);       // the tensor-core rollout takes this call
 cudaError_t prepare_split(const Ws& ws);
 cudaError_t launch_split_rollout(const Ws& ws, int kcols, double* out, int64_t ld, int sms, cudaStream_t s);
+bool split_compact_ok(const Ws& ws);               // compaction of this handle on the tensor cores
+cudaError_t launch_split_compact(const Ws& ws, int sms, cudaStream_t s);
 cudaError_t launch_rollout(const Ws& ws, const double* coef_src, int kcols, void* out, int64_t ld,
                            int coef_mode, cudaStream_t s);
 cudaError_t launch_check(const Ws& ws, cudaStream_t s);

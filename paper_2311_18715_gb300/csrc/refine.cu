@@ -281,14 +281,14 @@ __global__ void __launch_bounds__(128) k_refine_c(Ws ws, int cur) {
   __shared__ float2 t[kMaxCap];
   for (int a = tid; a < r0; a += 128) {
     Acc s = acc_zero();
-    for (int b = 0; b < r0; ++b) acc_fma_k(s, S.G[(size_t)b * cap + a], st.Q[(size_t)j * qld + b], b);
+    for (int b = 0; b < r0; ++b) acc_fma_k(s, S.G[(size_t)b * cap + a], d2f2(st.Q[(size_t)j * qld + b]), b);
     s = acc_norm(s);
     t[a] = make_float2(s.h, s.l);
   }
   __syncthreads();
   for (int i = tid; i < r; i += 128) {
     Acc s = acc_zero();
-    for (int a = 0; a < r0; ++a) acc_fma_k(s, st.Q[(size_t)i * qld + a], t[a], a);
+    for (int a = 0; a < r0; ++a) acc_fma_k(s, d2f2(st.Q[(size_t)i * qld + a]), t[a], a);
     s = acc_norm(s);
     S.C[(size_t)j * ws.rmax + i] = make_float2(s.h, s.l);
   }
@@ -539,9 +539,9 @@ __global__ void __launch_bounds__(128) k_refine_out(Ws ws, int cur) {
     }
     for (int a = tid; a < r0; a += 128) {
       Acc s = acc_zero();
-      for (int k = 0; k < r; ++k) acc_fma_k(s, st.Q[(size_t)k * qld + a], S.W[(size_t)pj * rm + k], k);
+      for (int k = 0; k < r; ++k) acc_fma_k(s, d2f2(st.Q[(size_t)k * qld + a]), S.W[(size_t)pj * rm + k], k);
       s = acc_norm(s);
-      nx.Q[(size_t)j * qld + a] = make_float2(s.h, s.l);
+      nx.Q[(size_t)j * qld + a] = (double)s.h + (double)s.l;
     }
     if (j == 0) {
       for (int jj = tid; jj < r; jj += 128) {

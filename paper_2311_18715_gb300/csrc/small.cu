@@ -715,7 +715,7 @@ __global__ void __launch_bounds__(64) k_coef(Ws ws, TArr ts, int k) {
   __syncthreads();
   for (int i = tid; i < r0; i += 64) {
     dd acc = dzero();
-    for (int l = 0; l < r; ++l) acc = dd_fma(LD(st.Q, (size_t)l * qld + i), LD(c, l), acc);
+    for (int l = 0; l < r; ++l) acc = dd_fma(dd_from_double(st.Q[(size_t)l * qld + i]), LD(c, l), acc);
     ws.sm.coef[(size_t)j * qld + i] = f2_of(acc);
   }
 }
@@ -835,7 +835,8 @@ __global__ void __launch_bounds__(kPowThreads) k_coef_pow(Ws ws, TArr ts, TOrd o
     const int i = e % r0, j = e / r0;
     dd acc = dzero();
     if (e < r0 * k)
-      for (int l = sub; l < r; l += 4) acc = dd_fma(LD(st.Q, (size_t)l * qld + i), LD(S.C, (size_t)j * kMaxR + l), acc);
+      for (int l = sub; l < r; l += 4)
+        acc = dd_fma(dd_from_double(st.Q[(size_t)l * qld + i]), LD(S.C, (size_t)j * kMaxR + l), acc);
     acc = group4_sum(acc);
     if (e < r0 * k && sub == 0) ws.sm.coef[(size_t)j * qld + i] = f2_of(acc);
   }
@@ -860,7 +861,7 @@ __global__ void __launch_bounds__(64) k_basis_coef(Ws ws) {
   const int r = st.hdr->r, r0 = st.hdr->r0, qld = ws.cap + 1;
   const int j = blockIdx.x;
   if (j >= r) return;
-  for (int i = threadIdx.x; i < r0; i += 64) ws.sm.coef[(size_t)j * qld + i] = st.Q[(size_t)j * qld + i];
+  for (int i = threadIdx.x; i < r0; i += 64) ws.sm.coef[(size_t)j * qld + i] = d2f2(st.Q[(size_t)j * qld + i]);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -1,7 +1,11 @@
-// Multi-horizon rollout X = L0 C on the tensor cores (Sec. 2.3: u(t) = Phi Lambda^t b for
-// many t at once is a tall N x r0 basis times a small r0 x k coefficient block), exact to the
-// double-float level through a split of both operands into 7-bit digits (Ozaki's scheme:
-// an error-free splitting into slices whose products a lower-precision unit sums exactly).
+// Tall x small products of the double-float basis on the tensor cores, exact to the
+// double-float level through a split of both operands into 7-bit digits (Ozaki's scheme: an
+// error-free splitting into slices whose products a lower-precision unit sums exactly):
+//   rollout     X = L0 C: u(t) = Phi Lambda^t b for many t at once (Sec. 2.3) is the tall
+//               N x r0 basis times a small r0 x k coefficient block; X in doubles;
+//   compaction  L0 <- [L0 j0] Q_B of the product-form update (Sec. 2.3, Brand's rank-1
+//               append kept as L = L0 Q): the new column j0 = (e - L0 s) / rho0 is formed per
+//               row from the stored residual, and the product is written back in place.
 //
 // Each row i of L0 (double-float hi + lo) is written on its own power-of-two grid,
 // a_ik = sum_{s=1..7} d_iks 2^(e_i - 7 s), and each column j of C on its own,
@@ -49,7 +53,8 @@ static_assert(kGroups * kNJ <= (int)kTmemCols, "seven accumulators fit the tenso
 // a group sums at most 7 digit pairs over K <= 64 columns of products |d d'| <= 2^14
 static_assert(7 * kMaxK * (1 << 14) < (1 << 24), "group sums stay below 2^24");
 
-__host__ __device__ inline int stage_bytes(int rs) { return ((2 * kTM * rs + 1023) / 1024) * 1024; }
+// staging buffer: the two basis planes of a tile, then the tile's stored residual (8 bytes a row)
+__host__ __device__ inline int stage_bytes(int rs) { return ((2 * kTM * rs + kTM * 8 + 1023) / 1024) * 1024; }
 __host__ __device__ inline int smem_bytes(int rs) { return stage_bytes(rs) + kSlices * kASlice + kSlices * kBSlice; }
 
 // exponent e with |v| < 2^e for every v of a set with maximum mx (0 for mx = 0)
@@ -75,37 +80,75 @@ __device__ __forceinline__ void digits7(float h, float l, int e, uint16_t (&d)[k
   }
 }
 
-__device__ __forceinline__ void issue_tile(const Ws& ws, unsigned char* stage, int rs, int64_t tile, uint64_t* bar) {
+// the tile's rows of both planes (and of the stored residual e when `with_e`) into the stage;
+// npad is a multiple of 64 rows, so every copy is a whole number of 16-byte units
+__device__ __forceinline__ void issue_tile(const Ws& ws, unsigned char* stage, int rs, int64_t tile, bool with_e,
+                                           uint64_t* bar) {
   const int64_t row0 = tile * kTM;
   const int64_t rows = (ws.npad - row0) < kTM ? (ws.npad - row0) : kTM;
   const uint32_t bytes = (uint32_t)(rows * rs);
-  mbar_arrive_expect_tx(bar, 2 * bytes);
+  mbar_arrive_expect_tx(bar, 2 * bytes + (with_e ? (uint32_t)(rows * 8) : 0u));
   bulk_g2s(stage, reinterpret_cast<const unsigned char*>(ws.Lh) + row0 * rs, bytes, bar);
   bulk_g2s(stage + (size_t)kTM * rs, reinterpret_cast<const unsigned char*>(ws.Ll) + row0 * rs, bytes, bar);
+  if (with_e) bulk_g2s(stage + (size_t)2 * kTM * rs, ws.ebuf + row0, (uint32_t)(rows * 8), bar);
 }
 
-__global__ void __launch_bounds__(kThreadsS, 1) k_split_rollout(Ws ws, int kcols, double* out, int64_t ld) {
+// COMPACT = false: X[:, j] = L0[:, :r0] coef[:, j] for j < kcols, X column-major doubles.
+// COMPACT = true: when the update in flight compacts, L0[:, :rnew] <- [L0[:, :r0] j0] Q_B in
+// place (the tile's rows are staged before they are overwritten, by the CTA that read them).
+template <bool COMPACT>
+__global__ void __launch_bounds__(kThreadsS, 1) k_split(Ws ws, int kcols, double* out, int64_t ld) {
+  if constexpr (COMPACT) {
+    pdl_wait();
+    if (ws.ctl->mode != PB_COMPACT) return;  // most updates: nothing to do
+  }
   extern __shared__ __align__(1024) unsigned char sp[];
   Ctl* ctl = ws.ctl;
-  const StateBuf st = ws.st[ctl->cur];
-  const int r0 = st.hdr->r0, qld = ws.cap + 1;
+  const int qld = ws.cap + 1;
+  // K: columns of the tall operand (j0 last when appended), J: output columns
+  int r0, K, J, append = 0;
+  const float2* bsrc;  // the small operand, column j at bsrc + j qld
+  if constexpr (COMPACT) {
+    append = ctl->append;
+    r0 = ctl->r0e - append;
+    K = r0 + append;
+    J = ctl->rnew;
+    bsrc = ws.sm.QB;
+  } else {
+    r0 = ws.st[ctl->cur].hdr->r0;
+    K = r0;
+    J = kcols;
+    bsrc = ws.sm.coef;
+  }
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int rs = ws.ldg * 4;
-  const int kpad = (r0 + kKC - 1) / kKC * kKC;
+  const int kpad = (K + kKC - 1) / kKC * kKC;
   const int nchunk = kpad / kKC;
   unsigned char* stage = sp;
   unsigned char* adig = sp + stage_bytes(rs);
   unsigned char* bdig = adig + kSlices * kASlice;
   __shared__ int fexp[kNJ];
   __shared__ int erow[kTM];
+  __shared__ float jh[kTM], jl[kTM];           // the new column j0 of the tile (compaction)
+  __shared__ float sh_s[kMaxK], sl_s[kMaxK];   // its coefficients s (compaction)
   __shared__ __align__(8) uint64_t bar_tma, bar_mma;
   __shared__ uint32_t tmem_slot;
+  const bool with_e = COMPACT && append;
+  dd inv = dd{0.f, 0.f};
+  if (with_e) {
+    inv = dd_from_double(1.0 / ctl->rho0);
+    for (int k = tid; k < kMaxK; k += kThreadsS) {
+      const float2 v = k < r0 ? ws.sm.red[k] : make_float2(0.f, 0.f);
+      sh_s[k] = v.x;
+      sl_s[k] = v.y;
+    }
+  }
 
-  // ---- digits of C: column j of the coefficients is row j of the B operand (K-major)
+  // ---- digits of the small operand: its column j is row j of the B operand (K-major)
   for (int j = warp; j < kNJ; j += kThreadsS / 32) {
     float mx = 0.f;
-    if (j < kcols)
-      for (int k = lane; k < r0; k += 32) mx = fmaxf(mx, fabsf(ws.sm.coef[(size_t)j * qld + k].x));
+    if (j < J)
+      for (int k = lane; k < K; k += 32) mx = fmaxf(mx, fabsf(bsrc[(size_t)j * qld + k].x));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (lane == 0) fexp[j] = grid_exp(mx);
@@ -114,8 +157,8 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split_rollout(Ws ws, int kcols
   for (int o = tid; o < kNJ * kMaxK; o += kThreadsS) {
     const int j = o / kMaxK, k = o % kMaxK;
     float h = 0.f, l = 0.f;
-    if (j < kcols && k < r0) {
-      const float2 q = ws.sm.coef[(size_t)j * qld + k];
+    if (j < J && k < K) {
+      const float2 q = bsrc[(size_t)j * qld + k];
       h = q.x;
       l = q.y;
     }
@@ -139,7 +182,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split_rollout(Ws ws, int kcols
   const int64_t ntiles = (ws.n + kTM - 1) / kTM;
   const int G = gridDim.x;
   const int my_tiles = (int)((ntiles - blockIdx.x + G - 1) / G);
-  if (tid == 0 && my_tiles > 0) issue_tile(ws, stage, rs, blockIdx.x, &bar_tma);
+  if (tid == 0 && my_tiles > 0) issue_tile(ws, stage, rs, blockIdx.x, with_e, &bar_tma);
   const uint32_t idesc = tc::instr_desc_bf16_f32(kTM, kNJ);
   uint32_t par_tma = 0, par_mma = 0;
   // work in flight that a timeout must still wait for (the same in every thread)
@@ -159,12 +202,31 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split_rollout(Ws ws, int kcols
     }
     par_tma ^= 1u;
     tma_out = false;
-    // the row's exponent: max |hi| over its r0 columns, half of them per thread
     const bool live = row0 + row < ws.n;
+    if (with_e) {
+      // j0 = (e - L0[:, :r0] s) / rho0 for this row, half of the dot per thread
+      Acc d = acc_zero();
+      if (live)
+        for (int k = half; k < r0; k += 2) acc_fma(d, sh[k], sl[k], sh_s[k], sl_s[k]);
+      acc_add(d, __shfl_xor_sync(0xffffffffu, d.h, 1), __shfl_xor_sync(0xffffffffu, d.l, 1));
+      if (half == 0) {
+        const float2 ev = reinterpret_cast<const float2*>(stage + (size_t)2 * kTM * rs)[row];
+        Acc e = Acc{ev.x, ev.y};
+        acc_add(e, -d.h, -d.l);
+        e = acc_norm(e);
+        Acc j = acc_zero();
+        acc_fma(j, e.h, e.l, inv.h, inv.l);
+        j = acc_norm(j);
+        jh[row] = live ? j.h : 0.f;
+        jl[row] = live ? j.l : 0.f;
+      }
+      __syncwarp();
+    }
+    // the row's exponent: max |hi| over its K columns, half of them per thread
     {
       float mx = 0.f;
       if (live)
-        for (int k = half; k < r0; k += 2) mx = fmaxf(mx, fabsf(sh[k]));
+        for (int k = half; k < K; k += 2) mx = fmaxf(mx, fabsf(k < r0 ? sh[k] : jh[row]));
       mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
       if (half == 0) erow[row] = grid_exp(mx);
     }
@@ -181,6 +243,9 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split_rollout(Ws ws, int kcols
           if (live && k < r0) {
             h = sh[k];
             l = sl[k];
+          } else if (live && k < K) {  // the new column (compaction)
+            h = jh[row];
+            l = jl[row];
           }
           uint16_t d[kSlices];
           digits7(h, l, my_e, d);
@@ -196,7 +261,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split_rollout(Ws ws, int kcols
       mma_out = true;
       if (tid == 0) {
         // the staging buffer is free once the tile's last digits are formed: next tile
-        if (last_digits && li + 1 < my_tiles) issue_tile(ws, stage, rs, tile + G, &bar_tma);
+        if (last_digits && li + 1 < my_tiles) issue_tile(ws, stage, rs, tile + G, with_e, &bar_tma);
         tc::fence_after_sync();
         for (int cc = c0; cc < c0 + 2 && cc < nchunk; ++cc) {
           const uint32_t aoff = (uint32_t)((cc - c0) * 2 * tc::kCoreBytes);
@@ -245,16 +310,47 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split_rollout(Ws ws, int kcols
                        : "r"(taddr));
         }
         tc::tmem_ld_wait();
+        if (orow >= ws.n || jb + c8 >= J) continue;
+        float vh[8], vl[8];
+        int sc[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-          const int j = jb + c8 + u;
-          if (j >= kcols || orow >= ws.n) continue;
           // smallest group first; every term G_g 2^(56 - 7 g) is an exact float
-          dd sum = dd{ldexpf(__uint_as_float(g[kGroups - 1][u]), 0), 0.f};
+          dd sum = dd{__uint_as_float(g[kGroups - 1][u]), 0.f};
 #pragma unroll
-          for (int q = kGroups - 2; q >= 0; --q) sum = sum + dd{ldexpf(__uint_as_float(g[q][u]), 7 * (kGroups - 1 - q)), 0.f};
-          const int sc = er + fexp[j] - 56;
-          out[(size_t)j * ld + orow] = ldexp((double)sum.h, sc) + ldexp((double)sum.l, sc);
+          for (int q = kGroups - 2; q >= 0; --q)
+            sum = sum + dd{ldexpf(__uint_as_float(g[q][u]), 7 * (kGroups - 1 - q)), 0.f};
+          vh[u] = sum.h;
+          vl[u] = sum.l;
+          sc[u] = er + fexp[jb + c8 + u] - 56;  // the value is 2^sc (vh + vl)
+        }
+        if constexpr (COMPACT) {
+          // whole 8-column pieces of the row as two 16-byte stores per plane
+          const size_t o = (size_t)orow * ws.ldg + jb + c8;
+          float* Lh = reinterpret_cast<float*>(ws.Lh);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            vh[u] = ldexpf(vh[u], sc[u]);  // basis entries: well inside the float range
+            vl[u] = ldexpf(vl[u], sc[u]);
+          }
+          if (jb + c8 + 8 <= J) {
+            *reinterpret_cast<float4*>(Lh + o) = make_float4(vh[0], vh[1], vh[2], vh[3]);
+            *reinterpret_cast<float4*>(Lh + o + 4) = make_float4(vh[4], vh[5], vh[6], vh[7]);
+            *reinterpret_cast<float4*>(ws.Ll + o) = make_float4(vl[0], vl[1], vl[2], vl[3]);
+            *reinterpret_cast<float4*>(ws.Ll + o + 4) = make_float4(vl[4], vl[5], vl[6], vl[7]);
+          } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+              if (jb + c8 + u < J) {
+                Lh[o + u] = vh[u];
+                ws.Ll[o + u] = vl[u];
+              }
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (jb + c8 + u < J)
+              out[(size_t)(jb + c8 + u) * ld + orow] = ldexp((double)vh[u], sc[u]) + ldexp((double)vl[u], sc[u]);
         }
       }
     }
@@ -277,25 +373,41 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split_rollout(Ws ws, int kcols
 
 }  // namespace split
 
-// The tensor-core rollout takes double-float storage, 8 to 64 horizons and at most 64 basis
-// columns (its shared memory holds C's digits for K <= 64 and one staged 128-row tile).
-bool split_rollout_ok(const Ws& ws, int kcols) {
-  // r0 <= cap for every committed state, so cap <= 64 bounds the basis columns
-  return ws.prec == ST_DD && kcols >= 8 && kcols <= split::kNJ && ws.cap <= split::kMaxK &&
-         split::smem_bytes(ws.ldg * 4) <= 227 * 1024;
+// The tensor-core paths take double-float storage and at most 64 columns in the tall operand
+// (r0 <= cap, plus the appended column of a compaction): C's or Q_B's digits for K <= 64 and
+// one staged 128-row tile fit in shared memory.
+static bool split_fits(const Ws& ws) {
+  return ws.prec == ST_DD && split::smem_bytes(ws.ldg * 4) <= 227 * 1024;
 }
+bool split_rollout_ok(const Ws& ws, int kcols) {
+  return split_fits(ws) && kcols >= 8 && kcols <= split::kNJ && ws.cap <= split::kMaxK;
+}
+bool split_compact_ok(const Ws& ws) { return split_fits(ws) && ws.cap + 1 <= split::kMaxK && ws.rmax <= split::kNJ; }
 
 cudaError_t prepare_split(const Ws& ws) {
-  if (ws.prec != ST_DD || split::smem_bytes(ws.ldg * 4) > 227 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(split::k_split_rollout, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              split::smem_bytes(ws.ldg * 4));
+  if (!split_fits(ws)) return cudaSuccess;
+  const int sm = split::smem_bytes(ws.ldg * 4);
+  cudaError_t e = cudaFuncSetAttribute(split::k_split<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(split::k_split<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  return e;
+}
+
+static int split_grid(const Ws& ws, int sms) {
+  const int64_t ntiles = (ws.n + split::kTM - 1) / split::kTM;
+  return (int)(ntiles < sms ? ntiles : sms);
 }
 
 cudaError_t launch_split_rollout(const Ws& ws, int kcols, double* out, int64_t ld, int sms, cudaStream_t s) {
-  const int64_t ntiles = (ws.n + split::kTM - 1) / split::kTM;
-  const int grid = (int)(ntiles < sms ? ntiles : sms);
-  split::k_split_rollout<<<grid, split::kThreadsS, split::smem_bytes(ws.ldg * 4), s>>>(ws, kcols, out, ld);
+  split::k_split<false><<<split_grid(ws, sms), split::kThreadsS, split::smem_bytes(ws.ldg * 4), s>>>(ws, kcols, out,
+                                                                                                     ld);
   return cudaGetLastError();
+}
+
+// launched after the small solves of every update (in the update graph); it returns at once
+// unless the update compacts
+cudaError_t launch_split_compact(const Ws& ws, int sms, cudaStream_t s) {
+  return launch_dependent(split::k_split<true>, split_grid(ws, sms), split::kThreadsS,
+                          (size_t)split::smem_bytes(ws.ldg * 4), s, ws, 0, (double*)nullptr, (int64_t)0);
 }
 
 }  // namespace odmd
