@@ -430,7 +430,10 @@ __global__ void __launch_bounds__(kRootThreads) k_roots(Ws ws) {
       lo = mu;
     else
       hi = mu;
-    if (fabs(f) <= 8.0 * kEps64 * (double)m * (1.0 + fabs(psi) + fabs(phi))) {
+    // f is formed from sums of terms of one sign each, so its rounding error is a few units
+    // of 1 + |psi| + |phi|; stop there (the step and bracket tests below end the iteration
+    // when the rounding of f alone moves it)
+    if (fabs(f) <= 8.0 * kEps64 * (1.0 + fabs(psi) + fabs(phi))) {
       conv = true;
       break;
     }

@@ -1,0 +1,97 @@
+// A double-float pair (h, l) times 2^sc as an IEEE double, rounded to nearest (ties to even),
+// with integer operations only.  On GB300 every conversion to double and every FP64
+// operation runs at FP64 rate (~2 per clock per SM, measured), against ~100 per clock for
+// FP32 and integer work, so an epilogue that writes one double per output builds the bits
+// itself.  The result equals the correctly rounded value of h 2^sc + l 2^sc.
+//
+// Preconditions (they hold for the normalized pairs the split epilogue forms): h is zero or
+// a normal float, |l| <= ulp(h) / 2 (l = 0 when h = 0), and the result is a normal double
+// (no overflow, no underflow).
+#pragma once
+#include <cstdint>
+#include <cstring>
+
+#ifndef __CUDACC__  // host compilers (the CPU test of this routine)
+#define __host__
+#define __device__
+#endif
+
+namespace odmd {
+
+#if defined(__CUDA_ARCH__)
+__device__ __forceinline__ uint32_t p2d_bits(float f) { return __float_as_uint(f); }
+__device__ __forceinline__ double p2d_double(uint64_t b) { return __longlong_as_double((long long)b); }
+__device__ __forceinline__ int p2d_clz64(uint64_t x) { return __clzll((long long)x); }
+#else
+inline uint32_t p2d_bits(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  return u;
+}
+inline double p2d_double(uint64_t b) {
+  double d;
+  std::memcpy(&d, &b, 8);
+  return d;
+}
+inline int p2d_clz64(uint64_t x) { return x ? __builtin_clzll(x) : 64; }
+#endif
+
+__host__ __device__ inline double pair_to_double(float h, float l, int sc) {
+  const uint32_t uh = p2d_bits(h);
+  const uint32_t eh = (uh >> 23) & 0xFFu;
+  if (eh == 0)  // h = 0 (then l = 0): the sum of two zeros is -0 only when both are -0
+    return p2d_double((uint64_t)((uh >> 31) & (p2d_bits(l) >> 31)) << 63);
+  const uint64_t sign = (uint64_t)(uh >> 31) << 63;
+  // h = mh 2^(eh - 150); M = mh 2^39 carries the value in units of 2^(eh - 189)
+  uint64_t M = (uint64_t)((uh & 0x7FFFFFu) | 0x800000u) << 39;
+  bool sticky = false;
+  const uint32_t ul = p2d_bits(l);
+  const uint32_t el = (ul >> 23) & 0xFFu;
+  if (el != 0) {
+    const uint64_t ml = (uint64_t)((ul & 0x7FFFFFu) | 0x800000u);
+    // l in the same units: ml 2^(el - eh + 39), with el <= eh - 24 so the shift is <= 15
+    const int d = (int)el - (int)eh + 39;
+    uint64_t add;
+    if (d >= 0) {
+      add = ml << d;
+    } else if (d > -64) {
+      add = ml >> (-d);
+      sticky = (ml & ((1ull << (-d)) - 1)) != 0;
+    } else {
+      add = 0;
+      sticky = true;
+    }
+    if ((ul >> 31) == (uh >> 31)) {
+      M += add;
+    } else {
+      // subtracting a truncated magnitude: the dropped bits belong to the subtrahend, so the
+      // exact value lies just below M - add; take one unit more off and keep a sticky bit
+      M -= add + (sticky ? 1ull : 0ull);
+    }
+  }
+  // normalize: leading bit to position 62 (|l| <= ulp(h)/2 moves it by at most one place)
+  const int lead = 63 - p2d_clz64(M);
+  int ex = (int)eh - 127;
+  if (lead > 62) {
+    sticky = sticky || (M & 1ull);
+    M >>= 1;
+    ex += 1;
+  } else if (lead < 62) {
+    M <<= (62 - lead);
+    ex -= (62 - lead);
+  }
+  // keep 53 bits (62 .. 10), round to nearest even on bits 9 .. 0 and the sticky bit
+  uint64_t mant = M >> 10;
+  const uint64_t rem = M & 0x3FFull;
+  if (rem > 0x200ull || (rem == 0x200ull && (sticky || (mant & 1ull)))) {
+    mant += 1;
+    if (mant >> 53) {
+      mant >>= 1;
+      ex += 1;
+    }
+  }
+  const uint64_t biased = (uint64_t)(ex + 1023 + sc);
+  return p2d_double(sign | (biased << 52) | (mant & ((1ull << 52) - 1)));
+}
+
+}  // namespace odmd

@@ -18,7 +18,9 @@
 // integer the FP32 accumulator holds exactly; pairs with g >= 9 are below 2^-49 K of
 // max|a_i| max|c_j| and are left out.  The epilogue adds the seven group sums, scaled by
 // 2^(56 - 7 g) (all exact floats), in double-float and scales the result by 2^(e_i + f_j -
-// 56), which is the double-float accuracy of the CUDA-core path.
+// 56), which is the double-float accuracy of the CUDA-core path; a rollout's doubles are
+// assembled from the pair by integer operations (pair2d.cuh: FP64 conversions run at the
+// FP64 rate on this GPU).
 //
 // One persistent CTA of 256 threads per SM (the seven accumulators take 448 of the SM's 512
 // tensor-memory columns).  C's digits are formed once per CTA.  A 128-row tile of L0 (both
@@ -33,6 +35,7 @@
 
 #include "dd.cuh"
 #include "odmd_internal.cuh"
+#include "pair2d.cuh"
 #include "tc.cuh"
 
 namespace odmd {
@@ -349,8 +352,8 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(Ws ws, int kcols, double
         } else {
 #pragma unroll
           for (int u = 0; u < 8; ++u)
-            if (jb + c8 + u < J)
-              out[(size_t)(jb + c8 + u) * ld + orow] = ldexp((double)vh[u], sc[u]) + ldexp((double)vl[u], sc[u]);
+            if (jb + c8 + u < J)  // the double's bits from the pair by integer operations
+              out[(size_t)(jb + c8 + u) * ld + orow] = pair_to_double(vh[u], vl[u], sc[u]);
         }
       }
     }
@@ -384,9 +387,13 @@ bool split_rollout_ok(const Ws& ws, int kcols) {
 }
 bool split_compact_ok(const Ws& ws) { return split_fits(ws) && ws.cap + 1 <= split::kMaxK && ws.rmax <= split::kNJ; }
 
+// The shared-memory limit is a property of the kernel, shared by every handle in the process:
+// set it for the widest rows this path takes (cap <= 64: an odd 17 chunks of 16 bytes)
 cudaError_t prepare_split(const Ws& ws) {
-  if (!split_fits(ws)) return cudaSuccess;
-  const int sm = split::smem_bytes(ws.ldg * 4);
+  if (ws.prec != ST_DD) return cudaSuccess;
+  const int sm = split::smem_bytes(16 * box_chunks(split::kMaxK, 4));
+  static_assert(16 * 17 * 2 * split::kTM + 8 * split::kTM + 7 * (split::kASlice + split::kBSlice) <= 227 * 1024,
+                "the widest staged tile and both digit buffers fit in shared memory");
   cudaError_t e = cudaFuncSetAttribute(split::k_split<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(split::k_split<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   return e;

@@ -1,0 +1,56 @@
+// Host test of pair_to_double (csrc/pair2d.cuh): the double built from a double-float pair by
+// integer operations must equal, bit for bit, the correctly rounded h 2^sc + l 2^sc.
+#include <cmath>
+#include <cstdio>
+#include <random>
+
+#include "pair2d.cuh"
+
+static long fails = 0, checked = 0;
+
+static void check(float h, float l, int sc) {
+  const double want = std::ldexp((double)h + (double)l, sc);  // one rounding, then exact scaling
+  const double got = odmd::pair_to_double(h, l, sc);
+  ++checked;
+  if (std::memcmp(&got, &want, 8) != 0) {
+    if (fails < 10) std::printf("h=%a l=%a sc=%d got %a want %a\n", h, l, sc, got, want);
+    ++fails;
+  }
+}
+
+int main() {
+  std::mt19937_64 rng(12345);
+  std::uniform_real_distribution<double> u(-1.0, 1.0);
+  std::uniform_int_distribution<int> ex(-60, 60), scd(-300, 300), gap(24, 90);
+  for (int i = 0; i < 2000000; ++i) {
+    // a normalized pair from a double: h = fl(x), l = fl(x - h)
+    const double x = std::ldexp(u(rng), ex(rng));
+    const float h = (float)x;
+    const float l = (float)(x - (double)h);
+    check(h, l, scd(rng));
+    // a low word far below the high word's last bit (the rounded and sticky paths)
+    const float h2 = (float)std::ldexp(u(rng), ex(rng));
+    if (h2 != 0.f) {
+      int e;
+      std::frexp(h2, &e);
+      const float l2 = (float)std::ldexp(u(rng), e - gap(rng));
+      check(h2, l2, scd(rng));
+    }
+  }
+  // ties to even, borrows at a power of two, zeros
+  const float hs[] = {1.0f, -1.0f, 1.5f, 0.75f, 3.0f, -2.0f, 1.0f + 0x1p-23f};
+  for (float h : hs) {
+    int e;
+    std::frexp(h, &e);
+    for (int k = 24; k <= 40; ++k)
+      for (float sgn : {1.f, -1.f}) {
+        const float l = sgn * (float)std::ldexp(1.0, e - 1 - k);
+        if (std::fabs(l) <= std::ldexp(1.0, e - 25)) check(h, l, 0);
+        check(h, sgn * (float)std::ldexp(1.0 + 0x1p-23, e - 1 - k), 7);
+      }
+  }
+  check(0.f, 0.f, 5);
+  check(-0.f, 0.f, 5);
+  std::printf("%ld checked, %ld mismatches\n", checked, fails);
+  return fails == 0 ? 0 : 1;
+}

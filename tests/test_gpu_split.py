@@ -1,13 +1,18 @@
-"""Multi-horizon rollouts on the tensor cores (split.cu: an exact 7-bit digit split of the
-basis and the coefficients, bfloat16 tcgen05.mma into exact FP32 group sums, double-float
-epilogue) against the oracle and against the CUDA-core path of the same stream.
+"""Tall x small products on the tensor cores (split.cu: an exact 7-bit digit split of the
+basis and of the small factor, bfloat16 tcgen05.mma into exact FP32 group sums,
+double-float epilogue): the multi-horizon rollout and the compaction of the product-form
+basis, against the oracle and against the CUDA-core paths.
 
-Bars: every predicted state within 1e-9 relative of the oracle's (the FP64 reconstruction
-tolerance), and within 1e-12 relative of the CUDA-core rollout (both paths are exact up to
-double-float rounding: 2^-48 relative per element, summed over at most 64 columns).  The
-horizon counts cover the smallest tensor-core call (8), a full launch (64), a launch split
-in two (65: 64 on the tensor cores, 1 on the CUDA cores) and the benchmark's 50; rows are
-ragged against the 128-row tile."""
+Rollouts: every predicted state within 1e-9 relative of the oracle's (the FP64
+reconstruction tolerance) and within 1e-12 relative of the CUDA-core rollout of the same
+model state (a checkpoint of the tensor-core handle loaded into a CUDA-core handle; both
+rollouts are exact up to double-float rounding, 2^-48 per element over at most 64 columns).
+Horizon counts cover the smallest tensor-core call (8), a full launch (64), a launch split in
+two (65: 64 on the tensor cores, 1 on the CUDA cores) and the benchmark's 50; rows are
+ragged against the 128-row tile.  Compaction: on a stream whose rank cap equals its planted
+rank (no choice among noise directions, so rounding differences stay small), a handle that
+compacts on the tensor cores and one that compacts on the CUDA cores agree to 1e-12 of
+sigma_1 in the singular values and 1e-10 in predictions, and both match the oracle."""
 import numpy as np
 import pytest
 
@@ -18,22 +23,29 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def _pair(X, r_max, slack):
-    import paper_2311_18715_gb300 as pkg
-
-    tc = pkg.OnlineDMD(X.shape[1], r_max, slack=slack)
-    cc = pkg.OnlineDMD(X.shape[1], r_max, slack=slack, tensor_cores=False)
-    ref = OnlineDMDRef(X.shape[1], r_max, 1e-10)
-    Xd = torch.from_numpy(X).cuda()
-    for k in range(X.shape[0]):
-        tc.update(Xd[k])
-        cc.update(Xd[k])
-        ref.update(X[k])
-    return tc, cc, ref
-
-
 def _rel(got, want):
     return np.linalg.norm(got - want, axis=1) / np.linalg.norm(want, axis=1)
+
+
+def _fed(X, r_max, slack, tensor_cores=True, ref=False):
+    import paper_2311_18715_gb300 as pkg
+
+    m = pkg.OnlineDMD(X.shape[1], r_max, slack=slack, tensor_cores=tensor_cores)
+    o = OnlineDMDRef(X.shape[1], r_max, 1e-10) if ref else None
+    Xd = torch.from_numpy(X).cuda()
+    for k in range(X.shape[0]):
+        m.update(Xd[k])
+        if o is not None:
+            o.update(X[k])
+    return m, o
+
+
+def _same_state_cuda_cores(tc):
+    import paper_2311_18715_gb300 as pkg
+
+    cc = pkg.OnlineDMD(tc.n, tc.r_max, slack=int(tc.cfg.slack), tensor_cores=False)
+    cc.load(tc.save())
+    return cc
 
 
 @pytest.mark.parametrize("case", ["planted", "random_ragged", "wake"])
@@ -44,8 +56,9 @@ def test_tensor_core_rollout_against_oracle_and_cuda_cores(case):
         X, r, sl = RandomPlanted(50001, seed=5).snapshots(0, 70), 24, 8
     else:
         X, r, sl = WakeField(128, 64, sigma=1e-6, seed=2).snapshots(0, 150), 40, 16  # the benchmark's cap
-    tc, cc, ref = _pair(X, r, sl)
-    assert tc.rank == ref.rank
+    tc, ref = _fed(X, r, sl, ref=True)
+    cc = _same_state_cuda_cores(tc)
+    assert tc.rank == ref.rank == cc.rank
     k = X.shape[0]
     for nh in (8, 50, 64, 65):
         ts = [float(k - 3 + h) for h in range(nh)]
@@ -54,23 +67,34 @@ def test_tensor_core_rollout_against_oracle_and_cuda_cores(case):
         base = cc.predict(ts).cpu().numpy()
         assert np.max(_rel(got, want)) < 1e-9, (case, nh, np.max(_rel(got, want)))
         assert np.max(_rel(got, base)) < 1e-12, (case, nh, np.max(_rel(got, base)))
-        assert np.max(_rel(base, want)) < 1e-9
 
 
 def test_tensor_core_rollout_full_size_benchmark_horizons():
     """The benchmark's configuration and call: n = 393,216 (3072 tiles over the SMs, every
-    CTA through many tiles), cap 56, 50 integer horizons, against the CUDA-core path."""
+    CTA through many tiles), cap 56, 50 integer horizons, against the CUDA-core rollout of the
+    same state."""
     X = WakeField(512, 256, sigma=1e-6, seed=0).snapshots(0, 60)
-    import paper_2311_18715_gb300 as pkg
-
-    tc = pkg.OnlineDMD(X.shape[1], 40, slack=16)
-    cc = pkg.OnlineDMD(X.shape[1], 40, slack=16, tensor_cores=False)
-    Xd = torch.from_numpy(X).cuda()
-    for x in Xd:
-        tc.update(x)
-        cc.update(x)
+    tc, _ = _fed(X, 40, 16)
+    cc = _same_state_cuda_cores(tc)
     ts = [float(60 + h) for h in range(50)]
     got = tc.predict(ts).cpu().numpy()
     base = cc.predict(ts).cpu().numpy()
     assert np.isfinite(got).all()
     assert np.max(_rel(got, base)) < 1e-12
+
+
+@pytest.mark.parametrize("slack,n", [(2, 4096), (5, 100003)])
+def test_tensor_core_compaction_against_cuda_cores_and_oracle(slack, n):
+    X = PlantedModes(n, sigma=0.0, seed=3).snapshots(0, 140)  # rank 6, no noise directions
+    tc, ref = _fed(X, 6, slack, ref=True)
+    cc, _ = _fed(X, 6, slack, tensor_cores=False)
+    assert tc.counts()[1] > 20 and tc.counts() == cc.counts()  # many compactions, the same ones
+    S, Sc = np.array(tc.singular_values()), np.array(cc.singular_values())
+    assert np.max(np.abs(S - Sc)) <= 1e-12 * Sc[0]
+    np.testing.assert_allclose(S, ref.S, rtol=0, atol=1e-10 * ref.S[0])
+    ts = [float(h) for h in range(130, 150)]
+    got, base, want = tc.predict(ts).cpu().numpy(), cc.predict(ts).cpu().numpy(), ref.predict(ts).T
+    assert np.max(_rel(got, base)) < 1e-10
+    assert np.max(_rel(got, want)) < 1e-9
+    L = tc.basis().cpu().numpy()
+    assert np.max(np.abs(L @ L.T - np.eye(L.shape[0]))) < 1e-12
