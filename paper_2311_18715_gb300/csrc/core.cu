@@ -173,23 +173,29 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(Ws ws) {
     red8[8 + warp] = zy;
   }
   __syncthreads();
-  zz = 0.0;
-  zy = 0.0;
-  for (int w8 = 0; w8 < 8; ++w8) {
-    zz += red8[w8];
-    zy += red8[8 + w8];
+  // rho, 1/rho and gamma once (FP64 square roots and divisions run at the FP64 rate)
+  __shared__ double rho_s, inv_s;
+  if (tid == 0) {
+    zz = 0.0;
+    zy = 0.0;
+    for (int w8 = 0; w8 < 8; ++w8) {
+      zz += red8[w8];
+      zy += red8[8 + w8];
+    }
+    double rh = sqrt(zz);
+    if (!(rh > thr)) rh = 0.0;
+    const double iv = rh > 0.0 ? 1.0 / rh : 0.0;
+    rho_s = rh;
+    inv_s = iv;
+    ctl->rho = rh;
+    ctl->gamma = zy * iv;
   }
-  double rho = sqrt(zz);
-  if (!(rho > thr)) rho = 0.0;
-  const double inv_rho = rho > 0.0 ? 1.0 / rho : 0.0;
+  __syncthreads();
+  const double rho = rho_s, inv_rho = inv_s;
   for (int i = tid; i < r0e; i += kPrepThreads) {
     ws.sm.qn[i] = z[i] * inv_rho;
     ws.sm.yext[i] = yx[i];
     if (i < r0) ws.sm.ac[i] = ac[i];
-  }
-  if (tid == 0) {
-    ctl->rho = rho;
-    ctl->gamma = zy * inv_rho;
   }
   // ---- secular problem of K = [[diag(S), p], [0, rho]], n = r + 1, scaled to max < 1
   if (warp == 0) {
@@ -233,21 +239,32 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(Ws ws) {
           last = i;
         }
       }
-      int m = 0, nd = 0;
-      for (int i = n - 1; i >= 0; --i) {  // ascending poles
-        if (defl[i]) {
-          ws.sm.defl[nd++] = i;
-        } else {
-          ws.sm.pole[m] = i;
-          ws.sm.d[m] = dsc[i];
-          ws.sm.z[m] = zsc[i];
-          ++m;
-        }
+      ctl->nrot = nrot;
+    }
+    __syncwarp();
+    // the poles in ascending order (core coordinates n-1 .. 0) and the deflated coordinates,
+    // positions by ballots over 32 coordinates at a time
+    int m = 0, nd = 0;
+    for (int base = 0; base < n; base += 32) {
+      const int i = n - 1 - (base + lane);  // ascending poles: descending coordinates
+      const bool in = base + lane < n;
+      const bool dfl = in && defl[i];
+      const unsigned bd = __ballot_sync(0xffffffffu, dfl), bp = __ballot_sync(0xffffffffu, in && !dfl);
+      const unsigned below = (1u << lane) - 1u;
+      if (dfl) ws.sm.defl[nd + __popc(bd & below)] = i;
+      if (in && !dfl) {
+        const int q = m + __popc(bp & below);
+        ws.sm.pole[q] = i;
+        ws.sm.d[q] = dsc[i];
+        ws.sm.z[q] = zsc[i];
       }
+      nd += __popc(bd);
+      m += __popc(bp);
+    }
+    if (lane == 0) {
       ctl->n = n;
       ctl->m = m;
       ctl->ndefl = nd;
-      ctl->nrot = nrot;
       ctl->scale_exp = e;
       if (!isfinite(rho) || !isfinite(mx)) atomicOr(&ctl->status, DEV_NONFINITE);
     }
@@ -708,7 +725,17 @@ __device__ void apply_column(const Ws& ws, int j, const StateBuf& st, const Stat
   const int n = r + 1, rnew = ctl->rnew;
   const int qld = ws.cap + 1, rm = ws.rmax;
   const double rho = ctl->rho, gamma = ctl->gamma;
+  // every product below runs from shared memory: M (r x r), Q (r0 x r) and the kept left
+  // singular vectors U (rnew x n) are staged first by all threads, coalesced, so that the
+  // short dependent FMA chains wait on shared memory rather than on L2
+  extern __shared__ __align__(16) double asm_[];
+  double* sM = asm_;                            // [k][i], ld r
+  double* sQ = sM + (size_t)kMaxR * kMaxR;      // [k][i], ld r0
+  double* sU = sQ + (size_t)kMaxR * (kMaxCap + 1);  // [i][k], ld n
   __shared__ double v[kMaxN], u[kMaxN], bv[kMaxN], qcol[kMaxCap + 1], rlv;
+  for (int idx = tid; idx < r * r; idx += kApplyThreads) sM[idx] = st.M[(size_t)(idx / r) * rm + idx % r];
+  for (int idx = tid; idx < r * r0; idx += kApplyThreads) sQ[idx] = st.Q[(size_t)(idx / r0) * qld + idx % r0];
+  for (int idx = tid; idx < rnew * n; idx += kApplyThreads) sU[idx] = ws.sm.U[(size_t)(idx / n) * kMaxN + idx % n];
   for (int i = tid; i < n; i += kApplyThreads) {
     v[i] = ws.sm.V[(size_t)j * kMaxN + i];
     u[i] = ws.sm.U[(size_t)j * kMaxN + i];
@@ -719,7 +746,7 @@ __device__ void apply_column(const Ws& ws, int j, const StateBuf& st, const Stat
     const int i = tid >> 2, sub = tid & 3;
     double acc = 0.0;
     if (i < r)
-      for (int k = sub; k < r; k += 4) acc = fma(st.M[(size_t)k * rm + i], v[k], acc);
+      for (int k = sub; k < r; k += 4) acc = fma(sM[(size_t)k * r + i], v[k], acc);
     acc = group4_sum_d(acc);
     if (i < r && sub == 0) bv[i] = fma(ws.sm.w[i], v[r], acc);
   }
@@ -736,7 +763,7 @@ __device__ void apply_column(const Ws& ws, int j, const StateBuf& st, const Stat
     const int i = (base + tid) >> 2, sub = tid & 3;
     double acc = 0.0;
     if (i < r0)
-      for (int k = sub; k < r; k += 4) acc = fma(st.Q[(size_t)k * qld + i], u[k], acc);
+      for (int k = sub; k < r; k += 4) acc = fma(sQ[(size_t)k * r0 + i], u[k], acc);
     acc = group4_sum_d(acc);
     if (i < r0e && sub == 0) qcol[i] = fma(ws.sm.qn[i], u[r], acc);
   }
@@ -748,7 +775,7 @@ __device__ void apply_column(const Ws& ws, int j, const StateBuf& st, const Stat
     const int i = tid >> 2, sub = tid & 3;
     double acc = 0.0;
     if (i < rnew)
-      for (int k = sub; k < n; k += 4) acc = fma(ws.sm.U[(size_t)i * kMaxN + k], bv[k], acc);
+      for (int k = sub; k < n; k += 4) acc = fma(sU[(size_t)i * n + k], bv[k], acc);
     acc = group4_sum_d(acc);
     if (i < rnew && sub == 0) nx.M[(size_t)j * rm + i] = acc;
   }
@@ -785,8 +812,13 @@ static int prep_smem_cap(int cap) {
   return (int)sizeof(double) * (qld * kMaxR + 3 * qld + 2 * kMaxN);
 }
 
+// staged M, Q and U of k_apply (largest sizes)
+constexpr int kApplySmem = (int)sizeof(double) * (kMaxR * kMaxR + kMaxR * (kMaxCap + 1) + kMaxR * kMaxN);
+
 cudaError_t prepare_core() {
-  return cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, prep_smem_cap(kMaxCap));
+  cudaError_t e = cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, prep_smem_cap(kMaxCap));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, kApplySmem);
+  return e;
 }
 
 cudaError_t launch_small(const Ws& ws, cudaStream_t s) {
@@ -794,7 +826,7 @@ cudaError_t launch_small(const Ws& ws, cudaStream_t s) {
   if (e == cudaSuccess) e = launch_dependent(k_roots, kMaxN, kRootThreads, 0, s, ws);
   if (e == cudaSuccess) e = launch_dependent(k_zhat, kMaxN + 1, kZhatThreads, 0, s, ws);
   if (e == cudaSuccess) e = launch_dependent(k_vectors, kMaxN, kVecThreads, 0, s, ws);
-  if (e == cudaSuccess) e = launch_dependent(k_apply, kMaxN, kApplyThreads, 0, s, ws);
+  if (e == cudaSuccess) e = launch_dependent(k_apply, kMaxN, kApplyThreads, (size_t)kApplySmem, s, ws);
   return e;
 }
 

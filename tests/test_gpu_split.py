@@ -10,7 +10,7 @@ rollouts are exact up to double-float rounding, 2^-48 per element over at most 6
 Horizon counts cover the smallest tensor-core call (8), a full launch (64), a launch split in
 two (65: 64 on the tensor cores, 1 on the CUDA cores) and the benchmark's 50; rows are
 ragged against the 128-row tile.  Compaction: on a stream whose rank cap equals its planted
-rank (no choice among noise directions, so rounding differences stay small), a handle that
+rank (every noise direction is dropped again, so rounding differences stay small), a handle that
 compacts on the tensor cores and one that compacts on the CUDA cores agree to 1e-12 of
 sigma_1 in the singular values and 1e-10 in predictions, and both match the oracle."""
 import numpy as np
@@ -85,7 +85,10 @@ def test_tensor_core_rollout_full_size_benchmark_horizons():
 
 @pytest.mark.parametrize("slack,n", [(2, 4096), (5, 100003)])
 def test_tensor_core_compaction_against_cuda_cores_and_oracle(slack, n):
-    X = PlantedModes(n, sigma=0.0, seed=3).snapshots(0, 140)  # rank 6, no noise directions
+    # rank cap = the planted rank: every snapshot's noise (std 1e-8) adds a direction that the
+    # truncation drops again, so columns are appended and compacted, with no choice among
+    # nearly equal directions
+    X = PlantedModes(n, sigma=1e-8, seed=3).snapshots(0, 140)
     tc, ref = _fed(X, 6, slack, ref=True)
     cc, _ = _fed(X, 6, slack, tensor_cores=False)
     assert tc.counts()[1] > 20 and tc.counts() == cc.counts()  # many compactions, the same ones
