@@ -48,7 +48,7 @@ constexpr int kSlices = 7;      // digits per value
 constexpr int kGroups = 7;      // g = s + t = 2 .. 8
 constexpr int kMaxK = 64;       // basis columns this path takes (4 K chunks)
 constexpr int kBufK = 32;       // K columns of L0 digits held at once (two chunks)
-constexpr int kThreadsS = 256;
+constexpr int kThreadsS = 512;   // 16 warps: 4 threads per row in the digit phase, 4 warps per TMEM lane quarter
 constexpr uint32_t kTmemCols = 512;
 constexpr int kASlice = kTM * kBufK * 2;   // bytes of one digit slice of the L0 buffer
 constexpr int kBSlice = kNJ * kMaxK * 2;   // bytes of one digit slice of C (K padded to 64)
@@ -57,6 +57,9 @@ static_assert(kGroups * kNJ <= (int)kTmemCols, "seven accumulators fit the tenso
 static_assert(7 * kMaxK * (1 << 14) < (1 << 24), "group sums stay below 2^24");
 
 // staging buffer: the two basis planes of a tile, then the tile's stored residual (8 bytes a row)
+// 2^(42 - 7 q): the scale of group g = q + 2 relative to the smallest group (g = 8)
+__constant__ float kGroupScale[kGroups] = {0x1p42f, 0x1p35f, 0x1p28f, 0x1p21f, 0x1p14f, 0x1p7f, 1.0f};
+
 __host__ __device__ inline int stage_bytes(int rs) { return ((2 * kTM * rs + kTM * 8 + 1023) / 1024) * 1024; }
 __host__ __device__ inline int smem_bytes(int rs) { return stage_bytes(rs) + kSlices * kASlice + kSlices * kBSlice; }
 
@@ -190,7 +193,9 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(Ws ws, int kcols, double
   uint32_t par_tma = 0, par_mma = 0;
   // work in flight that a timeout must still wait for (the same in every thread)
   bool tma_out = my_tiles > 0, mma_out = false;
-  const int row = tid >> 1, half = tid & 1;  // digit phase: two threads per row
+  // digit phase: four threads per row, thread q of a row owning buffer columns 8q .. 8q + 7
+  // (one 16-byte row of a core matrix per slice)
+  const int row = tid >> 2, quad = tid & 3;
   const float* sh = reinterpret_cast<const float*>(stage) + (size_t)row * (rs / 4);
   const float* sl = reinterpret_cast<const float*>(stage + (size_t)kTM * rs) + (size_t)row * (rs / 4);
   bool ok = true;
@@ -207,12 +212,13 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(Ws ws, int kcols, double
     tma_out = false;
     const bool live = row0 + row < ws.n;
     if (with_e) {
-      // j0 = (e - L0[:, :r0] s) / rho0 for this row, half of the dot per thread
+      // j0 = (e - L0[:, :r0] s) / rho0 for this row, a quarter of the dot per thread
       Acc d = acc_zero();
       if (live)
-        for (int k = half; k < r0; k += 2) acc_fma(d, sh[k], sl[k], sh_s[k], sl_s[k]);
+        for (int k = quad; k < r0; k += 4) acc_fma(d, sh[k], sl[k], sh_s[k], sl_s[k]);
       acc_add(d, __shfl_xor_sync(0xffffffffu, d.h, 1), __shfl_xor_sync(0xffffffffu, d.l, 1));
-      if (half == 0) {
+      acc_add(d, __shfl_xor_sync(0xffffffffu, d.h, 2), __shfl_xor_sync(0xffffffffu, d.l, 2));
+      if (quad == 0) {
         const float2 ev = reinterpret_cast<const float2*>(stage + (size_t)2 * kTM * rs)[row];
         Acc e = Acc{ev.x, ev.y};
         acc_add(e, -d.h, -d.l);
@@ -225,36 +231,56 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(Ws ws, int kcols, double
       }
       __syncwarp();
     }
-    // the row's exponent: max |hi| over its K columns, half of them per thread
+    // the row's exponent: max |hi| over its K columns, a quarter of them per thread
     {
       float mx = 0.f;
       if (live)
-        for (int k = half; k < K; k += 2) mx = fmaxf(mx, fabsf(k < r0 ? sh[k] : jh[row]));
+        for (int k = quad; k < K; k += 4) mx = fmaxf(mx, fabsf(k < r0 ? sh[k] : jh[row]));
       mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-      if (half == 0) erow[row] = grid_exp(mx);
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+      if (quad == 0) erow[row] = grid_exp(mx);
     }
     __syncwarp();
     const int my_e = erow[row];
     for (int c0 = 0; c0 < nchunk; c0 += 2) {
-      // digits of chunk c0 + half (16 columns of this row) into the buffer slot `half`
-      const int c = c0 + half;
-      if (c < nchunk) {
-#pragma unroll 2
-        for (int kk = 0; kk < kKC; ++kk) {
-          const int k = c * kKC + kk;
-          float h = 0.f, l = 0.f;
-          if (live && k < r0) {
-            h = sh[k];
-            l = sl[k];
-          } else if (live && k < K) {  // the new column (compaction)
-            h = jh[row];
-            l = jl[row];
-          }
-          uint16_t d[kSlices];
-          digits7(h, l, my_e, d);
-          const int off = tc::kmajor_off(row, half * kKC + kk, kBufK / 8);
+      // digits of basis columns kb .. kb + 7 of this row (chunk c0 + quad / 2) into buffer
+      // columns 8 quad .. 8 quad + 7: one 16-byte store per slice; columns at or past K
+      // (the chunk's zero padding) store zeros without arithmetic
+      const int kb = c0 * kKC + 8 * quad;
+      if (c0 * kKC + 8 * quad < nchunk * kKC) {
+        const int off = tc::kmajor_off(row, 8 * quad, kBufK / 8);
+        if (live && kb < K) {
+          uint32_t w[kSlices][4];
 #pragma unroll
-          for (int s = 0; s < kSlices; ++s) *reinterpret_cast<uint16_t*>(adig + s * kASlice + off) = d[s];
+          for (int kk = 0; kk < 8; kk += 2) {
+            uint16_t d0[kSlices], d1[kSlices];
+            const int k = kb + kk;
+            float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+            if (k < r0) {
+              h0 = sh[k];
+              l0 = sl[k];
+            } else if (k < K) {  // the new column (compaction)
+              h0 = jh[row];
+              l0 = jl[row];
+            }
+            if (k + 1 < r0) {
+              h1 = sh[k + 1];
+              l1 = sl[k + 1];
+            } else if (k + 1 < K) {
+              h1 = jh[row];
+              l1 = jl[row];
+            }
+            digits7(h0, l0, my_e, d0);
+            digits7(h1, l1, my_e, d1);
+#pragma unroll
+            for (int s = 0; s < kSlices; ++s) w[s][kk >> 1] = (uint32_t)d0[s] | ((uint32_t)d1[s] << 16);
+          }
+#pragma unroll
+          for (int s = 0; s < kSlices; ++s)
+            *reinterpret_cast<uint4*>(adig + s * kASlice + off) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+        } else {
+#pragma unroll
+          for (int s = 0; s < kSlices; ++s) *reinterpret_cast<uint4*>(adig + s * kASlice + off) = make_uint4(0, 0, 0, 0);
         }
       }
       tc::fence_proxy_async();
@@ -295,14 +321,14 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(Ws ws, int kcols, double
       tc::fence_after_sync();
     }
     if (!ok) break;
-    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows) and the 32
-    // columns of its half; X = sum_g G_g 2^(56 - 7 g), then 2^(e_i + f_j - 56)
+    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows) and 16 columns
+    // (quarter w / 4); X = 2^(e_i + f_j - 56) sum_g G_g 2^(56 - 7 g)
     {
       const int trow = 32 * (warp & 3) + lane;
       const int64_t orow = row0 + trow;
       const int er = erow[trow];
-      const int jb = 32 * (warp >> 2);
-      for (int c8 = 0; c8 < 32; c8 += 8) {
+      const int jb = 16 * (warp >> 2);
+      for (int c8 = 0; c8 < 16; c8 += 8) {
         uint32_t g[kGroups][8];
 #pragma unroll
         for (int q = 0; q < kGroups; ++q) {
@@ -318,11 +344,19 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(Ws ws, int kcols, double
         int sc[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-          // smallest group first; every term G_g 2^(56 - 7 g) is an exact float
-          dd sum = dd{__uint_as_float(g[kGroups - 1][u]), 0.f};
+          // every term G_g 2^(56 - 7 g) is an exact float (|G_g| < 2^23): a cascaded sum,
+          // smallest term first, with the exact rounding error of each addition (two-sum)
+          // gathered in a second float, then one renormalization
+          float sh_ = __uint_as_float(g[kGroups - 1][u]), el = 0.f;
 #pragma unroll
-          for (int q = kGroups - 2; q >= 0; --q)
-            sum = sum + dd{ldexpf(__uint_as_float(g[q][u]), 7 * (kGroups - 1 - q)), 0.f};
+          for (int q = kGroups - 2; q >= 0; --q) {
+            const float t = __fmul_rn(__uint_as_float(g[q][u]), kGroupScale[q]);
+            const float s2 = __fadd_rn(sh_, t);
+            const float bb = __fsub_rn(s2, sh_);
+            el = __fadd_rn(el, __fadd_rn(__fsub_rn(sh_, __fsub_rn(s2, bb)), __fsub_rn(t, bb)));
+            sh_ = s2;
+          }
+          const dd sum = fast_two_sum(sh_, el);
           vh[u] = sum.h;
           vl[u] = sum.l;
           sc[u] = er + fexp[jb + c8 + u] - 56;  // the value is 2^sc (vh + vl)
@@ -333,8 +367,15 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(Ws ws, int kcols, double
           float* Lh = reinterpret_cast<float*>(ws.Lh);
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
-            vh[u] = ldexpf(vh[u], sc[u]);  // basis entries: well inside the float range
-            vl[u] = ldexpf(vl[u], sc[u]);
+            // basis entries lie well inside the float range: an exact power-of-two product
+            if (sc[u] >= -126 && sc[u] <= 127) {
+              const float p2 = __int_as_float((sc[u] + 127) << 23);
+              vh[u] = __fmul_rn(vh[u], p2);
+              vl[u] = __fmul_rn(vl[u], p2);
+            } else {
+              vh[u] = ldexpf(vh[u], sc[u]);
+              vl[u] = ldexpf(vl[u], sc[u]);
+            }
           }
           if (jb + c8 + 8 <= J) {
             *reinterpret_cast<float4*>(Lh + o) = make_float4(vh[0], vh[1], vh[2], vh[3]);
