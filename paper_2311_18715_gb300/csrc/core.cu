@@ -209,9 +209,12 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(Ws ws) {
     int e = 0;
     if (mx > 0.0) frexp(mx, &e);
     const double tol = 8.0 * kEps64;  // in scaled units
+    // 2^-e built from its bits (|e| stays far inside the exponent range of doubles), so each
+    // scaling is one exact product
+    const double pw = __longlong_as_double((long long)(1023 - e) << 52);
     for (int i = lane; i < n; i += 32) {
-      const double di = i < r ? ldexp(st.S[i], -e) : 0.0;
-      const double zi = ldexp(i < r ? p[i] : rho, -e);
+      const double di = i < r ? st.S[i] * pw : 0.0;
+      const double zi = (i < r ? p[i] : rho) * pw;
       dsc[i] = di;
       const bool small = !(fabs(zi) > tol);
       zsc[i] = small ? 0.0 : zi;
@@ -423,11 +426,16 @@ __global__ void __launch_bounds__(kRootThreads) k_roots(Ws ws) {
     const double cand = (double)muf;
     if (isfinite(muf) && cand > lo && cand < hi) mu = cand;
   }
-  // ---- stage 2: f in FP64 (one pole per thread), the model step in FP32 for the
-  // correction delta = x - mu (shifted poles A - mu, B - mu), applied to the FP64 mu
+  // ---- stage 2: f in FP64 (one pole per thread, summed per warp), then the step by thread 0
+  // alone -- the bracket, the tests and the FP32 model step for the correction delta = x - mu
+  // (shifted poles A - mu, B - mu) -- broadcast through shared memory: FP64 operations run
+  // at 1/64 of the FP32 rate, so scalar work is not repeated in every thread
   const double ddo = mine ? (di - dob) * (di + dob) : 0.0;  // d_i^2 - d_o^2
+  __shared__ double mu_s;
+  __shared__ int done_s;
   bool conv = false;
-  for (int it = 0; it < 100; ++it, ++it_total) {
+  __syncthreads();  // every thread is done reading the partial sums of the stages above
+  for (int it = 0; it < 100; ++it) {
     double v[4] = {0.0, 0.0, 0.0, 0.0};  // psi, phi, psi', phi'
     if (mine) {
       const double t = zi / (ddo - mu);
@@ -440,51 +448,70 @@ __global__ void __launch_bounds__(kRootThreads) k_roots(Ws ws) {
         v[3] = dterm;
       }
     }
-    block_sum4(v, part[it_total & 1]);
-    const double psi = v[0], phi = v[1];
-    const double f = 1.0 + psi + phi;
-    if (f < 0.0)
-      lo = mu;
-    else
-      hi = mu;
-    // f is formed from sums of terms of one sign each, so its rounding error is a few units
-    // of 1 + |psi| + |phi|; stop there (the step and bracket tests below end the iteration
-    // when the rounding of f alone moves it)
-    if (fabs(f) <= 8.0 * kEps64 * (1.0 + fabs(psi) + fabs(phi))) {
-      conv = true;
-      break;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = warp_sum_d(v[k]);
+    if (lane == 0)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) part[0][tid >> 5][k] = v[k];
+    __syncthreads();
+    if (tid == 0) {
+      double psi = part[0][0][0], phi = part[0][0][1], dps = part[0][0][2], dph = part[0][0][3];
+      for (int w = 1; w < kRootThreads / 32; ++w) {
+        psi += part[0][w][0];
+        phi += part[0][w][1];
+        dps += part[0][w][2];
+        dph += part[0][w][3];
+      }
+      const double f = 1.0 + psi + phi;
+      if (f < 0.0)
+        lo = mu;
+      else
+        hi = mu;
+      int stop = 0;
+      // f is formed from sums of terms of one sign each, so its rounding error is a few units
+      // of 1 + |psi| + |phi|; stop there (the step and bracket tests below end the iteration
+      // when the rounding of f alone moves it)
+      if (fabs(f) <= 8.0 * kEps64 * (1.0 + fabs(psi) + fabs(phi))) {
+        stop = 1;
+      } else {
+        // two-pole model written around mu with f explicit:  f + psi' a d/(a - d) + phi' b
+        // d/(b - d) = 0, neighbouring poles at a = A - mu and b = B - mu, unknown d = x - mu,
+        // scaled by a power of two so that the FP32 coefficients stay inside the exponent range
+        const float fh = (float)f;
+        const float a = (float)(A - mu);
+        const float b = last ? 0.f : (float)(B - mu);
+        int ex = 0;
+        frexpf(fmaxf(fabsf(a), fabsf(b)), &ex);
+        const float sc = ldexpf(1.f, ex), as = ldexpf(a, -ex), bs = ldexpf(b, -ex);
+        const float ps = (float)dps * sc, hs = (float)dph * sc;
+        float delta;
+        if (!last) {
+          const float Qa = fh - ps * as - hs * bs;
+          const float Qb = as * bs * (ps + hs) - fh * (as + bs);
+          const float Qc = fh * as * bs;
+          const float disc = fmaxf(Qb * Qb - 4.f * Qa * Qc, 0.f);
+          const float q = -0.5f * (Qb >= 0.f ? Qb + sqrtf(disc) : Qb - sqrtf(disc));
+          const float d2 = q != 0.f ? Qc / q : 0.f;  // the root that tends to -f / f'
+          const float d1 = Qa != 0.f ? q / Qa : d2;
+          const float lo_s = ldexpf((float)(lo - mu), -ex), hi_s = ldexpf((float)(hi - mu), -ex);
+          const bool in2 = d2 > lo_s && d2 < hi_s, in1 = d1 > lo_s && d1 < hi_s;
+          delta = ldexpf(in2 ? d2 : (in1 ? d1 : d2), ex);
+        } else {
+          const float den = fh - ps * as;
+          delta = den != 0.f ? ldexpf(fh * as / den, ex) : 0.f;
+        }
+        double x = mu + (double)delta;
+        if (!isfinite(delta) || !(x > lo && x < hi)) x = 0.5 * (lo + hi);
+        const double step = fabs(x - mu);
+        mu = x;
+        if (step <= 4.0 * kEps64 * fabs(mu) || hi - lo <= 4.0 * kEps64 * fmax(fabs(lo), fabs(hi))) stop = 1;
+      }
+      mu_s = mu;
+      done_s = stop;
     }
-    // two-pole model written around mu with f explicit:  f + psi' a d/(a - d) + phi' b d/(b
-    // - d) = 0, neighbouring poles at a = A - mu and b = B - mu, unknown d = x - mu, scaled
-    // by a power of two so that the FP32 coefficients stay inside the exponent range
-    const float fh = (float)f;
-    const float a = (float)(A - mu);
-    const float b = last ? 0.f : (float)(B - mu);
-    int ex = 0;
-    frexpf(fmaxf(fabsf(a), fabsf(b)), &ex);
-    const float sc = ldexpf(1.f, ex), as = ldexpf(a, -ex), bs = ldexpf(b, -ex);
-    const float ps = (float)v[2] * sc, hs = (float)v[3] * sc;
-    float delta;
-    if (!last) {
-      const float Qa = fh - ps * as - hs * bs;
-      const float Qb = as * bs * (ps + hs) - fh * (as + bs);
-      const float Qc = fh * as * bs;
-      const float disc = fmaxf(Qb * Qb - 4.f * Qa * Qc, 0.f);
-      const float q = -0.5f * (Qb >= 0.f ? Qb + sqrtf(disc) : Qb - sqrtf(disc));
-      const float d2 = q != 0.f ? Qc / q : 0.f;  // the root that tends to -f / f'
-      const float d1 = Qa != 0.f ? q / Qa : d2;
-      const float lo_s = ldexpf((float)(lo - mu), -ex), hi_s = ldexpf((float)(hi - mu), -ex);
-      const bool in2 = d2 > lo_s && d2 < hi_s, in1 = d1 > lo_s && d1 < hi_s;
-      delta = ldexpf(in2 ? d2 : (in1 ? d1 : d2), ex);
-    } else {
-      const float den = fh - ps * as;
-      delta = den != 0.f ? ldexpf(fh * as / den, ex) : 0.f;
-    }
-    double x = mu + (double)delta;
-    if (!isfinite(delta) || !(x > lo && x < hi)) x = 0.5 * (lo + hi);
-    const double step = fabs(x - mu);
-    mu = x;
-    if (step <= 4.0 * kEps64 * fabs(mu) || hi - lo <= 4.0 * kEps64 * fmax(fabs(lo), fabs(hi))) {
+    __syncthreads();
+    mu = mu_s;
+    if (done_s) {
       conv = true;
       break;
     }
@@ -625,9 +652,13 @@ __global__ void __launch_bounds__(kVecThreads) k_vectors(Ws ws) {
       red[(tid >> 5) * 2 + 1] = sv;
     }
     __syncthreads();
-    const double iu = 1.0 / sqrt(red[0] + red[2]);
-    const double iv = 1.0 / sqrt(red[1] + red[3]);
+    __shared__ double inv_s[2];
+    if (tid == 0) {  // once: FP64 square roots and divisions run at the FP64 rate
+      inv_s[0] = 1.0 / sqrt(red[0] + red[2]);
+      inv_s[1] = 1.0 / sqrt(red[1] + red[3]);
+    }
     __syncthreads();
+    const double iu = inv_s[0], iv = inv_s[1];
     for (int i = tid; i < n; i += kVecThreads) {
       u[i] *= iu;
       v[i] *= iv;
@@ -800,7 +831,7 @@ __device__ void apply_column(const Ws& ws, int j, const StateBuf& st, const Stat
     if (lane == 0) {
       nx.rf[j] = st.hdr->pairs == 0 ? v[r] : rf;
       nx.rl[j] = v[r];
-      nx.S[j] = ldexp(ws.sm.sig[kMaxN + j], ctl->scale_exp);
+      nx.S[j] = ws.sm.sig[kMaxN + j] * __longlong_as_double((long long)(1023 + ctl->scale_exp) << 52);
       if (compact) nx.a[j] = d2f2(a);
     }
   }
