@@ -35,13 +35,20 @@ __device__ __forceinline__ double group4_sum_d(double a) {
   a += __shfl_xor_sync(0xffffffffu, a, 1);
   return a + __shfl_xor_sync(0xffffffffu, a, 2);
 }
-__device__ __forceinline__ double warp_max_d(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
 // nonnegative doubles order like their bit patterns read as integers
 __device__ __forceinline__ long long ord_key(double v) { return __double_as_longlong(v); }
+
+// Asynchronous copies of doubles from global into shared memory (cp.async, 8 bytes each):
+// every thread issues all of its copies before anyone waits, so staging an array costs one
+// L2 round trip instead of one per loop iteration.  Complete with cp_async_wait_all() and a
+// barrier.
+__device__ __forceinline__ void cp_async8(double* dst, const double* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void stage_doubles(double* dst, const double* src, int n, int tid, int nthreads) {
+  for (int i = tid; i < n; i += nthreads) cp_async8(dst + i, src + i);
+}
 
 // ---------------------------------------------------------------------------------------
 // k_prep
@@ -69,11 +76,12 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(Ws ws) {
   __shared__ int defl[kMaxN];
   const float2* red = ws.sm.red;
 
-  for (int idx = tid; idx < r * qld; idx += kPrepThreads) sQ[idx] = st.Q[idx];
+  stage_doubles(sQ, st.Q, r * qld, tid, kPrepThreads);
   for (int i = tid; i < r0; i += kPrepThreads) {
     ac[i] = dd2d(st.a[i]) + dd2d(red[i]);
     yx[i] = dd2d(red[r0 + i]);
   }
+  cp_async_wait_all();
   __syncthreads();
   // p = Q^T ac and w = Q^T y (4 threads per column j < r; Q has r0 rows, the appended
   // coordinate lies outside span(L)); a warp without column work meanwhile decides whether
@@ -173,15 +181,19 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(Ws ws) {
     red8[8 + warp] = zy;
   }
   __syncthreads();
-  // rho, 1/rho and gamma once (FP64 square roots and divisions run at the FP64 rate)
+  // rho, 1/rho and gamma once (FP64 square roots and divisions run at the FP64 rate); the
+  // eight warp partials are added by shuffles in warp 0 (three dependent additions, not seven)
   __shared__ double rho_s, inv_s;
-  if (tid == 0) {
-    zz = 0.0;
-    zy = 0.0;
-    for (int w8 = 0; w8 < 8; ++w8) {
-      zz += red8[w8];
-      zy += red8[8 + w8];
+  if (warp == 0) {
+    zz = lane < 8 ? red8[lane] : 0.0;
+    zy = lane < 8 ? red8[8 + lane] : 0.0;
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+      zz += __shfl_xor_sync(0xffffffffu, zz, o);
+      zy += __shfl_xor_sync(0xffffffffu, zy, o);
     }
+  }
+  if (tid == 0) {
     double rh = sqrt(zz);
     if (!(rh > thr)) rh = 0.0;
     const double iv = rh > 0.0 ? 1.0 / rh : 0.0;
@@ -200,14 +212,23 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(Ws ws) {
   // ---- secular problem of K = [[diag(S), p], [0, rho]], n = r + 1, scaled to max < 1
   if (warp == 0) {
     const int n = r + 1;
-    double mx = 0.0;
+    // the largest magnitude by integer maxima of the bit patterns with the sign cleared
+    // (nonnegative doubles order like their bits; an infinity or NaN orders above every
+    // finite value and is caught below), and its exponent from the bits
+    long long mb = 0;
     for (int i = lane; i < n; i += 32) {
-      mx = fmax(mx, fabs(i < r ? p[i] : rho));
-      if (i == 0 && r > 0) mx = fmax(mx, st.S[0]);
+      mb = max(mb, __double_as_longlong(i < r ? p[i] : rho) & 0x7FFFFFFFFFFFFFFFll);
+      if (i == 0 && r > 0) mb = max(mb, __double_as_longlong(st.S[0]) & 0x7FFFFFFFFFFFFFFFll);
     }
-    mx = warp_max_d(mx);
-    int e = 0;
-    if (mx > 0.0) frexp(mx, &e);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+    const double mx = __longlong_as_double(mb);
+    const int bexp = (int)(mb >> 52);
+    int e = 0;  // mx = f 2^e with f in [1/2, 1)
+    if (bexp > 0 && bexp < 2047)
+      e = bexp - 1022;
+    else if (mb > 0 && bexp == 0)
+      frexp(mx, &e);  // subnormal
     const double tol = 8.0 * kEps64;  // in scaled units
     // 2^-e built from its bits (|e| stays far inside the exponent range of doubles), so each
     // scaling is one exact product
@@ -222,8 +243,15 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(Ws ws) {
       ws.sm.dc[i] = di;
     }
     __syncwarp();
-    if (lane == 0) {
-      // merge nearly equal poles (the pole at 0, coordinate r, is never merged)
+    // merge nearly equal poles (the pole at 0, coordinate r, is never merged).  A pole merges
+    // into the last kept one above it; S is sorted in descending order, so a merge needs two
+    // neighbouring values within tol.  All lanes look for such neighbours (or an unsorted
+    // pair); the sequential merge runs only if they find one.
+    bool near = false;
+    for (int i = lane + 1; i < r; i += 32) near = near || !(dsc[i - 1] - dsc[i] > tol);
+    if (!__any_sync(0xffffffffu, near)) {
+      if (lane == 0) ctl->nrot = 0;
+    } else if (lane == 0) {
       int nrot = 0, last = -1;
       for (int i = 0; i < r; ++i) {
         if (defl[i]) continue;
@@ -280,19 +308,31 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(Ws ws) {
 constexpr int kRootThreads = 128;  // >= kMaxN: one pole per thread in the FP64 sums
 static_assert(kRootThreads >= kMaxN, "one pole per thread");
 
-// block sums of four values; every thread gets the same results (fixed order)
-__device__ __forceinline__ void block_sum4(double (&v)[4], double (*part)[4]) {
+// block sums (every thread gets the same results, in a fixed order): one double, or NF floats
+__device__ __forceinline__ double block_sum_d(double v, double* part) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum_d(v);
+  if (lane == 0) part[warp] = v;
+  __syncthreads();
+  double s = part[0];
+  for (int w = 1; w < kRootThreads / 32; ++w) s += part[w];
+  return s;
+}
+template <int NF>
+__device__ __forceinline__ void block_sum_f(float (&v)[NF], float* part) {  // part: warps x NF
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) v[k] = warp_sum_d(v[k]);
+  for (int k = 0; k < NF; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
   if (lane == 0)
 #pragma unroll
-    for (int k = 0; k < 4; ++k) part[warp][k] = v[k];
+    for (int k = 0; k < NF; ++k) part[warp * NF + k] = v[k];
   __syncthreads();
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    double s = part[0][k];
-    for (int w = 1; w < kRootThreads / 32; ++w) s += part[w][k];
+  for (int k = 0; k < NF; ++k) {
+    float s = part[k];
+    for (int w = 1; w < kRootThreads / 32; ++w) s += part[w * NF + k];
     v[k] = s;
   }
 }
@@ -307,40 +347,48 @@ __global__ void __launch_bounds__(kRootThreads) k_roots(Ws ws) {
   const double* z = ws.sm.z;
   const int tid = threadIdx.x, lane = tid & 31;
   __shared__ float df[kMaxN], zf[kMaxN];
-  __shared__ double part[2][kRootThreads / 32][4];
+  __shared__ float partf[2][kRootThreads / 32 * 3];
+  __shared__ double part64[2][kRootThreads / 32];
   const bool mine = tid < m;
   const double di = mine ? d[tid] : 0.0, zi = mine ? z[tid] : 0.0;
+  const float zif = __double2float_rn(zi);
   if (mine) {
     df[tid] = __double2float_rn(di);
-    zf[tid] = __double2float_rn(zi);
+    zf[tid] = zif;
   }
-  double zs[4] = {zi * zi, 0.0, 0.0, 0.0};
-  block_sum4(zs, part[0]);  // also publishes df, zf
-  const double zsq = zs[0];
   if (m == 1) {
     if (tid == 0) {
+      const double zsq = zi * zi;
       ws.sm.org[0] = 0;
       ws.sm.mu[0] = zsq;
-      ws.sm.sig[0] = sqrt(d[0] * d[0] + zsq);
+      ws.sm.sig[0] = sqrt(di * di + zsq);
     }
     return;
   }
   int o;
   double lo, hi, A, B;  // bracket of mu and the neighbouring poles, relative to d_o^2
   const bool last = (j == m - 1);
-  int it_total = 1;  // parity of the partial-sum buffer in use
+  int it_total = 0;  // parity of the partial-sum buffers in use
   if (!last) {
+    // the side of the interval's midpoint on which the root lies: the sign of f(mid), its
+    // terms in FP64 (a pole per thread), summed in FP32 with an error bound; only when the
+    // bound cannot decide the sign is the sum repeated in FP64
     const double dj = d[j], dj1 = d[j + 1];
     const double gap = (dj1 - dj) * (dj1 + dj);
     const double mid = gap * 0.5;
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
-    if (mine) {
-      const double t = zi / ((di - dj) * (di + dj) - mid);
-      v[0] = zi * t;
+    const double t = mine ? zi * (zi / ((di - dj) * (di + dj) - mid)) : 0.0;
+    float v[2] = {__double2float_rn(t), 0.f};
+    v[1] = fabsf(v[0]);
+    block_sum_f<2>(v, partf[it_total & 1]);
+    const float fm = 1.f + v[0];
+    bool right;  // f(mid) >= 0: the root lies left of the midpoint, next to d_j
+    if (fabsf(fm) > (float)(m + 4) * 0x1p-23f * (1.f + v[1])) {
+      right = fm >= 0.f;
+    } else {
+      right = 1.0 + block_sum_d(t, part64[it_total & 1]) >= 0.0;
     }
-    block_sum4(v, part[it_total & 1]);
     ++it_total;
-    if (1.0 + v[0] >= 0.0) {
+    if (right) {
       o = j;
       lo = 0.0;
       hi = mid;
@@ -354,9 +402,14 @@ __global__ void __launch_bounds__(kRootThreads) k_roots(Ws ws) {
       B = 0.0;
     }
   } else {
+    // the largest root lies below d_last^2 + |z|^2: |z|^2 in FP32 (values below 1 after
+    // the scaling), widened past its rounding error, is the upper end of the bracket
+    float v[1] = {zif * zif};
+    block_sum_f<1>(v, partf[it_total & 1]);
+    ++it_total;
     o = j;
     lo = 0.0;
-    hi = zsq;
+    hi = (double)v[0] * (1.0 + 0x1p-10);
     A = 0.0;
     B = 0.0;
   }
@@ -426,43 +479,52 @@ __global__ void __launch_bounds__(kRootThreads) k_roots(Ws ws) {
     const double cand = (double)muf;
     if (isfinite(muf) && cand > lo && cand < hi) mu = cand;
   }
-  // ---- stage 2: f in FP64 (one pole per thread, summed per warp), then the step by thread 0
+  // ---- stage 2: f in FP64 (one pole per thread, one block sum), then the step by thread 0
   // alone -- the bracket, the tests and the FP32 model step for the correction delta = x - mu
-  // (shifted poles A - mu, B - mu) -- broadcast through shared memory: FP64 operations run
-  // at 1/64 of the FP32 rate, so scalar work is not repeated in every thread
+  // (shifted poles A - mu, B - mu) -- broadcast through shared memory.  FP64 operations run
+  // at 1/64 of the FP32 rate, so scalar work is not repeated in every thread, and what only
+  // steers the iteration is summed in FP32: the derivatives psi', phi' of the model step and
+  // |psi| + |phi| = sum |z_i^2 / (d_i^2 - lambda)| of the stopping test (the terms of psi are
+  // negative and those of phi positive inside the bracket)
   const double ddo = mine ? (di - dob) * (di + dob) : 0.0;  // d_i^2 - d_o^2
   __shared__ double mu_s;
   __shared__ int done_s;
   bool conv = false;
-  __syncthreads();  // every thread is done reading the partial sums of the stages above
   for (int it = 0; it < 100; ++it) {
-    double v[4] = {0.0, 0.0, 0.0, 0.0};  // psi, phi, psi', phi'
+    double term = 0.0;
+    float v[3] = {0.f, 0.f, 0.f};  // sum |term|, psi', phi'
     if (mine) {
       const double t = zi / (ddo - mu);
-      const double term = zi * t, dterm = t * t;
-      if (tid <= j) {
-        v[0] = term;
-        v[2] = dterm;
-      } else {
-        v[1] = term;
-        v[3] = dterm;
-      }
+      term = zi * t;
+      const float tf = __double2float_rn(t);
+      v[0] = fabsf(zif * tf);
+      v[tid <= j ? 1 : 2] = tf * tf;
     }
+    // the FP64 sum and the FP32 sums share one barrier; the buffers alternate between
+    // iterations so a fast thread cannot overwrite partials another is still reading
+    const int pb = it_total & 1;
+    ++it_total;
+    term = warp_sum_d(term);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = warp_sum_d(v[k]);
-    if (lane == 0)
+    for (int k = 0; k < 3; ++k)
 #pragma unroll
-      for (int k = 0; k < 4; ++k) part[0][tid >> 5][k] = v[k];
+      for (int o2 = 16; o2 > 0; o2 >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o2);
+    if (lane == 0) {
+      part64[pb][tid >> 5] = term;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) partf[pb][(tid >> 5) * 3 + k] = v[k];
+    }
     __syncthreads();
     if (tid == 0) {
-      double psi = part[0][0][0], phi = part[0][0][1], dps = part[0][0][2], dph = part[0][0][3];
+      double sum = part64[pb][0];
+      float mag = partf[pb][0], dps = partf[pb][1], dph = partf[pb][2];
       for (int w = 1; w < kRootThreads / 32; ++w) {
-        psi += part[0][w][0];
-        phi += part[0][w][1];
-        dps += part[0][w][2];
-        dph += part[0][w][3];
+        sum += part64[pb][w];
+        mag += partf[pb][w * 3];
+        dps += partf[pb][w * 3 + 1];
+        dph += partf[pb][w * 3 + 2];
       }
-      const double f = 1.0 + psi + phi;
+      const double f = 1.0 + sum;
       if (f < 0.0)
         lo = mu;
       else
@@ -471,7 +533,7 @@ __global__ void __launch_bounds__(kRootThreads) k_roots(Ws ws) {
       // f is formed from sums of terms of one sign each, so its rounding error is a few units
       // of 1 + |psi| + |phi|; stop there (the step and bracket tests below end the iteration
       // when the rounding of f alone moves it)
-      if (fabs(f) <= 8.0 * kEps64 * (1.0 + fabs(psi) + fabs(phi))) {
+      if (fabs(f) <= 8.0 * kEps64 * (1.0 + (double)mag)) {
         stop = 1;
       } else {
         // two-pole model written around mu with f explicit:  f + psi' a d/(a - d) + phi' b
@@ -653,10 +715,8 @@ __global__ void __launch_bounds__(kVecThreads) k_vectors(Ws ws) {
     }
     __syncthreads();
     __shared__ double inv_s[2];
-    if (tid == 0) {  // once: FP64 square roots and divisions run at the FP64 rate
-      inv_s[0] = 1.0 / sqrt(red[0] + red[2]);
-      inv_s[1] = 1.0 / sqrt(red[1] + red[3]);
-    }
+    if (tid < 2)  // once: FP64 reciprocal square roots run at the FP64 rate
+      inv_s[tid] = rsqrt(red[tid] + red[2 + tid]);
     __syncthreads();
     const double iu = inv_s[0], iv = inv_s[1];
     for (int i = tid; i < n; i += kVecThreads) {
@@ -756,28 +816,28 @@ __device__ void apply_column(const Ws& ws, int j, const StateBuf& st, const Stat
   const int n = r + 1, rnew = ctl->rnew;
   const int qld = ws.cap + 1, rm = ws.rmax;
   const double rho = ctl->rho, gamma = ctl->gamma;
-  // every product below runs from shared memory: M (r x r), Q (r0 x r) and the kept left
-  // singular vectors U (rnew x n) are staged first by all threads, coalesced, so that the
+  // every product below runs from shared memory: M (r columns, ld rmax), Q (r columns, ld
+  // cap + 1) and the kept left singular vectors U (rnew columns, ld kMaxN) are copied in with
+  // their global leading dimensions by asynchronous copies all issued at once, so that the
   // short dependent FMA chains wait on shared memory rather than on L2
   extern __shared__ __align__(16) double asm_[];
-  double* sM = asm_;                            // [k][i], ld r
-  double* sQ = sM + (size_t)kMaxR * kMaxR;      // [k][i], ld r0
-  double* sU = sQ + (size_t)kMaxR * (kMaxCap + 1);  // [i][k], ld n
+  double* sM = asm_;                                // [k][i], ld rm
+  double* sQ = sM + (size_t)kMaxR * kMaxR;          // [k][i], ld qld
+  double* sU = sQ + (size_t)kMaxR * (kMaxCap + 1);  // [i][k], ld kMaxN
   __shared__ double v[kMaxN], u[kMaxN], bv[kMaxN], qcol[kMaxCap + 1], rlv;
-  for (int idx = tid; idx < r * r; idx += kApplyThreads) sM[idx] = st.M[(size_t)(idx / r) * rm + idx % r];
-  for (int idx = tid; idx < r * r0; idx += kApplyThreads) sQ[idx] = st.Q[(size_t)(idx / r0) * qld + idx % r0];
-  for (int idx = tid; idx < rnew * n; idx += kApplyThreads) sU[idx] = ws.sm.U[(size_t)(idx / n) * kMaxN + idx % n];
-  for (int i = tid; i < n; i += kApplyThreads) {
-    v[i] = ws.sm.V[(size_t)j * kMaxN + i];
-    u[i] = ws.sm.U[(size_t)j * kMaxN + i];
-  }
+  stage_doubles(sM, st.M, r * rm, tid, kApplyThreads);
+  stage_doubles(sQ, st.Q, r * qld, tid, kApplyThreads);
+  stage_doubles(sU, ws.sm.U, rnew * kMaxN, tid, kApplyThreads);
+  stage_doubles(v, ws.sm.V + (size_t)j * kMaxN, n, tid, kApplyThreads);
+  stage_doubles(u, ws.sm.U + (size_t)j * kMaxN, n, tid, kApplyThreads);
+  cp_async_wait_all();
   __syncthreads();
   // B v, rows 0..r-1: M v[0:r] + w v_r  (4 threads per row; r <= 64 rows)
   {
     const int i = tid >> 2, sub = tid & 3;
     double acc = 0.0;
     if (i < r)
-      for (int k = sub; k < r; k += 4) acc = fma(sM[(size_t)k * r + i], v[k], acc);
+      for (int k = sub; k < r; k += 4) acc = fma(sM[(size_t)k * rm + i], v[k], acc);
     acc = group4_sum_d(acc);
     if (i < r && sub == 0) bv[i] = fma(ws.sm.w[i], v[r], acc);
   }
@@ -794,7 +854,7 @@ __device__ void apply_column(const Ws& ws, int j, const StateBuf& st, const Stat
     const int i = (base + tid) >> 2, sub = tid & 3;
     double acc = 0.0;
     if (i < r0)
-      for (int k = sub; k < r; k += 4) acc = fma(sQ[(size_t)k * r0 + i], u[k], acc);
+      for (int k = sub; k < r; k += 4) acc = fma(sQ[(size_t)k * qld + i], u[k], acc);
     acc = group4_sum_d(acc);
     if (i < r0e && sub == 0) qcol[i] = fma(ws.sm.qn[i], u[r], acc);
   }
@@ -806,7 +866,7 @@ __device__ void apply_column(const Ws& ws, int j, const StateBuf& st, const Stat
     const int i = tid >> 2, sub = tid & 3;
     double acc = 0.0;
     if (i < rnew)
-      for (int k = sub; k < n; k += 4) acc = fma(sU[(size_t)i * n + k], bv[k], acc);
+      for (int k = sub; k < n; k += 4) acc = fma(sU[(size_t)i * kMaxN + k], bv[k], acc);
     acc = group4_sum_d(acc);
     if (i < rnew && sub == 0) nx.M[(size_t)j * rm + i] = acc;
   }

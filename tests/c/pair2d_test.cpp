@@ -1,17 +1,46 @@
 // Host test of pair_to_double (csrc/pair2d.cuh): the double built from a double-float pair by
-// integer operations must equal, bit for bit, the correctly rounded h 2^sc + l 2^sc.
+// integer operations must equal, bit for bit, the correctly rounded h 2^sc + l 2^sc.  For a
+// normalized pair (|l| <= ulp(h) / 2), pair_to_double_fast must give the same double or, at an
+// exact tie, the other of the two nearest doubles.
 #include <cmath>
 #include <cstdio>
 #include <random>
 
 #include "pair2d.cuh"
 
-static long fails = 0, checked = 0;
+static long fails = 0, checked = 0, fast_checked = 0, fast_fails = 0, fast_ties = 0;
+
+// a tie: h + l lies exactly halfway between want and its neighbour `other`
+static bool is_tie(float h, float l, double want, double other) {
+  // h - want is exact (want lies within an ulp of h), and so is adding l to it here
+  const double rest = ((double)h - want) + (double)l;
+  return rest != 0.0 && 2.0 * rest == other - want;
+}
+
+static void check_fast(float h, float l, int sc) {
+  int e;
+  std::frexp(h, &e);
+  if (h != 0.f && std::fabs((double)l) > std::ldexp(1.0, e - 25)) return;  // not normalized
+  const double want = std::ldexp((double)h + (double)l, sc);
+  const double got = odmd::pair_to_double_fast(h, l, sc);
+  ++fast_checked;
+  if (std::memcmp(&got, &want, 8) == 0) return;
+  const double want0 = (double)h + (double)l;
+  const double got0 = std::ldexp(got, -sc);
+  if ((got0 == std::nextafter(want0, INFINITY) || got0 == std::nextafter(want0, -INFINITY)) &&
+      is_tie(h, l, want0, got0)) {
+    ++fast_ties;
+    return;
+  }
+  if (fast_fails < 10) std::printf("fast: h=%a l=%a sc=%d got %a want %a\n", h, l, sc, got, want);
+  ++fast_fails;
+}
 
 static void check(float h, float l, int sc) {
   const double want = std::ldexp((double)h + (double)l, sc);  // one rounding, then exact scaling
   const double got = odmd::pair_to_double(h, l, sc);
   ++checked;
+  check_fast(h, l, sc);
   if (std::memcmp(&got, &want, 8) != 0) {
     if (fails < 10) std::printf("h=%a l=%a sc=%d got %a want %a\n", h, l, sc, got, want);
     ++fails;
@@ -52,5 +81,7 @@ int main() {
   check(0.f, 0.f, 5);
   check(-0.f, 0.f, 5);
   std::printf("%ld checked, %ld mismatches\n", checked, fails);
-  return fails == 0 ? 0 : 1;
+  std::printf("fast: %ld checked, %ld ties rounded the other way, %ld failures\n", fast_checked, fast_ties,
+              fast_fails);
+  return fails == 0 && fast_fails == 0 ? 0 : 1;
 }
