@@ -1,5 +1,5 @@
 // Tall x small products of the double-float basis on the tensor cores, exact to the
-// double-float level through a split of both operands into 7-bit digits (Ozaki's scheme: an
+// double-float level through a split of both operands into 8-bit digits (Ozaki's scheme: an
 // error-free splitting into slices whose products a lower-precision unit sums exactly):
 //   rollout     X = L0 C: u(t) = Phi Lambda^t b for many t at once (Sec. 2.3) is the tall
 //               N x r0 basis times a small r0 x k coefficient block; X in doubles;
@@ -7,24 +7,27 @@
 //               append kept as L = L0 Q): the new column j0 = (e - L0 s) / rho0 is formed per
 //               row from the stored residual, and the product is written back in place.
 //
-// Each row i of L0 (double-float hi + lo) is written on its own power-of-two grid,
-// a_ik = sum_{s=1..7} d_iks 2^(e_i - 7 s), and each column j of C on its own,
-// c_kj = sum_{t=1..7} d'_kjt 2^(f_j - 7 t), with integer digits |d| <= 128 (exact in
-// bfloat16); what is left after seven digits is below 2^-49 of the row (column) maximum.
-// Products of digits with s + t = g are integers on the common grid 2^(e_i + f_j - 7 g): the
-// 28 digit pairs with g <= 8 are bfloat16 products (tcgen05.mma kind::f16, M = 128, N = 64,
-// K = 16) into seven FP32 accumulators in tensor memory, one per g.  A group adds at most
-// 7 K products of |d d'| <= 2^14 with K <= 64, below 2^24, so every partial sum is an
-// integer the FP32 accumulator holds exactly; pairs with g >= 9 are below 2^-49 K of
-// max|a_i| max|c_j| and are left out.  The epilogue adds the seven group sums, scaled by
-// 2^(56 - 7 g) (all exact floats), in double-float and scales the result by 2^(e_i + f_j -
-// 56), which is the double-float accuracy of the CUDA-core path; a rollout's doubles are
-// assembled from the pair by integer operations (pair2d.cuh: FP64 conversions run at the
-// FP64 rate on this GPU).
+// Each row i of L0 (double-float hi + lo, |a_ik| < 2^e_i) is put on the fixed-point grid
+// 2^(e_i - 54): the integer I = round(hi 2^(54 - e_i)) + round(lo 2^(54 - e_i)) (within one
+// unit, 2^-53 of the row maximum; |I| < 2^54).  Adding 0x80 to each of its seven bytes makes
+// every byte b of I + 0x80808080808080 a balanced digit d = b - 128, |d| <= 128 (exact in
+// bfloat16, the top one |d| <= 64): a_ik = sum_{s=1..7} d_iks 2^(e_i - 54 + 8 (7 - s)), formed
+// by integer shifts and byte moves.  Each column j of C is written the same way on its own
+// grid 2^(f_j - 54).  Products of digits with s + t = g are integers on the common grid
+// 2^(e_i + f_j - 108 + 8 (14 - g)): the 28 digit pairs with g <= 8 are bfloat16 products
+// (tcgen05.mma kind::f16, M = 128, N = 64, K = 16) into seven FP32 accumulators in tensor
+// memory, one per g.  A group adds at most 7 K products of |d d'| <= 2^14 with K <= 64, below
+// 2^24, so every partial sum is an integer the FP32 accumulator holds exactly; pairs with
+// g >= 9 are below 2^-48 K of max|a_i| max|c_j| and are left out.  The epilogue adds the
+// seven group sums, scaled by 2^(8 (8 - g)) (all exact floats), in double-float (two
+// outputs per FP32x2 instruction) and scales the result by 2^(e_i + f_j - 60), which is the
+// double-float accuracy of the CUDA-core path; a rollout's doubles are assembled from the
+// pair by integer operations (pair2d.cuh: FP64 conversions run at the FP64 rate on this
+// GPU).
 //
 // One persistent CTA of 256 threads per SM (the seven accumulators take 448 of the SM's 512
 // tensor-memory columns).  C's digits are formed once per CTA.  A 128-row tile of L0 (both
-// planes) arrives by two bulk copies into a staging buffer; two threads per row form its
+// planes) arrives by two bulk copies into a staging buffer; four threads per row form its
 // digits, 32 basis columns (two K chunks) at a time, into the K-major core-matrix layout
 // the descriptors describe (tc.cuh); one thread issues the chunk's 28 MMAs and commits them
 // to an mbarrier; once the last digits of a tile are formed the staging buffer takes the
@@ -57,33 +60,56 @@ static_assert(kGroups * kNJ <= (int)kTmemCols, "seven accumulators fit the tenso
 static_assert(7 * kMaxK * (1 << 14) < (1 << 24), "group sums stay below 2^24");
 
 // staging buffer: the two basis planes of a tile, then the tile's stored residual (8 bytes a row)
-// 2^(42 - 7 q): the scale of group g = q + 2 relative to the smallest group (g = 8)
-__constant__ float kGroupScale[kGroups] = {0x1p42f, 0x1p35f, 0x1p28f, 0x1p21f, 0x1p14f, 0x1p7f, 1.0f};
+// 2^(8 (6 - q)): the scale of group g = q + 2 relative to the smallest group (g = 8)
+__device__ __forceinline__ float group_scale(int q) { return __int_as_float((127 + 8 * (6 - q)) << 23); }
+constexpr int kGridBits = 54;  // values on the grid 2^(e - 54): |I| < 2^54, seven bytes
+constexpr long long kDigitBias = 0x80808080808080ll;
 
 __host__ __device__ inline int stage_bytes(int rs) { return ((2 * kTM * rs + kTM * 8 + 1023) / 1024) * 1024; }
 __host__ __device__ inline int smem_bytes(int rs) { return stage_bytes(rs) + kSlices * kASlice + kSlices * kBSlice; }
 
-// exponent e with |v| < 2^e for every v of a set with maximum mx (0 for mx = 0)
+// exponent e with |v| < 2^e for every double-float v of a set whose largest |hi| is mx (from
+// the bits of mx; 0 for mx = 0): |hi + lo| < 2^e as well, since |lo| <= ulp(hi) / 2
 __device__ __forceinline__ int grid_exp(float mx) {
-  if (!(mx > 0.f)) return 0;
-  int e;
-  frexpf(mx, &e);
-  return e;
+  const int ex = (int)((__float_as_uint(mx) >> 23) & 0xFFu);
+  return mx > 0.f ? (ex ? ex : 1) - 126 : 0;
 }
 
-// the seven digits of v = h + l on the grid 2^(e - 7 s), s = 1..7, as bfloat16 bits: with
-// w = v 2^-e (|w| < 1), each step takes q = rint(128 w) and keeps 128 w - q (exact)
-__device__ __forceinline__ void digits7(float h, float l, int e, uint16_t (&d)[kSlices]) {
-  float wh = ldexpf(h, -e), wl = ldexpf(l, -e);
-#pragma unroll
-  for (int s = 0; s < kSlices; ++s) {
-    const float th = wh * 128.f, tl = wl * 128.f;
-    const float q = rintf(th);
-    const dd r = fast_two_sum(th - q, tl);
-    wh = r.h;
-    wl = r.l;
-    d[s] = __bfloat16_as_ushort(__float2bfloat16_rn(q));
-  }
+// round(x 2^k) as an integer, by shifting the significand (|x| < 2^(54 - k) keeps it below 2^54)
+__device__ __forceinline__ long long fixed_part(float x, int k) {
+  const uint32_t ux = __float_as_uint(x);
+  const int ex = (int)((ux >> 23) & 0xFFu);
+  const uint32_t m = (ux & 0x7FFFFFu) | (ex ? 0x800000u : 0u);
+  const int sh = (ex ? ex : 1) - 150 + k;
+  long long v = 0;
+  if (sh >= 0)
+    v = (long long)m << sh;
+  else if (sh > -32)
+    v = (long long)((m + (1u << (-sh - 1))) >> (-sh));
+  return (ux >> 31) ? -v : v;
+}
+
+// the biased fixed-point value of h + l on the grid 2^(e - 54): its byte s (from the top)
+// less 128 is digit s
+__device__ __forceinline__ unsigned long long biased_fixed(float h, float l, int e) {
+  const int k = kGridBits - e;
+  return (unsigned long long)(fixed_part(h, k) + fixed_part(l, k) + kDigitBias);
+}
+
+// digit s = 1..7 (most significant first) of a biased fixed-point value, as an exact float:
+// the byte is moved under the exponent of 2^23 (a float 2^23 + b), then 2^23 + 128 is taken off
+template <int S>
+__device__ __forceinline__ float digit_f(unsigned long long u) {
+  constexpr int byte = 7 - S;  // byte 6 holds digit 1
+  const uint32_t w = byte >= 4 ? (uint32_t)(u >> 32) : (uint32_t)u;
+  return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540u | (byte & 3))) - 8388736.0f;
+}
+
+// two values' digit s as a bfloat16 pair (the first value in the low half)
+template <int S>
+__device__ __forceinline__ uint32_t digit_pair(unsigned long long u0, unsigned long long u1) {
+  const __nv_bfloat162 p = __floats2bfloat162_rn(digit_f<S>(u0), digit_f<S>(u1));
+  return *reinterpret_cast<const uint32_t*>(&p);
 }
 
 // the tile's rows of both planes (and of the stored residual e when `with_e`) into the stage;
@@ -168,9 +194,16 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(Ws ws, int kcols, double
       h = q.x;
       l = q.y;
     }
-    uint16_t d[kSlices];
-    digits7(h, l, fexp[j], d);
+    const unsigned long long u = biased_fixed(h, l, fexp[j]);
     const int off = tc::kmajor_off(j, k, kMaxK / 8);
+    uint16_t d[kSlices];
+    d[0] = __bfloat16_as_ushort(__float2bfloat16_rn(digit_f<1>(u)));
+    d[1] = __bfloat16_as_ushort(__float2bfloat16_rn(digit_f<2>(u)));
+    d[2] = __bfloat16_as_ushort(__float2bfloat16_rn(digit_f<3>(u)));
+    d[3] = __bfloat16_as_ushort(__float2bfloat16_rn(digit_f<4>(u)));
+    d[4] = __bfloat16_as_ushort(__float2bfloat16_rn(digit_f<5>(u)));
+    d[5] = __bfloat16_as_ushort(__float2bfloat16_rn(digit_f<6>(u)));
+    d[6] = __bfloat16_as_ushort(__float2bfloat16_rn(digit_f<7>(u)));
 #pragma unroll
     for (int s = 0; s < kSlices; ++s) *reinterpret_cast<uint16_t*>(bdig + s * kBSlice + off) = d[s];
   }
@@ -190,6 +223,11 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(Ws ws, int kcols, double
   const int my_tiles = (int)((ntiles - blockIdx.x + G - 1) / G);
   if (tid == 0 && my_tiles > 0) issue_tile(ws, stage, rs, blockIdx.x, with_e, &bar_tma);
   const uint32_t idesc = tc::instr_desc_bf16_f32(kTM, kNJ);
+  // descriptors of digit slice 1 at chunk 0; every other operand differs only in its start
+  // address, so its descriptor is this one plus (byte offset >> 4) in the start field (shared
+  // memory addresses stay below 2^18, so the field never carries)
+  const uint64_t adesc0 = tc::smem_desc(smem_addr(adig), tc::kCoreBytes, (kBufK / 8) * tc::kCoreBytes);
+  const uint64_t bdesc0 = tc::smem_desc(smem_addr(bdig), tc::kCoreBytes, (kMaxK / 8) * tc::kCoreBytes);
   uint32_t par_tma = 0, par_mma = 0;
   // work in flight that a timeout must still wait for (the same in every thread)
   bool tma_out = my_tiles > 0, mma_out = false;
@@ -253,7 +291,6 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(Ws ws, int kcols, double
           uint32_t w[kSlices][4];
 #pragma unroll
           for (int kk = 0; kk < 8; kk += 2) {
-            uint16_t d0[kSlices], d1[kSlices];
             const int k = kb + kk;
             float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
             if (k < r0) {
@@ -270,10 +307,14 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(Ws ws, int kcols, double
               h1 = jh[row];
               l1 = jl[row];
             }
-            digits7(h0, l0, my_e, d0);
-            digits7(h1, l1, my_e, d1);
-#pragma unroll
-            for (int s = 0; s < kSlices; ++s) w[s][kk >> 1] = (uint32_t)d0[s] | ((uint32_t)d1[s] << 16);
+            const unsigned long long u0 = biased_fixed(h0, l0, my_e), u1 = biased_fixed(h1, l1, my_e);
+            w[0][kk >> 1] = digit_pair<1>(u0, u1);
+            w[1][kk >> 1] = digit_pair<2>(u0, u1);
+            w[2][kk >> 1] = digit_pair<3>(u0, u1);
+            w[3][kk >> 1] = digit_pair<4>(u0, u1);
+            w[4][kk >> 1] = digit_pair<5>(u0, u1);
+            w[5][kk >> 1] = digit_pair<6>(u0, u1);
+            w[6][kk >> 1] = digit_pair<7>(u0, u1);
           }
 #pragma unroll
           for (int s = 0; s < kSlices; ++s)
@@ -293,16 +334,15 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(Ws ws, int kcols, double
         if (last_digits && li + 1 < my_tiles) issue_tile(ws, stage, rs, tile + G, with_e, &bar_tma);
         tc::fence_after_sync();
         for (int cc = c0; cc < c0 + 2 && cc < nchunk; ++cc) {
-          const uint32_t aoff = (uint32_t)((cc - c0) * 2 * tc::kCoreBytes);
-          const uint32_t boff = (uint32_t)(cc * 2 * tc::kCoreBytes);
+          const uint64_t ab = adesc0 + (uint64_t)(((cc - c0) * 2 * tc::kCoreBytes) >> 4);
+          const uint64_t bb = bdesc0 + (uint64_t)((cc * 2 * tc::kCoreBytes) >> 4);
+#pragma unroll
           for (int gs = 2; gs <= 8; ++gs)
-            for (int s = 1; s < gs && s <= kSlices; ++s) {
-              const int t = gs - s;
-              if (t > kSlices) continue;
-              const uint64_t ad = tc::smem_desc(smem_addr(adig + (s - 1) * kASlice) + aoff, tc::kCoreBytes,
-                                                (kBufK / 8) * tc::kCoreBytes);
-              const uint64_t bd = tc::smem_desc(smem_addr(bdig + (t - 1) * kBSlice) + boff, tc::kCoreBytes,
-                                                (kMaxK / 8) * tc::kCoreBytes);
+#pragma unroll
+            for (int s = 1; s < gs; ++s) {
+              const int t = gs - s;  // s, t <= 7 since g <= 8
+              const uint64_t ad = ab + (uint64_t)(((s - 1) * kASlice) >> 4);
+              const uint64_t bd = bb + (uint64_t)(((t - 1) * kBSlice) >> 4);
               const uint32_t acc = (cc > 0 || s > 1) ? 1u : 0u;
               tc::mma_bf16(tmem + (uint32_t)((gs - 2) * kNJ), ad, bd, idesc, acc);
             }
@@ -322,7 +362,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(Ws ws, int kcols, double
     }
     if (!ok) break;
     // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows) and 16 columns
-    // (quarter w / 4); X = 2^(e_i + f_j - 56) sum_g G_g 2^(56 - 7 g)
+    // (quarter w / 4); X = 2^(e_i + f_j - 60) sum_g G_g 2^(8 (8 - g))
     {
       const int trow = 32 * (warp & 3) + lane;
       const int64_t orow = row0 + trow;
@@ -343,23 +383,28 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(Ws ws, int kcols, double
         float vh[8], vl[8];
         int sc[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          // every term G_g 2^(56 - 7 g) is an exact float (|G_g| < 2^23): a cascaded sum,
+        for (int u = 0; u < 8; u += 2) {
+          // every term G_g 2^(8 (8 - g)) is an exact float (|G_g| < 2^24): a cascaded sum,
           // smallest term first, with the exact rounding error of each addition (two-sum)
-          // gathered in a second float, then one renormalization
-          float sh_ = __uint_as_float(g[kGroups - 1][u]), el = 0.f;
+          // gathered in a second float, then one renormalization; columns u and u + 1 share
+          // each FP32x2 instruction
+          f2x sh2 = f2x_pack(__uint_as_float(g[kGroups - 1][u]), __uint_as_float(g[kGroups - 1][u + 1]));
+          f2x el2 = 0ull;
 #pragma unroll
           for (int q = kGroups - 2; q >= 0; --q) {
-            const float t = __fmul_rn(__uint_as_float(g[q][u]), kGroupScale[q]);
-            const float s2 = __fadd_rn(sh_, t);
-            const float bb = __fsub_rn(s2, sh_);
-            el = __fadd_rn(el, __fadd_rn(__fsub_rn(sh_, __fsub_rn(s2, bb)), __fsub_rn(t, bb)));
-            sh_ = s2;
+            const f2x t = mul2(f2x_pack(__uint_as_float(g[q][u]), __uint_as_float(g[q][u + 1])),
+                               f2x_pack(group_scale(q), group_scale(q)));
+            const f2x s2 = add2(sh2, t);
+            const f2x bb = sub2(s2, sh2);
+            el2 = add2(el2, add2(sub2(sh2, sub2(s2, bb)), sub2(t, bb)));
+            sh2 = s2;
           }
-          const dd sum = fast_two_sum(sh_, el);
-          vh[u] = sum.h;
-          vl[u] = sum.l;
-          sc[u] = er + fexp[jb + c8 + u] - 56;  // the value is 2^sc (vh + vl)
+          const f2x hs = add2(sh2, el2);  // fast two-sum: |sh| >= |el|
+          const f2x ls = sub2(el2, sub2(hs, sh2));
+          f2x_unpack(hs, vh[u], vh[u + 1]);
+          f2x_unpack(ls, vl[u], vl[u + 1]);
+          sc[u] = er + fexp[jb + c8 + u] - 60;  // the value is 2^sc (vh + vl)
+          sc[u + 1] = er + fexp[jb + c8 + u + 1] - 60;
         }
         if constexpr (COMPACT) {
           // whole 8-column pieces of the row as two 16-byte stores per plane
@@ -394,7 +439,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(Ws ws, int kcols, double
 #pragma unroll
           for (int u = 0; u < 8; ++u)
             if (jb + c8 + u < J)  // the double's bits from the pair by integer operations
-              out[(size_t)(jb + c8 + u) * ld + orow] = pair_to_double(vh[u], vl[u], sc[u]);
+              out[(size_t)(jb + c8 + u) * ld + orow] = pair_to_double_fast(vh[u], vl[u], sc[u]);
         }
       }
     }
