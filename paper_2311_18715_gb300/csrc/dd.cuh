@@ -10,6 +10,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "pair2d.cuh"
+
 namespace odmd {
 
 struct dd {
@@ -20,15 +22,22 @@ __device__ __forceinline__ dd dd_of(float h) { return dd{h, 0.f}; }
 __device__ __forceinline__ dd dd_of(float2 v) { return dd{v.x, v.y}; }
 __device__ __forceinline__ float2 f2_of(dd a) { return make_float2(a.h, a.l); }
 __device__ __forceinline__ double dd_to_double(dd a) { return (double)a.h + (double)a.l; }
+// a double as the pair h = RN(x), l = RN(x - h): from x's bits by integer operations
+// (pair2d.cuh; conversions and subtractions run at the FP64 rate), by conversions when a
+// part falls outside the normal float range
 __device__ __forceinline__ dd dd_from_double(double x) {
-  const float h = __double2float_rn(x);
-  return dd{h, __double2float_rn(x - (double)h)};
+  dd r;
+  if (!double_to_pair_fast(x, r.h, r.l)) {
+    r.h = __double2float_rn(x);
+    r.l = __double2float_rn(x - (double)r.h);
+  }
+  return r;
 }
 // a float pair (hi, lo) as the double it represents exactly, and a double rounded to a pair
 __device__ __forceinline__ double dd2d(float2 v) { return (double)v.x + (double)v.y; }
 __device__ __forceinline__ float2 d2f2(double x) {
-  const float h = __double2float_rn(x);
-  return make_float2(h, __double2float_rn(x - (double)h));
+  const dd r = dd_from_double(x);
+  return make_float2(r.h, r.l);
 }
 
 __device__ __forceinline__ dd fast_two_sum(float a, float b) {

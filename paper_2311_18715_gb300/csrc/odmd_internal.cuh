@@ -10,6 +10,7 @@
 #include <string>
 
 #include "odmd.h"
+#include "pair2d.cuh"
 #include <cstdint>
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -324,9 +325,13 @@ __device__ __forceinline__ void acc2_split(Acc2 A, Acc& a0, Acc& a1) {
   f2x_unpack(A.l, a0.l, a1.l);
 }
 
+// h = RN(x), l = RN(x - h): by integer operations on x's bits (pair2d.cuh), by conversions
+// (FP64 rate) when a part leaves the normal float range
 __device__ __forceinline__ void split_double(double x, float& h, float& l) {
-  h = __double2float_rn(x);
-  l = __double2float_rn(x - (double)h);
+  if (!double_to_pair_fast(x, h, l)) {
+    h = __double2float_rn(x);
+    l = __double2float_rn(x - (double)h);
+  }
 }
 
 __device__ __forceinline__ double join_double(float h, float l) { return (double)h + (double)l; }

@@ -24,6 +24,9 @@ namespace odmd {
 __device__ __forceinline__ uint32_t p2d_bits(float f) { return __float_as_uint(f); }
 __device__ __forceinline__ double p2d_double(uint64_t b) { return __longlong_as_double((long long)b); }
 __device__ __forceinline__ int p2d_clz64(uint64_t x) { return __clzll((long long)x); }
+__device__ __forceinline__ uint64_t p2d_dbits(double d) { return (uint64_t)__double_as_longlong(d); }
+__device__ __forceinline__ float p2d_float(uint32_t u) { return __uint_as_float(u); }
+__device__ __forceinline__ int p2d_clz32(uint32_t x) { return __clz((int)x); }
 #else
 inline uint32_t p2d_bits(float f) {
   uint32_t u;
@@ -36,6 +39,17 @@ inline double p2d_double(uint64_t b) {
   return d;
 }
 inline int p2d_clz64(uint64_t x) { return x ? __builtin_clzll(x) : 64; }
+inline uint64_t p2d_dbits(double d) {
+  uint64_t u;
+  std::memcpy(&u, &d, 8);
+  return u;
+}
+inline float p2d_float(uint32_t u) {
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+inline int p2d_clz32(uint32_t x) { return x ? __builtin_clz(x) : 32; }
 #endif
 
 __host__ __device__ inline double pair_to_double(float h, float l, int sc) {
@@ -125,6 +139,57 @@ __host__ __device__ inline double pair_to_double_fast(float h, float l, int sc) 
   const uint64_t bits = ((uint64_t)(uh >> 31) << 63) | ((uint64_t)(uint32_t)((int)eh + 896 + sc) << 52) |
                         ((uint64_t)(uh & 0x7FFFFFu) << 29);
   return p2d_double(opp ? bits - delta : bits + delta);
+}
+
+// The other direction: a double x as the pair h = RN(x), l = RN(x - h) (round to nearest
+// even, both as floats), which is exactly what two conversions and a subtraction give, built
+// from x's bits with integer operations: the 53-bit significand is rounded to 24 bits for h,
+// and the signed remainder (at most 29 bits) is rounded to 24 for l.  When x, h or l falls
+// outside the normal float range (zero, subnormal, overflow, a non-finite x), the result
+// comes from the conversions instead (`false` is returned for the caller's slow path on the
+// device; the host version converts itself).
+__host__ __device__ inline bool double_to_pair_fast(double x, float& h, float& l) {
+  const uint64_t b = p2d_dbits(x);
+  const uint32_t sign = (uint32_t)(b >> 63);
+  const int E = (int)((b >> 52) & 0x7FFu);
+  int ef = E - 1023 + 127;  // the float exponent field of x's binade
+  if (ef < 1 || ef > 254) return false;
+  const uint64_t m = (b & ((1ull << 52) - 1)) | (1ull << 52);
+  uint32_t q = (uint32_t)(m >> 29);
+  const uint32_t rem = (uint32_t)(m & ((1u << 29) - 1));
+  const bool up = rem > (1u << 28) || (rem == (1u << 28) && (q & 1u));
+  q += up ? 1u : 0u;
+  if (q == (1u << 24)) {  // rounded up to the next binade
+    q = 1u << 23;
+    ++ef;
+    if (ef > 254) return false;
+  }
+  h = p2d_float((sign << 31) | ((uint32_t)ef << 23) | (q & 0x7FFFFFu));
+  // x - h = r 2^(E - 1075), |r| <= 2^28 (negative when h was rounded up in magnitude)
+  const int32_t r = (int32_t)rem - (up ? (int32_t)(1u << 29) : 0);
+  if (r == 0) {
+    l = 0.f;
+    return true;
+  }
+  uint32_t a = (uint32_t)(r < 0 ? -r : r);
+  int lead = 31 - p2d_clz32(a);  // 0 .. 28
+  uint32_t mant;
+  if (lead <= 23) {
+    mant = a << (23 - lead);
+  } else {
+    const int sh = lead - 23;
+    mant = a >> sh;
+    const uint32_t rest = a & ((1u << sh) - 1u), half = 1u << (sh - 1);
+    if (rest > half || (rest == half && (mant & 1u))) ++mant;
+    if (mant == (1u << 24)) {
+      mant = 1u << 23;
+      ++lead;
+    }
+  }
+  const int el = lead + E - 948;  // biased exponent of l: a 2^(E - 1075) = 1.f 2^(lead + E - 1075)
+  if (el < 1) return false;
+  l = p2d_float(((sign ^ (r < 0 ? 1u : 0u)) << 31) | ((uint32_t)el << 23) | (mant & 0x7FFFFFu));
+  return true;
 }
 
 }  // namespace odmd

@@ -722,36 +722,70 @@ __global__ void __launch_bounds__(64) k_coef(Ws ws, TArr ts, int k) {
 
 // Rollout coefficients for integer horizons without the eigensolve: with A~ = V Lambda V^-1
 // and b = V^-1 y, y = S * r_first = L^T u^0,  V Lambda^t b = A~^t y  exactly, so
-// coef[:, j] = Q A~^{t_j} y.  The horizons are taken in ascending order (ord): the vector
-// advances by single products with A~ over short gaps and by binary powering (repeated
-// squaring of A~, applied to the vector on set bits) over long ones.  Double-float
-// throughout; one CTA.
-constexpr int kPowThreads = 1024;  // eight warps per scheduler hide the latency of the dependent double-float sums
-constexpr int kPowDirect = 8;  // gaps up to this many steps: repeated products
-// row stride of the r x r matrices: one element more than kMaxR, so that the rows a warp
-// reads at the same column fall in different shared-memory banks
-constexpr int kPowLd = kMaxR + 1;
+// coef[:, j] = Q A~^{t_j} y.  The horizons are taken in ascending order (ord).  The vector
+// reaches the first horizon t_1 by single products with A~ over a short gap and by binary
+// powering (repeated squaring of A~, applied to the vector on set bits) over a long one.
+// When every other horizon lies within 63 steps of t_1 (a rollout of consecutive states),
+// the vectors of all offsets 0 .. span-1 come from doubling rounds: round k multiplies the
+// 2^k vectors of offsets 0 .. 2^k - 1 by A~^(2^k) at once (a small matrix product), so 50
+// horizons take six products instead of 49 dependent ones.  Otherwise the horizons are
+// reached one after another as before.  Then coef = Q C for all horizons in one product.
+// Double-float throughout (the products accumulate two columns per FP32x2 instruction);
+// one CTA.  Q and A~ = M diag(S)^-1 are rounded from their FP64 state to double-float once,
+// into shared memory.
+constexpr int kPowThreads = 1024;
+constexpr int kPowDirect = 8;   // a gap up to this many steps: repeated products
+constexpr int kPowLd = kMaxR + 2;  // even row stride: column pairs are 8-byte aligned
+constexpr int kPowSpan = 64;    // offsets from the first horizon formed by doubling
+constexpr int kPowQRows = kMaxCap + 1;
 
 struct PowSmem {
-  float2 A[kMaxR * kPowLd];  // A~, row-major
-  float2 P[kMaxR * kPowLd];  // current power of A~
-  float2 T[kMaxR * kPowLd];  // scratch of a squaring
-  float2 v[2][kMaxR];        // the vector, ping-pong
-  float2 C[kRollK * kMaxR];  // A~^{t_j} y for every horizon j (row j)
+  float Ah[kMaxR * kPowLd], Al[kMaxR * kPowLd];  // A~ (row-major planes: hi, lo)
+  float Ph[kMaxR * kPowLd], Pl[kMaxR * kPowLd];  // a power of A~
+  float Th[kMaxR * kPowLd], Tl[kMaxR * kPowLd];  // the next power (squaring output)
+  float Vh[kMaxR * kPowLd], Vl[kMaxR * kPowLd];  // vectors as columns (an offset or a horizon each)
+  float Qh[kPowQRows * kPowLd], Ql[kPowQRows * kPowLd];  // Q (r0 x r, row-major)
+  float wh[2][kMaxR * 2], wl[2][kMaxR * 2];  // the advancing vector, ping-pong (column 0 of ld 2)
+  int col_of[kRollK];                         // the column of Vh/Vl that holds horizon j
 };
 
-// out = B v (B row-major r x r in shared memory), 4 threads per row
-__device__ __forceinline__ void pow_matvec(const float2* B, const float2* v, float2* out, int r) {
-  const int tid = threadIdx.x;
-  for (int base = 0; base < 4 * r; base += kPowThreads) {
-    const int i = (base + tid) >> 2, sub = tid & 3;
-    dd acc = dzero();
-    if (i < r)
-      for (int l = sub; l < r; l += 4) acc = dd_fma(LD(B, (size_t)i * kPowLd + l), LD(v, l), acc);
-    acc = group4_sum(acc);
-    if (i < r && sub == 0) out[i] = f2_of(acc);
+// Out[i][oc0 + c] = sum_{l < kdim} X[i][l] Y[l][c0 + c] for i < rows, c < ncol (planes
+// row-major with the given row strides; c0, yld even).  A thread forms two adjacent output
+// columns with packed double-float accumulation (acc2_fma); an odd last column pairs with
+// zero instead of reading past the range.  `store(i, c, acc)` writes output column c.
+template <class Store>
+__device__ __forceinline__ void mm_dd(const float* Xh, const float* Xl, int xld, const float* Yh, const float* Yl,
+                                      int yld, int c0, int rows, int kdim, int ncol, Store store) {
+  const int npairs = (ncol + 1) >> 1;
+  for (int it = threadIdx.x; it < rows * npairs; it += kPowThreads) {
+    const int i = it / npairs, c = 2 * (it - i * npairs);
+    const bool pair = c + 1 < ncol;
+    Acc2 acc = acc2_zero();
+    for (int l = 0; l < kdim; ++l) {
+      const float xh = Xh[i * xld + l], xl = Xl[i * xld + l];
+      const float* yh = Yh + l * yld + c0 + c;
+      const float* yl = Yl + l * yld + c0 + c;
+      const f2x ph = pair ? *reinterpret_cast<const f2x*>(yh) : f2x_pack(yh[0], 0.f);
+      const f2x pl = pair ? *reinterpret_cast<const f2x*>(yl) : f2x_pack(yl[0], 0.f);
+      acc2_fma(acc, ph, pl, f2x_pack(xh, xh), f2x_pack(-xh, -xh), f2x_pack(xl, xl));
+    }
+    Acc a0, a1;
+    acc2_split(acc, a0, a1);
+    store(i, c, acc_norm(a0));
+    if (pair) store(i, c + 1, acc_norm(a1));
   }
 }
+
+// a store into a row-major plane pair at column offset oc0
+struct PlaneStore {
+  float* h;
+  float* l;
+  int ld, oc0;
+  __device__ void operator()(int i, int c, Acc a) const {
+    h[i * ld + oc0 + c] = a.h;
+    l[i * ld + oc0 + c] = a.l;
+  }
+};
 
 __global__ void __launch_bounds__(kPowThreads) k_coef_pow(Ws ws, TArr ts, TOrd ord, int k) {
   extern __shared__ __align__(16) unsigned char pow_raw[];
@@ -764,92 +798,141 @@ __global__ void __launch_bounds__(kPowThreads) k_coef_pow(Ws ws, TArr ts, TOrd o
     if (tid == 0) atomicOr(&ctl->status, DEV_NOMODEL);
     return;
   }
+  if (k <= 0) return;
+  // A~ = M diag(S)^-1 (one FP64 reciprocal per column) and Q, rounded to double-float once
+  __shared__ double sinv[kMaxR];
+  __shared__ int bad;
+  for (int l = tid; l < r; l += kPowThreads) sinv[l] = 1.0 / st.S[l];
+  if (tid == 0) bad = 0;
+  __syncthreads();
   for (int idx = tid; idx < r * r; idx += kPowThreads) {
-    const int i = idx / r, l = idx % r;
-    S.A[i * kPowLd + l] = f2_of(dd_from_double(st.M[(size_t)l * rm + i] / st.S[l]));
+    const int i = idx / r, l = idx - i * r;
+    const dd a = dd_from_double(st.M[(size_t)l * rm + i] * sinv[l]);
+    S.Ah[i * kPowLd + l] = a.h;
+    S.Al[i * kPowLd + l] = a.l;
+  }
+  for (int idx = tid; idx < r0 * r; idx += kPowThreads) {
+    const int i = idx / r, l = idx - i * r;
+    const dd q = dd_from_double(st.Q[(size_t)l * qld + i]);
+    S.Qh[i * kPowLd + l] = q.h;
+    S.Ql[i * kPowLd + l] = q.l;
   }
   // start from a vector of the previous call when it belongs to this model: the latest of
   // its first and last horizons that is not after the first one asked for (a check of the
   // first or of the next state after a predict needs no powering)
   const unsigned long long ver = ctl->model_ver;
   int slot = -1;
-  if (k > 0 && ctl->pc_ver == ver + 1ull) {
-    const double t0 = ts.t[ord.i[0]];
+  const double t0 = ts.t[ord.i[0]];
+  if (ctl->pc_ver == ver + 1ull)
     for (int q = 0; q < 2; ++q)
       if (ctl->pc_t[q] <= t0 && (slot < 0 || ctl->pc_t[q] > ctl->pc_t[slot])) slot = q;
-  }
   long long tcur = slot >= 0 ? (long long)ctl->pc_t[slot] : 0;
-  for (int l = tid; l < r; l += kPowThreads)
-    S.v[0][l] = slot >= 0 ? ws.sm.pc[slot * kMaxN + l] : f2_of(dd_from_double(st.S[l] * st.rf[l]));
+  for (int l = tid; l < r; l += kPowThreads) {
+    const dd y = slot >= 0 ? dd_of(ws.sm.pc[slot * kMaxN + l]) : dd_from_double(st.S[l] * st.rf[l]);
+    S.wh[0][2 * l] = y.h;
+    S.wl[0][2 * l] = y.l;
+  }
   __syncthreads();
-  int cur = 0;  // S.v[cur] holds the vector
-  for (int q = 0; q < k; ++q) {
-    const int j = ord.i[q];
-    long long d = (long long)ts.t[j] - tcur;
-    tcur += d;
+  int cur = 0;  // S.wh[cur] holds the vector
+  // vector <- A~^d vector: d single products, or binary powering (A~^(2^i) in P and T in turn)
+  auto advance = [&](long long d) {
     if (d <= kPowDirect) {
       for (; d > 0; --d) {
-        pow_matvec(S.A, S.v[cur], S.v[cur ^ 1], r);
+        mm_dd(S.Ah, S.Al, kPowLd, S.wh[cur], S.wl[cur], 2, 0, r, r, 1, PlaneStore{S.wh[cur ^ 1], S.wl[cur ^ 1], 2, 0});
         cur ^= 1;
         __syncthreads();
       }
-    } else {
-      for (int idx = tid; idx < r * r; idx += kPowThreads) S.P[(idx / r) * kPowLd + idx % r] = S.A[(idx / r) * kPowLd + idx % r];
+      return;
+    }
+    const float *bh = S.Ah, *bl = S.Al;
+    float *nh = S.Ph, *nl = S.Pl;
+    while (d > 0) {
+      // the product with the vector and the next squaring read the same power and write
+      // different buffers: one barrier for both
+      if (d & 1) {
+        mm_dd(bh, bl, kPowLd, S.wh[cur], S.wl[cur], 2, 0, r, r, 1, PlaneStore{S.wh[cur ^ 1], S.wl[cur ^ 1], 2, 0});
+        cur ^= 1;
+      }
+      d >>= 1;
+      if (d) mm_dd(bh, bl, kPowLd, bh, bl, kPowLd, 0, r, r, r, PlaneStore{nh, nl, kPowLd, 0});
       __syncthreads();
-      while (d > 0) {
-        if (d & 1) {
-          pow_matvec(S.P, S.v[cur], S.v[cur ^ 1], r);
-          cur ^= 1;
-          __syncthreads();
-        }
-        d >>= 1;
-        if (d) {  // P <- P P
-          for (int base = 0; base < 4 * r * r; base += kPowThreads) {
-            const int e = (base + tid) >> 2, sub = tid & 3;
-            const int i = e / r, jj = e % r;
-            dd acc = dzero();
-            if (e < r * r)
-              for (int l = sub; l < r; l += 4) acc = dd_fma(LD(S.P, (size_t)i * kPowLd + l), LD(S.P, (size_t)l * kPowLd + jj), acc);
-            acc = group4_sum(acc);
-            if (e < r * r && sub == 0) S.T[i * kPowLd + jj] = f2_of(acc);
-          }
-          __syncthreads();
-          for (int idx = tid; idx < r * r; idx += kPowThreads) S.P[(idx / r) * kPowLd + idx % r] = S.T[(idx / r) * kPowLd + idx % r];
-          __syncthreads();
-        }
+      if (d) {
+        bh = nh;
+        bl = nl;
+        nh = (nh == S.Ph) ? S.Th : S.Ph;
+        nl = (nl == S.Pl) ? S.Tl : S.Pl;
       }
     }
-    for (int l = tid; l < r; l += kPowThreads) S.C[j * kMaxR + l] = S.v[cur][l];
-    if (q == 0) {
-      const long long tf = tcur;
-      __syncthreads();  // slot 0 may be the vector this call started from
-      for (int l = tid; l < r; l += kPowThreads) ws.sm.pc[l] = S.v[cur][l];
-      if (tid == 0) ctl->pc_t[0] = (double)tf;
+  };
+  // column c of V <- the current vector
+  auto keep = [&](int c) {
+    for (int l = tid; l < r; l += kPowThreads) {
+      S.Vh[l * kPowLd + c] = S.wh[cur][2 * l];
+      S.Vl[l * kPowLd + c] = S.wl[cur][2 * l];
     }
-    // (read only after the barrier that ends the next step, or the final one)
+  };
+  advance((long long)t0 - tcur);
+  tcur = (long long)t0;
+  // the first horizon's vector is kept for later calls
+  for (int l = tid; l < r; l += kPowThreads) ws.sm.pc[l] = make_float2(S.wh[cur][2 * l], S.wl[cur][2 * l]);
+  if (tid == 0) ctl->pc_t[0] = t0;
+  const double tlast = ts.t[ord.i[k - 1]];
+  const long long span = (long long)tlast - (long long)t0 + 1;
+  int last_col;
+  if (span <= kPowSpan) {
+    // doubling: offsets h .. 2h - 1 are A~^h times offsets 0 .. h - 1
+    keep(0);
+    __syncthreads();
+    if (span > 1) {
+      mm_dd(S.Ah, S.Al, kPowLd, S.Vh, S.Vl, kPowLd, 0, r, r, 1, PlaneStore{S.Vh, S.Vl, kPowLd, 1});
+      __syncthreads();
+    }
+    const float *bh = S.Ah, *bl = S.Al;
+    float *nh = S.Ph, *nl = S.Pl;
+    for (int h = 2; h < span; h *= 2) {
+      mm_dd(bh, bl, kPowLd, bh, bl, kPowLd, 0, r, r, r, PlaneStore{nh, nl, kPowLd, 0});  // A~^h
+      __syncthreads();
+      bh = nh;
+      bl = nl;
+      nh = (nh == S.Ph) ? S.Th : S.Ph;
+      nl = (nl == S.Pl) ? S.Tl : S.Pl;
+      const int ncols = (int)(span - h < h ? span - h : h);
+      mm_dd(bh, bl, kPowLd, S.Vh, S.Vl, kPowLd, 0, r, r, ncols, PlaneStore{S.Vh, S.Vl, kPowLd, h});
+      __syncthreads();
+    }
+    for (int j = tid; j < k; j += kPowThreads) S.col_of[j] = (int)((long long)ts.t[j] - (long long)t0);
+    last_col = (int)(span - 1);
+  } else {
+    // spread horizons: one after another
+    for (int q = 0; q < k; ++q) {
+      const int j = ord.i[q];
+      advance((long long)ts.t[j] - tcur);
+      tcur = (long long)ts.t[j];
+      keep(q);
+      if (tid == 0) S.col_of[j] = q;
+    }
+    last_col = k - 1;
   }
   __syncthreads();
-  // coef[:, j] = Q C[j] for every horizon at once (4 threads per output)
-  for (int base = 0; base < 4 * r0 * k; base += kPowThreads) {
-    const int e = (base + tid) >> 2, sub = tid & 3;
-    const int i = e % r0, j = e / r0;
-    dd acc = dzero();
-    if (e < r0 * k)
-      for (int l = sub; l < r; l += 4)
-        acc = dd_fma(dd_from_double(st.Q[(size_t)l * qld + i]), LD(S.C, (size_t)j * kMaxR + l), acc);
-    acc = group4_sum(acc);
-    if (e < r0 * k && sub == 0) ws.sm.coef[(size_t)j * qld + i] = f2_of(acc);
+  // coef[:, j] = Q C[:, j], C[:, j] = V[:, col_of[j]] gathered into T first
+  for (int idx = tid; idx < r * k; idx += kPowThreads) {
+    const int l = idx / k, j = idx - l * k;
+    S.Th[l * kPowLd + j] = S.Vh[l * kPowLd + S.col_of[j]];
+    S.Tl[l * kPowLd + j] = S.Vl[l * kPowLd + S.col_of[j]];
   }
-  if (k > 0) {
-    for (int l = tid; l < r; l += kPowThreads) ws.sm.pc[kMaxN + l] = S.v[cur][l];
-    if (tid == 0) {
-      ctl->pc_t[1] = (double)tcur;
-      ctl->pc_ver = ver + 1ull;
-    }
-  }
+  for (int l = tid; l < r; l += kPowThreads)
+    ws.sm.pc[kMaxN + l] = make_float2(S.Vh[l * kPowLd + last_col], S.Vl[l * kPowLd + last_col]);
+  __syncthreads();
+  float2* coef = ws.sm.coef;
+  int* badp = &bad;
+  mm_dd(S.Qh, S.Ql, kPowLd, S.Th, S.Tl, kPowLd, 0, r0, r, k, [=](int i, int j, Acc a) {
+    coef[(size_t)j * qld + i] = make_float2(a.h, a.l);
+    if (!isfinite(a.h) || !isfinite(a.l)) *badp = 1;
+  });
+  __syncthreads();
   if (tid == 0) {
-    bool bad = false;
-    for (int l = 0; l < r; ++l) bad |= !dd_isfinite(LD(S.v[cur], l));
+    ctl->pc_t[1] = tlast;
+    ctl->pc_ver = ver + 1ull;
     if (bad) atomicOr(&ctl->status, DEV_NONFINITE);
   }
 }

@@ -1509,14 +1509,31 @@ cudaError_t launch_first(const Ws& ws, cudaStream_t s) {
 
 // Copy a caller's double snapshot into the workspace as float pairs (all SMs; the only
 // FP64 instructions a snapshot meets).
+// one pair of elements per thread (16-byte loads and stores where the caller's array allows),
+// one thread per pair over the whole array: the loads of a launch are all in flight at once
 __global__ void __launch_bounds__(kThreads) k_ingest_dd(const double* __restrict__ src, float2* __restrict__ dst,
                                                         int64_t n) {
   pdl_wait();
-  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
-    float h, l;
-    split_double(src[i], h, l);
-    dst[i] = make_float2(h, l);
+  const int64_t i = 2 * ((int64_t)blockIdx.x * kThreads + threadIdx.x);
+  if (i >= n) return;
+  const bool vec = i + 1 < n && (reinterpret_cast<uintptr_t>(src) & 15u) == 0;
+  double v0, v1 = 0.0;
+  if (vec) {
+    const double2 v = *reinterpret_cast<const double2*>(src + i);
+    v0 = v.x;
+    v1 = v.y;
+  } else {
+    v0 = src[i];
+    if (i + 1 < n) v1 = src[i + 1];
   }
+  float h0, l0, h1, l1;
+  split_double(v0, h0, l0);
+  split_double(v1, h1, l1);
+  // dst is a workspace slot (256-byte aligned) and i is even
+  if (i + 1 < n)
+    *reinterpret_cast<float4*>(dst + i) = make_float4(h0, l0, h1, l1);
+  else
+    dst[i] = make_float2(h0, l0);
 }
 
 __global__ void __launch_bounds__(kThreads) k_ingest_f32(const float* __restrict__ src, float* __restrict__ dst,
@@ -1533,8 +1550,8 @@ static int ingest_grid(const Ws& ws) {
 
 cudaError_t launch_ingest(const Ws& ws, const void* src, void* dst, cudaStream_t s) {
   if (ws.prec == ST_DD)
-    k_ingest_dd<<<ingest_grid(ws), kThreads, 0, s>>>(reinterpret_cast<const double*>(src),
-                                                     reinterpret_cast<float2*>(dst), ws.n);
+    k_ingest_dd<<<(int)((ws.n + 2 * kThreads - 1) / (2 * kThreads)), kThreads, 0, s>>>(
+        reinterpret_cast<const double*>(src), reinterpret_cast<float2*>(dst), ws.n);
   else
     k_ingest_f32<<<ingest_grid(ws), kThreads, 0, s>>>(reinterpret_cast<const float*>(src),
                                                       reinterpret_cast<float*>(dst), ws.n);

@@ -9,6 +9,22 @@
 #include "pair2d.cuh"
 
 static long fails = 0, checked = 0, fast_checked = 0, fast_fails = 0, fast_ties = 0;
+static long split_checked = 0, split_fast = 0, split_fails = 0;
+
+// double_to_pair_fast against the conversions: h = (float)x, l = (float)(x - h), bit for bit,
+// whenever it takes the fast path
+static void check_split(double x) {
+  float h, l;
+  ++split_checked;
+  if (!odmd::double_to_pair_fast(x, h, l)) return;
+  ++split_fast;
+  const float wh = (float)x;
+  const float wl = (float)(x - (double)wh);
+  if (std::memcmp(&h, &wh, 4) != 0 || std::memcmp(&l, &wl, 4) != 0) {
+    if (split_fails < 10) std::printf("split: x=%a got (%a, %a) want (%a, %a)\n", x, h, l, wh, wl);
+    ++split_fails;
+  }
+}
 
 // a tie: h + l lies exactly halfway between want and its neighbour `other`
 static bool is_tie(float h, float l, double want, double other) {
@@ -80,8 +96,26 @@ int main() {
   }
   check(0.f, 0.f, 5);
   check(-0.f, 0.f, 5);
+  // doubles to pairs: random significands over the float range, ties of the high word (the
+  // low 29 bits exactly half), carries into the next binade, and values whose low word would
+  // be subnormal (slow path)
+  std::uniform_int_distribution<int> exd(-140, 140);
+  std::uniform_int_distribution<uint64_t> bits52(0, (1ull << 52) - 1);
+  for (int i = 0; i < 2000000; ++i) {
+    check_split(std::ldexp(u(rng), exd(rng)));
+    const uint64_t mb = (bits52(rng) & ~((1ull << 29) - 1)) | (1ull << 28);  // a tie for h
+    const double t = std::ldexp(1.0 + std::ldexp((double)mb, -52), exd(rng));
+    check_split(i & 1 ? t : -t);
+  }
+  for (int e = -120; e <= 120; e += 7) {
+    check_split(std::ldexp(2.0 - 0x1p-52, e));  // rounds up to the next power of two
+    check_split(-std::ldexp(1.0 + 0x1p-52, e));
+    check_split(std::ldexp(1.0, e));
+  }
+  check_split(0.0);
   std::printf("%ld checked, %ld mismatches\n", checked, fails);
   std::printf("fast: %ld checked, %ld ties rounded the other way, %ld failures\n", fast_checked, fast_ties,
               fast_fails);
-  return fails == 0 && fast_fails == 0 ? 0 : 1;
+  std::printf("split: %ld checked, %ld on the fast path, %ld failures\n", split_checked, split_fast, split_fails);
+  return fails == 0 && fast_fails == 0 && split_fails == 0 && split_fast > split_checked / 2 ? 0 : 1;
 }
