@@ -188,6 +188,7 @@ def test_wake_full_size_bench_configuration(monkeypatch):
     s_dev = strong_eigs(lam, amp, 1e-3)
     assert len(s_dev) == len(s_ref) >= 7
     err = match_eigs(s_dev, s_ref)
+    print(f"full-size wake: strong-eigenvalue error {err:.3e}, spread of the two FP64 oracles {spread:.3e}")
     assert err <= max(1e-10, 2 * spread), (err, spread)
     ts = [120.0, 121.0, 135.0, 150.0]
     assert_horizons(m.predict(ts).cpu().numpy(), ref.predict(ts).T, 1e-9)
