@@ -147,14 +147,28 @@ odmd_status odmd_update_host(odmd_t h, const void* host, int64_t count, int64_t 
 
 /* Many instances in one call (independent simulations, Sec. 2.1 per instance):
  * odmd_update_batch is odmd_update(hs[i], xs[i]) for i < count, and odmd_predict_batch is
- * odmd_predict(hs[i], ts[i], ks[i], outs[i], lds[i]); each instance's work is enqueued on
- * its own handle's stream, so instances created on different streams run concurrently on
- * the GPU (the update of one instance is a single CUDA-graph launch).  Handles must be
- * distinct within a call.  On the first failing instance the call stops and returns that
- * status; odmd_last_error(NULL) names the instance.  Earlier instances stay updated. */
+ * odmd_predict(hs[i], ts[i], ks[i], outs[i], lds[i]).  Handles must be distinct within a
+ * call; xs[i] is a device array of the handle's n elements in its snapshot format.
+ * The update runs instances of the same storage format and compaction kind together: one
+ * launch per step of the update (ingest, pass A, the five small-solve kernels, the
+ * compaction) over all of them, each CTA doing what it does in its instance's own launch,
+ * so every instance's result is bitwise that of odmd_update.  Such a group is split into S
+ * sub-batches balanced by rows, each a CUDA graph on its own stream, so that the small solves
+ * of one overlap the tall passes of another; S is picked by a tuner that times S = 1, 2, 4, 8
+ * (as the group's size allows) on the first calls for the same set of handles (those calls
+ * wait for their own step), then keeps the fastest.  The launches are ordered after each
+ * handle's earlier work and before its later work on its stream.  Instances that cannot join
+ * (their first snapshot, profiling on, row shards, another device) are updated one by one.
+ * The group's plan (graphs and streams, no device memory) is kept until one of its handles
+ * is destroyed or changes its row shards.  On a failure the call returns that status;
+ * odmd_last_error(NULL) says which step or instance failed. */
 odmd_status odmd_update_batch(odmd_t* hs, const void* const* xs, int32_t count);
 odmd_status odmd_predict_batch(odmd_t* hs, const double* const* ts, const int32_t* ks, void* const* outs,
                                const int64_t* lds, int32_t count);
+
+/* The sub-batch split S the tuner chose for the group of these handles, in this order: S >= 1
+ * once chosen, 0 while it is still timing, -1 if no call has run this set as one group. */
+odmd_status odmd_get_batch_split(odmd_t* hs, int32_t count, int32_t* split);
 
 /* Orthogonality refinement (no counterpart in the paper: it keeps L^T L = I over long
  * streams, where rounding in every rank-1 update lets it drift, most of all with FP32

@@ -7,7 +7,7 @@ from ._build import build
 from ._lib import EXPORTED, OdmdError, load_library
 
 __all__ = ["build", "load_library", "OdmdError", "EXPORTED", "OnlineDMD", "OnlineDMDPairs", "check_noalloc",
-           "update_batch", "predict_batch"]
+           "update_batch", "predict_batch", "batch_split"]
 
 
 def __getattr__(name):
@@ -17,7 +17,7 @@ def __getattr__(name):
     if name == "OnlineDMDPairs":
         from .odmd import OnlineDMDPairs
         return OnlineDMDPairs
-    if name in ("check_noalloc", "update_batch", "predict_batch"):
+    if name in ("check_noalloc", "update_batch", "predict_batch", "batch_split"):
         from . import odmd
         return getattr(odmd, name)
     raise AttributeError(name)

@@ -21,6 +21,7 @@ EXPORTED = [
     "odmd_pairs_footprint", "odmd_pairs_create", "odmd_pairs_update", "odmd_pairs_predict",
     "odmd_pairs_get_singular_values", "odmd_pairs_get_count", "odmd_pairs_last_error", "odmd_pairs_destroy",
     "odmd_pairs_hybrid_step_residual", "odmd_tc_selftest", "odmd_set_row_shards", "odmd_get_row_blocks",
+    "odmd_get_batch_split",
 ]
 # host callbacks of odmd_hybrid_step_residual: (user, step, u, r, b, stream) and (user, step, u, stream)
 RESIDUAL_FN = C.CFUNCTYPE(C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p)
@@ -76,6 +77,7 @@ def load_library(path: str | None = None) -> C.CDLL:
         "odmd_check_noalloc": [vp, vp, i64, dbl, vp, C.POINTER(dbl), C.POINTER(i32)],
         "odmd_hybrid_step": [vp, vp, dbl, vp, C.POINTER(i32), C.POINTER(dbl)],
         "odmd_update_batch": [C.POINTER(vp), C.POINTER(vp), i32],
+        "odmd_get_batch_split": [C.POINTER(vp), i32, C.POINTER(i32)],
         "odmd_refine": [vp],
         "odmd_checkpoint_size": [vp, C.POINTER(C.c_size_t)],
         "odmd_save": [vp, vp, C.c_size_t],

@@ -1,9 +1,12 @@
 // C ABI of libodmd: argument checks, workspace layout, call sequencing.  Every O(N)
 // or O(r^3) step runs in the kernels of tall.cu and small.cu; this file only decides
 // which kernels to enqueue and carries a few bytes between host and device.
+#include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -63,6 +66,11 @@ struct odmd_instance {
   // own; a slot is refilled only after the update that read it
   unsigned char* stage[2] = {nullptr, nullptr};
   cudaStream_t copy = nullptr;
+  // multi-instance updates (odmd_update_batch): this handle's Ws in its own workspace, a
+  // process-unique serial that names it in cached batch plans, an event for their ordering
+  Ws* wsv = nullptr;
+  unsigned long long serial = 0;
+  cudaEvent_t ev_batch = nullptr;
   cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
   bool stage_used[2] = {false, false};
   int stage_next = 0;
@@ -78,6 +86,7 @@ struct Layout {
   size_t total;
   size_t off_gpart = 0, off_rscr = 0;  // refinement scratch (refine_every > 0 only)
   size_t off_stage[2] = {0, 0};  // staging of snapshots read from host memory
+  size_t off_wsv = 0;            // the handle's workspace view (Ws), read by multi-instance launches
   size_t off_ctl, off_hdr[2], off_state[2], off_small, off_eig, off_out2, off_part, off_Lh, off_Ll, off_c[2],
       off_x, off_e, off_maps;
   size_t state_doubles, small_bytes, eig_doubles;
@@ -178,6 +187,7 @@ Layout make_layout(const odmd_config& c) {
   L.off_e = take((size_t)L.npad * sizeof(float2));
   L.off_stage[0] = take(snap);
   L.off_stage[1] = take(snap);
+  L.off_wsv = take(sizeof(Ws));
   L.total = o;
   return L;
 }
@@ -606,6 +616,11 @@ odmd_status odmd_create(const odmd_config* cfg, void* workspace_dev, size_t byte
   carve(h->ws, L, reinterpret_cast<unsigned char*>(workspace_dev), *cfg, gridA);
   h->stage[0] = reinterpret_cast<unsigned char*>(workspace_dev) + L.off_stage[0];
   h->stage[1] = reinterpret_cast<unsigned char*>(workspace_dev) + L.off_stage[1];
+  h->wsv = reinterpret_cast<Ws*>(reinterpret_cast<unsigned char*>(workspace_dev) + L.off_wsv);
+  {
+    static std::atomic<unsigned long long> serials{0};
+    h->serial = ++serials;
+  }
   {
     h->ws.shards = 1;
     h->ws.gridG = 2 * sms < kGramCtas ? 2 * sms : kGramCtas;
@@ -630,6 +645,7 @@ odmd_status odmd_create(const odmd_config* cfg, void* workspace_dev, size_t byte
     e = cudaMemcpyAsync(base_of(h, L), h->maps_host.data(), h->maps_host.size() * sizeof(CUtensorMap),
                         cudaMemcpyHostToDevice, h->stream);
   }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->wsv, &h->ws, sizeof(Ws), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     cudaFreeHost(h->pinned);
@@ -1156,16 +1172,320 @@ odmd_status odmd_update_host(odmd_t h, const void* host, int64_t count, int64_t 
   return ODMD_OK;
 }
 
+// ---------------------------------------------------------------- multi-instance updates
+// odmd_update_batch runs the update of many instances as one launch per step: ingest (kernel
+// parameters carry the snapshot pointers), then a CUDA graph of pass A, the five small-solve
+// kernels and the compaction, each a single launch over every instance of the batch (each
+// CTA finds its instance and its place in that instance's own grid; instance i's work is
+// exactly that of its own update, so the results are bitwise those of odmd_update).  The
+// graph is captured once per set of handles and kept in a plan; plans are dropped when one
+// of their handles is destroyed or changes its row shards.
+namespace {
+// one multi-instance launch sequence over a subset of a batch, on its own stream
+struct SubPlan {
+  std::vector<odmd_t> hs;
+  int prec = 0;
+  cudaStream_t s = nullptr;
+  cudaEvent_t done = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+// A batch (a set of handles) as S sub-batches balanced by rows, each a graph on its own
+// stream, so that one sub-batch's latency-bound small solves overlap another's tall passes.
+// The split S is picked by timing: the first calls of a plan try each candidate on the
+// caller's own updates (the results do not depend on S), then the fastest is kept.
+struct BatchPlan {
+  std::vector<unsigned long long> serials;  // the instances, in call order
+  std::vector<odmd_t> hs;
+  std::vector<int> cand;                    // candidate splits S
+  std::vector<std::vector<SubPlan*>> subs;  // per candidate, built on first use
+  std::vector<float> best_ms;               // per candidate, best step time seen
+  int tried = 0;                            // tuning calls made so far
+  int chosen = -1;                          // index into cand once tuning is done
+  cudaStream_t lead = nullptr;              // orders the sub-batches and times a step
+  cudaEvent_t t0 = nullptr, t1 = nullptr, joined = nullptr;
+};
+constexpr int kTuneRounds = 2;  // timed calls per candidate
+std::mutex g_plans_mu;
+std::vector<BatchPlan*> g_plans;
+
+void free_sub(SubPlan* p) {
+  if (p->s) cudaStreamSynchronize(p->s);
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  if (p->done) cudaEventDestroy(p->done);
+  if (p->s) cudaStreamDestroy(p->s);
+  delete p;
+}
+void free_plan(BatchPlan* p) {
+  for (auto& v : p->subs)
+    for (SubPlan* q : v) free_sub(q);
+  if (p->lead) cudaStreamSynchronize(p->lead);
+  for (cudaEvent_t e : {p->t0, p->t1, p->joined})
+    if (e) cudaEventDestroy(e);
+  if (p->lead) cudaStreamDestroy(p->lead);
+  delete p;
+}
+
+// the compaction of an instance on the tensor cores (else the CUDA-core pass B)
+bool split_compaction(odmd_t h) { return h->use_tc && split_compact_ok(h->ws); }
+
+// an update of h can join a multi-instance launch
+bool batchable(odmd_t h, int device) {
+  return h->use_graphs && h->ws.shards == 1 && h->nsnap >= 1 && !h->prof_on && h->device == device;
+}
+
+BatchTab tab_of(const std::vector<odmd_t>& hs, const std::vector<int>& per) {
+  BatchTab t{};
+  int f = 0;
+  for (size_t i = 0; i < hs.size(); ++i) {
+    t.ws[i] = hs[i]->wsv;
+    t.first[i] = f;
+    f += per[i];
+  }
+  t.first[hs.size()] = f;
+  t.ninst = (int)hs.size();
+  return t;
+}
+
+odmd_status build_sub(const std::vector<odmd_t>& hs, SubPlan** out) {
+  odmd_t h0 = hs[0];
+  SubPlan* p = new SubPlan;
+  p->hs = hs;
+  p->prec = h0->ws.prec;
+  const bool split = split_compaction(h0);
+  const size_t n = hs.size();
+  // the small solves' CTAs per instance are bounded by its own r_max (roots and columns of
+  // a core of order r + 1 <= r_max + 1; k_zhat's ordering CTA is its last)
+  std::vector<int> pa(n), pc(n), one(n, 1), root(n), zhat(n);
+  int sa = 0, sb = 0, sp = 0;
+  for (size_t i = 0; i < n; ++i) {
+    const Ws& w = hs[i]->ws;
+    pa[i] = w.gridA;
+    pc[i] = split ? split_grid_of(w, hs[i]->sms) : w.gridA;
+    root[i] = w.rmax + 1;
+    zhat[i] = w.rmax + 2;
+    sa = std::max(sa, pass_a_smem(w.prec, w.cap));
+    sb = std::max(sb, pass_b_smem(w.prec, w.cap));
+    sp = std::max(sp, prep_smem_of(w.cap));
+  }
+  cudaError_t e = prepare_tall_batch();
+  if (e == cudaSuccess) e = prepare_core_batch();
+  if (e == cudaSuccess) e = prepare_split_batch();
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->s, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(p->s, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    e = launch_pass_a_batch(tab_of(hs, pa), p->prec, sa, p->s);
+    if (e == cudaSuccess) e = launch_small_batch(tab_of(hs, one), tab_of(hs, root), tab_of(hs, zhat), sp, p->s);
+    if (e == cudaSuccess)
+      e = split ? launch_split_compact_batch(tab_of(hs, pc), p->s) : launch_pass_b_batch(tab_of(hs, pc), p->prec, sb, p->s);
+    const cudaError_t e2 = cudaStreamEndCapture(p->s, &p->graph);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+  if (e != cudaSuccess) {
+    free_sub(p);
+    return fail(nullptr, ODMD_ERR_CUDA, std::string("update_batch: plan: ") + cudaGetErrorString(e));
+  }
+  *out = p;
+  return ODMD_OK;
+}
+
+// S sub-batches balanced by rows: instances in decreasing n, each to the lightest sub-batch
+odmd_status build_split(const std::vector<odmd_t>& hs, int S, std::vector<SubPlan*>& out) {
+  std::vector<int> order(hs.size());
+  for (size_t i = 0; i < hs.size(); ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return hs[a]->cfg.n > hs[b]->cfg.n; });
+  std::vector<std::vector<odmd_t>> parts(S);
+  std::vector<int64_t> load(S, 0);
+  for (int i : order) {
+    const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    parts[k].push_back(hs[i]);
+    load[k] += hs[i]->cfg.n;
+  }
+  for (auto& part : parts) {
+    if (part.empty()) continue;
+    SubPlan* q = nullptr;
+    if (odmd_status st = build_sub(part, &q)) return st;
+    out.push_back(q);
+  }
+  return ODMD_OK;
+}
+
+BatchPlan* find_plan(const std::vector<odmd_t>& hs) {
+  for (BatchPlan* p : g_plans) {
+    if (p->serials.size() != hs.size()) continue;
+    bool same = true;
+    for (size_t i = 0; i < hs.size() && same; ++i) same = p->serials[i] == hs[i]->serial && p->hs[i] == hs[i];
+    if (same) return p;
+  }
+  return nullptr;
+}
+
+odmd_status new_plan(const std::vector<odmd_t>& hs, BatchPlan** out) {
+  BatchPlan* p = new BatchPlan;
+  p->hs = hs;
+  for (odmd_t h : hs) p->serials.push_back(h->serial);
+  for (int S : {1, 2, 4, 8})
+    if (S == 1 || (size_t)S * 2 <= hs.size()) p->cand.push_back(S);
+  p->subs.resize(p->cand.size());
+  p->best_ms.assign(p->cand.size(), 1e30f);
+  cudaError_t e = cudaStreamCreateWithFlags(&p->lead, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&p->t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&p->t1);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->joined, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    free_plan(p);
+    return fail(nullptr, ODMD_ERR_CUDA, std::string("update_batch: plan: ") + cudaGetErrorString(e));
+  }
+  *out = p;
+  return ODMD_OK;
+}
+
+// one multi-instance update of hs (all batchable, one precision and compaction kind)
+odmd_status run_batch(const std::vector<odmd_t>& hs, const std::vector<const void*>& xs) {
+  BatchPlan* p = nullptr;
+  std::lock_guard<std::mutex> lk(g_plans_mu);
+  p = find_plan(hs);
+  if (!p) {
+    if (odmd_status st = new_plan(hs, &p)) return st;
+    g_plans.push_back(p);
+  }
+  const bool tuning = p->chosen < 0;
+  const int ci = tuning ? p->tried % (int)p->cand.size() : p->chosen;
+  if (p->subs[ci].empty())
+    if (odmd_status st = build_split(hs, p->cand[ci], p->subs[ci])) return st;
+  odmd_t h0 = hs[0];
+  // the lead stream waits for each instance's earlier work; the sub-batches wait for it
+  for (odmd_t h : hs) {
+    if (!h->ev_batch) CK(h, cudaEventCreateWithFlags(&h->ev_batch, cudaEventDisableTiming), "batch event");
+    CK(h, cudaEventRecord(h->ev_batch, h->stream), "batch order");
+    CK(h, cudaStreamWaitEvent(p->lead, h->ev_batch, 0), "batch order");
+  }
+  CK(h0, cudaEventRecord(p->t0, p->lead), "batch order");
+  for (SubPlan* q : p->subs[ci]) {
+    CK(h0, cudaStreamWaitEvent(q->s, p->t0, 0), "batch order");
+    IngestTab it{};
+    int64_t f = 0;
+    for (size_t i = 0; i < q->hs.size(); ++i) {
+      odmd_t h = q->hs[i];
+      const size_t k = (size_t)(std::find(hs.begin(), hs.end(), h) - hs.begin());
+      it.src[i] = xs[k];
+      it.dst[i] = h->ws.cbuf[h->curc_h ^ 1];
+      it.n[i] = h->cfg.n;
+      it.first[i] = f;
+      f += (h->cfg.n + 1) / 2;
+    }
+    it.first[q->hs.size()] = f;
+    it.ninst = (int)q->hs.size();
+    CK(h0, launch_ingest_batch(it, q->prec, q->s), "batch ingest");
+    CK(h0, cudaGraphLaunch(q->exec, q->s), "batch graph launch");
+    CK(h0, cudaEventRecord(q->done, q->s), "batch order");
+    CK(h0, cudaStreamWaitEvent(p->lead, q->done, 0), "batch order");
+  }
+  CK(h0, cudaEventRecord(p->t1, p->lead), "batch order");
+  for (odmd_t h : hs) {
+    CK(h, cudaStreamWaitEvent(h->stream, p->t1, 0), "batch order");
+    h->launches[ODMD_K_PASS_A] += 1;
+    h->launches[ODMD_K_SMALL] += 5;
+    h->launches[ODMD_K_PASS_B] += 1;
+    h->cur_h ^= 1;
+    h->curc_h ^= 1;
+    h->nsnap += 1;
+    h->eig_dirty = true;
+  }
+  if (tuning) {
+    // the tuning calls wait for their own step to time it (the first calls of a plan only)
+    CK(h0, cudaEventSynchronize(p->t1), "batch tuning");
+    float ms = 0.f;
+    CK(h0, cudaEventElapsedTime(&ms, p->t0, p->t1), "batch tuning");
+    p->best_ms[ci] = std::min(p->best_ms[ci], ms);
+    if (++p->tried >= kTuneRounds * (int)p->cand.size()) {
+      p->chosen = (int)(std::min_element(p->best_ms.begin(), p->best_ms.end()) - p->best_ms.begin());
+      for (size_t c = 0; c < p->subs.size(); ++c)  // the other splits' graphs are not needed
+        if ((int)c != p->chosen) {
+          for (SubPlan* q : p->subs[c]) free_sub(q);
+          p->subs[c].clear();
+        }
+    }
+  }
+  for (odmd_t h : hs)
+    if (h->cfg.refine_every > 0 && (h->nsnap - 1) % h->cfg.refine_every == 0)
+      if (odmd_status st = odmd_refine(h)) return st;
+  return ODMD_OK;
+}
+}  // namespace
+
+odmd_status odmd_get_batch_split(odmd_t* hs, int32_t count, int32_t* split) {
+  if (count < 0 || !split || (count > 0 && !hs)) return fail(nullptr, ODMD_ERR_ARG, "get_batch_split: bad arguments");
+  std::lock_guard<std::mutex> lk(g_plans_mu);
+  std::vector<odmd_t> v(hs, hs + count);
+  BatchPlan* p = find_plan(v);
+  *split = p ? (p->chosen >= 0 ? p->cand[p->chosen] : 0) : -1;
+  return ODMD_OK;
+}
+
+static void drop_batch_plans(odmd_t h) {
+  std::lock_guard<std::mutex> lk(g_plans_mu);
+  for (size_t i = 0; i < g_plans.size();) {
+    BatchPlan* p = g_plans[i];
+    if (std::find(p->serials.begin(), p->serials.end(), h->serial) != p->serials.end()) {
+      free_plan(p);
+      g_plans.erase(g_plans.begin() + (long)i);
+    } else {
+      ++i;
+    }
+  }
+}
+
 odmd_status odmd_update_batch(odmd_t* hs, const void* const* xs, int32_t count) {
   if (count < 0 || (count > 0 && (!hs || !xs))) return fail(nullptr, ODMD_ERR_ARG, "update_batch: bad arguments");
   for (int32_t i = 0; i < count; ++i) {
     if (!hs[i]) return fail(nullptr, ODMD_ERR_ARG, "update_batch: handle " + std::to_string(i) + " is NULL");
+    if (!xs[i]) return fail(nullptr, ODMD_ERR_ARG, "update_batch: snapshot " + std::to_string(i) + " is NULL");
     for (int32_t j = 0; j < i; ++j)
       if (hs[j] == hs[i])
         return fail(nullptr, ODMD_ERR_ARG, "update_batch: handle " + std::to_string(i) + " repeats handle " +
                                                std::to_string(j));
   }
-  for (int32_t i = 0; i < count; ++i)
+  if (count == 0) return ODMD_OK;
+  // instances that can share launches, grouped by storage format and compaction kind, in
+  // groups of at most kMaxBatch; the others (first snapshot, profiling on, row shards, no
+  // graphs, another device) update one by one
+  const int dev = hs[0]->device;
+  std::vector<std::vector<int>> groups;
+  std::vector<int> solo;
+  for (int32_t i = 0; i < count; ++i) {
+    if (!batchable(hs[i], dev)) {
+      solo.push_back(i);
+      continue;
+    }
+    bool placed = false;
+    for (auto& g : groups) {
+      odmd_t a = hs[g[0]];
+      if ((int)g.size() < kMaxBatch && a->ws.prec == hs[i]->ws.prec && split_compaction(a) == split_compaction(hs[i])) {
+        g.push_back(i);
+        placed = true;
+        break;
+      }
+    }
+    if (!placed) groups.push_back({i});
+  }
+  for (auto& g : groups) {
+    if (g.size() == 1) {
+      solo.push_back(g[0]);
+      continue;
+    }
+    std::vector<odmd_t> gh;
+    std::vector<const void*> gx;
+    for (int i : g) {
+      gh.push_back(hs[i]);
+      gx.push_back(xs[i]);
+    }
+    if (odmd_status st = run_batch(gh, gx)) return fail(nullptr, st, "update_batch: " + g_err);
+  }
+  for (int i : solo)
     if (odmd_status s = odmd_update(hs[i], xs[i]))
       return fail(nullptr, s, "update_batch: instance " + std::to_string(i) + ": " + hs[i]->err);
   return ODMD_OK;
@@ -1327,7 +1647,9 @@ odmd_status odmd_set_row_shards(odmd_t h, int32_t shards) {
   if (shards == h->ws.shards) return ODMD_OK;
   CK(h, cudaStreamSynchronize(h->stream), "shards: sync");
   drop_update_graphs(h);
+  drop_batch_plans(h);
   h->ws.shards = shards;
+  CK(h, cudaMemcpy(h->wsv, &h->ws, sizeof(Ws), cudaMemcpyHostToDevice), "shards: workspace view");
   return ODMD_OK;
 }
 
@@ -1351,6 +1673,8 @@ odmd_status odmd_destroy(odmd_t h) {
   prof_collect(h);
   for (cudaEvent_t ev : h->pool) cudaEventDestroy(ev);
   drop_update_graphs(h);
+  drop_batch_plans(h);
+  if (h->ev_batch) cudaEventDestroy(h->ev_batch);
   if (h->cap) cudaStreamDestroy(h->cap);
   for (int b = 0; b < 2; ++b) {
     if (h->ev_copied[b]) cudaEventDestroy(h->ev_copied[b]);

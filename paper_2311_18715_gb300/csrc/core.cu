@@ -55,7 +55,7 @@ __device__ __forceinline__ void stage_doubles(double* dst, const double* src, in
 // ---------------------------------------------------------------------------------------
 constexpr int kPrepThreads = 256;
 
-__global__ void __launch_bounds__(kPrepThreads) k_prep(Ws ws) {
+__device__ __forceinline__ void prep_body(const Ws& ws, CtaPos cp) {
   pdl_wait();
   extern __shared__ __align__(16) double psm[];
   Ctl* ctl = ws.ctl;
@@ -302,6 +302,15 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(Ws ws) {
   }
 }
 
+__global__ void __launch_bounds__(kPrepThreads) k_prep(const __grid_constant__ Ws ws) {
+  prep_body(ws, cta_single());
+}
+__global__ void __launch_bounds__(kPrepThreads) k_prep_batch(const __grid_constant__ BatchTab t) {
+  const int i = batch_find(t, blockIdx.x);
+  prep_body(*t.ws[i], batch_pos(t, i));
+}
+
+
 // ---------------------------------------------------------------------------------------
 // k_roots: root j of 1 + sum_i z_i^2/(d_i^2 - lambda) = 0 in (d_j^2, d_{j+1}^2)
 // ---------------------------------------------------------------------------------------
@@ -337,11 +346,11 @@ __device__ __forceinline__ void block_sum_f(float (&v)[NF], float* part) {  // p
   }
 }
 
-__global__ void __launch_bounds__(kRootThreads) k_roots(Ws ws) {
+__device__ __forceinline__ void roots_body(const Ws& ws, CtaPos cp) {
   pdl_wait();
   Ctl* ctl = ws.ctl;
   const int m = ctl->m;
-  const int j = blockIdx.x;
+  const int j = cp.b;
   if (j >= m) return;
   const double* d = ws.sm.d;
   const double* z = ws.sm.z;
@@ -586,18 +595,27 @@ __global__ void __launch_bounds__(kRootThreads) k_roots(Ws ws) {
   }
 }
 
+__global__ void __launch_bounds__(kRootThreads) k_roots(const __grid_constant__ Ws ws) {
+  roots_body(ws, cta_single());
+}
+__global__ void __launch_bounds__(kRootThreads) k_roots_batch(const __grid_constant__ BatchTab t) {
+  const int i = batch_find(t, blockIdx.x);
+  roots_body(*t.ws[i], batch_pos(t, i));
+}
+
+
 // ---------------------------------------------------------------------------------------
 // k_zhat: Loewner weights z^_i^2 = prod_k (lambda_k - d_i^2) / prod_{k != i} (d_k^2 - d_i^2),
-// paired so every factor is O(1).  Block kMaxN orders all singular values of K.
+// paired so every factor is O(1).  The last CTA of the grid orders all singular values of K.
 // ---------------------------------------------------------------------------------------
 constexpr int kZhatThreads = 64;
 
-__global__ void __launch_bounds__(kZhatThreads) k_zhat(Ws ws) {
+__device__ __forceinline__ void zhat_body(const Ws& ws, CtaPos cp) {
   pdl_wait();
   Ctl* ctl = ws.ctl;
   const int m = ctl->m;
   const int tid = threadIdx.x;
-  if (blockIdx.x == kMaxN) {
+  if (cp.b == cp.g - 1) {  // the last CTA (kMaxN in an instance's own launch)
     // order roots (sig[0..m)) and deflated values (scaled diagonal at defl[k]), descending;
     // every value is >= 0, so its bit pattern orders it
     const int nd = ctl->ndefl;
@@ -638,7 +656,7 @@ __global__ void __launch_bounds__(kZhatThreads) k_zhat(Ws ws) {
     }
     return;
   }
-  const int i = blockIdx.x;
+  const int i = cp.b;
   if (i >= m) return;
   const double* d = ws.sm.d;
   const double di = d[i];
@@ -669,15 +687,24 @@ __global__ void __launch_bounds__(kZhatThreads) k_zhat(Ws ws) {
   }
 }
 
+__global__ void __launch_bounds__(kZhatThreads) k_zhat(const __grid_constant__ Ws ws) {
+  zhat_body(ws, cta_single());
+}
+__global__ void __launch_bounds__(kZhatThreads) k_zhat_batch(const __grid_constant__ BatchTab t) {
+  const int i = batch_find(t, blockIdx.x);
+  zhat_body(*t.ws[i], batch_pos(t, i));
+}
+
+
 // ---------------------------------------------------------------------------------------
 // k_vectors: kept column j -> u_j, v_j (core coordinates 0..r; r is the p/rho column)
 // ---------------------------------------------------------------------------------------
 constexpr int kVecThreads = 64;
 
-__global__ void __launch_bounds__(kVecThreads) k_vectors(Ws ws) {
+__device__ __forceinline__ void vectors_body(const Ws& ws, CtaPos cp) {
   pdl_wait();
   Ctl* ctl = ws.ctl;
-  const int j = blockIdx.x;
+  const int j = cp.b;
   if (j >= ctl->rnew) return;
   const int n = ctl->n, m = ctl->m, r = n - 1;
   const int tid = threadIdx.x;
@@ -747,6 +774,15 @@ __global__ void __launch_bounds__(kVecThreads) k_vectors(Ws ws) {
   }
 }
 
+__global__ void __launch_bounds__(kVecThreads) k_vectors(const __grid_constant__ Ws ws) {
+  vectors_body(ws, cta_single());
+}
+__global__ void __launch_bounds__(kVecThreads) k_vectors_batch(const __grid_constant__ BatchTab t) {
+  const int i = batch_find(t, blockIdx.x);
+  vectors_body(*t.ws[i], batch_pos(t, i));
+}
+
+
 // ---------------------------------------------------------------------------------------
 // k_apply: column j of the new small state (written to the other state buffer)
 //   M'    = U'^T [[M, w], [rho r_last^T, gamma]] V'
@@ -761,10 +797,10 @@ __device__ __forceinline__ int count4(int sub, int n) { return n > sub ? (n - su
 __device__ void apply_column(const Ws& ws, int j, const StateBuf& st, const StateBuf& nx, int r, int r0, int r0e,
                              bool compact);
 
-__global__ void __launch_bounds__(kApplyThreads) k_apply(Ws ws) {
+__device__ __forceinline__ void apply_body(const Ws& ws, CtaPos cp) {
   pdl_wait();
   Ctl* ctl = ws.ctl;
-  const int j = blockIdx.x;
+  const int j = cp.b;
   const int rnew = ctl->rnew;
   const int tid = threadIdx.x;
   const int cur = ctl->cur;
@@ -798,7 +834,7 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(Ws ws) {
   __syncthreads();
   if (tid == 0) ticket = atomicAdd(&ctl->ticket_b, 1u);
   __syncthreads();
-  if (ticket != gridDim.x - 1) return;
+  if (ticket != cp.g - 1) return;
   if (tid == 0) {
     __threadfence();
     ctl->cur = cur ^ 1;
@@ -808,6 +844,15 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(Ws ws) {
     ctl->ticket_b = 0u;
   }
 }
+
+__global__ void __launch_bounds__(kApplyThreads) k_apply(const __grid_constant__ Ws ws) {
+  apply_body(ws, cta_single());
+}
+__global__ void __launch_bounds__(kApplyThreads) k_apply_batch(const __grid_constant__ BatchTab t) {
+  const int i = batch_find(t, blockIdx.x);
+  apply_body(*t.ws[i], batch_pos(t, i));
+}
+
 
 __device__ void apply_column(const Ws& ws, int j, const StateBuf& st, const StateBuf& nx, int r, int r0, int r0e,
                              bool compact) {
@@ -909,6 +954,28 @@ constexpr int kApplySmem = (int)sizeof(double) * (kMaxR * kMaxR + kMaxR * (kMaxC
 cudaError_t prepare_core() {
   cudaError_t e = cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, prep_smem_cap(kMaxCap));
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, kApplySmem);
+  return e;
+}
+
+int prep_smem_of(int cap) { return prep_smem_cap(cap); }
+
+cudaError_t prepare_core_batch() {
+  cudaError_t e = cudaFuncSetAttribute(k_prep_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, prep_smem_cap(kMaxCap));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, kApplySmem);
+  return e;
+}
+
+// the five small-solve kernels of a batch's update, each one launch over every instance: one
+// CTA per instance for k_prep, kMaxN per instance for k_roots, k_vectors and k_apply, kMaxN + 1
+// for k_zhat (the CTAs past an instance's own sizes return at once, as in its own launches)
+cudaError_t launch_small_batch(const BatchTab& one, const BatchTab& per_root, const BatchTab& per_zhat, int prep_smem,
+                               cudaStream_t s) {
+  cudaError_t e = launch_dependent(k_prep_batch, one.first[one.ninst], kPrepThreads, prep_smem, s, one);
+  if (e == cudaSuccess) e = launch_dependent(k_roots_batch, per_root.first[per_root.ninst], kRootThreads, 0, s, per_root);
+  if (e == cudaSuccess) e = launch_dependent(k_zhat_batch, per_zhat.first[per_zhat.ninst], kZhatThreads, 0, s, per_zhat);
+  if (e == cudaSuccess) e = launch_dependent(k_vectors_batch, per_root.first[per_root.ninst], kVecThreads, 0, s, per_root);
+  if (e == cudaSuccess)
+    e = launch_dependent(k_apply_batch, per_root.first[per_root.ninst], kApplyThreads, (size_t)kApplySmem, s, per_root);
   return e;
 }
 

@@ -174,6 +174,49 @@ struct Ws {
   float2* out2;     // 4 double-floats for host read-back
 };
 
+// ------------------------------------------------------------------ multi-instance launches
+// Where a CTA sits within its instance: its index b and the instance's grid size g.  A
+// kernel of one instance takes blockIdx.x and gridDim.x; a kernel over many instances (one
+// launch for the same step of every instance of a batch) maps its grid onto the instances
+// of a table, instance i owning CTAs [first[i], first[i + 1]).
+struct CtaPos {
+  int b, g;
+};
+__device__ __forceinline__ CtaPos cta_single() { return CtaPos{(int)blockIdx.x, (int)gridDim.x}; }
+
+constexpr int kMaxBatch = 64;  // instances per multi-instance launch
+// passed by value (under 1 KB of kernel parameters): each instance's workspace view lives
+// in its own workspace (written at create), so a batch needs no memory of its own
+struct BatchTab {
+  const Ws* ws[kMaxBatch];     // the instances' workspace views (device memory)
+  int first[kMaxBatch + 1];    // first CTA of each instance in the launch's grid
+  int ninst;
+};
+// the instance that owns CTA blk (binary search over the prefix sums)
+__device__ __forceinline__ int batch_find(const BatchTab& t, int blk) {
+  int lo = 0, hi = t.ninst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (t.first[mid] <= blk)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+__device__ __forceinline__ CtaPos batch_pos(const BatchTab& t, int i) {
+  return CtaPos{(int)blockIdx.x - t.first[i], t.first[i + 1] - t.first[i]};
+}
+// the snapshots of a batch's update: instance i's n[i] elements from src[i] into dst[i];
+// first[] are prefix sums of the element pairs
+struct IngestTab {
+  const void* src[kMaxBatch];
+  void* dst[kMaxBatch];
+  int64_t n[kMaxBatch];
+  int64_t first[kMaxBatch + 1];
+  int ninst;
+};
+
 // ------------------------------------------------------------------ dependent launches
 // The kernels of an update run back to back in one CUDA graph.  Each is launched with
 // programmatic stream serialisation, so the grid is set up while its predecessor finishes;
@@ -459,7 +502,21 @@ cudaError_t launch_ingest(const Ws& ws, const void* src, void* dst, cudaStream_t
 const void* ingest_kernel(int prec);  // the kernel launch_ingest uses (graph node lookup)
 cudaError_t prepare_tall(const Ws& ws);
 cudaError_t prepare_small(const Ws& ws);
-cudaError_t prepare_core();  // shared-memory limits of the FP64 small solves of the update
+cudaError_t prepare_core();
+// multi-instance launches (one per step of the update over every instance of a batch)
+cudaError_t launch_ingest_batch(const IngestTab& t, int prec, cudaStream_t s);
+cudaError_t launch_pass_a_batch(const BatchTab& t, int prec, int smem, cudaStream_t s);
+cudaError_t launch_pass_b_batch(const BatchTab& t, int prec, int smem, cudaStream_t s);
+cudaError_t launch_small_batch(const BatchTab& one, const BatchTab& per_root, const BatchTab& per_zhat,
+                               int prep_smem, cudaStream_t s);
+cudaError_t launch_split_compact_batch(const BatchTab& t, cudaStream_t s);
+int split_grid_of(const Ws& ws, int sms);
+int pass_a_smem(int prec, int cap);
+int pass_b_smem(int prec, int cap);
+int prep_smem_of(int cap);
+cudaError_t prepare_tall_batch();
+cudaError_t prepare_core_batch();
+cudaError_t prepare_split_batch();  // shared-memory limits of the FP64 small solves of the update
 bool split_rollout_ok(const Ws& ws, int kcols);       // the tensor-core rollout takes this call
 cudaError_t prepare_split(const Ws& ws);
 cudaError_t launch_split_rollout(const Ws& ws, int kcols, double* out, int64_t ld, int sms, cudaStream_t s);

@@ -129,7 +129,7 @@ __device__ __forceinline__ void issue_tile(const Ws& ws, unsigned char* stage, i
 // COMPACT = true: when the update in flight compacts, L0[:, :rnew] <- [L0[:, :r0] j0] Q_B in
 // place (the tile's rows are staged before they are overwritten, by the CTA that read them).
 template <bool COMPACT>
-__global__ void __launch_bounds__(kThreadsS, 1) k_split(Ws ws, int kcols, double* out, int64_t ld) {
+__device__ __forceinline__ void split_body(const Ws& ws, CtaPos cp, int kcols, double* out, int64_t ld) {
   if constexpr (COMPACT) {
     pdl_wait();
     if (ws.ctl->mode != PB_COMPACT) return;  // most updates: nothing to do
@@ -219,9 +219,9 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(Ws ws, int kcols, double
   const uint32_t tmem = tmem_slot;
 
   const int64_t ntiles = (ws.n + kTM - 1) / kTM;
-  const int G = gridDim.x;
-  const int my_tiles = (int)((ntiles - blockIdx.x + G - 1) / G);
-  if (tid == 0 && my_tiles > 0) issue_tile(ws, stage, rs, blockIdx.x, with_e, &bar_tma);
+  const int G = cp.g;
+  const int my_tiles = (int)((ntiles - cp.b + G - 1) / G);
+  if (tid == 0 && my_tiles > 0) issue_tile(ws, stage, rs, cp.b, with_e, &bar_tma);
   const uint32_t idesc = tc::instr_desc_bf16_f32(kTM, kNJ);
   // descriptors of digit slice 1 at chunk 0; every other operand differs only in its start
   // address, so its descriptor is this one plus (byte offset >> 4) in the start field (shared
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(Ws ws, int kcols, double
   bool ok = true;
 
   for (int li = 0; li < my_tiles && ok; ++li) {
-    const int64_t tile = blockIdx.x + (int64_t)li * G;
+    const int64_t tile = cp.b + (int64_t)li * G;
     const int64_t row0 = tile * kTM;
     ok = mbar_wait(&bar_tma, par_tma, &ctl->status);
     if (__syncthreads_or(!ok)) {
@@ -460,6 +460,17 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_split(Ws ws, int kcols, double
   if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
 }
 
+template <bool COMPACT>
+__global__ void __launch_bounds__(kThreadsS, 1) k_split(const __grid_constant__ Ws ws, int kcols, double* out, int64_t ld) {
+  split_body<COMPACT>(ws, cta_single(), kcols, out, ld);
+}
+template <bool COMPACT>
+__global__ void __launch_bounds__(kThreadsS, 1) k_split_batch(const __grid_constant__ BatchTab t) {
+  const int i = batch_find(t, blockIdx.x);
+  split_body<COMPACT>(*t.ws[i], batch_pos(t, i), 0, (double*)nullptr, (int64_t)0);
+}
+
+
 }  // namespace split
 
 // The tensor-core paths take double-float storage and at most 64 columns in the tall operand
@@ -488,6 +499,20 @@ cudaError_t prepare_split(const Ws& ws) {
 static int split_grid(const Ws& ws, int sms) {
   const int64_t ntiles = (ws.n + split::kTM - 1) / split::kTM;
   return (int)(ntiles < sms ? ntiles : sms);
+}
+
+int split_grid_of(const Ws& ws, int sms) { return split_grid(ws, sms); }
+
+cudaError_t prepare_split_batch() {
+  const int sm = split::smem_bytes(16 * box_chunks(split::kMaxK, 4));
+  return cudaFuncSetAttribute(split::k_split_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+}
+
+// the compaction form over the instances of a batch (each instance's CTAs return at once
+// unless its update compacts); the largest shared memory any instance can ask for
+cudaError_t launch_split_compact_batch(const BatchTab& t, cudaStream_t s) {
+  const int sm = split::smem_bytes(16 * box_chunks(split::kMaxK, 4));
+  return launch_dependent(split::k_split_batch<true>, t.first[t.ninst], split::kThreadsS, (size_t)sm, s, t);
 }
 
 cudaError_t launch_split_rollout(const Ws& ws, int kcols, double* out, int64_t ld, int sms, cudaStream_t s) {

@@ -543,7 +543,7 @@ __device__ void fold_pass_a(const Ws& ws, const StateBuf& st, int r0) {
 }
 
 template <int ST>
-__global__ void __launch_bounds__(kThreadsA, 1) k_pass_a(Ws ws, int cta0, int fold) {
+__device__ __forceinline__ void pass_a_body(const Ws& ws, CtaPos cp, int cta0, int fold) {
   pdl_wait();
   using T = Traits<ST>;
   using stored_t = typename T::stored_t;
@@ -613,7 +613,7 @@ __global__ void __launch_bounds__(kThreadsA, 1) k_pass_a(Ws ws, int cta0, int fo
   const float pih = st.hdr->pinv.x, pil = st.hdr->pinv.y;
   // this CTA's row block, in tiles of kRowsA = 32 rows
   static_assert(kTile == 2 * kRowsA, "a row block is whole 64-row tiles");
-  const int blk = cta0 + blockIdx.x;
+  const int blk = cta0 + cp.b;
   int64_t b0, b1;
   block_tiles64(ws, blk, b0, b1);
   const int64_t ntiles = (ws.n + kRowsA - 1) / kRowsA;
@@ -845,10 +845,21 @@ __global__ void __launch_bounds__(kThreadsA, 1) k_pass_a(Ws ws, int cta0, int fo
   __syncthreads();
   if (tid == 0) ticket = atomicAdd(&ctl->ticket_a, 1u);
   __syncthreads();
-  if (ticket != gridDim.x - 1) return;
+  if (ticket != cp.g - 1) return;
   __threadfence();
   fold_pass_a(ws, st, r0);
 }
+
+template <int ST>
+__global__ void __launch_bounds__(kThreadsA, 1) k_pass_a(const __grid_constant__ Ws ws, int cta0, int fold) {
+  pass_a_body<ST>(ws, cta_single(), cta0, fold);
+}
+template <int ST>
+__global__ void __launch_bounds__(kThreadsA, 1) k_pass_a_batch(const __grid_constant__ BatchTab t) {
+  const int i = batch_find(t, blockIdx.x);
+  pass_a_body<ST>(*t.ws[i], batch_pos(t, i), 0, 1);
+}
+
 
 // the fold of pass A after a sharded run (one CTA): the exchange of per-block partials of a
 // row-sharded run, added in block order exactly as the unsharded pass adds them
@@ -867,7 +878,7 @@ constexpr int kRowLanes = 8;
 constexpr int kThreadsB = 512;
 
 template <int ST, bool FLUSH>
-__global__ void __launch_bounds__(kThreadsB) k_pass_b(Ws ws) {
+__device__ __forceinline__ void pass_b_body(const Ws& ws, CtaPos cp) {
   pdl_wait();
   using T = Traits<ST>;
   constexpr int epcC = (ST == ST_BF16) ? 8 : 4;  // basis columns per 16-byte chunk
@@ -899,7 +910,7 @@ __global__ void __launch_bounds__(kThreadsB) k_pass_b(Ws ws) {
     }
     sco = ws.sm.red;
   }
-  const int G = gridDim.x;
+  const int G = cp.g;
   if (work) {
     TilePipe<ST> P;
     P.setup(ws, r0, kStagesB);
@@ -950,16 +961,16 @@ __global__ void __launch_bounds__(kThreadsB) k_pass_b(Ws ws) {
     __syncthreads();
 
     const int64_t ntiles = (ws.n + kTile - 1) / kTile;
-    const int my_tiles = (int)((ntiles - blockIdx.x + G - 1) / G);
+    const int my_tiles = (int)((ntiles - cp.b + G - 1) / G);
     if (tid == 0) {
-      for (int li = 0; li < min(my_tiles, kStagesB); ++li) P.issue(blockIdx.x + li * G, li);
+      for (int li = 0; li < min(my_tiles, kStagesB); ++li) P.issue(cp.b + li * G, li);
     }
     const int t = tid >> 3, sub = tid & (kRowLanes - 1);
 
     for (int li = 0; li < my_tiles; ++li) {
       const int s = li % kStagesB;
       const uint32_t par = (uint32_t)((li / kStagesB) & 1);
-      const int tile = blockIdx.x + li * G;
+      const int tile = cp.b + li * G;
       const int64_t row0 = (int64_t)tile * kTile;
       const int rows = rows_in(ws.n, row0);
       const bool ok = mbar_wait(&P.bars[s], par, &ctl->status);
@@ -1054,7 +1065,7 @@ __global__ void __launch_bounds__(kThreadsB) k_pass_b(Ws ws) {
       // the stage is refilled by TMA (async proxy) after generic reads and writes
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
-      if (tid == 0 && li + kStagesB < my_tiles) P.issue(blockIdx.x + (li + kStagesB) * G, s);
+      if (tid == 0 && li + kStagesB < my_tiles) P.issue(cp.b + (li + kStagesB) * G, s);
     }
   }
   if constexpr (FLUSH) {
@@ -1070,6 +1081,17 @@ __global__ void __launch_bounds__(kThreadsB) k_pass_b(Ws ws) {
     }
   }
 }
+
+template <int ST, bool FLUSH>
+__global__ void __launch_bounds__(kThreadsB) k_pass_b(const __grid_constant__ Ws ws) {
+  pass_b_body<ST, FLUSH>(ws, cta_single());
+}
+template <int ST, bool FLUSH>
+__global__ void __launch_bounds__(kThreadsB) k_pass_b_batch(const __grid_constant__ BatchTab t) {
+  const int i = batch_find(t, blockIdx.x);
+  pass_b_body<ST, FLUSH>(*t.ws[i], batch_pos(t, i));
+}
+
 
 // ---------------------------------------------------------------------------------------
 // rollout: X[:, j] = L0 coef[:, j] (j < kcols), written in the snapshot type
@@ -1541,6 +1563,93 @@ __global__ void __launch_bounds__(kThreads) k_ingest_f32(const float* __restrict
   pdl_wait();
   for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
     dst[i] = src[i];
+}
+
+// the ingest of a batch: instance i's snapshot (n[i] elements) into its slot, one element
+// pair per thread as in k_ingest_dd, pairs of all instances in one grid
+template <bool DD>
+__global__ void __launch_bounds__(kThreads) k_ingest_batch(const __grid_constant__ IngestTab t) {
+  const int64_t q = (int64_t)blockIdx.x * kThreads + threadIdx.x;  // global pair index
+  if (q >= t.first[t.ninst]) return;
+  int lo = 0, hi = t.ninst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (t.first[mid] <= q)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const int64_t n = t.n[lo], i = 2 * (q - t.first[lo]);
+  if constexpr (DD) {
+    const double* src = static_cast<const double*>(t.src[lo]);
+    float2* dst = static_cast<float2*>(t.dst[lo]);
+    const double v0 = src[i], v1 = i + 1 < n ? src[i + 1] : 0.0;
+    float h0, l0, h1, l1;
+    split_double(v0, h0, l0);
+    split_double(v1, h1, l1);
+    dst[i] = make_float2(h0, l0);
+    if (i + 1 < n) dst[i + 1] = make_float2(h1, l1);
+  } else {
+    const float* src = static_cast<const float*>(t.src[lo]);
+    float* dst = static_cast<float*>(t.dst[lo]);
+    dst[i] = src[i];
+    if (i + 1 < n) dst[i + 1] = src[i + 1];
+  }
+}
+
+cudaError_t launch_ingest_batch(const IngestTab& t, int prec, cudaStream_t s) {
+  const int64_t blocks = (t.first[t.ninst] + kThreads - 1) / kThreads;
+  if (blocks == 0) return cudaSuccess;
+  if (prec == ST_DD)
+    k_ingest_batch<true><<<(unsigned)blocks, kThreads, 0, s>>>(t);
+  else
+    k_ingest_batch<false><<<(unsigned)blocks, kThreads, 0, s>>>(t);
+  return cudaGetLastError();
+}
+
+int pass_a_smem(int prec, int cap) { return smem_a(prec, cap); }
+int pass_b_smem(int prec, int cap) { return smem_b(prec, cap); }
+
+// one launch of pass A (or of the compaction's pass B) over the instances of a batch: the
+// grid is every instance's row blocks, each CTA doing what it does in the instance's own
+// launch (the last CTA of each instance folds its partials)
+cudaError_t launch_pass_a_batch(const BatchTab& t, int prec, int smem, cudaStream_t s) {
+  const int grid = t.first[t.ninst];
+  switch (prec) {
+    case ST_DD:
+      return launch_dependent(k_pass_a_batch<ST_DD>, grid, kThreadsA, smem, s, t);
+    case ST_F32:
+      return launch_dependent(k_pass_a_batch<ST_F32>, grid, kThreadsA, smem, s, t);
+    default:
+      return launch_dependent(k_pass_a_batch<ST_BF16>, grid, kThreadsA, smem, s, t);
+  }
+}
+cudaError_t launch_pass_b_batch(const BatchTab& t, int prec, int smem, cudaStream_t s) {
+  const int grid = t.first[t.ninst];
+  switch (prec) {
+    case ST_DD:
+      return launch_dependent(k_pass_b_batch<ST_DD, false>, grid, kThreadsB, smem, s, t);
+    case ST_F32:
+      return launch_dependent(k_pass_b_batch<ST_F32, false>, grid, kThreadsB, smem, s, t);
+    default:
+      return launch_dependent(k_pass_b_batch<ST_BF16, false>, grid, kThreadsB, smem, s, t);
+  }
+}
+
+// the batch kernels take the largest shared memory any instance asks for
+cudaError_t prepare_tall_batch() {
+  const int big = kSmemBudget;
+  cudaError_t e = cudaSuccess;
+  auto set = [&](const void* k) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  };
+  set((const void*)k_pass_a_batch<ST_DD>);
+  set((const void*)k_pass_a_batch<ST_F32>);
+  set((const void*)k_pass_a_batch<ST_BF16>);
+  set((const void*)k_pass_b_batch<ST_DD, false>);
+  set((const void*)k_pass_b_batch<ST_F32, false>);
+  set((const void*)k_pass_b_batch<ST_BF16, false>);
+  return e;
 }
 
 static int ingest_grid(const Ws& ws) {

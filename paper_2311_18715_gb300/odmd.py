@@ -323,6 +323,17 @@ def update_batch(models: Sequence[OnlineDMD], xs: Sequence[torch.Tensor]) -> Non
     check(lib, lib.odmd_update_batch(hs, ps, k))
 
 
+def batch_split(models: Sequence[OnlineDMD]) -> int:
+    """odmd_get_batch_split: the sub-batch split the tuner chose for this set of models (0
+    while it is still timing, -1 if the set has not run as one group)."""
+    lib = load_library()
+    k = len(models)
+    hs = (C.c_void_p * max(k, 1))(*[m._h for m in models])
+    out = C.c_int32()
+    check(lib, lib.odmd_get_batch_split(hs, k, C.byref(out)))
+    return int(out.value)
+
+
 def predict_batch(models: Sequence[OnlineDMD], ts: Sequence[Sequence[float]]) -> list[torch.Tensor]:
     """odmd_predict_batch: predictions of every model at its own step counts."""
     if len(models) != len(ts):

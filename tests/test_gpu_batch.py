@@ -53,3 +53,63 @@ def test_batch_rejects_repeated_handles():
     x = torch.ones(100, dtype=torch.float64, device="cuda")
     with pytest.raises(pkg.OdmdError):
         pkg.update_batch([m, m], [x, x])
+
+
+def test_batch_groups_by_storage_format():
+    """One call over FP32-storage and FP64-accuracy instances: the library runs each group of
+    like instances as one multi-instance launch per step (FP32 groups compact on the CUDA
+    cores, FP64 ones on the tensor cores), and every instance still equals the same instance
+    updated on its own, bitwise, through several compactions."""
+    import paper_2311_18715_gb300 as pkg
+
+    shapes = [(5000, 6, "fp32"), (20011, 10, "fp64"), (65537, 8, "fp32"), (3001, 12, "fp64"), (9000, 4, "fp32")]
+    steps = 24
+    gens = [RandomPlanted(n, seed=40 + i) for i, (n, _, _) in enumerate(shapes)]
+    data64 = [torch.from_numpy(g.snapshots(0, steps)).cuda() for g in gens]
+    data = [d.float() if p == "fp32" else d for d, (_, _, p) in zip(data64, shapes)]
+    torch.cuda.synchronize()
+    batch = [pkg.OnlineDMD(n, r, prec=p, slack=2, stream=torch.cuda.Stream()) for n, r, p in shapes]
+    single = [pkg.OnlineDMD(n, r, prec=p, slack=2) for n, r, p in shapes]
+    for k in range(steps):
+        pkg.update_batch(batch, [d[k] for d in data])
+        for m, d in zip(single, data):
+            m.update(d[k])
+    torch.cuda.synchronize()
+    # the tuner has timed every split on the first calls of each group and kept one
+    fp32 = [m for m, (_, _, p) in zip(batch, shapes) if p == "fp32"]
+    fp64 = [m for m, (_, _, p) in zip(batch, shapes) if p == "fp64"]
+    assert pkg.batch_split(fp32) in (1,)
+    assert pkg.batch_split(fp64) in (1,)
+    assert pkg.batch_split(batch) == -1  # never one group
+    for m, s in zip(batch, single):
+        assert m.rank == s.rank
+        assert m.counts()[1] == s.counts()[1] >= 3  # (snapshots, compactions)
+        assert np.array_equal(np.array(m.singular_values()), np.array(s.singular_values()))
+        t = [float(steps), float(steps + 7)]
+        assert torch.equal(m.predict(t), s.predict(t))
+
+
+def test_batch_tuner_splits_are_bitwise_equal():
+    """A group of eight instances: the tuner times S = 1, 2 and 4 sub-batches (two calls each)
+    and keeps one; every split gives the instances exactly the results of their own updates."""
+    import paper_2311_18715_gb300 as pkg
+
+    shapes = [(4000 + 1013 * i, 4 + (i % 3), "fp64") for i in range(8)]
+    steps = 14
+    data = [torch.from_numpy(RandomPlanted(n, seed=70 + i).snapshots(0, steps)).cuda()
+            for i, (n, _, _) in enumerate(shapes)]
+    torch.cuda.synchronize()
+    batch = [pkg.OnlineDMD(n, r, slack=3, stream=torch.cuda.Stream()) for n, r, _ in shapes]
+    single = [pkg.OnlineDMD(n, r, slack=3) for n, r, _ in shapes]
+    for k in range(steps):
+        pkg.update_batch(batch, [d[k] for d in data])
+        for m, d in zip(single, data):
+            m.update(d[k])
+        if k == 3:
+            assert pkg.batch_split(batch) == 0  # still timing (six calls from the second on)
+    torch.cuda.synchronize()
+    assert pkg.batch_split(batch) in (1, 2, 4)
+    for m, s in zip(batch, single):
+        assert np.array_equal(np.array(m.singular_values()), np.array(s.singular_values()))
+        t = [float(steps), float(steps + 3)]
+        assert torch.equal(m.predict(t), s.predict(t))
