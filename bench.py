@@ -740,8 +740,32 @@ def run_fp32_large(args) -> None:
         "kernel_ms_per_step": {c: prof[c][0] / K for c in ("pass_a", "small", "pass_b", "eig", "coef", "rollout")},
         "clocks": clocks,
     }
-    print(json.dumps(line), flush=True)
     model.close()
+    del model, out
+    torch.cuda.empty_cache()
+    # untimed: the same stream through the FP32-storage form (refined every 50 updates and
+    # before it predicts) and through the FP64-accuracy device path, at full size; every
+    # predicted state of the FP32 form against the FP64 path's (the oracle at n = 6.3 M would
+    # take hours on the host)
+    m32 = pkg.OnlineDMD(n, r_max, prec="fp32", slack=SLACK, trunc_tol=TAU, refine_every=50)
+    m64 = pkg.OnlineDMD(n, r_max, prec="fp64", slack=SLACK, trunc_tol=TAU)
+    n_cmp = 200
+    for k in range(n_cmp):
+        ds.draw(k, x)
+        m32.update(x)
+        m64.update(x.double())
+    m32.refine()
+    hz = [float(n_cmp + h) for h in range(BLOCK)]
+    p32 = m32.predict(hz).double()
+    p64 = m64.predict(hz)
+    err = ((p32 - p64).norm(dim=1) / p64.norm(dim=1)).max().item()
+    line["fp32_vs_fp64"] = {"updates": n_cmp, "horizons": BLOCK, "rank_fp32": m32.rank, "rank_fp64": m64.rank,
+                            "max_rel_err_per_state": err,
+                            "note": "FP32 storage refined before predicting, against the FP64-accuracy device path "
+                                    "on the same stream"}
+    m32.close()
+    m64.close()
+    print(json.dumps(line), flush=True)
 
 
 def run_pairs(args) -> None:
