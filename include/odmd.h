@@ -351,10 +351,12 @@ odmd_status odmd_destroy(odmd_t h);
  * rel_err, pass: host outputs (either may be NULL).  Sums are FP64.  Errors: ODMD_ERR_ARG,
  * ODMD_ERR_CUDA, ODMD_ERR_NUMERIC (non-finite input); the message is odmd_last_error(NULL).
  *
- * The first call on each device looks up the scratch array's device address with that
- * device current; make that first call before any stream capture on the device.  Every
- * call in the process shares the one array on a device: calls whose GPU work overlaps
- * (different streams or threads at the same time) race and may return wrong results. */
+ * Every call synchronises its stream and copies the result to the host, so no call can be
+ * captured into a CUDA graph.  The first call on each device loads the library's kernels
+ * there (under lazy module loading) and looks up the scratch array's device address: make
+ * one warm-up call at start-up, outside any section that must not allocate.  Every call in
+ * the process shares the one array on a device: calls whose GPU work overlaps (different
+ * streams or threads at the same time) race and may return wrong results. */
 odmd_status odmd_check_noalloc(const double* pred_dev, const double* x_fom_dev, int64_t n, double tol,
                                void* stream, double* rel_err, int32_t* pass);
 
