@@ -50,10 +50,11 @@ constexpr int kKC = 16;         // K of one MMA
 constexpr int kSlices = 7;      // digits per value
 constexpr int kGroups = 7;      // g = s + t = 2 .. 8
 constexpr int kMaxK = 64;       // basis columns this path takes (4 K chunks)
-constexpr int kBufK = 32;       // K columns of L0 digits held at once (two chunks)
+constexpr int kBufK = 16;       // K columns of L0 digits in one buffer (one chunk); two buffers
 constexpr int kThreadsS = 512;   // 16 warps: 4 threads per row in the digit phase, 4 warps per TMEM lane quarter
 constexpr uint32_t kTmemCols = 512;
-constexpr int kASlice = kTM * kBufK * 2;   // bytes of one digit slice of the L0 buffer
+constexpr int kASlice = kTM * kBufK * 2;   // bytes of one digit slice of an L0 buffer
+constexpr int kABuf = kSlices * kASlice;   // bytes of one L0 digit buffer (one chunk, all slices)
 constexpr int kBSlice = kNJ * kMaxK * 2;   // bytes of one digit slice of C (K padded to 64)
 static_assert(kGroups * kNJ <= (int)kTmemCols, "seven accumulators fit the tensor memory");
 // a group sums at most 7 digit pairs over K <= 64 columns of products |d d'| <= 2^14
@@ -66,7 +67,7 @@ constexpr int kGridBits = 54;  // values on the grid 2^(e - 54): |I| < 2^54, sev
 constexpr long long kDigitBias = 0x80808080808080ll;
 
 __host__ __device__ inline int stage_bytes(int rs) { return ((2 * kTM * rs + kTM * 8 + 1023) / 1024) * 1024; }
-__host__ __device__ inline int smem_bytes(int rs) { return stage_bytes(rs) + kSlices * kASlice + kSlices * kBSlice; }
+__host__ __device__ inline int smem_bytes(int rs) { return stage_bytes(rs) + 2 * kABuf + kSlices * kBSlice; }
 
 // exponent e with |v| < 2^e for every double-float v of a set whose largest |hi| is mx (from
 // the bits of mx; 0 for mx = 0): |hi + lo| < 2^e as well, since |lo| <= ulp(hi) / 2
@@ -158,12 +159,12 @@ __device__ __forceinline__ void split_body(const Ws& ws, CtaPos cp, int kcols, d
   const int nchunk = kpad / kKC;
   unsigned char* stage = sp;
   unsigned char* adig = sp + stage_bytes(rs);
-  unsigned char* bdig = adig + kSlices * kASlice;
+  unsigned char* bdig = adig + 2 * kABuf;
   __shared__ int fexp[kNJ];
   __shared__ int erow[kTM];
   __shared__ float jh[kTM], jl[kTM];           // the new column j0 of the tile (compaction)
   __shared__ float sh_s[kMaxK], sl_s[kMaxK];   // its coefficients s (compaction)
-  __shared__ __align__(8) uint64_t bar_tma, bar_mma;
+  __shared__ __align__(8) uint64_t bar_tma, bar_mma[2];
   __shared__ uint32_t tmem_slot;
   const bool with_e = COMPACT && append;
   dd inv = dd{0.f, 0.f};
@@ -209,7 +210,8 @@ __device__ __forceinline__ void split_body(const Ws& ws, CtaPos cp, int kcols, d
   }
   if (tid == 0) {
     mbar_init(&bar_tma, 1);
-    mbar_init(&bar_mma, 1);
+    mbar_init(&bar_mma[0], 1);
+    mbar_init(&bar_mma[1], 1);
     mbar_fence_init();
   }
   if (warp == 0) tc::tmem_alloc(&tmem_slot, kTmemCols);
@@ -227,12 +229,14 @@ __device__ __forceinline__ void split_body(const Ws& ws, CtaPos cp, int kcols, d
   // address, so its descriptor is this one plus (byte offset >> 4) in the start field (shared
   // memory addresses stay below 2^18, so the field never carries)
   const uint64_t adesc0 = tc::smem_desc(smem_addr(adig), tc::kCoreBytes, (kBufK / 8) * tc::kCoreBytes);
+  static_assert((kABuf >> 4) < (1 << 13), "a buffer offset fits the descriptor's start field");
   const uint64_t bdesc0 = tc::smem_desc(smem_addr(bdig), tc::kCoreBytes, (kMaxK / 8) * tc::kCoreBytes);
-  uint32_t par_tma = 0, par_mma = 0;
-  // work in flight that a timeout must still wait for (the same in every thread)
-  bool tma_out = my_tiles > 0, mma_out = false;
-  // digit phase: four threads per row, thread q of a row owning buffer columns 8q .. 8q + 7
-  // (one 16-byte row of a core matrix per slice)
+  uint32_t par_tma = 0, par_mma[2] = {0u, 0u};
+  // work in flight that a timeout must still wait for (the same in every thread): the next
+  // tile's copy, and a commit not yet waited for on each MMA barrier
+  bool tma_out = my_tiles > 0, mma_out[2] = {false, false};
+  // digit phase: four threads per row, thread q of a row owning columns 4q .. 4q + 3 of the
+  // chunk (half of a 16-byte core-matrix row per slice)
   const int row = tid >> 2, quad = tid & 3;
   const float* sh = reinterpret_cast<const float*>(stage) + (size_t)row * (rs / 4);
   const float* sl = reinterpret_cast<const float*>(stage + (size_t)kTM * rs) + (size_t)row * (rs / 4);
@@ -280,86 +284,99 @@ __device__ __forceinline__ void split_body(const Ws& ws, CtaPos cp, int kcols, d
     }
     __syncwarp();
     const int my_e = erow[row];
-    for (int c0 = 0; c0 < nchunk; c0 += 2) {
-      // digits of basis columns kb .. kb + 7 of this row (chunk c0 + quad / 2) into buffer
-      // columns 8 quad .. 8 quad + 7: one 16-byte store per slice; columns at or past K
-      // (the chunk's zero padding) store zeros without arithmetic
-      const int kb = c0 * kKC + 8 * quad;
-      if (c0 * kKC + 8 * quad < nchunk * kKC) {
-        const int off = tc::kmajor_off(row, 8 * quad, kBufK / 8);
-        if (live && kb < K) {
-          uint32_t w[kSlices][4];
-#pragma unroll
-          for (int kk = 0; kk < 8; kk += 2) {
-            const int k = kb + kk;
-            float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
-            if (k < r0) {
-              h0 = sh[k];
-              l0 = sl[k];
-            } else if (k < K) {  // the new column (compaction)
-              h0 = jh[row];
-              l0 = jl[row];
-            }
-            if (k + 1 < r0) {
-              h1 = sh[k + 1];
-              l1 = sl[k + 1];
-            } else if (k + 1 < K) {
-              h1 = jh[row];
-              l1 = jl[row];
-            }
-            const unsigned long long u0 = biased_fixed(h0, l0, my_e), u1 = biased_fixed(h1, l1, my_e);
-            w[0][kk >> 1] = digit_pair<1>(u0, u1);
-            w[1][kk >> 1] = digit_pair<2>(u0, u1);
-            w[2][kk >> 1] = digit_pair<3>(u0, u1);
-            w[3][kk >> 1] = digit_pair<4>(u0, u1);
-            w[4][kk >> 1] = digit_pair<5>(u0, u1);
-            w[5][kk >> 1] = digit_pair<6>(u0, u1);
-            w[6][kk >> 1] = digit_pair<7>(u0, u1);
-          }
-#pragma unroll
-          for (int s = 0; s < kSlices; ++s)
-            *reinterpret_cast<uint4*>(adig + s * kASlice + off) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
-        } else {
-#pragma unroll
-          for (int s = 0; s < kSlices; ++s) *reinterpret_cast<uint4*>(adig + s * kASlice + off) = make_uint4(0, 0, 0, 0);
+    // chunk cc's digits go to buffer cc % 2 while the products of chunk cc - 1 run from the
+    // other; before a buffer is refilled, the products that read it (chunk cc - 2) are waited
+    // for.  Each commit is waited for exactly once, in order, per barrier.
+    for (int cc = 0; cc < nchunk; ++cc) {
+      const int b = cc & 1;
+      if (cc >= 2) {
+        const bool done = mbar_wait(&bar_mma[b], par_mma[b], &ctl->status);
+        if (__syncthreads_or(!done)) {
+          ok = false;
+          break;
         }
+        par_mma[b] ^= 1u;
+        mma_out[b] = false;
+        tc::fence_after_sync();
+      }
+      unsigned char* abuf = adig + b * kABuf;
+      // digits of basis columns kb .. kb + 3 of this row; columns at or past K (the chunk's
+      // zero padding) store zeros without arithmetic
+      const int kb = cc * kKC + 4 * quad;
+      const int off = tc::kmajor_off(row, 4 * quad, kBufK / 8);
+      if (live && kb < K) {
+        uint32_t w[kSlices][2];
+#pragma unroll
+        for (int kk = 0; kk < 4; kk += 2) {
+          const int k = kb + kk;
+          float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+          if (k < r0) {
+            h0 = sh[k];
+            l0 = sl[k];
+          } else if (k < K) {  // the new column (compaction)
+            h0 = jh[row];
+            l0 = jl[row];
+          }
+          if (k + 1 < r0) {
+            h1 = sh[k + 1];
+            l1 = sl[k + 1];
+          } else if (k + 1 < K) {
+            h1 = jh[row];
+            l1 = jl[row];
+          }
+          const unsigned long long u0 = biased_fixed(h0, l0, my_e), u1 = biased_fixed(h1, l1, my_e);
+          w[0][kk >> 1] = digit_pair<1>(u0, u1);
+          w[1][kk >> 1] = digit_pair<2>(u0, u1);
+          w[2][kk >> 1] = digit_pair<3>(u0, u1);
+          w[3][kk >> 1] = digit_pair<4>(u0, u1);
+          w[4][kk >> 1] = digit_pair<5>(u0, u1);
+          w[5][kk >> 1] = digit_pair<6>(u0, u1);
+          w[6][kk >> 1] = digit_pair<7>(u0, u1);
+        }
+#pragma unroll
+        for (int s = 0; s < kSlices; ++s) *reinterpret_cast<uint2*>(abuf + s * kASlice + off) = make_uint2(w[s][0], w[s][1]);
+      } else {
+#pragma unroll
+        for (int s = 0; s < kSlices; ++s) *reinterpret_cast<uint2*>(abuf + s * kASlice + off) = make_uint2(0, 0);
       }
       tc::fence_proxy_async();
       __syncthreads();
-      const bool last_digits = c0 + 2 >= nchunk;
+      const bool last_digits = cc + 1 == nchunk;
       if (last_digits && li + 1 < my_tiles) tma_out = true;
-      mma_out = true;
+      mma_out[b] = true;
       if (tid == 0) {
         // the staging buffer is free once the tile's last digits are formed: next tile
         if (last_digits && li + 1 < my_tiles) issue_tile(ws, stage, rs, tile + G, with_e, &bar_tma);
         tc::fence_after_sync();
-        for (int cc = c0; cc < c0 + 2 && cc < nchunk; ++cc) {
-          const uint64_t ab = adesc0 + (uint64_t)(((cc - c0) * 2 * tc::kCoreBytes) >> 4);
-          const uint64_t bb = bdesc0 + (uint64_t)((cc * 2 * tc::kCoreBytes) >> 4);
+        const uint64_t ab = adesc0 + (uint64_t)((b * kABuf) >> 4);
+        const uint64_t bb = bdesc0 + (uint64_t)((cc * 2 * tc::kCoreBytes) >> 4);
 #pragma unroll
-          for (int gs = 2; gs <= 8; ++gs)
+        for (int gs = 2; gs <= 8; ++gs)
 #pragma unroll
-            for (int s = 1; s < gs; ++s) {
-              const int t = gs - s;  // s, t <= 7 since g <= 8
-              const uint64_t ad = ab + (uint64_t)(((s - 1) * kASlice) >> 4);
-              const uint64_t bd = bb + (uint64_t)(((t - 1) * kBSlice) >> 4);
-              const uint32_t acc = (cc > 0 || s > 1) ? 1u : 0u;
-              tc::mma_bf16(tmem + (uint32_t)((gs - 2) * kNJ), ad, bd, idesc, acc);
-            }
-        }
-        tc::mma_commit(&bar_mma);
+          for (int s = 1; s < gs; ++s) {
+            const int t = gs - s;  // s, t <= 7 since g <= 8
+            const uint64_t ad = ab + (uint64_t)(((s - 1) * kASlice) >> 4);
+            const uint64_t bd = bb + (uint64_t)(((t - 1) * kBSlice) >> 4);
+            const uint32_t acc = (cc > 0 || s > 1) ? 1u : 0u;
+            tc::mma_bf16(tmem + (uint32_t)((gs - 2) * kNJ), ad, bd, idesc, acc);
+          }
+        tc::mma_commit(&bar_mma[b]);
       }
-      // the buffer is rewritten (next chunks) or the accumulators read (epilogue) only
-      // once these products are done
-      const bool done = mbar_wait(&bar_mma, par_mma, &ctl->status);
+    }
+    // the accumulators are read (epilogue) only once every product of the tile is done: the
+    // outstanding commits, the earlier one first
+    for (int q = (nchunk >= 2 ? nchunk - 2 : nchunk - 1); ok && q < nchunk; ++q) {
+      const int b = q & 1;
+      if (!mma_out[b]) continue;
+      const bool done = mbar_wait(&bar_mma[b], par_mma[b], &ctl->status);
       if (__syncthreads_or(!done)) {
         ok = false;
         break;
       }
-      par_mma ^= 1u;
-      mma_out = false;
-      tc::fence_after_sync();
+      par_mma[b] ^= 1u;
+      mma_out[b] = false;
     }
+    tc::fence_after_sync();
     if (!ok) break;
     // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows) and 16 columns
     // (quarter w / 4); X = 2^(e_i + f_j - 60) sum_g G_g 2^(8 (8 - g))
@@ -452,8 +469,9 @@ __device__ __forceinline__ void split_body(const Ws& ws, CtaPos cp, int kcols, d
     const uint64_t t0 = global_ns();
     while (tma_out && !mbar_try_wait(&bar_tma, par_tma) && global_ns() - t0 < 500000000ull) {
     }
-    while (mma_out && !mbar_try_wait(&bar_mma, par_mma) && global_ns() - t0 < 1000000000ull) {
-    }
+    for (int b = 0; b < 2; ++b)
+      while (mma_out[b] && !mbar_try_wait(&bar_mma[b], par_mma[b]) && global_ns() - t0 < 1000000000ull) {
+      }
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -489,8 +507,8 @@ bool split_compact_ok(const Ws& ws) { return split_fits(ws) && ws.cap + 1 <= spl
 cudaError_t prepare_split(const Ws& ws) {
   if (ws.prec != ST_DD) return cudaSuccess;
   const int sm = split::smem_bytes(16 * box_chunks(split::kMaxK, 4));
-  static_assert(16 * 17 * 2 * split::kTM + 8 * split::kTM + 7 * (split::kASlice + split::kBSlice) <= 227 * 1024,
-                "the widest staged tile and both digit buffers fit in shared memory");
+  static_assert(16 * 17 * 2 * split::kTM + 8 * split::kTM + 2 * split::kABuf + 7 * split::kBSlice <= 227 * 1024,
+                "the widest staged tile and the digit buffers fit in shared memory");
   cudaError_t e = cudaFuncSetAttribute(split::k_split<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(split::k_split<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   return e;
