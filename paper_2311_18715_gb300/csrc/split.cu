@@ -51,7 +51,9 @@ constexpr int kSlices = 7;      // digits per value
 constexpr int kGroups = 7;      // g = s + t = 2 .. 8
 constexpr int kMaxK = 64;       // basis columns this path takes (4 K chunks)
 constexpr int kBufK = 16;       // K columns of L0 digits in one buffer (one chunk); two buffers
-constexpr int kThreadsS = 512;   // 16 warps: 4 threads per row in the digit phase, 4 warps per TMEM lane quarter
+constexpr int kWorkerWarps = 16;  // 4 threads per row in the digit phase, 4 warps per TMEM lane quarter
+constexpr int kWorkers = 32 * kWorkerWarps;
+constexpr int kThreadsS = kWorkers + 32;  // and one warp that issues the copies and the products
 constexpr uint32_t kTmemCols = 512;
 constexpr int kASlice = kTM * kBufK * 2;   // bytes of one digit slice of an L0 buffer
 constexpr int kABuf = kSlices * kASlice;   // bytes of one L0 digit buffer (one chunk, all slices)
@@ -68,6 +70,18 @@ constexpr long long kDigitBias = 0x80808080808080ll;
 
 __host__ __device__ inline int stage_bytes(int rs) { return ((2 * kTM * rs + kTM * 8 + 1023) / 1024) * 1024; }
 __host__ __device__ inline int smem_bytes(int rs) { return stage_bytes(rs) + 2 * kABuf + kSlices * kBSlice; }
+
+// a barrier of the worker warps alone (named barrier 1; the issuer warp is not in it) that
+// also returns whether v held in any of them
+__device__ __forceinline__ bool workers_sync_or(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n barrier.cta.red.or.pred p, 1, %2, q;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(kWorkers)
+      : "memory");
+  return r != 0;
+}
 
 // exponent e with |v| < 2^e for every double-float v of a set whose largest |hi| is mx (from
 // the bits of mx; 0 for mx = 0): |hi + lo| < 2^e as well, since |lo| <= ulp(hi) / 2
@@ -161,10 +175,13 @@ __device__ __forceinline__ void split_body(const Ws& ws, CtaPos cp, int kcols, d
   unsigned char* adig = sp + stage_bytes(rs);
   unsigned char* bdig = adig + 2 * kABuf;
   __shared__ int fexp[kNJ];
-  __shared__ int erow[kTM];
-  __shared__ float jh[kTM], jl[kTM];           // the new column j0 of the tile (compaction)
+  // per-row exponent and new column j0 (compaction) of a tile, by tile parity: a worker warp
+  // may start the next tile while others still read this tile's rows in their epilogue
+  __shared__ int erow_[2][kTM];
+  __shared__ float jh_[2][kTM], jl_[2][kTM];
   __shared__ float sh_s[kMaxK], sl_s[kMaxK];   // its coefficients s (compaction)
-  __shared__ __align__(8) uint64_t bar_tma, bar_mma[2];
+  __shared__ __align__(8) uint64_t bar_tma, bar_mma[2], bar_full[2], bar_drain;
+  __shared__ volatile int abort_s;
   __shared__ uint32_t tmem_slot;
   const bool with_e = COMPACT && append;
   dd inv = dd{0.f, 0.f};
@@ -212,6 +229,10 @@ __device__ __forceinline__ void split_body(const Ws& ws, CtaPos cp, int kcols, d
     mbar_init(&bar_tma, 1);
     mbar_init(&bar_mma[0], 1);
     mbar_init(&bar_mma[1], 1);
+    mbar_init(&bar_full[0], kWorkers);
+    mbar_init(&bar_full[1], kWorkers);
+    mbar_init(&bar_drain, 1);
+    abort_s = 0;
     mbar_fence_init();
   }
   if (warp == 0) tc::tmem_alloc(&tmem_slot, kTmemCols);
@@ -223,7 +244,6 @@ __device__ __forceinline__ void split_body(const Ws& ws, CtaPos cp, int kcols, d
   const int64_t ntiles = (ws.n + kTM - 1) / kTM;
   const int G = cp.g;
   const int my_tiles = (int)((ntiles - cp.b + G - 1) / G);
-  if (tid == 0 && my_tiles > 0) issue_tile(ws, stage, rs, cp.b, with_e, &bar_tma);
   const uint32_t idesc = tc::instr_desc_bf16_f32(kTM, kNJ);
   // descriptors of digit slice 1 at chunk 0; every other operand differs only in its start
   // address, so its descriptor is this one plus (byte offset >> 4) in the start field (shared
@@ -231,247 +251,266 @@ __device__ __forceinline__ void split_body(const Ws& ws, CtaPos cp, int kcols, d
   const uint64_t adesc0 = tc::smem_desc(smem_addr(adig), tc::kCoreBytes, (kBufK / 8) * tc::kCoreBytes);
   static_assert((kABuf >> 4) < (1 << 13), "a buffer offset fits the descriptor's start field");
   const uint64_t bdesc0 = tc::smem_desc(smem_addr(bdig), tc::kCoreBytes, (kMaxK / 8) * tc::kCoreBytes);
-  uint32_t par_tma = 0, par_mma[2] = {0u, 0u};
-  // work in flight that a timeout must still wait for (the same in every thread): the next
-  // tile's copy, and a commit not yet waited for on each MMA barrier
-  bool tma_out = my_tiles > 0, mma_out[2] = {false, false};
-  // digit phase: four threads per row, thread q of a row owning columns 4q .. 4q + 3 of the
-  // chunk (half of a 16-byte core-matrix row per slice)
-  const int row = tid >> 2, quad = tid & 3;
-  const float* sh = reinterpret_cast<const float*>(stage) + (size_t)row * (rs / 4);
-  const float* sl = reinterpret_cast<const float*>(stage + (size_t)kTM * rs) + (size_t)row * (rs / 4);
-  bool ok = true;
 
-  for (int li = 0; li < my_tiles && ok; ++li) {
-    const int64_t tile = cp.b + (int64_t)li * G;
-    const int64_t row0 = tile * kTM;
-    ok = mbar_wait(&bar_tma, par_tma, &ctl->status);
-    if (__syncthreads_or(!ok)) {
-      ok = false;
-      break;
+  // Roles.  The last warp issues the copies and the products; the 16 workers form digits and
+  // read the accumulators.  Handoffs by mbarriers: bar_tma (a tile is staged), bar_full[b]
+  // (every worker has put its digits of a chunk in buffer b), bar_mma[b] (the products that
+  // read buffer b are done: tcgen05.commit).  The workers never wait for the issuer to
+  // finish issuing, so the digits of chunk c + 1 are formed while the products of chunk c
+  // run.  Every wait is bounded: a timeout sets DEV_TIMEOUT and abort_s, and each role stops
+  // at its next check (the other role's waits then run out as well).
+  if (warp == kWorkerWarps) {
+    if (lane == 0 && my_tiles > 0) {
+      issue_tile(ws, stage, rs, cp.b, with_e, &bar_tma);
+      int tma_issued = 1;
+      uint32_t pf[2] = {0u, 0u};
+      bool issued = false;
+      for (int li = 0; li < my_tiles && !abort_s; ++li) {
+        const int64_t tile = cp.b + (int64_t)li * G;
+        for (int cc = 0; cc < nchunk; ++cc) {
+          const int b = cc & 1;
+          if (!mbar_wait(&bar_full[b], pf[b], &ctl->status)) {
+            abort_s = 1;
+            break;
+          }
+          pf[b] ^= 1u;
+          tc::fence_after_sync();
+          // the staging buffer is free once the tile's last digits are formed: next tile
+          if (cc + 1 == nchunk && li + 1 < my_tiles) {
+            issue_tile(ws, stage, rs, tile + G, with_e, &bar_tma);
+            ++tma_issued;
+          }
+          const uint64_t ab = adesc0 + (uint64_t)((b * kABuf) >> 4);
+          const uint64_t bb = bdesc0 + (uint64_t)((cc * 2 * tc::kCoreBytes) >> 4);
+#pragma unroll
+          for (int gs = 2; gs <= 8; ++gs)
+#pragma unroll
+            for (int s = 1; s < gs; ++s) {
+              const int t = gs - s;  // s, t <= 7 since g <= 8
+              const uint64_t ad = ab + (uint64_t)(((s - 1) * kASlice) >> 4);
+              const uint64_t bd = bb + (uint64_t)(((t - 1) * kBSlice) >> 4);
+              const uint32_t acc = (cc > 0 || s > 1) ? 1u : 0u;
+              tc::mma_bf16(tmem + (uint32_t)((gs - 2) * kNJ), ad, bd, idesc, acc);
+            }
+          tc::mma_commit(&bar_mma[b]);
+          issued = true;
+        }
+      }
+      // before the shared and tensor memory are released: every product issued is done and
+      // every copy issued has landed (bounded waits; normally already so)
+      const uint64_t t0 = global_ns();
+      if (issued) {
+        tc::mma_commit(&bar_drain);
+        while (!mbar_try_wait(&bar_drain, 0u) && global_ns() - t0 < 1000000000ull) {
+        }
+      }
+      while (!mbar_try_wait(&bar_tma, (uint32_t)((tma_issued - 1) & 1)) && global_ns() - t0 < 1500000000ull) {
+      }
     }
-    par_tma ^= 1u;
-    tma_out = false;
-    const bool live = row0 + row < ws.n;
-    if (with_e) {
-      // j0 = (e - L0[:, :r0] s) / rho0 for this row, a quarter of the dot per thread
-      Acc d = acc_zero();
-      if (live)
-        for (int k = quad; k < r0; k += 4) acc_fma(d, sh[k], sl[k], sh_s[k], sl_s[k]);
-      acc_add(d, __shfl_xor_sync(0xffffffffu, d.h, 1), __shfl_xor_sync(0xffffffffu, d.l, 1));
-      acc_add(d, __shfl_xor_sync(0xffffffffu, d.h, 2), __shfl_xor_sync(0xffffffffu, d.l, 2));
-      if (quad == 0) {
-        const float2 ev = reinterpret_cast<const float2*>(stage + (size_t)2 * kTM * rs)[row];
-        Acc e = Acc{ev.x, ev.y};
-        acc_add(e, -d.h, -d.l);
-        e = acc_norm(e);
-        Acc j = acc_zero();
-        acc_fma(j, e.h, e.l, inv.h, inv.l);
-        j = acc_norm(j);
-        jh[row] = live ? j.h : 0.f;
-        jl[row] = live ? j.l : 0.f;
+  } else {
+    // digit phase: four threads per row, thread q of a row owning columns 4q .. 4q + 3 of a
+    // chunk (half of a 16-byte core-matrix row per slice)
+    const int row = tid >> 2, quad = tid & 3;
+    const float* sh = reinterpret_cast<const float*>(stage) + (size_t)row * (rs / 4);
+    const float* sl = reinterpret_cast<const float*>(stage + (size_t)kTM * rs) + (size_t)row * (rs / 4);
+    uint32_t par_tma = 0, par_mma[2] = {0u, 0u};
+    bool ok = true;
+    for (int li = 0; li < my_tiles; ++li) {
+      const int64_t tile = cp.b + (int64_t)li * G;
+      const int64_t row0 = tile * kTM;
+      if (ok && !mbar_wait(&bar_tma, par_tma, &ctl->status)) {
+        ok = false;
+        abort_s = 1;
+      }
+      par_tma ^= 1u;
+      int* erow = erow_[li & 1];
+      float* jh = jh_[li & 1];
+      float* jl = jl_[li & 1];
+      const bool live = row0 + row < ws.n;
+      if (with_e) {
+        // j0 = (e - L0[:, :r0] s) / rho0 for this row, a quarter of the dot per thread
+        Acc d = acc_zero();
+        if (live)
+          for (int k = quad; k < r0; k += 4) acc_fma(d, sh[k], sl[k], sh_s[k], sl_s[k]);
+        acc_add(d, __shfl_xor_sync(0xffffffffu, d.h, 1), __shfl_xor_sync(0xffffffffu, d.l, 1));
+        acc_add(d, __shfl_xor_sync(0xffffffffu, d.h, 2), __shfl_xor_sync(0xffffffffu, d.l, 2));
+        if (quad == 0) {
+          const float2 ev = reinterpret_cast<const float2*>(stage + (size_t)2 * kTM * rs)[row];
+          Acc e = Acc{ev.x, ev.y};
+          acc_add(e, -d.h, -d.l);
+          e = acc_norm(e);
+          Acc j = acc_zero();
+          acc_fma(j, e.h, e.l, inv.h, inv.l);
+          j = acc_norm(j);
+          jh[row] = live ? j.h : 0.f;
+          jl[row] = live ? j.l : 0.f;
+        }
+        __syncwarp();
+      }
+      // the row's exponent: max |hi| over its K columns, a quarter of them per thread
+      {
+        float mx = 0.f;
+        if (live)
+          for (int k = quad; k < K; k += 4) mx = fmaxf(mx, fabsf(k < r0 ? sh[k] : jh[row]));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+        if (quad == 0) erow[row] = grid_exp(mx);
       }
       __syncwarp();
-    }
-    // the row's exponent: max |hi| over its K columns, a quarter of them per thread
-    {
-      float mx = 0.f;
-      if (live)
-        for (int k = quad; k < K; k += 4) mx = fmaxf(mx, fabsf(k < r0 ? sh[k] : jh[row]));
-      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
-      if (quad == 0) erow[row] = grid_exp(mx);
-    }
-    __syncwarp();
-    const int my_e = erow[row];
-    // chunk cc's digits go to buffer cc % 2 while the products of chunk cc - 1 run from the
-    // other; before a buffer is refilled, the products that read it (chunk cc - 2) are waited
-    // for.  Each commit is waited for exactly once, in order, per barrier.
-    for (int cc = 0; cc < nchunk; ++cc) {
-      const int b = cc & 1;
-      if (cc >= 2) {
-        const bool done = mbar_wait(&bar_mma[b], par_mma[b], &ctl->status);
-        if (__syncthreads_or(!done)) {
+      const int my_e = erow[row];
+      for (int cc = 0; cc < nchunk; ++cc) {
+        const int b = cc & 1;
+        if (cc >= 2) {  // the products that read buffer b (chunk cc - 2) are done
+          if (ok && !mbar_wait(&bar_mma[b], par_mma[b], &ctl->status)) {
+            ok = false;
+            abort_s = 1;
+          }
+          par_mma[b] ^= 1u;
+          tc::fence_after_sync();
+        }
+        unsigned char* abuf = adig + b * kABuf;
+        // digits of basis columns kb .. kb + 3 of this row; columns at or past K (the chunk's
+        // zero padding) store zeros without arithmetic
+        const int kb = cc * kKC + 4 * quad;
+        const int off = tc::kmajor_off(row, 4 * quad, kBufK / 8);
+        if (live && kb < K) {
+          uint32_t w[kSlices][2];
+#pragma unroll
+          for (int kk = 0; kk < 4; kk += 2) {
+            const int k = kb + kk;
+            float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+            if (k < r0) {
+              h0 = sh[k];
+              l0 = sl[k];
+            } else if (k < K) {  // the new column (compaction)
+              h0 = jh[row];
+              l0 = jl[row];
+            }
+            if (k + 1 < r0) {
+              h1 = sh[k + 1];
+              l1 = sl[k + 1];
+            } else if (k + 1 < K) {
+              h1 = jh[row];
+              l1 = jl[row];
+            }
+            const unsigned long long u0 = biased_fixed(h0, l0, my_e), u1 = biased_fixed(h1, l1, my_e);
+            w[0][kk >> 1] = digit_pair<1>(u0, u1);
+            w[1][kk >> 1] = digit_pair<2>(u0, u1);
+            w[2][kk >> 1] = digit_pair<3>(u0, u1);
+            w[3][kk >> 1] = digit_pair<4>(u0, u1);
+            w[4][kk >> 1] = digit_pair<5>(u0, u1);
+            w[5][kk >> 1] = digit_pair<6>(u0, u1);
+            w[6][kk >> 1] = digit_pair<7>(u0, u1);
+          }
+#pragma unroll
+          for (int s = 0; s < kSlices; ++s) *reinterpret_cast<uint2*>(abuf + s * kASlice + off) = make_uint2(w[s][0], w[s][1]);
+        } else {
+#pragma unroll
+          for (int s = 0; s < kSlices; ++s) *reinterpret_cast<uint2*>(abuf + s * kASlice + off) = make_uint2(0, 0);
+        }
+        tc::fence_proxy_async();
+        mbar_arrive(&bar_full[b]);
+      }
+      // the accumulators are read only once every product of the tile is done: the commits
+      // not yet waited for, the earlier one first
+      for (int q = (nchunk >= 2 ? nchunk - 2 : 0); q < nchunk; ++q) {
+        const int b = q & 1;
+        if (ok && !mbar_wait(&bar_mma[b], par_mma[b], &ctl->status)) {
           ok = false;
-          break;
+          abort_s = 1;
         }
         par_mma[b] ^= 1u;
-        mma_out[b] = false;
-        tc::fence_after_sync();
       }
-      unsigned char* abuf = adig + b * kABuf;
-      // digits of basis columns kb .. kb + 3 of this row; columns at or past K (the chunk's
-      // zero padding) store zeros without arithmetic
-      const int kb = cc * kKC + 4 * quad;
-      const int off = tc::kmajor_off(row, 4 * quad, kBufK / 8);
-      if (live && kb < K) {
-        uint32_t w[kSlices][2];
+      tc::fence_after_sync();
+      // every worker's row exponents are in place (the epilogue reads other warps' rows), and
+      // all workers agree whether to go on
+      if (workers_sync_or(!ok || abort_s != 0)) break;
+      // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows) and 16 columns
+      // (quarter w / 4); X = 2^(e_i + f_j - 60) sum_g G_g 2^(8 (8 - g))
+      {
+        const int trow = 32 * (warp & 3) + lane;
+        const int64_t orow = row0 + trow;
+        const int er = erow[trow];
+        const int jb = 16 * (warp >> 2);
+        for (int c8 = 0; c8 < 16; c8 += 8) {
+          uint32_t g[kGroups][8];
 #pragma unroll
-        for (int kk = 0; kk < 4; kk += 2) {
-          const int k = kb + kk;
-          float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
-          if (k < r0) {
-            h0 = sh[k];
-            l0 = sl[k];
-          } else if (k < K) {  // the new column (compaction)
-            h0 = jh[row];
-            l0 = jl[row];
+          for (int q = 0; q < kGroups; ++q) {
+            const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(q * kNJ + jb + c8);
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                         : "=r"(g[q][0]), "=r"(g[q][1]), "=r"(g[q][2]), "=r"(g[q][3]), "=r"(g[q][4]), "=r"(g[q][5]),
+                           "=r"(g[q][6]), "=r"(g[q][7])
+                         : "r"(taddr));
           }
-          if (k + 1 < r0) {
-            h1 = sh[k + 1];
-            l1 = sl[k + 1];
-          } else if (k + 1 < K) {
-            h1 = jh[row];
-            l1 = jl[row];
-          }
-          const unsigned long long u0 = biased_fixed(h0, l0, my_e), u1 = biased_fixed(h1, l1, my_e);
-          w[0][kk >> 1] = digit_pair<1>(u0, u1);
-          w[1][kk >> 1] = digit_pair<2>(u0, u1);
-          w[2][kk >> 1] = digit_pair<3>(u0, u1);
-          w[3][kk >> 1] = digit_pair<4>(u0, u1);
-          w[4][kk >> 1] = digit_pair<5>(u0, u1);
-          w[5][kk >> 1] = digit_pair<6>(u0, u1);
-          w[6][kk >> 1] = digit_pair<7>(u0, u1);
-        }
+          tc::tmem_ld_wait();
+          if (orow >= ws.n || jb + c8 >= J) continue;
+          float vh[8], vl[8];
+          int sc[8];
 #pragma unroll
-        for (int s = 0; s < kSlices; ++s) *reinterpret_cast<uint2*>(abuf + s * kASlice + off) = make_uint2(w[s][0], w[s][1]);
-      } else {
+          for (int u = 0; u < 8; u += 2) {
+            // every term G_g 2^(8 (8 - g)) is an exact float (|G_g| < 2^24): a cascaded sum,
+            // smallest term first, with the exact rounding error of each addition (two-sum)
+            // gathered in a second float, then one renormalization; columns u and u + 1 share
+            // each FP32x2 instruction
+            f2x sh2 = f2x_pack(__uint_as_float(g[kGroups - 1][u]), __uint_as_float(g[kGroups - 1][u + 1]));
+            f2x el2 = 0ull;
 #pragma unroll
-        for (int s = 0; s < kSlices; ++s) *reinterpret_cast<uint2*>(abuf + s * kASlice + off) = make_uint2(0, 0);
-      }
-      tc::fence_proxy_async();
-      __syncthreads();
-      const bool last_digits = cc + 1 == nchunk;
-      if (last_digits && li + 1 < my_tiles) tma_out = true;
-      mma_out[b] = true;
-      if (tid == 0) {
-        // the staging buffer is free once the tile's last digits are formed: next tile
-        if (last_digits && li + 1 < my_tiles) issue_tile(ws, stage, rs, tile + G, with_e, &bar_tma);
-        tc::fence_after_sync();
-        const uint64_t ab = adesc0 + (uint64_t)((b * kABuf) >> 4);
-        const uint64_t bb = bdesc0 + (uint64_t)((cc * 2 * tc::kCoreBytes) >> 4);
-#pragma unroll
-        for (int gs = 2; gs <= 8; ++gs)
-#pragma unroll
-          for (int s = 1; s < gs; ++s) {
-            const int t = gs - s;  // s, t <= 7 since g <= 8
-            const uint64_t ad = ab + (uint64_t)(((s - 1) * kASlice) >> 4);
-            const uint64_t bd = bb + (uint64_t)(((t - 1) * kBSlice) >> 4);
-            const uint32_t acc = (cc > 0 || s > 1) ? 1u : 0u;
-            tc::mma_bf16(tmem + (uint32_t)((gs - 2) * kNJ), ad, bd, idesc, acc);
-          }
-        tc::mma_commit(&bar_mma[b]);
-      }
-    }
-    // the accumulators are read (epilogue) only once every product of the tile is done: the
-    // outstanding commits, the earlier one first
-    for (int q = (nchunk >= 2 ? nchunk - 2 : nchunk - 1); ok && q < nchunk; ++q) {
-      const int b = q & 1;
-      if (!mma_out[b]) continue;
-      const bool done = mbar_wait(&bar_mma[b], par_mma[b], &ctl->status);
-      if (__syncthreads_or(!done)) {
-        ok = false;
-        break;
-      }
-      par_mma[b] ^= 1u;
-      mma_out[b] = false;
-    }
-    tc::fence_after_sync();
-    if (!ok) break;
-    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows) and 16 columns
-    // (quarter w / 4); X = 2^(e_i + f_j - 60) sum_g G_g 2^(8 (8 - g))
-    {
-      const int trow = 32 * (warp & 3) + lane;
-      const int64_t orow = row0 + trow;
-      const int er = erow[trow];
-      const int jb = 16 * (warp >> 2);
-      for (int c8 = 0; c8 < 16; c8 += 8) {
-        uint32_t g[kGroups][8];
-#pragma unroll
-        for (int q = 0; q < kGroups; ++q) {
-          const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(q * kNJ + jb + c8);
-          asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                       : "=r"(g[q][0]), "=r"(g[q][1]), "=r"(g[q][2]), "=r"(g[q][3]), "=r"(g[q][4]), "=r"(g[q][5]),
-                         "=r"(g[q][6]), "=r"(g[q][7])
-                       : "r"(taddr));
-        }
-        tc::tmem_ld_wait();
-        if (orow >= ws.n || jb + c8 >= J) continue;
-        float vh[8], vl[8];
-        int sc[8];
-#pragma unroll
-        for (int u = 0; u < 8; u += 2) {
-          // every term G_g 2^(8 (8 - g)) is an exact float (|G_g| < 2^24): a cascaded sum,
-          // smallest term first, with the exact rounding error of each addition (two-sum)
-          // gathered in a second float, then one renormalization; columns u and u + 1 share
-          // each FP32x2 instruction
-          f2x sh2 = f2x_pack(__uint_as_float(g[kGroups - 1][u]), __uint_as_float(g[kGroups - 1][u + 1]));
-          f2x el2 = 0ull;
-#pragma unroll
-          for (int q = kGroups - 2; q >= 0; --q) {
-            const f2x t = mul2(f2x_pack(__uint_as_float(g[q][u]), __uint_as_float(g[q][u + 1])),
-                               f2x_pack(group_scale(q), group_scale(q)));
-            const f2x s2 = add2(sh2, t);
-            const f2x bb = sub2(s2, sh2);
-            el2 = add2(el2, add2(sub2(sh2, sub2(s2, bb)), sub2(t, bb)));
-            sh2 = s2;
-          }
-          const f2x hs = add2(sh2, el2);  // fast two-sum: |sh| >= |el|
-          const f2x ls = sub2(el2, sub2(hs, sh2));
-          f2x_unpack(hs, vh[u], vh[u + 1]);
-          f2x_unpack(ls, vl[u], vl[u + 1]);
-          sc[u] = er + fexp[jb + c8 + u] - 60;  // the value is 2^sc (vh + vl)
-          sc[u + 1] = er + fexp[jb + c8 + u + 1] - 60;
-        }
-        if constexpr (COMPACT) {
-          // whole 8-column pieces of the row as two 16-byte stores per plane
-          const size_t o = (size_t)orow * ws.ldg + jb + c8;
-          float* Lh = reinterpret_cast<float*>(ws.Lh);
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            // basis entries lie well inside the float range: an exact power-of-two product
-            if (sc[u] >= -126 && sc[u] <= 127) {
-              const float p2 = __int_as_float((sc[u] + 127) << 23);
-              vh[u] = __fmul_rn(vh[u], p2);
-              vl[u] = __fmul_rn(vl[u], p2);
-            } else {
-              vh[u] = ldexpf(vh[u], sc[u]);
-              vl[u] = ldexpf(vl[u], sc[u]);
+            for (int q = kGroups - 2; q >= 0; --q) {
+              const f2x t = mul2(f2x_pack(__uint_as_float(g[q][u]), __uint_as_float(g[q][u + 1])),
+                                 f2x_pack(group_scale(q), group_scale(q)));
+              const f2x s2 = add2(sh2, t);
+              const f2x bb = sub2(s2, sh2);
+              el2 = add2(el2, add2(sub2(sh2, sub2(s2, bb)), sub2(t, bb)));
+              sh2 = s2;
             }
+            const f2x hs = add2(sh2, el2);  // fast two-sum: |sh| >= |el|
+            const f2x ls = sub2(el2, sub2(hs, sh2));
+            f2x_unpack(hs, vh[u], vh[u + 1]);
+            f2x_unpack(ls, vl[u], vl[u + 1]);
+            sc[u] = er + fexp[jb + c8 + u] - 60;  // the value is 2^sc (vh + vl)
+            sc[u + 1] = er + fexp[jb + c8 + u + 1] - 60;
           }
-          if (jb + c8 + 8 <= J) {
-            *reinterpret_cast<float4*>(Lh + o) = make_float4(vh[0], vh[1], vh[2], vh[3]);
-            *reinterpret_cast<float4*>(Lh + o + 4) = make_float4(vh[4], vh[5], vh[6], vh[7]);
-            *reinterpret_cast<float4*>(ws.Ll + o) = make_float4(vl[0], vl[1], vl[2], vl[3]);
-            *reinterpret_cast<float4*>(ws.Ll + o + 4) = make_float4(vl[4], vl[5], vl[6], vl[7]);
+          if constexpr (COMPACT) {
+            // whole 8-column pieces of the row as two 16-byte stores per plane
+            const size_t o = (size_t)orow * ws.ldg + jb + c8;
+            float* Lh = reinterpret_cast<float*>(ws.Lh);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              // basis entries lie well inside the float range: an exact power-of-two product
+              if (sc[u] >= -126 && sc[u] <= 127) {
+                const float p2 = __int_as_float((sc[u] + 127) << 23);
+                vh[u] = __fmul_rn(vh[u], p2);
+                vl[u] = __fmul_rn(vl[u], p2);
+              } else {
+                vh[u] = ldexpf(vh[u], sc[u]);
+                vl[u] = ldexpf(vl[u], sc[u]);
+              }
+            }
+            if (jb + c8 + 8 <= J) {
+              *reinterpret_cast<float4*>(Lh + o) = make_float4(vh[0], vh[1], vh[2], vh[3]);
+              *reinterpret_cast<float4*>(Lh + o + 4) = make_float4(vh[4], vh[5], vh[6], vh[7]);
+              *reinterpret_cast<float4*>(ws.Ll + o) = make_float4(vl[0], vl[1], vl[2], vl[3]);
+              *reinterpret_cast<float4*>(ws.Ll + o + 4) = make_float4(vl[4], vl[5], vl[6], vl[7]);
+            } else {
+#pragma unroll
+              for (int u = 0; u < 8; ++u)
+                if (jb + c8 + u < J) {
+                  Lh[o + u] = vh[u];
+                  ws.Ll[o + u] = vl[u];
+                }
+            }
           } else {
 #pragma unroll
             for (int u = 0; u < 8; ++u)
-              if (jb + c8 + u < J) {
-                Lh[o + u] = vh[u];
-                ws.Ll[o + u] = vl[u];
-              }
+              if (jb + c8 + u < J)  // the double's bits from the pair by integer operations
+                out[(size_t)(jb + c8 + u) * ld + orow] = pair_to_double_fast(vh[u], vl[u], sc[u]);
           }
-        } else {
-#pragma unroll
-          for (int u = 0; u < 8; ++u)
-            if (jb + c8 + u < J)  // the double's bits from the pair by integer operations
-              out[(size_t)(jb + c8 + u) * ld + orow] = pair_to_double_fast(vh[u], vl[u], sc[u]);
         }
       }
+      // the accumulators are read before the next tile's first products, which the issuer
+      // starts after this worker's next arrival on bar_full
+      tc::fence_before_sync();
     }
-    tc::fence_before_sync();
-    __syncthreads();
-  }
-  if (!ok && tid == 0) {
-    // a wait ran out (DEV_TIMEOUT is set): give the copy and the products still in flight a
-    // bounded wait before the shared and tensor memory are released
-    const uint64_t t0 = global_ns();
-    while (tma_out && !mbar_try_wait(&bar_tma, par_tma) && global_ns() - t0 < 500000000ull) {
-    }
-    for (int b = 0; b < 2; ++b)
-      while (mma_out[b] && !mbar_try_wait(&bar_mma[b], par_mma[b]) && global_ns() - t0 < 1000000000ull) {
-      }
   }
   tc::fence_before_sync();
   __syncthreads();
