@@ -221,7 +221,10 @@ struct IngestTab {
 // The kernels of an update run back to back in one CUDA graph.  Each is launched with
 // programmatic stream serialisation, so the grid is set up while its predecessor finishes;
 // its first statement waits for the predecessor's completion and memory (and returns at
-// once when the kernel was launched without the attribute).
+// once when the kernel was launched without the attribute).  Every kernel that can be
+// launched this way begins with pdl_wait.  (Letting each kernel trigger its successor at its
+// start, so that the successor's CTAs are placed while it runs, measured slower: 5,926
+// against 6,362 snapshot updates/s.)
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 template <typename... KArgs, typename... Args>

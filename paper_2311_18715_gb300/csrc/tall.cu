@@ -1118,6 +1118,7 @@ __device__ void fold_check(const Ws& ws) {
 }
 
 __global__ void __launch_bounds__(32) k_fold_check(Ws ws) {
+  pdl_wait();
   if (threadIdx.x == 0) fold_check(ws);
 }
 
@@ -1127,6 +1128,7 @@ __global__ void __launch_bounds__(32) k_fold_check(Ws ws) {
 // blockIdx.x works on that row block.
 template <int ST, bool CHECK>
 __global__ void __launch_bounds__(kThreads) k_rollout(Ws ws, int kcols, void* out, int64_t ld, int cta0, int fold) {
+  pdl_wait();
   using T = Traits<ST>;
   using snap_t = typename T::snap_t;
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -1354,6 +1356,7 @@ __device__ void fold_first(const Ws& ws) {
 }
 
 __global__ void __launch_bounds__(32) k_fold_first(Ws ws) {
+  pdl_wait();
   if (threadIdx.x == 0) fold_first(ws);
 }
 
@@ -1361,6 +1364,7 @@ __global__ void __launch_bounds__(32) k_fold_first(Ws ws) {
 // per stream, negligible
 template <typename stored_t>
 __global__ void __launch_bounds__(kThreads) k_first(Ws ws, int cta0, int fold) {
+  pdl_wait();
   Ctl* ctl = ws.ctl;
   const stored_t* c = reinterpret_cast<const stored_t*>(ws.cbuf[ctl->cur_c]);
   const int blk = cta0 + blockIdx.x;
