@@ -114,7 +114,12 @@ __device__ __forceinline__ void prep_body(const Ws& ws, CtaPos cp) {
     sy = warp_sum_d(sy);
     if (lane == 0) {
       const double eta = dd2d(red[2 * r0]), ex = dd2d(red[2 * r0 + 1]);
-      const double rho0 = sqrt(fmax(eta - ssq, 0.0));
+      // rho0 and 1 / rho0 from one reciprocal square root: every dependent FP64 operation of
+      // this one thread costs ~100 cycles, and a square root followed by a division is a
+      // chain about twice as long
+      const double e2 = fmax(eta - ssq, 0.0);
+      const double irho0 = e2 > 0.0 ? rsqrt(e2) : 0.0;
+      const double rho0 = e2 * irho0;
       const double cn = sqrt(dd2d(st.hdr->cn2));
       const double sig1 = r > 0 ? st.S[0] : 0.0;
       const double thr = ws.tau * fmax(sig1, cn);
@@ -125,7 +130,7 @@ __device__ __forceinline__ void prep_body(const Ws& ws, CtaPos cp) {
       ctl->r0e = r0 + append;
       if (append) {
         ac[r0] = rho0;
-        yx[r0] = (ex - sy) / rho0;
+        yx[r0] = (ex - sy) * irho0;
       }
       append_s = append;
       thr_s = thr;
@@ -194,9 +199,9 @@ __device__ __forceinline__ void prep_body(const Ws& ws, CtaPos cp) {
     }
   }
   if (tid == 0) {
-    double rh = sqrt(zz);
-    if (!(rh > thr)) rh = 0.0;
-    const double iv = rh > 0.0 ? 1.0 / rh : 0.0;
+    const double irh = zz > 0.0 ? rsqrt(zz) : 0.0;  // rho and 1 / rho from one reciprocal root
+    double rh = zz * irh, iv = irh;
+    if (!(rh > thr)) rh = iv = 0.0;
     rho_s = rh;
     inv_s = iv;
     ctl->rho = rh;
@@ -659,16 +664,27 @@ __device__ __forceinline__ void zhat_body(const Ws& ws, CtaPos cp) {
   const int i = cp.b;
   if (i >= m) return;
   const double* d = ws.sm.d;
-  const double di = d[i];
+  // the poles and the roots' origins and offsets into shared memory at once (asynchronous
+  // copies), so that each factor's operands are one shared-memory read away
+  __shared__ double sd[kMaxN], smu[kMaxN];
+  __shared__ int sorg[kMaxN];
+  for (int k = tid; k < m; k += kZhatThreads) {
+    cp_async8(sd + k, d + k);
+    cp_async8(smu + k, ws.sm.mu + k);
+  }
+  for (int k = tid; k < m; k += kZhatThreads) sorg[k] = ws.sm.org[k];
+  cp_async_wait_all();
+  __syncthreads();
+  const double di = sd[i];
   double prod = 1.0;
   for (int k = tid; k < m; k += kZhatThreads) {
-    const double dko = d[ws.sm.org[k]];
-    const double lam_m_di = ws.sm.mu[k] - (di - dko) * (di + dko);  // lambda_k - d_i^2
+    const double dko = sd[sorg[k]];
+    const double lam_m_di = smu[k] - (di - dko) * (di + dko);  // lambda_k - d_i^2
     double f;
     if (k == m - 1) {
       f = lam_m_di;
     } else {
-      const double dk = d[k < i ? k : k + 1];
+      const double dk = sd[k < i ? k : k + 1];
       f = lam_m_di / ((dk - di) * (dk + di));
     }
     prod *= f;
@@ -705,29 +721,32 @@ __device__ __forceinline__ void vectors_body(const Ws& ws, CtaPos cp) {
   pdl_wait();
   Ctl* ctl = ws.ctl;
   const int j = cp.b;
+  const int tid = threadIdx.x;
+  const double* d = ws.sm.d;
+  // this thread's first pole (the arrays hold kMaxN entries): loaded before the dependent
+  // chain rnew -> src -> org -> d below, so that their latencies overlap
+  const double d0 = d[tid], zh0 = ws.sm.zhat[tid];
+  const int pole0 = ws.sm.pole[tid];
   if (j >= ctl->rnew) return;
   const int n = ctl->n, m = ctl->m, r = n - 1;
-  const int tid = threadIdx.x;
+  const int code = ws.sm.src[j];
   __shared__ double u[kMaxN], v[kMaxN], red[4];
   for (int i = tid; i < n; i += kVecThreads) {
     u[i] = 0.0;
-    v[i] = 0.0;
+    v[i] = (code >= 0 && i == r) ? -1.0 : 0.0;  // v = (d_i u_i, -1) for a root
   }
   __syncthreads();
-  const int code = ws.sm.src[j];
   if (code >= 0) {
-    const double* d = ws.sm.d;
     const double dob = d[ws.sm.org[code]];
     const double mu = ws.sm.mu[code];
     for (int i = tid; i < m; i += kVecThreads) {
-      const double di = d[i];
-      const double ui = ws.sm.zhat[i] / ((di - dob) * (di + dob) - mu);  // z^_i / (d_i^2 - lambda)
-      const int c = ws.sm.pole[i];
+      const bool first = i == tid;
+      const double di = first ? d0 : d[i];
+      const double ui = (first ? zh0 : ws.sm.zhat[i]) / ((di - dob) * (di + dob) - mu);  // z^_i / (d_i^2 - lambda)
+      const int c = first ? pole0 : ws.sm.pole[i];
       u[c] = ui;
       if (c < r) v[c] = di * ui;
     }
-    __syncthreads();
-    if (tid == 0) v[r] = -1.0;
     __syncthreads();
     double su = 0.0, sv = 0.0;
     for (int i = tid; i < n; i += kVecThreads) {
@@ -869,7 +888,7 @@ __device__ void apply_column(const Ws& ws, int j, const StateBuf& st, const Stat
   double* sM = asm_;                                // [k][i], ld rm
   double* sQ = sM + (size_t)kMaxR * kMaxR;          // [k][i], ld qld
   double* sU = sQ + (size_t)kMaxR * (kMaxCap + 1);  // [i][k], ld kMaxN
-  __shared__ double v[kMaxN], u[kMaxN], bv[kMaxN], qcol[kMaxCap + 1], rlv;
+  __shared__ double v[kMaxN], u[kMaxN], bv[kMaxN], qcol[kMaxCap + 1];
   stage_doubles(sM, st.M, r * rm, tid, kApplyThreads);
   stage_doubles(sQ, st.Q, r * qld, tid, kApplyThreads);
   stage_doubles(sU, ws.sm.U, rnew * kMaxN, tid, kApplyThreads);
@@ -886,13 +905,13 @@ __device__ void apply_column(const Ws& ws, int j, const StateBuf& st, const Stat
     acc = group4_sum_d(acc);
     if (i < r && sub == 0) bv[i] = fma(ws.sm.w[i], v[r], acc);
   }
-  // row r: rho (r_last . v[0:r]) + gamma v_r   (warp 7)
+  // row r: rho (r_last . v[0:r]) + gamma v_r   (warp 7, which writes it itself)
   if ((tid >> 5) == 7) {
     const int lane = tid & 31;
     double t = 0.0;
     for (int k = lane; k < r; k += 32) t = fma(st.rl[k], v[k], t);
     t = warp_sum_d(t);
-    if (lane == 0) rlv = t;
+    if (lane == 0) bv[r] = fma(rho, t, gamma * v[r]);
   }
   // Q' column j (rows 0..r0e-1): Q u[0:r] + qn u_r
   for (int base = 0; base < 4 * r0e; base += kApplyThreads) {
@@ -903,8 +922,6 @@ __device__ void apply_column(const Ws& ws, int j, const StateBuf& st, const Stat
     acc = group4_sum_d(acc);
     if (i < r0e && sub == 0) qcol[i] = fma(ws.sm.qn[i], u[r], acc);
   }
-  __syncthreads();
-  if (tid == 0) bv[r] = fma(rho, rlv, gamma * v[r]);
   __syncthreads();
   // M' column j: U'^T (B v)   (4 threads per output row i < rnew)
   {
