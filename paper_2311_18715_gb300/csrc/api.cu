@@ -157,7 +157,7 @@ Layout make_layout(const odmd_config& c) {
     return at;
   };
   L.off_ctl = take(sizeof(Ctl));
-  L.off_maps = take(2 * kMaxMaps * sizeof(CUtensorMap));
+  L.off_maps = take(4 * kMaxMaps * sizeof(CUtensorMap));
   L.off_hdr[0] = take(sizeof(StateHdr));
   L.off_hdr[1] = take(sizeof(StateHdr));
   L.state_doubles = 3 * (size_t)L.rmax + (size_t)L.rmax * L.rmax + (size_t)qld * L.rmax + 2 * (size_t)qld;
@@ -320,27 +320,30 @@ odmd_status encode_maps(odmd_t h, const Layout& L) {
   const int esz = esz_of(h->cfg.prec);
   const int planes = h->cfg.prec == ODMD_FP64 ? 2 : 1;
   const int maxc = box_chunks(L.cap, esz);
-  h->maps_host.assign(2 * kMaxMaps, CUtensorMap{});
+  h->maps_host.assign(4 * kMaxMaps, CUtensorMap{});
   const CUtensorMapDataType dt = h->cfg.prec == ODMD_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-  for (int pl = 0; pl < planes; ++pl) {
-    void* gaddr = pl == 0 ? h->ws.Lh : (void*)h->ws.Ll;
-    for (int k = 0; k < kMaxMaps; ++k) {
-      const int c = 2 * k + 1;
-      if (c > maxc) break;
-      const cuuint64_t dims[2] = {(cuuint64_t)L.ldg, (cuuint64_t)L.npad};
-      const cuuint64_t strides[1] = {(cuuint64_t)L.ldg * esz};
-      const cuuint32_t box[2] = {(cuuint32_t)(c * 16 / esz), (cuuint32_t)kTile};
-      const cuuint32_t estr[2] = {1, 1};
-      CUresult r = encode(&h->maps_host[pl * kMaxMaps + k], dt, 2, gaddr, dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-      if (r != CUDA_SUCCESS) {
-        char buf[96];
-        std::snprintf(buf, sizeof buf, "cuTensorMapEncodeTiled failed (%d) for box %d", (int)r, c);
-        return fail(h, ODMD_ERR_CUDA, buf);
+  // boxes of kTile rows (the tile passes) and of kPassARows rows (pass A), per plane, for
+  // every odd chunk width up to the widest basis
+  for (int hh = 0; hh < 2; ++hh)
+    for (int pl = 0; pl < planes; ++pl) {
+      void* gaddr = pl == 0 ? h->ws.Lh : (void*)h->ws.Ll;
+      for (int k = 0; k < kMaxMaps; ++k) {
+        const int c = 2 * k + 1;
+        if (c > maxc) break;
+        const cuuint64_t dims[2] = {(cuuint64_t)L.ldg, (cuuint64_t)L.npad};
+        const cuuint64_t strides[1] = {(cuuint64_t)L.ldg * esz};
+        const cuuint32_t box[2] = {(cuuint32_t)(c * 16 / esz), (cuuint32_t)(hh == 0 ? kTile : kPassARows)};
+        const cuuint32_t estr[2] = {1, 1};
+        CUresult r = encode(&h->maps_host[(2 * hh + pl) * kMaxMaps + k], dt, 2, gaddr, dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+          char buf[96];
+          std::snprintf(buf, sizeof buf, "cuTensorMapEncodeTiled failed (%d) for box %d", (int)r, c);
+          return fail(h, ODMD_ERR_CUDA, buf);
+        }
       }
     }
-  }
   return ODMD_OK;
 }
 

@@ -26,7 +26,8 @@ constexpr int kMaxR = 64;          // largest r_max
 constexpr int kMaxSlack = 32;      // largest slack
 constexpr int kMaxCap = kMaxR + kMaxSlack;  // largest number of basis columns r0
 constexpr int kMaxN = kMaxR + 1;   // largest core matrix order r + 1
-constexpr int kMaxMaps = 13;       // tensor maps per plane: box widths of 1, 3, ..., 25 chunks
+constexpr int kMaxMaps = 13;       // tensor maps per plane and box height: widths of 1, 3, ..., 25 chunks
+constexpr int kPassARows = 32;     // rows of a pass-A tile (its tensor maps' box height)
 constexpr int kRollK = 64;         // horizons (columns) per rollout launch
 constexpr int kGramCtas = 304;     // most CTAs of the Gram pass of the orthogonality refinement
 
@@ -163,8 +164,9 @@ struct Ws {
   void* cbuf[2];    // snapshot buffers (npad elements: float pairs in FP64 mode, else floats)
   void* xbuf;       // scratch snapshot (check input copy), same format
   float2* ebuf;     // first-pass residual e = c - L0 a of the update in flight (hi, lo)
-  const CUtensorMap* maps;  // [plane][k]: 2-D tile maps of the basis planes, box of
-                            // (2k+1) chunks x kTile rows; plane 1 only in FP64 mode
+  const CUtensorMap* maps;  // [2 plane + p][k] for box heights (kTile, kPassARows) x planes:
+                            // 2-D maps of the basis planes, boxes of (2k+1) chunks; plane 1
+                            // only in FP64 mode
   float2* part;     // per-CTA partial sums: gridA x (2*cap+3)
   float2* gpart;    // refinement: per-CTA Gram partials, kGramCtas x cap(cap+1)/2 (or null)
   float2* rscr;     // refinement: small matrices (or null)
@@ -454,6 +456,16 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
           "r"(smem_addr(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// The same load with an L2 eviction-priority hint (a policy from l2_evict_first_policy).
+__device__ __forceinline__ void tma_load_2d_hint(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar,
+                                                 uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%2, "
+      "%3}], [%4], %5;" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar)), "l"(policy)
       : "memory");
 }
 

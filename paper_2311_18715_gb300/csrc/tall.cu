@@ -362,7 +362,8 @@ __device__ __forceinline__ void tile_dot8_term(const float (&xh)[R], const float
 // arithmetic runs on packed FP32x2 instructions; the row dots are unrolled for the
 // tile's chunk count.
 // ---------------------------------------------------------------------------------------
-constexpr int kRowsA = 32;                      // rows per tile (one warp)
+constexpr int kRowsA = kPassARows;              // rows per tile (one warp)
+static_assert(kRowsA == 32, "a pass-A tile is one row per lane");
 constexpr int kWarpsA = 8;                      // compute warps per CTA
 constexpr int kThreadsA = 32 * kWarpsA;
 #ifndef ODMD_PASS_A_MAX_STAGES
@@ -391,25 +392,26 @@ __host__ __device__ inline size_t pass_a_region(int stage_sz, int nstages) {
   return a > b ? a : b;
 }
 
-// The rows of a 32-row tile are contiguous in both basis planes (row pitch ldg), so a tile
-// is one 1-D bulk copy per plane: two TMA operations per tile, each several KB.
+// A tile is one 2-D tensor copy per plane of its 32 rows and only the chunks the row dots
+// read (nch = the odd chunk count that covers r0, not the padded row pitch); in shared
+// memory its rows are nch chunks apart (an odd number of 16-byte chunks, so the lanes of a
+// warp reading one chunk of consecutive rows hit distinct banks).
 template <int ST>
 struct PipeA {
   using T = Traits<ST>;
   unsigned char* base;
   uint64_t* full;
-  int stage_sz, rs, nch, plane_off;
-  const unsigned char* gh;  // hi (or only) plane
-  const unsigned char* gl;  // lo plane (double-float)
-  uint64_t policy;          // L2 evict-first: the planes are streamed once per pass
+  int stage_sz, rs, nch, plane_off;  // rs: shared-memory row pitch = 16 nch bytes
+  const CUtensorMap* mh;             // hi (or only) plane's map of box (nch chunks, 32 rows)
+  const CUtensorMap* ml;             // lo plane's (double-float)
+  uint64_t policy;                   // L2 evict-first: the planes are streamed once per pass
   __device__ unsigned char* plane_h(int s) const { return base + (size_t)s * stage_sz; }
   __device__ unsigned char* plane_l(int s) const { return plane_h(s) + plane_off; }
   // the copies of tile `tile` into stage s (one thread)
   __device__ void issue(int tile, int s) const {
-    const size_t off = (size_t)tile * kRowsA * rs;
     mbar_arrive_expect_tx(&full[s], (uint32_t)(kRowsA * rs * T::planes));
-    bulk_g2s_hint(plane_h(s), gh + off, kRowsA * rs, &full[s], policy);
-    if (T::planes == 2) bulk_g2s_hint(plane_l(s), gl + off, kRowsA * rs, &full[s], policy);
+    tma_load_2d_hint(plane_h(s), mh, 0, tile * kRowsA, &full[s], policy);
+    if (T::planes == 2) tma_load_2d_hint(plane_l(s), ml, 0, tile * kRowsA, &full[s], policy);
   }
 };
 
@@ -563,11 +565,14 @@ __device__ __forceinline__ void pass_a_body(const Ws& ws, CtaPos cp, int cta0, i
 
   PipeA<ST> P;
   P.stage_sz = stage_bytes_a<ST>(ws.cap);
-  P.rs = ws.ldg * T::esz;  // = 16 box_chunks(cap): an odd number of 16-byte chunks
-  P.plane_off = kRowsA * P.rs;
   P.nch = r0 > 0 ? box_chunks(r0, T::esz) : 0;
-  P.gh = reinterpret_cast<const unsigned char*>(ws.Lh);
-  P.gl = reinterpret_cast<const unsigned char*>(ws.Ll);
+  {
+    const int nb = P.nch > 0 ? P.nch : 1;  // with no columns yet, copy the first chunk anyway
+    P.rs = 16 * nb;
+    P.mh = ws.maps + 2 * kMaxMaps + (nb - 1) / 2;
+    P.ml = ws.maps + 3 * kMaxMaps + (nb - 1) / 2;
+  }
+  P.plane_off = kRowsA * P.rs;
   // per-row vectors come in by plain loads, issued before the tile's wait: c, x, the stored
   // residual of the previous update
   const stored_t* cvec = reinterpret_cast<const stored_t*>(ws.cbuf[curc]);
@@ -744,7 +749,7 @@ __device__ __forceinline__ void pass_a_body(const Ws& ws, CtaPos cp, int cta0, i
             }
           }
         };
-        rows16(cq < P.nch ? cq : P.nch - 1, std::integral_constant<int, 0>{});
+        rows16(cq < P.nch ? cq : (P.nch > 0 ? P.nch - 1 : 0), std::integral_constant<int, 0>{});
         if constexpr (kCS > 1) {
           if (P.nch > 16) rows16(cq + 16 < P.nch ? cq + 16 : P.nch - 1, std::integral_constant<int, kCS - 1>{});
         }
