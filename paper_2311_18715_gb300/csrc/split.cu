@@ -25,15 +25,18 @@
 // pair by integer operations (pair2d.cuh: FP64 conversions run at the FP64 rate on this
 // GPU).
 //
-// One persistent CTA of 256 threads per SM (the seven accumulators take 448 of the SM's 512
-// tensor-memory columns).  C's digits are formed once per CTA.  A 128-row tile of L0 (both
-// planes) arrives by two bulk copies into a staging buffer; four threads per row form its
-// digits, 32 basis columns (two K chunks) at a time, into the K-major core-matrix layout
-// the descriptors describe (tc.cuh); one thread issues the chunk's 28 MMAs and commits them
-// to an mbarrier; once the last digits of a tile are formed the staging buffer takes the
-// next tile while the products and the epilogue of this one run.  Every wait is bounded
-// (2 s): a timeout sets DEV_TIMEOUT, waits (bounded) for the work in flight, and frees the
-// tensor memory before the CTA returns.
+// One persistent CTA per SM (the seven accumulators take 448 of the SM's 512 tensor-memory
+// columns) with two roles.  Sixteen worker warps: C's digits once per CTA; for each 128-row
+// tile of L0 (both planes staged by two bulk copies), four threads per row form its digits
+// one 16-column K chunk at a time into one of two buffers (the K-major core-matrix layout
+// the descriptors describe, tc.cuh), and read the accumulators in the epilogue.  One issuer
+// warp: the tile copies and, per chunk, the 28 MMAs and their commit.  They hand over by
+// mbarriers (a buffer's digits are complete; a buffer's products are done), so the workers
+// form chunk c + 1 while the tensor core multiplies chunk c and never wait while the issuing
+// thread is held by the tensor core's queue; the staging buffer takes the next tile once the
+// tile's last digits are formed.  Every wait is bounded (2 s): a timeout sets DEV_TIMEOUT
+// and each role stops at its next check; the issuer waits (bounded) for the copies and
+// products it issued before the tensor memory is freed.
 #include <cstdint>
 
 #include "dd.cuh"
