@@ -61,6 +61,9 @@ struct odmd_instance {
   cudaStream_t cap = nullptr;
   bool use_graphs = true;
   bool use_tc = true;   // multi-horizon rollouts on the tensor cores where split.cu takes them
+  // false once nothing can be pending: the last call that changed the state was followed by
+  // a flush or a tensor-core rollout (which write the pending basis column)
+  bool maybe_pend = true;
   int sms = 0;          // streaming multiprocessors of the handle's device
   // odmd_update_host: two staging slots in the workspace, filled on a copy stream of their
   // own; a slot is refilled only after the update that read it
@@ -509,9 +512,10 @@ odmd_status build_update_graph(odmd_t h, int par, int prof) {
 // Write the column appended by the last update if the next tall pass has not yet done
 // so (the kernel returns at once when nothing is pending).
 odmd_status flush_pending(odmd_t h) {
-  if (h->nsnap < 2) return ODMD_OK;
+  if (h->nsnap < 2 || !h->maybe_pend) return ODMD_OK;
   ProfScope ps(h, ODMD_K_PASS_B, 1);
   CK(h, launch_flush(h->ws, h->stream), "flush launch");
+  h->maybe_pend = false;
   return ODMD_OK;
 }
 
@@ -595,6 +599,7 @@ odmd_status odmd_create(const odmd_config* cfg, void* workspace_dev, size_t byte
   h->cur_h = 0;
   h->curc_h = 0;
   h->eig_dirty = true;
+  h->maybe_pend = true;
   h->prof_on = false;
   for (int i = 0; i < ODMD_K_COUNT; ++i) {
     h->prof_ms[i] = 0.0;
@@ -738,6 +743,7 @@ odmd_status odmd_update(odmd_t h, const void* x_dev) {
   h->curc_h ^= 1;
   h->nsnap += 1;
   h->eig_dirty = true;
+  h->maybe_pend = true;
   // periodic orthogonality refinement, every refine_every snapshot pairs
   if (h->cfg.refine_every > 0 && (h->nsnap - 1) % h->cfg.refine_every == 0) return odmd_refine(h);
   return ODMD_OK;
@@ -753,7 +759,14 @@ odmd_status odmd_predict(odmd_t h, const double* t_host, int32_t k, void* out_de
   const bool by_powers = integer_horizons(t_host, k);
   if (!by_powers)
     if (odmd_status s = ensure_eig(h)) return s;
-  if (odmd_status s = flush_pending(h)) return s;
+  // the tensor-core rollout forms a pending basis column itself; the other form reads L0
+  // as it is, so the column is written first
+  const bool tc_first = k > 0 && h->use_tc && split_rollout_ok(h->ws, k < kRollK ? k : kRollK);
+  if (!tc_first) {
+    if (odmd_status s = flush_pending(h)) return s;
+  } else {
+    h->maybe_pend = false;  // the first launch below writes the column
+  }
   const size_t vs = (size_t)vsz_of(h->cfg.prec);
   for (int j0 = 0; j0 < k; j0 += kRollK) {
     const int kk = (k - j0) < kRollK ? (k - j0) : kRollK;
@@ -812,6 +825,7 @@ odmd_status odmd_refine(odmd_t h) {
   }
   h->cur_h ^= 1;
   h->eig_dirty = true;
+  h->maybe_pend = true;
   return ODMD_OK;
 }
 
@@ -981,6 +995,7 @@ odmd_status odmd_load(odmd_t h, const void* host_buf, size_t bytes) {
   h->cur_h = hd.cur_h;
   h->curc_h = hd.curc_h;
   h->eig_dirty = true;
+  h->maybe_pend = true;
   return ODMD_OK;
 }
 
@@ -1397,6 +1412,7 @@ odmd_status run_batch(const std::vector<odmd_t>& hs, const std::vector<const voi
     h->curc_h ^= 1;
     h->nsnap += 1;
     h->eig_dirty = true;
+    h->maybe_pend = true;
   }
   if (tuning) {
     // the tuning calls wait for their own step to time it (the first calls of a plan only)

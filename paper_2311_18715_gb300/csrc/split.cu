@@ -143,7 +143,9 @@ __device__ __forceinline__ void issue_tile(const Ws& ws, unsigned char* stage, i
   if (with_e) bulk_g2s(stage + (size_t)2 * kTM * rs, ws.ebuf + row0, (uint32_t)(rows * 8), bar);
 }
 
-// COMPACT = false: X[:, j] = L0[:, :r0] coef[:, j] for j < kcols, X column-major doubles.
+// COMPACT = false: X[:, j] = L0[:, :r0] coef[:, j] for j < kcols, X column-major doubles;
+// a pending basis column (its residual stored by the last update) is formed on the way and
+// written to L0, so no separate pass over the basis is needed before a prediction.
 // COMPACT = true: when the update in flight compacts, L0[:, :rnew] <- [L0[:, :r0] j0] Q_B in
 // place (the tile's rows are staged before they are overwritten, by the CTA that read them).
 template <bool COMPACT>
@@ -155,9 +157,11 @@ __device__ __forceinline__ void split_body(const Ws& ws, CtaPos cp, int kcols, d
   extern __shared__ __align__(1024) unsigned char sp[];
   Ctl* ctl = ws.ctl;
   const int qld = ws.cap + 1;
-  // K: columns of the tall operand (j0 last when appended), J: output columns
+  // K: columns of the tall operand (j0 last when appended, or the pending column of a
+  // rollout), J: output columns; r0 of them come from the staged rows
   int r0, K, J, append = 0;
   const float2* bsrc;  // the small operand, column j at bsrc + j qld
+  const StateBuf st = ws.st[ctl->cur];
   if constexpr (COMPACT) {
     append = ctl->append;
     r0 = ctl->r0e - append;
@@ -165,8 +169,11 @@ __device__ __forceinline__ void split_body(const Ws& ws, CtaPos cp, int kcols, d
     J = ctl->rnew;
     bsrc = ws.sm.QB;
   } else {
-    r0 = ws.st[ctl->cur].hdr->r0;
-    K = r0;
+    // column r0 - 1 of L0 may still be pending (its residual stored, the column not yet
+    // written): the rollout forms it per row, uses it and writes it back
+    append = st.hdr->pend;
+    K = st.hdr->r0;
+    r0 = K - append;
     J = kcols;
     bsrc = ws.sm.coef;
   }
@@ -186,12 +193,18 @@ __device__ __forceinline__ void split_body(const Ws& ws, CtaPos cp, int kcols, d
   __shared__ __align__(8) uint64_t bar_tma, bar_mma[2], bar_full[2], bar_drain;
   __shared__ volatile int abort_s;
   __shared__ uint32_t tmem_slot;
-  const bool with_e = COMPACT && append;
+  const bool with_e = append != 0;
   dd inv = dd{0.f, 0.f};
   if (with_e) {
-    inv = dd_from_double(1.0 / ctl->rho0);
+    // the new column's coefficients s and 1/rho0: of the update in flight (compaction) or
+    // of the update that left the column pending (rollout)
+    const float2* sco = COMPACT ? ws.sm.red : st.ps;
+    if constexpr (COMPACT)
+      inv = dd_from_double(1.0 / ctl->rho0);
+    else
+      inv = dd{st.hdr->pinv.x, st.hdr->pinv.y};
     for (int k = tid; k < kMaxK; k += kThreadsS) {
-      const float2 v = k < r0 ? ws.sm.red[k] : make_float2(0.f, 0.f);
+      const float2 v = k < r0 ? sco[k] : make_float2(0.f, 0.f);
       sh_s[k] = v.x;
       sl_s[k] = v.y;
     }
@@ -347,6 +360,11 @@ __device__ __forceinline__ void split_body(const Ws& ws, CtaPos cp, int kcols, d
           j = acc_norm(j);
           jh[row] = live ? j.h : 0.f;
           jl[row] = live ? j.l : 0.f;
+          if (!COMPACT && live) {  // the pending column, as stored
+            const size_t o = (size_t)(row0 + row) * ws.ldg + r0;
+            reinterpret_cast<float*>(ws.Lh)[o] = j.h;
+            ws.Ll[o] = j.l;
+          }
         }
         __syncwarp();
       }
@@ -518,6 +536,18 @@ __device__ __forceinline__ void split_body(const Ws& ws, CtaPos cp, int kcols, d
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+  if (!COMPACT && with_e) {
+    // the last CTA to finish (every CTA read the flag at its start) marks the column written
+    __shared__ unsigned ticket;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) ticket = atomicAdd(&ctl->ticket_b, 1u);
+    __syncthreads();
+    if (tid == 0 && ticket == (unsigned)(G - 1)) {
+      st.hdr->pend = 0;
+      ctl->ticket_b = 0u;
+    }
+  }
 }
 
 template <bool COMPACT>

@@ -83,6 +83,42 @@ def test_tensor_core_rollout_full_size_benchmark_horizons():
     assert np.max(_rel(got, base)) < 1e-12
 
 
+def test_tensor_core_rollout_forms_the_pending_column():
+    """Predictions straight after updates that appended a basis column: the tensor-core
+    rollout forms that column from the stored residual, uses it and writes it to the basis.
+    Handle a predicts after every update; its twin b has the column written by the separate
+    flush pass (save() flushes) and its states come from a CUDA-core handle loaded from it.
+    States within 1e-12 of b's and 1e-9 of the oracle's at 8, 50 and 65 horizons (65: the
+    second launch, on the CUDA cores, reads the column the first one wrote); afterwards the
+    bases agree to 1e-12 (a column left unwritten would not) and both handles go on alike."""
+    import paper_2311_18715_gb300 as pkg
+
+    X = WakeField(128, 64, sigma=1e-6, seed=2).snapshots(0, 160)
+    n = X.shape[1]
+    a = pkg.OnlineDMD(n, 40, slack=16)
+    b = pkg.OnlineDMD(n, 40, slack=16)
+    o = OnlineDMDRef(n, 40, 1e-10)
+    Xd = torch.from_numpy(X).cuda()
+    for k in range(X.shape[0]):
+        a.update(Xd[k])
+        b.update(Xd[k])
+        o.update(X[k])
+        if k >= 138:
+            nh = (8, 50, 65)[k % 3]
+            ts = [float(k - 2 + h) for h in range(nh)]
+            got = a.predict(ts).cpu().numpy()
+            base = _same_state_cuda_cores(b).predict(ts).cpu().numpy()
+            want = o.predict(ts).T
+            assert np.max(_rel(got, base)) < 1e-12, (k, nh, np.max(_rel(got, base)))
+            assert np.max(_rel(got, want)) < 1e-9, (k, nh, np.max(_rel(got, want)))
+            La, Lb = a.basis().cpu().numpy(), b.basis().cpu().numpy()
+            assert La.shape == Lb.shape
+            assert np.max(np.abs(La - Lb)) < 1e-12, (k, np.max(np.abs(La - Lb)))
+    assert a.counts() == b.counts()
+    Sa, Sb = np.array(a.singular_values()), np.array(b.singular_values())
+    assert np.max(np.abs(Sa - Sb)) <= 1e-12 * Sb[0]
+
+
 @pytest.mark.parametrize("slack,n", [(2, 4096), (5, 100003)])
 def test_tensor_core_compaction_against_cuda_cores_and_oracle(slack, n):
     # rank cap = the planted rank: every snapshot's noise (std 1e-8) adds a direction that the
