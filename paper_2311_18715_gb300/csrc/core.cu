@@ -35,6 +35,10 @@ __device__ __forceinline__ double group4_sum_d(double a) {
   a += __shfl_xor_sync(0xffffffffu, a, 1);
   return a + __shfl_xor_sync(0xffffffffu, a, 2);
 }
+// the binary exponent of |v| from its bits (zero and subnormals give -1023)
+__device__ __forceinline__ int dexp(double v) {
+  return (int)((__double_as_longlong(v) >> 52) & 0x7FF) - 1023;
+}
 // nonnegative doubles order like their bit patterns read as integers
 __device__ __forceinline__ long long ord_key(double v) { return __double_as_longlong(v); }
 
@@ -50,6 +54,40 @@ __device__ __forceinline__ void stage_doubles(double* dst, const double* src, in
   for (int i = tid; i < n; i += nthreads) cp_async8(dst + i, src + i);
 }
 
+// Staging of the larger arrays by the bulk copy engine: one thread issues one copy per
+// array, completing on an mbarrier, instead of every thread issuing 8-byte copies.  A bulk
+// copy moves whole 16-byte units between 16-byte aligned addresses, so an array's shared
+// copy starts at the same address modulo 16 as its source (bulk_dst: a 16-byte aligned
+// region one double longer than the array), and a first or last double outside the
+// aligned body is copied by a plain load (bulk_ends).
+struct BulkSpan {
+  int head, body;  // doubles: the unaligned first one (0 or 1), then an even count
+};
+__device__ __forceinline__ BulkSpan bulk_span(const double* src, int n) {
+  const int h = (n > 0 && (reinterpret_cast<uintptr_t>(src) & 8u)) ? 1 : 0;
+  return BulkSpan{h, (n - h) & ~1};
+}
+__device__ __forceinline__ double* bulk_dst(double* region, const double* src) {
+  return region + ((reinterpret_cast<uintptr_t>(src) & 8u) ? 1 : 0);
+}
+__device__ __forceinline__ void bulk_issue(double* dst, const double* src, BulkSpan sp, uint64_t* bar) {
+  if (sp.body > 0) bulk_g2s(dst + sp.head, src + sp.head, 8u * (uint32_t)sp.body, bar);
+}
+__device__ __forceinline__ void bulk_ends(double* dst, const double* src, int n) {
+  const BulkSpan sp = bulk_span(src, n);
+  if (sp.head) dst[0] = src[0];
+  if (n - sp.head - sp.body == 1) dst[n - 1] = src[n - 1];
+}
+// every thread: the copies on bar have landed (bounded; on a timeout the status is set, and
+// the copies still in flight get a last bounded wait before the block may go on and exit)
+__device__ __forceinline__ void bulk_wait(uint64_t* bar, int* status) {
+  if (!mbar_wait(bar, 0u, status)) {
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, 0u) && global_ns() - t0 < 1000000000ull) {
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // k_prep
 // ---------------------------------------------------------------------------------------
@@ -63,8 +101,8 @@ __device__ __forceinline__ void prep_body(const Ws& ws, CtaPos cp) {
   const int cur = ctl->cur;
   const StateBuf st = ws.st[cur];
   const int r = st.hdr->r, r0 = st.hdr->r0, qld = ws.cap + 1;
-  double* sQ = psm;  // r columns of Q, ld qld
-  double* ac = sQ + (size_t)qld * kMaxR;
+  double* sQ = bulk_dst(psm, st.Q);  // r columns of Q, ld qld (bulk-copied, region qld kMaxR + 2)
+  double* ac = psm + (size_t)qld * kMaxR + 2;
   double* yx = ac + qld;
   double* z = yx + qld;
   double* p = z + qld;
@@ -72,21 +110,33 @@ __device__ __forceinline__ void prep_body(const Ws& ws, CtaPos cp) {
   __shared__ double red8[16];
   __shared__ double thr_s;
   __shared__ int append_s;
-  __shared__ double dsc[kMaxN], zsc[kMaxN];
+  __shared__ double dsc[kMaxN], zsc[kMaxN], sS[kMaxN];
   __shared__ int defl[kMaxN];
+  __shared__ __align__(8) uint64_t sbar;
   const float2* red = ws.sm.red;
 
-  stage_doubles(sQ, st.Q, r * qld, tid, kPrepThreads);
+  if (tid == 0) {
+    mbar_init(&sbar, 1);
+    mbar_fence_init();
+    const BulkSpan sp = bulk_span(st.Q, r * qld);
+    mbar_arrive_expect_tx(&sbar, 8u * (uint32_t)sp.body);
+    bulk_issue(sQ, st.Q, sp, &sbar);
+  }
+  if (tid == 32) bulk_ends(sQ, st.Q, r * qld);
+  stage_doubles(sS, st.S, r, tid, kPrepThreads);
   for (int i = tid; i < r0; i += kPrepThreads) {
     ac[i] = dd2d(st.a[i]) + dd2d(red[i]);
     yx[i] = dd2d(red[r0 + i]);
   }
   cp_async_wait_all();
   __syncthreads();
+  bulk_wait(&sbar, &ctl->status);
   // p = Q^T ac and w = Q^T y (4 threads per column j < r; Q has r0 rows, the appended
   // coordinate lies outside span(L)); a warp without column work meanwhile decides whether
   // the residual is appended (rho0 against the truncation threshold)
-  {
+  // (FP64 instructions cost the SM's FP64 pipe whether or not a lane has work, so warps
+  // with no column or row skip each phase as a whole)
+  if (8 * warp < r) {
     const int j = tid >> 2, sub = tid & 3;
     double ap = 0.0, aw = 0.0;
     if (j < r)
@@ -121,7 +171,7 @@ __device__ __forceinline__ void prep_body(const Ws& ws, CtaPos cp) {
       const double irho0 = e2 > 0.0 ? rsqrt(e2) : 0.0;
       const double rho0 = e2 * irho0;
       const double cn = sqrt(dd2d(st.hdr->cn2));
-      const double sig1 = r > 0 ? st.S[0] : 0.0;
+      const double sig1 = r > 0 ? sS[0] : 0.0;
       const double thr = ws.tau * fmax(sig1, cn);
       const int append = rho0 > thr ? 1 : 0;
       ctl->thr = thr;
@@ -142,6 +192,7 @@ __device__ __forceinline__ void prep_body(const Ws& ws, CtaPos cp) {
   const double thr = thr_s;
   // z = ac - Q p (rows < r0; the appended coordinate is ac itself)
   for (int base = 0; base < 4 * r0e; base += kPrepThreads) {
+    if (base + 32 * warp >= 4 * r0e) continue;
     const int i = (base + tid) >> 2, sub = tid & 3;
     double acc = 0.0;
     if (i < r0)
@@ -151,7 +202,7 @@ __device__ __forceinline__ void prep_body(const Ws& ws, CtaPos cp) {
   }
   __syncthreads();
   // second Gram-Schmidt pass in the small space: p2 = Q^T z, z -= Q p2, p += p2
-  {
+  if (8 * warp < r) {
     const int j = tid >> 2, sub = tid & 3;
     double acc = 0.0;
     if (j < r)
@@ -161,6 +212,7 @@ __device__ __forceinline__ void prep_body(const Ws& ws, CtaPos cp) {
   }
   __syncthreads();
   for (int base = 0; base < 4 * r0; base += kPrepThreads) {
+    if (base + 32 * warp >= 4 * r0) continue;
     const int i = (base + tid) >> 2, sub = tid & 3;
     double acc = 0.0;
     if (i < r0)
@@ -175,14 +227,17 @@ __device__ __forceinline__ void prep_body(const Ws& ws, CtaPos cp) {
   __syncthreads();
   // ||z||^2 and z . y in one block reduction; rho = ||z||, gamma = q_n . y = (z . y) / rho
   double zz = 0.0, zy = 0.0;
-  for (int i = tid; i < r0e; i += kPrepThreads) {
-    zz = fma(z[i], z[i], zz);
-    zy = fma(z[i], yx[i], zy);
+  const int zw = (r0e + 31) >> 5;  // warps holding entries of z (r0e <= cap + 1 <= 256)
+  if (warp < zw) {
+    for (int i = tid; i < r0e; i += kPrepThreads) {
+      zz = fma(z[i], z[i], zz);
+      zy = fma(z[i], yx[i], zy);
+    }
+    zz = warp_sum_d(zz);
+    zy = warp_sum_d(zy);
   }
-  zz = warp_sum_d(zz);
-  zy = warp_sum_d(zy);
   if (lane == 0) {
-    red8[warp] = zz;
+    red8[warp] = zz;  // zero for the warps without entries
     red8[8 + warp] = zy;
   }
   __syncthreads();
@@ -223,7 +278,7 @@ __device__ __forceinline__ void prep_body(const Ws& ws, CtaPos cp) {
     long long mb = 0;
     for (int i = lane; i < n; i += 32) {
       mb = max(mb, __double_as_longlong(i < r ? p[i] : rho) & 0x7FFFFFFFFFFFFFFFll);
-      if (i == 0 && r > 0) mb = max(mb, __double_as_longlong(st.S[0]) & 0x7FFFFFFFFFFFFFFFll);
+      if (i == 0 && r > 0) mb = max(mb, __double_as_longlong(sS[0]) & 0x7FFFFFFFFFFFFFFFll);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
@@ -239,7 +294,7 @@ __device__ __forceinline__ void prep_body(const Ws& ws, CtaPos cp) {
     // scaling is one exact product
     const double pw = __longlong_as_double((long long)(1023 - e) << 52);
     for (int i = lane; i < n; i += 32) {
-      const double di = i < r ? st.S[i] * pw : 0.0;
+      const double di = i < r ? sS[i] * pw : 0.0;
       const double zi = (i < r ? p[i] : rho) * pw;
       dsc[i] = di;
       const bool small = !(fabs(zi) > tol);
@@ -360,14 +415,13 @@ __device__ __forceinline__ void roots_body(const Ws& ws, CtaPos cp) {
   const double* d = ws.sm.d;
   const double* z = ws.sm.z;
   const int tid = threadIdx.x, lane = tid & 31;
-  __shared__ float df[kMaxN], zf[kMaxN];
+  __shared__ float zf[kMaxN];
   __shared__ float partf[2][kRootThreads / 32 * 3];
   __shared__ double part64[2][kRootThreads / 32];
   const bool mine = tid < m;
   const double di = mine ? d[tid] : 0.0, zi = mine ? z[tid] : 0.0;
   const float zif = __double2float_rn(zi);
   if (mine) {
-    df[tid] = __double2float_rn(di);
     zf[tid] = zif;
   }
   if (m == 1) {
@@ -428,10 +482,15 @@ __device__ __forceinline__ void roots_body(const Ws& ws, CtaPos cp) {
     B = 0.0;
   }
   const double dob = d[o];
+  // d_i^2 - d_o^2 in FP64 (the difference of two nearby squares would lose the leading bits
+  // in FP32), rounded to FP32 for stage 1
+  const double ddo = mine ? (di - dob) * (di + dob) : 0.0;
+  __shared__ float ddf[kMaxN];
+  if (mine) ddf[tid] = __double2float_rn(ddo);
+  __syncthreads();
   // ---- stage 1, FP32: locate the root to ~1e-7 relative (every warp the same way)
   double mu = 0.5 * (lo + hi);
   {
-    const float dof = df[o];
     const float Af = (float)A, Bf = (float)B;
     float lof = (float)lo, hif = (float)hi, muf = (float)mu;
     for (int it = 0; it < 40; ++it) {
@@ -440,8 +499,8 @@ __device__ __forceinline__ void roots_body(const Ws& ws, CtaPos cp) {
       for (int q_ = 0; q_ < (kMaxN + 31) / 32; ++q_) {
         const int i = lane + 32 * q_;
         if (i >= m) break;
-        const float dv = df[i], zv = zf[i];
-        const float del = (dv - dof) * (dv + dof) - muf;
+        const float zv = zf[i];
+        const float del = ddf[i] - muf;
         const float t = zv / del;
         if (i <= j) {
           psi = fmaf(zv, t, psi);
@@ -500,10 +559,10 @@ __device__ __forceinline__ void roots_body(const Ws& ws, CtaPos cp) {
   // steers the iteration is summed in FP32: the derivatives psi', phi' of the model step and
   // |psi| + |phi| = sum |z_i^2 / (d_i^2 - lambda)| of the stopping test (the terms of psi are
   // negative and those of phi positive inside the bracket)
-  const double ddo = mine ? (di - dob) * (di + dob) : 0.0;  // d_i^2 - d_o^2
   __shared__ double mu_s;
   __shared__ int done_s;
   bool conv = false;
+  double prev_step = 0.0;  // thread 0: the previous FP64 step (none yet: the test below fails)
   for (int it = 0; it < 100; ++it) {
     double term = 0.0;
     float v[3] = {0.f, 0.f, 0.f};  // sum |term|, psi', phi'
@@ -518,11 +577,13 @@ __device__ __forceinline__ void roots_body(const Ws& ws, CtaPos cp) {
     // iterations so a fast thread cannot overwrite partials another is still reading
     const int pb = it_total & 1;
     ++it_total;
-    term = warp_sum_d(term);
+    if (32 * (tid >> 5) < m) {  // warps without poles hold zeros: no sums there
+      term = warp_sum_d(term);
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
+      for (int k = 0; k < 3; ++k)
 #pragma unroll
-      for (int o2 = 16; o2 > 0; o2 >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o2);
+        for (int o2 = 16; o2 > 0; o2 >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o2);
+    }
     if (lane == 0) {
       part64[pb][tid >> 5] = term;
 #pragma unroll
@@ -581,6 +642,15 @@ __device__ __forceinline__ void roots_body(const Ws& ws, CtaPos cp) {
         const double step = fabs(x - mu);
         mu = x;
         if (step <= 4.0 * kEps64 * fabs(mu) || hi - lo <= 4.0 * kEps64 * fmax(fabs(lo), fabs(hi))) stop = 1;
+        // the model step converges quadratically: with steps s1 then s2 the constant is about
+        // s2 / s1^2, so the error left after s2 is about s2^3 / s1^2.  Once that lies below
+        // 2^-60 |mu| (and s2 itself below 2^-26 |mu|, inside the quadratic regime), the next
+        // evaluation of f could only confirm the root: stop here instead of paying for it.
+        // The test runs on the binary exponents (integer operations, off the FP64 pipe):
+        // v in [2^e, 2^(e+1)) bounds s2^3 / s1^2 below 2^(3 e2 + 3 - 2 e1)
+        const int em = dexp(mu), e2 = dexp(step), e1 = dexp(prev_step);
+        if (em > -600 && e2 <= em - 26 && 3 * e2 - 2 * e1 <= em - 63) stop = 1;
+        prev_step = step;
       }
       mu_s = mu;
       done_s = stop;
@@ -810,6 +880,11 @@ __global__ void __launch_bounds__(kVecThreads) k_vectors_batch(const __grid_cons
 //   S' = sigma'[0:rnew] (unscaled);  a' = L0'^T x
 // ---------------------------------------------------------------------------------------
 constexpr int kApplyThreads = 256;
+// shared regions of the bulk-staged arrays of k_apply, in doubles (even: 16-byte aligned)
+constexpr int kApplyRegM = kMaxR * kMaxR + 2;
+constexpr int kApplyRegQ = kMaxR * (kMaxCap + 1) + 2;
+constexpr int kApplyRegU = kMaxR * kMaxN + 2;
+static_assert(kApplyRegM % 2 == 0 && kApplyRegQ % 2 == 0 && kApplyRegU % 2 == 0, "16-byte aligned regions");
 
 __device__ __forceinline__ int count4(int sub, int n) { return n > sub ? (n - sub + 3) >> 2 : 0; }
 
@@ -885,17 +960,41 @@ __device__ void apply_column(const Ws& ws, int j, const StateBuf& st, const Stat
   // their global leading dimensions by asynchronous copies all issued at once, so that the
   // short dependent FMA chains wait on shared memory rather than on L2
   extern __shared__ __align__(16) double asm_[];
-  double* sM = asm_;                                // [k][i], ld rm
-  double* sQ = sM + (size_t)kMaxR * kMaxR;          // [k][i], ld qld
-  double* sU = sQ + (size_t)kMaxR * (kMaxCap + 1);  // [i][k], ld kMaxN
+  // M, Q and U by bulk copies (regions of an even number of doubles, each one longer than
+  // its array); the short vectors by 8-byte asynchronous copies
+  double* sM = bulk_dst(asm_, st.M);                                     // [k][i], ld rm
+  double* sQ = bulk_dst(asm_ + kApplyRegM, st.Q);                        // [k][i], ld qld
+  double* sU = bulk_dst(asm_ + kApplyRegM + kApplyRegQ, ws.sm.U);        // [i][k], ld kMaxN
   __shared__ double v[kMaxN], u[kMaxN], bv[kMaxN], qcol[kMaxCap + 1];
-  stage_doubles(sM, st.M, r * rm, tid, kApplyThreads);
-  stage_doubles(sQ, st.Q, r * qld, tid, kApplyThreads);
-  stage_doubles(sU, ws.sm.U, rnew * kMaxN, tid, kApplyThreads);
+  __shared__ double sw[kMaxN], srl[kMaxN], srf[kMaxN], sqn[kMaxCap + 1], syx[kMaxCap + 1];
+  __shared__ __align__(8) uint64_t sbar;
+  const int nM = r * rm, nQ = r * qld, nU = rnew * kMaxN;
+  if (tid == 0) {
+    mbar_init(&sbar, 1);
+    mbar_fence_init();
+    const BulkSpan a = bulk_span(st.M, nM), b = bulk_span(st.Q, nQ), c = bulk_span(ws.sm.U, nU);
+    mbar_arrive_expect_tx(&sbar, 8u * (uint32_t)(a.body + b.body + c.body));
+    bulk_issue(sM, st.M, a, &sbar);
+    bulk_issue(sQ, st.Q, b, &sbar);
+    bulk_issue(sU, ws.sm.U, c, &sbar);
+  }
+  if (tid == 32) bulk_ends(sM, st.M, nM);
+  if (tid == 64) bulk_ends(sQ, st.Q, nQ);
+  if (tid == 96) bulk_ends(sU, ws.sm.U, nU);
   stage_doubles(v, ws.sm.V + (size_t)j * kMaxN, n, tid, kApplyThreads);
   stage_doubles(u, ws.sm.U + (size_t)j * kMaxN, n, tid, kApplyThreads);
+  stage_doubles(sw, ws.sm.w, r, tid, kApplyThreads);
+  stage_doubles(srl, st.rl, r, tid, kApplyThreads);
+  stage_doubles(srf, st.rf, r, tid, kApplyThreads);
+  stage_doubles(sqn, ws.sm.qn, r0e, tid, kApplyThreads);
+  if (compact) stage_doubles(syx, ws.sm.yext, r0e, tid, kApplyThreads);
+  // scalars read by the tail of warp 0, loaded before the waits
+  const int pairs = st.hdr->pairs;
+  const int sexp = ctl->scale_exp;
+  const double sigj = ws.sm.sig[kMaxN + j];
   cp_async_wait_all();
   __syncthreads();
+  bulk_wait(&sbar, &ctl->status);
   // B v, rows 0..r-1: M v[0:r] + w v_r  (4 threads per row; r <= 64 rows)
   {
     const int i = tid >> 2, sub = tid & 3;
@@ -903,13 +1002,13 @@ __device__ void apply_column(const Ws& ws, int j, const StateBuf& st, const Stat
     if (i < r)
       for (int k = sub; k < r; k += 4) acc = fma(sM[(size_t)k * rm + i], v[k], acc);
     acc = group4_sum_d(acc);
-    if (i < r && sub == 0) bv[i] = fma(ws.sm.w[i], v[r], acc);
+    if (i < r && sub == 0) bv[i] = fma(sw[i], v[r], acc);
   }
   // row r: rho (r_last . v[0:r]) + gamma v_r   (warp 7, which writes it itself)
   if ((tid >> 5) == 7) {
     const int lane = tid & 31;
     double t = 0.0;
-    for (int k = lane; k < r; k += 32) t = fma(st.rl[k], v[k], t);
+    for (int k = lane; k < r; k += 32) t = fma(srl[k], v[k], t);
     t = warp_sum_d(t);
     if (lane == 0) bv[r] = fma(rho, t, gamma * v[r]);
   }
@@ -920,7 +1019,7 @@ __device__ void apply_column(const Ws& ws, int j, const StateBuf& st, const Stat
     if (i < r0)
       for (int k = sub; k < r; k += 4) acc = fma(sQ[(size_t)k * qld + i], u[k], acc);
     acc = group4_sum_d(acc);
-    if (i < r0e && sub == 0) qcol[i] = fma(ws.sm.qn[i], u[r], acc);
+    if (i < r0e && sub == 0) qcol[i] = fma(sqn[i], u[r], acc);
   }
   __syncthreads();
   // M' column j: U'^T (B v)   (4 threads per output row i < rnew)
@@ -943,17 +1042,19 @@ __device__ void apply_column(const Ws& ws, int j, const StateBuf& st, const Stat
   if (tid < 32) {
     const int lane = tid;
     double rf = 0.0;
-    if (st.hdr->pairs != 0)
-      for (int k = lane; k < r; k += 32) rf = fma(st.rf[k], v[k], rf);
-    rf = warp_sum_d(rf);
+    if (pairs != 0) {
+      for (int k = lane; k < r; k += 32) rf = fma(srf[k], v[k], rf);
+      rf = warp_sum_d(rf);
+    }
     double a = 0.0;
-    if (compact)
-      for (int i = lane; i < r0e; i += 32) a = fma(qcol[i], ws.sm.yext[i], a);
-    a = warp_sum_d(a);
+    if (compact) {
+      for (int i = lane; i < r0e; i += 32) a = fma(qcol[i], syx[i], a);
+      a = warp_sum_d(a);
+    }
     if (lane == 0) {
-      nx.rf[j] = st.hdr->pairs == 0 ? v[r] : rf;
+      nx.rf[j] = pairs == 0 ? v[r] : rf;
       nx.rl[j] = v[r];
-      nx.S[j] = ws.sm.sig[kMaxN + j] * __longlong_as_double((long long)(1023 + ctl->scale_exp) << 52);
+      nx.S[j] = sigj * __longlong_as_double((long long)(1023 + sexp) << 52);
       if (compact) nx.a[j] = d2f2(a);
     }
   }
@@ -961,12 +1062,12 @@ __device__ void apply_column(const Ws& ws, int j, const StateBuf& st, const Stat
 
 // ---------------------------------------------------------------------------------------
 static int prep_smem_cap(int cap) {
-  const int qld = cap + 1;
-  return (int)sizeof(double) * (qld * kMaxR + 3 * qld + 2 * kMaxN);
+  const int qld = cap + 1;  // Q's region (bulk-copied: one double longer, kept even), then ac, yx, z, p, p2
+  return (int)sizeof(double) * (qld * kMaxR + 2 + 3 * qld + 2 * kMaxN);
 }
 
-// staged M, Q and U of k_apply (largest sizes)
-constexpr int kApplySmem = (int)sizeof(double) * (kMaxR * kMaxR + kMaxR * (kMaxCap + 1) + kMaxR * kMaxN);
+// staged M, Q and U of k_apply (largest sizes, each region one double longer, kept even)
+constexpr int kApplySmem = (int)sizeof(double) * (kApplyRegM + kApplyRegQ + kApplyRegU);
 
 cudaError_t prepare_core() {
   cudaError_t e = cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, prep_smem_cap(kMaxCap));
