@@ -297,7 +297,7 @@ def run_ours(args) -> None:
     gen = WakeField(NX, NY, sigma=SIGMA, seed=rank)
     K, W = args.steps, args.warmup
     n_dev = PRETRAIN + (W + 2 * K) * BLOCK + 1  # warm-up, the timed steps, the profiled steps
-    n_e2e = K * BLOCK + 1
+    n_e2e = (W + K) * BLOCK + 1  # end-to-end: W warm-up steps, then the K timed ones
     host = np.empty((n_dev + n_e2e, N), dtype=np.float64)
     for k in range(n_dev + n_e2e):
         host[k] = gen.snapshot(k)
@@ -431,11 +431,10 @@ def run_ours(args) -> None:
     outs_h = [torch.empty((BLOCK, N), dtype=torch.float64).pin_memory() for _ in range(2)]
     d2h = torch.cuda.Stream(dev)
     done = [torch.cuda.Event(), torch.cuda.Event()]
-    torch.cuda.synchronize()
-    barrier(dist)
-    t0 = time.perf_counter()
     ke = 0
-    for blk in range(K):
+
+    def e2e_step(blk: int) -> None:
+        nonlocal ke, k
         b = blk & 1
         with torch.cuda.stream(stream):
             # the block's snapshots straight from pinned host memory through the C ABI
@@ -444,13 +443,23 @@ def run_ours(args) -> None:
             ke += BLOCK
             stream.wait_event(done[b])  # the read-back of this buffer two blocks ago is over
             model.predict([float(k + h) for h in range(BLOCK)], out=outs[b])
+            # the check's FOM state first: its small copy would otherwise queue behind the
+            # states' read-back
+            x_stage.copy_(Xh[ke], non_blocking=True)
+            model.check(float(k + BLOCK), x_stage)
             d2h.wait_stream(stream)
             with torch.cuda.stream(d2h):
                 outs_h[b].copy_(outs[b], non_blocking=True)
                 done[b].record(d2h)
-            x_stage.copy_(Xh[ke], non_blocking=True)
-            model.check(float(k + BLOCK), x_stage)
         k += BLOCK
+
+    for blk in range(W):  # untimed: the first host-fed calls and graph launches
+        e2e_step(blk)
+    torch.cuda.synchronize()
+    barrier(dist)
+    t0 = time.perf_counter()
+    for blk in range(K):
+        e2e_step(W + blk)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
     barrier(dist)

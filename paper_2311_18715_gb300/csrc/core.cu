@@ -94,7 +94,6 @@ __device__ __forceinline__ void bulk_wait(uint64_t* bar, int* status) {
 constexpr int kPrepThreads = 256;
 
 __device__ __forceinline__ void prep_body(const Ws& ws, CtaPos cp) {
-  pdl_wait();
   extern __shared__ __align__(16) double psm[];
   Ctl* ctl = ws.ctl;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -124,6 +123,10 @@ __device__ __forceinline__ void prep_body(const Ws& ws, CtaPos cp) {
   }
   if (tid == 32) bulk_ends(sQ, st.Q, r * qld);
   stage_doubles(sS, st.S, r, tid, kPrepThreads);
+  // Until here only the committed state is read (written by the last kernel of the previous
+  // update, which completed before pass A started), so its copies run during the wait for
+  // pass A; the reduced sums of pass A are read after it
+  pdl_wait();
   for (int i = tid; i < r0; i += kPrepThreads) {
     ac[i] = dd2d(st.a[i]) + dd2d(red[i]);
     yx[i] = dd2d(red[r0 + i]);
@@ -888,15 +891,14 @@ static_assert(kApplyRegM % 2 == 0 && kApplyRegQ % 2 == 0 && kApplyRegU % 2 == 0,
 
 __device__ __forceinline__ int count4(int sub, int n) { return n > sub ? (n - sub + 3) >> 2 : 0; }
 
-__device__ void apply_column(const Ws& ws, int j, const StateBuf& st, const StateBuf& nx, int r, int r0, int r0e,
-                             bool compact);
-
 __device__ __forceinline__ void apply_body(const Ws& ws, CtaPos cp) {
-  pdl_wait();
   Ctl* ctl = ws.ctl;
   const int j = cp.b;
-  const int rnew = ctl->rnew;
   const int tid = threadIdx.x;
+  // Before the wait on the previous kernel (k_vectors) only what earlier kernels wrote is
+  // read: the committed state, and the scalars and vectors of k_prep and k_zhat.  Nothing
+  // is written before it.
+  const int rnew = ctl->rnew;
   const int cur = ctl->cur;
   const StateBuf st = ws.st[cur], nx = ws.st[cur ^ 1];
   const int r = st.hdr->r, r0 = st.hdr->r0;
@@ -904,6 +906,46 @@ __device__ __forceinline__ void apply_body(const Ws& ws, CtaPos cp) {
   const int cap = ws.cap;
   const bool compact = r0e > cap;
   const int append = ctl->append;
+  const int n = r + 1;
+  const int qld = cap + 1, rm = ws.rmax;
+  const bool mine = j < rnew;  // this CTA forms column j
+  // every product below runs from shared memory: M (r columns, ld rmax), Q (r columns, ld
+  // cap + 1) and the kept left singular vectors U (rnew columns, ld kMaxN) by bulk copies
+  // (regions of an even number of doubles, each one longer than its array), the short
+  // vectors by 8-byte asynchronous copies
+  extern __shared__ __align__(16) double asm_[];
+  double* sM = bulk_dst(asm_, st.M);                               // [k][i], ld rm
+  double* sQ = bulk_dst(asm_ + kApplyRegM, st.Q);                  // [k][i], ld qld
+  double* sU = bulk_dst(asm_ + kApplyRegM + kApplyRegQ, ws.sm.U);  // [i][k], ld kMaxN
+  __shared__ double v[kMaxN], u[kMaxN], bv[kMaxN], qcol[kMaxCap + 1];
+  __shared__ double sw[kMaxN], srl[kMaxN], srf[kMaxN], sqn[kMaxCap + 1], syx[kMaxCap + 1];
+  __shared__ __align__(8) uint64_t sbar;
+  const int nM = r * rm, nQ = r * qld, nU = rnew * kMaxN;
+  int pairs = 0, sexp = 0;
+  double sigj = 0.0, rho = 0.0, gamma = 0.0;
+  if (mine) {
+    if (tid == 0) {
+      mbar_init(&sbar, 1);
+      mbar_fence_init();
+      const BulkSpan a = bulk_span(st.M, nM), b = bulk_span(st.Q, nQ), c = bulk_span(ws.sm.U, nU);
+      mbar_arrive_expect_tx(&sbar, 8u * (uint32_t)(a.body + b.body + c.body));  // U joins after the wait
+      bulk_issue(sM, st.M, a, &sbar);
+      bulk_issue(sQ, st.Q, b, &sbar);
+    }
+    if (tid == 32) bulk_ends(sM, st.M, nM);
+    if (tid == 64) bulk_ends(sQ, st.Q, nQ);
+    stage_doubles(sw, ws.sm.w, r, tid, kApplyThreads);
+    stage_doubles(srl, st.rl, r, tid, kApplyThreads);
+    stage_doubles(srf, st.rf, r, tid, kApplyThreads);
+    stage_doubles(sqn, ws.sm.qn, r0e, tid, kApplyThreads);
+    if (compact) stage_doubles(syx, ws.sm.yext, r0e, tid, kApplyThreads);
+    pairs = st.hdr->pairs;
+    sexp = ctl->scale_exp;
+    sigj = ws.sm.sig[kMaxN + j];
+    rho = ctl->rho;
+    gamma = ctl->gamma;
+  }
+  pdl_wait();
   if (j == 0 && tid == 0) {
     nx.hdr->r = rnew;
     nx.hdr->r0 = compact ? rnew : r0e;
@@ -921,7 +963,78 @@ __device__ __forceinline__ void apply_body(const Ws& ws, CtaPos cp) {
     if (append && !compact)
       for (int i = tid; i < r0; i += kApplyThreads) nx.ps[i] = ws.sm.red[i];
   }
-  if (j < rnew) apply_column(ws, j, st, nx, r, r0, r0e, compact);
+  if (mine) {
+    // the singular vectors of k_vectors
+    if (tid == 0) bulk_issue(sU, ws.sm.U, bulk_span(ws.sm.U, nU), &sbar);
+    if (tid == 96) bulk_ends(sU, ws.sm.U, nU);
+    stage_doubles(v, ws.sm.V + (size_t)j * kMaxN, n, tid, kApplyThreads);
+    stage_doubles(u, ws.sm.U + (size_t)j * kMaxN, n, tid, kApplyThreads);
+    cp_async_wait_all();
+    __syncthreads();
+    bulk_wait(&sbar, &ctl->status);
+    // B v, rows 0..r-1: M v[0:r] + w v_r  (4 threads per row; r <= 64 rows)
+    {
+      const int i = tid >> 2, sub = tid & 3;
+      double acc = 0.0;
+      if (i < r)
+        for (int k = sub; k < r; k += 4) acc = fma(sM[(size_t)k * rm + i], v[k], acc);
+      acc = group4_sum_d(acc);
+      if (i < r && sub == 0) bv[i] = fma(sw[i], v[r], acc);
+    }
+    // row r: rho (r_last . v[0:r]) + gamma v_r   (warp 7, which writes it itself)
+    if ((tid >> 5) == 7) {
+      const int lane = tid & 31;
+      double t = 0.0;
+      for (int k = lane; k < r; k += 32) t = fma(srl[k], v[k], t);
+      t = warp_sum_d(t);
+      if (lane == 0) bv[r] = fma(rho, t, gamma * v[r]);
+    }
+    // Q' column j (rows 0..r0e-1): Q u[0:r] + qn u_r
+    for (int base = 0; base < 4 * r0e; base += kApplyThreads) {
+      const int i = (base + tid) >> 2, sub = tid & 3;
+      double acc = 0.0;
+      if (i < r0)
+        for (int k = sub; k < r; k += 4) acc = fma(sQ[(size_t)k * qld + i], u[k], acc);
+      acc = group4_sum_d(acc);
+      if (i < r0e && sub == 0) qcol[i] = fma(sqn[i], u[r], acc);
+    }
+    __syncthreads();
+    // M' column j: U'^T (B v)   (4 threads per output row i < rnew)
+    {
+      const int i = tid >> 2, sub = tid & 3;
+      double acc = 0.0;
+      if (i < rnew)
+        for (int k = sub; k < n; k += 4) acc = fma(sU[(size_t)i * kMaxN + k], bv[k], acc);
+      acc = group4_sum_d(acc);
+      if (i < rnew && sub == 0) nx.M[(size_t)j * rm + i] = acc;
+    }
+    if (compact) {
+      for (int i = tid; i < r0e; i += kApplyThreads) ws.sm.QB[(size_t)j * qld + i] = d2f2(qcol[i]);
+      for (int i = tid; i < rnew; i += kApplyThreads) nx.Q[(size_t)j * qld + i] = i == j ? 1.0 : 0.0;
+    } else {
+      for (int i = tid; i < r0e; i += kApplyThreads) nx.Q[(size_t)j * qld + i] = qcol[i];
+    }
+    // r_first', r_last', S', a' (compaction)  -- warp 0
+    if (tid < 32) {
+      const int lane = tid;
+      double rf = 0.0;
+      if (pairs != 0) {
+        for (int k = lane; k < r; k += 32) rf = fma(srf[k], v[k], rf);
+        rf = warp_sum_d(rf);
+      }
+      double a = 0.0;
+      if (compact) {
+        for (int i = lane; i < r0e; i += 32) a = fma(qcol[i], syx[i], a);
+        a = warp_sum_d(a);
+      }
+      if (lane == 0) {
+        nx.rf[j] = pairs == 0 ? v[r] : rf;
+        nx.rl[j] = v[r];
+        nx.S[j] = sigj * __longlong_as_double((long long)(1023 + sexp) << 52);
+        if (compact) nx.a[j] = d2f2(a);
+      }
+    }
+  }
   // the last CTA commits the new state and snapshot buffers
   __shared__ unsigned ticket;
   __threadfence();
@@ -945,119 +1058,6 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(const __grid_constant__
 __global__ void __launch_bounds__(kApplyThreads) k_apply_batch(const __grid_constant__ BatchTab t) {
   const int i = batch_find(t, blockIdx.x);
   apply_body(*t.ws[i], batch_pos(t, i));
-}
-
-
-__device__ void apply_column(const Ws& ws, int j, const StateBuf& st, const StateBuf& nx, int r, int r0, int r0e,
-                             bool compact) {
-  Ctl* ctl = ws.ctl;
-  const int tid = threadIdx.x;
-  const int n = r + 1, rnew = ctl->rnew;
-  const int qld = ws.cap + 1, rm = ws.rmax;
-  const double rho = ctl->rho, gamma = ctl->gamma;
-  // every product below runs from shared memory: M (r columns, ld rmax), Q (r columns, ld
-  // cap + 1) and the kept left singular vectors U (rnew columns, ld kMaxN) are copied in with
-  // their global leading dimensions by asynchronous copies all issued at once, so that the
-  // short dependent FMA chains wait on shared memory rather than on L2
-  extern __shared__ __align__(16) double asm_[];
-  // M, Q and U by bulk copies (regions of an even number of doubles, each one longer than
-  // its array); the short vectors by 8-byte asynchronous copies
-  double* sM = bulk_dst(asm_, st.M);                                     // [k][i], ld rm
-  double* sQ = bulk_dst(asm_ + kApplyRegM, st.Q);                        // [k][i], ld qld
-  double* sU = bulk_dst(asm_ + kApplyRegM + kApplyRegQ, ws.sm.U);        // [i][k], ld kMaxN
-  __shared__ double v[kMaxN], u[kMaxN], bv[kMaxN], qcol[kMaxCap + 1];
-  __shared__ double sw[kMaxN], srl[kMaxN], srf[kMaxN], sqn[kMaxCap + 1], syx[kMaxCap + 1];
-  __shared__ __align__(8) uint64_t sbar;
-  const int nM = r * rm, nQ = r * qld, nU = rnew * kMaxN;
-  if (tid == 0) {
-    mbar_init(&sbar, 1);
-    mbar_fence_init();
-    const BulkSpan a = bulk_span(st.M, nM), b = bulk_span(st.Q, nQ), c = bulk_span(ws.sm.U, nU);
-    mbar_arrive_expect_tx(&sbar, 8u * (uint32_t)(a.body + b.body + c.body));
-    bulk_issue(sM, st.M, a, &sbar);
-    bulk_issue(sQ, st.Q, b, &sbar);
-    bulk_issue(sU, ws.sm.U, c, &sbar);
-  }
-  if (tid == 32) bulk_ends(sM, st.M, nM);
-  if (tid == 64) bulk_ends(sQ, st.Q, nQ);
-  if (tid == 96) bulk_ends(sU, ws.sm.U, nU);
-  stage_doubles(v, ws.sm.V + (size_t)j * kMaxN, n, tid, kApplyThreads);
-  stage_doubles(u, ws.sm.U + (size_t)j * kMaxN, n, tid, kApplyThreads);
-  stage_doubles(sw, ws.sm.w, r, tid, kApplyThreads);
-  stage_doubles(srl, st.rl, r, tid, kApplyThreads);
-  stage_doubles(srf, st.rf, r, tid, kApplyThreads);
-  stage_doubles(sqn, ws.sm.qn, r0e, tid, kApplyThreads);
-  if (compact) stage_doubles(syx, ws.sm.yext, r0e, tid, kApplyThreads);
-  // scalars read by the tail of warp 0, loaded before the waits
-  const int pairs = st.hdr->pairs;
-  const int sexp = ctl->scale_exp;
-  const double sigj = ws.sm.sig[kMaxN + j];
-  cp_async_wait_all();
-  __syncthreads();
-  bulk_wait(&sbar, &ctl->status);
-  // B v, rows 0..r-1: M v[0:r] + w v_r  (4 threads per row; r <= 64 rows)
-  {
-    const int i = tid >> 2, sub = tid & 3;
-    double acc = 0.0;
-    if (i < r)
-      for (int k = sub; k < r; k += 4) acc = fma(sM[(size_t)k * rm + i], v[k], acc);
-    acc = group4_sum_d(acc);
-    if (i < r && sub == 0) bv[i] = fma(sw[i], v[r], acc);
-  }
-  // row r: rho (r_last . v[0:r]) + gamma v_r   (warp 7, which writes it itself)
-  if ((tid >> 5) == 7) {
-    const int lane = tid & 31;
-    double t = 0.0;
-    for (int k = lane; k < r; k += 32) t = fma(srl[k], v[k], t);
-    t = warp_sum_d(t);
-    if (lane == 0) bv[r] = fma(rho, t, gamma * v[r]);
-  }
-  // Q' column j (rows 0..r0e-1): Q u[0:r] + qn u_r
-  for (int base = 0; base < 4 * r0e; base += kApplyThreads) {
-    const int i = (base + tid) >> 2, sub = tid & 3;
-    double acc = 0.0;
-    if (i < r0)
-      for (int k = sub; k < r; k += 4) acc = fma(sQ[(size_t)k * qld + i], u[k], acc);
-    acc = group4_sum_d(acc);
-    if (i < r0e && sub == 0) qcol[i] = fma(sqn[i], u[r], acc);
-  }
-  __syncthreads();
-  // M' column j: U'^T (B v)   (4 threads per output row i < rnew)
-  {
-    const int i = tid >> 2, sub = tid & 3;
-    double acc = 0.0;
-    if (i < rnew)
-      for (int k = sub; k < n; k += 4) acc = fma(sU[(size_t)i * kMaxN + k], bv[k], acc);
-    acc = group4_sum_d(acc);
-    if (i < rnew && sub == 0) nx.M[(size_t)j * rm + i] = acc;
-  }
-  if (compact) {
-    for (int i = tid; i < r0e; i += kApplyThreads) ws.sm.QB[(size_t)j * qld + i] = d2f2(qcol[i]);
-    for (int i = tid; i < rnew; i += kApplyThreads)
-      nx.Q[(size_t)j * qld + i] = i == j ? 1.0 : 0.0;
-  } else {
-    for (int i = tid; i < r0e; i += kApplyThreads) nx.Q[(size_t)j * qld + i] = qcol[i];
-  }
-  // r_first', r_last', S', a' (compaction)  -- warp 0
-  if (tid < 32) {
-    const int lane = tid;
-    double rf = 0.0;
-    if (pairs != 0) {
-      for (int k = lane; k < r; k += 32) rf = fma(srf[k], v[k], rf);
-      rf = warp_sum_d(rf);
-    }
-    double a = 0.0;
-    if (compact) {
-      for (int i = lane; i < r0e; i += 32) a = fma(qcol[i], syx[i], a);
-      a = warp_sum_d(a);
-    }
-    if (lane == 0) {
-      nx.rf[j] = pairs == 0 ? v[r] : rf;
-      nx.rl[j] = v[r];
-      nx.S[j] = sigj * __longlong_as_double((long long)(1023 + sexp) << 52);
-      if (compact) nx.a[j] = d2f2(a);
-    }
-  }
 }
 
 // ---------------------------------------------------------------------------------------
