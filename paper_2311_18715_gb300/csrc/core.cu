@@ -143,6 +143,7 @@ __device__ __forceinline__ void prep_body(const Ws& ws, CtaPos cp) {
     const int j = tid >> 2, sub = tid & 3;
     double ap = 0.0, aw = 0.0;
     if (j < r)
+      #pragma unroll 1  // a dependent chain: unrolling adds code, not speed
       for (int i = sub; i < r0; i += 4) {
         const double q = sQ[(size_t)j * qld + i];
         ap = fma(q, ac[i], ap);
@@ -158,6 +159,7 @@ __device__ __forceinline__ void prep_body(const Ws& ws, CtaPos cp) {
   const int dwarp = 4 * r <= kPrepThreads - 32 ? 7 : 0;
   if (warp == dwarp) {
     double ssq = 0.0, sy = 0.0;
+    #pragma unroll 1  // a dependent chain: unrolling adds code, not speed
     for (int i = lane; i < r0; i += 32) {
       const double si = dd2d(red[i]);
       ssq = fma(si, si, ssq);
@@ -199,6 +201,7 @@ __device__ __forceinline__ void prep_body(const Ws& ws, CtaPos cp) {
     const int i = (base + tid) >> 2, sub = tid & 3;
     double acc = 0.0;
     if (i < r0)
+      #pragma unroll 1  // a dependent chain: unrolling adds code, not speed
       for (int j = sub; j < r; j += 4) acc = fma(sQ[(size_t)j * qld + i], p[j], acc);
     acc = group4_sum_d(acc);
     if (i < r0e && sub == 0) z[i] = i < r0 ? ac[i] - acc : ac[i];
@@ -209,6 +212,7 @@ __device__ __forceinline__ void prep_body(const Ws& ws, CtaPos cp) {
     const int j = tid >> 2, sub = tid & 3;
     double acc = 0.0;
     if (j < r)
+      #pragma unroll 1  // a dependent chain: unrolling adds code, not speed
       for (int i = sub; i < r0; i += 4) acc = fma(sQ[(size_t)j * qld + i], z[i], acc);
     acc = group4_sum_d(acc);
     if (j < r && sub == 0) p2[j] = acc;
@@ -219,6 +223,7 @@ __device__ __forceinline__ void prep_body(const Ws& ws, CtaPos cp) {
     const int i = (base + tid) >> 2, sub = tid & 3;
     double acc = 0.0;
     if (i < r0)
+      #pragma unroll 1  // a dependent chain: unrolling adds code, not speed
       for (int j = sub; j < r; j += 4) acc = fma(sQ[(size_t)j * qld + i], p2[j], acc);
     acc = group4_sum_d(acc);
     if (i < r0 && sub == 0) z[i] -= acc;
@@ -977,6 +982,7 @@ __device__ __forceinline__ void apply_body(const Ws& ws, CtaPos cp) {
       const int i = tid >> 2, sub = tid & 3;
       double acc = 0.0;
       if (i < r)
+        #pragma unroll 1  // a dependent chain: unrolling adds code, not speed
         for (int k = sub; k < r; k += 4) acc = fma(sM[(size_t)k * rm + i], v[k], acc);
       acc = group4_sum_d(acc);
       if (i < r && sub == 0) bv[i] = fma(sw[i], v[r], acc);
@@ -985,6 +991,7 @@ __device__ __forceinline__ void apply_body(const Ws& ws, CtaPos cp) {
     if ((tid >> 5) == 7) {
       const int lane = tid & 31;
       double t = 0.0;
+      #pragma unroll 1  // a dependent chain: unrolling adds code, not speed
       for (int k = lane; k < r; k += 32) t = fma(srl[k], v[k], t);
       t = warp_sum_d(t);
       if (lane == 0) bv[r] = fma(rho, t, gamma * v[r]);
@@ -994,6 +1001,7 @@ __device__ __forceinline__ void apply_body(const Ws& ws, CtaPos cp) {
       const int i = (base + tid) >> 2, sub = tid & 3;
       double acc = 0.0;
       if (i < r0)
+        #pragma unroll 1  // a dependent chain: unrolling adds code, not speed
         for (int k = sub; k < r; k += 4) acc = fma(sQ[(size_t)k * qld + i], u[k], acc);
       acc = group4_sum_d(acc);
       if (i < r0e && sub == 0) qcol[i] = fma(sqn[i], u[r], acc);
@@ -1004,6 +1012,7 @@ __device__ __forceinline__ void apply_body(const Ws& ws, CtaPos cp) {
       const int i = tid >> 2, sub = tid & 3;
       double acc = 0.0;
       if (i < rnew)
+        #pragma unroll 1  // a dependent chain: unrolling adds code, not speed
         for (int k = sub; k < n; k += 4) acc = fma(sU[(size_t)i * kMaxN + k], bv[k], acc);
       acc = group4_sum_d(acc);
       if (i < rnew && sub == 0) nx.M[(size_t)j * rm + i] = acc;
@@ -1019,11 +1028,13 @@ __device__ __forceinline__ void apply_body(const Ws& ws, CtaPos cp) {
       const int lane = tid;
       double rf = 0.0;
       if (pairs != 0) {
+        #pragma unroll 1  // a dependent chain: unrolling adds code, not speed
         for (int k = lane; k < r; k += 32) rf = fma(srf[k], v[k], rf);
         rf = warp_sum_d(rf);
       }
       double a = 0.0;
       if (compact) {
+        #pragma unroll 1  // a dependent chain: unrolling adds code, not speed
         for (int i = lane; i < r0e; i += 32) a = fma(qcol[i], syx[i], a);
         a = warp_sum_d(a);
       }
