@@ -127,6 +127,7 @@ __device__ __forceinline__ void prep_body(const Ws& ws, CtaPos cp) {
   // update, which completed before pass A started), so its copies run during the wait for
   // pass A; the reduced sums of pass A are read after it
   pdl_wait();
+  pdl_trigger();  // k_roots' CTAs are placed now and wait in their pdl_wait for this grid
   for (int i = tid; i < r0; i += kPrepThreads) {
     ac[i] = dd2d(st.a[i]) + dd2d(red[i]);
     yx[i] = dd2d(red[r0 + i]);
@@ -416,6 +417,9 @@ __device__ __forceinline__ void block_sum_f(float (&v)[NF], float* part) {  // p
 
 __device__ __forceinline__ void roots_body(const Ws& ws, CtaPos cp) {
   pdl_wait();
+  // after the wait, so that a successor placed now may read what any kernel before this one
+  // wrote; it waits in its own pdl_wait for this grid, on the SMs this grid leaves free
+  pdl_trigger();
   Ctl* ctl = ws.ctl;
   const int m = ctl->m;
   const int j = cp.b;
@@ -695,6 +699,9 @@ constexpr int kZhatThreads = 64;
 
 __device__ __forceinline__ void zhat_body(const Ws& ws, CtaPos cp) {
   pdl_wait();
+  // after the wait, so that a successor placed now may read what any kernel before this one
+  // wrote; it waits in its own pdl_wait for this grid, on the SMs this grid leaves free
+  pdl_trigger();
   Ctl* ctl = ws.ctl;
   const int m = ctl->m;
   const int tid = threadIdx.x;
@@ -797,6 +804,9 @@ constexpr int kVecThreads = 64;
 
 __device__ __forceinline__ void vectors_body(const Ws& ws, CtaPos cp) {
   pdl_wait();
+  // after the wait, so that a successor placed now may read what any kernel before this one
+  // wrote; it waits in its own pdl_wait for this grid, on the SMs this grid leaves free
+  pdl_trigger();
   Ctl* ctl = ws.ctl;
   const int j = cp.b;
   const int tid = threadIdx.x;

@@ -228,6 +228,11 @@ struct IngestTab {
 // start, so that the successor's CTAs are placed while it runs, measured slower: 5,926
 // against 6,362 snapshot updates/s.)
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Lets the successor's CTAs be placed now (they still wait for this grid's completion in
+// their pdl_wait): used only by the small-solve kernels, whose grids leave most SMs free,
+// and only after their own pdl_wait, so that whatever a successor reads before its wait
+// was written by kernels that have completed.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_dependent(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
