@@ -456,15 +456,20 @@ __device__ __forceinline__ void roots_body(const Ws& ws, CtaPos cp) {
     const double dj = d[j], dj1 = d[j + 1];
     const double gap = (dj1 - dj) * (dj1 + dj);
     const double mid = gap * 0.5;
-    const double t = mine ? zi * (zi / ((di - dj) * (di + dj) - mid)) : 0.0;
-    float v[2] = {__double2float_rn(t), 0.f};
-    v[1] = fabsf(v[0]);
+    // the terms in FP32 from d_i^2 - d_j^2 formed in FP64: every pole lies outside the
+    // interval, so |d_i^2 - d_j^2 - mid| >= mid and each term carries at most ~8 units of
+    // 2^-24 of relative error; with the summation's the bound below stays under
+    // (m + 10) 2^-23 (1 + sum |t|)
+    const double ddj = mine ? (di - dj) * (di + dj) : 0.0;
+    const float tf = mine ? zif * (zif / (__double2float_rn(ddj) - __double2float_rn(mid))) : 0.f;
+    float v[2] = {tf, fabsf(tf)};
     block_sum_f<2>(v, partf[it_total & 1]);
     const float fm = 1.f + v[0];
     bool right;  // f(mid) >= 0: the root lies left of the midpoint, next to d_j
-    if (fabsf(fm) > (float)(m + 4) * 0x1p-23f * (1.f + v[1])) {
+    if (fabsf(fm) > (float)(m + 10) * 0x1p-23f * (1.f + v[1])) {
       right = fm >= 0.f;
     } else {
+      const double t = mine ? zi * (zi / (ddj - mid)) : 0.0;
       right = 1.0 + block_sum_d(t, part64[it_total & 1]) >= 0.0;
     }
     ++it_total;
@@ -961,6 +966,7 @@ __device__ __forceinline__ void apply_body(const Ws& ws, CtaPos cp) {
     gamma = ctl->gamma;
   }
   pdl_wait();
+  pdl_trigger();  // the compaction kernel's CTAs are placed now (most return at once)
   if (j == 0 && tid == 0) {
     nx.hdr->r = rnew;
     nx.hdr->r0 = compact ? rnew : r0e;

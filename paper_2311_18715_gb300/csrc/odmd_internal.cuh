@@ -224,9 +224,10 @@ struct IngestTab {
 // programmatic stream serialisation, so the grid is set up while its predecessor finishes;
 // its first statement waits for the predecessor's completion and memory (and returns at
 // once when the kernel was launched without the attribute).  Every kernel that can be
-// launched this way begins with pdl_wait.  (Letting each kernel trigger its successor at its
-// start, so that the successor's CTAs are placed while it runs, measured slower: 5,926
-// against 6,362 snapshot updates/s.)
+// launched this way begins with pdl_wait.  (Letting every kernel trigger its successor at
+// its start, so that the successor's CTAs are placed while it runs, measured slower: 5,926
+// against 6,362 snapshot updates/s; the small-solve kernels, whose grids leave most SMs
+// free, do trigger, after their own wait: see pdl_trigger.)
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 // Lets the successor's CTAs be placed now (they still wait for this grid's completion in
 // their pdl_wait): used only by the small-solve kernels, whose grids leave most SMs free,
