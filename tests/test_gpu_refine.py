@@ -37,6 +37,11 @@ def _signal_projector(L, p):
     return L[:, :p] @ L[:, :p].T
 
 
+def _rel_h(got, want):
+    """relative error of each predicted state (one row per horizon), the largest of them"""
+    return float(np.max(np.linalg.norm(got - want, axis=1) / np.linalg.norm(want, axis=1)))
+
+
 def test_refinement_preserves_the_model_fp64():
     X = PlantedModes(4096, sigma=1e-8, seed=0).snapshots(0, 150)   # planted rank 6
     a, _ = _run(X, 10, 4, "fp64", 0)
@@ -51,7 +56,7 @@ def test_refinement_preserves_the_model_fp64():
     np.testing.assert_allclose(b.singular_values(), Sa, rtol=0, atol=1e-10 * Sa[0])
     ts = [0.0, 75.5, 149.0, 180.0]
     pa, pb = a.predict(ts).cpu().numpy(), b.predict(ts).cpu().numpy()
-    assert np.linalg.norm(pa - pb) / np.linalg.norm(pa) <= 1e-9
+    assert _rel_h(pb, pa) <= 1e-9
     # an explicit call on top of the periodic ones changes nothing beyond rounding
     b.refine()
     np.testing.assert_allclose(b.singular_values(), Sa, rtol=0, atol=1e-10 * Sa[0])
@@ -59,7 +64,7 @@ def test_refinement_preserves_the_model_fp64():
     assert oc <= 1e-13
     assert np.max(np.abs(_signal_projector(Lc, 6) - _signal_projector(Lb, 6))) <= 1e-12
     pc = b.predict(ts).cpu().numpy()
-    assert np.linalg.norm(pc - pb) / np.linalg.norm(pb) <= 1e-9
+    assert _rel_h(pc, pb) <= 1e-9
 
 
 def test_refinement_fp32_storage_against_oracle():
@@ -77,7 +82,7 @@ def test_refinement_fp32_storage_against_oracle():
     ts = [300.0, 320.0]
     got = refd.predict(ts).double().cpu().numpy()
     want = ref.predict(ts).T
-    assert np.linalg.norm(got - want) / np.linalg.norm(want) <= 1e-5
+    assert _rel_h(got, want) <= 1e-5
 
 
 def test_refine_needs_reserved_scratch():
@@ -104,4 +109,4 @@ def test_refinement_orthogonality_full_size():
     assert o <= 1e-13, o
     np.testing.assert_allclose(m.singular_values(), S0, rtol=0, atol=1e-12 * S0[0])
     p1 = m.predict(ts).cpu().numpy()
-    assert np.linalg.norm(p1 - p0) / np.linalg.norm(p0) <= 1e-9
+    assert _rel_h(p1, p0) <= 1e-9
