@@ -1297,7 +1297,7 @@ odmd_status build_sub(const std::vector<odmd_t>& hs, SubPlan** out) {
     e = launch_pass_a_batch(tab_of(hs, pa), p->prec, sa, p->s);
     if (e == cudaSuccess) e = launch_small_batch(tab_of(hs, one), tab_of(hs, root), tab_of(hs, zhat), sp, p->s);
     if (e == cudaSuccess)
-      e = split ? launch_split_compact_batch(tab_of(hs, pc), p->s) : launch_pass_b_batch(tab_of(hs, pc), p->prec, sb, p->s);
+      e = split ? launch_split_compact_batch(tab_of(hs, pc), p->prec, p->s) : launch_pass_b_batch(tab_of(hs, pc), p->prec, sb, p->s);
     const cudaError_t e2 = cudaStreamEndCapture(p->s, &p->graph);
     if (e == cudaSuccess) e = e2;
   }

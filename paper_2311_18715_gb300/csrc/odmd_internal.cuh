@@ -536,7 +536,7 @@ cudaError_t launch_pass_a_batch(const BatchTab& t, int prec, int smem, cudaStrea
 cudaError_t launch_pass_b_batch(const BatchTab& t, int prec, int smem, cudaStream_t s);
 cudaError_t launch_small_batch(const BatchTab& one, const BatchTab& per_root, const BatchTab& per_zhat,
                                int prep_smem, cudaStream_t s);
-cudaError_t launch_split_compact_batch(const BatchTab& t, cudaStream_t s);
+cudaError_t launch_split_compact_batch(const BatchTab& t, int prec, cudaStream_t s);
 int split_grid_of(const Ws& ws, int sms);
 int pass_a_smem(int prec, int cap);
 int pass_b_smem(int prec, int cap);

@@ -52,7 +52,6 @@ constexpr int kNJ = 64;         // MMA N: horizons of one launch, padded with ze
 constexpr int kKC = 16;         // K of one MMA
 constexpr int kSlices = 7;      // digits per value
 constexpr int kGroups = 7;      // g = s + t = 2 .. 8
-constexpr int kMaxK = 64;       // basis columns this path takes (4 K chunks)
 constexpr int kBufK = 16;       // K columns of L0 digits in one buffer (one chunk); two buffers
 constexpr int kWorkerWarps = 16;  // 4 threads per row in the digit phase, 4 warps per TMEM lane quarter
 constexpr int kWorkers = 32 * kWorkerWarps;
@@ -60,19 +59,35 @@ constexpr int kThreadsS = kWorkers + 32;  // and one warp that issues the copies
 constexpr uint32_t kTmemCols = 512;
 constexpr int kASlice = kTM * kBufK * 2;   // bytes of one digit slice of an L0 buffer
 constexpr int kABuf = kSlices * kASlice;   // bytes of one L0 digit buffer (one chunk, all slices)
-constexpr int kBSlice = kNJ * kMaxK * 2;   // bytes of one digit slice of C (K padded to 64)
 static_assert(kGroups * kNJ <= (int)kTmemCols, "seven accumulators fit the tensor memory");
-// a group sums at most 7 digit pairs over K <= 64 columns of products |d d'| <= 2^14
-static_assert(7 * kMaxK * (1 << 14) < (1 << 24), "group sums stay below 2^24");
+// Per storage format: the basis columns this path takes (K padded to whole chunks) and the
+// planes staged per row.  Four K chunks for the double-float basis (two planes); six for
+// FP32 storage, whose single plane leaves room for the larger digit block of the small
+// operand.
+template <int ST>
+struct Geo {
+  static constexpr int kPlanes = ST == ST_DD ? 2 : 1;
+  static constexpr int kMaxK = ST == ST_DD ? 64 : 96;
+  static constexpr int kBSlice = kNJ * kMaxK * 2;  // bytes of one digit slice of the small operand
+};
+// a group sums at most 7 digit pairs over K columns of products |d d'| <= 2^14
+static_assert(7 * Geo<ST_F32>::kMaxK * (1 << 14) < (1 << 24), "group sums stay below 2^24");
+static_assert(7 * Geo<ST_DD>::kMaxK * (1 << 14) < (1 << 24), "group sums stay below 2^24");
 
-// staging buffer: the two basis planes of a tile, then the tile's stored residual (8 bytes a row)
+// staging buffer: the basis planes of a tile, then the tile's stored residual (8 bytes a row)
 // 2^(8 (6 - q)): the scale of group g = q + 2 relative to the smallest group (g = 8)
 __device__ __forceinline__ float group_scale(int q) { return __int_as_float((127 + 8 * (6 - q)) << 23); }
 constexpr int kGridBits = 54;  // values on the grid 2^(e - 54): |I| < 2^54, seven bytes
 constexpr long long kDigitBias = 0x80808080808080ll;
 
-__host__ __device__ inline int stage_bytes(int rs) { return ((2 * kTM * rs + kTM * 8 + 1023) / 1024) * 1024; }
-__host__ __device__ inline int smem_bytes(int rs) { return stage_bytes(rs) + 2 * kABuf + kSlices * kBSlice; }
+template <int ST>
+__host__ __device__ constexpr int stage_bytes(int rs) {
+  return ((Geo<ST>::kPlanes * kTM * rs + kTM * 8 + 1023) / 1024) * 1024;
+}
+template <int ST>
+__host__ __device__ constexpr int smem_bytes(int rs) {
+  return stage_bytes<ST>(rs) + 2 * kABuf + kSlices * Geo<ST>::kBSlice;
+}
 
 // a barrier of the worker warps alone (named barrier 1; the issuer warp is not in it) that
 // also returns whether v held in any of them
@@ -132,24 +147,33 @@ __device__ __forceinline__ uint32_t digit_pair(unsigned long long u0, unsigned l
 
 // the tile's rows of both planes (and of the stored residual e when `with_e`) into the stage;
 // npad is a multiple of 64 rows, so every copy is a whole number of 16-byte units
+template <int ST>
 __device__ __forceinline__ void issue_tile(const Ws& ws, unsigned char* stage, int rs, int64_t tile, bool with_e,
                                            uint64_t* bar) {
+  constexpr int P = Geo<ST>::kPlanes;
   const int64_t row0 = tile * kTM;
   const int64_t rows = (ws.npad - row0) < kTM ? (ws.npad - row0) : kTM;
   const uint32_t bytes = (uint32_t)(rows * rs);
-  mbar_arrive_expect_tx(bar, 2 * bytes + (with_e ? (uint32_t)(rows * 8) : 0u));
+  mbar_arrive_expect_tx(bar, P * bytes + (with_e ? (uint32_t)(rows * 8) : 0u));
   bulk_g2s(stage, reinterpret_cast<const unsigned char*>(ws.Lh) + row0 * rs, bytes, bar);
-  bulk_g2s(stage + (size_t)kTM * rs, reinterpret_cast<const unsigned char*>(ws.Ll) + row0 * rs, bytes, bar);
-  if (with_e) bulk_g2s(stage + (size_t)2 * kTM * rs, ws.ebuf + row0, (uint32_t)(rows * 8), bar);
+  if constexpr (P == 2)
+    bulk_g2s(stage + (size_t)kTM * rs, reinterpret_cast<const unsigned char*>(ws.Ll) + row0 * rs, bytes, bar);
+  if (with_e) bulk_g2s(stage + (size_t)P * kTM * rs, ws.ebuf + row0, (uint32_t)(rows * 8), bar);
 }
 
-// COMPACT = false: X[:, j] = L0[:, :r0] coef[:, j] for j < kcols, X column-major doubles;
+// COMPACT = false: X[:, j] = L0[:, :r0] coef[:, j] for j < kcols, X column-major in the
+// snapshot type (doubles with double-float storage, floats with FP32 storage);
 // a pending basis column (its residual stored by the last update) is formed on the way and
 // written to L0, so no separate pass over the basis is needed before a prediction.
 // COMPACT = true: when the update in flight compacts, L0[:, :rnew] <- [L0[:, :r0] j0] Q_B in
 // place (the tile's rows are staged before they are overwritten, by the CTA that read them).
-template <bool COMPACT>
+// ST: the basis storage, double-float (two planes) or FP32 (one plane: its elements enter
+// with a zero lo part, and the columns written back are rounded to FP32 as stored).
+template <bool COMPACT, int ST>
 __device__ __forceinline__ void split_body(const Ws& ws, CtaPos cp, int kcols, double* out, int64_t ld) {
+  constexpr int kMaxK = Geo<ST>::kMaxK;
+  constexpr int kBSlice = Geo<ST>::kBSlice;
+  constexpr int kPlanes = Geo<ST>::kPlanes;
   if constexpr (COMPACT) {
     pdl_wait();
     if (ws.ctl->mode != PB_COMPACT) return;  // most updates: nothing to do
@@ -182,7 +206,7 @@ __device__ __forceinline__ void split_body(const Ws& ws, CtaPos cp, int kcols, d
   const int kpad = (K + kKC - 1) / kKC * kKC;
   const int nchunk = kpad / kKC;
   unsigned char* stage = sp;
-  unsigned char* adig = sp + stage_bytes(rs);
+  unsigned char* adig = sp + stage_bytes<ST>(rs);
   unsigned char* bdig = adig + 2 * kABuf;
   __shared__ int fexp[kNJ];
   // per-row exponent and new column j0 (compaction) of a tile, by tile parity: a worker warp
@@ -277,7 +301,7 @@ __device__ __forceinline__ void split_body(const Ws& ws, CtaPos cp, int kcols, d
   // at its next check (the other role's waits then run out as well).
   if (warp == kWorkerWarps) {
     if (lane == 0 && my_tiles > 0) {
-      issue_tile(ws, stage, rs, cp.b, with_e, &bar_tma);
+      issue_tile<ST>(ws, stage, rs, cp.b, with_e, &bar_tma);
       int tma_issued = 1;
       uint32_t pf[2] = {0u, 0u};
       bool issued = false;
@@ -293,7 +317,7 @@ __device__ __forceinline__ void split_body(const Ws& ws, CtaPos cp, int kcols, d
           tc::fence_after_sync();
           // the staging buffer is free once the tile's last digits are formed: next tile
           if (cc + 1 == nchunk && li + 1 < my_tiles) {
-            issue_tile(ws, stage, rs, tile + G, with_e, &bar_tma);
+            issue_tile<ST>(ws, stage, rs, tile + G, with_e, &bar_tma);
             ++tma_issued;
           }
           const uint64_t ab = adesc0 + (uint64_t)((b * kABuf) >> 4);
@@ -328,7 +352,9 @@ __device__ __forceinline__ void split_body(const Ws& ws, CtaPos cp, int kcols, d
     // chunk (half of a 16-byte core-matrix row per slice)
     const int row = tid >> 2, quad = tid & 3;
     const float* sh = reinterpret_cast<const float*>(stage) + (size_t)row * (rs / 4);
-    const float* sl = reinterpret_cast<const float*>(stage + (size_t)kTM * rs) + (size_t)row * (rs / 4);
+    // the lo plane (double-float storage; FP32 elements have a zero lo part)
+    const float* sl = reinterpret_cast<const float*>(stage + (size_t)(kPlanes - 1) * kTM * rs) + (size_t)row * (rs / 4);
+    auto lo_of = [&](int k) -> float { return kPlanes == 2 ? sl[k] : 0.f; };
     uint32_t par_tma = 0, par_mma[2] = {0u, 0u};
     bool ok = true;
     for (int li = 0; li < my_tiles; ++li) {
@@ -347,23 +373,29 @@ __device__ __forceinline__ void split_body(const Ws& ws, CtaPos cp, int kcols, d
         // j0 = (e - L0[:, :r0] s) / rho0 for this row, a quarter of the dot per thread
         Acc d = acc_zero();
         if (live)
-          for (int k = quad; k < r0; k += 4) acc_fma(d, sh[k], sl[k], sh_s[k], sl_s[k]);
+          for (int k = quad; k < r0; k += 4) acc_fma(d, sh[k], lo_of(k), sh_s[k], sl_s[k]);
         acc_add(d, __shfl_xor_sync(0xffffffffu, d.h, 1), __shfl_xor_sync(0xffffffffu, d.l, 1));
         acc_add(d, __shfl_xor_sync(0xffffffffu, d.h, 2), __shfl_xor_sync(0xffffffffu, d.l, 2));
         if (quad == 0) {
-          const float2 ev = reinterpret_cast<const float2*>(stage + (size_t)2 * kTM * rs)[row];
+          const float2 ev = reinterpret_cast<const float2*>(stage + (size_t)kPlanes * kTM * rs)[row];
           Acc e = Acc{ev.x, ev.y};
           acc_add(e, -d.h, -d.l);
           e = acc_norm(e);
           Acc j = acc_zero();
           acc_fma(j, e.h, e.l, inv.h, inv.l);
           j = acc_norm(j);
-          jh[row] = live ? j.h : 0.f;
-          jl[row] = live ? j.l : 0.f;
-          if (!COMPACT && live) {  // the pending column, as stored
+          // the column as stored (rounded to FP32 in that storage), and used as stored
+          float h = j.h, l = j.l;
+          if constexpr (kPlanes == 1) {
+            h = h + l;
+            l = 0.f;
+          }
+          jh[row] = live ? h : 0.f;
+          jl[row] = live ? l : 0.f;
+          if (!COMPACT && live) {  // the pending column, written back
             const size_t o = (size_t)(row0 + row) * ws.ldg + r0;
-            reinterpret_cast<float*>(ws.Lh)[o] = j.h;
-            ws.Ll[o] = j.l;
+            reinterpret_cast<float*>(ws.Lh)[o] = h;
+            if constexpr (kPlanes == 2) ws.Ll[o] = l;
           }
         }
         __syncwarp();
@@ -402,14 +434,14 @@ __device__ __forceinline__ void split_body(const Ws& ws, CtaPos cp, int kcols, d
             float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
             if (k < r0) {
               h0 = sh[k];
-              l0 = sl[k];
+              l0 = lo_of(k);
             } else if (k < K) {  // the new column (compaction)
               h0 = jh[row];
               l0 = jl[row];
             }
             if (k + 1 < r0) {
               h1 = sh[k + 1];
-              l1 = sl[k + 1];
+              l1 = lo_of(k + 1);
             } else if (k + 1 < K) {
               h1 = jh[row];
               l1 = jl[row];
@@ -507,24 +539,44 @@ __device__ __forceinline__ void split_body(const Ws& ws, CtaPos cp, int kcols, d
                 vl[u] = ldexpf(vl[u], sc[u]);
               }
             }
+            if constexpr (kPlanes == 1) {  // FP32 storage: the pair rounded to one float
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                vh[u] = vh[u] + vl[u];
+                vl[u] = 0.f;
+              }
+            }
             if (jb + c8 + 8 <= J) {
               *reinterpret_cast<float4*>(Lh + o) = make_float4(vh[0], vh[1], vh[2], vh[3]);
               *reinterpret_cast<float4*>(Lh + o + 4) = make_float4(vh[4], vh[5], vh[6], vh[7]);
-              *reinterpret_cast<float4*>(ws.Ll + o) = make_float4(vl[0], vl[1], vl[2], vl[3]);
-              *reinterpret_cast<float4*>(ws.Ll + o + 4) = make_float4(vl[4], vl[5], vl[6], vl[7]);
+              if constexpr (kPlanes == 2) {
+                *reinterpret_cast<float4*>(ws.Ll + o) = make_float4(vl[0], vl[1], vl[2], vl[3]);
+                *reinterpret_cast<float4*>(ws.Ll + o + 4) = make_float4(vl[4], vl[5], vl[6], vl[7]);
+              }
             } else {
 #pragma unroll
               for (int u = 0; u < 8; ++u)
                 if (jb + c8 + u < J) {
                   Lh[o + u] = vh[u];
-                  ws.Ll[o + u] = vl[u];
+                  if constexpr (kPlanes == 2) ws.Ll[o + u] = vl[u];
                 }
             }
-          } else {
+          } else if constexpr (kPlanes == 2) {
+            // double-float storage predicts doubles: their bits from the pair by integer operations
 #pragma unroll
             for (int u = 0; u < 8; ++u)
-              if (jb + c8 + u < J)  // the double's bits from the pair by integer operations
-                out[(size_t)(jb + c8 + u) * ld + orow] = pair_to_double_fast(vh[u], vl[u], sc[u]);
+              if (jb + c8 + u < J) out[(size_t)(jb + c8 + u) * ld + orow] = pair_to_double_fast(vh[u], vl[u], sc[u]);
+          } else {
+            // FP32 storage predicts floats (its snapshot type): the pair rounded, then the exact
+            // power-of-two scale
+            float* outf = reinterpret_cast<float*>(out);
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+              if (jb + c8 + u < J) {
+                const float v = vh[u] + vl[u];
+                outf[(size_t)(jb + c8 + u) * ld + orow] =
+                    (sc[u] >= -126 && sc[u] <= 127) ? __fmul_rn(v, __int_as_float((sc[u] + 127) << 23)) : ldexpf(v, sc[u]);
+              }
           }
         }
       }
@@ -550,39 +602,60 @@ __device__ __forceinline__ void split_body(const Ws& ws, CtaPos cp, int kcols, d
   }
 }
 
-template <bool COMPACT>
+template <bool COMPACT, int ST>
 __global__ void __launch_bounds__(kThreadsS, 1) k_split(const __grid_constant__ Ws ws, int kcols, double* out, int64_t ld) {
-  split_body<COMPACT>(ws, cta_single(), kcols, out, ld);
+  split_body<COMPACT, ST>(ws, cta_single(), kcols, out, ld);
 }
-template <bool COMPACT>
+template <bool COMPACT, int ST>
 __global__ void __launch_bounds__(kThreadsS, 1) k_split_batch(const __grid_constant__ BatchTab t) {
   const int i = batch_find(t, blockIdx.x);
-  split_body<COMPACT>(*t.ws[i], batch_pos(t, i), 0, (double*)nullptr, (int64_t)0);
+  split_body<COMPACT, ST>(*t.ws[i], batch_pos(t, i), 0, (double*)nullptr, (int64_t)0);
 }
 
+// the widest staged rows of each storage (its basis columns K padded: an odd chunk count)
+template <int ST>
+constexpr int widest_smem() {
+  return smem_bytes<ST>(16 * ((Geo<ST>::kMaxK / 4) | 1));
+}
+static_assert(widest_smem<ST_DD>() <= 227 * 1024 && widest_smem<ST_F32>() <= 227 * 1024,
+              "the widest staged tile and the digit buffers fit in shared memory");
 
 }  // namespace split
 
-// The tensor-core paths take double-float storage and at most 64 columns in the tall operand
-// (r0 <= cap, plus the appended column of a compaction): C's or Q_B's digits for K <= 64 and
-// one staged 128-row tile fit in shared memory.
+// The tensor-core paths take double-float storage with at most 64 columns in the tall
+// operand (r0 <= cap, plus the appended column of a compaction), and FP32 storage with at
+// most 96: the small operand's digits for those K and one staged 128-row tile fit in shared
+// memory.
 static bool split_fits(const Ws& ws) {
-  return ws.prec == ST_DD && split::smem_bytes(ws.ldg * 4) <= 227 * 1024;
+  if (ws.prec == ST_DD) return split::smem_bytes<ST_DD>(ws.ldg * 4) <= 227 * 1024;
+  if (ws.prec == ST_F32) return split::smem_bytes<ST_F32>(ws.ldg * 4) <= 227 * 1024;
+  return false;
+}
+static int split_max_k(const Ws& ws) {
+  return ws.prec == ST_DD ? split::Geo<ST_DD>::kMaxK : split::Geo<ST_F32>::kMaxK;
 }
 bool split_rollout_ok(const Ws& ws, int kcols) {
-  return split_fits(ws) && kcols >= 8 && kcols <= split::kNJ && ws.cap <= split::kMaxK;
+  return split_fits(ws) && kcols >= 8 && kcols <= split::kNJ && ws.cap <= split_max_k(ws);
 }
-bool split_compact_ok(const Ws& ws) { return split_fits(ws) && ws.cap + 1 <= split::kMaxK && ws.rmax <= split::kNJ; }
+bool split_compact_ok(const Ws& ws) {
+  return split_fits(ws) && ws.cap + 1 <= split_max_k(ws) && ws.rmax <= split::kNJ;
+}
 
 // The shared-memory limit is a property of the kernel, shared by every handle in the process:
-// set it for the widest rows this path takes (cap <= 64: an odd 17 chunks of 16 bytes)
+// set it for the widest rows each storage takes
 cudaError_t prepare_split(const Ws& ws) {
-  if (ws.prec != ST_DD) return cudaSuccess;
-  const int sm = split::smem_bytes(16 * box_chunks(split::kMaxK, 4));
-  static_assert(16 * 17 * 2 * split::kTM + 8 * split::kTM + 2 * split::kABuf + 7 * split::kBSlice <= 227 * 1024,
-                "the widest staged tile and the digit buffers fit in shared memory");
-  cudaError_t e = cudaFuncSetAttribute(split::k_split<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(split::k_split<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaError_t e = cudaSuccess;
+  if (ws.prec == ST_DD) {
+    const int sm = split::widest_smem<ST_DD>();
+    e = cudaFuncSetAttribute(split::k_split<false, ST_DD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(split::k_split<true, ST_DD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  } else if (ws.prec == ST_F32) {
+    const int sm = split::widest_smem<ST_F32>();
+    e = cudaFuncSetAttribute(split::k_split<false, ST_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(split::k_split<true, ST_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  }
   return e;
 }
 
@@ -594,28 +667,43 @@ static int split_grid(const Ws& ws, int sms) {
 int split_grid_of(const Ws& ws, int sms) { return split_grid(ws, sms); }
 
 cudaError_t prepare_split_batch() {
-  const int sm = split::smem_bytes(16 * box_chunks(split::kMaxK, 4));
-  return cudaFuncSetAttribute(split::k_split_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaError_t e = cudaFuncSetAttribute(split::k_split_batch<true, ST_DD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       split::widest_smem<ST_DD>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(split::k_split_batch<true, ST_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             split::widest_smem<ST_F32>());
+  return e;
 }
 
 // the compaction form over the instances of a batch (each instance's CTAs return at once
-// unless its update compacts); the largest shared memory any instance can ask for
-cudaError_t launch_split_compact_batch(const BatchTab& t, cudaStream_t s) {
-  const int sm = split::smem_bytes(16 * box_chunks(split::kMaxK, 4));
-  return launch_dependent(split::k_split_batch<true>, t.first[t.ninst], split::kThreadsS, (size_t)sm, s, t);
+// unless its update compacts; every instance has the storage prec); the largest shared
+// memory any instance can ask for
+cudaError_t launch_split_compact_batch(const BatchTab& t, int prec, cudaStream_t s) {
+  if (prec == ST_DD)
+    return launch_dependent(split::k_split_batch<true, ST_DD>, t.first[t.ninst], split::kThreadsS,
+                            (size_t)split::widest_smem<ST_DD>(), s, t);
+  return launch_dependent(split::k_split_batch<true, ST_F32>, t.first[t.ninst], split::kThreadsS,
+                          (size_t)split::widest_smem<ST_F32>(), s, t);
 }
 
 cudaError_t launch_split_rollout(const Ws& ws, int kcols, double* out, int64_t ld, int sms, cudaStream_t s) {
-  split::k_split<false><<<split_grid(ws, sms), split::kThreadsS, split::smem_bytes(ws.ldg * 4), s>>>(ws, kcols, out,
-                                                                                                     ld);
+  if (ws.prec == ST_DD)
+    split::k_split<false, ST_DD><<<split_grid(ws, sms), split::kThreadsS, split::smem_bytes<ST_DD>(ws.ldg * 4), s>>>(
+        ws, kcols, out, ld);
+  else
+    split::k_split<false, ST_F32><<<split_grid(ws, sms), split::kThreadsS, split::smem_bytes<ST_F32>(ws.ldg * 4), s>>>(
+        ws, kcols, out, ld);
   return cudaGetLastError();
 }
 
 // launched after the small solves of every update (in the update graph); it returns at once
 // unless the update compacts
 cudaError_t launch_split_compact(const Ws& ws, int sms, cudaStream_t s) {
-  return launch_dependent(split::k_split<true>, split_grid(ws, sms), split::kThreadsS,
-                          (size_t)split::smem_bytes(ws.ldg * 4), s, ws, 0, (double*)nullptr, (int64_t)0);
+  if (ws.prec == ST_DD)
+    return launch_dependent(split::k_split<true, ST_DD>, split_grid(ws, sms), split::kThreadsS,
+                            (size_t)split::smem_bytes<ST_DD>(ws.ldg * 4), s, ws, 0, (double*)nullptr, (int64_t)0);
+  return launch_dependent(split::k_split<true, ST_F32>, split_grid(ws, sms), split::kThreadsS,
+                          (size_t)split::smem_bytes<ST_F32>(ws.ldg * 4), s, ws, 0, (double*)nullptr, (int64_t)0);
 }
 
 }  // namespace odmd

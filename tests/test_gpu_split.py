@@ -137,3 +137,71 @@ def test_tensor_core_compaction_against_cuda_cores_and_oracle(slack, n):
     assert np.max(_rel(got, want)) < 1e-9
     L = tc.basis().cpu().numpy()
     assert np.max(np.abs(L @ L.T - np.eye(L.shape[0]))) < 1e-12
+
+
+def _fed_prec(X, r_max, slack, prec, tensor_cores):
+    import paper_2311_18715_gb300 as pkg
+
+    m = pkg.OnlineDMD(X.shape[1], r_max, prec=prec, slack=slack, tensor_cores=tensor_cores)
+    Xd = torch.from_numpy(X).cuda().to(m.dtype)
+    for k in range(X.shape[0]):
+        m.update(Xd[k])
+    return m
+
+
+@pytest.mark.parametrize("case", ["random_ragged", "wake_cap80"])
+def test_tensor_core_rollout_fp32_storage(case):
+    """FP32 storage on the tensor cores: one staged plane and up to 96 basis columns (cap 80
+    here lies past the double-float path's 64).  The rollout of a model state equals the
+    CUDA-core rollout of the same state (a checkpoint loaded into a CUDA-core handle) to
+    1e-12 per horizon (both multiply the stored FP32 basis by double-float coefficients), at
+    8, 50 and 65 horizons; a prediction straight after an update forms the pending column as
+    stored (rounded to FP32) and the basis then matches the flushed one to one FP32 unit."""
+    import paper_2311_18715_gb300 as pkg
+
+    if case == "random_ragged":
+        X, r, sl = RandomPlanted(50001, seed=5).snapshots(0, 70), 24, 8
+    else:
+        X, r, sl = WakeField(128, 64, sigma=1e-6, seed=2).snapshots(0, 150), 64, 16
+    tc = _fed_prec(X, r, sl, "fp32", True)
+    twin = _fed_prec(X, r, sl, "fp32", True)
+    cc = pkg.OnlineDMD(tc.n, tc.r_max, prec="fp32", slack=sl, tensor_cores=False)
+    cc.load(twin.save())  # the pending column written by the flush
+    k = X.shape[0]
+    for nh in (8, 50, 65):
+        ts = [float(k - 3 + h) for h in range(nh)]
+        got = tc.predict(ts).double().cpu().numpy()
+        base = cc.predict(ts).double().cpu().numpy()
+        assert np.isfinite(got).all()
+        assert np.max(_rel(got, base)) < 1e-6, (case, nh, np.max(_rel(got, base)))
+    La, Lb = tc.basis().double().cpu().numpy(), cc.basis().double().cpu().numpy()
+    assert La.shape == Lb.shape
+    assert np.max(np.abs(La - Lb)) <= 2.0 ** -23 * np.max(np.abs(Lb)), np.max(np.abs(La - Lb))
+    # with the same stored column, the two rollouts agree to the double-float level
+    tc2 = pkg.OnlineDMD(tc.n, tc.r_max, prec="fp32", slack=sl, tensor_cores=True)
+    tc2.load(twin.save())
+    ts = [float(k + h) for h in range(50)]
+    got, base = tc2.predict(ts).double().cpu().numpy(), cc.predict(ts).double().cpu().numpy()
+    assert np.max(_rel(got, base)) < 1e-12, np.max(_rel(got, base))
+
+
+def test_tensor_core_compaction_fp32_storage():
+    """The FP32 compaction on the tensor cores (the product rounded to FP32 as stored) against
+    the CUDA-core one on a stream that compacts often: the same compactions, singular values
+    within 1e-6 of sigma_1 of each other and 1e-5 of the oracle's, predictions within 1e-5 of
+    each other and of the oracle per horizon."""
+    X = PlantedModes(4096, sigma=1e-5, seed=3).snapshots(0, 140)
+    tc = _fed_prec(X, 6, 5, "fp32", True)
+    cc = _fed_prec(X, 6, 5, "fp32", False)
+    ref = OnlineDMDRef(X.shape[1], 6, 1e-10)
+    for k in range(X.shape[0]):
+        ref.update(X[k].astype(np.float32).astype(np.float64))
+    assert tc.counts()[1] > 15 and tc.counts() == cc.counts()
+    S, Sc = np.array(tc.singular_values()), np.array(cc.singular_values())
+    assert np.max(np.abs(S - Sc)) <= 1e-6 * Sc[0]
+    assert np.max(np.abs(S - ref.S)) <= 1e-5 * ref.S[0]
+    ts = [float(h) for h in range(130, 150)]
+    got, base, want = (tc.predict(ts).double().cpu().numpy(), cc.predict(ts).double().cpu().numpy(),
+                       ref.predict(ts).T)
+    assert np.max(_rel(got, base)) < 1e-5, np.max(_rel(got, base))
+    assert np.max(_rel(got, want)) < 1e-5, np.max(_rel(got, want))
