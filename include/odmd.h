@@ -75,14 +75,21 @@ typedef struct {
   odmd_precision prec;  /* basis storage, see above */
   int32_t refine_every; /* refine orthogonality after every this many pairs (0: never);
                            see odmd_refine */
-  uint32_t flags;       /* 0, or ODMD_CUDA_CORES; other bits are rejected */
+  uint32_t flags;       /* 0, or ODMD_CUDA_CORES and/or ODMD_NO_PIPELINE; other bits are rejected */
 } odmd_config;
 
-/* flags: keep multi-horizon rollouts on the CUDA cores.  By default a prediction of 8 to 64
- * states with FP64 storage and at most 64 basis columns (r_max + slack <= 64) runs as an
- * exact split product on the tensor cores; this flag keeps the CUDA-core path (the same
- * values to the double-float rounding level). */
+/* flags: keep multi-horizon rollouts and compactions on the CUDA cores.  By default a
+ * prediction of 8 to 64 states, and the compaction of the product-form basis, run as exact
+ * split products on the tensor cores when the basis has at most 64 columns (FP64 storage,
+ * r_max + slack <= 63 for a compaction) or 96 (FP32 storage); this flag keeps the CUDA-core
+ * path (the same values to the double-float rounding level). */
 #define ODMD_CUDA_CORES 1u
+/* flags: run every update to its end before the next one starts.  By default an update's
+ * core SVD and operator update (Sec. 2.3: they do not feed the next projection, which needs
+ * only the new basis column and the projection of the snapshot) run beside the next
+ * update's pass over the basis, and complete before any other call on the handle reads the
+ * model; the results are bitwise the same either way. */
+#define ODMD_NO_PIPELINE 2u
 
 /* Fill *cfg with the defaults for a stream of length n and rank cap r_max:
  * slack 16, trunc_tol 1e-10, check_tol 1e-5, ODMD_FP64, refine_every 0, flags 0. */

@@ -58,6 +58,17 @@ struct odmd_instance {
     cudaEvent_t ph[6] = {};           // events recorded by the nodes at capture (kept alive)
   };
   UpdGraph ug[2][2];
+  // Pipelined updates: the graph of update k + 1 runs its ingest and pass A on one branch and
+  // the SVD tail of update k (k_roots .. k_apply, the compaction kernel) on another, joined
+  // before its k_prep; update k + 1's own tail then waits for the next update or a settle.
+  // pg[cur][curc][tail]: the state and snapshot buffers of update k + 1, with or without a
+  // previous tail to run; tg: a pending tail alone.
+  UpdGraph pg[2][2][2];
+  UpdGraph tg;
+  cudaStream_t cap2 = nullptr;  // the forked branch while a pipelined graph is captured
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool pipe = true;             // pipelined updates wherever the graph path runs
+  bool tail_pending = false;    // the last update's tail has not been enqueued yet
   cudaStream_t cap = nullptr;
   bool use_graphs = true;
   bool use_tc = true;   // multi-horizon rollouts on the tensor cores where split.cu takes them
@@ -133,8 +144,8 @@ odmd_status check_cfg(const odmd_config* c, std::string& why) {
     why = "ODMD_BF16 basis storage is not supported by the rank-1 update; use ODMD_FP32";
     return ODMD_ERR_ARG;
   }
-  if ((c->flags & ~ODMD_CUDA_CORES) != 0) {
-    why = "unknown flags (only ODMD_CUDA_CORES is defined)";
+  if ((c->flags & ~(ODMD_CUDA_CORES | ODMD_NO_PIPELINE)) != 0) {
+    why = "unknown flags (only ODMD_CUDA_CORES and ODMD_NO_PIPELINE are defined)";
     return ODMD_ERR_ARG;
   }
   if (c->refine_every < 0) {
@@ -434,6 +445,8 @@ void prof_collect(odmd_t h) {
 
 // Capture the update sequence for snapshot-buffer parity `par` (the new snapshot goes to
 // cbuf[par ^ 1]); with `prof`, event-record nodes bracket the three kernel groups.
+odmd_status finish_graph(odmd_t h, odmd_instance::UpdGraph& G, cudaGraph_t graph, bool want_ingest);
+
 odmd_status build_update_graph(odmd_t h, int par, int prof) {
   odmd_instance::UpdGraph& G = h->ug[par][prof];
   if (G.exec) return ODMD_OK;
@@ -459,8 +472,15 @@ odmd_status build_update_graph(odmd_t h, int par, int prof) {
     if (graph) cudaGraphDestroy(graph);
     return cuda_fail(h, e, "update graph capture");
   }
-  // find the ingest node (its source pointer changes every update) and the event nodes;
-  // the captured graph is released on every way out that does not keep it
+  return finish_graph(h, G, graph, true);
+}
+
+// Keep a captured graph in G: find its ingest node (the snapshot pointer changes every
+// update; want_ingest) and its event nodes, and instantiate it.  The graph is released on
+// every way out that does not keep it.
+odmd_status finish_graph(odmd_t h, odmd_instance::UpdGraph& G, cudaGraph_t graph, bool want_ingest) {
+  cudaEvent_t* ph = G.ph;
+  cudaError_t e = cudaSuccess;
   size_t nn = 0;
   e = cudaGraphGetNodes(graph, nullptr, &nn);
   std::vector<cudaGraphNode_t> nodes(e == cudaSuccess ? nn : 0);
@@ -490,7 +510,7 @@ odmd_status build_update_graph(odmd_t h, int par, int prof) {
     G.ingest = nullptr;
     return cuda_fail(h, e, "update graph nodes");
   }
-  if (!G.ingest) {
+  if (want_ingest && !G.ingest) {
     cudaGraphDestroy(graph);
     return fail(h, ODMD_ERR_CUDA, "update graph: ingest node not found");
   }
@@ -506,6 +526,77 @@ odmd_status build_update_graph(odmd_t h, int par, int prof) {
   G.args[2] = &G.n;
   G.kp.kernelParams = G.args;
   G.kp.extra = nullptr;
+  return ODMD_OK;
+}
+
+// the SVD tail of an update on stream s: k_roots .. k_apply, then the compaction kernel
+// (which returns at once unless the update compacts)
+cudaError_t launch_update_tail(odmd_t h, cudaStream_t s) {
+  cudaError_t e = launch_small_tail(h->ws, s);
+  if (e == cudaSuccess)
+    e = (h->use_tc && split_compact_ok(h->ws)) ? launch_split_compact(h->ws, h->sms, s) : launch_pass_b(h->ws, s);
+  return e;
+}
+
+// Capture the pipelined update for state buffer `cur` and snapshot parity `curc` (its new
+// snapshot goes to cbuf[curc ^ 1]).  With `tail` the previous update's tail runs on a forked
+// branch beside this update's ingest and pass A; that pass A returns at once if the previous
+// update compacts and runs again after the join in that case (pass_a_body's gate).
+odmd_status build_pipe_graph(odmd_t h, int cur, int curc, int tail) {
+  odmd_instance::UpdGraph& G = h->pg[cur][curc][tail];
+  if (G.exec) return ODMD_OK;
+  if (!h->cap2) {
+    CK(h, cudaStreamCreateWithFlags(&h->cap2, cudaStreamNonBlocking), "pipeline capture stream");
+    CK(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming), "pipeline events");
+    CK(h, cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming), "pipeline events");
+  }
+  const int sel = cur | (curc << 1);
+  cudaGraph_t graph = nullptr;
+  CK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+  cudaError_t e = cudaSuccess;
+  if (tail) {
+    e = cudaEventRecord(h->ev_fork, h->cap);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->cap2, h->ev_fork, 0);
+  }
+  if (e == cudaSuccess) e = launch_ingest(h->ws, h->ws.cbuf[curc], h->ws.cbuf[curc ^ 1], h->cap);
+  if (e == cudaSuccess) e = launch_pass_a_sel(h->ws, sel | ((tail ? 1 : 0) << 2), h->cap);
+  if (tail) {
+    if (e == cudaSuccess) e = launch_update_tail(h, h->cap2);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_join, h->cap2);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->cap, h->ev_join, 0);
+    if (e == cudaSuccess) e = launch_pass_a_sel(h->ws, sel | (2 << 2), h->cap);
+  }
+  if (e == cudaSuccess) e = launch_prep(h->ws, h->cap);
+  cudaError_t e2 = cudaStreamEndCapture(h->cap, &graph);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_fail(h, e, "pipelined update graph capture");
+  }
+  return finish_graph(h, G, graph, true);
+}
+
+// Enqueue the tail of the last pipelined update, if it has not run yet; every call that
+// reads or changes the model other than an update begins with this.
+odmd_status settle(odmd_t h) {
+  if (!h->tail_pending) return ODMD_OK;
+  odmd_instance::UpdGraph& G = h->tg;
+  if (!G.exec) {
+    cudaGraph_t graph = nullptr;
+    CK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+    cudaError_t e = launch_update_tail(h, h->cap);
+    cudaError_t e2 = cudaStreamEndCapture(h->cap, &graph);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return cuda_fail(h, e, "update tail graph capture");
+    }
+    if (odmd_status st = finish_graph(h, G, graph, false)) return st;
+  }
+  CK(h, cudaGraphLaunch(G.exec, h->stream), "update tail launch");
+  h->launches[ODMD_K_SMALL] += 4;
+  h->launches[ODMD_K_PASS_B] += 1;
+  h->tail_pending = false;
   return ODMD_OK;
 }
 
@@ -640,6 +731,7 @@ odmd_status odmd_create(const odmd_config* cfg, void* workspace_dev, size_t byte
   if (e == cudaSuccess) e = prepare_split(h->ws);
   h->sms = sms;
   h->use_tc = (cfg->flags & ODMD_CUDA_CORES) == 0;
+  h->pipe = (cfg->flags & ODMD_NO_PIPELINE) == 0;
   if (e == cudaSuccess && cfg->refine_every > 0) e = prepare_refine();
   if (e == cudaSuccess) e = cudaMemsetAsync(workspace_dev, 0, L.total, h->stream);
   if (e == cudaSuccess) {
@@ -677,7 +769,25 @@ odmd_status odmd_update(odmd_t h, const void* x_dev) {
     return ODMD_OK;
   }
   bool graphed = false;
-  if (h->use_graphs) {
+  if (h->use_graphs && h->pipe && !h->prof_on && h->ws.shards == 1) {
+    // pipelined: this update's ingest and pass A beside the last update's tail
+    const int tail = h->tail_pending ? 1 : 0;
+    if (odmd_status st = build_pipe_graph(h, h->cur_h, h->curc_h, tail)) return st;
+    odmd_instance::UpdGraph& G = h->pg[h->cur_h][h->curc_h][tail];
+    G.src = x_dev;
+    G.dst = h->ws.cbuf[h->curc_h ^ 1];
+    G.n = h->cfg.n;
+    CK(h, cudaGraphExecKernelNodeSetParams(G.exec, G.ingest, &G.kp), "graph ingest params");
+    CK(h, cudaGraphLaunch(G.exec, h->stream), "pipelined update graph launch");
+    h->launches[ODMD_K_PASS_A] += 1 + tail;
+    h->launches[ODMD_K_SMALL] += 1 + 4 * tail;
+    h->launches[ODMD_K_PASS_B] += tail;
+    h->tail_pending = true;
+    graphed = true;
+  } else if (odmd_status st = settle(h)) {
+    return st;
+  }
+  if (!graphed && h->use_graphs) {
     const int par = h->curc_h, prof = h->prof_on ? 1 : 0;
     if (odmd_status st = build_update_graph(h, par, prof)) return st;
     odmd_instance::UpdGraph& G = h->ug[par][prof];
@@ -751,6 +861,7 @@ odmd_status odmd_update(odmd_t h, const void* x_dev) {
 
 odmd_status odmd_predict(odmd_t h, const double* t_host, int32_t k, void* out_dev, int64_t ld) {
   if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
+  if (odmd_status st_ = settle(h)) return st_;
   if (k < 0 || (k > 0 && (!t_host || !out_dev))) return fail(h, ODMD_ERR_ARG, "bad t/out/k");
   if (ld < h->cfg.n) return fail(h, ODMD_ERR_ARG, "ld < n");
   if (h->nsnap < 2) return fail(h, ODMD_ERR_STATE, "predict needs two snapshots");
@@ -785,6 +896,7 @@ odmd_status odmd_predict(odmd_t h, const double* t_host, int32_t k, void* out_de
 
 odmd_status odmd_check(odmd_t h, double t, const void* x_fom_dev, double tol, double* rel_err, int32_t* pass) {
   if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
+  if (odmd_status st_ = settle(h)) return st_;
   if (!x_fom_dev) return fail(h, ODMD_ERR_ARG, "x_fom is NULL");
   if (!(t >= 0.0) || !std::isfinite(t)) return fail(h, ODMD_ERR_ARG, "t must be finite and >= 0");
   if (h->nsnap < 2) return fail(h, ODMD_ERR_STATE, "check needs two snapshots");
@@ -816,6 +928,7 @@ odmd_status odmd_check(odmd_t h, double t, const void* x_fom_dev, double tol, do
 
 odmd_status odmd_refine(odmd_t h) {
   if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
+  if (odmd_status st_ = settle(h)) return st_;
   if (!h->ws.gpart) return fail(h, ODMD_ERR_STATE, "refinement scratch not reserved: create with refine_every > 0");
   if (h->nsnap < 2) return ODMD_OK;  // no basis yet
   if (odmd_status s = flush_pending(h)) return s;
@@ -904,6 +1017,7 @@ odmd_status odmd_checkpoint_size(odmd_t h, size_t* bytes) {
 
 odmd_status odmd_save(odmd_t h, void* host_buf, size_t bytes) {
   if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
+  if (odmd_status st_ = settle(h)) return st_;
   if (!host_buf) return fail(h, ODMD_ERR_ARG, "host buffer must not be NULL");
   const size_t need = ckpt_bytes(h);
   if (bytes < need) return fail(h, ODMD_ERR_ARG, "checkpoint buffer of " + std::to_string(bytes) +
@@ -948,6 +1062,7 @@ odmd_status odmd_save(odmd_t h, void* host_buf, size_t bytes) {
 
 odmd_status odmd_load(odmd_t h, const void* host_buf, size_t bytes) {
   if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
+  if (odmd_status st_ = settle(h)) return st_;
   if (!host_buf) return fail(h, ODMD_ERR_ARG, "host buffer must not be NULL");
   if (bytes < sizeof(CkptHeader)) return fail(h, ODMD_ERR_ARG, "checkpoint shorter than its header");
   CkptHeader hd;
@@ -1002,6 +1117,7 @@ odmd_status odmd_load(odmd_t h, const void* host_buf, size_t bytes) {
 odmd_status odmd_hybrid_step(odmd_t h, const void* x_fom_dev, double tol, void* state_out_dev, int32_t* accepted,
                              double* rel_err) {
   if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
+  if (odmd_status st_ = settle(h)) return st_;
   if (!x_fom_dev || !state_out_dev) return fail(h, ODMD_ERR_ARG, "x_fom and state_out must not be NULL");
   if (state_out_dev == x_fom_dev) return fail(h, ODMD_ERR_ARG, "state_out must not alias x_fom");
   int32_t acc = 0;
@@ -1035,6 +1151,7 @@ odmd_status odmd_hybrid_step_residual(odmd_t h, odmd_residual_fn residual, odmd_
                                       void* state_out_dev, void* r_dev, void* b_dev, int32_t* accepted,
                                       double* rel_res) {
   if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
+  if (odmd_status st_ = settle(h)) return st_;
   if (!residual || !fom) return fail(h, ODMD_ERR_ARG, "the residual and FOM callbacks must not be NULL");
   if (!state_out_dev || !r_dev || !b_dev) return fail(h, ODMD_ERR_ARG, "state_out, r and b must not be NULL");
   if (state_out_dev == r_dev || state_out_dev == b_dev || r_dev == b_dev)
@@ -1109,6 +1226,7 @@ odmd_status odmd_hybrid_run(odmd_t h, odmd_residual_fn residual, odmd_fom_fn fom
                             int64_t t_final, int32_t check_every, int32_t conv_checks, double conv_tol,
                             void* state_out_dev, void* prev_dev, void* r_dev, void* b_dev, odmd_run_report* report) {
   if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
+  if (odmd_status st_ = settle(h)) return st_;
   if (!prev_dev || prev_dev == state_out_dev || prev_dev == r_dev || prev_dev == b_dev)
     return fail(h, ODMD_ERR_ARG, "prev must be a buffer of its own");
   if (t_final < h->nsnap) return fail(h, ODMD_ERR_ARG, "t_final lies before the next step");
@@ -1469,6 +1587,8 @@ odmd_status odmd_update_batch(odmd_t* hs, const void* const* xs, int32_t count) 
                                                std::to_string(j));
   }
   if (count == 0) return ODMD_OK;
+  for (int32_t i = 0; i < count; ++i)  // any pipelined tail first
+    if (odmd_status s = settle(hs[i])) return fail(nullptr, s, "update_batch: instance " + std::to_string(i) + ": " + hs[i]->err);
   // instances that can share launches, grouped by storage format and compaction kind, in
   // groups of at most kMaxBatch; the others (first snapshot, profiling on, row shards, no
   // graphs, another device) update one by one
@@ -1524,6 +1644,7 @@ odmd_status odmd_predict_batch(odmd_t* hs, const double* const* ts, const int32_
 
 odmd_status odmd_sync(odmd_t h) {
   if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
+  if (odmd_status st_ = settle(h)) return st_;
   return device_status(h);
 }
 
@@ -1538,6 +1659,7 @@ static odmd_status read_hdr(odmd_t h, StateHdr* hdr) {
 
 odmd_status odmd_get_rank(odmd_t h, int32_t* r) {
   if (!h || !r) return fail(h, ODMD_ERR_ARG, "NULL argument");
+  if (odmd_status st_ = settle(h)) return st_;
   StateHdr hdr;
   if (odmd_status s = read_hdr(h, &hdr)) return s;
   *r = hdr.r;
@@ -1546,6 +1668,7 @@ odmd_status odmd_get_rank(odmd_t h, int32_t* r) {
 
 odmd_status odmd_get_singular_values(odmd_t h, double* s_host, int32_t cap, int32_t* r) {
   if (!h || !r || (cap > 0 && !s_host)) return fail(h, ODMD_ERR_ARG, "NULL argument");
+  if (odmd_status st_ = settle(h)) return st_;
   StateHdr hdr;
   if (odmd_status s = read_hdr(h, &hdr)) return s;
   *r = hdr.r;
@@ -1558,6 +1681,7 @@ odmd_status odmd_get_singular_values(odmd_t h, double* s_host, int32_t cap, int3
 
 odmd_status odmd_get_eigs(odmd_t h, double* re_host, double* im_host, double* amp_host, int32_t cap, int32_t* r) {
   if (!h || !r || (cap > 0 && (!re_host || !im_host))) return fail(h, ODMD_ERR_ARG, "NULL argument");
+  if (odmd_status st_ = settle(h)) return st_;
   if (h->nsnap < 2) return fail(h, ODMD_ERR_STATE, "no model yet");
   if (odmd_status s = ensure_eig(h)) return s;
   StateHdr hdr;
@@ -1583,6 +1707,7 @@ odmd_status odmd_get_eigs(odmd_t h, double* re_host, double* im_host, double* am
 
 odmd_status odmd_get_basis(odmd_t h, void* out_dev, int64_t ld, int32_t* r) {
   if (!h || !out_dev || !r) return fail(h, ODMD_ERR_ARG, "NULL argument");
+  if (odmd_status st_ = settle(h)) return st_;
   if (ld < h->cfg.n) return fail(h, ODMD_ERR_ARG, "ld < n");
   StateHdr hdr;
   if (odmd_status s = read_hdr(h, &hdr)) return s;
@@ -1602,6 +1727,7 @@ odmd_status odmd_get_basis(odmd_t h, void* out_dev, int64_t ld, int32_t* r) {
 
 odmd_status odmd_get_counts(odmd_t h, int64_t* snapshots, int64_t* compactions) {
   if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
+  if (odmd_status st_ = settle(h)) return st_;
   if (snapshots) *snapshots = h->nsnap;
   if (compactions) {
     StateHdr hdr;
@@ -1622,6 +1748,7 @@ static odmd_status read_prof_counters(odmd_t h, unsigned long long* out2) {
 
 odmd_status odmd_profile_enable(odmd_t h, int32_t enable) {
   if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
+  if (odmd_status st_ = settle(h)) return st_;
   prof_collect(h);
   for (int i = 0; i < ODMD_K_COUNT; ++i) h->prof_ms[i] = 0.0;
   if (odmd_status s = read_prof_counters(h, h->r0_base)) return s;
@@ -1631,6 +1758,7 @@ odmd_status odmd_profile_enable(odmd_t h, int32_t enable) {
 
 odmd_status odmd_profile_read(odmd_t h, double* ms_total, int64_t* launches, int32_t cap, double* mean_r0) {
   if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
+  if (odmd_status st_ = settle(h)) return st_;
   if (odmd_status s = device_status(h)) return s;
   prof_collect(h);
   const int nc = cap < ODMD_K_COUNT ? cap : ODMD_K_COUNT;
@@ -1648,19 +1776,25 @@ odmd_status odmd_profile_read(odmd_t h, double* ms_total, int64_t* launches, int
 }
 
 // release the captured update graphs (they are captured again on the next update)
+static void drop_graph(odmd_instance::UpdGraph& g) {
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (g.graph) cudaGraphDestroy(g.graph);
+  for (cudaEvent_t ev : g.ph)
+    if (ev) cudaEventDestroy(ev);
+  g = odmd_instance::UpdGraph{};
+}
 static void drop_update_graphs(odmd_t h) {
   for (auto& row : h->ug)
-    for (auto& g : row) {
-      if (g.exec) cudaGraphExecDestroy(g.exec);
-      if (g.graph) cudaGraphDestroy(g.graph);
-      for (cudaEvent_t ev : g.ph)
-        if (ev) cudaEventDestroy(ev);
-      g = odmd_instance::UpdGraph{};
-    }
+    for (auto& g : row) drop_graph(g);
+  for (auto& a : h->pg)
+    for (auto& b : a)
+      for (auto& g : b) drop_graph(g);
+  drop_graph(h->tg);
 }
 
 odmd_status odmd_set_row_shards(odmd_t h, int32_t shards) {
   if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
+  if (odmd_status st_ = settle(h)) return st_;
   if (shards < 1 || shards > h->ws.gridA)
     return fail(h, ODMD_ERR_ARG, "shards must lie in [1, " + std::to_string(h->ws.gridA) + "] (the row blocks)");
   if (shards == h->ws.shards) return ODMD_OK;
@@ -1695,6 +1829,9 @@ odmd_status odmd_destroy(odmd_t h) {
   drop_batch_plans(h);
   if (h->ev_batch) cudaEventDestroy(h->ev_batch);
   if (h->cap) cudaStreamDestroy(h->cap);
+  if (h->cap2) cudaStreamDestroy(h->cap2);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   for (int b = 0; b < 2; ++b) {
     if (h->ev_copied[b]) cudaEventDestroy(h->ev_copied[b]);
     if (h->ev_used[b]) cudaEventDestroy(h->ev_used[b]);

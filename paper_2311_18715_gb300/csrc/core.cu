@@ -196,6 +196,29 @@ __device__ __forceinline__ void prep_body(const Ws& ws, CtaPos cp) {
   const int append = append_s;
   const int r0e = r0 + append;
   const double thr = thr_s;
+  // The next state's inputs of the next tall pass, published here rather than by k_apply so
+  // that a pipelined next pass A may run beside this update's SVD: its header (all but the
+  // rank; r0 too unless the update compacts, when k_apply writes it with the new rank), its
+  // projection a = L0'^T x and the pending column's s.  A compacting update also sets
+  // pipe_flag, on which a pipelined next pass A waits for the compaction.
+  {
+    const bool compact = r0e > ws.cap;
+    const StateBuf nx = ws.st[cur ^ 1];
+    if (tid == 0) {
+      nx.hdr->pairs = st.hdr->pairs + 1;
+      nx.hdr->compactions = st.hdr->compactions + (compact ? 1 : 0);
+      nx.hdr->cn2 = red[2 * r0 + 2];
+      nx.hdr->pend = (append && !compact) ? 1 : 0;
+      nx.hdr->pinv = append ? d2f2(1.0 / ctl->rho0) : make_float2(0.f, 0.f);
+      if (!compact) nx.hdr->r0 = r0e;
+      ctl->pipe_flag = compact ? 1 : 0;
+    }
+    if (!compact) {
+      for (int i = tid; i < r0e; i += kPrepThreads) nx.a[i] = d2f2(yx[i]);
+      if (append)
+        for (int i = tid; i < r0; i += kPrepThreads) nx.ps[i] = red[i];
+    }
+  }
   // z = ac - Q p (rows < r0; the appended coordinate is ac itself)
   for (int base = 0; base < 4 * r0e; base += kPrepThreads) {
     if (base + 32 * warp >= 4 * r0e) continue;
@@ -967,22 +990,12 @@ __device__ __forceinline__ void apply_body(const Ws& ws, CtaPos cp) {
   }
   pdl_wait();
   pdl_trigger();  // the compaction kernel's CTAs are placed now (most return at once)
+  // k_prep wrote the rest of the next state's header, its a and s (an update that does not
+  // compact); an appended column is formed by the next tall pass (compaction forms it at once)
   if (j == 0 && tid == 0) {
     nx.hdr->r = rnew;
-    nx.hdr->r0 = compact ? rnew : r0e;
-    nx.hdr->pairs = st.hdr->pairs + 1;
-    nx.hdr->compactions = st.hdr->compactions + (compact ? 1 : 0);
-    nx.hdr->cn2 = ws.sm.red[2 * r0 + 2];
-    // an appended column is formed by the next tall pass (compaction forms it at once)
-    nx.hdr->pend = (append && !compact) ? 1 : 0;
-    nx.hdr->pinv = append ? d2f2(1.0 / ctl->rho0) : make_float2(0.f, 0.f);
+    if (compact) nx.hdr->r0 = rnew;
     ctl->mode = compact ? PB_COMPACT : (append ? PB_APPEND : PB_NONE);
-  }
-  if (j == 0) {
-    if (!compact)
-      for (int i = tid; i < r0e; i += kApplyThreads) nx.a[i] = d2f2(ws.sm.yext[i]);
-    if (append && !compact)
-      for (int i = tid; i < r0; i += kApplyThreads) nx.ps[i] = ws.sm.red[i];
   }
   if (mine) {
     // the singular vectors of k_vectors
@@ -1124,12 +1137,20 @@ cudaError_t launch_small_batch(const BatchTab& one, const BatchTab& per_root, co
   return e;
 }
 
-cudaError_t launch_small(const Ws& ws, cudaStream_t s) {
-  cudaError_t e = launch_dependent(k_prep, 1, kPrepThreads, prep_smem_cap(ws.cap), s, ws);
-  if (e == cudaSuccess) e = launch_dependent(k_roots, kMaxN, kRootThreads, 0, s, ws);
+cudaError_t launch_prep(const Ws& ws, cudaStream_t s) {
+  return launch_dependent(k_prep, 1, kPrepThreads, prep_smem_cap(ws.cap), s, ws);
+}
+// the core SVD and the operator update after k_prep: k_roots, k_zhat, k_vectors, k_apply
+cudaError_t launch_small_tail(const Ws& ws, cudaStream_t s) {
+  cudaError_t e = launch_dependent(k_roots, kMaxN, kRootThreads, 0, s, ws);
   if (e == cudaSuccess) e = launch_dependent(k_zhat, kMaxN + 1, kZhatThreads, 0, s, ws);
   if (e == cudaSuccess) e = launch_dependent(k_vectors, kMaxN, kVecThreads, 0, s, ws);
   if (e == cudaSuccess) e = launch_dependent(k_apply, kMaxN, kApplyThreads, (size_t)kApplySmem, s, ws);
+  return e;
+}
+cudaError_t launch_small(const Ws& ws, cudaStream_t s) {
+  cudaError_t e = launch_prep(ws, s);
+  if (e == cudaSuccess) e = launch_small_tail(ws, s);
   return e;
 }
 

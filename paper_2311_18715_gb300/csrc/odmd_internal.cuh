@@ -90,6 +90,7 @@ struct Ctl {
   int eig_valid;    // eigen-cache matches the committed state
   int eig_r;        // rank the eigen-cache was built for
   int scale_exp;    // the core matrix is scaled by 2^-scale_exp for the secular solve
+  int pipe_flag;    // 1: the update in flight compacts (a pipelined next tall pass must wait for it)
   double thr;       // tau * max(sigma_1, ||c||)
   double rho0;      // norm of the part of c outside span(L0)
   double rho;       // norm of the part of c outside span(L)
@@ -556,6 +557,9 @@ int tall_smem_bytes(int prec);
 int stages_a(int prec, int cap);  // pass A pipeline depth for this storage format and cap
 // small.cu
 cudaError_t launch_small(const Ws& ws, cudaStream_t s);
+cudaError_t launch_prep(const Ws& ws, cudaStream_t s);        // k_prep alone
+cudaError_t launch_small_tail(const Ws& ws, cudaStream_t s);  // k_roots .. k_apply
+cudaError_t launch_pass_a_sel(const Ws& ws, int sel, cudaStream_t s);  // pipelined pass A (tall.cu)
 cudaError_t prepare_refine();
 cudaError_t launch_norm_ratio(const Ws& ws, const void* r, const void* b, cudaStream_t s);  // sum r^2, sum b^2 -> out2
 cudaError_t launch_refine(const Ws& ws, int cur, cudaStream_t s);  // Gram pass + small refinement

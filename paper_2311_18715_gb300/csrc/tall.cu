@@ -544,8 +544,13 @@ __device__ void fold_pass_a(const Ws& ws, const StateBuf& st, int r0) {
   }
 }
 
+// sel < 0: the committed state and snapshot buffers (Ctl::cur, Ctl::cur_c).  sel >= 0 (the
+// pipelined update, which runs this pass beside the previous update's SVD, before that
+// update commits): state sel & 1, snapshot buffers (sel >> 1) & 1, and a gate sel >> 2: 0 run,
+// 1 return at once if the previous update compacts (Ctl::pipe_flag; the pass then runs again
+// after the compaction with gate 2), 2 run only if it compacts.
 template <int ST>
-__device__ __forceinline__ void pass_a_body(const Ws& ws, CtaPos cp, int cta0, int fold) {
+__device__ __forceinline__ void pass_a_body(const Ws& ws, CtaPos cp, int cta0, int fold, int sel = -1) {
   pdl_wait();
   using T = Traits<ST>;
   using stored_t = typename T::stored_t;
@@ -554,7 +559,16 @@ __device__ __forceinline__ void pass_a_body(const Ws& ws, CtaPos cp, int cta0, i
   constexpr int kCS = (ST == ST_BF16) ? 1 : 2;      // chunks a lane owns in the column sums
   extern __shared__ __align__(1024) unsigned char smem[];
   Ctl* ctl = ws.ctl;
-  const int cur = ctl->cur, curc = ctl->cur_c;
+  int cur, curc;
+  if (sel < 0) {
+    cur = ctl->cur;
+    curc = ctl->cur_c;
+  } else {
+    const int gate = sel >> 2, compacts = ctl->pipe_flag;
+    if ((gate == 1 && compacts) || (gate == 2 && !compacts)) return;  // uniform over the grid
+    cur = sel & 1;
+    curc = (sel >> 1) & 1;
+  }
   const StateBuf st = ws.st[cur];
   const int r0 = st.hdr->r0;
   const int pend = st.hdr->pend;  // column p = r0 - 1 is formed here
@@ -858,6 +872,10 @@ __device__ __forceinline__ void pass_a_body(const Ws& ws, CtaPos cp, int cta0, i
 template <int ST>
 __global__ void __launch_bounds__(kThreadsA, 1) k_pass_a(const __grid_constant__ Ws ws, int cta0, int fold) {
   pass_a_body<ST>(ws, cta_single(), cta0, fold);
+}
+template <int ST>
+__global__ void __launch_bounds__(kThreadsA, 1) k_pass_a_sel(const __grid_constant__ Ws ws, int sel) {
+  pass_a_body<ST>(ws, cta_single(), 0, 1, sel);
 }
 template <int ST>
 __global__ void __launch_bounds__(kThreadsA, 1) k_pass_a_batch(const __grid_constant__ BatchTab t) {
@@ -1463,18 +1481,21 @@ cudaError_t prepare_tall(const Ws& ws) {
   switch (p) {
     case ST_DD:
       if ((e = prep_attr(k_pass_a<ST_DD>, sa))) return e;
+      if ((e = prep_attr(k_pass_a_sel<ST_DD>, sa))) return e;
       if ((e = prep_attr(k_pass_b<ST_DD, false>, sb))) return e;
       if ((e = prep_attr(k_pass_b<ST_DD, true>, sb))) return e;
       if ((e = prep_attr(k_rollout<ST_DD, false>, sr))) return e;
       return prep_attr(k_rollout<ST_DD, true>, sr);
     case ST_F32:
       if ((e = prep_attr(k_pass_a<ST_F32>, sa))) return e;
+      if ((e = prep_attr(k_pass_a_sel<ST_F32>, sa))) return e;
       if ((e = prep_attr(k_pass_b<ST_F32, false>, sb))) return e;
       if ((e = prep_attr(k_pass_b<ST_F32, true>, sb))) return e;
       if ((e = prep_attr(k_rollout<ST_F32, false>, sr))) return e;
       return prep_attr(k_rollout<ST_F32, true>, sr);
     default:
       if ((e = prep_attr(k_pass_a<ST_BF16>, sa))) return e;
+      if ((e = prep_attr(k_pass_a_sel<ST_BF16>, sa))) return e;
       if ((e = prep_attr(k_pass_b<ST_BF16, false>, sb))) return e;
       if ((e = prep_attr(k_pass_b<ST_BF16, true>, sb))) return e;
       if ((e = prep_attr(k_rollout<ST_BF16, false>, sr))) return e;
@@ -1512,6 +1533,19 @@ cudaError_t launch_pass_a(const Ws& ws, cudaStream_t s) {
       return launch_blocks(k_pass_a<ST_F32>, &k_fold_a, kThreadsA, kThreadsA, sm, ws, s);
     default:
       return launch_blocks(k_pass_a<ST_BF16>, &k_fold_a, kThreadsA, kThreadsA, sm, ws, s);
+  }
+}
+
+// pass A of a pipelined update (one launch, no row shards): see pass_a_body for sel
+cudaError_t launch_pass_a_sel(const Ws& ws, int sel, cudaStream_t s) {
+  const int sm = smem_a(ws.prec, ws.cap);
+  switch (ws.prec) {
+    case ST_DD:
+      return launch_dependent(k_pass_a_sel<ST_DD>, ws.gridA, kThreadsA, sm, s, ws, sel);
+    case ST_F32:
+      return launch_dependent(k_pass_a_sel<ST_F32>, ws.gridA, kThreadsA, sm, s, ws, sel);
+    default:
+      return launch_dependent(k_pass_a_sel<ST_BF16>, ws.gridA, kThreadsA, sm, s, ws, sel);
   }
 }
 

@@ -27,7 +27,7 @@ class OnlineDMD:
     def __init__(self, n: int, r_max: int, prec: str = "fp64", slack: int = 16,
                  trunc_tol: float = 1e-10, check_tol: float = 1e-5, refine_every: int = 0,
                  stream: torch.cuda.Stream | None = None, device: torch.device | int | None = None,
-                 tensor_cores: bool = True):
+                 tensor_cores: bool = True, pipeline: bool = True):
         if prec not in PREC:
             raise ValueError(f"prec must be one of {sorted(PREC)}")
         self._lib = load_library()
@@ -44,7 +44,7 @@ class OnlineDMD:
         cfg.check_tol = float(check_tol)
         cfg.prec = PREC[prec]
         cfg.refine_every = int(refine_every)
-        cfg.flags = 0 if tensor_cores else 1  # ODMD_CUDA_CORES
+        cfg.flags = (0 if tensor_cores else 1) | (0 if pipeline else 2)  # ODMD_CUDA_CORES, ODMD_NO_PIPELINE
         self.cfg = cfg
         nbytes = C.c_size_t()
         check(self._lib, self._lib.odmd_footprint(C.byref(cfg), C.byref(nbytes)))

@@ -40,9 +40,9 @@ int main(void) {
   EXPECT(odmd_footprint(&cfg, &small) == ODMD_ERR_ARG);
   EXPECT(odmd_config_default(NULL, 10, 8) == ODMD_ERR_ARG);
   EXPECT(odmd_config_default(&cfg, 1000, 8) == ODMD_OK);
-  cfg.flags = ODMD_CUDA_CORES;
-  EXPECT(odmd_footprint(&cfg, &small) == ODMD_OK);       /* the one defined flag */
-  cfg.flags = 2u;
+  cfg.flags = ODMD_CUDA_CORES | ODMD_NO_PIPELINE;
+  EXPECT(odmd_footprint(&cfg, &small) == ODMD_OK);       /* the two defined flags */
+  cfg.flags = 4u;
   EXPECT(odmd_footprint(&cfg, &small) == ODMD_ERR_ARG);  /* unknown bits */
   EXPECT(odmd_footprint(NULL, &small) == ODMD_ERR_ARG);
 

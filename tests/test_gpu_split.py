@@ -205,3 +205,36 @@ def test_tensor_core_compaction_fp32_storage():
                        ref.predict(ts).T)
     assert np.max(_rel(got, base)) < 1e-5, np.max(_rel(got, base))
     assert np.max(_rel(got, want)) < 1e-5, np.max(_rel(got, want))
+
+
+@pytest.mark.parametrize("prec,r,sl", [("fp64", 40, 16), ("fp64", 6, 2), ("fp32", 24, 8)])
+def test_pipelined_updates_equal_serial_updates(prec, r, sl):
+    """Pipelined updates (an update's core SVD and operator update beside the next update's
+    pass over the basis, the default) against updates run one after another
+    (ODMD_NO_PIPELINE): bitwise the same singular values, counts, basis and predictions,
+    read back at several points of the stream (each read settles the pending update), over
+    stretches that compact (slack 2) and that do not, and after a checkpoint round trip."""
+    import paper_2311_18715_gb300 as pkg
+
+    X = (WakeField(128, 64, sigma=1e-6, seed=4).snapshots(0, 90) if r == 40 else
+         PlantedModes(8192, sigma=1e-6, seed=4).snapshots(0, 90))
+    a = pkg.OnlineDMD(X.shape[1], r, prec=prec, slack=sl)
+    b = pkg.OnlineDMD(X.shape[1], r, prec=prec, slack=sl, pipeline=False)
+    Xd = torch.from_numpy(X).cuda().to(a.dtype)
+    for k in range(X.shape[0]):
+        a.update(Xd[k])
+        b.update(Xd[k])
+        if k in (5, 33, 34, 61, 89):
+            assert a.singular_values() == b.singular_values(), k
+            assert a.counts() == b.counts(), k
+            ts = [float(k + h) for h in range(10)]
+            assert torch.equal(a.predict(ts), b.predict(ts)), k
+            assert torch.equal(a.basis(), b.basis()), k
+    assert b.counts()[1] > 0 or sl == 16
+    c = pkg.OnlineDMD(X.shape[1], r, prec=prec, slack=sl)
+    c.load(a.save())
+    for k in range(X.shape[0] - 20, X.shape[0]):
+        a.update(Xd[k])
+        c.update(Xd[k])
+    ts = [float(100 + h) for h in range(50)]
+    assert torch.equal(a.predict(ts), c.predict(ts))
