@@ -926,11 +926,15 @@ __global__ void __launch_bounds__(kVecThreads) k_vectors_batch(const __grid_cons
 //   S' = sigma'[0:rnew] (unscaled);  a' = L0'^T x
 // ---------------------------------------------------------------------------------------
 constexpr int kApplyThreads = 256;
-// shared regions of the bulk-staged arrays of k_apply, in doubles (even: 16-byte aligned)
-constexpr int kApplyRegM = kMaxR * kMaxR + 2;
-constexpr int kApplyRegQ = kMaxR * (kMaxCap + 1) + 2;
-constexpr int kApplyRegU = kMaxR * kMaxN + 2;
-static_assert(kApplyRegM % 2 == 0 && kApplyRegQ % 2 == 0 && kApplyRegU % 2 == 0, "16-byte aligned regions");
+// shared regions of the bulk-staged arrays of k_apply, in doubles: one double longer than the
+// array, rounded up to an even count (16-byte aligned), for the handle's r_max and cap
+__host__ __device__ constexpr int apply_reg(int n) { return (n + 3) & ~1; }
+__host__ __device__ constexpr int apply_reg_m(int rm) { return apply_reg(rm * rm); }
+__host__ __device__ constexpr int apply_reg_q(int rm, int cap) { return apply_reg(rm * (cap + 1)); }
+__host__ __device__ constexpr int apply_reg_u(int rm) { return apply_reg(rm * kMaxN); }
+__host__ __device__ constexpr int apply_smem(int rm, int cap) {
+  return (int)sizeof(double) * (apply_reg_m(rm) + apply_reg_q(rm, cap) + apply_reg_u(rm));
+}
 
 __device__ __forceinline__ int count4(int sub, int n) { return n > sub ? (n - sub + 3) >> 2 : 0; }
 
@@ -957,9 +961,9 @@ __device__ __forceinline__ void apply_body(const Ws& ws, CtaPos cp) {
   // (regions of an even number of doubles, each one longer than its array), the short
   // vectors by 8-byte asynchronous copies
   extern __shared__ __align__(16) double asm_[];
-  double* sM = bulk_dst(asm_, st.M);                               // [k][i], ld rm
-  double* sQ = bulk_dst(asm_ + kApplyRegM, st.Q);                  // [k][i], ld qld
-  double* sU = bulk_dst(asm_ + kApplyRegM + kApplyRegQ, ws.sm.U);  // [i][k], ld kMaxN
+  double* sM = bulk_dst(asm_, st.M);                                           // [k][i], ld rm
+  double* sQ = bulk_dst(asm_ + apply_reg_m(rm), st.Q);                         // [k][i], ld qld
+  double* sU = bulk_dst(asm_ + apply_reg_m(rm) + apply_reg_q(rm, cap), ws.sm.U);  // [i][k], ld kMaxN
   __shared__ double v[kMaxN], u[kMaxN], bv[kMaxN], qcol[kMaxCap + 1];
   __shared__ double sw[kMaxN], srl[kMaxN], srf[kMaxN], sqn[kMaxCap + 1], syx[kMaxCap + 1];
   __shared__ __align__(8) uint64_t sbar;
@@ -1106,8 +1110,9 @@ static int prep_smem_cap(int cap) {
   return (int)sizeof(double) * (qld * kMaxR + 2 + 3 * qld + 2 * kMaxN);
 }
 
-// staged M, Q and U of k_apply (largest sizes, each region one double longer, kept even)
-constexpr int kApplySmem = (int)sizeof(double) * (kApplyRegM + kApplyRegQ + kApplyRegU);
+// staged M, Q and U of k_apply at the largest sizes (a batch's launch); a single handle's
+// launch asks for its own r_max and cap only (apply_smem)
+constexpr int kApplySmem = apply_smem(kMaxR, kMaxCap);
 
 cudaError_t prepare_core() {
   cudaError_t e = cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, prep_smem_cap(kMaxCap));
@@ -1145,7 +1150,7 @@ cudaError_t launch_small_tail(const Ws& ws, cudaStream_t s) {
   cudaError_t e = launch_dependent(k_roots, kMaxN, kRootThreads, 0, s, ws);
   if (e == cudaSuccess) e = launch_dependent(k_zhat, kMaxN + 1, kZhatThreads, 0, s, ws);
   if (e == cudaSuccess) e = launch_dependent(k_vectors, kMaxN, kVecThreads, 0, s, ws);
-  if (e == cudaSuccess) e = launch_dependent(k_apply, kMaxN, kApplyThreads, (size_t)kApplySmem, s, ws);
+  if (e == cudaSuccess) e = launch_dependent(k_apply, kMaxN, kApplyThreads, (size_t)apply_smem(ws.rmax, ws.cap), s, ws);
   return e;
 }
 cudaError_t launch_small(const Ws& ws, cudaStream_t s) {

@@ -373,6 +373,10 @@ constexpr int kMaxStagesA = ODMD_PASS_A_MAX_STAGES;
 constexpr int kBarBytesA = (8 * kMaxStagesA + 15) / 16 * 16;  // one barrier per stage
 static_assert((kMaxCap + 8) * 4 % 16 == 0, "pass A coefficient arrays must stay 16-byte aligned");
 constexpr int kSmemBudget = 227 * 1024 - 2048;  // dynamic shared memory per CTA, less the static part
+// pass A's budget: enough stages to cover DRAM latency (~45 KB in flight per SM at the HBM
+// rate) while leaving room on the SM for a CTA of the previous update's k_apply, which runs
+// beside it in a pipelined update
+constexpr int kSmemBudgetA = 168 * 1024;
 constexpr int kCo = 128;  // length of a coefficient array: zero past r0, so chunk groups may overrun
 
 // one stage: 32 whole rows (the full row pitch) of each basis plane
@@ -1432,7 +1436,7 @@ static int stage_a_of(int prec, int cap) {
 // more HBM reads in flight; a stage is held until its compute warp is done with it)
 int stages_a(int prec, int cap) {
   const int sz = stage_a_of(prec, cap);
-  int n = (kSmemBudget - smem_a_fixed()) / sz;
+  int n = (kSmemBudgetA - 2048 - smem_a_fixed()) / sz;
   if (n > kMaxStagesA) n = kMaxStagesA;
   return n < 2 ? 2 : n;
 }
