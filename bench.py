@@ -44,7 +44,7 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernels
 # (dram__bytes_read.sum + dram__bytes_write.sum); pass A copies whole rows, so its traffic
 # does not depend on r0.  Kernels without a capture report null.
-TRAFFIC = {"pass_a": 214.7e6}
+TRAFFIC = {"pass_a": 207.6e6}
 WORKLOAD = (f"cylinder-wake field {NX}x{NY}x3 (n={N}), r_max={R_MAX}, FP64 accuracy, "
             f"{BLOCK}-snapshot blocks: {BLOCK} updates + {BLOCK}-state rollout + 1 check")
 
