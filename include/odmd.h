@@ -110,7 +110,10 @@ odmd_status odmd_create(const odmd_config* cfg, void* workspace_dev, size_t byte
  * The first call stores u^0; every later call adds the pair (u^{k-1}, u^k): U^- gains
  * u^{k-1}, U^+ gains u^k, and the model is updated by one rank-1 step (Sec. 2.3).
  * The snapshot is copied into the workspace on the stream, so the caller may reuse
- * its buffer once the stream has passed this call. */
+ * its buffer once the stream has passed this call.  Unless ODMD_NO_PIPELINE is set, the
+ * last part of the update (core SVD, operator update, compaction) is enqueued with the next
+ * update, beside its pass over the basis, or by the next other call on the handle; the
+ * model any call observes is the same either way. */
 odmd_status odmd_update(odmd_t h, const void* x_dev);
 
 /* Predict u(t_j) = Re(Phi Lambda^{t_j} Phi^+ u^0) for j < k (Sec. 2.3).  t_host: k step

@@ -1,13 +1,15 @@
-// Tall x small products of the double-float basis on the tensor cores, exact to the
-// double-float level through a split of both operands into 8-bit digits (Ozaki's scheme: an
-// error-free splitting into slices whose products a lower-precision unit sums exactly):
+// Tall x small products of the basis (double-float, or FP32 storage) on the tensor cores,
+// exact to the double-float level through a split of both operands into 8-bit digits
+// (Ozaki's scheme: an error-free splitting into slices whose products a lower-precision unit
+// sums exactly):
 //   rollout     X = L0 C: u(t) = Phi Lambda^t b for many t at once (Sec. 2.3) is the tall
 //               N x r0 basis times a small r0 x k coefficient block; X in doubles;
 //   compaction  L0 <- [L0 j0] Q_B of the product-form update (Sec. 2.3, Brand's rank-1
 //               append kept as L = L0 Q): the new column j0 = (e - L0 s) / rho0 is formed per
 //               row from the stored residual, and the product is written back in place.
 //
-// Each row i of L0 (double-float hi + lo, |a_ik| < 2^e_i) is put on the fixed-point grid
+// Each row i of L0 (double-float hi + lo, or an FP32 value with lo = 0; |a_ik| < 2^e_i) is
+// put on the fixed-point grid
 // 2^(e_i - 54): the integer I = round(hi 2^(54 - e_i)) + round(lo 2^(54 - e_i)) (within one
 // unit, 2^-53 of the row maximum; |I| < 2^54).  Adding 0x80 to each of its seven bytes makes
 // every byte b of I + 0x80808080808080 a balanced digit d = b - 128, |d| <= 128 (exact in
@@ -16,8 +18,9 @@
 // grid 2^(f_j - 54).  Products of digits with s + t = g are integers on the common grid
 // 2^(e_i + f_j - 108 + 8 (14 - g)): the 28 digit pairs with g <= 8 are bfloat16 products
 // (tcgen05.mma kind::f16, M = 128, N = 64, K = 16) into seven FP32 accumulators in tensor
-// memory, one per g.  A group adds at most 7 K products of |d d'| <= 2^14 with K <= 64, below
-// 2^24, so every partial sum is an integer the FP32 accumulator holds exactly; pairs with
+// memory, one per g.  A group adds at most 7 K products of |d d'| <= 2^14 with K <= 64
+// (double-float storage) or 96 (FP32 storage), below 2^24, so every partial sum is an integer
+// the FP32 accumulator holds exactly; pairs with
 // g >= 9 are below 2^-48 K of max|a_i| max|c_j| and are left out.  The epilogue adds the
 // seven group sums, scaled by 2^(8 (8 - g)) (all exact floats), in double-float (two
 // outputs per FP32x2 instruction) and scales the result by 2^(e_i + f_j - 60), which is the
@@ -27,7 +30,7 @@
 //
 // One persistent CTA per SM (the seven accumulators take 448 of the SM's 512 tensor-memory
 // columns) with two roles.  Sixteen worker warps: C's digits once per CTA; for each 128-row
-// tile of L0 (both planes staged by two bulk copies), four threads per row form its digits
+// tile of L0 (its planes staged by bulk copies), four threads per row form its digits
 // one 16-column K chunk at a time into one of two buffers (the K-major core-matrix layout
 // the descriptors describe, tc.cuh), and read the accumulators in the epilogue.  One issuer
 // warp: the tile copies and, per chunk, the 28 MMAs and their commit.  They hand over by

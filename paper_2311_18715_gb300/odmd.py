@@ -21,7 +21,9 @@ class OnlineDMD:
 
     update(x) appends u^k; predict(ts) returns u(t) = Re(Phi Lambda^t Phi^+ u^0) for the
     step counts in ts (rows of the result); check(t, x_fom) is the relative-L2
-    credibility test of the hybrid FOM/ROM loop (Sec. 2.2).
+    credibility test of the hybrid FOM/ROM loop (Sec. 2.2).  tensor_cores=False keeps
+    rollouts and compactions on the CUDA cores (ODMD_CUDA_CORES); pipeline=False runs each
+    update to its end before the next (ODMD_NO_PIPELINE), with bitwise the same results.
     """
 
     def __init__(self, n: int, r_max: int, prec: str = "fp64", slack: int = 16,
