@@ -758,7 +758,14 @@ odmd_status odmd_create(const odmd_config* cfg, void* workspace_dev, size_t byte
   return ODMD_OK;
 }
 
-odmd_status odmd_update(odmd_t h, const void* x_dev) {
+// one update; `may_pipe`: it may leave its tail to the next call (odmd_update).  The
+// hybrid loops, which read the model right after every update, run it to its end instead:
+// a pipelined update there would only add the settle's launch.
+static odmd_status update_impl(odmd_t h, const void* x_dev, bool may_pipe);
+
+odmd_status odmd_update(odmd_t h, const void* x_dev) { return update_impl(h, x_dev, true); }
+
+static odmd_status update_impl(odmd_t h, const void* x_dev, bool may_pipe) {
   if (!h) return fail(nullptr, ODMD_ERR_ARG, "handle is NULL");
   if (!x_dev) return fail(h, ODMD_ERR_ARG, "x is NULL");
   if (h->nsnap == 0) {
@@ -769,7 +776,7 @@ odmd_status odmd_update(odmd_t h, const void* x_dev) {
     return ODMD_OK;
   }
   bool graphed = false;
-  if (h->use_graphs && h->pipe && !h->prof_on && h->ws.shards == 1) {
+  if (may_pipe && h->use_graphs && h->pipe && !h->prof_on && h->ws.shards == 1) {
     // pipelined: this update's ingest and pass A beside the last update's tail
     const int tail = h->tail_pending ? 1 : 0;
     if (odmd_status st = build_pipe_graph(h, h->cur_h, h->curc_h, tail)) return st;
@@ -1139,7 +1146,7 @@ odmd_status odmd_hybrid_step(odmd_t h, const void* x_fom_dev, double tol, void* 
        "copy the FOM state");
   }
   // the state taken, accepted prediction or FOM state, joins the snapshot stream
-  if (odmd_status s = odmd_update(h, state_out_dev)) return s;
+  if (odmd_status s = update_impl(h, state_out_dev, false)) return s;
   if (accepted) *accepted = acc;
   if (rel_err) *rel_err = err;
   return ODMD_OK;
@@ -1179,7 +1186,7 @@ odmd_status odmd_hybrid_step_residual(odmd_t h, odmd_residual_fn residual, odmd_
   if (!acc && fom(user, step, state_out_dev, h->stream) != 0)
     return fail(h, ODMD_ERR_STATE, "FOM callback reported a failure");
   // the state taken, accepted prediction or FOM state, joins the snapshot stream
-  if (odmd_status s = odmd_update(h, state_out_dev)) return s;
+  if (odmd_status s = update_impl(h, state_out_dev, false)) return s;
   if (accepted) *accepted = acc;
   if (rel_res) *rel_res = rel;
   return ODMD_OK;
