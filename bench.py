@@ -24,7 +24,6 @@ import math
 import os
 import statistics
 import subprocess
-import tempfile
 import sys
 import time
 
@@ -104,34 +103,64 @@ CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.ac
 
 
 class ClockSampler:
+    """nvidia-smi samples (every 50 ms) stamped on arrival; only those taken while a window
+    is open (the timed regions) count.  start() returns once the first sample has arrived,
+    so that sampling is live before the timed work begins, and opens a window."""
+
     def __init__(self, gpu_index: int):
         self.proc = None
         self.gpu = gpu_index
-        self.path = os.path.join(tempfile.gettempdir(), f"odmd_clocks_{os.getpid()}.csv")
+        self.rows = []      # (monotonic time, fields)
+        self.windows = []   # [t_open, t_close or None]
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.monotonic(), [p.strip() for p in line.split(",")]))
 
     def start(self):
+        import threading
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={CLOCK_QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
-                                         stdout=self.f, stderr=subprocess.DEVNULL)
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        t0 = time.monotonic()
+        while not self.rows and time.monotonic() - t0 < 5.0 and self.proc.poll() is None:
+            time.sleep(0.01)
+        self.resume()
+
+    def pause(self):
+        if self.windows and self.windows[-1][1] is None:
+            self.windows[-1][1] = time.monotonic()
+
+    def resume(self):
+        if not self.windows or self.windows[-1][1] is not None:
+            self.windows.append([time.monotonic(), None])
 
     def stop(self) -> dict:
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.pause()
+        time.sleep(0.06)  # the sample that closes the last window
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        self.f.close()
+        self.thread.join(timeout=5)
+        inside = [f for t, f in self.rows if any(a <= t <= b for a, b in self.windows)]
+        if not inside:  # windows shorter than the interval: the first sample after each opens
+            for a, _ in self.windows:
+                after = [f for t, f in self.rows if t >= a]
+                if after:
+                    inside.append(after[0])
         sms, maxes, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
+        for parts in inside:
             if len(parts) < 9:
                 continue
             try:
@@ -144,7 +173,8 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sms) if sms else None,
                 "sm_max_mhz": max(maxes) if maxes else None,
-                "reasons": sorted(reasons), "samples": len(sms)}
+                "reasons": sorted(reasons), "samples": len(sms),
+                "timed_s": sum(b - a for a, b in self.windows)}
 
 
 # ------------------------------------------------------------------ CPU oracle leg
@@ -371,7 +401,7 @@ def run_ours(args) -> None:
     torch.cuda.synchronize()
     barrier(dist)
     torch.cuda.synchronize()
-    clocks = sampler.stop()
+    sampler.pause()
     prof = model.profile_read()
     model.profile(False)
     prof_step_ms = [evs[0][0].elapsed_time(evs[-1][1]) for evs in prof_steps]
@@ -459,11 +489,13 @@ def run_ours(args) -> None:
         e2e_step(blk)
     torch.cuda.synchronize()
     barrier(dist)
+    sampler.resume()
     t0 = time.perf_counter()
     for blk in range(K):
         e2e_step(W + blk)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    clocks = sampler.stop()
     barrier(dist)
     e2e_value = sum_over_ranks(float(BLOCK * K), dist, dev) / e2e_s
 

@@ -5,6 +5,7 @@ import json
 import os
 import subprocess
 import sys
+import time
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -58,36 +59,52 @@ def test_reference_arm_under_torchrun_prints_once():
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
 
 
-def test_clock_sampler_reads_median_clock_and_throttle_reasons(tmp_path):
+def test_clock_sampler_reads_median_clock_and_throttle_reasons(tmp_path, monkeypatch):
     """The clocks object of the JSON line: median SM clock under load, the maximum, and every
-    throttle reason seen active (the names the rejection rule checks)."""
+    throttle reason seen active (the names the rejection rule checks), over the samples taken
+    while the timed regions run.  A stand-in nvidia-smi prints a sample every 20 ms from a
+    state file; throttled samples printed while the sampler is paused are not counted."""
     sys.path.insert(0, ROOT)
     import bench
 
-    class _Proc:
-        def terminate(self):
-            pass
-
-        def wait(self, timeout=None):
-            return 0
+    state = tmp_path / "state"
+    state.write_text("good")
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text(
+        "#!" + sys.executable + "\n"
+        "import sys, time\n"
+        "k = 0\n"
+        "while True:\n"
+        f"    s = open({str(state)!r}).read().strip()\n"
+        "    if s == 'bad':\n"
+        "        print('0, 1500, 2070, 1400.0, 0x8, Active, Not Active, Not Active, Not Active', flush=True)\n"
+        "    elif k % 3 == 1:\n"
+        "        print('0, 1980, 2070, 1390.5, 0x4, Not Active, Not Active, Not Active, Active', flush=True)\n"
+        "    else:\n"
+        "        print('0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active', flush=True)\n"
+        "    print('garbled line', flush=True)\n"
+        "    k += 1\n"
+        "    time.sleep(0.02)\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", str(tmp_path) + os.pathsep + os.environ["PATH"])
 
     s = bench.ClockSampler(0)
-    s.path = str(tmp_path / "clocks.csv")
-    lines = [
-        "0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
-        "0, 1980, 2070, 1390.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
-        "0, 2070, 2070, 1200.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
-        "garbled line",
-        "0, 1500, 2070, 1400.0, 0x0000000000000008, Active, Not Active, Not Active, Not Active",
-    ]
-    with open(s.path, "w") as f:
-        f.write("\n".join(lines) + "\n")
-    s.proc = _Proc()
-    s.f = open(os.devnull, "w")
+    s.start()
+    assert s.rows, "start() returns once the first sample is in"
+    time.sleep(0.4)
+    s.pause()
+    state.write_text("bad")
+    time.sleep(0.3)
+    state.write_text("good")
+    time.sleep(0.2)
+    s.resume()
+    time.sleep(0.4)
     c = s.stop()
-    assert c["samples"] == 4
-    assert c["sm_mhz"] == 2025.0 and c["sm_max_mhz"] == 2070.0
-    assert c["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    assert c["samples"] >= 10
+    assert c["sm_mhz"] in (1980.0, 2025.0, 2070.0) and c["sm_max_mhz"] == 2070.0
+    assert c["reasons"] == ["sw_power_cap"]
+    assert any(len(f) > 1 and f[1] == "1500" for _, f in s.rows), "throttled samples were printed while paused"
+    assert 0.7 < c["timed_s"] < 1.5
 
 
 def test_oracle_child_times_whole_blocks_with_the_thread_count_set():
