@@ -177,12 +177,19 @@ def test_tensor_core_rollout_fp32_storage(case):
     La, Lb = tc.basis().double().cpu().numpy(), cc.basis().double().cpu().numpy()
     assert La.shape == Lb.shape
     assert np.max(np.abs(La - Lb)) <= 2.0 ** -23 * np.max(np.abs(Lb)), np.max(np.abs(La - Lb))
-    # with the same stored column, the two rollouts agree to the double-float level
+    # with the same stored column, the two rollouts agree to 1e-12 of each horizon's scale
+    # before their outputs are rounded to the FP32 of the snapshots: every element within
+    # that plus one FP32 unit of itself (the two sums may lie on either side of a rounding
+    # boundary)
     tc2 = pkg.OnlineDMD(tc.n, tc.r_max, prec="fp32", slack=sl, tensor_cores=True)
     tc2.load(twin.save())
     ts = [float(k + h) for h in range(50)]
-    got, base = tc2.predict(ts).double().cpu().numpy(), cc.predict(ts).double().cpu().numpy()
-    assert np.max(_rel(got, base)) < 1e-12, np.max(_rel(got, base))
+    got, base = tc2.predict(ts).cpu().numpy(), cc.predict(ts).cpu().numpy()
+    assert got.dtype == base.dtype == np.float32
+    d = np.abs(got.astype(np.float64) - base.astype(np.float64))
+    scale = np.max(np.abs(base), axis=1, keepdims=True).astype(np.float64)
+    bound = np.spacing(np.abs(base)).astype(np.float64) + 1e-12 * scale
+    assert np.all(d <= bound), np.max(d / bound)
 
 
 def test_tensor_core_compaction_fp32_storage():
