@@ -6,6 +6,9 @@
 //
 //   k_prep     reduced tall sums -> projections p = L^T c, w = L^T x, the new direction,
 //              the core matrix K = [[diag(S), p], [0, rho]] and its deflated secular problem
+//              (a pipelined update runs it in two launches: k_prep_a, the append decision
+//              and the next state's inputs of the next pass A; k_prep_b, the rest, at the
+//              head of the tail that runs beside that pass)
 //   k_roots    one CTA per singular value of K: root of the secular equation
 //   k_zhat     one CTA per pole: Loewner weights; one extra CTA orders the values
 //   k_vectors  one CTA per kept singular pair: left/right singular vectors of K
@@ -93,7 +96,17 @@ __device__ __forceinline__ void bulk_wait(uint64_t* bar, int* status) {
 // ---------------------------------------------------------------------------------------
 constexpr int kPrepThreads = 256;
 
+__device__ __forceinline__ void prep_rest(const Ws& ws, const StateBuf& st, int r, int r0, int r0e, double thr,
+                                          const double* sQ, const double* sS, const double* ac, const double* yx,
+                                          double* z, double* p, double* p2);
+
+// PART 1: the append decision and the next state's inputs of the next tall pass (all a
+// pipelined next pass A waits for); ac = a + L0^T e and y (with the appended coordinate)
+// are left in ws.sm.ac / ws.sm.yext, since the next pass A overwrites the reduced sums.
+// PART 2: the rest, from those (the head of a pipelined update's tail).  PART 3: both.
+template <int PART>
 __device__ __forceinline__ void prep_body(const Ws& ws, CtaPos cp) {
+  constexpr bool kA = (PART & 1) != 0, kB = (PART & 2) != 0;
   extern __shared__ __align__(16) double psm[];
   Ctl* ctl = ws.ctl;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -106,41 +119,49 @@ __device__ __forceinline__ void prep_body(const Ws& ws, CtaPos cp) {
   double* z = yx + qld;
   double* p = z + qld;
   double* p2 = p + kMaxN;
-  __shared__ double red8[16];
   __shared__ double thr_s;
   __shared__ int append_s;
-  __shared__ double dsc[kMaxN], zsc[kMaxN], sS[kMaxN];
-  __shared__ int defl[kMaxN];
+  __shared__ double sS[kMaxN];
   __shared__ __align__(8) uint64_t sbar;
   const float2* red = ws.sm.red;
 
-  if (tid == 0) {
-    mbar_init(&sbar, 1);
-    mbar_fence_init();
-    const BulkSpan sp = bulk_span(st.Q, r * qld);
-    mbar_arrive_expect_tx(&sbar, 8u * (uint32_t)sp.body);
-    bulk_issue(sQ, st.Q, sp, &sbar);
+  if constexpr (kB) {
+    if (tid == 0) {
+      mbar_init(&sbar, 1);
+      mbar_fence_init();
+      const BulkSpan sp = bulk_span(st.Q, r * qld);
+      mbar_arrive_expect_tx(&sbar, 8u * (uint32_t)sp.body);
+      bulk_issue(sQ, st.Q, sp, &sbar);
+    }
+    if (tid == 32) bulk_ends(sQ, st.Q, r * qld);
+    stage_doubles(sS, st.S, r, tid, kPrepThreads);
+  } else {
+    if (tid == 0) sS[0] = r > 0 ? st.S[0] : 0.0;
   }
-  if (tid == 32) bulk_ends(sQ, st.Q, r * qld);
-  stage_doubles(sS, st.S, r, tid, kPrepThreads);
   // Until here only the committed state is read (written by the last kernel of the previous
   // update, which completed before pass A started), so its copies run during the wait for
-  // pass A; the reduced sums of pass A are read after it
+  // pass A; the reduced sums of pass A (or the first part's results) are read after it
   pdl_wait();
-  pdl_trigger();  // k_roots' CTAs are placed now and wait in their pdl_wait for this grid
-  for (int i = tid; i < r0; i += kPrepThreads) {
-    ac[i] = dd2d(st.a[i]) + dd2d(red[i]);
-    yx[i] = dd2d(red[r0 + i]);
+  pdl_trigger();  // the next kernel's CTAs are placed now and wait in their pdl_wait for this grid
+  if constexpr (kA) {
+    for (int i = tid; i < r0; i += kPrepThreads) {
+      ac[i] = dd2d(st.a[i]) + dd2d(red[i]);
+      yx[i] = dd2d(red[r0 + i]);
+    }
+  } else {
+    const int n_e = ctl->r0e;  // r0 + the first part's append decision
+    stage_doubles(ac, ws.sm.ac, n_e, tid, kPrepThreads);
+    stage_doubles(yx, ws.sm.yext, n_e, tid, kPrepThreads);
   }
   cp_async_wait_all();
   __syncthreads();
-  bulk_wait(&sbar, &ctl->status);
+  if constexpr (kB) bulk_wait(&sbar, &ctl->status);
   // p = Q^T ac and w = Q^T y (4 threads per column j < r; Q has r0 rows, the appended
   // coordinate lies outside span(L)); a warp without column work meanwhile decides whether
   // the residual is appended (rho0 against the truncation threshold)
   // (FP64 instructions cost the SM's FP64 pipe whether or not a lane has work, so warps
   // with no column or row skip each phase as a whole)
-  if (8 * warp < r) {
+  if (kB && 8 * warp < r) {
     const int j = tid >> 2, sub = tid & 3;
     double ap = 0.0, aw = 0.0;
     if (j < r)
@@ -158,7 +179,7 @@ __device__ __forceinline__ void prep_body(const Ws& ws, CtaPos cp) {
     }
   }
   const int dwarp = 4 * r <= kPrepThreads - 32 ? 7 : 0;
-  if (warp == dwarp) {
+  if (kA && warp == dwarp) {
     double ssq = 0.0, sy = 0.0;
     #pragma unroll 1  // a dependent chain: unrolling adds code, not speed
     for (int i = lane; i < r0; i += 32) {
@@ -193,15 +214,15 @@ __device__ __forceinline__ void prep_body(const Ws& ws, CtaPos cp) {
     }
   }
   __syncthreads();
-  const int append = append_s;
+  const int append = kA ? append_s : ctl->append;
   const int r0e = r0 + append;
-  const double thr = thr_s;
+  const double thr = kA ? thr_s : ctl->thr;
   // The next state's inputs of the next tall pass, published here rather than by k_apply so
   // that a pipelined next pass A may run beside this update's SVD: its header (all but the
   // rank; r0 too unless the update compacts, when k_apply writes it with the new rank), its
   // projection a = L0'^T x and the pending column's s.  A compacting update also sets
   // pipe_flag, on which a pipelined next pass A waits for the compaction.
-  {
+  if constexpr (kA) {
     const bool compact = r0e > ws.cap;
     const StateBuf nx = ws.st[cur ^ 1];
     if (tid == 0) {
@@ -218,7 +239,24 @@ __device__ __forceinline__ void prep_body(const Ws& ws, CtaPos cp) {
       if (append)
         for (int i = tid; i < r0; i += kPrepThreads) nx.ps[i] = red[i];
     }
+    for (int i = tid; i < r0e; i += kPrepThreads) {
+      ws.sm.ac[i] = ac[i];
+      ws.sm.yext[i] = yx[i];
+    }
   }
+  if constexpr (kB) prep_rest(ws, st, r, r0, r0e, thr, sQ, sS, ac, yx, z, p, p2);
+}
+
+// the second part of k_prep from the appended basis: z, the second Gram-Schmidt pass, rho
+// and gamma, and the secular problem
+__device__ __forceinline__ void prep_rest(const Ws& ws, const StateBuf& st, int r, int r0, int r0e, double thr,
+                                          const double* sQ, const double* sS, const double* ac, const double* yx,
+                                          double* z, double* p, double* p2) {
+  Ctl* ctl = ws.ctl;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, qld = ws.cap + 1;
+  __shared__ double red8[16];
+  __shared__ double dsc[kMaxN], zsc[kMaxN];
+  __shared__ int defl[kMaxN];
   // z = ac - Q p (rows < r0; the appended coordinate is ac itself)
   for (int base = 0; base < 4 * r0e; base += kPrepThreads) {
     if (base + 32 * warp >= 4 * r0e) continue;
@@ -298,8 +336,6 @@ __device__ __forceinline__ void prep_body(const Ws& ws, CtaPos cp) {
   const double rho = rho_s, inv_rho = inv_s;
   for (int i = tid; i < r0e; i += kPrepThreads) {
     ws.sm.qn[i] = z[i] * inv_rho;
-    ws.sm.yext[i] = yx[i];
-    if (i < r0) ws.sm.ac[i] = ac[i];
   }
   // ---- secular problem of K = [[diag(S), p], [0, rho]], n = r + 1, scaled to max < 1
   if (warp == 0) {
@@ -395,11 +431,17 @@ __device__ __forceinline__ void prep_body(const Ws& ws, CtaPos cp) {
 }
 
 __global__ void __launch_bounds__(kPrepThreads) k_prep(const __grid_constant__ Ws ws) {
-  prep_body(ws, cta_single());
+  prep_body<3>(ws, cta_single());
+}
+__global__ void __launch_bounds__(kPrepThreads) k_prep_a(const __grid_constant__ Ws ws) {
+  prep_body<1>(ws, cta_single());
+}
+__global__ void __launch_bounds__(kPrepThreads) k_prep_b(const __grid_constant__ Ws ws) {
+  prep_body<2>(ws, cta_single());
 }
 __global__ void __launch_bounds__(kPrepThreads) k_prep_batch(const __grid_constant__ BatchTab t) {
   const int i = batch_find(t, blockIdx.x);
-  prep_body(*t.ws[i], batch_pos(t, i));
+  prep_body<3>(*t.ws[i], batch_pos(t, i));
 }
 
 
@@ -1116,6 +1158,8 @@ constexpr int kApplySmem = apply_smem(kMaxR, kMaxCap);
 
 cudaError_t prepare_core() {
   cudaError_t e = cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, prep_smem_cap(kMaxCap));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_prep_a, cudaFuncAttributeMaxDynamicSharedMemorySize, prep_smem_cap(kMaxCap));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_prep_b, cudaFuncAttributeMaxDynamicSharedMemorySize, prep_smem_cap(kMaxCap));
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, kApplySmem);
   return e;
 }
@@ -1142,20 +1186,28 @@ cudaError_t launch_small_batch(const BatchTab& one, const BatchTab& per_root, co
   return e;
 }
 
+// the first part of k_prep alone: a pipelined update's last kernel (the next pass A waits
+// for it; the rest of the update runs beside that pass)
 cudaError_t launch_prep(const Ws& ws, cudaStream_t s) {
-  return launch_dependent(k_prep, 1, kPrepThreads, prep_smem_cap(ws.cap), s, ws);
+  return launch_dependent(k_prep_a, 1, kPrepThreads, prep_smem_cap(ws.cap), s, ws);
 }
-// the core SVD and the operator update after k_prep: k_roots, k_zhat, k_vectors, k_apply
-cudaError_t launch_small_tail(const Ws& ws, cudaStream_t s) {
+static cudaError_t launch_roots_to_apply(const Ws& ws, cudaStream_t s) {
   cudaError_t e = launch_dependent(k_roots, kMaxN, kRootThreads, 0, s, ws);
   if (e == cudaSuccess) e = launch_dependent(k_zhat, kMaxN + 1, kZhatThreads, 0, s, ws);
   if (e == cudaSuccess) e = launch_dependent(k_vectors, kMaxN, kVecThreads, 0, s, ws);
   if (e == cudaSuccess) e = launch_dependent(k_apply, kMaxN, kApplyThreads, (size_t)apply_smem(ws.rmax, ws.cap), s, ws);
   return e;
 }
+// the rest of an update after launch_prep: the second part of k_prep, then k_roots .. k_apply
+cudaError_t launch_small_tail(const Ws& ws, cudaStream_t s) {
+  cudaError_t e = launch_dependent(k_prep_b, 1, kPrepThreads, prep_smem_cap(ws.cap), s, ws);
+  if (e == cudaSuccess) e = launch_roots_to_apply(ws, s);
+  return e;
+}
+// the small solves of an update in one chain (k_prep whole)
 cudaError_t launch_small(const Ws& ws, cudaStream_t s) {
-  cudaError_t e = launch_prep(ws, s);
-  if (e == cudaSuccess) e = launch_small_tail(ws, s);
+  cudaError_t e = launch_dependent(k_prep, 1, kPrepThreads, prep_smem_cap(ws.cap), s, ws);
+  if (e == cudaSuccess) e = launch_roots_to_apply(ws, s);
   return e;
 }
 

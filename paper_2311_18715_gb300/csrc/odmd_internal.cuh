@@ -557,8 +557,8 @@ int tall_smem_bytes(int prec);
 int stages_a(int prec, int cap);  // pass A pipeline depth for this storage format and cap
 // small.cu
 cudaError_t launch_small(const Ws& ws, cudaStream_t s);
-cudaError_t launch_prep(const Ws& ws, cudaStream_t s);        // k_prep alone
-cudaError_t launch_small_tail(const Ws& ws, cudaStream_t s);  // k_roots .. k_apply
+cudaError_t launch_prep(const Ws& ws, cudaStream_t s);        // the first part of k_prep (pipelined)
+cudaError_t launch_small_tail(const Ws& ws, cudaStream_t s);  // the rest: k_prep part 2, k_roots .. k_apply
 cudaError_t launch_pass_a_sel(const Ws& ws, int sel, cudaStream_t s);  // pipelined pass A (tall.cu)
 cudaError_t prepare_refine();
 cudaError_t launch_norm_ratio(const Ws& ws, const void* r, const void* b, cudaStream_t s);  // sum r^2, sum b^2 -> out2
