@@ -594,7 +594,7 @@ odmd_status settle(odmd_t h) {
     if (odmd_status st = finish_graph(h, G, graph, false)) return st;
   }
   CK(h, cudaGraphLaunch(G.exec, h->stream), "update tail launch");
-  h->launches[ODMD_K_SMALL] += 4;
+  h->launches[ODMD_K_SMALL] += 5;  // k_prep_b, k_roots .. k_apply
   h->launches[ODMD_K_PASS_B] += 1;
   h->tail_pending = false;
   return ODMD_OK;
@@ -787,7 +787,7 @@ static odmd_status update_impl(odmd_t h, const void* x_dev, bool may_pipe) {
     CK(h, cudaGraphExecKernelNodeSetParams(G.exec, G.ingest, &G.kp), "graph ingest params");
     CK(h, cudaGraphLaunch(G.exec, h->stream), "pipelined update graph launch");
     h->launches[ODMD_K_PASS_A] += 1 + tail;
-    h->launches[ODMD_K_SMALL] += 1 + 4 * tail;
+    h->launches[ODMD_K_SMALL] += 1 + 5 * tail;
     h->launches[ODMD_K_PASS_B] += tail;
     h->tail_pending = true;
     graphed = true;

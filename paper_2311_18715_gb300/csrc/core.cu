@@ -119,8 +119,8 @@ __device__ __forceinline__ void prep_body(const Ws& ws, CtaPos cp) {
   double* z = yx + qld;
   double* p = z + qld;
   double* p2 = p + kMaxN;
-  __shared__ double thr_s;
-  __shared__ int append_s;
+  __shared__ double thr_s, rho0_s, cn2_s;
+  __shared__ int append_s, pairs_s, comp_s;
   __shared__ double sS[kMaxN];
   __shared__ __align__(8) uint64_t sbar;
   const float2* red = ws.sm.red;
@@ -138,14 +138,24 @@ __device__ __forceinline__ void prep_body(const Ws& ws, CtaPos cp) {
   } else {
     if (tid == 0) sS[0] = r > 0 ? st.S[0] : 0.0;
   }
+  if constexpr (kA) {
+    // the committed state's part of ac = a + L0^T e, and the header fields the next state
+    // continues from
+    for (int i = tid; i < r0; i += kPrepThreads) ac[i] = dd2d(st.a[i]);
+    if (tid == 0) {
+      pairs_s = st.hdr->pairs;
+      comp_s = st.hdr->compactions;
+      cn2_s = dd2d(st.hdr->cn2);
+    }
+  }
   // Until here only the committed state is read (written by the last kernel of the previous
   // update, which completed before pass A started), so its copies run during the wait for
   // pass A; the reduced sums of pass A (or the first part's results) are read after it
   pdl_wait();
   pdl_trigger();  // the next kernel's CTAs are placed now and wait in their pdl_wait for this grid
   if constexpr (kA) {
-    for (int i = tid; i < r0; i += kPrepThreads) {
-      ac[i] = dd2d(st.a[i]) + dd2d(red[i]);
+    for (int i = tid; i < r0; i += kPrepThreads) {  // the same thread's entry as above
+      ac[i] += dd2d(red[i]);
       yx[i] = dd2d(red[r0 + i]);
     }
   } else {
@@ -197,7 +207,7 @@ __device__ __forceinline__ void prep_body(const Ws& ws, CtaPos cp) {
       const double e2 = fmax(eta - ssq, 0.0);
       const double irho0 = e2 > 0.0 ? rsqrt(e2) : 0.0;
       const double rho0 = e2 * irho0;
-      const double cn = sqrt(dd2d(st.hdr->cn2));
+      const double cn = sqrt(cn2_s);
       const double sig1 = r > 0 ? sS[0] : 0.0;
       const double thr = ws.tau * fmax(sig1, cn);
       const int append = rho0 > thr ? 1 : 0;
@@ -211,6 +221,7 @@ __device__ __forceinline__ void prep_body(const Ws& ws, CtaPos cp) {
       }
       append_s = append;
       thr_s = thr;
+      rho0_s = rho0;
     }
   }
   __syncthreads();
@@ -226,11 +237,11 @@ __device__ __forceinline__ void prep_body(const Ws& ws, CtaPos cp) {
     const bool compact = r0e > ws.cap;
     const StateBuf nx = ws.st[cur ^ 1];
     if (tid == 0) {
-      nx.hdr->pairs = st.hdr->pairs + 1;
-      nx.hdr->compactions = st.hdr->compactions + (compact ? 1 : 0);
+      nx.hdr->pairs = pairs_s + 1;
+      nx.hdr->compactions = comp_s + (compact ? 1 : 0);
       nx.hdr->cn2 = red[2 * r0 + 2];
       nx.hdr->pend = (append && !compact) ? 1 : 0;
-      nx.hdr->pinv = append ? d2f2(1.0 / ctl->rho0) : make_float2(0.f, 0.f);
+      nx.hdr->pinv = append ? d2f2(1.0 / rho0_s) : make_float2(0.f, 0.f);
       if (!compact) nx.hdr->r0 = r0e;
       ctl->pipe_flag = compact ? 1 : 0;
     }
